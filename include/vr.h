@@ -1,0 +1,148 @@
+/*
+ * vr.h -- C ABI of the B300 Vietoris-Rips filtered-complex builder.
+ *
+ * One call builds, on the GPU, the filtered Vietoris-Rips complex of a point
+ * cloud up to simplex dimension 2 and its boundary matrix over F2:
+ *
+ *   - an edge {i,j} is present when |x_i - x_j| <= maxrad, a triangle when its
+ *     three edges are (arXiv 1809.04424, Sec. 2.1 "Homological Persistence":
+ *     the threshold acts as time, so a simplex enters with its longest edge);
+ *   - the edge lengths are ranked into integer filtration grades, the rank
+ *     matrix Eirene returns as "symmat" with per-dimension "filtration" grades
+ *     (Sec. 3; ranking is the sort permutation of Sec. 4.4).  Equal squared
+ *     distances share a grade; grade 0 is squared distance 0 and holds every
+ *     vertex; grade g >= 1 is the g-th smallest distinct positive squared
+ *     distance among the kept edges;
+ *   - each dimension's simplices are listed in (grade, vertex tuple
+ *     lexicographic) order, vertices ascending inside a simplex, a triangle's
+ *     grade being its largest edge grade;
+ *   - the boundary matrix D of Sec. 2.2 is stored per dimension k >= 1 in CSC
+ *     over F2 (no values; Sec. 4.5 works mod 2 on CSC): column j lists the
+ *     order indices of the k+1 faces of simplex j in the (k-1) order,
+ *     ascending, and colptr[j] = (k+1) * j.
+ *
+ * Distances: integer inputs use exact integer squared distances; float32
+ * inputs are ranked by the FP64 value acc = 0; for each coordinate k:
+ * t = fl(x_ik - x_jk); acc = fl(acc + fl(t*t)) (round to nearest, nothing
+ * fused), so equal ranks are bit-reproducible.  Every result is exactly that
+ * of this definition: there is no approximation in any output.
+ *
+ * Errors: every entry point returns a vr_status; on failure vr_last_error()
+ * gives a message for the calling thread and no output is produced.  Device
+ * errors that a kernel detects (bad values, range) are returned by the call
+ * that launched it, which synchronises on its stream before returning.
+ * Thread safety: calls may come from several threads; results are separate
+ * objects.  All device work is ordered on the stream passed in.
+ */
+#ifndef VR_H
+#define VR_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (same type); NULL is the legacy default stream. */
+typedef struct CUstream_st *vr_stream_t;
+
+typedef enum vr_status {
+  VR_OK = 0,
+  VR_ERR_ARG = 1,         /* bad argument or non-finite input value          */
+  VR_ERR_RANGE = 2,       /* size or value beyond the documented limits      */
+  VR_ERR_UNSUPPORTED = 3, /* valid request this build does not offer         */
+  VR_ERR_OOM = 4,         /* device or host allocation failed                */
+  VR_ERR_CUDA = 5,        /* CUDA runtime error                              */
+  VR_ERR_TIMEOUT = 6,     /* result not ready within the time given          */
+  VR_ERR_BUSY = 7,        /* queue full; try again later                     */
+  VR_ERR_INTERNAL = 8     /* invariant violated inside the library           */
+} vr_status;
+
+typedef enum vr_dtype { VR_I8 = 1, VR_I32 = 2, VR_F32 = 3 } vr_dtype;
+
+/* Limits.  Vertex ids travel in 13-bit fields of 64-bit sort keys. */
+#define VR_MAX_POINTS 8192
+#define VR_MAX_DIM_SIMPLEX 2
+/* Integer squared distances of kept edges must be below 2^38. */
+#define VR_MAX_INT_D2_BITS 38
+/* |float coordinate| must not exceed 2^50 (fp32 squares stay finite). */
+#define VR_MAX_F32_ABS 1125899906842624.0
+
+typedef struct vr_complex vr_complex;
+
+/* View of one dimension of a result.  Pointers are DEVICE pointers owned by
+ * the vr_complex; they stay valid until vr_complex_free. */
+typedef struct vr_dim_view {
+  int32_t k;              /* simplex dimension                                */
+  int64_t count;          /* number of k-simplices                            */
+  const int32_t *verts;   /* count x (k+1), row-major, ascending per simplex  */
+  const int32_t *grade;   /* count                                            */
+  const int64_t *colptr;  /* count+1 (k >= 1); NULL for k = 0                 */
+  const int32_t *rowidx;  /* (k+1)*count face order indices (k >= 1); else NULL */
+} vr_dim_view;
+
+/* Build statistics of one result (host values). */
+typedef struct vr_build_stats {
+  int64_t kept_edges;       /* edges after the cap                            */
+  int64_t triangles;        /* 2-simplices (0 when maxdim < 2)                */
+  int64_t ngrades;          /* distinct grades, including grade 0             */
+  int64_t near_tie_edges;   /* float input: edges re-sorted by their FP64 value */
+  double max_rel_dist_err;  /* float input: max |d_approx - d_fp64| / d_fp64
+                               over kept edges of the fp32 first-pass value  */
+} vr_build_stats;
+
+/* Build the filtered complex of one point cloud.
+ *   points  n x d row-major elements of `dtype`, in device memory or in host
+ *           memory (pageable or pinned; detected per call and copied in on
+ *           `stream`).  Borrowed: it must stay valid until the call returns.
+ *   n       1 .. VR_MAX_POINTS, else VR_ERR_RANGE.
+ *   d       >= 1, else VR_ERR_ARG.
+ *   maxdim  top simplex dimension, 0 .. 2; 3 and above give VR_ERR_UNSUPPORTED.
+ *   maxrad  inclusive radius cap (keep |x_i - x_j| <= maxrad).  +INFINITY
+ *           keeps every pair.  NaN or negative gives VR_ERR_ARG.  Integer
+ *           inputs keep d^2 <= floor(fl(maxrad*maxrad)); float inputs keep
+ *           d^2_fp64 <= fl(maxrad*maxrad).
+ *   stream  all device work runs on it; the call waits for it to learn sizes.
+ *   out     receives a new result, owned by the caller, released with
+ *           vr_complex_free.
+ * Value errors found on the device: a non-finite float coordinate gives
+ * VR_ERR_ARG; |float coordinate| > VR_MAX_F32_ABS, an integer kept d^2 >=
+ * 2^VR_MAX_INT_D2_BITS, or more than 2^31-1 simplices of one dimension give
+ * VR_ERR_RANGE.  Device memory exhaustion gives VR_ERR_OOM. */
+vr_status vr_build(const void *points, int32_t n, int32_t d, vr_dtype dtype,
+                   int32_t maxdim, double maxrad, vr_stream_t stream,
+                   vr_complex **out);
+
+/* Fill `view` for dimension k (0 <= k <= maxdim, else VR_ERR_ARG). */
+vr_status vr_complex_dim(const vr_complex *c, int32_t k, vr_dim_view *view);
+
+/* Device pointer to the squared distance of every grade (grade_value[0] = 0)
+ * and the number of grades. */
+vr_status vr_complex_grade_values(const vr_complex *c, const double **values,
+                                  int64_t *ngrades);
+
+/* Host-side sizes: counts[k] for k = 0..2 (0 above maxdim) and maxdim. */
+vr_status vr_complex_counts(const vr_complex *c, int64_t counts[3],
+                            int32_t *maxdim);
+
+vr_status vr_complex_stats(const vr_complex *c, vr_build_stats *stats);
+
+/* Copy dimension k to host arrays sized as in vr_dim_view (any may be NULL;
+ * colptr/rowidx are ignored for k = 0).  Synchronous on the build stream. */
+vr_status vr_complex_to_host(const vr_complex *c, int32_t k, int32_t *verts,
+                             int32_t *grade, int64_t *colptr, int32_t *rowidx);
+
+/* Copy the grade values (ngrades doubles) to host memory. */
+vr_status vr_complex_grade_values_to_host(const vr_complex *c, double *values);
+
+/* Release a result (stream-ordered on the stream it was built on, which must
+ * still exist).  NULL is ignored. */
+void vr_complex_free(vr_complex *c);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *vr_last_error(void);
+const char *vr_status_string(vr_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VR_H */

@@ -1,0 +1,423 @@
+// prims.cuh -- device primitives of the VR builder: error plumbing, the
+// device status word, exclusive scans and a stable LSD radix sort.  All are
+// written here (no CUB, no Thrust).  sm_103a, 32-wide warps.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+
+#include "../../include/vr.h"
+
+namespace vr {
+
+// ---------------------------------------------------------------- errors
+
+void set_error(const char *fmt, ...);   // thread-local message (api.cu)
+vr_status cuda_status(cudaError_t e, const char *what, const char *file, int line);
+
+#define VR_TRY(x)                                                     \
+  do {                                                                \
+    vr_status s_ = (x);                                               \
+    if (s_ != VR_OK) return s_;                                       \
+  } while (0)
+#define VR_CUDA(x)                                                    \
+  do {                                                                \
+    cudaError_t e_ = (x);                                             \
+    if (e_ != cudaSuccess)                                            \
+      return ::vr::cuda_status(e_, #x, __FILE__, __LINE__);           \
+  } while (0)
+
+// Flags a kernel can raise in the device status word.
+enum : int32_t {
+  F_NONFINITE = 1,   // non-finite float coordinate           -> VR_ERR_ARG
+  F_F32_RANGE = 2,   // |float coordinate| > VR_MAX_F32_ABS   -> VR_ERR_RANGE
+  F_INT_KEY = 4,     // kept integer d^2 >= 2^38              -> VR_ERR_RANGE
+  F_INTERNAL = 8,    // invariant violated                    -> VR_ERR_INTERNAL
+  F_TIMEOUT = 16,    // a bounded wait gave up                -> VR_ERR_TIMEOUT
+  F_OVERFLOW = 32,   // an output arena was too small         -> retried by host
+};
+
+// Device-resident status and counters of one build (read back at sync points).
+struct DevStatus {
+  int32_t flags;
+  int32_t pad;
+  int64_t E;                 // kept edges
+  int64_t T;                 // triangles
+  int64_t ngrades;
+  int64_t near_tie;          // float: edges inside multi-edge repair groups
+  uint64_t max_rel_err_bits; // float: max relative distance error (double bits)
+  int64_t big_seg_max;       // largest triangle segment needing a global sort
+  int64_t big_seg_count;
+  int64_t big_grp_max;       // float: largest repair group needing a global sort
+  int64_t big_grp_count;
+};
+
+__device__ __forceinline__ void raise_flag(DevStatus *st, int32_t f) { atomicOr(&st->flags, f); }
+
+inline vr_status flags_to_status(int32_t f) {
+  if (f & F_INTERNAL) { set_error("internal invariant violated on the device"); return VR_ERR_INTERNAL; }
+  if (f & F_NONFINITE) { set_error("non-finite float coordinate"); return VR_ERR_ARG; }
+  if (f & F_F32_RANGE) { set_error("float coordinate magnitude above 2^50"); return VR_ERR_RANGE; }
+  if (f & F_INT_KEY) { set_error("integer squared distance of a kept edge is >= 2^38"); return VR_ERR_RANGE; }
+  if (f & F_TIMEOUT) { set_error("a bounded device wait timed out"); return VR_ERR_TIMEOUT; }
+  return VR_OK;
+}
+
+// ------------------------------------------------------------- warp level
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane_id() >= o) v += u;
+  }
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim.x <= 1024,
+// a multiple of 32).  `sh` holds >= 33 elements.  Returns the exclusive
+// prefix; *total gets the block sum.
+template <typename T>
+__device__ T block_excl_scan(T v, T *sh, T *total) {
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T inc = warp_incl_scan(v);
+  if (lane_id() == 31) sh[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    T x = lane_id() < nw ? sh[lane_id()] : T(0);
+    T xi = warp_incl_scan(x);
+    if (lane_id() < nw) sh[lane_id()] = xi - x;
+    if (lane_id() == nw - 1) sh[32] = xi;
+  }
+  __syncthreads();
+  T r = sh[w] + inc - v;
+  if (total) *total = sh[32];
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------------ scans
+// out[i] = sum_{j<i} in[j] for i in [0, L]; out[L] = total.  L is known on the
+// host.  Three launches for long arrays (chunk sums, one-CTA scan of the
+// sums, chunk scans with offsets), one for short ones.
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
+
+template <typename TI>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const TI *in, int64_t L, int64_t *bs) {
+  __shared__ int64_t sh[33];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
+  int64_t s = 0;
+  for (int t = threadIdx.x; t < SCAN_CHUNK; t += SCAN_THREADS) {
+    int64_t i = base + t;
+    if (i < L) s += (int64_t)in[i];
+  }
+  int64_t tot;
+  block_excl_scan<int64_t>(s, sh, &tot);
+  if (threadIdx.x == 0) bs[blockIdx.x] = tot;
+}
+
+// One CTA: exclusive scan of bs[0..nb) in place, bs[nb] = total.
+__global__ void __launch_bounds__(1024) k_scan_sums(int64_t *bs, int64_t nb) {
+  __shared__ int64_t sh[33];
+  int64_t carry = 0;
+  for (int64_t b0 = 0; b0 < nb; b0 += 1024) {
+    int64_t i = b0 + threadIdx.x;
+    int64_t v = i < nb ? bs[i] : 0;
+    int64_t tot;
+    int64_t e = block_excl_scan<int64_t>(v, sh, &tot);
+    if (i < nb) bs[i] = carry + e;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) bs[nb] = carry;
+}
+
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(const TI *in, int64_t L, const int64_t *bs, TO *out) {
+  __shared__ int64_t buf[SCAN_CHUNK];
+  __shared__ int64_t sh[33];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
+  for (int t = threadIdx.x; t < SCAN_CHUNK; t += SCAN_THREADS) {
+    int64_t i = base + t;
+    buf[t] = i < L ? (int64_t)in[i] : 0;
+  }
+  __syncthreads();
+  int64_t loc[SCAN_ITEMS];
+  int64_t s = 0;
+#pragma unroll
+  for (int q = 0; q < SCAN_ITEMS; ++q) {
+    loc[q] = s;
+    s += buf[threadIdx.x * SCAN_ITEMS + q];
+  }
+  __syncthreads();
+  int64_t tot;
+  const int64_t off = bs ? bs[blockIdx.x] : 0;
+  int64_t pre = block_excl_scan<int64_t>(s, sh, &tot) + off;
+#pragma unroll
+  for (int q = 0; q < SCAN_ITEMS; ++q) buf[threadIdx.x * SCAN_ITEMS + q] = pre + loc[q];
+  __syncthreads();
+  for (int t = threadIdx.x; t < SCAN_CHUNK; t += SCAN_THREADS) {
+    int64_t i = base + t;
+    if (i < L) out[i] = (TO)buf[t];
+  }
+  if (threadIdx.x == 0 && base + SCAN_CHUNK >= L) out[L] = (TO)(off + tot);
+}
+
+// `bs` needs scan_tmp_slots(L) slots.  out has L + 1 slots.
+inline int64_t scan_tmp_slots(int64_t L) { return (L + SCAN_CHUNK - 1) / SCAN_CHUNK + 1; }
+
+template <typename TI, typename TO>
+inline vr_status scan_exclusive(const TI *in, TO *out, int64_t L, int64_t *bs, cudaStream_t s) {
+  int64_t nb = (L + SCAN_CHUNK - 1) / SCAN_CHUNK;
+  if (nb <= 1) {
+    k_scan_final<TI, TO><<<1, SCAN_THREADS, 0, s>>>(in, L, nullptr, out);
+  } else {
+    k_scan_reduce<TI><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, L, bs);
+    k_scan_sums<<<1, 1024, 0, s>>>(bs, nb);
+    k_scan_final<TI, TO><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, L, bs, out);
+  }
+  VR_CUDA(cudaGetLastError());
+  return VR_OK;
+}
+
+// ------------------------------------------------------------ radix sort
+// Stable LSD radix sort of u64 keys (optional u32 payload) on bits
+// [bit_lo, bit_lo + nbits), 8-bit digits.  Stability comes from ranking each
+// 4096-key tile in order: a warp ranks 32 consecutive keys per round with
+// __match_any_sync, warps cover consecutive 512-key slices, and the digit
+// offsets of earlier warps/tiles are added.
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 16;                    // keys per lane
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 4096 keys per tile
+constexpr int RS_BINS = 256;
+
+__device__ __forceinline__ uint32_t digit_of(uint64_t k, int shift) { return (uint32_t)(k >> shift) & 0xffu; }
+
+// Rank the keys of one tile (positions [t0, t0 + cnt) of src).  On return
+// rank[q] holds, for the lane's q-th key, its position among equal digits in
+// the tile, and sh_cnt[d] the tile's count of digit d.  Keys are read by warp
+// w at t0 + w*512 + q*32 + lane.
+__device__ __forceinline__ void tile_rank(const uint64_t *src, int64_t t0, int64_t cnt, int shift,
+                                          uint64_t (&key)[RS_ITEMS], uint32_t (&rank)[RS_ITEMS],
+                                          uint32_t (*sh_wcnt)[RS_BINS], uint32_t *sh_cnt) {
+  const int w = threadIdx.x >> 5, l = lane_id();
+  for (int b = threadIdx.x; b < RS_WARPS * RS_BINS; b += RS_THREADS) (&sh_wcnt[0][0])[b] = 0;
+  __syncthreads();
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int q = 0; q < RS_ITEMS; ++q) {
+    int64_t idx = (int64_t)w * (32 * RS_ITEMS) + q * 32 + l;
+    bool ok = idx < cnt;
+    key[q] = ok ? src[t0 + idx] : ~0ull;
+    uint32_t dg = ok ? digit_of(key[q], shift) : RS_BINS;  // sentinel for empty lanes
+    uint32_t peers = __match_any_sync(0xffffffffu, dg);
+    uint32_t before = ok ? sh_wcnt[w][dg] : 0;
+    rank[q] = before + __popc(peers & lt);
+    __syncwarp();
+    if (ok && (peers & lt) == 0) sh_wcnt[w][dg] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // Exclusive prefix over warps for each digit, and tile totals.
+  for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int ww = 0; ww < RS_WARPS; ++ww) {
+      uint32_t c = sh_wcnt[ww][d];
+      sh_wcnt[ww][d] = s;
+      s += c;
+    }
+    sh_cnt[d] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < RS_ITEMS; ++q) {
+    int64_t idx = (int64_t)w * (32 * RS_ITEMS) + q * 32 + l;
+    if (idx < cnt) rank[q] += sh_wcnt[w][digit_of(key[q], shift)];
+  }
+}
+
+// Multi-CTA pass, step 1: per-tile digit histogram, digit-major layout
+// hist[d * ntiles + tile].
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *src, int64_t n, int shift, int64_t ntiles,
+                                                        int64_t *hist) {
+  __shared__ uint32_t h[RS_BINS];
+  for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) h[b] = 0;
+  __syncthreads();
+  const int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
+  for (int t = threadIdx.x; t < RS_TILE; t += RS_THREADS) {
+    int64_t i = t0 + t;
+    if (i < n) atomicAdd(&h[digit_of(src[i], shift)], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) hist[(int64_t)b * ntiles + blockIdx.x] = h[b];
+}
+
+// Multi-CTA pass, step 3: stable scatter using the scanned histogram.
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *src, const uint32_t *vsrc, uint64_t *dst,
+                                                           uint32_t *vdst, int64_t n, int shift, int64_t ntiles,
+                                                           const int64_t *off) {
+  __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
+  __shared__ uint32_t cnt[RS_BINS];
+  __shared__ int64_t base[RS_BINS];
+  const int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
+  const int64_t c = n - t0 < RS_TILE ? n - t0 : RS_TILE;
+  uint64_t key[RS_ITEMS];
+  uint32_t rank[RS_ITEMS];
+  for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) base[b] = off[(int64_t)b * ntiles + blockIdx.x];
+  tile_rank(src, t0, c, shift, key, rank, wcnt, cnt);
+  const int w = threadIdx.x >> 5, l = lane_id();
+#pragma unroll
+  for (int q = 0; q < RS_ITEMS; ++q) {
+    int64_t idx = (int64_t)w * (32 * RS_ITEMS) + q * 32 + l;
+    if (idx < c) {
+      int64_t p = base[digit_of(key[q], shift)] + rank[q];
+      dst[p] = key[q];
+      if (vsrc) vdst[p] = vsrc[t0 + idx];
+    }
+  }
+}
+
+// One CTA sorts [0, n) of global arrays in place through tkeys/tvals (any n):
+// each pass histograms everything, then ranks tile after tile in order with a
+// running digit base.  Used for small sorts and for per-segment fix-ups.
+__device__ void cta_radix_sort_global(uint64_t *keys, uint32_t *vals, uint64_t *tkeys, uint32_t *tvals, int64_t n,
+                                      int bit_lo, int nbits) {
+  __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
+  __shared__ uint32_t cnt[RS_BINS];
+  __shared__ int64_t base[RS_BINS];
+  __shared__ int64_t sh[33];
+  uint64_t *src = keys, *dst = tkeys;
+  uint32_t *vs = vals, *vd = tvals;
+  const int passes = (nbits + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = bit_lo + 8 * p;
+    for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) cnt[b] = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += RS_THREADS) atomicAdd(&cnt[digit_of(src[i], shift)], 1u);
+    __syncthreads();
+    {
+      int64_t v = threadIdx.x < RS_BINS ? (int64_t)cnt[threadIdx.x] : 0;
+      int64_t e = block_excl_scan<int64_t>(v, sh, (int64_t *)nullptr);
+      if (threadIdx.x < RS_BINS) base[threadIdx.x] = e;
+      __syncthreads();
+    }
+    for (int64_t t0 = 0; t0 < n; t0 += RS_TILE) {
+      int64_t c = n - t0 < RS_TILE ? n - t0 : RS_TILE;
+      uint64_t key[RS_ITEMS];
+      uint32_t rank[RS_ITEMS];
+      tile_rank(src, t0, c, shift, key, rank, wcnt, cnt);
+      const int w = threadIdx.x >> 5, l = lane_id();
+#pragma unroll
+      for (int q = 0; q < RS_ITEMS; ++q) {
+        int64_t idx = (int64_t)w * (32 * RS_ITEMS) + q * 32 + l;
+        if (idx < c) {
+          int64_t pos = base[digit_of(key[q], shift)] + rank[q];
+          dst[pos] = key[q];
+          if (vs) vd[pos] = vs[t0 + idx];
+        }
+      }
+      __syncthreads();
+      for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) base[b] += cnt[b];
+      __syncthreads();
+    }
+    uint64_t *tk = src; src = dst; dst = tk;
+    uint32_t *tv = vs; vs = vd; vd = tv;
+    __syncthreads();
+  }
+  if (passes & 1) {  // result sits in the temporaries: copy back
+    for (int64_t i = threadIdx.x; i < n; i += RS_THREADS) {
+      keys[i] = tkeys[i];
+      if (vals) vals[i] = tvals[i];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_single(uint64_t *keys, uint32_t *vals, uint64_t *tkeys,
+                                                          uint32_t *tvals, int64_t n, int bit_lo, int nbits) {
+  cta_radix_sort_global(keys, vals, tkeys, tvals, n, bit_lo, nbits);
+}
+
+// Scratch for radix_sort: temporaries of n keys/vals, histogram and offsets
+// of 256 * ntiles int64 each, scan sums.  The sorted result ends in `keys`.
+struct RadixScratch {
+  uint64_t *tkeys;
+  uint32_t *tvals;
+  int64_t *hist;
+  int64_t *off;
+  int64_t *bs;
+};
+inline int64_t rs_tiles(int64_t n) { return (n + RS_TILE - 1) / RS_TILE; }
+
+inline vr_status radix_sort(uint64_t *keys, uint32_t *vals, int64_t n, int bit_lo, int nbits, const RadixScratch &sc,
+                            cudaStream_t s) {
+  if (n <= 1 || nbits <= 0) return VR_OK;
+  if (n <= 2 * RS_TILE) {
+    k_rs_single<<<1, RS_THREADS, 0, s>>>(keys, vals, sc.tkeys, sc.tvals, n, bit_lo, nbits);
+    VR_CUDA(cudaGetLastError());
+    return VR_OK;
+  }
+  const int64_t nt = rs_tiles(n);
+  uint64_t *src = keys, *dst = sc.tkeys;
+  uint32_t *vs = vals, *vd = vals ? sc.tvals : nullptr;
+  const int passes = (nbits + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = bit_lo + 8 * p;
+    k_rs_hist<<<(unsigned)nt, RS_THREADS, 0, s>>>(src, n, shift, nt, sc.hist);
+    VR_TRY((scan_exclusive<int64_t, int64_t>(sc.hist, sc.off, RS_BINS * nt, sc.bs, s)));
+    k_rs_scatter<<<(unsigned)nt, RS_THREADS, 0, s>>>(src, vs, dst, vd, n, shift, nt, sc.off);
+    VR_CUDA(cudaGetLastError());
+    uint64_t *tk = src; src = dst; dst = tk;
+    uint32_t *tv = vs; vs = vd; vd = tv;
+  }
+  if (passes & 1) {
+    VR_CUDA(cudaMemcpyAsync(keys, src, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+    if (vals) VR_CUDA(cudaMemcpyAsync(vals, vs, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+  }
+  return VR_OK;
+}
+
+// ------------------------------------------------------- bitonic (smem)
+// Sort cap (a power of two) pairs (key, val) ascending in shared memory; keys
+// unique, slots past the live count already hold ~0 keys.
+__device__ void cta_bitonic(uint64_t *key, uint32_t *val, int cap) {
+  for (int k = 2; k <= cap; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < cap; i += blockDim.x) {
+        int x = i ^ j;
+        if (x > i) {
+          bool up = (i & k) == 0;
+          uint64_t a = key[i], b = key[x];
+          if ((a > b) == up) {
+            key[i] = b; key[x] = a;
+            uint32_t t = val[i]; val[i] = val[x]; val[x] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace vr
