@@ -1,0 +1,181 @@
+// api.cu -- the extern "C" entry points of vr.h: argument checks, host/device
+// input detection, result access and error reporting.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "complex.h"
+#include "prims.cuh"
+
+namespace vr {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+vr_status cuda_status(cudaError_t e, const char *what, const char *file, int line) {
+  cudaGetLastError();
+  set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  return e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA;
+}
+
+// Pool memory stays reserved between builds, so repeated calls do not go
+// back to the driver for every workspace.
+static void keep_pool_warm() {
+  static thread_local int done_dev = -1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return; }
+  if (done_dev == dev) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done_dev = dev;
+}
+
+static bool is_device_pointer(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static size_t elem_size(vr_dtype t) { return t == VR_I8 ? 1 : 4; }
+
+}  // namespace vr
+
+using namespace vr;
+
+extern "C" {
+
+const char *vr_last_error(void) { return g_err; }
+
+const char *vr_status_string(vr_status s) {
+  switch (s) {
+    case VR_OK: return "VR_OK";
+    case VR_ERR_ARG: return "VR_ERR_ARG";
+    case VR_ERR_RANGE: return "VR_ERR_RANGE";
+    case VR_ERR_UNSUPPORTED: return "VR_ERR_UNSUPPORTED";
+    case VR_ERR_OOM: return "VR_ERR_OOM";
+    case VR_ERR_CUDA: return "VR_ERR_CUDA";
+    case VR_ERR_TIMEOUT: return "VR_ERR_TIMEOUT";
+    case VR_ERR_BUSY: return "VR_ERR_BUSY";
+    case VR_ERR_INTERNAL: return "VR_ERR_INTERNAL";
+  }
+  return "VR_ERR_UNKNOWN";
+}
+
+vr_status vr_build(const void *points, int32_t n, int32_t d, vr_dtype dtype, int32_t maxdim, double maxrad,
+                   vr_stream_t stream, vr_complex **out) {
+  g_err[0] = 0;
+  if (!out) { set_error("out is NULL"); return VR_ERR_ARG; }
+  *out = nullptr;
+  if (!points) { set_error("points is NULL"); return VR_ERR_ARG; }
+  if (dtype != VR_I8 && dtype != VR_I32 && dtype != VR_F32) { set_error("unknown dtype %d", (int)dtype); return VR_ERR_ARG; }
+  if (d < 1) { set_error("d = %d must be >= 1", d); return VR_ERR_ARG; }
+  if (n < 1 || n > VR_MAX_POINTS) { set_error("n = %d outside [1, %d]", n, VR_MAX_POINTS); return VR_ERR_RANGE; }
+  if (maxdim < 0) { set_error("maxdim = %d is negative", maxdim); return VR_ERR_ARG; }
+  if (maxdim > VR_MAX_DIM_SIMPLEX) { set_error("maxdim = %d above %d is not offered", maxdim, VR_MAX_DIM_SIMPLEX); return VR_ERR_UNSUPPORTED; }
+  if (std::isnan(maxrad) || maxrad < 0.0) { set_error("maxrad must be >= 0 and not NaN"); return VR_ERR_ARG; }
+  keep_pool_warm();
+  cudaStream_t s = (cudaStream_t)stream;
+  vr_complex *res = new (std::nothrow) vr_complex();
+  if (!res) { set_error("host allocation failed"); return VR_ERR_OOM; }
+  cudaGetDevice(&res->device);
+  const void *dpts = points;
+  void *staged = nullptr;
+  const size_t bytes = (size_t)n * d * elem_size(dtype);
+  if (!is_device_pointer(points)) {
+    if (cudaMallocAsync(&staged, bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      delete res;
+      set_error("device allocation for the input copy failed");
+      return VR_ERR_OOM;
+    }
+    cudaMemcpyAsync(staged, points, bytes, cudaMemcpyHostToDevice, s);
+    dpts = staged;
+  }
+  vr_status st = build_cloud(dpts, n, d, dtype, maxdim, maxrad, s, res);
+  if (staged) cudaFreeAsync(staged, s);
+  if (st != VR_OK) {
+    for (void *p : res->allocs) cudaFreeAsync(p, s);
+    delete res;
+    return st;
+  }
+  *out = res;
+  return VR_OK;
+}
+
+vr_status vr_complex_dim(const vr_complex *c, int32_t k, vr_dim_view *v) {
+  if (!c || !v) { set_error("NULL argument"); return VR_ERR_ARG; }
+  if (k < 0 || k > c->maxdim) { set_error("dimension %d outside [0, %d]", k, c->maxdim); return VR_ERR_ARG; }
+  v->k = k;
+  v->count = c->count[k];
+  v->verts = c->verts[k];
+  v->grade = c->grade[k];
+  v->colptr = k >= 1 ? c->colptr[k] : nullptr;
+  v->rowidx = k >= 1 ? c->rowidx[k] : nullptr;
+  return VR_OK;
+}
+
+vr_status vr_complex_grade_values(const vr_complex *c, const double **values, int64_t *ngrades) {
+  if (!c || !values || !ngrades) { set_error("NULL argument"); return VR_ERR_ARG; }
+  *values = c->grade_value;
+  *ngrades = c->ngrades;
+  return VR_OK;
+}
+
+vr_status vr_complex_counts(const vr_complex *c, int64_t counts[3], int32_t *maxdim) {
+  if (!c || !counts) { set_error("NULL argument"); return VR_ERR_ARG; }
+  for (int k = 0; k < 3; ++k) counts[k] = c->count[k];
+  if (maxdim) *maxdim = c->maxdim;
+  return VR_OK;
+}
+
+vr_status vr_complex_stats(const vr_complex *c, vr_build_stats *s) {
+  if (!c || !s) { set_error("NULL argument"); return VR_ERR_ARG; }
+  *s = c->stats;
+  return VR_OK;
+}
+
+vr_status vr_complex_to_host(const vr_complex *c, int32_t k, int32_t *verts, int32_t *grade, int64_t *colptr,
+                             int32_t *rowidx) {
+  if (!c) { set_error("NULL complex"); return VR_ERR_ARG; }
+  if (k < 0 || k > c->maxdim) { set_error("dimension %d outside [0, %d]", k, c->maxdim); return VR_ERR_ARG; }
+  const int64_t m = c->count[k];
+  cudaStream_t s = c->stream;
+  if (verts && m) VR_CUDA(cudaMemcpyAsync(verts, c->verts[k], sizeof(int32_t) * m * (k + 1), cudaMemcpyDeviceToHost, s));
+  if (grade && m) VR_CUDA(cudaMemcpyAsync(grade, c->grade[k], sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
+  if (k >= 1 && colptr) VR_CUDA(cudaMemcpyAsync(colptr, c->colptr[k], sizeof(int64_t) * (m + 1), cudaMemcpyDeviceToHost, s));
+  if (k >= 1 && rowidx && m) VR_CUDA(cudaMemcpyAsync(rowidx, c->rowidx[k], sizeof(int32_t) * m * (k + 1), cudaMemcpyDeviceToHost, s));
+  VR_CUDA(cudaStreamSynchronize(s));
+  return VR_OK;
+}
+
+vr_status vr_complex_grade_values_to_host(const vr_complex *c, double *values) {
+  if (!c || !values) { set_error("NULL argument"); return VR_ERR_ARG; }
+  VR_CUDA(cudaMemcpyAsync(values, c->grade_value, sizeof(double) * c->ngrades, cudaMemcpyDeviceToHost, c->stream));
+  VR_CUDA(cudaStreamSynchronize(c->stream));
+  return VR_OK;
+}
+
+void vr_complex_free(vr_complex *c) {
+  if (!c) return;
+  if (c->owned)
+    for (void *p : c->allocs) cudaFreeAsync(p, c->stream);
+  cudaGetLastError();
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,327 @@
+// build.cu -- host orchestration of one Vietoris-Rips build on one stream.
+//
+// Kernels in launch order (kernels.cuh): stage -> distance/bitmap -> row
+// counts -> scans -> [sync 1: kept-edge count, value errors] -> edge keys in
+// lexicographic order -> stable LSD radix sort on the distance bits -> (float:
+// FP64 values + repair groups) -> dense-rank scan -> edge outputs and the
+// neighbour CSR -> triangle counts -> scan -> tie groups -> [sync 2: triangle
+// count] -> triangle emission -> tie-group merge.  Only sizes cross to the host.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "complex.h"
+#include "kernels.cuh"
+
+namespace vr {
+
+// Stream-ordered allocations that are released together (on scope exit for
+// workspaces; handed over to the result for outputs).
+struct Arena {
+  cudaStream_t s;
+  std::vector<void *> ptrs;
+  explicit Arena(cudaStream_t st) : s(st) {}
+  ~Arena() {
+    for (void *p : ptrs) cudaFreeAsync(p, s);
+  }
+  template <typename T>
+  vr_status alloc(T **p, int64_t count) {
+    size_t bytes = sizeof(T) * (size_t)std::max<int64_t>(count, 1);
+    cudaError_t e = cudaMallocAsync((void **)p, bytes, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA;
+    }
+    ptrs.push_back(*p);
+    return VR_OK;
+  }
+  void release_to(std::vector<void *> &dst) {
+    dst.insert(dst.end(), ptrs.begin(), ptrs.end());
+    ptrs.clear();
+  }
+};
+
+static unsigned grid_for(int64_t work, int threads, int cap_ctas = 148 * 16) {
+  int64_t g = (work + threads - 1) / threads;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, cap_ctas));
+}
+
+static int bitlen(uint64_t v) { return v ? 64 - __builtin_clzll(v) : 0; }
+
+// Read the status word back (pinned buffer, stream sync).
+static vr_status read_status(const DevStatus *dst, DevStatus *host, cudaStream_t s) {
+  VR_CUDA(cudaMemcpyAsync(host, dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  VR_CUDA(cudaStreamSynchronize(s));
+  return flags_to_status(host->flags);
+}
+
+static DevStatus *pinned_status() {
+  thread_local DevStatus *p = nullptr;
+  if (!p && cudaMallocHost((void **)&p, sizeof(DevStatus)) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+
+template <bool F, int DR>
+static void launch_dist(const void *X, int n, int d, int W, const Cap &cap, uint32_t *adj, DevStatus *st,
+                        cudaStream_t s) {
+  const int B = (n + 31) / 32;
+  dim3 grid(B, (B + 7) / 8);
+  k_dist_bitmap<F, DR><<<grid, 256, 0, s>>>(X, n, d, W, cap, adj, st);
+}
+
+template <bool F>
+static void dist_dispatch(const void *X, int n, int d, int W, const Cap &cap, uint32_t *adj, DevStatus *st,
+                          cudaStream_t s) {
+  if (d <= 4) launch_dist<F, 4>(X, n, d, W, cap, adj, st, s);
+  else if (d <= 16) launch_dist<F, 16>(X, n, d, W, cap, adj, st, s);
+  else if (d <= 32) launch_dist<F, 32>(X, n, d, W, cap, adj, st, s);
+  else launch_dist<F, 0>(X, n, d, W, cap, adj, st, s);
+}
+
+template <bool F>
+static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dtype, int32_t maxdim, double maxrad,
+                            cudaStream_t s, vr_complex *res) {
+  DevStatus *hst = pinned_status();
+  if (!hst) {
+    set_error("pinned host status buffer allocation failed");
+    return VR_ERR_OOM;
+  }
+  Arena ws(s), out(s);
+  const int W = (n + 31) / 32;
+  const int64_t nd = (int64_t)n * d;
+
+  // Cap parameters (integer: floor(fl(maxrad^2)); float: fl(maxrad^2)).
+  Cap cap{};
+  const double r2 = maxrad * maxrad;
+  cap.keep_all = std::isinf(r2) ? 1 : 0;
+  cap.r2 = r2;
+  cap.crel = (d + 5) * std::ldexp(1.0, -24);
+  if (!F && !cap.keep_all) {
+    double f = std::floor(r2);
+    cap.r2i = f >= 18446744073709551615.0 ? ~0ull : (uint64_t)f;
+  }
+
+  DevStatus *st;
+  void *X;
+  uint32_t *adj;
+  int32_t *adjpre, *deg, *up, *nbr_ptr;
+  int64_t *lex_ptr, *bs_small;
+  VR_TRY(ws.alloc(&st, 1));
+  VR_TRY(F ? ws.alloc((float **)&X, nd) : ws.alloc((int32_t **)&X, nd));
+  VR_TRY(ws.alloc(&adj, (int64_t)n * W));
+  VR_TRY(ws.alloc(&adjpre, (int64_t)n * W));
+  VR_TRY(ws.alloc(&deg, n));
+  VR_TRY(ws.alloc(&up, n));
+  VR_TRY(ws.alloc(&nbr_ptr, n + 1));
+  VR_TRY(ws.alloc(&lex_ptr, n + 1));
+  VR_TRY(ws.alloc(&bs_small, scan_tmp_slots(n)));
+  VR_CUDA(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
+
+  // Stage: convert to the working element type and check values.
+  const unsigned gs = grid_for(nd, 256, 148 * 8);
+  if (dtype == VR_I8) k_stage<int8_t, false><<<gs, 256, 0, s>>>((const int8_t *)dpts, nd, (int32_t *)X, st);
+  else if (dtype == VR_I32) k_stage<int32_t, false><<<gs, 256, 0, s>>>((const int32_t *)dpts, nd, (int32_t *)X, st);
+  else k_stage<float, true><<<gs, 256, 0, s>>>((const float *)dpts, nd, (float *)X, st);
+  VR_CUDA(cudaGetLastError());
+
+  dist_dispatch<F>(X, n, d, W, cap, adj, st, s);
+  VR_CUDA(cudaGetLastError());
+  k_rows<<<(n + 7) / 8, 256, 0, s>>>(adj, n, W, adjpre, deg, up);
+  VR_CUDA(cudaGetLastError());
+  VR_TRY((scan_exclusive<int32_t, int32_t>(deg, nbr_ptr, n, bs_small, s)));
+  VR_TRY((scan_exclusive<int32_t, int64_t>(up, lex_ptr, n, bs_small, s)));
+  VR_CUDA(cudaMemcpyAsync(&st->E, lex_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+
+  // ---- sync 1: kept-edge count and value errors.
+  VR_TRY(read_status(st, hst, s));
+  const int64_t E = hst->E;
+  if (E > INT32_MAX) {
+    set_error("%lld edges exceed the 2^31-1 limit of one dimension", (long long)E);
+    return VR_ERR_RANGE;
+  }
+
+  uint64_t *keys;
+  RadixScratch rs{};
+  int32_t *flag, *gex, *nbr_ord, *gstart;
+  int32_t *everts, *egrade, *erow;
+  int64_t *ecol, *bs_e;
+  double *gval, *d64 = nullptr;
+  const int64_t nt = rs_tiles(E);
+  VR_TRY(ws.alloc(&keys, E));
+  VR_TRY(ws.alloc(&rs.tkeys, E));
+  VR_TRY(ws.alloc(&rs.hist, (int64_t)RS_BINS * nt));
+  VR_TRY(ws.alloc(&rs.off, (int64_t)RS_BINS * nt + 1));
+  VR_TRY(ws.alloc(&rs.bs, scan_tmp_slots((int64_t)RS_BINS * nt)));
+  VR_TRY(ws.alloc(&flag, E));
+  VR_TRY(ws.alloc(&gex, E + 1));
+  VR_TRY(ws.alloc(&bs_e, scan_tmp_slots(E)));
+  VR_TRY(ws.alloc(&nbr_ord, 2 * E));
+  VR_TRY(ws.alloc(&gstart, E + 2));
+  VR_TRY(out.alloc(&everts, 2 * E));
+  VR_TRY(out.alloc(&egrade, E));
+  VR_TRY(out.alloc(&ecol, E + 1));
+  VR_TRY(out.alloc(&erow, 2 * E));
+  VR_TRY(out.alloc(&gval, E + 1));
+
+  const unsigned ge = grid_for(E, 256);
+  if (E > 0) {
+    k_edge_keys<F><<<(n + 7) / 8, 256, 0, s>>>(X, n, d, W, adj, adjpre, deg, up, lex_ptr, keys);
+    VR_CUDA(cudaGetLastError());
+    // Keys arrive in (i, j) order, so a stable sort on the distance bits
+    // alone yields (distance, i, j).
+    int kbits;
+    if (F) kbits = 31;
+    else {
+      uint64_t bound = dtype == VR_I8 ? (uint64_t)d * 255ull * 255ull : INT_KEY_LIMIT - 1;
+      if (!cap.keep_all) bound = std::min(bound, cap.r2i);
+      kbits = std::max(1, bitlen(bound));
+    }
+    VR_TRY(radix_sort(keys, nullptr, E, KEY_SHIFT, kbits, rs, s));
+
+    if (F) {
+      int32_t *split, *gbeg, *midq, *bigq;
+      uint64_t *k1, *k2, *gk;
+      uint32_t *v1, *v2;
+      double *gd;
+      VR_TRY(ws.alloc(&d64, E));
+      VR_TRY(ws.alloc(&split, E));
+      VR_TRY(ws.alloc(&gbeg, E + 1));
+      VR_TRY(ws.alloc(&midq, E));
+      VR_TRY(ws.alloc(&bigq, E));
+      k_f64_values<<<ge, 256, 0, s>>>((const float *)X, d, keys, E, cap.crel, d64, split, st);
+      VR_TRY((scan_exclusive<int32_t, int32_t>(split, gex, E, bs_e, s)));
+      k_group_starts<<<ge, 256, 0, s>>>(split, gex, E, gbeg);
+      // Group count is gex[E]; launch over the E upper bound, threads skip.
+      k_repair_small<<<ge, 256, 0, s>>>(gbeg, gex + E, keys, d64, midq, bigq, st);
+      VR_CUDA(cudaGetLastError());
+      k_repair_mid<<<296, 256, 0, s>>>(gbeg, midq, st, keys, d64);
+      VR_TRY(ws.alloc(&k1, E));
+      VR_TRY(ws.alloc(&k2, E));
+      VR_TRY(ws.alloc(&gk, E));
+      VR_TRY(ws.alloc(&v1, E));
+      VR_TRY(ws.alloc(&v2, E));
+      VR_TRY(ws.alloc(&gd, E));
+      k_repair_big<<<1, RS_THREADS, 0, s>>>(gbeg, bigq, st, keys, d64, k1, v1, k2, v2, gk, gd);
+      VR_CUDA(cudaGetLastError());
+    }
+    k_edge_flags<F><<<ge, 256, 0, s>>>(keys, d64, E, flag);
+    VR_TRY((scan_exclusive<int32_t, int32_t>(flag, gex, E, bs_e, s)));
+    k_edge_emit<F><<<ge, 256, 0, s>>>(keys, d64, E, flag, gex, adj, adjpre, W, nbr_ptr, everts, egrade, ecol, erow,
+                                      gval, gstart, nbr_ord, st);
+    VR_CUDA(cudaGetLastError());
+  } else {
+    const double zero = 0.0;
+    const int64_t zero64 = 0;
+    VR_CUDA(cudaMemcpyAsync(gval, &zero, sizeof(double), cudaMemcpyHostToDevice, s));
+    VR_CUDA(cudaMemcpyAsync(ecol, &zero64, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  }
+
+  int32_t *tcnt = nullptr, *tmidq = nullptr, *tbigq = nullptr;
+  int64_t *toff = nullptr;
+  if (maxdim >= 2 && E > 0) {
+    VR_TRY(ws.alloc(&tcnt, E));
+    VR_TRY(ws.alloc(&toff, E + 1));
+    VR_TRY(ws.alloc(&tmidq, E + 1));
+    VR_TRY(ws.alloc(&tbigq, E + 1));
+    k_tri_count<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, E, adj, adjpre, W, nbr_ptr, nbr_ord, tcnt);
+    VR_TRY((scan_exclusive<int32_t, int64_t>(tcnt, toff, E, bs_e, s)));
+    VR_CUDA(cudaMemcpyAsync(&st->T, toff + E, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    k_tri_groups<<<grid_for(E + 1, 256), 256, 0, s>>>(gstart, tcnt, toff, tmidq, tbigq, st);
+    VR_CUDA(cudaGetLastError());
+  }
+
+  // ---- sync 2: grade count, triangle count, tie-group sizes.
+  VR_TRY(read_status(st, hst, s));
+  const int64_t ngrades = E > 0 ? hst->ngrades : 1;
+  const int64_t T = (maxdim >= 2 && E > 0) ? hst->T : 0;
+  if (T > INT32_MAX) {
+    set_error("%lld triangles exceed the 2^31-1 limit of one dimension", (long long)T);
+    return VR_ERR_RANGE;
+  }
+
+  // Vertices.
+  int32_t *vverts, *vgrade;
+  VR_TRY(out.alloc(&vverts, n));
+  VR_TRY(out.alloc(&vgrade, n));
+  k_vertices<<<grid_for(n, 256), 256, 0, s>>>(n, vverts, vgrade);
+  VR_CUDA(cudaGetLastError());
+
+  int32_t *tverts = nullptr, *tgrade = nullptr, *trow = nullptr;
+  int64_t *tcol = nullptr;
+  if (maxdim >= 2) {
+    VR_TRY(out.alloc(&tverts, 3 * T));
+    VR_TRY(out.alloc(&tgrade, T));
+    VR_TRY(out.alloc(&tcol, T + 1));
+    VR_TRY(out.alloc(&trow, 3 * T));
+    const int64_t tlast = 3 * T;
+    VR_CUDA(cudaMemcpyAsync(tcol + T, &tlast, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    if (T > 0) {
+      k_tri_emit<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr, nbr_ord, toff,
+                                                          tverts, tgrade, tcol, trow);
+      VR_CUDA(cudaGetLastError());
+      if (hst->mid_seg_count > 0) {
+        const size_t smem = (size_t)TRI_MID * (8 + 4 + 12);
+        VR_CUDA(cudaFuncSetAttribute(k_tri_fix_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_tri_fix_mid<<<std::min(hst->mid_seg_count, 148 * 2), 256, smem, s>>>(gstart, toff, tmidq, st, tverts, trow);
+        VR_CUDA(cudaGetLastError());
+      }
+      if (hst->big_seg_count > 0) {
+        const int64_t m = hst->big_seg_max;
+        uint64_t *k1, *k2;
+        uint32_t *v1, *v2;
+        int32_t *rtmp;
+        VR_TRY(ws.alloc(&k1, m));
+        VR_TRY(ws.alloc(&k2, m));
+        VR_TRY(ws.alloc(&v1, m));
+        VR_TRY(ws.alloc(&v2, m));
+        VR_TRY(ws.alloc(&rtmp, 3 * m));
+        k_tri_fix_big<<<1, RS_THREADS, 0, s>>>(gstart, toff, tbigq, st, tverts, trow, k1, v1, k2, v2, rtmp);
+        VR_CUDA(cudaGetLastError());
+      }
+    }
+  }
+
+  // Hand the outputs to the result.
+  res->n = n;
+  res->d = d;
+  res->maxdim = maxdim;
+  res->stream = s;
+  res->count[0] = n;
+  res->count[1] = maxdim >= 1 ? E : 0;
+  res->count[2] = maxdim >= 2 ? T : 0;
+  res->verts[0] = vverts;
+  res->grade[0] = vgrade;
+  res->verts[1] = everts;
+  res->grade[1] = egrade;
+  res->colptr[1] = ecol;
+  res->rowidx[1] = erow;
+  res->verts[2] = tverts;
+  res->grade[2] = tgrade;
+  res->colptr[2] = tcol;
+  res->rowidx[2] = trow;
+  res->grade_value = gval;
+  res->ngrades = ngrades;
+  res->stats.kept_edges = E;
+  res->stats.triangles = T;
+  res->stats.ngrades = ngrades;
+  // The float repair counters are final once the stream passes the repair
+  // kernels, which precede sync 2.
+  res->stats.near_tie_edges = F ? hst->near_tie : 0;
+  double mre = 0.0;
+  memcpy(&mre, &hst->max_rel_err_bits, sizeof(double));
+  res->stats.max_rel_dist_err = F ? mre : 0.0;
+  out.release_to(res->allocs);
+  return VR_OK;
+}
+
+vr_status build_cloud(const void *dpts, int32_t n, int32_t d, vr_dtype dtype, int32_t maxdim, double maxrad,
+                      cudaStream_t s, vr_complex *res) {
+  if (dtype == VR_F32) return build_impl<true>(dpts, n, d, dtype, maxdim, maxrad, s, res);
+  return build_impl<false>(dpts, n, d, dtype, maxdim, maxrad, s, res);
+}
+
+}  // namespace vr

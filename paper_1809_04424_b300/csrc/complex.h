@@ -1,0 +1,29 @@
+// complex.h -- the result object behind the opaque vr_complex handle.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/vr.h"
+
+struct vr_complex {
+  int32_t n = 0, d = 0, maxdim = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int64_t count[3] = {0, 0, 0};
+  int32_t *verts[3] = {nullptr, nullptr, nullptr};
+  int32_t *grade[3] = {nullptr, nullptr, nullptr};
+  int64_t *colptr[3] = {nullptr, nullptr, nullptr};
+  int32_t *rowidx[3] = {nullptr, nullptr, nullptr};
+  double *grade_value = nullptr;
+  int64_t ngrades = 0;
+  vr_build_stats stats{};
+  std::vector<void *> allocs;   // device allocations owned by this result
+  bool owned = true;            // false for views into a batch
+};
+
+namespace vr {
+vr_status build_cloud(const void *dpts, int32_t n, int32_t d, vr_dtype dtype, int32_t maxdim, double maxrad,
+                      cudaStream_t s, vr_complex *res);
+}

@@ -1,0 +1,676 @@
+// kernels.cuh -- device steps of the Vietoris-Rips build (arXiv 1809.04424,
+// Sec. 2.1 construction; Sec. 3 / Sec. 4.4 ranking; Sec. 2.2 boundary).
+//
+// Layout in HBM for one cloud of n points (W = ceil(n/32) words per row):
+//   X       n*d int32 (integer inputs) or float (float inputs), row-major
+//   adj     n*W u32   kept-edge adjacency bitmap, symmetric, no diagonal
+//   adjpre  n*W i32   exclusive prefix popcount of each row's words, so the
+//                     rank of neighbour j in row i is adjpre + popc(word & below)
+//   nbr_ptr n+1 i32   row starts of the neighbour CSR (neighbours ascending)
+//   nbr_ord 2E  i32   order index of the edge behind each neighbour entry
+//   keys    E   u64   (d2 key << 26) | i << 13 | j, i < j
+// Every step is one kernel; the host only learns sizes at two sync points.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "prims.cuh"
+
+namespace vr {
+
+constexpr int ID_BITS = 13;
+constexpr uint64_t ID_MASK = (1ull << ID_BITS) - 1;
+constexpr int KEY_SHIFT = 2 * ID_BITS;  // d2 part of an edge key starts at bit 26
+constexpr uint64_t INT_KEY_LIMIT = 1ull << 38;
+
+// Parameters of the cap shared by the distance kernels.
+struct Cap {
+  int keep_all;     // maxrad = +inf
+  uint64_t r2i;     // integer inputs: floor(fl(maxrad^2)) clamped to u64
+  double r2;        // float inputs: fl(maxrad^2)
+  double crel;      // float inputs: relative bound of the fp32 first pass
+};
+
+// Absolute slack of the fp32 bound: covers underflow of tiny squares.
+constexpr double F32_ABS_SLACK = 7.888609052210118e-31;  // 2^-100
+
+// --------------------------------------------------------------- distances
+
+// Exact integer squared distance, saturating at 2^64-1.  |x_i - x_j| < 2^32
+// for int32 inputs, so every square fits in u64.
+__device__ __forceinline__ uint64_t d2_int(const int32_t *xi, const int32_t *xj, int d) {
+  uint64_t acc = 0;
+  for (int k = 0; k < d; ++k) {
+    int64_t t = (int64_t)xi[k] - (int64_t)xj[k];
+    uint64_t m = (uint64_t)(t < 0 ? -t : t);
+    uint64_t s = acc + m * m;
+    acc = s < acc ? ~0ull : s;
+  }
+  return acc;
+}
+
+// fp32 first pass: acc = fma(t, t, acc) over coordinates in order, t = fl32
+// difference.  The same sequence everywhere, so every kernel that evaluates a
+// pair gets the same bits (the value is symmetric in i, j: t only flips sign).
+__device__ __forceinline__ float d2_f32(const float *xi, const float *xj, int d) {
+  float acc = 0.f;
+  for (int k = 0; k < d; ++k) {
+    float t = __fsub_rn(xi[k], xj[k]);
+    acc = __fmaf_rn(t, t, acc);
+  }
+  return acc;
+}
+
+// Canonical FP64 squared distance: acc = 0; t = fl(x_ik - x_jk);
+// acc = fl(acc + fl(t*t)) in coordinate order, each operation rounded to
+// nearest, nothing fused.  This is the value float inputs are ranked by.
+__device__ __forceinline__ double d2_f64(const float *xi, const float *xj, int d) {
+  double acc = 0.0;
+  for (int k = 0; k < d; ++k) {
+    double t = __dsub_rn((double)xi[k], (double)xj[k]);
+    acc = __dadd_rn(acc, __dmul_rn(t, t));
+  }
+  return acc;
+}
+
+// Bounds of the canonical value from the fp32 first pass A:
+//   |A - D| <= ((d+2) u32 + O(u^2)) D + underflow, |F - D| <= (d+2) u64 D
+// (D exact, F canonical FP64), so |A - F| <= crel * A + 2^-100 with
+// crel = (d + 5) * 2^-24 (slack for the second-order terms).
+__device__ __forceinline__ double f32_lo(float a, double crel) { return (double)a * (1.0 - crel) - F32_ABS_SLACK; }
+__device__ __forceinline__ double f32_hi(float a, double crel) { return (double)a * (1.0 + crel) + F32_ABS_SLACK; }
+
+// ------------------------------------------------------------------ stage
+
+template <typename TIn, bool F>
+__global__ void k_stage(const TIn *in, int64_t count, typename std::conditional<F, float, int32_t>::type *X,
+                        DevStatus *st) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (F) {
+      float v = (float)in[t];
+      if (!isfinite(v)) raise_flag(st, F_NONFINITE);
+      else if (fabsf(v) > (float)VR_MAX_F32_ABS) raise_flag(st, F_F32_RANGE);
+      X[t] = v;
+    } else {
+      X[t] = (int32_t)in[t];
+    }
+  }
+}
+
+// ------------------------------------------------------- distance + bitmap
+// One warp per 32x32 block (bi <= bj) of the pair matrix.  Lane l owns column
+// j = 32*bj + l and walks the 32 rows i of the block; __ballot_sync of the
+// keep test gives row i's bitmap word directly (the ballot/popc idea of the
+// paper's init_supp kernel, Sec. 4.3), and each lane accumulates its own
+// column word for the mirrored block, so both halves are written without
+// atomics.  grid = (B, ceil(B/8)), 8 warps per CTA.
+
+template <bool F, int DR>
+__global__ void __launch_bounds__(256) k_dist_bitmap(const void *Xv, int n, int d, int W, Cap cap, uint32_t *adj,
+                                                     DevStatus *st) {
+  using T = typename std::conditional<F, float, int32_t>::type;
+  const T *X = (const T *)Xv;
+  const int bj = blockIdx.x;
+  const int bi = blockIdx.y * 8 + (threadIdx.x >> 5);
+  const int l = lane_id();
+  if (bi > bj) return;
+  const int j = bj * 32 + l;
+  const bool jv = j < n;
+  T xj[DR > 0 ? DR : 1];
+  if constexpr (DR > 0) {
+#pragma unroll
+    for (int k = 0; k < DR; ++k) xj[k] = (jv && k < d) ? X[(int64_t)j * d + k] : T(0);
+  }
+  const T *pj = X + (int64_t)(jv ? j : 0) * d;
+  uint32_t myrow = 0, mycol = 0;
+  bool key_overflow = false;
+  const int rows = min(32, n - bi * 32);
+  for (int r = 0; r < rows; ++r) {
+    const int i = bi * 32 + r;
+    const T *pi = X + (int64_t)i * d;
+    bool kept = false;
+    if (jv && j != i) {
+      if constexpr (F) {
+        float a;
+        if constexpr (DR > 0) {
+          a = 0.f;
+#pragma unroll
+          for (int k = 0; k < DR; ++k)
+            if (k < d) {
+              float t = __fsub_rn(pi[k], xj[k]);
+              a = __fmaf_rn(t, t, a);
+            }
+        } else {
+          a = d2_f32(pi, pj, d);
+        }
+        if (cap.keep_all) kept = true;
+        else if (f32_hi(a, cap.crel) <= cap.r2) kept = true;
+        else if (f32_lo(a, cap.crel) > cap.r2) kept = false;
+        else kept = d2_f64(pi, pj, d) <= cap.r2;  // near the cap: decide exactly
+      } else {
+        uint64_t v;
+        if constexpr (DR > 0) {
+          v = 0;
+#pragma unroll
+          for (int k = 0; k < DR; ++k)
+            if (k < d) {
+              int64_t t = (int64_t)pi[k] - (int64_t)xj[k];
+              uint64_t m = (uint64_t)(t < 0 ? -t : t);
+              uint64_t s = v + m * m;
+              v = s < v ? ~0ull : s;
+            }
+        } else {
+          v = d2_int(pi, pj, d);
+        }
+        kept = cap.keep_all || v <= cap.r2i;
+        if (kept && v >= INT_KEY_LIMIT) key_overflow = true;
+      }
+    }
+    uint32_t word = __ballot_sync(0xffffffffu, kept);
+    if (l == r) myrow = word;
+    mycol |= (uint32_t)kept << r;
+  }
+  if (key_overflow) raise_flag(st, F_INT_KEY);
+  const int i = bi * 32 + l;
+  if (i < n) adj[(int64_t)i * W + bj] = myrow;
+  if (bi < bj && jv) adj[(int64_t)j * W + bi] = mycol;
+}
+
+// ------------------------------------------------------------- row counts
+// One warp per row: degree, number of neighbours above the row id, and the
+// exclusive prefix popcount of the row's words.
+static __global__ void __launch_bounds__(256) k_rows(const uint32_t *adj, int n, int W, int32_t *adjpre, int32_t *deg,
+                                              int32_t *up) {
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int l = lane_id();
+  if (i >= n) return;
+  int carry = 0, upc = 0;
+  for (int w0 = 0; w0 < W; w0 += 32) {
+    const int w = w0 + l;
+    uint32_t word = w < W ? adj[(int64_t)i * W + w] : 0u;
+    int c = __popc(word);
+    int inc = warp_incl_scan(c);
+    if (w < W) adjpre[(int64_t)i * W + w] = carry + inc - c;
+    carry += __shfl_sync(0xffffffffu, inc, 31);
+    // bits j > i inside this word
+    uint32_t m;
+    const int lo = w * 32;
+    if (lo > i) m = 0xffffffffu;
+    else if (lo + 31 <= i) m = 0u;
+    else m = ~((2u << (i & 31)) - 1u);
+    upc += __popc(word & m);
+  }
+  upc = warp_sum(upc);
+  if (l == 0) {
+    deg[i] = carry;
+    up[i] = upc;
+  }
+}
+
+__device__ __forceinline__ int32_t bit_rank(const uint32_t *adj_row, const int32_t *pre_row, int c) {
+  const int w = c >> 5, b = c & 31;
+  return pre_row[w] + __popc(adj_row[w] & ((1u << b) - 1u));
+}
+
+// --------------------------------------------------------------- edge keys
+// One warp per row i: every kept j > i, in ascending j, at its lexicographic
+// position lex_ptr[i] + (rank of j in row i) - (neighbours <= i).
+template <bool F>
+__global__ void __launch_bounds__(256) k_edge_keys(const void *Xv, int n, int d, int W, const uint32_t *adj,
+                                                   const int32_t *adjpre, const int32_t *deg, const int32_t *up,
+                                                   const int64_t *lex_ptr, uint64_t *keys) {
+  using T = typename std::conditional<F, float, int32_t>::type;
+  const T *X = (const T *)Xv;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int l = lane_id();
+  if (i >= n) return;
+  const int64_t base = lex_ptr[i] - (int64_t)(deg[i] - up[i]);
+  const uint32_t *row = adj + (int64_t)i * W;
+  const int32_t *pre = adjpre + (int64_t)i * W;
+  for (int w = ((i + 1) >> 5) + l; w < W; w += 32) {
+    uint32_t word = row[w];
+    const int lo = w * 32;
+    if (lo <= i) word &= (lo + 31 <= i) ? 0u : ~((2u << (i & 31)) - 1u);
+    // rank of this word's first upper bit: the row's bits before it
+    int32_t r = pre[w] + (__popc(row[w]) - __popc(word));
+    while (word) {
+      const int b = __ffs(word) - 1;
+      word &= word - 1;
+      const int j = lo + b;
+      uint64_t dk;
+      if constexpr (F) dk = (uint64_t)__float_as_uint(d2_f32(X + (int64_t)i * d, X + (int64_t)j * d, d));
+      else dk = d2_int(X + (int64_t)i * d, X + (int64_t)j * d, d);
+      keys[base + r] = (dk << KEY_SHIFT) | ((uint64_t)i << ID_BITS) | (uint64_t)j;
+      ++r;
+    }
+  }
+}
+
+__device__ __forceinline__ int key_i(uint64_t k) { return (int)((k >> ID_BITS) & ID_MASK); }
+__device__ __forceinline__ int key_j(uint64_t k) { return (int)(k & ID_MASK); }
+
+// ---------------------------------------------------------- float repair
+// After the sort by the fp32 first pass, every edge gets its canonical FP64
+// value.  Neighbours whose first-pass intervals [lo, hi] overlap may be out
+// of order; they form a repair group (a maximal run where each step's
+// intervals overlap), re-sorted by (FP64 value, i, j).  Across a group
+// boundary the FP64 values are strictly ordered already.
+static __global__ void k_f64_values(const float *X, int d, const uint64_t *keys, int64_t E, double crel, double *d64,
+                             int32_t *split, DevStatus *st) {
+  double worst = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = keys[k];
+    const int i = key_i(key), j = key_j(key);
+    const double f = d2_f64(X + (int64_t)i * d, X + (int64_t)j * d, d);
+    d64[k] = f;
+    const float a = __uint_as_float((uint32_t)(key >> KEY_SHIFT));
+    int s = 1;
+    if (k > 0) {
+      const float ap = __uint_as_float((uint32_t)(keys[k - 1] >> KEY_SHIFT));
+      s = f32_lo(a, crel) > f32_hi(ap, crel) ? 1 : 0;
+    }
+    split[k] = s;
+    if (f > 0.0) {
+      double e = fabs(sqrt((double)a) - sqrt(f)) / sqrt(f);
+      worst = fmax(worst, e);
+    }
+  }
+  if (worst > 0.0) atomicMax((unsigned long long *)&st->max_rel_err_bits, (unsigned long long)__double_as_longlong(worst));
+}
+
+// Group starts from the exclusive scan of split: gbeg[gid] = k.
+static __global__ void k_group_starts(const int32_t *split, const int32_t *gex, int64_t E, int32_t *gbeg) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x)
+    if (split[k]) gbeg[gex[k]] = (int32_t)k;
+  if (blockIdx.x == 0 && threadIdx.x == 0) gbeg[gex[E]] = (int32_t)E;
+}
+
+__device__ __forceinline__ bool f64_less(double da, uint64_t ka, double db, uint64_t kb) {
+  return da < db || (da == db && (ka & ((1ull << KEY_SHIFT) - 1)) < (kb & ((1ull << KEY_SHIFT) - 1)));
+}
+
+constexpr int REPAIR_SMALL = 32;
+constexpr int REPAIR_MID = 2048;
+
+// Thread per group: insertion sort of groups up to REPAIR_SMALL edges; larger
+// groups are queued for the CTA kernels.
+static __global__ void k_repair_small(const int32_t *gbeg, const int32_t *ngroups_ptr, uint64_t *keys, double *d64,
+                               int32_t *midq, int32_t *bigq, DevStatus *st) {
+  const int64_t ngroups = *ngroups_ptr;
+  int64_t nt = 0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = gbeg[g], e = gbeg[g + 1], s = e - b;
+    if (s < 2) continue;
+    nt += s;
+    if (s > REPAIR_MID) {
+      int q = atomicAdd((int *)&st->big_grp_count, 1);
+      bigq[q] = (int32_t)g;
+      atomicMax((unsigned long long *)&st->big_grp_max, (unsigned long long)s);
+      continue;
+    }
+    if (s > REPAIR_SMALL) {
+      int q = atomicAdd(&st->mid_grp_count, 1);
+      midq[q] = (int32_t)g;
+      continue;
+    }
+    for (int64_t x = b + 1; x < e; ++x) {
+      uint64_t kx = keys[x];
+      double dx = d64[x];
+      int64_t y = x - 1;
+      while (y >= b && f64_less(dx, kx, d64[y], keys[y])) {
+        keys[y + 1] = keys[y];
+        d64[y + 1] = d64[y];
+        --y;
+      }
+      keys[y + 1] = kx;
+      d64[y + 1] = dx;
+    }
+  }
+  if (nt) atomicAdd((unsigned long long *)&st->near_tie, (unsigned long long)nt);
+}
+
+// CTA per queued mid-size group: bitonic sort in shared memory on the pair
+// (FP64 bits, i<<13|j) packed as two words; val = position in the group.
+static __global__ void __launch_bounds__(256) k_repair_mid(const int32_t *gbeg, const int32_t *midq, const DevStatus *st,
+                                                    uint64_t *keys, double *d64) {
+  __shared__ uint64_t hi[REPAIR_MID];
+  __shared__ uint32_t lo[REPAIR_MID];
+  __shared__ uint32_t val[REPAIR_MID];
+  const int nq = st->mid_grp_count;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int g = midq[q];
+    const int64_t b = gbeg[g];
+    const int s = (int)(gbeg[g + 1] - b);
+    int cap = 1;
+    while (cap < s) cap <<= 1;
+    for (int t = threadIdx.x; t < cap; t += blockDim.x) {
+      if (t < s) {
+        hi[t] = (uint64_t)__double_as_longlong(d64[b + t]);
+        lo[t] = (uint32_t)(keys[b + t] & ((1ull << KEY_SHIFT) - 1));
+      } else {
+        hi[t] = ~0ull;
+        lo[t] = ~0u;
+      }
+      val[t] = t;
+    }
+    __syncthreads();
+    for (int k = 2; k <= cap; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < cap; i += blockDim.x) {
+          int x = i ^ j;
+          if (x > i) {
+            bool up = (i & k) == 0;
+            bool gt = hi[i] > hi[x] || (hi[i] == hi[x] && lo[i] > lo[x]);
+            if (gt == up) {
+              uint64_t th = hi[i]; hi[i] = hi[x]; hi[x] = th;
+              uint32_t tl = lo[i]; lo[i] = lo[x]; lo[x] = tl;
+              uint32_t tv = val[i]; val[i] = val[x]; val[x] = tv;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    // Permute: keys' top bits and d64 follow val.  Read all first, then write.
+    uint64_t kk[REPAIR_MID / 256];
+    double dd[REPAIR_MID / 256];
+    int c = 0;
+    for (int t = threadIdx.x; t < s; t += blockDim.x, ++c) {
+      kk[c] = keys[b + val[t]];
+      dd[c] = d64[b + val[t]];
+    }
+    __syncthreads();
+    c = 0;
+    for (int t = threadIdx.x; t < s; t += blockDim.x, ++c) {
+      keys[b + t] = kk[c];
+      d64[b + t] = dd[c];
+    }
+    __syncthreads();
+  }
+}
+
+// One CTA for the queued large groups (rare: massive near-ties): stable LSD
+// sort by (i<<13|j), then by the FP64 bits, through global temporaries.
+static __global__ void __launch_bounds__(RS_THREADS) k_repair_big(const int32_t *gbeg, const int32_t *bigq,
+                                                           const DevStatus *st, uint64_t *keys, double *d64,
+                                                           uint64_t *k1, uint32_t *v1, uint64_t *k2, uint32_t *v2,
+                                                           uint64_t *gk, double *gd) {
+  const int nq = (int)st->big_grp_count;
+  for (int q = 0; q < nq; ++q) {
+    const int g = bigq[q];
+    const int64_t b = gbeg[g];
+    const int64_t s = gbeg[g + 1] - b;
+    for (int64_t t = threadIdx.x; t < s; t += blockDim.x) {
+      k1[t] = keys[b + t] & ((1ull << KEY_SHIFT) - 1);
+      v1[t] = (uint32_t)t;
+    }
+    __syncthreads();
+    cta_radix_sort_global(k1, v1, k2, v2, s, 0, KEY_SHIFT);
+    for (int64_t t = threadIdx.x; t < s; t += blockDim.x) k1[t] = (uint64_t)__double_as_longlong(d64[b + v1[t]]);
+    __syncthreads();
+    cta_radix_sort_global(k1, v1, k2, v2, s, 0, 64);
+    for (int64_t t = threadIdx.x; t < s; t += blockDim.x) {
+      gk[t] = keys[b + v1[t]];
+      gd[t] = d64[b + v1[t]];
+    }
+    __syncthreads();
+    for (int64_t t = threadIdx.x; t < s; t += blockDim.x) {
+      keys[b + t] = gk[t];
+      d64[b + t] = gd[t];
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ edge grades
+// flag[k] = 1 where the squared distance differs from the previous edge's
+// (or from 0 for k = 0): the dense rank is the running sum of flags.
+template <bool F>
+__global__ void k_edge_flags(const uint64_t *keys, const double *d64, int64_t E, int32_t *flag) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
+    int f;
+    if constexpr (F) f = k == 0 ? (d64[0] != 0.0) : (d64[k] != d64[k - 1]);
+    else f = k == 0 ? ((keys[0] >> KEY_SHIFT) != 0) : ((keys[k] >> KEY_SHIFT) != (keys[k - 1] >> KEY_SHIFT));
+    flag[k] = f;
+  }
+}
+
+// Edge outputs (verts, grade, CSC column = {i, j}), grade values, grade-group
+// starts, and the neighbour CSR scatter: entry (i -> j) sits at
+// nbr_ptr[i] + rank of j in row i, so each row lists neighbours ascending.
+template <bool F>
+__global__ void k_edge_emit(const uint64_t *keys, const double *d64, int64_t E, const int32_t *flag,
+                            const int32_t *gex, const uint32_t *adj, const int32_t *adjpre, int W,
+                            const int32_t *nbr_ptr, int32_t *verts, int32_t *grade, int64_t *colptr, int32_t *rowidx,
+                            double *gval, int32_t *gstart, int32_t *nbr_ord, DevStatus *st) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = keys[k];
+    const int i = key_i(key), j = key_j(key);
+    const int g = gex[k + 1];
+    verts[2 * k] = i;
+    verts[2 * k + 1] = j;
+    rowidx[2 * k] = i;
+    rowidx[2 * k + 1] = j;
+    colptr[k] = 2 * k;
+    grade[k] = g;
+    if (flag[k]) {
+      gval[g] = F ? d64[k] : (double)(key >> KEY_SHIFT);
+      gstart[g] = (int32_t)k;
+    }
+    nbr_ord[nbr_ptr[i] + bit_rank(adj + (int64_t)i * W, adjpre + (int64_t)i * W, j)] = (int32_t)k;
+    nbr_ord[nbr_ptr[j] + bit_rank(adj + (int64_t)j * W, adjpre + (int64_t)j * W, i)] = (int32_t)k;
+    if (k == E - 1) {
+      colptr[E] = 2 * E;
+      gstart[g + 1] = (int32_t)E;
+      st->ngrades = g + 1;
+    }
+    if (k == 0) {
+      gval[0] = 0.0;
+      gstart[0] = 0;
+    }
+  }
+}
+
+static __global__ void k_vertices(int n, int32_t *verts, int32_t *grade) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    verts[v] = v;
+    grade[v] = 0;
+  }
+}
+
+// -------------------------------------------------------------- triangles
+// Edge e = (a, b) in filtration order.  The candidates c are the set bits of
+// adj[a] & adj[b]; a triangle {a, b, c} is counted at e iff e is its largest
+// edge in the total (grade, lex) order, i.e. ord(a,c) < e and ord(b,c) < e,
+// so each triangle appears exactly once and its grade is grade(e).  One warp
+// per edge; lane l takes word 32*r + l in round r, so the warp's output is in
+// ascending c, which is already lexicographic for the sorted triple.
+
+__device__ __forceinline__ uint32_t tri_word_mask(const uint32_t *ra, const uint32_t *rb, const int32_t *pa,
+                                                  const int32_t *pb, const int32_t *ord_a, const int32_t *ord_b,
+                                                  int w, int32_t e) {
+  const uint32_t wa = ra[w], wb = rb[w];
+  uint32_t m = wa & wb, vm = 0;
+  while (m) {
+    const int bit = __ffs(m) - 1;
+    m &= m - 1;
+    const uint32_t below = (1u << bit) - 1u;
+    const int32_t oac = ord_a[pa[w] + __popc(wa & below)];
+    const int32_t obc = ord_b[pb[w] + __popc(wb & below)];
+    if (oac < e && obc < e) vm |= 1u << bit;
+  }
+  return vm;
+}
+
+static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts, int64_t E, const uint32_t *adj,
+                                                   const int32_t *adjpre, int W, const int32_t *nbr_ptr,
+                                                   const int32_t *nbr_ord, int32_t *tcnt) {
+  const int l = lane_id();
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
+    const int a = everts[2 * e], b = everts[2 * e + 1];
+    const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
+    const int32_t *pa = adjpre + (int64_t)a * W, *pb = adjpre + (int64_t)b * W;
+    const int32_t *oa = nbr_ord + nbr_ptr[a], *ob = nbr_ord + nbr_ptr[b];
+    int cnt = 0;
+    for (int w = l; w < W; w += 32) cnt += __popc(tri_word_mask(ra, rb, pa, pb, oa, ob, w, (int32_t)e));
+    cnt = warp_sum(cnt);
+    if (l == 0) tcnt[e] = cnt;
+  }
+}
+
+static __global__ void __launch_bounds__(256) k_tri_emit(const int32_t *everts, const int32_t *egrade, int64_t E,
+                                                  const uint32_t *adj, const int32_t *adjpre, int W,
+                                                  const int32_t *nbr_ptr, const int32_t *nbr_ord,
+                                                  const int64_t *toff, int32_t *tverts, int32_t *tgrade,
+                                                  int64_t *tcolptr, int32_t *trow) {
+  const int l = lane_id();
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
+    const int a = everts[2 * e], b = everts[2 * e + 1];
+    const int32_t g = egrade[e];
+    const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
+    const int32_t *pa = adjpre + (int64_t)a * W, *pb = adjpre + (int64_t)b * W;
+    const int32_t *oa = nbr_ord + nbr_ptr[a], *ob = nbr_ord + nbr_ptr[b];
+    int64_t t = toff[e];
+    for (int w0 = 0; w0 < W; w0 += 32) {
+      const int w = w0 + l;
+      uint32_t vm = w < W ? tri_word_mask(ra, rb, pa, pb, oa, ob, w, (int32_t)e) : 0u;
+      const int c = __popc(vm);
+      const int inc = warp_incl_scan(c);
+      int64_t p = t + inc - c;
+      while (vm) {
+        const int bit = __ffs(vm) - 1;
+        vm &= vm - 1;
+        const int cv = w * 32 + bit;
+        const uint32_t below = (1u << bit) - 1u;
+        const int32_t oac = oa[pa[w] + __popc(ra[w] & below)];
+        const int32_t obc = ob[pb[w] + __popc(rb[w] & below)];
+        int x0, x1, x2;
+        if (cv < a) { x0 = cv; x1 = a; x2 = b; }
+        else if (cv < b) { x0 = a; x1 = cv; x2 = b; }
+        else { x0 = a; x1 = b; x2 = cv; }
+        tverts[3 * p] = x0;
+        tverts[3 * p + 1] = x1;
+        tverts[3 * p + 2] = x2;
+        tgrade[p] = g;
+        tcolptr[p] = 3 * p;
+        trow[3 * p] = min(oac, obc);
+        trow[3 * p + 1] = max(oac, obc);
+        trow[3 * p + 2] = (int32_t)e;
+        ++p;
+      }
+      t += __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+}
+
+// Per grade group: triangles of a group that spans several edges with
+// triangles must be merged into lexicographic order.  Queue such groups.
+constexpr int TRI_MID = 4096;
+
+static __global__ void k_tri_groups(const int32_t *gstart, const int32_t *tcnt, const int64_t *toff, int32_t *midq,
+                             int32_t *bigq, DevStatus *st) {
+  const int64_t ngrades = st->ngrades;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngrades; g += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = gstart[g], e = gstart[g + 1];
+    if (e - b < 2) continue;
+    int runs = 0;
+    for (int32_t x = b; x < e && runs < 2; ++x) runs += tcnt[x] > 0;
+    if (runs < 2) continue;
+    const int64_t s = toff[e] - toff[b];
+    if (s <= TRI_MID) {
+      int q = atomicAdd(&st->mid_seg_count, 1);
+      midq[q] = (int32_t)g;
+    } else {
+      int q = atomicAdd((int *)&st->big_seg_count, 1);
+      bigq[q] = (int32_t)g;
+      atomicMax((unsigned long long *)&st->big_seg_max, (unsigned long long)s);
+    }
+  }
+}
+
+__device__ __forceinline__ uint64_t lex3(int a, int b, int c) {
+  return ((uint64_t)a << (2 * ID_BITS)) | ((uint64_t)b << ID_BITS) | (uint64_t)c;
+}
+
+// CTA per queued group: sort the segment by lexicographic key in shared
+// memory and rewrite verts and rowidx (grade and colptr do not change).
+static __global__ void __launch_bounds__(256) k_tri_fix_mid(const int32_t *gstart, const int64_t *toff, const int32_t *midq,
+                                                     const DevStatus *st, int32_t *tverts, int32_t *trow) {
+  extern __shared__ unsigned char smem[];
+  uint64_t *key = (uint64_t *)smem;                   // TRI_MID
+  uint32_t *val = (uint32_t *)(key + TRI_MID);        // TRI_MID
+  int32_t *rows = (int32_t *)(val + TRI_MID);         // 3 * TRI_MID
+  const int nq = st->mid_seg_count;
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
+    const int g = midq[q];
+    const int64_t s0 = toff[gstart[g]];
+    const int s = (int)(toff[gstart[g + 1]] - s0);
+    int cap = 1;
+    while (cap < s) cap <<= 1;
+    for (int t = threadIdx.x; t < cap; t += blockDim.x) {
+      if (t < s) {
+        key[t] = lex3(tverts[3 * (s0 + t)], tverts[3 * (s0 + t) + 1], tverts[3 * (s0 + t) + 2]);
+        rows[3 * t] = trow[3 * (s0 + t)];
+        rows[3 * t + 1] = trow[3 * (s0 + t) + 1];
+        rows[3 * t + 2] = trow[3 * (s0 + t) + 2];
+      } else {
+        key[t] = ~0ull;
+      }
+      val[t] = t;
+    }
+    __syncthreads();
+    cta_bitonic(key, val, cap);
+    for (int t = threadIdx.x; t < s; t += blockDim.x) {
+      const uint64_t k = key[t];
+      const int64_t p = s0 + t;
+      tverts[3 * p] = (int32_t)(k >> (2 * ID_BITS));
+      tverts[3 * p + 1] = (int32_t)((k >> ID_BITS) & ID_MASK);
+      tverts[3 * p + 2] = (int32_t)(k & ID_MASK);
+      const uint32_t v = val[t];
+      trow[3 * p] = rows[3 * v];
+      trow[3 * p + 1] = rows[3 * v + 1];
+      trow[3 * p + 2] = rows[3 * v + 2];
+    }
+    __syncthreads();
+  }
+}
+
+// One CTA for the rare groups above TRI_MID triangles: stable LSD sort of the
+// 39-bit lexicographic keys through global temporaries.
+static __global__ void __launch_bounds__(RS_THREADS) k_tri_fix_big(const int32_t *gstart, const int64_t *toff,
+                                                            const int32_t *bigq, const DevStatus *st, int32_t *tverts,
+                                                            int32_t *trow, uint64_t *k1, uint32_t *v1, uint64_t *k2,
+                                                            uint32_t *v2, int32_t *rtmp) {
+  const int nq = (int)st->big_seg_count;
+  for (int q = 0; q < nq; ++q) {
+    const int g = bigq[q];
+    const int64_t s0 = toff[gstart[g]];
+    const int64_t s = toff[gstart[g + 1]] - s0;
+    for (int64_t t = threadIdx.x; t < s; t += blockDim.x) {
+      const int64_t p = s0 + t;
+      k1[t] = lex3(tverts[3 * p], tverts[3 * p + 1], tverts[3 * p + 2]);
+      v1[t] = (uint32_t)t;
+      rtmp[3 * t] = trow[3 * p];
+      rtmp[3 * t + 1] = trow[3 * p + 1];
+      rtmp[3 * t + 2] = trow[3 * p + 2];
+    }
+    __syncthreads();
+    cta_radix_sort_global(k1, v1, k2, v2, s, 0, 3 * ID_BITS);
+    for (int64_t t = threadIdx.x; t < s; t += blockDim.x) {
+      const uint64_t k = k1[t];
+      const int64_t p = s0 + t;
+      tverts[3 * p] = (int32_t)(k >> (2 * ID_BITS));
+      tverts[3 * p + 1] = (int32_t)((k >> ID_BITS) & ID_MASK);
+      tverts[3 * p + 2] = (int32_t)(k & ID_MASK);
+      const uint32_t v = v1[t];
+      trow[3 * p] = rtmp[3 * v];
+      trow[3 * p + 1] = rtmp[3 * v + 1];
+      trow[3 * p + 2] = rtmp[3 * v + 2];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace vr

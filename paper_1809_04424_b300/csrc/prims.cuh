@@ -42,6 +42,8 @@ enum : int32_t {
 // Device-resident status and counters of one build (read back at sync points).
 struct DevStatus {
   int32_t flags;
+  int32_t mid_grp_count;     // float: repair groups queued for the CTA sort
+  int32_t mid_seg_count;     // triangle segments queued for the CTA sort
   int32_t pad;
   int64_t E;                 // kept edges
   int64_t T;                 // triangles
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const TI *in, int6
 }
 
 // One CTA: exclusive scan of bs[0..nb) in place, bs[nb] = total.
-__global__ void __launch_bounds__(1024) k_scan_sums(int64_t *bs, int64_t nb) {
+static __global__ void __launch_bounds__(1024) k_scan_sums(int64_t *bs, int64_t nb) {
   __shared__ int64_t sh[33];
   int64_t carry = 0;
   for (int64_t b0 = 0; b0 < nb; b0 += 1024) {
@@ -259,7 +261,7 @@ __device__ __forceinline__ void tile_rank(const uint64_t *src, int64_t t0, int64
 
 // Multi-CTA pass, step 1: per-tile digit histogram, digit-major layout
 // hist[d * ntiles + tile].
-__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *src, int64_t n, int shift, int64_t ntiles,
+static __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *src, int64_t n, int shift, int64_t ntiles,
                                                         int64_t *hist) {
   __shared__ uint32_t h[RS_BINS];
   for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) h[b] = 0;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *src, int
 }
 
 // Multi-CTA pass, step 3: stable scatter using the scanned histogram.
-__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *src, const uint32_t *vsrc, uint64_t *dst,
+static __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *src, const uint32_t *vsrc, uint64_t *dst,
                                                            uint32_t *vdst, int64_t n, int shift, int64_t ntiles,
                                                            const int64_t *off) {
   __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *src, 
 // One CTA sorts [0, n) of global arrays in place through tkeys/tvals (any n):
 // each pass histograms everything, then ranks tile after tile in order with a
 // running digit base.  Used for small sorts and for per-segment fix-ups.
-__device__ void cta_radix_sort_global(uint64_t *keys, uint32_t *vals, uint64_t *tkeys, uint32_t *tvals, int64_t n,
+static __device__ void cta_radix_sort_global(uint64_t *keys, uint32_t *vals, uint64_t *tkeys, uint32_t *tvals, int64_t n,
                                       int bit_lo, int nbits) {
   __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
   __shared__ uint32_t cnt[RS_BINS];
@@ -354,7 +356,7 @@ __device__ void cta_radix_sort_global(uint64_t *keys, uint32_t *vals, uint64_t *
   }
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_rs_single(uint64_t *keys, uint32_t *vals, uint64_t *tkeys,
+static __global__ void __launch_bounds__(RS_THREADS) k_rs_single(uint64_t *keys, uint32_t *vals, uint64_t *tkeys,
                                                           uint32_t *tvals, int64_t n, int bit_lo, int nbits) {
   cta_radix_sort_global(keys, vals, tkeys, tvals, n, bit_lo, nbits);
 }
@@ -401,7 +403,7 @@ inline vr_status radix_sort(uint64_t *keys, uint32_t *vals, int64_t n, int bit_l
 // ------------------------------------------------------- bitonic (smem)
 // Sort cap (a power of two) pairs (key, val) ascending in shared memory; keys
 // unique, slots past the live count already hold ~0 keys.
-__device__ void cta_bitonic(uint64_t *key, uint32_t *val, int cap) {
+static __device__ void cta_bitonic(uint64_t *key, uint32_t *val, int cap) {
   for (int k = 2; k <= cap; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int i = threadIdx.x; i < cap; i += blockDim.x) {
