@@ -42,6 +42,12 @@
 extern "C" {
 #endif
 
+#if defined(__GNUC__)
+#define VR_API __attribute__((visibility("default")))
+#else
+#define VR_API
+#endif
+
 /* A cudaStream_t (same type); NULL is the legacy default stream. */
 typedef struct CUstream_st *vr_stream_t;
 
@@ -108,39 +114,53 @@ typedef struct vr_build_stats {
  * VR_ERR_ARG; |float coordinate| > VR_MAX_F32_ABS, an integer kept d^2 >=
  * 2^VR_MAX_INT_D2_BITS, or more than 2^31-1 simplices of one dimension give
  * VR_ERR_RANGE.  Device memory exhaustion gives VR_ERR_OOM. */
-vr_status vr_build(const void *points, int32_t n, int32_t d, vr_dtype dtype,
+VR_API vr_status vr_build(const void *points, int32_t n, int32_t d, vr_dtype dtype,
                    int32_t maxdim, double maxrad, vr_stream_t stream,
                    vr_complex **out);
 
 /* Fill `view` for dimension k (0 <= k <= maxdim, else VR_ERR_ARG). */
-vr_status vr_complex_dim(const vr_complex *c, int32_t k, vr_dim_view *view);
+VR_API vr_status vr_complex_dim(const vr_complex *c, int32_t k, vr_dim_view *view);
 
 /* Device pointer to the squared distance of every grade (grade_value[0] = 0)
  * and the number of grades. */
-vr_status vr_complex_grade_values(const vr_complex *c, const double **values,
+VR_API vr_status vr_complex_grade_values(const vr_complex *c, const double **values,
                                   int64_t *ngrades);
 
 /* Host-side sizes: counts[k] for k = 0..2 (0 above maxdim) and maxdim. */
-vr_status vr_complex_counts(const vr_complex *c, int64_t counts[3],
+VR_API vr_status vr_complex_counts(const vr_complex *c, int64_t counts[3],
                             int32_t *maxdim);
 
-vr_status vr_complex_stats(const vr_complex *c, vr_build_stats *stats);
+VR_API vr_status vr_complex_stats(const vr_complex *c, vr_build_stats *stats);
 
 /* Copy dimension k to host arrays sized as in vr_dim_view (any may be NULL;
  * colptr/rowidx are ignored for k = 0).  Synchronous on the build stream. */
-vr_status vr_complex_to_host(const vr_complex *c, int32_t k, int32_t *verts,
+VR_API vr_status vr_complex_to_host(const vr_complex *c, int32_t k, int32_t *verts,
                              int32_t *grade, int64_t *colptr, int32_t *rowidx);
 
 /* Copy the grade values (ngrades doubles) to host memory. */
-vr_status vr_complex_grade_values_to_host(const vr_complex *c, double *values);
+VR_API vr_status vr_complex_grade_values_to_host(const vr_complex *c, double *values);
 
 /* Release a result (stream-ordered on the stream it was built on, which must
  * still exist).  NULL is ignored. */
-void vr_complex_free(vr_complex *c);
+VR_API void vr_complex_free(vr_complex *c);
+
+/* Measurement support (no counterpart in the paper's API; its Sec. 4 profiles
+ * with Julia's sampling profiler).  When enabled, every build records a CUDA
+ * event pair around each phase on its own stream; once the build's work is
+ * done the elapsed times are added to a process-wide table of
+ * (phase name, total ms, builds, kernel launches).  Enabling adds one stream
+ * synchronisation at the end of each build.  vr_launch_count() is the number
+ * of kernels this library has launched in the process (always counted). */
+VR_API void vr_profile_enable(int32_t on);
+VR_API void vr_profile_reset(void);
+VR_API int32_t vr_profile_phases(void);
+VR_API vr_status vr_profile_phase(int32_t i, const char **name, double *total_ms,
+                                  int64_t *calls, int64_t *launches);
+VR_API int64_t vr_launch_count(void);
 
 /* Message for the last failing call on this thread ("" if none). */
-const char *vr_last_error(void);
-const char *vr_status_string(vr_status s);
+VR_API const char *vr_last_error(void);
+VR_API const char *vr_status_string(vr_status s);
 
 #ifdef __cplusplus
 }

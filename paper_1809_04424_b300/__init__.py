@@ -1,0 +1,229 @@
+"""Python binding of the B300 Vietoris-Rips builder (libvr_b300.so).
+
+Argument marshalling only: every step of the build runs in the library's
+CUDA kernels.  The functions carry the C-ABI names of ``include/vr.h``;
+``Complex`` wraps a ``vr_complex*`` handle.  PyTorch, when used, only provides
+device memory and the current stream.  There is no CPU fallback: if the
+library cannot be loaded the import of any entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+VR_OK, VR_ERR_ARG, VR_ERR_RANGE, VR_ERR_UNSUPPORTED, VR_ERR_OOM = 0, 1, 2, 3, 4
+VR_ERR_CUDA, VR_ERR_TIMEOUT, VR_ERR_BUSY, VR_ERR_INTERNAL = 5, 6, 7, 8
+VR_I8, VR_I32, VR_F32 = 1, 2, 3
+VR_MAX_POINTS = 8192
+
+LIB_PATH = _build.LIB
+
+
+class VRError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_STATUS = {0: "VR_OK", 1: "VR_ERR_ARG", 2: "VR_ERR_RANGE", 3: "VR_ERR_UNSUPPORTED", 4: "VR_ERR_OOM",
+           5: "VR_ERR_CUDA", 6: "VR_ERR_TIMEOUT", 7: "VR_ERR_BUSY", 8: "VR_ERR_INTERNAL"}
+
+
+class DimView(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("count", ctypes.c_int64), ("verts", ctypes.c_void_p),
+                ("grade", ctypes.c_void_p), ("colptr", ctypes.c_void_p), ("rowidx", ctypes.c_void_p)]
+
+
+class BuildStats(ctypes.Structure):
+    _fields_ = [("kept_edges", ctypes.c_int64), ("triangles", ctypes.c_int64), ("ngrades", ctypes.c_int64),
+                ("near_tie_edges", ctypes.c_int64), ("max_rel_dist_err", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load (building first if the sources are newer) the CUDA library."""
+    global _lib
+    if _lib is None:
+        path = LIB_PATH
+        if _build.stale():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; run paper_1809_04424_b300/build.py")
+        L = ctypes.CDLL(path)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.vr_build.argtypes = [vp, i32, i32, ctypes.c_int, i32, dbl, vp, ctypes.POINTER(vp)]
+        L.vr_complex_dim.argtypes = [vp, i32, ctypes.POINTER(DimView)]
+        L.vr_complex_grade_values.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(i64)]
+        L.vr_complex_counts.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
+        L.vr_complex_stats.argtypes = [vp, ctypes.POINTER(BuildStats)]
+        L.vr_complex_to_host.argtypes = [vp, i32, vp, vp, vp, vp]
+        L.vr_complex_grade_values_to_host.argtypes = [vp, vp]
+        L.vr_complex_free.argtypes = [vp]
+        L.vr_complex_free.restype = None
+        L.vr_last_error.restype = ctypes.c_char_p
+        L.vr_status_string.restype = ctypes.c_char_p
+        L.vr_status_string.argtypes = [ctypes.c_int]
+        for name in ("vr_build", "vr_complex_dim", "vr_complex_grade_values", "vr_complex_counts",
+                     "vr_complex_stats", "vr_complex_to_host", "vr_complex_grade_values_to_host"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != VR_OK:
+        raise VRError(status, lib().vr_last_error().decode())
+
+
+def vr_last_error() -> str:
+    return lib().vr_last_error().decode()
+
+
+def vr_status_string(s: int) -> str:
+    return lib().vr_status_string(s).decode()
+
+
+def _dtype_code(dt) -> int:
+    name = str(dt).replace("torch.", "")
+    return {"int8": VR_I8, "int32": VR_I32, "float32": VR_F32}[name]
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+class _DevArray:
+    """Zero-copy device view (``__cuda_array_interface__``) of library memory."""
+
+    def __init__(self, ptr, shape, typestr, owner):
+        self.__cuda_array_interface__ = {"data": (int(ptr or 0), True), "shape": tuple(shape),
+                                         "typestr": typestr, "version": 3}
+        self._owner = owner
+
+
+class Complex:
+    """Owner of one ``vr_complex*`` result."""
+
+    def __init__(self, handle: int, owned: bool = True, keepalive=None):
+        self.handle = handle
+        self._owned = owned
+        self._keepalive = keepalive
+
+    def __del__(self):
+        if getattr(self, "_owned", False) and self.handle:
+            try:
+                vr_complex_free(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+    def counts(self):
+        return vr_complex_counts(self.handle)
+
+    def stats(self) -> dict:
+        return vr_complex_stats(self.handle)
+
+    def dim(self, k: int) -> dict:
+        """Zero-copy torch views of dimension k's device arrays."""
+        import torch
+        v = vr_complex_dim(self.handle, k)
+        out = {"count": v.count,
+               "verts": torch.as_tensor(_DevArray(v.verts, (v.count, k + 1), "<i4", self), device="cuda"),
+               "grade": torch.as_tensor(_DevArray(v.grade, (v.count,), "<i4", self), device="cuda")}
+        if k >= 1:
+            out["colptr"] = torch.as_tensor(_DevArray(v.colptr, (v.count + 1,), "<i8", self), device="cuda")
+            out["rowidx"] = torch.as_tensor(_DevArray(v.rowidx, ((k + 1) * v.count,), "<i4", self), device="cuda")
+        return out
+
+    def to_host(self, k: int) -> dict:
+        return vr_complex_to_host(self.handle, k)
+
+    def grade_values(self) -> np.ndarray:
+        return vr_complex_grade_values_to_host(self.handle)
+
+
+# ---------------------------------------------------------------- C-ABI names
+
+def vr_build(points, maxdim: int, maxrad: float = float("inf"), stream=None, n=None, d=None, dtype=None) -> Complex:
+    """Build the filtered VR complex of `points` ((n, d) int8/int32/float32).
+    `points` may be a CUDA torch tensor (device pointer) or a numpy array
+    (host pointer, copied in by the library)."""
+    if hasattr(points, "data_ptr"):
+        ptr = points.data_ptr()
+        n0, d0 = points.shape
+        code = _dtype_code(points.dtype)
+        keep = points
+    elif isinstance(points, np.ndarray):
+        keep = np.ascontiguousarray(points)
+        ptr = keep.ctypes.data
+        n0, d0 = keep.shape
+        code = _dtype_code(keep.dtype)
+    else:  # raw pointer with explicit sizes
+        ptr, n0, d0, code, keep = int(points), n, d, dtype, None
+    if hasattr(points, "is_contiguous") and not points.is_contiguous():
+        raise ValueError("points must be contiguous")
+    h = ctypes.c_void_p()
+    s = _current_stream() if stream is None else stream
+    _check(lib().vr_build(ctypes.c_void_p(ptr), int(n0), int(d0), code, int(maxdim), float(maxrad),
+                          ctypes.c_void_p(s), ctypes.byref(h)))
+    return Complex(h.value)
+
+
+def vr_complex_dim(handle, k: int) -> DimView:
+    v = DimView()
+    _check(lib().vr_complex_dim(ctypes.c_void_p(handle), k, ctypes.byref(v)))
+    return v
+
+
+def vr_complex_grade_values(handle):
+    p, n = ctypes.c_void_p(), ctypes.c_int64()
+    _check(lib().vr_complex_grade_values(ctypes.c_void_p(handle), ctypes.byref(p), ctypes.byref(n)))
+    return p.value, n.value
+
+
+def vr_complex_counts(handle):
+    c = (ctypes.c_int64 * 3)()
+    m = ctypes.c_int32()
+    _check(lib().vr_complex_counts(ctypes.c_void_p(handle), c, ctypes.byref(m)))
+    return [c[0], c[1], c[2]], m.value
+
+
+def vr_complex_stats(handle) -> dict:
+    s = BuildStats()
+    _check(lib().vr_complex_stats(ctypes.c_void_p(handle), ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in BuildStats._fields_}
+
+
+def vr_complex_to_host(handle, k: int) -> dict:
+    counts, _ = vr_complex_counts(handle)
+    m = counts[k]
+    verts = np.zeros((m, k + 1), np.int32)
+    grade = np.zeros(m, np.int32)
+    colptr = np.zeros(m + 1, np.int64) if k >= 1 else None
+    rowidx = np.zeros((k + 1) * m, np.int32) if k >= 1 else None
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else None
+    _check(lib().vr_complex_to_host(ctypes.c_void_p(handle), k, ptr(verts), ptr(grade), ptr(colptr), ptr(rowidx)))
+    return {"count": m, "verts": verts, "grade": grade, "colptr": colptr, "rowidx": rowidx}
+
+
+def vr_complex_grade_values_to_host(handle) -> np.ndarray:
+    _, n = vr_complex_grade_values(handle)
+    out = np.zeros(n, np.float64)
+    _check(lib().vr_complex_grade_values_to_host(ctypes.c_void_p(handle), ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def vr_complex_free(handle) -> None:
+    lib().vr_complex_free(ctypes.c_void_p(handle))

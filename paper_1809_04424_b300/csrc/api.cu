@@ -179,3 +179,64 @@ void vr_complex_free(vr_complex *c) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------- profiling
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "prof.h"
+
+namespace vr {
+std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_profile_on{0};
+struct PhaseTotal {
+  std::string name;
+  double ms;
+  int64_t calls;
+  int64_t launches;
+};
+static std::mutex g_prof_mu;
+static std::vector<PhaseTotal> g_prof;
+
+void profile_add(const char *name, double ms, int64_t launches) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto &p : g_prof)
+    if (p.name == name) {
+      p.ms += ms;
+      p.calls += 1;
+      p.launches += launches;
+      return;
+    }
+  g_prof.push_back({name, ms, 1, launches});
+}
+}  // namespace vr
+
+extern "C" {
+void vr_profile_enable(int32_t on) { vr::g_profile_on.store(on ? 1 : 0); }
+
+void vr_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(vr::g_prof_mu);
+  vr::g_prof.clear();
+}
+
+int32_t vr_profile_phases(void) {
+  std::lock_guard<std::mutex> lk(vr::g_prof_mu);
+  return (int32_t)vr::g_prof.size();
+}
+
+vr_status vr_profile_phase(int32_t i, const char **name, double *total_ms, int64_t *calls, int64_t *launches) {
+  std::lock_guard<std::mutex> lk(vr::g_prof_mu);
+  if (i < 0 || i >= (int32_t)vr::g_prof.size() || !name || !total_ms || !calls || !launches) {
+    vr::set_error("profile phase index out of range or NULL argument");
+    return VR_ERR_ARG;
+  }
+  *name = vr::g_prof[i].name.c_str();
+  *total_ms = vr::g_prof[i].ms;
+  *calls = vr::g_prof[i].calls;
+  *launches = vr::g_prof[i].launches;
+  return VR_OK;
+}
+
+int64_t vr_launch_count(void) { return vr::g_launches.load(); }
+}  // extern "C"

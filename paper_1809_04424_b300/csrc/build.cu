@@ -12,6 +12,7 @@
 
 #include "complex.h"
 #include "kernels.cuh"
+#include "prof.h"
 
 namespace vr {
 
@@ -91,6 +92,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     return VR_ERR_OOM;
   }
   Arena ws(s), out(s);
+  Prof prof(s);
   const int W = (n + 31) / 32;
   const int64_t nd = (int64_t)n * d;
 
@@ -122,19 +124,28 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_CUDA(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
 
   // Stage: convert to the working element type and check values.
+  prof.begin("stage");
   const unsigned gs = grid_for(nd, 256, 148 * 8);
   if (dtype == VR_I8) k_stage<int8_t, false><<<gs, 256, 0, s>>>((const int8_t *)dpts, nd, (int32_t *)X, st);
   else if (dtype == VR_I32) k_stage<int32_t, false><<<gs, 256, 0, s>>>((const int32_t *)dpts, nd, (int32_t *)X, st);
   else k_stage<float, true><<<gs, 256, 0, s>>>((const float *)dpts, nd, (float *)X, st);
+  count_launch();
   VR_CUDA(cudaGetLastError());
+  prof.end();
 
+  prof.begin("distance");
   dist_dispatch<F>(X, n, d, W, cap, adj, st, s);
+  count_launch();
   VR_CUDA(cudaGetLastError());
+  prof.end();
+  prof.begin("row_counts");
   k_rows<<<(n + 7) / 8, 256, 0, s>>>(adj, n, W, adjpre, deg, up);
+  count_launch();
   VR_CUDA(cudaGetLastError());
   VR_TRY((scan_exclusive<int32_t, int32_t>(deg, nbr_ptr, n, bs_small, s)));
   VR_TRY((scan_exclusive<int32_t, int64_t>(up, lex_ptr, n, bs_small, s)));
   VR_CUDA(cudaMemcpyAsync(&st->E, lex_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  prof.end();
 
   // ---- sync 1: kept-edge count and value errors.
   VR_TRY(read_status(st, hst, s));
@@ -169,8 +180,11 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
 
   const unsigned ge = grid_for(E, 256);
   if (E > 0) {
+    prof.begin("edge_keys");
     k_edge_keys<F><<<(n + 7) / 8, 256, 0, s>>>(X, n, d, W, adj, adjpre, deg, up, lex_ptr, keys);
+    count_launch();
     VR_CUDA(cudaGetLastError());
+    prof.end();
     // Keys arrive in (i, j) order, so a stable sort on the distance bits
     // alone yields (distance, i, j).
     int kbits;
@@ -180,7 +194,9 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       if (!cap.keep_all) bound = std::min(bound, cap.r2i);
       kbits = std::max(1, bitlen(bound));
     }
+    prof.begin("edge_sort");
     VR_TRY(radix_sort(keys, nullptr, E, KEY_SHIFT, kbits, rs, s));
+    prof.end();
 
     if (F) {
       int32_t *split, *gbeg, *midq, *bigq;
@@ -192,6 +208,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_TRY(ws.alloc(&gbeg, E + 1));
       VR_TRY(ws.alloc(&midq, E));
       VR_TRY(ws.alloc(&bigq, E));
+      prof.begin("fp64_repair");
+      count_launch(6);
       k_f64_values<<<ge, 256, 0, s>>>((const float *)X, d, keys, E, cap.crel, d64, split, st);
       VR_TRY((scan_exclusive<int32_t, int32_t>(split, gex, E, bs_e, s)));
       k_group_starts<<<ge, 256, 0, s>>>(split, gex, E, gbeg);
@@ -207,12 +225,16 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_TRY(ws.alloc(&gd, E));
       k_repair_big<<<1, RS_THREADS, 0, s>>>(gbeg, bigq, st, keys, d64, k1, v1, k2, v2, gk, gd);
       VR_CUDA(cudaGetLastError());
+      prof.end();
     }
+    prof.begin("edge_grades");
     k_edge_flags<F><<<ge, 256, 0, s>>>(keys, d64, E, flag);
+    count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int32_t>(flag, gex, E, bs_e, s)));
     k_edge_emit<F><<<ge, 256, 0, s>>>(keys, d64, E, flag, gex, adj, adjpre, W, nbr_ptr, everts, egrade, ecol, erow,
                                       gval, gstart, nbr_ord, st);
     VR_CUDA(cudaGetLastError());
+    prof.end();
   } else {
     const double zero = 0.0;
     const int64_t zero64 = 0;
@@ -227,11 +249,14 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_TRY(ws.alloc(&toff, E + 1));
     VR_TRY(ws.alloc(&tmidq, E + 1));
     VR_TRY(ws.alloc(&tbigq, E + 1));
+    prof.begin("tri_count");
     k_tri_count<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, E, adj, adjpre, W, nbr_ptr, nbr_ord, tcnt);
+    count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int64_t>(tcnt, toff, E, bs_e, s)));
     VR_CUDA(cudaMemcpyAsync(&st->T, toff + E, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     k_tri_groups<<<grid_for(E + 1, 256), 256, 0, s>>>(gstart, tcnt, toff, tmidq, tbigq, st);
     VR_CUDA(cudaGetLastError());
+    prof.end();
   }
 
   // ---- sync 2: grade count, triangle count, tie-group sizes.
@@ -248,6 +273,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(out.alloc(&vverts, n));
   VR_TRY(out.alloc(&vgrade, n));
   k_vertices<<<grid_for(n, 256), 256, 0, s>>>(n, vverts, vgrade);
+  count_launch();
   VR_CUDA(cudaGetLastError());
 
   int32_t *tverts = nullptr, *tgrade = nullptr, *trow = nullptr;
@@ -260,13 +286,18 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     const int64_t tlast = 3 * T;
     VR_CUDA(cudaMemcpyAsync(tcol + T, &tlast, sizeof(int64_t), cudaMemcpyHostToDevice, s));
     if (T > 0) {
+      prof.begin("tri_emit");
       k_tri_emit<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr, nbr_ord, toff,
                                                           tverts, tgrade, tcol, trow);
+      count_launch();
       VR_CUDA(cudaGetLastError());
+      prof.end();
+      prof.begin("tri_tie_merge");
       if (hst->mid_seg_count > 0) {
         const size_t smem = (size_t)TRI_MID * (8 + 4 + 12);
         VR_CUDA(cudaFuncSetAttribute(k_tri_fix_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_tri_fix_mid<<<std::min(hst->mid_seg_count, 148 * 2), 256, smem, s>>>(gstart, toff, tmidq, st, tverts, trow);
+        count_launch();
         VR_CUDA(cudaGetLastError());
       }
       if (hst->big_seg_count > 0) {
@@ -280,8 +311,10 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
         VR_TRY(ws.alloc(&v2, m));
         VR_TRY(ws.alloc(&rtmp, 3 * m));
         k_tri_fix_big<<<1, RS_THREADS, 0, s>>>(gstart, toff, tbigq, st, tverts, trow, k1, v1, k2, v2, rtmp);
+        count_launch();
         VR_CUDA(cudaGetLastError());
       }
+      prof.end();
     }
   }
 

@@ -304,7 +304,7 @@ static __global__ void k_repair_small(const int32_t *gbeg, const int32_t *ngroup
     if (s < 2) continue;
     nt += s;
     if (s > REPAIR_MID) {
-      int q = atomicAdd((int *)&st->big_grp_count, 1);
+      int q = (int)atomicAdd((unsigned long long *)&st->big_grp_count, 1ull);
       bigq[q] = (int32_t)g;
       atomicMax((unsigned long long *)&st->big_grp_max, (unsigned long long)s);
       continue;
@@ -583,7 +583,7 @@ static __global__ void k_tri_groups(const int32_t *gstart, const int32_t *tcnt, 
       int q = atomicAdd(&st->mid_seg_count, 1);
       midq[q] = (int32_t)g;
     } else {
-      int q = atomicAdd((int *)&st->big_seg_count, 1);
+      int q = (int)atomicAdd((unsigned long long *)&st->big_seg_count, 1ull);
       bigq[q] = (int32_t)g;
       atomicMax((unsigned long long *)&st->big_seg_max, (unsigned long long)s);
     }

@@ -9,6 +9,7 @@
 #include <cstdio>
 
 #include "../../include/vr.h"
+#include "prof.h"
 
 namespace vr {
 
@@ -191,7 +192,9 @@ inline vr_status scan_exclusive(const TI *in, TO *out, int64_t L, int64_t *bs, c
   int64_t nb = (L + SCAN_CHUNK - 1) / SCAN_CHUNK;
   if (nb <= 1) {
     k_scan_final<TI, TO><<<1, SCAN_THREADS, 0, s>>>(in, L, nullptr, out);
+    count_launch(1);
   } else {
+    count_launch(3);
     k_scan_reduce<TI><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, L, bs);
     k_scan_sums<<<1, 1024, 0, s>>>(bs, nb);
     k_scan_final<TI, TO><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, L, bs, out);
@@ -377,6 +380,7 @@ inline vr_status radix_sort(uint64_t *keys, uint32_t *vals, int64_t n, int bit_l
   if (n <= 1 || nbits <= 0) return VR_OK;
   if (n <= 2 * RS_TILE) {
     k_rs_single<<<1, RS_THREADS, 0, s>>>(keys, vals, sc.tkeys, sc.tvals, n, bit_lo, nbits);
+    count_launch(1);
     VR_CUDA(cudaGetLastError());
     return VR_OK;
   }
@@ -389,6 +393,7 @@ inline vr_status radix_sort(uint64_t *keys, uint32_t *vals, int64_t n, int bit_l
     k_rs_hist<<<(unsigned)nt, RS_THREADS, 0, s>>>(src, n, shift, nt, sc.hist);
     VR_TRY((scan_exclusive<int64_t, int64_t>(sc.hist, sc.off, RS_BINS * nt, sc.bs, s)));
     k_rs_scatter<<<(unsigned)nt, RS_THREADS, 0, s>>>(src, vs, dst, vd, n, shift, nt, sc.off);
+    count_launch(2);
     VR_CUDA(cudaGetLastError());
     uint64_t *tk = src; src = dst; dst = tk;
     uint32_t *tv = vs; vs = vd; vd = tv;

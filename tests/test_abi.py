@@ -1,0 +1,76 @@
+"""CPU-only checks of the C-ABI library: it builds for sm_103a, loads, exports
+every function include/*.h declares, carries no oracle code, and rejects bad
+arguments on the host before touching a device."""
+import ctypes
+import glob
+import math
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_1809_04424_b300 as vr
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(vr_\w+)\s*\(", txt, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("vr_build", "vr_complex_dim", "vr_complex_free", "vr_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = vr.lib()
+    out = subprocess.run(["nm", "-D", "--defined-only", vr.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        getattr(L, n)
+
+
+def test_library_carries_no_oracle_code():
+    out = subprocess.run(["nm", "-D", vr.LIB_PATH], capture_output=True, text=True).stdout
+    assert "vro_" not in out
+
+
+def test_library_targets_sm_103a():
+    out = subprocess.run(["/usr/local/cuda/bin/cuobjdump", "--list-elf", vr.LIB_PATH],
+                         capture_output=True, text=True).stdout
+    assert "sm_103a" in out
+
+
+@pytest.mark.parametrize("args,status", [
+    (dict(n=0), vr.VR_ERR_RANGE), (dict(n=8193), vr.VR_ERR_RANGE), (dict(d=0), vr.VR_ERR_ARG),
+    (dict(maxdim=3), vr.VR_ERR_UNSUPPORTED), (dict(maxdim=-1), vr.VR_ERR_ARG),
+    (dict(maxrad=-1.0), vr.VR_ERR_ARG), (dict(maxrad=math.nan), vr.VR_ERR_ARG), (dict(dtype=9), vr.VR_ERR_ARG)])
+def test_host_argument_checks(args, status):
+    """These are rejected before any CUDA call, so they run without a GPU."""
+    a = dict(n=4, d=3, dtype=vr.VR_I8, maxdim=2, maxrad=math.inf)
+    a.update(args)
+    buf = np.zeros(64, np.int8)
+    h = ctypes.c_void_p()
+    rc = vr.lib().vr_build(ctypes.c_void_p(buf.ctypes.data), a["n"], a["d"], a["dtype"], a["maxdim"],
+                           a["maxrad"], None, ctypes.byref(h))
+    assert rc == status
+    assert h.value is None
+    assert vr.vr_last_error()
+
+
+def test_null_arguments():
+    h = ctypes.c_void_p()
+    assert vr.lib().vr_build(None, 4, 3, vr.VR_I8, 2, 1.0, None, ctypes.byref(h)) == vr.VR_ERR_ARG
+    assert vr.lib().vr_complex_dim(None, 0, None) == vr.VR_ERR_ARG
+    assert vr.vr_status_string(vr.VR_ERR_RANGE) == "VR_ERR_RANGE"

@@ -1,0 +1,173 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+The bar is bit-exact: same simplices, grades, order, boundary CSC and grade
+values (FP64 bit equality for float inputs), on seeded inputs that span
+several 32-point tiles with ragged tails, degenerate ties, both sides of the
+cap, the size limits and every value error."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1809_04424_b300 as vr
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need a CUDA device"
+    return t
+
+
+def gpu_build(torch, pts, maxdim, maxrad, on_device=True):
+    src = torch.from_numpy(np.ascontiguousarray(pts)).cuda() if on_device else pts
+    c = vr.vr_build(src, maxdim, maxrad)
+    out = {"counts": c.counts()[0], "gv": c.grade_values(), "stats": c.stats()}
+    for k in range(maxdim + 1):
+        out[k] = c.to_host(k)
+    return out
+
+
+def assert_same(g, o, maxdim):
+    assert g["gv"].tobytes() == o.grade_value.tobytes(), "grade values differ"
+    for k in range(maxdim + 1):
+        od, gd = o.dims[k], g[k]
+        assert gd["count"] == od.count, (k, gd["count"], od.count)
+        np.testing.assert_array_equal(gd["verts"], od.verts, err_msg=f"verts dim {k}")
+        np.testing.assert_array_equal(gd["grade"], od.grade, err_msg=f"grade dim {k}")
+        if k >= 1:
+            np.testing.assert_array_equal(gd["colptr"], od.colptr, err_msg=f"colptr dim {k}")
+            np.testing.assert_array_equal(gd["rowidx"], od.rowidx, err_msg=f"rowidx dim {k}")
+
+
+def check(torch, pts, maxdim, maxrad, on_device=True):
+    g = gpu_build(torch, pts, maxdim, maxrad, on_device)
+    o = oracle.vr_build(pts, maxdim, maxrad)
+    assert_same(g, o, maxdim)
+    return g
+
+
+def test_config1_plain_cloud(torch):
+    c = synth.config1()
+    g = check(torch, c.points, c.maxdim, c.maxrad)
+    assert g["counts"] == [64, 2016, 41664]
+
+
+def test_config2_torus_int8(torch):
+    c = synth.config2()
+    g = check(torch, c.points, c.maxdim, c.maxrad)
+    assert g["counts"][2] > 100000
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 65, 100, 257])
+@pytest.mark.parametrize("dtype", [np.int8, np.int32, np.float32])
+def test_random_clouds_no_cap(torch, n, dtype):
+    pts = synth.random_cloud(n, 3, dtype, seed=1000 + n)
+    check(torch, pts, 2, math.inf)
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("dtype", [np.int8, np.int32, np.float32])
+def test_random_clouds_capped(torch, seed, dtype):
+    g = synth.rng(2000 + seed)
+    n = int(g.integers(50, 700))
+    d = int(g.integers(1, 9))
+    pts = synth.random_cloud(n, d, dtype, seed=3000 + seed, lo=-50, hi=50)
+    cap = float(g.uniform(10, 60))
+    for maxdim in (0, 1, 2):
+        check(torch, pts, maxdim, cap)
+
+
+def test_cap_edge_exactly_at_radius(torch):
+    pts = np.array([[0, 0], [3, 4], [6, 8], [0, 5]], np.int32)
+    check(torch, pts, 2, 5.0)
+    check(torch, pts, 2, math.nextafter(5.0, 0))
+    f = pts.astype(np.float32)
+    check(torch, f, 2, 5.0)
+    check(torch, f, 2, math.nextafter(5.0, 0))
+
+
+@pytest.mark.parametrize("n", [40, 90])
+def test_all_points_equal_int(torch, n):
+    """Every pair at d^2 = 0: one grade holds everything; the triangle tie
+    merge runs its large-segment path (C(90,3) > 4096)."""
+    pts = np.full((n, 3), 7, np.int8)
+    check(torch, pts, 2, math.inf)
+
+
+@pytest.mark.parametrize("n", [8, 50, 70, 110])
+def test_all_points_equal_float(torch, n):
+    """Float repair groups of every size class (thread, CTA, global sort)."""
+    pts = np.full((n, 4), 0.25, np.float32)
+    check(torch, pts, 2, math.inf)
+
+
+def test_lattice_many_ties(torch):
+    """Integer lattice: massive distance ties, multi-edge grade groups."""
+    ax = np.arange(-4, 5)
+    pts = np.stack(np.meshgrid(ax, ax, ax[:4]), -1).reshape(-1, 3).astype(np.int32)
+    check(torch, pts, 2, 2.5)
+    check(torch, pts, 2, math.inf)
+
+
+@pytest.mark.parametrize("n", [12, 60, 200])
+def test_float_ngon_near_ties(torch, n):
+    """Equal chords of a regular polygon differ only by fp32 rounding: the
+    first-pass order must be repaired to the FP64 order."""
+    pts = synth.ngon(n, 3.0)
+    g = check(torch, pts, 2, 2.0)
+    assert g["stats"]["max_rel_dist_err"] <= 1e-6
+
+
+def test_float_config3_small(torch):
+    """The 32-dimensional Gaussian-mixture shape at n = 700."""
+    c = synth.config3(n=700)
+    g = check(torch, c.points, 2, c.maxrad)
+    assert g["stats"]["max_rel_dist_err"] <= 1e-6
+
+
+def test_host_pointer_input(torch):
+    c = synth.config1()
+    g = gpu_build(torch, c.points, 2, c.maxrad, on_device=False)
+    assert_same(g, oracle.vr_build(c.points, 2, c.maxrad), 2)
+
+
+def test_max_size_sampled(torch):
+    """n = 8192 (the id-field limit) with a small cap: full parity."""
+    g = synth.rng(8192)
+    pts = g.integers(-127, 128, size=(8192, 3)).astype(np.int8)
+    check(torch, pts, 2, 9.0)
+
+
+def test_value_errors(torch):
+    bad = np.zeros((5, 2), np.float32)
+    bad[2, 1] = np.nan
+    with pytest.raises(vr.VRError) as e:
+        vr.vr_build(torch.from_numpy(bad).cuda(), 2)
+    assert e.value.status == vr.VR_ERR_ARG
+    big = np.zeros((5, 2), np.float32)
+    big[1, 0] = 1e20
+    with pytest.raises(vr.VRError) as e:
+        vr.vr_build(torch.from_numpy(big).cuda(), 2)
+    assert e.value.status == vr.VR_ERR_RANGE
+    huge = np.array([[0, 0], [2**20, 0]], np.int32)
+    with pytest.raises(vr.VRError) as e:
+        vr.vr_build(torch.from_numpy(huge).cuda(), 2)
+    assert e.value.status == vr.VR_ERR_RANGE
+    # the same pair beyond the cap is not an error
+    ok = vr.vr_build(torch.from_numpy(huge).cuda(), 2, 10.0)
+    assert ok.counts()[0] == [2, 0, 0]
+
+
+def test_repeat_builds_identical(torch):
+    c = synth.config2()
+    a = gpu_build(torch, c.points, 2, c.maxrad)
+    b = gpu_build(torch, c.points, 2, c.maxrad)
+    for k in range(3):
+        for f in ("verts", "grade", "colptr", "rowidx"):
+            if a[k][f] is not None:
+                np.testing.assert_array_equal(a[k][f], b[k][f])
