@@ -1,0 +1,314 @@
+"""Benchmark: VR filtered-complex build throughput (simplices/s) on one cloud.
+
+Workload (default): 1000 points on a torus (R=3, r=1) + N(0, 0.05^2) noise,
+scaled by 30 to an int8 grid, radius cap at the 15th-percentile pairwise
+squared distance, simplices up to dimension 2 (vertices, edges, triangles).
+
+One step = one complete vr_build (distances, cap, ranking, enumeration,
+(grade, lex) order, boundary CSC) from device-resident points; its result is
+freed after the step's end event.  L2 is flushed (256 MB write) between timed
+steps, outside the per-step events.  e2e repeats the step through the same
+C-ABI call with the points in pinned host memory and copies every output
+array back to pinned host memory inside the timed region.
+
+--impl reference times the plain CPU oracle (the correctness reference) on
+the host cores on the same workload; it is a deliberately slow program.
+Multi-GPU (torchrun): the single-cloud build does not shard, so every rank
+builds its own replica ("replicas only"); value = all ranks' simplices / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "torus n=1000 d=3 int8 (scale 30, noise 0.05), cap at 15th-pct d^2, maxdim 2"
+METRIC = "VR simplices/s"
+
+# Algorithmic bytes per unit of each phase.
+#   tri_emit:  36 B written per triangle (verts 12, grade 4, rowidx 12, colptr 8)
+#   edge_sort: 8 B read + 8 B written per key per pass
+#   edge_grades: keys 8 read, flags 4+4, outputs 8+4+8+8, CSR scatter 8 per edge
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the run."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_rate(cloud, seconds: float):
+    """Time the oracle as it stands on full builds of the workload."""
+    import oracle
+    oracle.build()
+    reps, t0 = 0, time.perf_counter()
+    simp = 0
+    while True:
+        cx = oracle.vr_build(cloud.points, cloud.maxdim, cloud.maxrad)
+        simp += sum(d.count for d in cx.dims)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return simp / el, reps, el
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    cloud = synth.config2()
+    for _ in range(args.warmup):
+        oracle.vr_build(cloud.points, cloud.maxdim, cloud.maxrad)
+    t0 = time.perf_counter()
+    simp = 0
+    for _ in range(args.steps):
+        cx = oracle.vr_build(cloud.points, cloud.maxdim, cloud.maxrad)
+        simp += sum(d.count for d in cx.dims)
+    el = time.perf_counter() - t0
+    v = simp / el
+    line = {"metric": METRIC, "value": v, "unit": "simplices/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": cloud.n, "d": cloud.d, "maxdim": cloud.maxdim},
+            "cpu_baseline": {"value": v, "unit": "simplices/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full builds of the workload, single-threaded C oracle"},
+            "e2e": {"value": v, "unit": "simplices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1809_04424_b300 as vr
+
+    world, rank, local = dist_env()
+    assert torch.cuda.is_available(), "bench needs a CUDA device"
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    W = max(args.warmup, 3)
+    L = vr.lib()
+
+    cloud = synth.config2()
+    pts_dev = torch.from_numpy(cloud.points).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        c = vr.vr_build(pts_dev, cloud.maxdim, cloud.maxrad)
+        return c
+
+    for _ in range(W):
+        c = step()
+        counts = c.counts()[0]
+        del c
+    torch.cuda.synchronize()
+    simplices = sum(counts)
+
+    # ---- timed region: K steps, per-step CUDA events, L2 flushed between.
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    L.vr_profile_reset()
+    L.vr_profile_enable(1)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = L.vr_launch_count()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            c = step()
+            ev[k][1].record(stream)
+            del c
+        torch.cuda.synchronize()
+    launches = L.vr_launch_count() - launches0
+    L.vr_profile_enable(0)
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = simplices * args.steps * world / (total_ms / 1e3)
+
+    # Per-phase times from the library's events on the build stream.
+    import ctypes
+    phases = {}
+    for i in range(L.vr_profile_phases()):
+        nm, ms, calls, nl = ctypes.c_char_p(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        L.vr_profile_phase(i, ctypes.byref(nm), ctypes.byref(ms), ctypes.byref(calls), ctypes.byref(nl))
+        phases[nm.value.decode()] = {"ms_per_call": ms.value / max(calls.value, 1), "calls": calls.value,
+                                     "launches_per_call": nl.value / max(calls.value, 1)}
+
+    # ---- e2e: host (pinned) points in, every output array back to pinned host.
+    host_pts = torch.from_numpy(cloud.points).pin_memory()
+    c0 = vr.vr_build(pts_dev, cloud.maxdim, cloud.maxrad)
+    cnt, _ = c0.counts()
+    del c0
+    bufs = []
+    for k in range(3):
+        m = cnt[k]
+        bufs.append([torch.empty(m * (k + 1), dtype=torch.int32).pin_memory(),
+                     torch.empty(m, dtype=torch.int32).pin_memory(),
+                     torch.empty(m + 1, dtype=torch.int64).pin_memory() if k else None,
+                     torch.empty(m * (k + 1), dtype=torch.int32).pin_memory() if k else None])
+    d2h = sum(b.numel() * b.element_size() for bb in bufs for b in bb if b is not None)
+    gv = None
+
+    def e2e_step():
+        nonlocal gv
+        c = vr.vr_build(host_pts.data_ptr(), cloud.maxdim, cloud.maxrad, n=cloud.n, d=cloud.d,
+                        dtype=vr.VR_I8)
+        for k in range(3):
+            b = bufs[k]
+            p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+            rc = L.vr_complex_to_host(ctypes.c_void_p(c.handle), k, p(b[0]), p(b[1]), p(b[2]), p(b[3]))
+            assert rc == 0, vr.vr_last_error()
+        _, ng = vr.vr_complex_grade_values(c.handle)
+        if gv is None:
+            gv = torch.empty(ng, dtype=torch.float64).pin_memory()
+        L.vr_complex_grade_values_to_host(ctypes.c_void_p(c.handle), ctypes.c_void_p(gv.data_ptr()))
+        del c
+
+    for _ in range(W):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    d2h += gv.numel() * 8
+    e2e_val = simplices * args.steps * world / e2e_s
+
+    # ---- roofline of the dominant phase.
+    hbm, src = peaks()
+    dom = max(phases, key=lambda k: phases[k]["ms_per_call"]) if phases else None
+    E, T = cnt[1], cnt[2]
+    alg_bytes = {"tri_emit": 36 * T, "edge_sort": 16 * E * 2, "edge_grades": 52 * E,
+                 "tri_count": 4 * E, "tri_tie_merge": 48 * T}
+    roof = None
+    if dom in alg_bytes:
+        ms = phases[dom]["ms_per_call"]
+        ach = alg_bytes[dom] / (ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": src,
+                "algorithmic_bytes_per_launch": alg_bytes[dom]}
+
+    line = {"metric": METRIC, "value": value, "unit": "simplices/s", "n_gpus": world, "steps": args.steps,
+            "warmup": W, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": cloud.n, "d": cloud.d, "maxdim": cloud.maxdim,
+                       "maxrad": cloud.maxrad, "simplices_per_step": simplices,
+                       "counts": counts, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "e2e": {"value": e2e_val, "unit": "simplices/s", "h2d_bytes_per_step": cloud.n * cloud.d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "phases_ms": {k: round(v["ms_per_call"], 4) for k, v in phases.items()},
+            "clocks": clk.summary()}
+    if rank == 0 and world == 1:
+        r, reps, el = oracle_rate(cloud, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": r, "unit": "simplices/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{reps} full builds of the workload in {el:.1f} s, single-threaded"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
