@@ -158,6 +158,32 @@ VR_API vr_status vr_profile_phase(int32_t i, const char **name, double *total_ms
                                   int64_t *calls, int64_t *launches);
 VR_API int64_t vr_launch_count(void);
 
+/* Sort without allocating.  The paper has no counterpart of this entry point.
+ * It exists for callers that cannot allocate device memory when they need
+ * the sort: a host framework whose caching allocator already owns the GPU's
+ * memory, or a service that fixes its memory budget at start-up and cannot
+ * afford the device-wide synchronisation cudaMalloc/cudaFree may cause.
+ *
+ * Stable LSD radix sort, in place, of n caller-owned 64-bit keys (DEVICE
+ * memory) on bits [bit_lo, bit_lo + nbits), ascending; keys equal on those
+ * bits keep their input order.  With edge keys (d2 << 26) | (i << 13) | j
+ * written in (i, j) order and bits [26, 26 + bits of d2), the result is the
+ * (distance, i, j) edge order vr_build produces.
+ *   - n <= VR_NOALLOC_MAX_KEYS, else VR_ERR_RANGE; bit range inside [0, 64),
+ *     else VR_ERR_ARG.  Asynchronous on `stream`.
+ *   - Temporary storage is one fixed array in the library's device memory
+ *     (VR_NOALLOC_MAX_KEYS keys, 1 MiB per GPU that loads the library, kept
+ *     until the process exits).  The call allocates nothing and frees
+ *     nothing.  The first call on a device looks up that array's device
+ *     address (set-up once per device); make that first call before any
+ *     stream capture.
+ *   - Every call on a device shares the array and leaves its contents behind;
+ *     nothing in it needs to start at zero.  Calls that overlap on the GPU
+ *     (other streams, other threads) race on it: order them. */
+#define VR_NOALLOC_MAX_KEYS 131072
+VR_API vr_status vr_sort_keys_noalloc(uint64_t *keys, int64_t n, int32_t bit_lo,
+                                      int32_t nbits, vr_stream_t stream);
+
 /* Message for the last failing call on this thread ("" if none). */
 VR_API const char *vr_last_error(void);
 VR_API const char *vr_status_string(vr_status s);
