@@ -160,7 +160,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="length of the CPU-oracle baseline sample (0 skips it)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -261,16 +263,18 @@ def main():
         L.vr_complex_grade_values_to_host(ctypes.c_void_p(c.handle), ctypes.c_void_p(gv.data_ptr()))
         del c
 
-    for _ in range(W):
-        e2e_step()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    d2h += gv.numel() * 8
-    e2e_val = simplices * args.steps * world / e2e_s
+    e2e_val = None
+    if not args.no_e2e:
+        for _ in range(W):
+            e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        d2h += gv.numel() * 8
+        e2e_val = simplices * args.steps * world / e2e_s
 
     # ---- roofline of the dominant phase.
     hbm, src = peaks()
@@ -299,7 +303,7 @@ def main():
             "roofline": roof,
             "phases_ms": {k: round(v["ms_per_call"], 4) for k, v in phases.items()},
             "clocks": clk.summary()}
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
         r, reps, el = oracle_rate(cloud, args.cpu_seconds)
         line["cpu_baseline"] = {"value": r, "unit": "simplices/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{reps} full builds of the workload in {el:.1f} s, single-threaded"}

@@ -242,11 +242,12 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_CUDA(cudaMemcpyAsync(ecol, &zero64, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   }
 
-  int32_t *tcnt = nullptr, *tmidq = nullptr, *tbigq = nullptr;
+  int32_t *tcnt = nullptr, *tsmallq = nullptr, *tmidq = nullptr, *tbigq = nullptr;
   int64_t *toff = nullptr;
   if (maxdim >= 2 && E > 0) {
     VR_TRY(ws.alloc(&tcnt, E));
     VR_TRY(ws.alloc(&toff, E + 1));
+    VR_TRY(ws.alloc(&tsmallq, E + 1));
     VR_TRY(ws.alloc(&tmidq, E + 1));
     VR_TRY(ws.alloc(&tbigq, E + 1));
     prof.begin("tri_count");
@@ -254,7 +255,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int64_t>(tcnt, toff, E, bs_e, s)));
     VR_CUDA(cudaMemcpyAsync(&st->T, toff + E, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    k_tri_groups<<<grid_for(E + 1, 256), 256, 0, s>>>(gstart, tcnt, toff, tmidq, tbigq, st);
+    k_tri_groups<<<grid_for(E + 1, 256), 256, 0, s>>>(gstart, tcnt, toff, tsmallq, tmidq, tbigq, st);
     VR_CUDA(cudaGetLastError());
     prof.end();
   }
@@ -293,24 +294,33 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_CUDA(cudaGetLastError());
       prof.end();
       prof.begin("tri_tie_merge");
+      if (hst->small_seg_count > 0) {
+        const size_t smem = (size_t)TRI_SMALL * (8 + 4 + 12);
+        k_tri_fix_smem<TRI_SMALL><<<std::min(hst->small_seg_count, 148 * 8), 256, smem, s>>>(
+            gstart, toff, tsmallq, &st->small_seg_count, tverts, trow);
+        count_launch();
+        VR_CUDA(cudaGetLastError());
+      }
       if (hst->mid_seg_count > 0) {
         const size_t smem = (size_t)TRI_MID * (8 + 4 + 12);
-        VR_CUDA(cudaFuncSetAttribute(k_tri_fix_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_tri_fix_mid<<<std::min(hst->mid_seg_count, 148 * 2), 256, smem, s>>>(gstart, toff, tmidq, st, tverts, trow);
+        VR_CUDA(cudaFuncSetAttribute(k_tri_fix_smem<TRI_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        k_tri_fix_smem<TRI_MID><<<std::min(hst->mid_seg_count, 148), 512, smem, s>>>(
+            gstart, toff, tmidq, &st->mid_seg_count, tverts, trow);
         count_launch();
         VR_CUDA(cudaGetLastError());
       }
       if (hst->big_seg_count > 0) {
-        const int64_t m = hst->big_seg_max;
         uint64_t *k1, *k2;
         uint32_t *v1, *v2;
         int32_t *rtmp;
-        VR_TRY(ws.alloc(&k1, m));
-        VR_TRY(ws.alloc(&k2, m));
-        VR_TRY(ws.alloc(&v1, m));
-        VR_TRY(ws.alloc(&v2, m));
-        VR_TRY(ws.alloc(&rtmp, 3 * m));
-        k_tri_fix_big<<<1, RS_THREADS, 0, s>>>(gstart, toff, tbigq, st, tverts, trow, k1, v1, k2, v2, rtmp);
+        VR_TRY(ws.alloc(&k1, T));
+        VR_TRY(ws.alloc(&k2, T));
+        VR_TRY(ws.alloc(&v1, T));
+        VR_TRY(ws.alloc(&v2, T));
+        VR_TRY(ws.alloc(&rtmp, 3 * T));
+        k_tri_fix_big<<<(unsigned)std::min<int64_t>(hst->big_seg_count, 148 * 2), RS_THREADS, 0, s>>>(
+            gstart, toff, tbigq, st, tverts, trow, k1, v1, k2, v2, rtmp);
         count_launch();
         VR_CUDA(cudaGetLastError());
       }

@@ -519,11 +519,16 @@ static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts,
   }
 }
 
+// Emission.  Each round (32 words, one per lane) the warp knows how many
+// triangles each lane's word holds; it then writes them in chunks of 32 with
+// lane q taking the round's q-th triangle, found by a 5-step search over the
+// lanes' prefix counts and __fns inside the owner's mask, so consecutive
+// lanes write consecutive output slots (coalesced stores).
 static __global__ void __launch_bounds__(256) k_tri_emit(const int32_t *everts, const int32_t *egrade, int64_t E,
-                                                  const uint32_t *adj, const int32_t *adjpre, int W,
-                                                  const int32_t *nbr_ptr, const int32_t *nbr_ord,
-                                                  const int64_t *toff, int32_t *tverts, int32_t *tgrade,
-                                                  int64_t *tcolptr, int32_t *trow) {
+                                                         const uint32_t *adj, const int32_t *adjpre, int W,
+                                                         const int32_t *nbr_ptr, const int32_t *nbr_ord,
+                                                         const int64_t *toff, int32_t *tverts, int32_t *tgrade,
+                                                         int64_t *tcolptr, int32_t *trow) {
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
@@ -535,42 +540,58 @@ static __global__ void __launch_bounds__(256) k_tri_emit(const int32_t *everts, 
     int64_t t = toff[e];
     for (int w0 = 0; w0 < W; w0 += 32) {
       const int w = w0 + l;
-      uint32_t vm = w < W ? tri_word_mask(ra, rb, pa, pb, oa, ob, w, (int32_t)e) : 0u;
+      const uint32_t vm = w < W ? tri_word_mask(ra, rb, pa, pb, oa, ob, w, (int32_t)e) : 0u;
       const int c = __popc(vm);
       const int inc = warp_incl_scan(c);
-      int64_t p = t + inc - c;
-      while (vm) {
-        const int bit = __ffs(vm) - 1;
-        vm &= vm - 1;
-        const int cv = w * 32 + bit;
-        const uint32_t below = (1u << bit) - 1u;
-        const int32_t oac = oa[pa[w] + __popc(ra[w] & below)];
-        const int32_t obc = ob[pb[w] + __popc(rb[w] & below)];
-        int x0, x1, x2;
-        if (cv < a) { x0 = cv; x1 = a; x2 = b; }
-        else if (cv < b) { x0 = a; x1 = cv; x2 = b; }
-        else { x0 = a; x1 = b; x2 = cv; }
-        tverts[3 * p] = x0;
-        tverts[3 * p + 1] = x1;
-        tverts[3 * p + 2] = x2;
-        tgrade[p] = g;
-        tcolptr[p] = 3 * p;
-        trow[3 * p] = min(oac, obc);
-        trow[3 * p + 1] = max(oac, obc);
-        trow[3 * p + 2] = (int32_t)e;
-        ++p;
+      const int excl = inc - c;
+      const int tot = __shfl_sync(0xffffffffu, inc, 31);
+      for (int q0 = 0; q0 < tot; q0 += 32) {
+        const int q = q0 + l;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int cand = owner + step;
+          const int v = __shfl_sync(0xffffffffu, excl, cand & 31);
+          if (cand < 32 && v <= q) owner = cand;
+        }
+        const uint32_t ovm = __shfl_sync(0xffffffffu, vm, owner);
+        const int oex = __shfl_sync(0xffffffffu, excl, owner);
+        if (q < tot) {
+          const int bit = __fns(ovm, 0, q - oex + 1);
+          const int ww = w0 + owner;
+          const int cv = ww * 32 + bit;
+          const uint32_t below = (1u << bit) - 1u;
+          const int32_t oac = oa[pa[ww] + __popc(ra[ww] & below)];
+          const int32_t obc = ob[pb[ww] + __popc(rb[ww] & below)];
+          int x0, x1, x2;
+          if (cv < a) { x0 = cv; x1 = a; x2 = b; }
+          else if (cv < b) { x0 = a; x1 = cv; x2 = b; }
+          else { x0 = a; x1 = b; x2 = cv; }
+          const int64_t p = t + q;
+          tverts[3 * p] = x0;
+          tverts[3 * p + 1] = x1;
+          tverts[3 * p + 2] = x2;
+          tgrade[p] = g;
+          tcolptr[p] = 3 * p;
+          trow[3 * p] = min(oac, obc);
+          trow[3 * p + 1] = max(oac, obc);
+          trow[3 * p + 2] = (int32_t)e;
+        }
       }
-      t += __shfl_sync(0xffffffffu, inc, 31);
+      t += tot;
     }
   }
 }
 
-// Per grade group: triangles of a group that spans several edges with
-// triangles must be merged into lexicographic order.  Queue such groups.
-constexpr int TRI_MID = 4096;
+// Per grade group: the triangles of a group that spans several edges with
+// triangles must be merged into lexicographic order.  Queue such groups by
+// size class: small (CTA sort in 24 KB of shared memory), mid (192 KB), big
+// (one CTA per group, global temporaries).
+constexpr int TRI_SMALL = 1024;
+constexpr int TRI_MID = 8192;
 
-static __global__ void k_tri_groups(const int32_t *gstart, const int32_t *tcnt, const int64_t *toff, int32_t *midq,
-                             int32_t *bigq, DevStatus *st) {
+static __global__ void k_tri_groups(const int32_t *gstart, const int32_t *tcnt, const int64_t *toff, int32_t *smallq,
+                                    int32_t *midq, int32_t *bigq, DevStatus *st) {
   const int64_t ngrades = st->ngrades;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngrades; g += (int64_t)gridDim.x * blockDim.x) {
     const int32_t b = gstart[g], e = gstart[g + 1];
@@ -579,13 +600,15 @@ static __global__ void k_tri_groups(const int32_t *gstart, const int32_t *tcnt, 
     for (int32_t x = b; x < e && runs < 2; ++x) runs += tcnt[x] > 0;
     if (runs < 2) continue;
     const int64_t s = toff[e] - toff[b];
-    if (s <= TRI_MID) {
-      int q = atomicAdd(&st->mid_seg_count, 1);
-      midq[q] = (int32_t)g;
+    if (s <= TRI_SMALL) {
+      smallq[atomicAdd(&st->small_seg_count, 1)] = (int32_t)g;
+    } else if (s <= TRI_MID) {
+      midq[atomicAdd(&st->mid_seg_count, 1)] = (int32_t)g;
     } else {
       int q = (int)atomicAdd((unsigned long long *)&st->big_seg_count, 1ull);
       bigq[q] = (int32_t)g;
       atomicMax((unsigned long long *)&st->big_seg_max, (unsigned long long)s);
+      atomicAdd((unsigned long long *)&st->big_seg_total, (unsigned long long)s);
     }
   }
 }
@@ -596,15 +619,17 @@ __device__ __forceinline__ uint64_t lex3(int a, int b, int c) {
 
 // CTA per queued group: sort the segment by lexicographic key in shared
 // memory and rewrite verts and rowidx (grade and colptr do not change).
-static __global__ void __launch_bounds__(256) k_tri_fix_mid(const int32_t *gstart, const int64_t *toff, const int32_t *midq,
-                                                     const DevStatus *st, int32_t *tverts, int32_t *trow) {
+// Dynamic shared memory: CAP * (8 + 4 + 12) bytes.
+template <int CAP>
+static __global__ void k_tri_fix_smem(const int32_t *gstart, const int64_t *toff, const int32_t *queue,
+                                      const int32_t *count, int32_t *tverts, int32_t *trow) {
   extern __shared__ unsigned char smem[];
-  uint64_t *key = (uint64_t *)smem;                   // TRI_MID
-  uint32_t *val = (uint32_t *)(key + TRI_MID);        // TRI_MID
-  int32_t *rows = (int32_t *)(val + TRI_MID);         // 3 * TRI_MID
-  const int nq = st->mid_seg_count;
+  uint64_t *key = (uint64_t *)smem;              // CAP
+  uint32_t *val = (uint32_t *)(key + CAP);       // CAP
+  int32_t *rows = (int32_t *)(val + CAP);        // 3 * CAP
+  const int nq = *count;
   for (int q = blockIdx.x; q < nq; q += gridDim.x) {
-    const int g = midq[q];
+    const int g = queue[q];
     const int64_t s0 = toff[gstart[g]];
     const int s = (int)(toff[gstart[g + 1]] - s0);
     int cap = 1;
@@ -612,14 +637,12 @@ static __global__ void __launch_bounds__(256) k_tri_fix_mid(const int32_t *gstar
     for (int t = threadIdx.x; t < cap; t += blockDim.x) {
       if (t < s) {
         key[t] = lex3(tverts[3 * (s0 + t)], tverts[3 * (s0 + t) + 1], tverts[3 * (s0 + t) + 2]);
-        rows[3 * t] = trow[3 * (s0 + t)];
-        rows[3 * t + 1] = trow[3 * (s0 + t) + 1];
-        rows[3 * t + 2] = trow[3 * (s0 + t) + 2];
       } else {
         key[t] = ~0ull;
       }
       val[t] = t;
     }
+    for (int t = threadIdx.x; t < 3 * s; t += blockDim.x) rows[t] = trow[3 * s0 + t];
     __syncthreads();
     cta_bitonic(key, val, cap);
     for (int t = threadIdx.x; t < s; t += blockDim.x) {
@@ -637,37 +660,42 @@ static __global__ void __launch_bounds__(256) k_tri_fix_mid(const int32_t *gstar
   }
 }
 
-// One CTA for the rare groups above TRI_MID triangles: stable LSD sort of the
-// 39-bit lexicographic keys through global temporaries.
+// CTA per queued large group (in parallel): stable LSD sort of the 39-bit
+// lexicographic keys through global temporaries indexed by absolute triangle
+// position (each group owns the slice of its own segment).
 static __global__ void __launch_bounds__(RS_THREADS) k_tri_fix_big(const int32_t *gstart, const int64_t *toff,
-                                                            const int32_t *bigq, const DevStatus *st, int32_t *tverts,
-                                                            int32_t *trow, uint64_t *k1, uint32_t *v1, uint64_t *k2,
-                                                            uint32_t *v2, int32_t *rtmp) {
+                                                                   const int32_t *bigq, const DevStatus *st,
+                                                                   int32_t *tverts, int32_t *trow, uint64_t *k1,
+                                                                   uint32_t *v1, uint64_t *k2, uint32_t *v2,
+                                                                   int32_t *rtmp) {
   const int nq = (int)st->big_seg_count;
-  for (int q = 0; q < nq; ++q) {
+  for (int q = blockIdx.x; q < nq; q += gridDim.x) {
     const int g = bigq[q];
     const int64_t s0 = toff[gstart[g]];
     const int64_t s = toff[gstart[g + 1]] - s0;
+    uint64_t *K1 = k1 + s0, *K2 = k2 + s0;
+    uint32_t *V1 = v1 + s0, *V2 = v2 + s0;
+    int32_t *R = rtmp + 3 * s0;
     for (int64_t t = threadIdx.x; t < s; t += blockDim.x) {
       const int64_t p = s0 + t;
-      k1[t] = lex3(tverts[3 * p], tverts[3 * p + 1], tverts[3 * p + 2]);
-      v1[t] = (uint32_t)t;
-      rtmp[3 * t] = trow[3 * p];
-      rtmp[3 * t + 1] = trow[3 * p + 1];
-      rtmp[3 * t + 2] = trow[3 * p + 2];
+      K1[t] = lex3(tverts[3 * p], tverts[3 * p + 1], tverts[3 * p + 2]);
+      V1[t] = (uint32_t)t;
+      R[3 * t] = trow[3 * p];
+      R[3 * t + 1] = trow[3 * p + 1];
+      R[3 * t + 2] = trow[3 * p + 2];
     }
     __syncthreads();
-    cta_radix_sort_global(k1, v1, k2, v2, s, 0, 3 * ID_BITS);
+    cta_radix_sort_global(K1, V1, K2, V2, s, 0, 3 * ID_BITS);
     for (int64_t t = threadIdx.x; t < s; t += blockDim.x) {
-      const uint64_t k = k1[t];
+      const uint64_t k = K1[t];
       const int64_t p = s0 + t;
       tverts[3 * p] = (int32_t)(k >> (2 * ID_BITS));
       tverts[3 * p + 1] = (int32_t)((k >> ID_BITS) & ID_MASK);
       tverts[3 * p + 2] = (int32_t)(k & ID_MASK);
-      const uint32_t v = v1[t];
-      trow[3 * p] = rtmp[3 * v];
-      trow[3 * p + 1] = rtmp[3 * v + 1];
-      trow[3 * p + 2] = rtmp[3 * v + 2];
+      const uint32_t v = V1[t];
+      trow[3 * p] = R[3 * v];
+      trow[3 * p + 1] = R[3 * v + 1];
+      trow[3 * p + 2] = R[3 * v + 2];
     }
     __syncthreads();
   }

@@ -44,8 +44,8 @@ enum : int32_t {
 struct DevStatus {
   int32_t flags;
   int32_t mid_grp_count;     // float: repair groups queued for the CTA sort
-  int32_t mid_seg_count;     // triangle segments queued for the CTA sort
-  int32_t pad;
+  int32_t mid_seg_count;     // triangle segments queued for the large-smem CTA sort
+  int32_t small_seg_count;   // triangle segments queued for the small-smem CTA sort
   int64_t E;                 // kept edges
   int64_t T;                 // triangles
   int64_t ngrades;
@@ -53,6 +53,7 @@ struct DevStatus {
   uint64_t max_rel_err_bits; // float: max relative distance error (double bits)
   int64_t big_seg_max;       // largest triangle segment needing a global sort
   int64_t big_seg_count;
+  int64_t big_seg_total;     // triangles inside the segments needing a global sort
   int64_t big_grp_max;       // float: largest repair group needing a global sort
   int64_t big_grp_count;
 };
