@@ -251,7 +251,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_TRY(ws.alloc(&tmidq, E + 1));
     VR_TRY(ws.alloc(&tbigq, E + 1));
     prof.begin("tri_count");
-    k_tri_count<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, E, adj, adjpre, W, nbr_ptr, nbr_ord, tcnt);
+    k_tri_count<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, E, adj, adjpre, W, nbr_ptr, nbr_ord, deg, up,
+                                                           lex_ptr, st, tcnt);
     count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int64_t>(tcnt, toff, E, bs_e, s)));
     VR_CUDA(cudaMemcpyAsync(&st->T, toff + E, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
@@ -286,7 +287,31 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_TRY(out.alloc(&trow, 3 * T));
     const int64_t tlast = 3 * T;
     VR_CUDA(cudaMemcpyAsync(tcol + T, &tlast, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    if (T > 0) {
+    if (T > 0 && lex_mode(E, ngrades)) {
+      // Lex-order generation, stable sort on the grade bits, final write.
+      uint64_t *tk;
+      RadixScratch trs{};
+      const int64_t tnt = rs_tiles(T);
+      VR_TRY(ws.alloc(&tk, T));
+      VR_TRY(ws.alloc(&trs.tkeys, T));
+      VR_TRY(ws.alloc(&trs.hist, (int64_t)RS_BINS * tnt));
+      VR_TRY(ws.alloc(&trs.off, (int64_t)RS_BINS * tnt + 1));
+      VR_TRY(ws.alloc(&trs.bs, scan_tmp_slots((int64_t)RS_BINS * tnt)));
+      prof.begin("tri_lex_gen");
+      k_lex_tri_gen<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr, nbr_ord, deg,
+                                                             up, lex_ptr, toff, tk);
+      count_launch();
+      VR_CUDA(cudaGetLastError());
+      prof.end();
+      prof.begin("tri_grade_sort");
+      VR_TRY(radix_sort(tk, nullptr, T, LEX_SHIFT, std::max(1, bitlen((uint64_t)(ngrades - 1))), trs, s));
+      prof.end();
+      prof.begin("tri_final");
+      k_tri_final<<<grid_for(T, 256), 256, 0, s>>>(tk, T, adj, adjpre, W, nbr_ptr, nbr_ord, tverts, tgrade, tcol, trow);
+      count_launch();
+      VR_CUDA(cudaGetLastError());
+      prof.end();
+    } else if (T > 0) {
       prof.begin("tri_emit");
       k_tri_emit<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr, nbr_ord, toff,
                                                           tverts, tgrade, tcol, trow);

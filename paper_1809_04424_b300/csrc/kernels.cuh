@@ -502,20 +502,137 @@ __device__ __forceinline__ uint32_t tri_word_mask(const uint32_t *ra, const uint
   return vm;
 }
 
+// Two enumeration orders (both exact):
+//  * max-edge order (above): a triangle is produced by its largest edge, so
+//    the output is already in (grade, lex) order when no grade group spans
+//    several edges with triangles -- the case for float data;
+//  * lex order: a triangle is produced by its first edge (a, b), a < b < c,
+//    as the key grade << 39 | (a, b, c); a stable sort on the grade bits then
+//    gives (grade, lex) with no merge -- the case for tie-heavy integer data.
+// The mode is chosen on the device from the grade count (same rule on host).
+constexpr int LEX_SHIFT = 3 * ID_BITS;
+__device__ __forceinline__ uint64_t lex3(int a, int b, int c) {
+  return ((uint64_t)a << (2 * ID_BITS)) | ((uint64_t)b << ID_BITS) | (uint64_t)c;
+}
+
+__host__ __device__ __forceinline__ bool lex_mode(int64_t E, int64_t ngrades) {
+  return (E - (ngrades - 1)) * 20 > E;  // more than 5% of edges share a grade
+}
+
+// Bits of the words of row b strictly above column b.
+__device__ __forceinline__ uint32_t above_mask(int b, int w) {
+  const int lo = w * 32;
+  if (lo > b) return 0xffffffffu;
+  if (lo + 31 <= b) return 0u;
+  return ~((2u << (b & 31)) - 1u);
+}
+
+__device__ __forceinline__ int64_t lex_pos(int a, int b, const uint32_t *adj, const int32_t *adjpre, int W,
+                                           const int32_t *deg, const int32_t *up, const int64_t *lex_ptr) {
+  return lex_ptr[a] + bit_rank(adj + (int64_t)a * W, adjpre + (int64_t)a * W, b) - (deg[a] - up[a]);
+}
+
 static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts, int64_t E, const uint32_t *adj,
-                                                   const int32_t *adjpre, int W, const int32_t *nbr_ptr,
-                                                   const int32_t *nbr_ord, int32_t *tcnt) {
+                                                          const int32_t *adjpre, int W, const int32_t *nbr_ptr,
+                                                          const int32_t *nbr_ord, const int32_t *deg,
+                                                          const int32_t *up, const int64_t *lex_ptr,
+                                                          const DevStatus *st, int32_t *tcnt) {
+  const int l = lane_id();
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  const bool lexm = lex_mode(E, st->ngrades);
+  for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
+    const int a = everts[2 * e], b = everts[2 * e + 1];
+    const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
+    int cnt = 0;
+    if (lexm) {
+      for (int w = (b >> 5) + l; w < W; w += 32) cnt += __popc(ra[w] & rb[w] & above_mask(b, w));
+    } else {
+      const int32_t *pa = adjpre + (int64_t)a * W, *pb = adjpre + (int64_t)b * W;
+      const int32_t *oa = nbr_ord + nbr_ptr[a], *ob = nbr_ord + nbr_ptr[b];
+      for (int w = l; w < W; w += 32) cnt += __popc(tri_word_mask(ra, rb, pa, pb, oa, ob, w, (int32_t)e));
+    }
+    cnt = warp_sum(cnt);
+    if (l == 0) tcnt[lexm ? lex_pos(a, b, adj, adjpre, W, deg, up, lex_ptr) : e] = cnt;
+  }
+}
+
+// Lex-order generation: warp per edge (a, b); its triangles (a, b, c), c > b
+// ascending, land at toff[lex position of (a, b)]; the key carries the
+// triangle's grade (largest of its three edge grades).  Coalesced chunked
+// stores as in k_tri_emit.
+static __global__ void __launch_bounds__(256) k_lex_tri_gen(const int32_t *everts, const int32_t *egrade, int64_t E,
+                                                            const uint32_t *adj, const int32_t *adjpre, int W,
+                                                            const int32_t *nbr_ptr, const int32_t *nbr_ord,
+                                                            const int32_t *deg, const int32_t *up,
+                                                            const int64_t *lex_ptr, const int64_t *toff,
+                                                            uint64_t *tkeys) {
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
     const int a = everts[2 * e], b = everts[2 * e + 1];
+    const int32_t gab = egrade[e];
     const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
     const int32_t *pa = adjpre + (int64_t)a * W, *pb = adjpre + (int64_t)b * W;
     const int32_t *oa = nbr_ord + nbr_ptr[a], *ob = nbr_ord + nbr_ptr[b];
-    int cnt = 0;
-    for (int w = l; w < W; w += 32) cnt += __popc(tri_word_mask(ra, rb, pa, pb, oa, ob, w, (int32_t)e));
-    cnt = warp_sum(cnt);
-    if (l == 0) tcnt[e] = cnt;
+    int64_t t = toff[lex_pos(a, b, adj, adjpre, W, deg, up, lex_ptr)];
+    for (int w0 = (b >> 5); w0 < W; w0 += 32) {
+      const int w = w0 + l;
+      const uint32_t vm = w < W ? (ra[w] & rb[w] & above_mask(b, w)) : 0u;
+      const int c = __popc(vm);
+      const int inc = warp_incl_scan(c);
+      const int excl = inc - c;
+      const int tot = __shfl_sync(0xffffffffu, inc, 31);
+      for (int q0 = 0; q0 < tot; q0 += 32) {
+        const int q = q0 + l;
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int cand = owner + step;
+          const int v = __shfl_sync(0xffffffffu, excl, cand & 31);
+          if (cand < 32 && v <= q) owner = cand;
+        }
+        const uint32_t ovm = __shfl_sync(0xffffffffu, vm, owner);
+        const int oex = __shfl_sync(0xffffffffu, excl, owner);
+        if (q < tot) {
+          const int bit = __fns(ovm, 0, q - oex + 1);
+          const int ww = w0 + owner;
+          const int cv = ww * 32 + bit;
+          const uint32_t below = (1u << bit) - 1u;
+          const int32_t gac = egrade[oa[pa[ww] + __popc(ra[ww] & below)]];
+          const int32_t gbc = egrade[ob[pb[ww] + __popc(rb[ww] & below)]];
+          const int32_t g = max(gab, max(gac, gbc));
+          tkeys[t + q] = ((uint64_t)g << LEX_SHIFT) | lex3(a, b, cv);
+        }
+      }
+      t += tot;
+    }
+  }
+}
+
+// Final write of lex-mode triangles, sorted by (grade, a, b, c): verts,
+// grade, colptr and the boundary column (order indices of the three faces,
+// ascending), one thread per triangle so stores are coalesced.
+static __global__ void k_tri_final(const uint64_t *tkeys, int64_t T, const uint32_t *adj, const int32_t *adjpre,
+                                   int W, const int32_t *nbr_ptr, const int32_t *nbr_ord, int32_t *tverts,
+                                   int32_t *tgrade, int64_t *tcolptr, int32_t *trow) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = tkeys[p];
+    const int a = (int)((k >> (2 * ID_BITS)) & ID_MASK), b = (int)((k >> ID_BITS) & ID_MASK), c = (int)(k & ID_MASK);
+    const int32_t *ra = adjpre + (int64_t)a * W, *rb = adjpre + (int64_t)b * W;
+    const uint32_t *wa = adj + (int64_t)a * W, *wb = adj + (int64_t)b * W;
+    int32_t o0 = nbr_ord[nbr_ptr[a] + bit_rank(wa, ra, b)];  // (a, b)
+    int32_t o1 = nbr_ord[nbr_ptr[a] + bit_rank(wa, ra, c)];  // (a, c)
+    int32_t o2 = nbr_ord[nbr_ptr[b] + bit_rank(wb, rb, c)];  // (b, c)
+    int32_t lo = min(o0, min(o1, o2)), hi = max(o0, max(o1, o2));
+    int32_t mid = o0 + o1 + o2 - lo - hi;
+    tverts[3 * p] = a;
+    tverts[3 * p + 1] = b;
+    tverts[3 * p + 2] = c;
+    tgrade[p] = (int32_t)(k >> LEX_SHIFT);
+    tcolptr[p] = 3 * p;
+    trow[3 * p] = lo;
+    trow[3 * p + 1] = mid;
+    trow[3 * p + 2] = hi;
   }
 }
 
@@ -593,6 +710,7 @@ constexpr int TRI_MID = 8192;
 static __global__ void k_tri_groups(const int32_t *gstart, const int32_t *tcnt, const int64_t *toff, int32_t *smallq,
                                     int32_t *midq, int32_t *bigq, DevStatus *st) {
   const int64_t ngrades = st->ngrades;
+  if (lex_mode(st->E, ngrades)) return;  // lex mode needs no merge
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngrades; g += (int64_t)gridDim.x * blockDim.x) {
     const int32_t b = gstart[g], e = gstart[g + 1];
     if (e - b < 2) continue;
@@ -611,10 +729,6 @@ static __global__ void k_tri_groups(const int32_t *gstart, const int32_t *tcnt, 
       atomicAdd((unsigned long long *)&st->big_seg_total, (unsigned long long)s);
     }
   }
-}
-
-__device__ __forceinline__ uint64_t lex3(int a, int b, int c) {
-  return ((uint64_t)a << (2 * ID_BITS)) | ((uint64_t)b << ID_BITS) | (uint64_t)c;
 }
 
 // CTA per queued group: sort the segment by lexicographic key in shared

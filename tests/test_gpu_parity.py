@@ -171,3 +171,27 @@ def test_repeat_builds_identical(torch):
         for f in ("verts", "grade", "colptr", "rowidx"):
             if a[k][f] is not None:
                 np.testing.assert_array_equal(a[k][f], b[k][f])
+
+
+@pytest.mark.parametrize("cluster,spread", [(12, 600), (30, 1000), (60, 2000)])
+def test_rare_ties_merge_paths(torch, cluster, spread):
+    """Few tied edges (max-edge enumeration) but one grade group -- the
+    duplicated points' d^2 = 0 -- spanning many edges with triangles: C(12,3),
+    C(30,3) and C(60,3) triangles exercise the small, mid and large merges."""
+    g = synth.rng(4000 + cluster)
+    pts = g.integers(-20000, 20001, size=(spread, 3)).astype(np.int64)
+    pts[:cluster] = pts[0]
+    iu = np.triu_indices(spread, 1)
+    d2 = ((pts[iu[0]] - pts[iu[1]]) ** 2).sum(1)
+    want = 25 * cluster * (cluster - 1) // 2              # tied edges stay near 4%
+    cap2 = np.partition(d2, want)[want]
+    pts = pts.astype(np.int32)
+    check(torch, pts, 2, math.sqrt(float(cap2)))
+
+
+def test_both_enumeration_orders_on_one_cloud(torch):
+    """The same torus cloud through both orders: lex order (ties, default cap)
+    and, with a cap so small that few edges tie, max-edge order."""
+    c = synth.config2(n=400)
+    check(torch, c.points, 2, c.maxrad)
+    check(torch, c.points, 2, 6.0)
