@@ -180,7 +180,7 @@ def test_rare_ties_merge_paths(torch, cluster, spread):
     C(30,3) and C(60,3) triangles exercise the small, mid and large merges."""
     g = synth.rng(4000 + cluster)
     pts = g.integers(-20000, 20001, size=(spread, 3)).astype(np.int64)
-    pts[:cluster] = pts[0]
+    pts[:cluster] = 100000          # far beyond the cap from every other point
     iu = np.triu_indices(spread, 1)
     d2 = ((pts[iu[0]] - pts[iu[1]]) ** 2).sum(1)
     want = 25 * cluster * (cluster - 1) // 2              # tied edges stay near 4%
