@@ -195,7 +195,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       kbits = std::max(1, bitlen(bound));
     }
     prof.begin("edge_sort");
-    VR_TRY(radix_sort(keys, nullptr, E, KEY_SHIFT, kbits, rs, s));
+    static const char *const etag[3] = {"edge_sort.hist", "edge_sort.scan", "edge_sort.scatter"};
+    VR_TRY(radix_sort(keys, nullptr, E, KEY_SHIFT, kbits, rs, s, &prof, etag));
     prof.end();
 
     if (F) {
@@ -304,7 +305,9 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_CUDA(cudaGetLastError());
       prof.end();
       prof.begin("tri_grade_sort");
-      VR_TRY(radix_sort(tk, nullptr, T, LEX_SHIFT, std::max(1, bitlen((uint64_t)(ngrades - 1))), trs, s));
+      static const char *const ttag[3] = {"tri_sort.hist", "tri_sort.scan", "tri_sort.scatter"};
+      VR_TRY(radix_sort(tk, nullptr, T, LEX_SHIFT, std::max(1, bitlen((uint64_t)(ngrades - 1))), trs, s, &prof,
+                        ttag));
       prof.end();
       prof.begin("tri_final");
       k_tri_final<<<grid_for(T, 256), 256, 0, s>>>(tk, T, adj, adjpre, W, nbr_ptr, nbr_ord, tverts, tgrade, tcol, trow);

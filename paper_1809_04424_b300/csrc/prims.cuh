@@ -376,8 +376,9 @@ struct RadixScratch {
 };
 inline int64_t rs_tiles(int64_t n) { return (n + RS_TILE - 1) / RS_TILE; }
 
+// `prof`/`tag`: optional per-kernel timing ("<tag>.hist", ".scan", ".scatter").
 inline vr_status radix_sort(uint64_t *keys, uint32_t *vals, int64_t n, int bit_lo, int nbits, const RadixScratch &sc,
-                            cudaStream_t s) {
+                            cudaStream_t s, Prof *prof = nullptr, const char *const *tag = nullptr) {
   if (n <= 1 || nbits <= 0) return VR_OK;
   if (n <= 2 * RS_TILE) {
     k_rs_single<<<1, RS_THREADS, 0, s>>>(keys, vals, sc.tkeys, sc.tvals, n, bit_lo, nbits);
@@ -391,10 +392,17 @@ inline vr_status radix_sort(uint64_t *keys, uint32_t *vals, int64_t n, int bit_l
   const int passes = (nbits + 7) / 8;
   for (int p = 0; p < passes; ++p) {
     const int shift = bit_lo + 8 * p;
+    int tk_ = prof ? prof->begin(tag[0]) : -1;
     k_rs_hist<<<(unsigned)nt, RS_THREADS, 0, s>>>(src, n, shift, nt, sc.hist);
+    count_launch(1);
+    if (prof) prof->end(tk_);
+    tk_ = prof ? prof->begin(tag[1]) : -1;
     VR_TRY((scan_exclusive<int64_t, int64_t>(sc.hist, sc.off, RS_BINS * nt, sc.bs, s)));
+    if (prof) prof->end(tk_);
+    tk_ = prof ? prof->begin(tag[2]) : -1;
     k_rs_scatter<<<(unsigned)nt, RS_THREADS, 0, s>>>(src, vs, dst, vd, n, shift, nt, sc.off);
-    count_launch(2);
+    count_launch(1);
+    if (prof) prof->end(tk_);
     VR_CUDA(cudaGetLastError());
     uint64_t *tk = src; src = dst; dst = tk;
     uint32_t *tv = vs; vs = vd; vd = tv;

@@ -21,21 +21,26 @@ class Prof {
  public:
   explicit Prof(cudaStream_t s) : s_(s), on_(g_profile_on.load() != 0) {}
   ~Prof() { finish(); }
-  void begin(const char *name) {
-    cur_ = name;
-    l0_ = g_launches.load();
-    if (!on_) return;
-    Rec r{name, nullptr, nullptr, 0};
+  // Open a timed region; returns a token for end().  Regions may nest.
+  int begin(const char *name) {
+    if (!on_) return -1;
+    Rec r{name, nullptr, nullptr, g_launches.load()};
     cudaEventCreate(&r.a);
     cudaEventCreate(&r.b);
     cudaEventRecord(r.a, s_);
     recs_.push_back(r);
+    open_.push_back((int)recs_.size() - 1);
+    return (int)recs_.size() - 1;
   }
-  void end() {
-    if (!on_ || recs_.empty()) return;
-    cudaEventRecord(recs_.back().b, s_);
-    recs_.back().launches = g_launches.load() - l0_;
+  void end(int tok) {
+    if (!on_ || tok < 0) return;
+    cudaEventRecord(recs_[tok].b, s_);
+    recs_[tok].launches = g_launches.load() - recs_[tok].launches;
+    for (size_t i = open_.size(); i-- > 0;)
+      if (open_[i] == tok) { open_.erase(open_.begin() + i); break; }
   }
+  // Close the innermost region still open.
+  void end() { end(open_.empty() ? -1 : open_.back()); }
   void finish() {
     if (!on_) return;
     for (auto &r : recs_) {
@@ -47,6 +52,7 @@ class Prof {
     }
     cudaGetLastError();
     recs_.clear();
+    open_.clear();
   }
 
  private:
@@ -57,9 +63,8 @@ class Prof {
   };
   cudaStream_t s_;
   bool on_;
-  const char *cur_ = nullptr;
-  int64_t l0_ = 0;
   std::vector<Rec> recs_;
+  std::vector<int> open_;
 };
 
 }  // namespace vr
