@@ -276,19 +276,33 @@ def main():
         d2h += gv.numel() * 8
         e2e_val = simplices * args.steps * world / e2e_s
 
-    # ---- roofline of the dominant phase.
+    # ---- roofline of the dominant kernel: single-kernel regions timed by the
+    # library's CUDA events on the build stream; bytes per launch below.
     hbm, src = peaks()
-    dom = max(phases, key=lambda k: phases[k]["ms_per_call"]) if phases else None
     E, T = cnt[1], cnt[2]
-    alg_bytes = {"tri_emit": 36 * T, "edge_sort": 16 * E * 2, "edge_grades": 52 * E,
-                 "tri_count": 4 * E, "tri_tie_merge": 48 * T}
+    n, d = cloud.n, cloud.d
+    Wd = (n + 31) // 32
+    per_launch_bytes = {
+        "tri_sort.scatter": 16 * T,        # read + write one 8 B key
+        "tri_sort.hist": 8 * T,            # read one 8 B key
+        "tri_final": 44 * T,               # read key 8 B, write verts 12 + grade 4 + rowidx 12 + colptr 8
+        "tri_lex_gen": 8 * T,              # write one 8 B key
+        "tri_emit": 36 * T,                # write verts 12 + grade 4 + rowidx 12 + colptr 8
+        "edge_sort.scatter": 16 * E,
+        "edge_sort.hist": 8 * E,
+        "distance": n * d + 4 * n * Wd,    # read points, write the bitmap
+        "edge_keys": 8 * E,
+    }
+    single = {k: v for k, v in phases.items() if k in per_launch_bytes}
     roof = None
-    if dom in alg_bytes:
-        ms = phases[dom]["ms_per_call"]
-        ach = alg_bytes[dom] / (ms / 1e3) / 1e9
+    if single:
+        dom = max(single, key=lambda k: single[k]["ms_per_call"])
+        per_launch_ms = single[dom]["ms_per_call"] / max(single[dom]["launches_per_call"], 1)
+        ach = per_launch_bytes[dom] / (per_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": None, "peak_source": src,
-                "algorithmic_bytes_per_launch": alg_bytes[dom]}
+                "algorithmic_bytes_per_launch": per_launch_bytes[dom],
+                "launch_ms": per_launch_ms}
 
     line = {"metric": METRIC, "value": value, "unit": "simplices/s", "n_gpus": world, "steps": args.steps,
             "warmup": W, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -302,6 +316,7 @@ def main():
             "gpu_launches": launches,
             "roofline": roof,
             "phases_ms": {k: round(v["ms_per_call"], 4) for k, v in phases.items()},
+            "phase_launches": {k: v["launches_per_call"] for k, v in phases.items()},
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         r, reps, el = oracle_rate(cloud, args.cpu_seconds)
