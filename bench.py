@@ -35,7 +35,13 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-WORKLOAD = "torus n=1000 d=3 int8 (scale 30, noise 0.05), cap at 15th-pct d^2, maxdim 2"
+WORKLOADS = {
+    "torus": ("torus n=1000 d=3 int8 (scale 30, noise 0.05), cap at 15th-pct d^2, maxdim 2",
+              lambda: synth.config2(), "int64"),
+    "plain64": ("uniform int32 n=64 d=3 in [-100,100], no cap, maxdim 2", lambda: synth.config1(), "int64"),
+    "gauss32": ("8-Gaussian mixture n=4000 d=32 float32, cap at 5th-pct d^2, maxdim 2",
+                lambda: synth.config3(), "f64"),
+}
 METRIC = "VR simplices/s"
 
 # Algorithmic bytes per unit of each phase.
@@ -132,7 +138,8 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    cloud = synth.config2()
+    WORKLOAD, make, dtype_name = WORKLOADS[args.config]
+    cloud = make()
     for _ in range(args.warmup):
         oracle.vr_build(cloud.points, cloud.maxdim, cloud.maxrad)
     t0 = time.perf_counter()
@@ -144,7 +151,7 @@ def run_reference(args):
     v = simp / el
     line = {"metric": METRIC, "value": v, "unit": "simplices/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype_name, "data": "synthetic",
             "impl": "reference",
             "config": {"workload": WORKLOAD, "n": cloud.n, "d": cloud.d, "maxdim": cloud.maxdim},
             "cpu_baseline": {"value": v, "unit": "simplices/s", "cores": 1, "kind": "oracle",
@@ -163,6 +170,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="length of the CPU-oracle baseline sample (0 skips it)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--config", default="torus", choices=sorted(WORKLOADS),
+                    help="workload (default: the headline torus cloud)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -180,7 +189,8 @@ def main():
     W = max(args.warmup, 3)
     L = vr.lib()
 
-    cloud = synth.config2()
+    WORKLOAD, make, dtype_name = WORKLOADS[args.config]
+    cloud = make()
     pts_dev = torch.from_numpy(cloud.points).cuda()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -251,7 +261,7 @@ def main():
     def e2e_step():
         nonlocal gv
         c = vr.vr_build(host_pts.data_ptr(), cloud.maxdim, cloud.maxrad, n=cloud.n, d=cloud.d,
-                        dtype=vr.VR_I8)
+                        dtype=cloud.dtype_code)
         for k in range(3):
             b = bufs[k]
             p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
@@ -306,12 +316,13 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "simplices/s", "n_gpus": world, "steps": args.steps,
             "warmup": W, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "vs_baseline": None, "dtype": dtype_name, "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": cloud.n, "d": cloud.d, "maxdim": cloud.maxdim,
                        "maxrad": cloud.maxrad, "simplices_per_step": simplices,
                        "counts": counts, "l2": "flushed between steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "e2e": {"value": e2e_val, "unit": "simplices/s", "h2d_bytes_per_step": cloud.n * cloud.d,
+            "e2e": {"value": e2e_val, "unit": "simplices/s",
+                    "h2d_bytes_per_step": cloud.points.nbytes,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "roofline": roof,

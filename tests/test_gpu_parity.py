@@ -195,3 +195,12 @@ def test_both_enumeration_orders_on_one_cloud(torch):
     c = synth.config2(n=400)
     check(torch, c.points, 2, c.maxrad)
     check(torch, c.points, 2, 6.0)
+
+
+@pytest.mark.parametrize("maxdim", [2, 1])
+def test_config3_gaussian_mixture_full(torch, maxdim):
+    """Full size: 4000 float32 points in d = 32, cap keeping 5% of pairs
+    (about 0.4M edges and 19.8M triangles), every output bit-exact."""
+    c = synth.config3(maxdim=maxdim)
+    g = check(torch, c.points, maxdim, c.maxrad)
+    assert g["stats"]["max_rel_dist_err"] <= 1e-6
