@@ -300,7 +300,7 @@ def main():
         "tri_emit": 36 * T,                # write verts 12 + grade 4 + rowidx 12 + colptr 8
         "edge_sort.scatter": 16 * E,
         "edge_sort.hist": 8 * E,
-        "distance": n * d + 4 * n * Wd,    # read points, write the bitmap
+        "distance": cloud.points.nbytes + 4 * n * Wd,  # read points, write the bitmap
         "edge_keys": 8 * E,
     }
     single = {k: v for k, v in phases.items() if k in per_launch_bytes}
