@@ -211,10 +211,13 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_TRY(ws.alloc(&bigq, E));
       prof.begin("fp64_repair");
       count_launch(6);
+      int tkf = prof.begin("fp64_values");
       k_f64_values<<<ge, 256, 0, s>>>((const float *)X, d, keys, E, cap.crel, d64, split, st);
+      prof.end(tkf);
       VR_TRY((scan_exclusive<int32_t, int32_t>(split, gex, E, bs_e, s)));
       k_group_starts<<<ge, 256, 0, s>>>(split, gex, E, gbeg);
       // Group count is gex[E]; launch over the E upper bound, threads skip.
+      int tkr = prof.begin("fp64_regroup");
       k_repair_small<<<ge, 256, 0, s>>>(gbeg, gex + E, keys, d64, midq, bigq, st);
       VR_CUDA(cudaGetLastError());
       k_repair_mid<<<296, 256, 0, s>>>(gbeg, midq, st, keys, d64);
@@ -226,6 +229,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_TRY(ws.alloc(&gd, E));
       k_repair_big<<<1, RS_THREADS, 0, s>>>(gbeg, bigq, st, keys, d64, k1, v1, k2, v2, gk, gd);
       VR_CUDA(cudaGetLastError());
+      prof.end(tkr);
       prof.end();
     }
     prof.begin("edge_grades");

@@ -272,8 +272,11 @@ static __global__ void k_f64_values(const float *X, int d, const uint64_t *keys,
     }
     split[k] = s;
     if (f > 0.0) {
-      double e = fabs(sqrt((double)a) - sqrt(f)) / sqrt(f);
-      worst = fmax(worst, e);
+      // |sqrt(a) - sqrt(f)| / sqrt(f) = |a - f| / (sqrt(f) (sqrt(a) + sqrt(f))),
+      // evaluated in fp32: a statistic, not part of the result.
+      const float ff = (float)f, sf = sqrtf(ff);
+      const float e = fabsf((float)((double)a - f)) / (sf * (sqrtf(a) + sf));
+      worst = fmax(worst, (double)e);
     }
   }
   if (worst > 0.0) atomicMax((unsigned long long *)&st->max_rel_err_bits, (unsigned long long)__double_as_longlong(worst));
