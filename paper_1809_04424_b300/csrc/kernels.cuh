@@ -74,6 +74,105 @@ __device__ __forceinline__ double d2_f64(const float *xi, const float *xj, int d
   return acc;
 }
 
+// The same canonical value without FP64 instructions (B300 runs FP64 at a
+// small fraction of its integer rate).  A positive double is held as (M, E)
+// with M in [2^52, 2^53) and value M * 2^E; zero as M = 0.  Per coordinate:
+//   t = x - y is exact as an integer D * 2^emin when the fp32 exponents are
+//       within 29 of each other (|D| < 2^53), the case handled here;
+//   s = RN(t*t): D^2 is exact in 128 bits, rounded to 53 bits, ties to even;
+//   acc = RN(acc + s): both positive, aligned in 64 bits with 10 guard bits
+//       and a sticky bit, at most one carry, rounded to 53 bits, ties to even.
+// IEEE 754 round-to-nearest-even makes each step's result unique, so this
+// equals the hardware sequence bit for bit.  Returns false (caller falls back
+// to d2_f64) when some coordinate pair is outside the exact case.
+__device__ __forceinline__ void f32_decode(float v, int64_t &mant, int &ex) {
+  const uint32_t b = __float_as_uint(v);
+  const int be = (int)((b >> 23) & 0xff);
+  const int64_t m = (int64_t)(b & 0x7fffff);
+  if (be == 0) { mant = m; ex = -149; }                 // zero or subnormal
+  else { mant = m | 0x800000; ex = be - 150; }
+  if (b >> 31) mant = -mant;
+}
+
+__device__ __forceinline__ void soft_round_u128(unsigned __int128 p, int e0, uint64_t &M, int &E) {
+  // p * 2^e0 rounded to a 53-bit significand (p > 0).
+  const uint64_t hi = (uint64_t)(p >> 64), lo = (uint64_t)p;
+  const int L = hi ? 128 - __clzll(hi) : 64 - __clzll(lo);
+  if (L <= 53) {
+    M = lo << (53 - L);
+    E = e0 - (53 - L);
+    return;
+  }
+  const int sh = L - 53;
+  uint64_t m = (uint64_t)(p >> sh);
+  const unsigned __int128 rem = p & ((((unsigned __int128)1) << sh) - 1);
+  const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
+  if (rem > half || (rem == half && (m & 1))) ++m;
+  int e = e0 + sh;
+  if (m == (1ull << 53)) { m >>= 1; ++e; }
+  M = m;
+  E = e;
+}
+
+__device__ __forceinline__ void soft_add(uint64_t &Ma, int &Ea, uint64_t Ms, int Es) {
+  if (Ms == 0) return;
+  if (Ma == 0) { Ma = Ms; Ea = Es; return; }
+  uint64_t big = Ma, sm = Ms;
+  int Eb = Ea, diff = Ea - Es;
+  if (diff < 0) { big = Ms; sm = Ma; Eb = Es; diff = -diff; }
+  const uint64_t b10 = big << 10;
+  uint64_t s10 = sm << 10;
+  if (diff >= 64) s10 = 1;                                // all of it is sticky
+  else if (diff > 0) s10 = (s10 >> diff) | ((s10 & ((1ull << diff) - 1)) != 0);
+  uint64_t sum = b10 + s10;
+  if (sum >> 63) { sum = (sum >> 1) | (sum & 1); ++Eb; }
+  uint64_t m = sum >> 10;
+  const uint64_t rem = sum & 0x3ff;
+  if (rem > 0x200 || (rem == 0x200 && (m & 1))) ++m;
+  if (m == (1ull << 53)) { m >>= 1; ++Eb; }
+  Ma = m;
+  Ea = Eb;
+}
+
+__device__ __forceinline__ bool d2_f64_soft(const float *xi, const float *xj, int d, double &out) {
+  uint64_t M = 0;
+  int E = 0;
+  for (int k = 0; k < d; ++k) {
+    int64_t a, b;
+    int ea, eb;
+    f32_decode(xi[k], a, ea);
+    f32_decode(xj[k], b, eb);
+    int64_t D;
+    int emin;
+    if (a == 0 || b == 0) {                                // t = x or -y exactly
+      D = a ? a : -b;
+      emin = a ? ea : eb;
+    } else {
+      emin = min(ea, eb);
+      const int da = ea - emin, db = eb - emin;
+      if (da > 29 || db > 29) return false;               // t might round: not the exact case
+      D = (a << da) - (b << db);                          // |D| < 2^54
+    }
+    const uint64_t ad = (uint64_t)(D < 0 ? -D : D);
+    if (ad >> 53) return false;
+    if (ad == 0) continue;
+    uint64_t Ms;
+    int Es;
+    soft_round_u128((unsigned __int128)ad * ad, 2 * emin, Ms, Es);
+    soft_add(M, E, Ms, Es);
+  }
+  if (M == 0) { out = 0.0; return true; }
+  const uint64_t bits = ((uint64_t)(E + 52 + 1023) << 52) | (M & ((1ull << 52) - 1));
+  out = __longlong_as_double((long long)bits);
+  return true;
+}
+
+__device__ __forceinline__ double d2_canonical(const float *xi, const float *xj, int d) {
+  double v;
+  if (d2_f64_soft(xi, xj, d, v)) return v;
+  return d2_f64(xi, xj, d);
+}
+
 // Bounds of the canonical value from the fp32 first pass A:
 //   |A - D| <= ((d+2) u32 + O(u^2)) D + underflow, |F - D| <= (d+2) u64 D
 // (D exact, F canonical FP64), so |A - F| <= crel * A + 2^-100 with
@@ -147,7 +246,7 @@ __global__ void __launch_bounds__(256) k_dist_bitmap(const void *Xv, int n, int 
         if (cap.keep_all) kept = true;
         else if (f32_hi(a, cap.crel) <= cap.r2) kept = true;
         else if (f32_lo(a, cap.crel) > cap.r2) kept = false;
-        else kept = d2_f64(pi, pj, d) <= cap.r2;  // near the cap: decide exactly
+        else kept = d2_canonical(pi, pj, d) <= cap.r2;  // near the cap: decide exactly
       } else {
         uint64_t v;
         if constexpr (DR > 0) {
@@ -262,7 +361,7 @@ static __global__ void k_f64_values(const float *X, int d, const uint64_t *keys,
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = keys[k];
     const int i = key_i(key), j = key_j(key);
-    const double f = d2_f64(X + (int64_t)i * d, X + (int64_t)j * d, d);
+    const double f = d2_canonical(X + (int64_t)i * d, X + (int64_t)j * d, d);
     d64[k] = f;
     const float a = __uint_as_float((uint32_t)(key >> KEY_SHIFT));
     int s = 1;

@@ -204,3 +204,15 @@ def test_config3_gaussian_mixture_full(torch, maxdim):
     c = synth.config3(maxdim=maxdim)
     g = check(torch, c.points, maxdim, c.maxrad)
     assert g["stats"]["max_rel_dist_err"] <= 1e-6
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_float_wide_dynamic_range(torch, seed):
+    """Coordinates spanning many binades, zeros included: the integer
+    evaluation of the FP64 sequence and its hardware fallback (exponents more
+    than 29 apart) must both reproduce the oracle's doubles exactly."""
+    g = synth.rng(7000 + seed)
+    pts = g.normal(size=(300, 6)) * 10.0 ** g.integers(-12, 6, size=(300, 6))
+    pts[g.random(size=pts.shape) < 0.2] = 0.0
+    pts = pts.astype(np.float32)
+    check(torch, pts, 2, math.inf if seed == 1 else 1e-3)
