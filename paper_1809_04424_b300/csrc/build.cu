@@ -181,7 +181,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   const unsigned ge = grid_for(E, 256);
   if (E > 0) {
     prof.begin("edge_keys");
-    k_edge_keys<F><<<(n + 7) / 8, 256, 0, s>>>(X, n, d, W, adj, adjpre, deg, up, lex_ptr, keys);
+    k_edge_keys<F><<<(n + 7) / 8, 256, 0, s>>>(X, n, d, W, adj, lex_ptr, keys);
     count_launch();
     VR_CUDA(cudaGetLastError());
     prof.end();

@@ -307,6 +307,40 @@ static __global__ void __launch_bounds__(256) k_rows(const uint32_t *adj, int n,
   }
 }
 
+// Bits of the words of row b strictly above column b.
+__device__ __forceinline__ uint32_t above_mask(int b, int w) {
+  const int lo = w * 32;
+  if (lo > b) return 0xffffffffu;
+  if (lo + 31 <= b) return 0u;
+  return ~((2u << (b & 31)) - 1u);
+}
+
+// Balanced walk over the set bits of one round of per-lane masks m (lane l
+// owns word w0 + l): the round's candidates are taken 32 at a time, lane q
+// taking the q-th, located by a 5-step search over the lanes' prefix counts
+// and __fns inside the owner lane's mask.  Every lane does the same number of
+// iterations whatever the bits' distribution.  Returns, per chunk, through
+// the callback: ok (lane has a candidate), owner lane, bit.
+struct BitChunk {
+  int tot;     // candidates in the round
+  int excl;    // this lane's exclusive prefix
+};
+__device__ __forceinline__ BitChunk bit_round(uint32_t m) {
+  const int c = __popc(m);
+  const int inc = warp_incl_scan(c);
+  return BitChunk{__shfl_sync(0xffffffffu, inc, 31), inc - c};
+}
+__device__ __forceinline__ int bit_owner(const BitChunk &r, int q) {
+  int owner = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    const int cand = owner + step;
+    const int v = __shfl_sync(0xffffffffu, r.excl, cand & 31);
+    if (cand < 32 && v <= q) owner = cand;
+  }
+  return owner;
+}
+
 __device__ __forceinline__ int32_t bit_rank(const uint32_t *adj_row, const int32_t *pre_row, int c) {
   const int w = c >> 5, b = c & 31;
   return pre_row[w] + __popc(adj_row[w] & ((1u << b) - 1u));
@@ -317,32 +351,32 @@ __device__ __forceinline__ int32_t bit_rank(const uint32_t *adj_row, const int32
 // position lex_ptr[i] + (rank of j in row i) - (neighbours <= i).
 template <bool F>
 __global__ void __launch_bounds__(256) k_edge_keys(const void *Xv, int n, int d, int W, const uint32_t *adj,
-                                                   const int32_t *adjpre, const int32_t *deg, const int32_t *up,
                                                    const int64_t *lex_ptr, uint64_t *keys) {
   using T = typename std::conditional<F, float, int32_t>::type;
   const T *X = (const T *)Xv;
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int l = lane_id();
   if (i >= n) return;
-  const int64_t base = lex_ptr[i] - (int64_t)(deg[i] - up[i]);
   const uint32_t *row = adj + (int64_t)i * W;
-  const int32_t *pre = adjpre + (int64_t)i * W;
-  for (int w = ((i + 1) >> 5) + l; w < W; w += 32) {
-    uint32_t word = row[w];
-    const int lo = w * 32;
-    if (lo <= i) word &= (lo + 31 <= i) ? 0u : ~((2u << (i & 31)) - 1u);
-    // rank of this word's first upper bit: the row's bits before it
-    int32_t r = pre[w] + (__popc(row[w]) - __popc(word));
-    while (word) {
-      const int b = __ffs(word) - 1;
-      word &= word - 1;
-      const int j = lo + b;
-      uint64_t dk;
-      if constexpr (F) dk = (uint64_t)__float_as_uint(d2_f32(X + (int64_t)i * d, X + (int64_t)j * d, d));
-      else dk = d2_int(X + (int64_t)i * d, X + (int64_t)j * d, d);
-      keys[base + r] = (dk << KEY_SHIFT) | ((uint64_t)i << ID_BITS) | (uint64_t)j;
-      ++r;
+  int64_t t = lex_ptr[i];
+  for (int w0 = (i + 1) >> 5; w0 < W; w0 += 32) {
+    const int w = w0 + l;
+    const uint32_t word = w < W ? row[w] & above_mask(i, w) : 0u;
+    const BitChunk r = bit_round(word);
+    for (int q0 = 0; q0 < r.tot; q0 += 32) {
+      const int q = q0 + l;
+      const int ow = bit_owner(r, q);
+      const uint32_t om = __shfl_sync(0xffffffffu, word, ow);
+      const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
+      if (q < r.tot) {
+        const int j = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
+        uint64_t dk;
+        if constexpr (F) dk = (uint64_t)__float_as_uint(d2_f32(X + (int64_t)i * d, X + (int64_t)j * d, d));
+        else dk = d2_int(X + (int64_t)i * d, X + (int64_t)j * d, d);
+        keys[t + q] = (dk << KEY_SHIFT) | ((uint64_t)i << ID_BITS) | (uint64_t)j;
+      }
     }
+    t += r.tot;
   }
 }
 
@@ -588,22 +622,6 @@ static __global__ void k_vertices(int n, int32_t *verts, int32_t *grade) {
 // per edge; lane l takes word 32*r + l in round r, so the warp's output is in
 // ascending c, which is already lexicographic for the sorted triple.
 
-__device__ __forceinline__ uint32_t tri_word_mask(const uint32_t *ra, const uint32_t *rb, const int32_t *pa,
-                                                  const int32_t *pb, const int32_t *ord_a, const int32_t *ord_b,
-                                                  int w, int32_t e) {
-  const uint32_t wa = ra[w], wb = rb[w];
-  uint32_t m = wa & wb, vm = 0;
-  while (m) {
-    const int bit = __ffs(m) - 1;
-    m &= m - 1;
-    const uint32_t below = (1u << bit) - 1u;
-    const int32_t oac = ord_a[pa[w] + __popc(wa & below)];
-    const int32_t obc = ord_b[pb[w] + __popc(wb & below)];
-    if (oac < e && obc < e) vm |= 1u << bit;
-  }
-  return vm;
-}
-
 // Two enumeration orders (both exact):
 //  * max-edge order (above): a triangle is produced by its largest edge, so
 //    the output is already in (grade, lex) order when no grade group spans
@@ -619,14 +637,6 @@ __device__ __forceinline__ uint64_t lex3(int a, int b, int c) {
 
 __host__ __device__ __forceinline__ bool lex_mode(int64_t E, int64_t ngrades) {
   return (E - (ngrades - 1)) * 20 > E;  // more than 5% of edges share a grade
-}
-
-// Bits of the words of row b strictly above column b.
-__device__ __forceinline__ uint32_t above_mask(int b, int w) {
-  const int lo = w * 32;
-  if (lo > b) return 0xffffffffu;
-  if (lo + 31 <= b) return 0u;
-  return ~((2u << (b & 31)) - 1u);
 }
 
 __device__ __forceinline__ int64_t lex_pos(int a, int b, const uint32_t *adj, const int32_t *adjpre, int W,
@@ -651,9 +661,30 @@ static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts,
     } else {
       const int32_t *pa = adjpre + (int64_t)a * W, *pb = adjpre + (int64_t)b * W;
       const int32_t *oa = nbr_ord + nbr_ptr[a], *ob = nbr_ord + nbr_ptr[b];
-      for (int w = l; w < W; w += 32) cnt += __popc(tri_word_mask(ra, rb, pa, pb, oa, ob, w, (int32_t)e));
+      for (int w0 = 0; w0 < W; w0 += 32) {
+        const int w = w0 + l;
+        const uint32_t wa = w < W ? ra[w] : 0u, wb = w < W ? rb[w] : 0u;
+        const int32_t qa = w < W ? pa[w] : 0, qb = w < W ? pb[w] : 0;
+        const uint32_t m = wa & wb;
+        const BitChunk r = bit_round(m);
+        for (int q0 = 0; q0 < r.tot; q0 += 32) {
+          const int q = q0 + l;
+          const int ow = bit_owner(r, q);
+          const uint32_t om = __shfl_sync(0xffffffffu, m, ow), owa = __shfl_sync(0xffffffffu, wa, ow),
+                         owb = __shfl_sync(0xffffffffu, wb, ow);
+          const int32_t oqa = __shfl_sync(0xffffffffu, qa, ow), oqb = __shfl_sync(0xffffffffu, qb, ow);
+          const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
+          bool ok = false;
+          if (q < r.tot) {
+            const int bit = __fns(om, 0, q - oex + 1);
+            const uint32_t below = (1u << bit) - 1u;
+            ok = oa[oqa + __popc(owa & below)] < (int32_t)e && ob[oqb + __popc(owb & below)] < (int32_t)e;
+          }
+          cnt += __popc(__ballot_sync(0xffffffffu, ok));
+        }
+      }
     }
-    cnt = warp_sum(cnt);
+    if (lexm) cnt = warp_sum(cnt);  // max-edge lanes already hold the warp total
     if (l == 0) tcnt[lexm ? lex_pos(a, b, adj, adjpre, W, deg, up, lex_ptr) : e] = cnt;
   }
 }
@@ -749,6 +780,7 @@ static __global__ void __launch_bounds__(256) k_tri_emit(const int32_t *everts, 
                                                          const int64_t *toff, int32_t *tverts, int32_t *tgrade,
                                                          int64_t *tcolptr, int32_t *trow) {
   const int l = lane_id();
+  const uint32_t lt = lanemask_lt();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
     const int a = everts[2 * e], b = everts[2 * e + 1];
@@ -759,34 +791,35 @@ static __global__ void __launch_bounds__(256) k_tri_emit(const int32_t *everts, 
     int64_t t = toff[e];
     for (int w0 = 0; w0 < W; w0 += 32) {
       const int w = w0 + l;
-      const uint32_t vm = w < W ? tri_word_mask(ra, rb, pa, pb, oa, ob, w, (int32_t)e) : 0u;
-      const int c = __popc(vm);
-      const int inc = warp_incl_scan(c);
-      const int excl = inc - c;
-      const int tot = __shfl_sync(0xffffffffu, inc, 31);
-      for (int q0 = 0; q0 < tot; q0 += 32) {
+      const uint32_t wa = w < W ? ra[w] : 0u, wb = w < W ? rb[w] : 0u;
+      const int32_t qa = w < W ? pa[w] : 0, qb = w < W ? pb[w] : 0;
+      const uint32_t m = wa & wb;
+      const BitChunk r = bit_round(m);
+      for (int q0 = 0; q0 < r.tot; q0 += 32) {
         const int q = q0 + l;
-        int owner = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int cand = owner + step;
-          const int v = __shfl_sync(0xffffffffu, excl, cand & 31);
-          if (cand < 32 && v <= q) owner = cand;
-        }
-        const uint32_t ovm = __shfl_sync(0xffffffffu, vm, owner);
-        const int oex = __shfl_sync(0xffffffffu, excl, owner);
-        if (q < tot) {
-          const int bit = __fns(ovm, 0, q - oex + 1);
-          const int ww = w0 + owner;
-          const int cv = ww * 32 + bit;
+        const int ow = bit_owner(r, q);
+        const uint32_t om = __shfl_sync(0xffffffffu, m, ow), owa = __shfl_sync(0xffffffffu, wa, ow),
+                       owb = __shfl_sync(0xffffffffu, wb, ow);
+        const int32_t oqa = __shfl_sync(0xffffffffu, qa, ow), oqb = __shfl_sync(0xffffffffu, qb, ow);
+        const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
+        bool ok = false;
+        int cv = 0;
+        int32_t oac = 0, obc = 0;
+        if (q < r.tot) {
+          const int bit = __fns(om, 0, q - oex + 1);
           const uint32_t below = (1u << bit) - 1u;
-          const int32_t oac = oa[pa[ww] + __popc(ra[ww] & below)];
-          const int32_t obc = ob[pb[ww] + __popc(rb[ww] & below)];
+          cv = (w0 + ow) * 32 + bit;
+          oac = oa[oqa + __popc(owa & below)];
+          obc = ob[oqb + __popc(owb & below)];
+          ok = oac < (int32_t)e && obc < (int32_t)e;
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+          const int64_t p = t + __popc(bal & lt);
           int x0, x1, x2;
           if (cv < a) { x0 = cv; x1 = a; x2 = b; }
           else if (cv < b) { x0 = a; x1 = cv; x2 = b; }
           else { x0 = a; x1 = b; x2 = cv; }
-          const int64_t p = t + q;
           tverts[3 * p] = x0;
           tverts[3 * p + 1] = x1;
           tverts[3 * p + 2] = x2;
@@ -796,8 +829,8 @@ static __global__ void __launch_bounds__(256) k_tri_emit(const int32_t *everts, 
           trow[3 * p + 1] = max(oac, obc);
           trow[3 * p + 2] = (int32_t)e;
         }
+        t += __popc(bal);
       }
-      t += tot;
     }
   }
 }
