@@ -66,6 +66,26 @@ static DevStatus *pinned_status() {
   return p;
 }
 
+// fp32 thresholds of the cap test: a_keep = largest float a with
+// a (1 + crel) + 2^-100 <= r2 (certainly kept), a_drop = smallest float a with
+// a (1 - crel) - 2^-100 > r2 (certainly dropped); both bounds are monotone in a.
+static void f32_thresholds(double r2, double crel, float *a_keep, float *a_drop) {
+  auto hi = [&](float a) { return (double)a * (1.0 + crel) + F32_ABS_SLACK; };
+  auto lo = [&](float a) { return (double)a * (1.0 - crel) - F32_ABS_SLACK; };
+  // Start from the solutions of the two linear bounds; a few ulp steps fix
+  // the rounding of the estimate.
+  float k = (float)((r2 - F32_ABS_SLACK) / (1.0 + crel));
+  if (k < 0.f) k = 0.f;
+  while (k > 0.f && hi(k) > r2) k = std::nextafter(k, -INFINITY);
+  while (hi(std::nextafter(k, INFINITY)) <= r2) k = std::nextafter(k, INFINITY);
+  if (hi(k) > r2) k = -1.f;  // nothing is certainly kept
+  float dr = (float)((r2 + F32_ABS_SLACK) / (1.0 - crel));
+  while (lo(dr) <= r2) dr = std::nextafter(dr, INFINITY);
+  while (dr > 0.f && lo(std::nextafter(dr, -INFINITY)) > r2) dr = std::nextafter(dr, -INFINITY);
+  *a_keep = k;
+  *a_drop = dr;
+}
+
 template <bool F, int DR>
 static void launch_dist(const void *X, int n, int d, int W, const Cap &cap, uint32_t *adj, DevStatus *st,
                         cudaStream_t s) {
@@ -105,6 +125,10 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   if (!F && !cap.keep_all) {
     double f = std::floor(r2);
     cap.r2i = f >= 18446744073709551615.0 ? ~0ull : (uint64_t)f;
+  }
+  if (F && !cap.keep_all) {
+    if (r2 >= 1e38) cap.keep_all = 1;  // beyond any fp32 first-pass value of valid input
+    else f32_thresholds(r2, cap.crel, &cap.a_keep, &cap.a_drop);
   }
 
   DevStatus *st;
@@ -160,7 +184,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   int32_t *flag, *gex, *nbr_ord, *gstart;
   int32_t *everts, *egrade, *erow;
   int64_t *ecol, *bs_e;
-  double *gval, *d64 = nullptr;
+  double *gval, *d64 = nullptr, *d64_lex = nullptr;
   const int64_t nt = rs_tiles(E);
   VR_TRY(ws.alloc(&keys, E));
   VR_TRY(ws.alloc(&rs.tkeys, E));
@@ -181,7 +205,12 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   const unsigned ge = grid_for(E, 256);
   if (E > 0) {
     prof.begin("edge_keys");
-    k_edge_keys<F><<<(n + 7) / 8, 256, 0, s>>>(X, n, d, W, adj, lex_ptr, keys);
+    if constexpr (F) {
+      VR_TRY(ws.alloc(&d64_lex, E));
+      k_edge_keys_f32<<<(n + 7) / 8, 256, 0, s>>>((const float *)X, n, d, W, adj, lex_ptr, keys, d64_lex, st);
+    } else {
+      k_edge_keys<F><<<(n + 7) / 8, 256, 0, s>>>(X, n, d, W, adj, lex_ptr, keys);
+    }
     count_launch();
     VR_CUDA(cudaGetLastError());
     prof.end();
@@ -212,7 +241,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       prof.begin("fp64_repair");
       count_launch(6);
       int tkf = prof.begin("fp64_values");
-      k_f64_values<<<ge, 256, 0, s>>>((const float *)X, d, keys, E, cap.crel, d64, split, st);
+      k_f64_gather<<<ge, 256, 0, s>>>(keys, E, d64_lex, adj, adjpre, W, deg, up, lex_ptr, d64, split);
       prof.end(tkf);
       VR_TRY((scan_exclusive<int32_t, int32_t>(split, gex, E, bs_e, s)));
       k_group_starts<<<ge, 256, 0, s>>>(split, gex, E, gbeg);

@@ -30,6 +30,8 @@ struct Cap {
   uint64_t r2i;     // integer inputs: floor(fl(maxrad^2)) clamped to u64
   double r2;        // float inputs: fl(maxrad^2)
   double crel;      // float inputs: relative bound of the fp32 first pass
+  float a_keep;     // float inputs: fp32 value at or below which a pair is certainly kept
+  float a_drop;     // float inputs: fp32 value at or above which a pair is certainly dropped
 };
 
 // Absolute slack of the fp32 bound: covers underflow of tiny squares.
@@ -243,9 +245,8 @@ __global__ void __launch_bounds__(256) k_dist_bitmap(const void *Xv, int n, int 
         } else {
           a = d2_f32(pi, pj, d);
         }
-        if (cap.keep_all) kept = true;
-        else if (f32_hi(a, cap.crel) <= cap.r2) kept = true;
-        else if (f32_lo(a, cap.crel) > cap.r2) kept = false;
+        if (cap.keep_all || a <= cap.a_keep) kept = true;
+        else if (a >= cap.a_drop) kept = false;
         else kept = d2_canonical(pi, pj, d) <= cap.r2;  // near the cap: decide exactly
       } else {
         uint64_t v;
@@ -380,6 +381,109 @@ __global__ void __launch_bounds__(256) k_edge_keys(const void *Xv, int n, int d,
   }
 }
 
+// Float edge keys, in lexicographic order: warp per row i, 32 candidates per
+// chunk (one per lane).  The chunk's 32 candidate rows are staged through
+// shared memory 32 coordinates at a time with coalesced loads; each lane then
+// walks its row in coordinate order evaluating the canonical FP64 sum (integer
+// emulation, hardware FP64 only on the rare inexact case) and the fp32 first
+// pass for the error statistic.  Key = RN32(FP64 value) bits, i, j.
+struct SoftAcc {
+  uint64_t M;
+  int E;
+  bool ok;
+};
+__device__ __forceinline__ void soft_step(SoftAcc &s, float x, float y) {
+  int64_t a, b;
+  int ea, eb;
+  f32_decode(x, a, ea);
+  f32_decode(y, b, eb);
+  int64_t D;
+  int emin;
+  if (a == 0 || b == 0) {
+    D = a ? a : -b;
+    emin = a ? ea : eb;
+  } else {
+    emin = min(ea, eb);
+    const int da = ea - emin, db = eb - emin;
+    if (da > 29 || db > 29) { s.ok = false; return; }
+    D = (a << da) - (b << db);
+  }
+  const uint64_t ad = (uint64_t)(D < 0 ? -D : D);
+  if (ad >> 53) { s.ok = false; return; }
+  if (ad == 0) return;
+  uint64_t Ms;
+  int Es;
+  soft_round_u128((unsigned __int128)ad * ad, 2 * emin, Ms, Es);
+  soft_add(s.M, s.E, Ms, Es);
+}
+__device__ __forceinline__ double soft_value(const SoftAcc &s) {
+  if (s.M == 0) return 0.0;
+  return __longlong_as_double((long long)(((uint64_t)(s.E + 52 + 1023) << 52) | (s.M & ((1ull << 52) - 1))));
+}
+
+static __global__ void __launch_bounds__(256) k_edge_keys_f32(const float *X, int n, int d, int W,
+                                                              const uint32_t *adj, const int64_t *lex_ptr,
+                                                              uint64_t *keys, double *d64_lex, DevStatus *st) {
+  __shared__ float tile[8][32][33];
+  __shared__ float rowi[8][32];
+  const int wid = threadIdx.x >> 5;
+  const int i = blockIdx.x * 8 + wid;
+  const int l = lane_id();
+  if (i >= n) return;
+  const uint32_t *row = adj + (int64_t)i * W;
+  int64_t t = lex_ptr[i];
+  float worst = 0.f;
+  for (int w0 = (i + 1) >> 5; w0 < W; w0 += 32) {
+    const int w = w0 + l;
+    const uint32_t word = w < W ? row[w] & above_mask(i, w) : 0u;
+    const BitChunk r = bit_round(word);
+    for (int q0 = 0; q0 < r.tot; q0 += 32) {
+      const int q = q0 + l;
+      const int ow = bit_owner(r, q);
+      const uint32_t om = __shfl_sync(0xffffffffu, word, ow);
+      const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
+      const bool has = q < r.tot;
+      const int j = has ? (w0 + ow) * 32 + __fns(om, 0, q - oex + 1) : i;
+      SoftAcc acc{0, 0, true};
+      float a = 0.f;
+      for (int k0 = 0; k0 < d; k0 += 32) {
+        const int kn = min(32, d - k0);
+        rowi[wid][l] = l < kn ? X[(int64_t)i * d + k0 + l] : 0.f;
+        for (int rr = 0; rr < 32; ++rr) {
+          const int jr = __shfl_sync(0xffffffffu, j, rr);
+          tile[wid][rr][l] = l < kn ? X[(int64_t)jr * d + k0 + l] : 0.f;
+        }
+        __syncwarp();
+        for (int k = 0; k < kn; ++k) {
+          const float xv = rowi[wid][k], yv = tile[wid][l][k];
+          const float tt = __fsub_rn(xv, yv);
+          a = __fmaf_rn(tt, tt, a);
+          if (acc.ok) soft_step(acc, xv, yv);
+        }
+        __syncwarp();
+      }
+      if (has) {
+        const double f = acc.ok ? soft_value(acc) : d2_f64(X + (int64_t)i * d, X + (int64_t)j * d, d);
+        d64_lex[t + q] = f;
+        keys[t + q] = ((uint64_t)__float_as_uint(__double2float_rn(f)) << KEY_SHIFT) |
+                      ((uint64_t)i << ID_BITS) | (uint64_t)j;
+        if (f > 0.0) {
+          const float ff = (float)f, sf = sqrtf(ff);
+          worst = fmaxf(worst, fabsf((float)((double)a - f)) / (sf * (sqrtf(a) + sf)));
+        }
+      }
+    }
+    t += r.tot;
+  }
+  worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 16));
+  worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 8));
+  worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 4));
+  worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 2));
+  worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 1));
+  if (l == 0 && worst > 0.f)
+    atomicMax((unsigned long long *)&st->max_rel_err_bits, (unsigned long long)__double_as_longlong((double)worst));
+}
+
 __device__ __forceinline__ int key_i(uint64_t k) { return (int)((k >> ID_BITS) & ID_MASK); }
 __device__ __forceinline__ int key_j(uint64_t k) { return (int)(k & ID_MASK); }
 
@@ -389,30 +493,21 @@ __device__ __forceinline__ int key_j(uint64_t k) { return (int)(k & ID_MASK); }
 // of order; they form a repair group (a maximal run where each step's
 // intervals overlap), re-sorted by (FP64 value, i, j).  Across a group
 // boundary the FP64 values are strictly ordered already.
-static __global__ void k_f64_values(const float *X, int d, const uint64_t *keys, int64_t E, double crel, double *d64,
-                             int32_t *split, DevStatus *st) {
-  double worst = 0.0;
+// After the sort: each edge's canonical value (computed in lexicographic
+// order by k_edge_keys_f32) is gathered through its lex position, and a
+// repair group starts wherever the fp32 key bits change.  Keys are RN32 of
+// the canonical value, which is monotone, so different keys are already in
+// FP64 order; only runs of equal keys need re-sorting by (FP64, i, j).
+static __global__ void k_f64_gather(const uint64_t *keys, int64_t E, const double *d64_lex, const uint32_t *adj,
+                                    const int32_t *adjpre, int W, const int32_t *deg, const int32_t *up,
+                                    const int64_t *lex_ptr, double *d64, int32_t *split) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = keys[k];
-    const int i = key_i(key), j = key_j(key);
-    const double f = d2_canonical(X + (int64_t)i * d, X + (int64_t)j * d, d);
-    d64[k] = f;
-    const float a = __uint_as_float((uint32_t)(key >> KEY_SHIFT));
-    int s = 1;
-    if (k > 0) {
-      const float ap = __uint_as_float((uint32_t)(keys[k - 1] >> KEY_SHIFT));
-      s = f32_lo(a, crel) > f32_hi(ap, crel) ? 1 : 0;
-    }
-    split[k] = s;
-    if (f > 0.0) {
-      // |sqrt(a) - sqrt(f)| / sqrt(f) = |a - f| / (sqrt(f) (sqrt(a) + sqrt(f))),
-      // evaluated in fp32: a statistic, not part of the result.
-      const float ff = (float)f, sf = sqrtf(ff);
-      const float e = fabsf((float)((double)a - f)) / (sf * (sqrtf(a) + sf));
-      worst = fmax(worst, (double)e);
-    }
+    const int i = (int)((key >> ID_BITS) & ID_MASK), j = (int)(key & ID_MASK);
+    const int64_t lp = lex_ptr[i] + bit_rank(adj + (int64_t)i * W, adjpre + (int64_t)i * W, j) - (deg[i] - up[i]);
+    d64[k] = d64_lex[lp];
+    split[k] = (k == 0 || (key >> KEY_SHIFT) != (keys[k - 1] >> KEY_SHIFT)) ? 1 : 0;
   }
-  if (worst > 0.0) atomicMax((unsigned long long *)&st->max_rel_err_bits, (unsigned long long)__double_as_longlong(worst));
 }
 
 // Group starts from the exclusive scan of split: gbeg[gid] = k.
