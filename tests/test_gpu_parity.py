@@ -216,3 +216,11 @@ def test_float_wide_dynamic_range(torch, seed):
     pts[g.random(size=pts.shape) < 0.2] = 0.0
     pts = pts.astype(np.float32)
     check(torch, pts, 2, math.inf if seed == 1 else 1e-3)
+
+
+@pytest.mark.parametrize("dtype", [np.int8, np.float32])
+def test_zero_radius_keeps_duplicates(torch, dtype):
+    """maxrad = 0: only coincident points are joined (d^2 = 0 <= 0)."""
+    pts = synth.random_cloud(40, 2, dtype, seed=91, lo=-3, hi=3)
+    g = check(torch, pts, 2, 0.0)
+    assert g["counts"][1] > 0
