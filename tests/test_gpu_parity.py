@@ -221,6 +221,6 @@ def test_float_wide_dynamic_range(torch, seed):
 @pytest.mark.parametrize("dtype", [np.int8, np.float32])
 def test_zero_radius_keeps_duplicates(torch, dtype):
     """maxrad = 0: only coincident points are joined (d^2 = 0 <= 0)."""
-    pts = synth.random_cloud(40, 2, dtype, seed=91, lo=-3, hi=3)
+    pts = synth.random_cloud(40, 2, np.int8, seed=91, lo=-3, hi=3).astype(dtype)
     g = check(torch, pts, 2, 0.0)
     assert g["counts"][1] > 0
