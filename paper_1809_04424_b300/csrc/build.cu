@@ -287,6 +287,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     count_launch();
     VR_CUDA(cudaGetLastError());
     VR_TRY((scan_exclusive<int32_t, int64_t>(tcnt, toff, E, bs_e, s)));
+    VR_CUDA(cudaMemcpyAsync(&st->T, toff + E, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     prof.end();
   }
 
@@ -294,8 +295,9 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(read_status(st, hst, s));
   const int64_t ngrades = E > 0 ? hst->ngrades : 1;
   const int64_t T = (maxdim >= 2 && E > 0) ? hst->tsum3 / 3 : 0;
-  if (maxdim >= 2 && E > 0 && hst->tsum3 % 3 != 0) {
-    set_error("triangle incidence sum %lld is not a multiple of 3", (long long)hst->tsum3);
+  if (maxdim >= 2 && E > 0 && (hst->tsum3 % 3 != 0 || hst->T != T)) {
+    set_error("triangle sizing disagrees: incidence sum %lld, lex total %lld", (long long)hst->tsum3,
+              (long long)hst->T);
     return VR_ERR_INTERNAL;
   }
   if (T > INT32_MAX) {
@@ -332,7 +334,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_TRY(ws.alloc(&trs.bs, scan_tmp_slots((int64_t)RS_BINS * tnt)));
       prof.begin("tri_lex_gen");
       k_lex_tri_gen<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr, nbr_ord, deg,
-                                                             up, lex_ptr, toff, tk);
+                                                             up, lex_ptr, toff, T, tk, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();
@@ -356,8 +358,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_CUDA(cudaMemsetAsync(&st->ticket, 0, sizeof(uint64_t), s));
       VR_CUDA(cudaMemcpyAsync(toff_me + E, &T, sizeof(int64_t), cudaMemcpyHostToDevice, s));
       prof.begin("tri_emit");
-      k_tri_fused<<<148 * 6, 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr, nbr_ord, tstat, toff_me, tverts,
-                                          tgrade, tcol, trow, st);
+      k_tri_fused<<<148 * 6, 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr, nbr_ord, tstat, toff_me, T,
+                                          tverts, tgrade, tcol, trow, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();

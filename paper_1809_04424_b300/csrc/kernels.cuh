@@ -833,7 +833,7 @@ constexpr int MAX_ROUNDS = (VR_MAX_POINTS / 32 + 31) / 32;  // 8 rounds of 32 wo
 static __global__ void __launch_bounds__(256) k_tri_fused(const int32_t *everts, const int32_t *egrade, int64_t E,
                                                           const uint32_t *adj, const int32_t *adjpre, int W,
                                                           const int32_t *nbr_ptr, const int32_t *nbr_ord,
-                                                          unsigned long long *tstat, int64_t *toff,
+                                                          unsigned long long *tstat, int64_t *toff, int64_t T,
                                                           int32_t *tverts, int32_t *tgrade, int64_t *tcolptr,
                                                           int32_t *trow, DevStatus *st) {
   __shared__ uint32_t smask[8][32];
@@ -909,6 +909,10 @@ static __global__ void __launch_bounds__(256) k_tri_fused(const int32_t *everts,
             else if (cv < b) { x0 = a; x1 = cv; x2 = b; }
             else { x0 = a; x1 = b; x2 = cv; }
             const int64_t p = t + q;
+            if (p >= T) {  // counts disagree with the sizing pass: never write past the outputs
+              raise_flag(st, F_INTERNAL);
+              continue;
+            }
             tverts[3 * p] = x0;
             tverts[3 * p + 1] = x1;
             tverts[3 * p + 2] = x2;
@@ -934,7 +938,7 @@ static __global__ void __launch_bounds__(256) k_lex_tri_gen(const int32_t *evert
                                                             const int32_t *nbr_ptr, const int32_t *nbr_ord,
                                                             const int32_t *deg, const int32_t *up,
                                                             const int64_t *lex_ptr, const int64_t *toff,
-                                                            uint64_t *tkeys) {
+                                                            int64_t T, uint64_t *tkeys, DevStatus *st) {
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
@@ -970,7 +974,8 @@ static __global__ void __launch_bounds__(256) k_lex_tri_gen(const int32_t *evert
           const int32_t gac = egrade[oa[pa[ww] + __popc(ra[ww] & below)]];
           const int32_t gbc = egrade[ob[pb[ww] + __popc(rb[ww] & below)]];
           const int32_t g = max(gab, max(gac, gbc));
-          tkeys[t + q] = ((uint64_t)g << LEX_SHIFT) | lex3(a, b, cv);
+          if (t + q < T) tkeys[t + q] = ((uint64_t)g << LEX_SHIFT) | lex3(a, b, cv);
+          else raise_flag(st, F_INTERNAL);
         }
       }
       t += tot;
