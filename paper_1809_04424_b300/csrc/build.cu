@@ -355,10 +355,15 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_TRY(ws.alloc(&tstat, E));
       VR_TRY(ws.alloc(&toff_me, E + 1));
       VR_CUDA(cudaMemsetAsync(tstat, 0, sizeof(unsigned long long) * E, s));
-      VR_CUDA(cudaMemsetAsync(&st->ticket, 0, sizeof(uint64_t), s));
       VR_CUDA(cudaMemcpyAsync(toff_me + E, &T, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+      // Every CTA of the ordered pass must be resident at once.
+      int dev = 0, nsm = 0, per_sm = 0;
+      VR_CUDA(cudaGetDevice(&dev));
+      VR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      VR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tri_fused, 256, 0));
+      const unsigned fused_grid = (unsigned)std::max(1, std::min(nsm * per_sm, (int)((E + 7) / 8)));
       prof.begin("tri_emit");
-      k_tri_fused<<<148 * 6, 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr, nbr_ord, tstat, toff_me, T,
+      k_tri_fused<<<fused_grid, 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr, nbr_ord, tstat, toff_me, T,
                                           tverts, tgrade, tcol, trow, st);
       count_launch();
       VR_CUDA(cudaGetLastError());

@@ -784,13 +784,15 @@ static __global__ void __launch_bounds__(256) k_tri_prep(const int32_t *everts, 
   }
 }
 
-// Ordered single-pass emission in max-edge order.  Warps take edges in order
-// by ticket; each checks every candidate c of its edge (ord(a,c) < e and
-// ord(b,c) < e) once, keeping the valid bits, publishes its count, and finds
-// its output offset by decoupled look-back over the predecessors' published
-// counts (a 64-bit word: 2 flag bits + value).  A warp only waits on lower
-// tickets, which were taken by warps already running, so every wait ends;
-// it is still bounded, and gives up with F_TIMEOUT.
+// Ordered single-pass emission in max-edge order.  Warp w of a grid that is
+// entirely resident (sized from the occupancy query) handles edges w, w + N,
+// w + 2N, ... in increasing order; for each it checks every candidate c
+// (ord(a,c) < e and ord(b,c) < e) once, keeping the valid bits, publishes its
+// count, and finds its output offset by decoupled look-back over the
+// predecessors' published counts (a 64-bit word: 2 flag bits + value).  A
+// count is published before any wait, and every predecessor belongs to a
+// resident warp, so every wait ends; it is still bounded, and gives up with
+// F_TIMEOUT.
 constexpr uint64_t LB_AGG = 1ull << 62, LB_PRE = 2ull << 62, LB_VAL = (1ull << 62) - 1;
 constexpr int LB_SPIN_LIMIT = 1 << 24;
 
@@ -840,11 +842,8 @@ static __global__ void __launch_bounds__(256) k_tri_fused(const int32_t *everts,
   const int wid = threadIdx.x >> 5, l = lane_id();
   const uint32_t lt = lanemask_lt();
   const int R = (W + 31) / 32;
-  for (;;) {
-    int64_t e = 0;
-    if (l == 0) e = (int64_t)atomicAdd((unsigned long long *)&st->ticket, 1ull);
-    e = __shfl_sync(0xffffffffu, e, 0);
-    if (e >= E) break;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; e < E; e += nwarps) {
     const int a = everts[2 * e], b = everts[2 * e + 1];
     const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
     const int32_t *pa = adjpre + (int64_t)a * W, *pb = adjpre + (int64_t)b * W;
