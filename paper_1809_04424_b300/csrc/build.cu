@@ -363,10 +363,17 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tri_fused, 256, 0));
       const unsigned fused_grid = (unsigned)std::max(1, std::min(nsm * per_sm, (int)((E + 7) / 8)));
       prof.begin("tri_emit");
-      k_tri_fused<<<fused_grid, 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr, nbr_ord, tstat, toff_me, T,
-                                          tverts, tgrade, tcol, trow, st);
+      {
+        // Cooperative launch: the runtime guarantees all CTAs are co-resident,
+        // which the look-back waits rely on (concurrent kernels included).
+        int64_t Tv = T;
+        void *args[] = {(void *)&everts, (void *)&egrade, (void *)&E,       (void *)&adj,     (void *)&adjpre,
+                        (void *)&W,      (void *)&nbr_ptr, (void *)&nbr_ord, (void *)&tstat,   (void *)&toff_me,
+                        (void *)&Tv,     (void *)&tverts, (void *)&tgrade,  (void *)&tcol,    (void *)&trow,
+                        (void *)&st};
+        VR_CUDA(cudaLaunchCooperativeKernel((const void *)k_tri_fused, dim3(fused_grid), dim3(256), args, 0, s));
+      }
       count_launch();
-      VR_CUDA(cudaGetLastError());
       prof.end();
       if (hst->tie_upper > 0) {
         // Grade groups spanning several edges with triangles: merge to lex order.
