@@ -276,30 +276,29 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_CUDA(cudaMemcpyAsync(ecol, &zero64, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   }
 
-  int32_t *tcnt = nullptr;
+  int32_t *tcnt = nullptr, *tsmallq = nullptr, *tmidq = nullptr, *tbigq = nullptr;
   int64_t *toff = nullptr;
   if (maxdim >= 2 && E > 0) {
     VR_TRY(ws.alloc(&tcnt, E));
     VR_TRY(ws.alloc(&toff, E + 1));
-    prof.begin("tri_prep");
-    k_tri_prep<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, deg, up, lex_ptr, gstart,
-                                                          tcnt, st);
-    count_launch();
-    VR_CUDA(cudaGetLastError());
+    VR_TRY(ws.alloc(&tsmallq, E + 1));
+    VR_TRY(ws.alloc(&tmidq, E + 1));
+    VR_TRY(ws.alloc(&tbigq, E + 1));
+    prof.begin("tri_count");
+    k_tri_count<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, E, adj, adjpre, W, nbr_ptr, nbr_ord, deg, up,
+                                                           lex_ptr, st, tcnt);
+    count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int64_t>(tcnt, toff, E, bs_e, s)));
     VR_CUDA(cudaMemcpyAsync(&st->T, toff + E, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    k_tri_groups<<<grid_for(E + 1, 256), 256, 0, s>>>(gstart, tcnt, toff, tsmallq, tmidq, tbigq, st);
+    VR_CUDA(cudaGetLastError());
     prof.end();
   }
 
-  // ---- sync 2: grade count, triangle count, tie bound.
+  // ---- sync 2: grade count, triangle count, tie-group sizes.
   VR_TRY(read_status(st, hst, s));
   const int64_t ngrades = E > 0 ? hst->ngrades : 1;
-  const int64_t T = (maxdim >= 2 && E > 0) ? hst->tsum3 / 3 : 0;
-  if (maxdim >= 2 && E > 0 && (hst->tsum3 % 3 != 0 || hst->T != T)) {
-    set_error("triangle sizing disagrees: incidence sum %lld, lex total %lld", (long long)hst->tsum3,
-              (long long)hst->T);
-    return VR_ERR_INTERNAL;
-  }
+  const int64_t T = (maxdim >= 2 && E > 0) ? hst->T : 0;
   if (T > INT32_MAX) {
     set_error("%lld triangles exceed the 2^31-1 limit of one dimension", (long long)T);
     return VR_ERR_RANGE;
@@ -349,70 +348,44 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_CUDA(cudaGetLastError());
       prof.end();
     } else if (T > 0) {
-      // Max-edge order: one ordered pass with decoupled look-back.
-      unsigned long long *tstat;
-      int64_t *toff_me;
-      VR_TRY(ws.alloc(&tstat, E));
-      VR_TRY(ws.alloc(&toff_me, E + 1));
-      VR_CUDA(cudaMemsetAsync(tstat, 0, sizeof(unsigned long long) * E, s));
-      VR_CUDA(cudaMemcpyAsync(toff_me + E, &T, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-      // Every CTA of the ordered pass must be resident at once.
-      int dev = 0, nsm = 0, per_sm = 0;
-      VR_CUDA(cudaGetDevice(&dev));
-      VR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-      VR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tri_fused, 256, 0));
-      const unsigned fused_grid = (unsigned)std::max(1, std::min(nsm * per_sm, (int)((E + 7) / 8)));
       prof.begin("tri_emit");
-      {
-        // Cooperative launch: the runtime guarantees all CTAs are co-resident,
-        // which the look-back waits rely on (concurrent kernels included).
-        int64_t Tv = T;
-        void *args[] = {(void *)&everts, (void *)&egrade, (void *)&E,       (void *)&adj,     (void *)&adjpre,
-                        (void *)&W,      (void *)&nbr_ptr, (void *)&nbr_ord, (void *)&tstat,   (void *)&toff_me,
-                        (void *)&Tv,     (void *)&tverts, (void *)&tgrade,  (void *)&tcol,    (void *)&trow,
-                        (void *)&st};
-        VR_CUDA(cudaLaunchCooperativeKernel((const void *)k_tri_fused, dim3(fused_grid), dim3(256), args, 0, s));
-      }
+      k_tri_emit<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr, nbr_ord, toff,
+                                                          T, tverts, tgrade, tcol, trow, st);
       count_launch();
+      VR_CUDA(cudaGetLastError());
       prof.end();
-      if (hst->tie_upper > 0) {
-        // Grade groups spanning several edges with triangles: merge to lex order.
-        prof.begin("tri_tie_merge");
-        int32_t *tsmallq, *tmidq, *tbigq;
-        int64_t *tbigoff;
-        VR_TRY(ws.alloc(&tsmallq, E + 1));
-        VR_TRY(ws.alloc(&tmidq, E + 1));
-        VR_TRY(ws.alloc(&tbigq, E + 1));
-        VR_TRY(ws.alloc(&tbigoff, E + 1));
-        k_tri_groups<<<grid_for(E + 1, 256), 256, 0, s>>>(gstart, toff_me, tsmallq, tmidq, tbigq, tbigoff, st);
-        k_tri_fix_smem<TRI_SMALL><<<148 * 8, 256, (size_t)TRI_SMALL * (8 + 4 + 12), s>>>(
-            gstart, toff_me, tsmallq, &st->small_seg_count, tverts, trow);
-        const size_t smem_mid = (size_t)TRI_MID * (8 + 4 + 12);
-        VR_CUDA(cudaFuncSetAttribute(k_tri_fix_smem<TRI_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_mid));
-        k_tri_fix_smem<TRI_MID><<<148, 512, smem_mid, s>>>(gstart, toff_me, tmidq, &st->mid_seg_count, tverts, trow);
-        count_launch(3);
+      prof.begin("tri_tie_merge");
+      if (hst->small_seg_count > 0) {
+        const size_t smem = (size_t)TRI_SMALL * (8 + 4 + 12);
+        k_tri_fix_smem<TRI_SMALL><<<std::min(hst->small_seg_count, 148 * 8), 256, smem, s>>>(
+            gstart, toff, tsmallq, &st->small_seg_count, tverts, trow);
+        count_launch();
         VR_CUDA(cudaGetLastError());
-        if (hst->tie_upper > TRI_MID) {
-          // Segments above TRI_MID hold at most tie_upper triangles in all.
-          const int64_t m = hst->tie_upper;
-          uint64_t *k1, *k2;
-          uint32_t *v1, *v2;
-          int32_t *rtmp;
-          VR_TRY(ws.alloc(&k1, m));
-          VR_TRY(ws.alloc(&k2, m));
-          VR_TRY(ws.alloc(&v1, m));
-          VR_TRY(ws.alloc(&v2, m));
-          VR_TRY(ws.alloc(&rtmp, 3 * m));
-          k_tri_fix_big<<<148 * 2, RS_THREADS, 0, s>>>(gstart, toff_me, tbigq, tbigoff, st, tverts, trow, k1, v1, k2,
-                                                      v2, rtmp);
-          count_launch();
-          VR_CUDA(cudaGetLastError());
-        }
-        prof.end();
       }
-      // The ordered pass reports a (never expected) look-back timeout here.
-      VR_TRY(read_status(st, hst, s));
+      if (hst->mid_seg_count > 0) {
+        const size_t smem = (size_t)TRI_MID * (8 + 4 + 12);
+        VR_CUDA(cudaFuncSetAttribute(k_tri_fix_smem<TRI_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+        k_tri_fix_smem<TRI_MID><<<std::min(hst->mid_seg_count, 148), 512, smem, s>>>(
+            gstart, toff, tmidq, &st->mid_seg_count, tverts, trow);
+        count_launch();
+        VR_CUDA(cudaGetLastError());
+      }
+      if (hst->big_seg_count > 0) {
+        uint64_t *k1, *k2;
+        uint32_t *v1, *v2;
+        int32_t *rtmp;
+        VR_TRY(ws.alloc(&k1, T));
+        VR_TRY(ws.alloc(&k2, T));
+        VR_TRY(ws.alloc(&v1, T));
+        VR_TRY(ws.alloc(&v2, T));
+        VR_TRY(ws.alloc(&rtmp, 3 * T));
+        k_tri_fix_big<<<(unsigned)std::min<int64_t>(hst->big_seg_count, 148 * 2), RS_THREADS, 0, s>>>(
+            gstart, toff, tbigq, st, tverts, trow, k1, v1, k2, v2, rtmp);
+        count_launch();
+        VR_CUDA(cudaGetLastError());
+      }
+      prof.end();
     }
   }
 

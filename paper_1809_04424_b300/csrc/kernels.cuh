@@ -739,192 +739,48 @@ __device__ __forceinline__ int64_t lex_pos(int a, int b, const uint32_t *adj, co
   return lex_ptr[a] + bit_rank(adj + (int64_t)a * W, adjpre + (int64_t)a * W, b) - (deg[a] - up[a]);
 }
 
-// Triangle sizing, one cheap pass (popcounts only): every triangle of the
-// kept graph belongs to the complex, so T = (sum over edges of
-// |N(a) & N(b)|) / 3 exactly.  The same pass writes each edge's lex-order
-// count (c > b), used by the lex enumeration, and bounds the triangles of
-// multi-edge grade groups (the only ones the max-edge order may need to merge).
-static __global__ void __launch_bounds__(256) k_tri_prep(const int32_t *everts, const int32_t *egrade, int64_t E,
-                                                         const uint32_t *adj, const int32_t *adjpre, int W,
-                                                         const int32_t *deg, const int32_t *up,
-                                                         const int64_t *lex_ptr, const int32_t *gstart,
-                                                         int32_t *tcnt, DevStatus *st) {
-  __shared__ unsigned long long bsum[2];
-  if (threadIdx.x < 2) bsum[threadIdx.x] = 0;
-  __syncthreads();
+static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts, int64_t E, const uint32_t *adj,
+                                                          const int32_t *adjpre, int W, const int32_t *nbr_ptr,
+                                                          const int32_t *nbr_ord, const int32_t *deg,
+                                                          const int32_t *up, const int64_t *lex_ptr,
+                                                          const DevStatus *st, int32_t *tcnt) {
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
-  uint64_t full_acc = 0, tie_acc = 0;
+  const bool lexm = lex_mode(E, st->ngrades);
   for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
     const int a = everts[2 * e], b = everts[2 * e + 1];
     const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
-    int full = 0, lexc = 0;
-    for (int w = l; w < W; w += 32) {
-      const uint32_t m = ra[w] & rb[w];
-      full += __popc(m);
-      lexc += __popc(m & above_mask(b, w));
-    }
-    full = warp_sum(full);
-    lexc = warp_sum(lexc);
-    if (l == 0) {
-      tcnt[lex_pos(a, b, adj, adjpre, W, deg, up, lex_ptr)] = lexc;
-      full_acc += (uint64_t)full;
-      const int32_t g = egrade[e];
-      if (gstart[g + 1] - gstart[g] >= 2) tie_acc += (uint64_t)full;
-    }
-  }
-  if (l == 0) {
-    atomicAdd(&bsum[0], (unsigned long long)full_acc);
-    atomicAdd(&bsum[1], (unsigned long long)tie_acc);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    atomicAdd((unsigned long long *)&st->tsum3, bsum[0]);
-    atomicAdd((unsigned long long *)&st->tie_upper, bsum[1]);
-  }
-}
-
-// Ordered single-pass emission in max-edge order.  Warp w of a grid that is
-// entirely resident (sized from the occupancy query) handles edges w, w + N,
-// w + 2N, ... in increasing order; for each it checks every candidate c
-// (ord(a,c) < e and ord(b,c) < e) once, keeping the valid bits, publishes its
-// count, and finds its output offset by decoupled look-back over the
-// predecessors' published counts (a 64-bit word: 2 flag bits + value).  A
-// count is published before any wait, and every predecessor belongs to a
-// resident warp, so every wait ends; it is still bounded, and gives up with
-// F_TIMEOUT.
-constexpr uint64_t LB_AGG = 1ull << 62, LB_PRE = 2ull << 62, LB_VAL = (1ull << 62) - 1;
-constexpr int LB_SPIN_LIMIT = 1 << 24;
-
-__device__ __forceinline__ int64_t warp_lookback(unsigned long long *tstat, int64_t e, int64_t cnt, DevStatus *st) {
-  const int l = lane_id();
-  volatile unsigned long long *vs = tstat;
-  if (e == 0) {
-    if (l == 0) vs[0] = LB_PRE | (uint64_t)cnt;
-    return 0;
-  }
-  if (l == 0) vs[e] = LB_AGG | (uint64_t)cnt;
-  int64_t prefix = 0;
-  for (int64_t k = e - 1;; k -= 32) {
-    const int64_t idx = k - l;
-    uint64_t v = LB_PRE;  // before the first edge: a zero prefix
-    if (idx >= 0) {
-      v = vs[idx];
-      int it = 0;
-      while ((v >> 62) == 0 && it < LB_SPIN_LIMIT) {
-        __nanosleep(64);
-        v = vs[idx];
-        ++it;
-      }
-      if ((v >> 62) == 0) {
-        raise_flag(st, F_TIMEOUT);
-        v = LB_PRE;
-      }
-    }
-    const uint32_t pre = __ballot_sync(0xffffffffu, (v >> 62) == 2);
-    const int stop = pre ? __ffs(pre) - 1 : 31;
-    prefix += warp_sum(l <= stop ? (int64_t)(v & LB_VAL) : (int64_t)0);
-    if (pre) break;
-  }
-  if (l == 0) vs[e] = LB_PRE | (uint64_t)(prefix + cnt);
-  return prefix;
-}
-
-constexpr int MAX_ROUNDS = (VR_MAX_POINTS / 32 + 31) / 32;  // 8 rounds of 32 words
-
-static __global__ void __launch_bounds__(256) k_tri_fused(const int32_t *everts, const int32_t *egrade, int64_t E,
-                                                          const uint32_t *adj, const int32_t *adjpre, int W,
-                                                          const int32_t *nbr_ptr, const int32_t *nbr_ord,
-                                                          unsigned long long *tstat, int64_t *toff, int64_t T,
-                                                          int32_t *tverts, int32_t *tgrade, int64_t *tcolptr,
-                                                          int32_t *trow, DevStatus *st) {
-  __shared__ uint32_t smask[8][32];
-  const int wid = threadIdx.x >> 5, l = lane_id();
-  const uint32_t lt = lanemask_lt();
-  const int R = (W + 31) / 32;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; e < E; e += nwarps) {
-    const int a = everts[2 * e], b = everts[2 * e + 1];
-    const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
-    const int32_t *pa = adjpre + (int64_t)a * W, *pb = adjpre + (int64_t)b * W;
-    const int32_t *oa = nbr_ord + nbr_ptr[a], *ob = nbr_ord + nbr_ptr[b];
-    uint32_t vm[MAX_ROUNDS];
     int cnt = 0;
-#pragma unroll
-    for (int r = 0; r < MAX_ROUNDS; ++r) {
-      vm[r] = 0;
-      if (r < R) {
-        const int w0 = r * 32, w = w0 + l;
+    if (lexm) {
+      for (int w = (b >> 5) + l; w < W; w += 32) cnt += __popc(ra[w] & rb[w] & above_mask(b, w));
+    } else {
+      const int32_t *pa = adjpre + (int64_t)a * W, *pb = adjpre + (int64_t)b * W;
+      const int32_t *oa = nbr_ord + nbr_ptr[a], *ob = nbr_ord + nbr_ptr[b];
+      for (int w0 = 0; w0 < W; w0 += 32) {
+        const int w = w0 + l;
         const uint32_t wa = w < W ? ra[w] : 0u, wb = w < W ? rb[w] : 0u;
         const int32_t qa = w < W ? pa[w] : 0, qb = w < W ? pb[w] : 0;
         const uint32_t m = wa & wb;
-        smask[wid][l] = 0;
-        __syncwarp();
-        const BitChunk rc = bit_round(m);
-        for (int q0 = 0; q0 < rc.tot; q0 += 32) {
+        const BitChunk r = bit_round(m);
+        for (int q0 = 0; q0 < r.tot; q0 += 32) {
           const int q = q0 + l;
-          const int ow = bit_owner(rc, q);
+          const int ow = bit_owner(r, q);
           const uint32_t om = __shfl_sync(0xffffffffu, m, ow), owa = __shfl_sync(0xffffffffu, wa, ow),
                          owb = __shfl_sync(0xffffffffu, wb, ow);
           const int32_t oqa = __shfl_sync(0xffffffffu, qa, ow), oqb = __shfl_sync(0xffffffffu, qb, ow);
-          const int oex = __shfl_sync(0xffffffffu, rc.excl, ow);
-          if (q < rc.tot) {
+          const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
+          bool ok = false;
+          if (q < r.tot) {
             const int bit = __fns(om, 0, q - oex + 1);
             const uint32_t below = (1u << bit) - 1u;
-            if (oa[oqa + __popc(owa & below)] < (int32_t)e && ob[oqb + __popc(owb & below)] < (int32_t)e)
-              atomicOr(&smask[wid][ow], 1u << bit);
+            ok = oa[oqa + __popc(owa & below)] < (int32_t)e && ob[oqb + __popc(owb & below)] < (int32_t)e;
           }
+          cnt += __popc(__ballot_sync(0xffffffffu, ok));
         }
-        __syncwarp();
-        vm[r] = smask[wid][l];
-        __syncwarp();
-        cnt += __popc(vm[r]);
       }
     }
-    cnt = warp_sum(cnt);
-    const int64_t base = warp_lookback(tstat, e, cnt, st);
-    if (l == 0) toff[e] = base;
-    const int32_t g = egrade[e];
-    int64_t t = base;
-#pragma unroll
-    for (int r = 0; r < MAX_ROUNDS; ++r) {
-      if (r < R) {
-        const uint32_t m = vm[r];
-        const BitChunk rc = bit_round(m);
-        for (int q0 = 0; q0 < rc.tot; q0 += 32) {
-          const int q = q0 + l;
-          const int ow = bit_owner(rc, q);
-          const uint32_t om = __shfl_sync(0xffffffffu, m, ow);
-          const int oex = __shfl_sync(0xffffffffu, rc.excl, ow);
-          if (q < rc.tot) {
-            const int ww = r * 32 + ow;
-            const int bit = __fns(om, 0, q - oex + 1);
-            const uint32_t below = (1u << bit) - 1u;
-            const int cv = ww * 32 + bit;
-            const int32_t oac = oa[pa[ww] + __popc(ra[ww] & below)];
-            const int32_t obc = ob[pb[ww] + __popc(rb[ww] & below)];
-            int x0, x1, x2;
-            if (cv < a) { x0 = cv; x1 = a; x2 = b; }
-            else if (cv < b) { x0 = a; x1 = cv; x2 = b; }
-            else { x0 = a; x1 = b; x2 = cv; }
-            const int64_t p = t + q;
-            if (p >= T) {  // counts disagree with the sizing pass: never write past the outputs
-              raise_flag(st, F_INTERNAL);
-              continue;
-            }
-            tverts[3 * p] = x0;
-            tverts[3 * p + 1] = x1;
-            tverts[3 * p + 2] = x2;
-            tgrade[p] = g;
-            tcolptr[p] = 3 * p;
-            trow[3 * p] = min(oac, obc);
-            trow[3 * p + 1] = max(oac, obc);
-            trow[3 * p + 2] = (int32_t)e;
-          }
-        }
-        t += rc.tot;
-      }
-    }
+    if (lexm) cnt = warp_sum(cnt);  // max-edge lanes already hold the warp total
+    if (l == 0) tcnt[lexm ? lex_pos(a, b, adj, adjpre, W, deg, up, lex_ptr) : e] = cnt;
   }
 }
 
@@ -974,7 +830,7 @@ static __global__ void __launch_bounds__(256) k_lex_tri_gen(const int32_t *evert
           const int32_t gbc = egrade[ob[pb[ww] + __popc(rb[ww] & below)]];
           const int32_t g = max(gab, max(gac, gbc));
           if (t + q < T) tkeys[t + q] = ((uint64_t)g << LEX_SHIFT) | lex3(a, b, cv);
-          else raise_flag(st, F_INTERNAL);
+          else raise_flag(st, F_INTERNAL);  // never write past the key array
         }
       }
       t += tot;
@@ -1009,6 +865,77 @@ static __global__ void k_tri_final(const uint64_t *tkeys, int64_t T, const uint3
   }
 }
 
+// Emission.  Each round (32 words, one per lane) the warp knows how many
+// triangles each lane's word holds; it then writes them in chunks of 32 with
+// lane q taking the round's q-th triangle, found by a 5-step search over the
+// lanes' prefix counts and __fns inside the owner's mask, so consecutive
+// lanes write consecutive output slots (coalesced stores).
+static __global__ void __launch_bounds__(256) k_tri_emit(const int32_t *everts, const int32_t *egrade, int64_t E,
+                                                         const uint32_t *adj, const int32_t *adjpre, int W,
+                                                         const int32_t *nbr_ptr, const int32_t *nbr_ord,
+                                                         const int64_t *toff, int64_t T, int32_t *tverts,
+                                                         int32_t *tgrade, int64_t *tcolptr, int32_t *trow,
+                                                         DevStatus *st) {
+  const int l = lane_id();
+  const uint32_t lt = lanemask_lt();
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
+    const int a = everts[2 * e], b = everts[2 * e + 1];
+    const int32_t g = egrade[e];
+    const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
+    const int32_t *pa = adjpre + (int64_t)a * W, *pb = adjpre + (int64_t)b * W;
+    const int32_t *oa = nbr_ord + nbr_ptr[a], *ob = nbr_ord + nbr_ptr[b];
+    int64_t t = toff[e];
+    for (int w0 = 0; w0 < W; w0 += 32) {
+      const int w = w0 + l;
+      const uint32_t wa = w < W ? ra[w] : 0u, wb = w < W ? rb[w] : 0u;
+      const int32_t qa = w < W ? pa[w] : 0, qb = w < W ? pb[w] : 0;
+      const uint32_t m = wa & wb;
+      const BitChunk r = bit_round(m);
+      for (int q0 = 0; q0 < r.tot; q0 += 32) {
+        const int q = q0 + l;
+        const int ow = bit_owner(r, q);
+        const uint32_t om = __shfl_sync(0xffffffffu, m, ow), owa = __shfl_sync(0xffffffffu, wa, ow),
+                       owb = __shfl_sync(0xffffffffu, wb, ow);
+        const int32_t oqa = __shfl_sync(0xffffffffu, qa, ow), oqb = __shfl_sync(0xffffffffu, qb, ow);
+        const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
+        bool ok = false;
+        int cv = 0;
+        int32_t oac = 0, obc = 0;
+        if (q < r.tot) {
+          const int bit = __fns(om, 0, q - oex + 1);
+          const uint32_t below = (1u << bit) - 1u;
+          cv = (w0 + ow) * 32 + bit;
+          oac = oa[oqa + __popc(owa & below)];
+          obc = ob[oqb + __popc(owb & below)];
+          ok = oac < (int32_t)e && obc < (int32_t)e;
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+        if (ok && t + __popc(bal & lt) >= T) {  // never write past the outputs
+          raise_flag(st, F_INTERNAL);
+          ok = false;
+        }
+        if (ok) {
+          const int64_t p = t + __popc(bal & lt);
+          int x0, x1, x2;
+          if (cv < a) { x0 = cv; x1 = a; x2 = b; }
+          else if (cv < b) { x0 = a; x1 = cv; x2 = b; }
+          else { x0 = a; x1 = b; x2 = cv; }
+          tverts[3 * p] = x0;
+          tverts[3 * p + 1] = x1;
+          tverts[3 * p + 2] = x2;
+          tgrade[p] = g;
+          tcolptr[p] = 3 * p;
+          trow[3 * p] = min(oac, obc);
+          trow[3 * p + 1] = max(oac, obc);
+          trow[3 * p + 2] = (int32_t)e;
+        }
+        t += __popc(bal);
+      }
+    }
+  }
+}
+
 // Per grade group: the triangles of a group that spans several edges with
 // triangles must be merged into lexicographic order.  Queue such groups by
 // size class: small (CTA sort in 24 KB of shared memory), mid (192 KB), big
@@ -1016,14 +943,15 @@ static __global__ void k_tri_final(const uint64_t *tkeys, int64_t T, const uint3
 constexpr int TRI_SMALL = 1024;
 constexpr int TRI_MID = 8192;
 
-static __global__ void k_tri_groups(const int32_t *gstart, const int64_t *toff, int32_t *smallq, int32_t *midq,
-                                    int32_t *bigq, int64_t *bigoff, DevStatus *st) {
+static __global__ void k_tri_groups(const int32_t *gstart, const int32_t *tcnt, const int64_t *toff, int32_t *smallq,
+                                    int32_t *midq, int32_t *bigq, DevStatus *st) {
   const int64_t ngrades = st->ngrades;
+  if (lex_mode(st->E, ngrades)) return;  // lex mode needs no merge
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngrades; g += (int64_t)gridDim.x * blockDim.x) {
     const int32_t b = gstart[g], e = gstart[g + 1];
     if (e - b < 2) continue;
     int runs = 0;
-    for (int32_t x = b; x < e && runs < 2; ++x) runs += toff[x + 1] > toff[x];
+    for (int32_t x = b; x < e && runs < 2; ++x) runs += tcnt[x] > 0;
     if (runs < 2) continue;
     const int64_t s = toff[e] - toff[b];
     if (s <= TRI_SMALL) {
@@ -1033,8 +961,8 @@ static __global__ void k_tri_groups(const int32_t *gstart, const int64_t *toff, 
     } else {
       int q = (int)atomicAdd((unsigned long long *)&st->big_seg_count, 1ull);
       bigq[q] = (int32_t)g;
-      bigoff[q] = (int64_t)atomicAdd((unsigned long long *)&st->big_seg_total, (unsigned long long)s);
       atomicMax((unsigned long long *)&st->big_seg_max, (unsigned long long)s);
+      atomicAdd((unsigned long long *)&st->big_seg_total, (unsigned long long)s);
     }
   }
 }
@@ -1086,19 +1014,18 @@ static __global__ void k_tri_fix_smem(const int32_t *gstart, const int64_t *toff
 // lexicographic keys through global temporaries indexed by absolute triangle
 // position (each group owns the slice of its own segment).
 static __global__ void __launch_bounds__(RS_THREADS) k_tri_fix_big(const int32_t *gstart, const int64_t *toff,
-                                                                   const int32_t *bigq, const int64_t *bigoff,
-                                                                   const DevStatus *st, int32_t *tverts,
-                                                                   int32_t *trow, uint64_t *k1, uint32_t *v1,
-                                                                   uint64_t *k2, uint32_t *v2, int32_t *rtmp) {
+                                                                   const int32_t *bigq, const DevStatus *st,
+                                                                   int32_t *tverts, int32_t *trow, uint64_t *k1,
+                                                                   uint32_t *v1, uint64_t *k2, uint32_t *v2,
+                                                                   int32_t *rtmp) {
   const int nq = (int)st->big_seg_count;
   for (int q = blockIdx.x; q < nq; q += gridDim.x) {
     const int g = bigq[q];
     const int64_t s0 = toff[gstart[g]];
     const int64_t s = toff[gstart[g + 1]] - s0;
-    const int64_t o = bigoff[q];  // this group's slice of the temporaries
-    uint64_t *K1 = k1 + o, *K2 = k2 + o;
-    uint32_t *V1 = v1 + o, *V2 = v2 + o;
-    int32_t *R = rtmp + 3 * o;
+    uint64_t *K1 = k1 + s0, *K2 = k2 + s0;
+    uint32_t *V1 = v1 + s0, *V2 = v2 + s0;
+    int32_t *R = rtmp + 3 * s0;
     for (int64_t t = threadIdx.x; t < s; t += blockDim.x) {
       const int64_t p = s0 + t;
       K1[t] = lex3(tverts[3 * p], tverts[3 * p + 1], tverts[3 * p + 2]);

@@ -56,9 +56,6 @@ struct DevStatus {
   int64_t big_seg_total;     // triangles inside the segments needing a global sort
   int64_t big_grp_max;       // float: largest repair group needing a global sort
   int64_t big_grp_count;
-  int64_t tsum3;             // sum over edges of |N(a) & N(b)| = 3 T
-  int64_t tie_upper;         // bound on triangles of multi-edge grade groups
-  uint64_t ticket;           // next edge for the ordered (look-back) emission
 };
 
 __device__ __forceinline__ void raise_flag(DevStatus *st, int32_t f) { atomicOr(&st->flags, f); }
