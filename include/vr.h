@@ -144,6 +144,32 @@ VR_API vr_status vr_complex_grade_values_to_host(const vr_complex *c, double *va
  * still exist).  NULL is ignored. */
 VR_API void vr_complex_free(vr_complex *c);
 
+/* ---- Batches: many clouds in two launches.
+ * vr_build_batch builds the complex of each of n_clouds clouds concatenated
+ * row-wise in `points` (d coordinates each, one dtype; device or host
+ * memory), cloud c being rows [offsets[c], offsets[c+1]) of a HOST array of
+ * n_clouds+1 row offsets (offsets[0] = 0).  maxdim and maxrad are HOST arrays
+ * of n_clouds values (NULL: 2 and +INFINITY for every cloud); their meaning is
+ * that of vr_build.  Each cloud's result is exactly vr_build's.  One CTA
+ * builds one cloud at a time (largest first) with its working set in shared
+ * memory; clouds too large for that take the single-cloud path.  The call
+ * synchronises on `stream` twice (sizes, then completion).
+ * Argument errors fail the whole call; a value error (non-finite float, ...)
+ * fails only its cloud, reported by vr_batch_get. */
+typedef struct vr_batch vr_batch;
+VR_API vr_status vr_build_batch(const void *points, const int64_t *offsets,
+                                int32_t n_clouds, int32_t d, vr_dtype dtype,
+                                const int32_t *maxdim, const double *maxrad,
+                                vr_stream_t stream, vr_batch **out);
+/* The result of one cloud: a view owned by the batch (do not pass it to
+ * vr_complex_free; it lives until vr_batch_free), and the cloud's status
+ * (view NULL when that status is not VR_OK). */
+VR_API vr_status vr_batch_get(const vr_batch *b, int32_t cloud,
+                              const vr_complex **view, vr_status *cloud_status);
+VR_API vr_status vr_batch_info(const vr_batch *b, int32_t *n_clouds,
+                               int64_t *total_simplices, int32_t *n_failed);
+VR_API void vr_batch_free(vr_batch *b);
+
 /* Measurement support (no counterpart in the paper's API; its Sec. 4 profiles
  * with Julia's sampling profiler).  When enabled, every build records a CUDA
  * event pair around each phase on its own stream; once the build's work is

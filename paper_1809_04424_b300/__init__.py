@@ -227,3 +227,85 @@ def vr_complex_grade_values_to_host(handle) -> np.ndarray:
 
 def vr_complex_free(handle) -> None:
     lib().vr_complex_free(ctypes.c_void_p(handle))
+
+
+# ---------------------------------------------------------------- batches
+
+class Batch:
+    """Owner of one ``vr_batch*``: per-cloud results as non-owning views."""
+
+    def __init__(self, handle: int, keepalive=None):
+        self.handle = handle
+        self._keep = keepalive
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                vr_batch_free(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+    def info(self) -> dict:
+        return vr_batch_info(self.handle)
+
+    def get(self, cloud: int):
+        """(status, Complex view or None) of one cloud; the view lives as long
+        as this batch."""
+        view, st = vr_batch_get(self.handle, cloud)
+        return st, (Complex(view, owned=False, keepalive=self) if view else None)
+
+
+def _set_batch_types(L):
+    if getattr(L, "_batch_types", False):
+        return
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    L.vr_build_batch.argtypes = [vp, vp, i32, i32, ctypes.c_int, vp, vp, vp, ctypes.POINTER(vp)]
+    L.vr_build_batch.restype = ctypes.c_int
+    L.vr_batch_get.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int)]
+    L.vr_batch_get.restype = ctypes.c_int
+    L.vr_batch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32)]
+    L.vr_batch_info.restype = ctypes.c_int
+    L.vr_batch_free.argtypes = [vp]
+    L.vr_batch_free.restype = None
+    L._batch_types = True
+
+
+def vr_build_batch(points, offsets, maxdim=None, maxrad=None, stream=None) -> Batch:
+    """Build every cloud of a row-concatenated point array (CUDA tensor or
+    numpy array) with host row `offsets` (n_clouds + 1)."""
+    L = lib()
+    _set_batch_types(L)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nc = off.shape[0] - 1
+    md = None if maxdim is None else np.ascontiguousarray(np.broadcast_to(maxdim, (nc,)), dtype=np.int32)
+    mr = None if maxrad is None else np.ascontiguousarray(np.broadcast_to(maxrad, (nc,)), dtype=np.float64)
+    if hasattr(points, "data_ptr"):
+        ptr, d, code, keep = points.data_ptr(), points.shape[1], _dtype_code(points.dtype), points
+    else:
+        keep = np.ascontiguousarray(points)
+        ptr, d, code = keep.ctypes.data, keep.shape[1], _dtype_code(keep.dtype)
+    h = ctypes.c_void_p()
+    s = _current_stream() if stream is None else stream
+    cp = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else None
+    _check(L.vr_build_batch(ctypes.c_void_p(ptr), cp(off), nc, d, code, cp(md), cp(mr), ctypes.c_void_p(s),
+                            ctypes.byref(h)))
+    return Batch(h.value, keepalive=(keep, off, md, mr))
+
+
+def vr_batch_get(handle, cloud: int):
+    v, st = ctypes.c_void_p(), ctypes.c_int()
+    _check(lib().vr_batch_get(ctypes.c_void_p(handle), cloud, ctypes.byref(v), ctypes.byref(st)))
+    return v.value, st.value
+
+
+def vr_batch_info(handle) -> dict:
+    nc, tot, nf = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+    _check(lib().vr_batch_info(ctypes.c_void_p(handle), ctypes.byref(nc), ctypes.byref(tot), ctypes.byref(nf)))
+    return {"n_clouds": nc.value, "total_simplices": tot.value, "n_failed": nf.value}
+
+
+def vr_batch_free(handle) -> None:
+    L = lib()
+    _set_batch_types(L)
+    L.vr_batch_free(ctypes.c_void_p(handle))

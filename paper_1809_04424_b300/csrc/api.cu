@@ -171,7 +171,7 @@ vr_status vr_complex_grade_values_to_host(const vr_complex *c, double *values) {
 }
 
 void vr_complex_free(vr_complex *c) {
-  if (!c) return;
+  if (!c || c->in_batch) return;
   if (c->owned)
     for (void *p : c->allocs) cudaFreeAsync(p, c->stream);
   cudaGetLastError();

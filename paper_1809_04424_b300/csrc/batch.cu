@@ -1,0 +1,846 @@
+// batch.cu -- many point clouds in two launches.
+//
+// vr_build_batch takes clouds concatenated row-wise with host offsets.  One
+// CTA owns one cloud at a time, taking clouds from a work list ordered by
+// descending size (longest first), and runs the whole build of that cloud
+// with its bitmap, prefix counts and per-row arrays in shared memory and its
+// longer arrays (keys, sort temporaries, neighbour CSR) in a per-CTA slice of
+// global scratch that stays in L2:
+//   k_batch_size  -- values check, kept-edge bitmap, E, and T as
+//                    (sum over edges of |N(a) & N(b)|) / 3;
+//   [one host sync: exact output arenas, per-cloud slices]
+//   k_batch_build -- bitmap again, lexicographic edge keys, CTA radix sort on
+//                    the distance bits, dense-rank grades, edge outputs and
+//                    neighbour CSR, lexicographic triangle keys carrying the
+//                    grade, CTA radix sort on the grade bits, final write.
+// Triangles always take the lexicographic enumeration (exact with ties).
+// A cloud beyond the fused limits (its bitmap, prefix counts and points above
+// 200 KB of shared memory, or a float run of equal fp32 keys longer than 64)
+// is rebuilt by the single-cloud path.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "complex.h"
+#include "kernels.cuh"
+#include "prof.h"
+
+namespace vr {
+
+constexpr int BT = RS_THREADS;  // 256: the CTA sort's tile ranking assumes it
+constexpr int BWARPS = BT / 32;
+constexpr size_t FUSED_SMEM = 200 * 1024;  // shared-memory budget of one fused cloud
+constexpr int RUN_MAX = 64;     // longest float run of equal fp32 keys handled in-CTA
+
+// Per-cloud descriptor (device and host copies).
+struct CloudDesc {
+  int64_t pt;                 // first row of the cloud in the concatenated points
+  int32_t n, maxdim;
+  int32_t keep_all, kbits;    // cap: keep everything; distance bits to sort
+  double maxrad;              // as given
+  uint64_t r2i;               // integer cap
+  double r2;                  // float cap
+  float a_keep, a_drop;       // float thresholds of the cap test
+  int64_t E, T;               // sizes (sizing pass)
+  int64_t eo, to, go, vo, co, ko;  // output offsets: edges, triangles, grade values, vertices, colptr
+  int32_t flags;              // value / internal flags of this cloud
+  int32_t fallback;           // 1: rebuild with the single-cloud path
+  int64_t ngrades;
+  double max_rel_err;
+};
+
+struct BatchOut {
+  int32_t *everts, *egrade, *erow;
+  int64_t *ecol;
+  int32_t *tverts, *tgrade, *trow;
+  int64_t *tcol;
+  int32_t *vverts, *vgrade;
+  double *gval;
+};
+
+// Per-CTA scratch slice layout (bytes from the slice base), sized from the
+// batch's largest E and T.
+struct ScratchLayout {
+  int64_t keys, tkeys, d64lex, d64, flag, gex, nbr_ord, gstart, tcnt, toff, tk, tk2, bytes;
+};
+
+static ScratchLayout scratch_layout(int64_t Emax, int64_t Tmax, bool F) {
+  ScratchLayout L{};
+  int64_t o = 0;
+  auto take = [&](int64_t bytes) {
+    int64_t at = o;
+    o += (bytes + 255) / 256 * 256;
+    return at;
+  };
+  const int64_t E1 = Emax + 2, T1 = std::max<int64_t>(Tmax, 1);
+  L.keys = take(8 * E1);
+  L.tkeys = take(8 * E1);
+  L.d64lex = F ? take(8 * E1) : 0;
+  L.d64 = F ? take(8 * E1) : 0;
+  L.flag = take(4 * E1);
+  L.gex = take(4 * E1);
+  L.nbr_ord = take(8 * E1);
+  L.gstart = take(4 * E1);
+  L.tcnt = take(4 * E1);
+  L.toff = take(8 * E1);
+  L.tk = take(8 * T1);
+  L.tk2 = take(8 * T1);
+  L.bytes = o;
+  return L;
+}
+
+// ----------------------------------------------------------- CTA helpers
+
+// Shared-memory layout of one fused cloud of up to nmax points (every region
+// 16-byte aligned): bitmap u32, prefix counts u16, deg, up, row pointers
+// (i32, n+2), lex pointers (i64, n+1), points (4 B each).
+struct SmemLayout {
+  size_t adj, pre, deg, up, nptr, lptr, X, bytes;
+};
+__host__ __device__ __forceinline__ size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
+__host__ __device__ __forceinline__ SmemLayout smem_layout(int nmax, int d) {
+  const size_t nw = (size_t)nmax * ((nmax + 31) / 32);
+  SmemLayout L;
+  L.adj = 0;
+  L.pre = L.adj + al16(nw * 4);
+  L.deg = L.pre + al16(nw * 2);
+  L.up = L.deg + al16((size_t)nmax * 4);
+  L.nptr = L.up + al16((size_t)nmax * 4);
+  L.lptr = L.nptr + al16((size_t)(nmax + 2) * 4);
+  L.X = L.lptr + al16((size_t)(nmax + 1) * 8);
+  L.bytes = L.X + al16((size_t)nmax * d * 4);
+  return L;
+}
+
+// Exclusive scan of in[0..L) into out[0..L], out[L] = total, by one CTA.
+template <typename TI, typename TO>
+__device__ void cta_scan(const TI *in, TO *out, int64_t L) {
+  __shared__ int64_t sh[33];
+  int64_t carry = 0;
+  for (int64_t b0 = 0; b0 < L; b0 += BT) {
+    const int64_t i = b0 + threadIdx.x;
+    const int64_t v = i < L ? (int64_t)in[i] : 0;
+    int64_t tot;
+    const int64_t e = block_excl_scan<int64_t>(v, sh, &tot);
+    if (i < L) out[i] = (TO)(carry + e);
+    carry += tot;
+  }
+  if (threadIdx.x == 0) out[L] = (TO)carry;
+  __syncthreads();
+}
+
+__device__ __forceinline__ int64_t cta_sum(int64_t v) {
+  __shared__ int64_t sh[33];
+  int64_t tot;
+  block_excl_scan<int64_t>(v, sh, &tot);
+  return tot;
+}
+
+__device__ __forceinline__ int32_t rank16(const uint32_t *row, const uint16_t *pre, int c) {
+  const int w = c >> 5, b = c & 31;
+  return (int32_t)pre[w] + __popc(row[w] & ((1u << b) - 1u));
+}
+
+// Stage points, bitmap (warp per 32x32 block of the upper triangle, ballot
+// rows, lane-accumulated mirrored columns), all in shared memory.
+template <bool F>
+__device__ void cta_bitmap(const void *pts, const CloudDesc &c, int d, void *Xs, uint32_t *adj, int32_t *flags) {
+  using T = typename std::conditional<F, float, int32_t>::type;
+  const int n = c.n, W = (n + 31) / 32;
+  T *X = (T *)Xs;
+  for (int t = threadIdx.x; t < n * d; t += BT) {
+    if constexpr (F) {
+      const float v = ((const float *)pts)[c.pt * d + t];
+      if (!isfinite(v)) atomicOr(flags, F_NONFINITE);
+      else if (fabsf(v) > (float)VR_MAX_F32_ABS) atomicOr(flags, F_F32_RANGE);
+      X[t] = v;
+    }
+  }
+  __syncthreads();
+  const int wid = threadIdx.x >> 5, l = lane_id();
+  const int nblk = W * W;
+  for (int blk = wid; blk < nblk; blk += BWARPS) {
+    const int bi = blk / W, bj = blk % W;
+    if (bi > bj) continue;
+    const int j = bj * 32 + l;
+    const bool jv = j < n;
+    uint32_t myrow = 0, mycol = 0;
+    bool over = false;
+    const int rows = min(32, n - bi * 32);
+    for (int r = 0; r < rows; ++r) {
+      const int i = bi * 32 + r;
+      bool kept = false;
+      if (jv && j != i) {
+        if constexpr (F) {
+          const float a = d2_f32(X + i * d, X + j * d, d);
+          if (c.keep_all || a <= c.a_keep) kept = true;
+          else if (a >= c.a_drop) kept = false;
+          else kept = d2_canonical(X + i * d, X + j * d, d) <= c.r2;
+        } else {
+          const uint64_t v = d2_int(X + i * d, X + j * d, d);
+          kept = c.keep_all || v <= c.r2i;
+          if (kept && v >= INT_KEY_LIMIT) over = true;
+        }
+      }
+      const uint32_t word = __ballot_sync(0xffffffffu, kept);
+      if (l == r) myrow = word;
+      mycol |= (uint32_t)kept << r;
+    }
+    if (over) atomicOr(flags, F_INT_KEY);
+    const int i = bi * 32 + l;
+    if (i < n) adj[i * W + bj] = myrow;
+    if (bi < bj && jv) adj[j * W + bi] = mycol;
+  }
+  __syncthreads();
+}
+
+// Integer clouds are staged by a typed loop (int8 or int32 source).
+template <typename TIn>
+__device__ void cta_stage_int(const TIn *pts, const CloudDesc &c, int d, int32_t *X) {
+  for (int t = threadIdx.x; t < c.n * d; t += BT) X[t] = (int32_t)pts[c.pt * d + t];
+}
+
+// Work list: clouds in descending size, fetched one per CTA iteration.
+__device__ __forceinline__ int next_cloud(int *cursor, const int32_t *order, int n_clouds) {
+  __shared__ int idx;
+  if (threadIdx.x == 0) idx = atomicAdd(cursor, 1);
+  __syncthreads();
+  const int k = idx;
+  __syncthreads();
+  return k < n_clouds ? order[k] : -1;
+}
+
+// ------------------------------------------------------------------ sizing
+
+template <bool F, typename TIn>
+__global__ void __launch_bounds__(BT) k_batch_size(const TIn *pts, int d, CloudDesc *desc, const int32_t *order,
+                                                   int n_clouds, int *cursor, int nmax) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int Wmax = (nmax + 31) / 32;
+  uint32_t *adj = (uint32_t *)smem;
+  void *Xs = (void *)(smem + al16((size_t)nmax * Wmax * 4));
+  __shared__ int32_t flags;
+  for (int ci; (ci = next_cloud(cursor, order, n_clouds)) >= 0;) {
+    CloudDesc &c = desc[ci];
+    if (c.fallback) continue;
+    if (threadIdx.x == 0) flags = 0;
+    __syncthreads();
+    if constexpr (!F) cta_stage_int<TIn>(pts, c, d, (int32_t *)Xs);
+    cta_bitmap<F>(pts, c, d, Xs, adj, &flags);
+    const int n = c.n, W = (n + 31) / 32;
+    const int wid = threadIdx.x >> 5, l = lane_id();
+    // E: upper-triangle bits; 3T: sum over edges (a < b) of |N(a) & N(b)|.
+    int64_t e_loc = 0, t3_loc = 0;
+    for (int a = wid; a < n; a += BWARPS) {
+      const uint32_t *ra = adj + a * W;
+      for (int w0 = (a + 1) >> 5; w0 < W; w0 += 32) {
+        const int w = w0 + l;
+        const uint32_t word = w < W ? ra[w] & above_mask(a, w) : 0u;
+        e_loc += __popc(word);
+        const BitChunk r = bit_round(word);
+        for (int q0 = 0; q0 < r.tot; q0 += 32) {
+          const int q = q0 + l;
+          const int ow = bit_owner(r, q);
+          const uint32_t om = __shfl_sync(0xffffffffu, word, ow);
+          const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
+          if (q < r.tot) {
+            const int b = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
+            const uint32_t *rb = adj + b * W;
+            for (int x = 0; x < W; ++x) t3_loc += __popc(ra[x] & rb[x]);
+          }
+        }
+      }
+    }
+    const int64_t E = cta_sum(e_loc), T3 = cta_sum(t3_loc);
+    if (threadIdx.x == 0) {
+      c.E = E;
+      c.T = c.maxdim >= 2 ? T3 / 3 : 0;
+      c.flags |= flags;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------- build
+
+template <bool F, typename TIn>
+__global__ void __launch_bounds__(BT) k_batch_build(const TIn *pts, int d, CloudDesc *desc, const int32_t *order,
+                                                    int n_clouds, int *cursor, int nmax, unsigned char *scratch,
+                                                    ScratchLayout SL, BatchOut out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const SmemLayout SM = smem_layout(nmax, d);
+  uint32_t *adj = (uint32_t *)(smem + SM.adj);
+  uint16_t *pre = (uint16_t *)(smem + SM.pre);
+  int32_t *deg = (int32_t *)(smem + SM.deg);
+  int32_t *up = (int32_t *)(smem + SM.up);
+  int32_t *nptr = (int32_t *)(smem + SM.nptr);
+  int64_t *lptr = (int64_t *)(smem + SM.lptr);
+  void *Xs = (void *)(smem + SM.X);
+  __shared__ int32_t flags;
+  __shared__ int64_t ngr;
+
+  unsigned char *base = scratch + (size_t)blockIdx.x * SL.bytes;
+  uint64_t *keys = (uint64_t *)(base + SL.keys), *tkeys = (uint64_t *)(base + SL.tkeys);
+  double *d64lex = (double *)(base + SL.d64lex), *d64 = (double *)(base + SL.d64);
+  int32_t *flag = (int32_t *)(base + SL.flag), *gex = (int32_t *)(base + SL.gex);
+  int32_t *nbr_ord = (int32_t *)(base + SL.nbr_ord), *gstart = (int32_t *)(base + SL.gstart);
+  int32_t *tcnt = (int32_t *)(base + SL.tcnt);
+  int64_t *toff = (int64_t *)(base + SL.toff);
+  uint64_t *tk = (uint64_t *)(base + SL.tk), *tk2 = (uint64_t *)(base + SL.tk2);
+  const int wid = threadIdx.x >> 5, l = lane_id();
+  const uint32_t lt = lanemask_lt();
+
+  for (int ci; (ci = next_cloud(cursor, order, n_clouds)) >= 0;) {
+    CloudDesc &c = desc[ci];
+    if (c.fallback || c.flags) continue;
+    if (threadIdx.x == 0) {
+      flags = 0;
+      ngr = 1;
+    }
+    __syncthreads();
+    const int n = c.n, W = (n + 31) / 32;
+    if constexpr (!F) cta_stage_int<TIn>(pts, c, d, (int32_t *)Xs);
+    cta_bitmap<F>(pts, c, d, Xs, adj, &flags);
+    using TX = typename std::conditional<F, float, int32_t>::type;
+    const TX *X = (const TX *)Xs;
+
+    // Row counts and prefix popcounts (u16: n <= 1024).
+    for (int i = wid; i < n; i += BWARPS) {
+      int carry = 0, upc = 0;
+      for (int w0 = 0; w0 < W; w0 += 32) {
+        const int w = w0 + l;
+        const uint32_t word = w < W ? adj[i * W + w] : 0u;
+        const int cc = __popc(word), inc = warp_incl_scan(cc);
+        if (w < W) pre[i * W + w] = (uint16_t)(carry + inc - cc);
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+        upc += __popc(word & above_mask(i, w));
+      }
+      upc = warp_sum(upc);
+      if (l == 0) {
+        deg[i] = carry;
+        up[i] = upc;
+      }
+    }
+    __syncthreads();
+    cta_scan<int32_t, int32_t>(deg, nptr, n);
+    cta_scan<int32_t, int64_t>(up, lptr, n);
+    const int64_t E = lptr[n];
+    if (E != c.E) {
+      if (threadIdx.x == 0) c.flags |= F_INTERNAL;
+      continue;
+    }
+
+    // Lexicographic edge keys (float: canonical FP64 value alongside).
+    for (int i = wid; i < n; i += BWARPS) {
+      int64_t t = lptr[i];
+      for (int w0 = (i + 1) >> 5; w0 < W; w0 += 32) {
+        const int w = w0 + l;
+        const uint32_t word = w < W ? adj[i * W + w] & above_mask(i, w) : 0u;
+        const BitChunk r = bit_round(word);
+        for (int q0 = 0; q0 < r.tot; q0 += 32) {
+          const int q = q0 + l;
+          const int ow = bit_owner(r, q);
+          const uint32_t om = __shfl_sync(0xffffffffu, word, ow);
+          const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
+          if (q < r.tot) {
+            const int j = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
+            uint64_t dk;
+            if constexpr (F) {
+              const double f = d2_canonical(X + i * d, X + j * d, d);
+              d64lex[t + q] = f;
+              dk = (uint64_t)__float_as_uint(__double2float_rn(f));
+            } else {
+              dk = d2_int(X + i * d, X + j * d, d);
+            }
+            keys[t + q] = (dk << KEY_SHIFT) | ((uint64_t)i << ID_BITS) | (uint64_t)j;
+          }
+        }
+        t += r.tot;
+      }
+    }
+    __syncthreads();
+    cta_radix_sort_global(keys, nullptr, tkeys, nullptr, E, KEY_SHIFT, c.kbits);
+
+    if constexpr (F) {
+      // Canonical values in sorted order; re-sort runs of equal fp32 keys by
+      // (FP64 value, i, j).  A run longer than RUN_MAX sends the cloud to the
+      // single-cloud path.
+      for (int64_t k = threadIdx.x; k < E; k += BT) {
+        const uint64_t key = keys[k];
+        const int i = (int)((key >> ID_BITS) & ID_MASK), j = (int)(key & ID_MASK);
+        d64[k] = d64lex[lptr[i] + rank16(adj + i * W, pre + i * W, j) - (deg[i] - up[i])];
+      }
+      __syncthreads();
+      for (int64_t k = threadIdx.x; k < E; k += BT) {
+        const uint64_t dk = keys[k] >> KEY_SHIFT;
+        if (k > 0 && (keys[k - 1] >> KEY_SHIFT) == dk) continue;  // not a run start
+        int64_t e = k + 1;
+        while (e < E && (keys[e] >> KEY_SHIFT) == dk && e - k <= RUN_MAX) ++e;
+        if (e - k > RUN_MAX) {
+          atomicOr(&flags, F_OVERFLOW);
+          continue;
+        }
+        for (int64_t x = k + 1; x < e; ++x) {
+          const uint64_t kx = keys[x];
+          const double dx = d64[x];
+          int64_t y = x - 1;
+          while (y >= k && f64_less(dx, kx, d64[y], keys[y])) {
+            keys[y + 1] = keys[y];
+            d64[y + 1] = d64[y];
+            --y;
+          }
+          keys[y + 1] = kx;
+          d64[y + 1] = dx;
+        }
+      }
+      __syncthreads();
+      if (flags & F_OVERFLOW) {
+        if (threadIdx.x == 0) c.fallback = 1;
+        continue;
+      }
+    }
+
+    // Dense-rank grades, edge outputs, grade values, neighbour CSR.
+    for (int64_t k = threadIdx.x; k < E; k += BT) {
+      int f;
+      if constexpr (F) f = k == 0 ? (d64[0] != 0.0) : (d64[k] != d64[k - 1]);
+      else f = k == 0 ? ((keys[0] >> KEY_SHIFT) != 0) : ((keys[k] >> KEY_SHIFT) != (keys[k - 1] >> KEY_SHIFT));
+      flag[k] = f;
+    }
+    __syncthreads();
+    cta_scan<int32_t, int32_t>(flag, gex, E);
+    for (int64_t k = threadIdx.x; k < E; k += BT) {
+      const uint64_t key = keys[k];
+      const int i = (int)((key >> ID_BITS) & ID_MASK), j = (int)(key & ID_MASK);
+      const int g = gex[k + 1];
+      const int64_t p = c.eo + k;
+      out.everts[2 * p] = i;
+      out.everts[2 * p + 1] = j;
+      out.erow[2 * p] = i;
+      out.erow[2 * p + 1] = j;
+      out.ecol[c.co + k] = 2 * k;
+      out.egrade[p] = g;
+      if (flag[k]) {
+        double v;
+        if constexpr (F) v = d64[k];
+        else v = (double)(key >> KEY_SHIFT);
+        out.gval[c.go + g] = v;
+        gstart[g] = (int32_t)k;
+      }
+      nbr_ord[nptr[i] + rank16(adj + i * W, pre + i * W, j)] = (int32_t)k;
+      nbr_ord[nptr[j] + rank16(adj + j * W, pre + j * W, i)] = (int32_t)k;
+      if (k == E - 1) ngr = g + 1;
+    }
+    if (threadIdx.x == 0) {
+      out.gval[c.go] = 0.0;
+      out.ecol[c.co + E] = 2 * E;
+    }
+    for (int v = threadIdx.x; v < n; v += BT) {
+      out.vverts[c.vo + v] = v;
+      out.vgrade[c.vo + v] = 0;
+    }
+    __syncthreads();
+    const int64_t ngrades = ngr;
+
+    const int64_t T = c.T;
+    if (c.maxdim >= 2) {
+      if (threadIdx.x == 0) out.tcol[c.ko + T] = 3 * T;
+      // Lex counts: triangle (a, b, c'), a < b < c', counted at its first edge.
+      for (int64_t e = wid; e < E; e += BWARPS) {
+        const int a = out.everts[2 * (c.eo + e)], b = out.everts[2 * (c.eo + e) + 1];
+        int cnt = 0;
+        for (int w = (b >> 5) + l; w < W; w += 32) cnt += __popc(adj[a * W + w] & adj[b * W + w] & above_mask(b, w));
+        cnt = warp_sum(cnt);
+        if (l == 0) tcnt[lptr[a] + rank16(adj + a * W, pre + a * W, b) - (deg[a] - up[a])] = cnt;
+      }
+      __syncthreads();
+      cta_scan<int32_t, int64_t>(tcnt, toff, E);
+      if (toff[E] != T) {
+        if (threadIdx.x == 0) c.flags |= F_INTERNAL;
+        continue;
+      }
+      // Keys grade << 39 | (a, b, c').
+      for (int64_t e = wid; e < E; e += BWARPS) {
+        const int a = out.everts[2 * (c.eo + e)], b = out.everts[2 * (c.eo + e) + 1];
+        const int32_t gab = out.egrade[c.eo + e];
+        const int32_t *oa = nbr_ord + nptr[a], *ob = nbr_ord + nptr[b];
+        int64_t t = toff[lptr[a] + rank16(adj + a * W, pre + a * W, b) - (deg[a] - up[a])];
+        for (int w0 = b >> 5; w0 < W; w0 += 32) {
+          const int w = w0 + l;
+          const uint32_t vm = w < W ? (adj[a * W + w] & adj[b * W + w] & above_mask(b, w)) : 0u;
+          const BitChunk r = bit_round(vm);
+          for (int q0 = 0; q0 < r.tot; q0 += 32) {
+            const int q = q0 + l;
+            const int ow = bit_owner(r, q);
+            const uint32_t om = __shfl_sync(0xffffffffu, vm, ow);
+            const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
+            if (q < r.tot) {
+              const int cv = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
+              const int32_t gac = out.egrade[c.eo + oa[rank16(adj + a * W, pre + a * W, cv)]];
+              const int32_t gbc = out.egrade[c.eo + ob[rank16(adj + b * W, pre + b * W, cv)]];
+              if (t + q < T) tk[t + q] = ((uint64_t)max(gab, max(gac, gbc)) << LEX_SHIFT) | lex3(a, b, cv);
+            }
+          }
+          t += r.tot;
+        }
+      }
+      __syncthreads();
+      int gbits = 1;
+      while ((1ll << gbits) < ngrades) ++gbits;
+      cta_radix_sort_global(tk, nullptr, tk2, nullptr, T, LEX_SHIFT, gbits);
+      for (int64_t p = threadIdx.x; p < T; p += BT) {
+        const uint64_t k = tk[p];
+        const int a = (int)((k >> (2 * ID_BITS)) & ID_MASK), b = (int)((k >> ID_BITS) & ID_MASK),
+                  cc = (int)(k & ID_MASK);
+        const int32_t o0 = nbr_ord[nptr[a] + rank16(adj + a * W, pre + a * W, b)];
+        const int32_t o1 = nbr_ord[nptr[a] + rank16(adj + a * W, pre + a * W, cc)];
+        const int32_t o2 = nbr_ord[nptr[b] + rank16(adj + b * W, pre + b * W, cc)];
+        const int32_t lo = min(o0, min(o1, o2)), hi = max(o0, max(o1, o2));
+        const int64_t q = c.to + p;
+        out.tverts[3 * q] = a;
+        out.tverts[3 * q + 1] = b;
+        out.tverts[3 * q + 2] = cc;
+        out.tgrade[q] = (int32_t)(k >> LEX_SHIFT);
+        out.tcol[c.ko + p] = 3 * p;
+        out.trow[3 * q] = lo;
+        out.trow[3 * q + 1] = o0 + o1 + o2 - lo - hi;
+        out.trow[3 * q + 2] = hi;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      c.ngrades = ngrades;
+      c.flags |= flags;
+    }
+    __syncthreads();
+  }
+  (void)lt;
+}
+
+}  // namespace vr
+
+// ================================================================== host
+
+struct vr_batch {
+  int32_t n_clouds = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<void *> allocs;              // arenas owned by the batch
+  std::vector<vr_complex *> views;         // one per cloud (views or owned fallbacks)
+  std::vector<vr_status> status;           // per cloud
+  int64_t total_simplices = 0;
+};
+
+namespace vr {
+
+template <typename T>
+static vr_status dalloc(std::vector<void *> &v, T **p, int64_t count, cudaStream_t s) {
+  size_t bytes = sizeof(T) * (size_t)std::max<int64_t>(count, 1);
+  cudaError_t e = cudaMallocAsync((void **)p, bytes, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA;
+  }
+  v.push_back(*p);
+  return VR_OK;
+}
+
+static void free_all(std::vector<void *> &v, cudaStream_t s) {
+  for (void *p : v) cudaFreeAsync(p, s);
+  v.clear();
+}
+
+static void thresholds_host(double r2, double crel, float *a_keep, float *a_drop) {
+  auto hi = [&](float a) { return (double)a * (1.0 + crel) + F32_ABS_SLACK; };
+  auto lo = [&](float a) { return (double)a * (1.0 - crel) - F32_ABS_SLACK; };
+  float k = (float)((r2 - F32_ABS_SLACK) / (1.0 + crel));
+  if (k < 0.f) k = 0.f;
+  while (k > 0.f && hi(k) > r2) k = std::nextafter(k, -INFINITY);
+  while (hi(std::nextafter(k, INFINITY)) <= r2) k = std::nextafter(k, INFINITY);
+  if (hi(k) > r2) k = -1.f;
+  float dr = (float)((r2 + F32_ABS_SLACK) / (1.0 - crel));
+  while (lo(dr) <= r2) dr = std::nextafter(dr, INFINITY);
+  while (dr > 0.f && lo(std::nextafter(dr, -INFINITY)) > r2) dr = std::nextafter(dr, -INFINITY);
+  *a_keep = k;
+  *a_drop = dr;
+}
+
+static int bitlen64(uint64_t v) { return v ? 64 - __builtin_clzll(v) : 0; }
+
+// Shared memory of one fused cloud: bitmap (4 B/word), u16 prefix counts,
+// per-row arrays, row pointers, points.
+static size_t fused_smem(int n, int d) { return smem_layout(n, d).bytes; }
+
+template <bool F, typename TIn>
+static vr_status run_batch(const TIn *dpts, int d, vr_dtype dtype, std::vector<CloudDesc> &hd, cudaStream_t s,
+                           vr_batch *b) {
+  const int nc = (int)hd.size();
+  int nmax = 1;
+  for (auto &c : hd)
+    if (!c.fallback) nmax = std::max(nmax, c.n);
+  const int Wmax = (nmax + 31) / 32;
+  std::vector<int32_t> order(nc);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hd[x].n > hd[y].n; });
+
+  std::vector<void *> ws;
+  CloudDesc *dd;
+  int32_t *dorder;
+  int *cursor;
+  VR_TRY(dalloc(ws, &dd, nc, s));
+  VR_TRY(dalloc(ws, &dorder, nc, s));
+  VR_TRY(dalloc(ws, &cursor, 2, s));
+  VR_CUDA(cudaMemcpyAsync(dd, hd.data(), sizeof(CloudDesc) * nc, cudaMemcpyHostToDevice, s));
+  VR_CUDA(cudaMemcpyAsync(dorder, order.data(), sizeof(int32_t) * nc, cudaMemcpyHostToDevice, s));
+  VR_CUDA(cudaMemsetAsync(cursor, 0, 2 * sizeof(int), s));
+
+  int dev = 0, nsm = 0;
+  VR_CUDA(cudaGetDevice(&dev));
+  VR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const size_t xbytes = (size_t)nmax * d * 4;
+  Prof prof(s);
+  // ---- sizing
+  {
+    const size_t smem = al16((size_t)nmax * Wmax * 4) + al16(xbytes);
+    VR_CUDA(cudaFuncSetAttribute(k_batch_size<F, TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per = 0;
+    VR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_size<F, TIn>, BT, smem));
+    const int grid = std::max(1, std::min(nc, nsm * std::max(per, 1)));
+    prof.begin("batch_size");
+    k_batch_size<F, TIn><<<grid, BT, smem, s>>>(dpts, d, dd, dorder, nc, cursor, nmax);
+    count_launch();
+    VR_CUDA(cudaGetLastError());
+    prof.end();
+  }
+  VR_CUDA(cudaMemcpyAsync(hd.data(), dd, sizeof(CloudDesc) * nc, cudaMemcpyDeviceToHost, s));
+  VR_CUDA(cudaStreamSynchronize(s));
+
+  // ---- exact arenas
+  int64_t Etot = 0, Ttot = 0, Vtot = 0, Gtot = 0, Ctot = 0, Ktot = 0, Emax = 0, Tmax = 0;
+  for (auto &c : hd) {
+    if (c.fallback || c.flags) continue;
+    c.eo = Etot;
+    c.to = Ttot;
+    c.vo = Vtot;
+    c.go = Gtot;
+    c.co = Ctot;
+    c.ko = Ktot;
+    Etot += c.E;
+    Ttot += c.T;
+    Vtot += c.n;
+    Gtot += c.E + 1;
+    Ctot += c.E + 1;
+    Ktot += c.maxdim >= 2 ? c.T + 1 : 0;
+    Emax = std::max(Emax, c.E);
+    Tmax = std::max(Tmax, c.T);
+  }
+  BatchOut o{};
+  VR_TRY(dalloc(b->allocs, &o.everts, 2 * Etot, s));
+  VR_TRY(dalloc(b->allocs, &o.egrade, Etot, s));
+  VR_TRY(dalloc(b->allocs, &o.erow, 2 * Etot, s));
+  VR_TRY(dalloc(b->allocs, &o.ecol, Ctot, s));
+  VR_TRY(dalloc(b->allocs, &o.tverts, 3 * Ttot, s));
+  VR_TRY(dalloc(b->allocs, &o.tgrade, Ttot, s));
+  VR_TRY(dalloc(b->allocs, &o.trow, 3 * Ttot, s));
+  VR_TRY(dalloc(b->allocs, &o.tcol, Ktot, s));
+  VR_TRY(dalloc(b->allocs, &o.vverts, Vtot, s));
+  VR_TRY(dalloc(b->allocs, &o.vgrade, Vtot, s));
+  VR_TRY(dalloc(b->allocs, &o.gval, Gtot, s));
+
+  const ScratchLayout SL = scratch_layout(Emax, Tmax, F);
+  const size_t smem = fused_smem(nmax, d);
+  VR_CUDA(cudaFuncSetAttribute(k_batch_build<F, TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per = 0;
+  VR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_build<F, TIn>, BT, smem));
+  const int grid = std::max(1, std::min(nc, nsm * std::max(per, 1)));
+  unsigned char *scratch;
+  VR_TRY(dalloc(ws, &scratch, (int64_t)grid * SL.bytes, s));
+  VR_CUDA(cudaMemcpyAsync(dd, hd.data(), sizeof(CloudDesc) * nc, cudaMemcpyHostToDevice, s));
+  prof.begin("batch_build");
+  k_batch_build<F, TIn><<<grid, BT, smem, s>>>(dpts, d, dd, dorder, nc, cursor + 1, nmax, scratch, SL, o);
+  count_launch();
+  VR_CUDA(cudaGetLastError());
+  prof.end();
+  VR_CUDA(cudaMemcpyAsync(hd.data(), dd, sizeof(CloudDesc) * nc, cudaMemcpyDeviceToHost, s));
+  VR_CUDA(cudaStreamSynchronize(s));
+  free_all(ws, s);
+
+  // ---- per-cloud views; clouds the fused path declined go the single-cloud way
+  for (int ci = 0; ci < nc; ++ci) {
+    CloudDesc &c = hd[ci];
+    vr_complex *v = nullptr;
+    vr_status st = VR_OK;
+    if (c.flags && !(c.flags & F_OVERFLOW)) {
+      st = flags_to_status(c.flags);
+    } else if (c.fallback) {
+      v = new vr_complex();
+      v->device = dev;
+      const size_t es = dtype == VR_I8 ? 1 : 4;
+      st = build_cloud((const unsigned char *)dpts + (size_t)c.pt * d * es, c.n, d, dtype, c.maxdim, c.maxrad, s, v);
+      if (st != VR_OK) {
+        for (void *p : v->allocs) cudaFreeAsync(p, s);
+        delete v;
+        v = nullptr;
+      } else {
+        v->owned = true;
+      }
+    } else {
+      v = new vr_complex();
+      v->owned = false;
+      v->device = dev;
+      v->n = c.n;
+      v->d = d;
+      v->maxdim = c.maxdim;
+      v->stream = s;
+      v->count[0] = c.n;
+      v->count[1] = c.maxdim >= 1 ? c.E : 0;
+      v->count[2] = c.maxdim >= 2 ? c.T : 0;
+      v->verts[0] = o.vverts + c.vo;
+      v->grade[0] = o.vgrade + c.vo;
+      v->verts[1] = o.everts + 2 * c.eo;
+      v->grade[1] = o.egrade + c.eo;
+      v->colptr[1] = o.ecol + c.co;
+      v->rowidx[1] = o.erow + 2 * c.eo;
+      if (c.maxdim >= 2) {
+        v->verts[2] = o.tverts + 3 * c.to;
+        v->grade[2] = o.tgrade + c.to;
+        v->colptr[2] = o.tcol + c.ko;
+        v->rowidx[2] = o.trow + 3 * c.to;
+      }
+      v->grade_value = o.gval + c.go;
+      v->ngrades = c.ngrades;
+      v->stats.kept_edges = c.E;
+      v->stats.triangles = c.T;
+      v->stats.ngrades = c.ngrades;
+    }
+    if (v) v->in_batch = true;
+    b->views[ci] = v;
+    b->status[ci] = st;
+    if (v) b->total_simplices += v->count[0] + v->count[1] + v->count[2];
+  }
+  return VR_OK;
+}
+
+}  // namespace vr
+
+// ================================================================ C ABI
+
+using namespace vr;
+
+extern "C" {
+
+vr_status vr_build_batch(const void *points, const int64_t *offsets, int32_t n_clouds, int32_t d, vr_dtype dtype,
+                         const int32_t *maxdim, const double *maxrad, vr_stream_t stream, vr_batch **out) {
+  if (!out) { set_error("out is NULL"); return VR_ERR_ARG; }
+  *out = nullptr;
+  if (!points || !offsets) { set_error("points or offsets is NULL"); return VR_ERR_ARG; }
+  if (n_clouds < 1) { set_error("n_clouds = %d must be >= 1", n_clouds); return VR_ERR_ARG; }
+  if (d < 1) { set_error("d = %d must be >= 1", d); return VR_ERR_ARG; }
+  if (dtype != VR_I8 && dtype != VR_I32 && dtype != VR_F32) { set_error("unknown dtype"); return VR_ERR_ARG; }
+  if (offsets[0] != 0) { set_error("offsets[0] must be 0"); return VR_ERR_ARG; }
+  std::vector<CloudDesc> hd(n_clouds);
+  const double crel = (d + 5) * std::ldexp(1.0, -24);
+  for (int i = 0; i < n_clouds; ++i) {
+    CloudDesc &c = hd[i];
+    memset(&c, 0, sizeof(c));
+    const int64_t n = offsets[i + 1] - offsets[i];
+    if (n < 1 || n > VR_MAX_POINTS) { set_error("cloud %d has %lld points", i, (long long)n); return VR_ERR_RANGE; }
+    c.pt = offsets[i];
+    c.n = (int32_t)n;
+    c.maxdim = maxdim ? maxdim[i] : 2;
+    if (c.maxdim < 0) { set_error("cloud %d: maxdim < 0", i); return VR_ERR_ARG; }
+    if (c.maxdim > VR_MAX_DIM_SIMPLEX) { set_error("cloud %d: maxdim above 2", i); return VR_ERR_UNSUPPORTED; }
+    c.maxrad = maxrad ? maxrad[i] : INFINITY;
+    if (std::isnan(c.maxrad) || c.maxrad < 0) { set_error("cloud %d: bad maxrad", i); return VR_ERR_ARG; }
+    const double r2 = c.maxrad * c.maxrad;
+    c.keep_all = std::isinf(r2) ? 1 : 0;
+    c.r2 = r2;
+    if (dtype == VR_F32) {
+      if (!c.keep_all && r2 >= 1e38) c.keep_all = 1;
+      if (!c.keep_all) thresholds_host(r2, crel, &c.a_keep, &c.a_drop);
+      c.kbits = 31;
+    } else {
+      uint64_t bound = dtype == VR_I8 ? (uint64_t)d * 255ull * 255ull : INT_KEY_LIMIT - 1;
+      if (!c.keep_all) {
+        const double f = std::floor(r2);
+        c.r2i = f >= 18446744073709551615.0 ? ~0ull : (uint64_t)f;
+        bound = std::min(bound, c.r2i);
+      }
+      c.kbits = std::max(1, bitlen64(bound));
+    }
+    c.fallback = fused_smem(c.n, d) > FUSED_SMEM ? 1 : 0;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  vr_batch *b = new (std::nothrow) vr_batch();
+  if (!b) { set_error("host allocation failed"); return VR_ERR_OOM; }
+  b->n_clouds = n_clouds;
+  b->stream = s;
+  b->views.assign(n_clouds, nullptr);
+  b->status.assign(n_clouds, VR_OK);
+  // Input: device pointer as is; host input copied in once.
+  const size_t es = dtype == VR_I8 ? 1 : 4;
+  const size_t bytes = (size_t)offsets[n_clouds] * d * es;
+  const void *dpts = points;
+  cudaPointerAttributes pa;
+  bool on_dev = cudaPointerGetAttributes(&pa, points) == cudaSuccess &&
+                (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
+  if (!on_dev) {
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      delete b;
+      set_error("device allocation for the input copy failed");
+      return VR_ERR_OOM;
+    }
+    b->allocs.push_back(p);
+    cudaMemcpyAsync(p, points, bytes, cudaMemcpyHostToDevice, s);
+    dpts = p;
+  }
+  vr_status st;
+  if (dtype == VR_F32) st = run_batch<true, float>((const float *)dpts, d, dtype, hd, s, b);
+  else if (dtype == VR_I8) st = run_batch<false, int8_t>((const int8_t *)dpts, d, dtype, hd, s, b);
+  else st = run_batch<false, int32_t>((const int32_t *)dpts, d, dtype, hd, s, b);
+  if (st != VR_OK) {
+    vr_batch_free(b);
+    return st;
+  }
+  *out = b;
+  return VR_OK;
+}
+
+vr_status vr_batch_get(const vr_batch *b, int32_t cloud, const vr_complex **view, vr_status *cloud_status) {
+  if (!b || !view) { set_error("NULL argument"); return VR_ERR_ARG; }
+  if (cloud < 0 || cloud >= b->n_clouds) { set_error("cloud %d outside [0, %d)", cloud, b->n_clouds); return VR_ERR_ARG; }
+  *view = b->views[cloud];
+  if (cloud_status) *cloud_status = b->status[cloud];
+  return VR_OK;
+}
+
+vr_status vr_batch_info(const vr_batch *b, int32_t *n_clouds, int64_t *total_simplices, int32_t *n_failed) {
+  if (!b) { set_error("NULL batch"); return VR_ERR_ARG; }
+  if (n_clouds) *n_clouds = b->n_clouds;
+  if (total_simplices) *total_simplices = b->total_simplices;
+  if (n_failed) {
+    int32_t f = 0;
+    for (auto s : b->status) f += s != VR_OK;
+    *n_failed = f;
+  }
+  return VR_OK;
+}
+
+void vr_batch_free(vr_batch *b) {
+  if (!b) return;
+  for (vr_complex *v : b->views) {
+    if (!v) continue;
+    if (v->owned)
+      for (void *p : v->allocs) cudaFreeAsync(p, b->stream);
+    delete v;
+  }
+  free_all(b->allocs, b->stream);
+  cudaGetLastError();
+  delete b;
+}
+
+}  // extern "C"

@@ -20,7 +20,8 @@ struct vr_complex {
   int64_t ngrades = 0;
   vr_build_stats stats{};
   std::vector<void *> allocs;   // device allocations owned by this result
-  bool owned = true;            // false for views into a batch
+  bool owned = true;            // false for views into a batch's arenas
+  bool in_batch = false;        // owned by a vr_batch: vr_complex_free ignores it
 };
 
 namespace vr {

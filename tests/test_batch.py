@@ -1,0 +1,86 @@
+"""Batched builds: every cloud of a batch must equal the oracle's complex bit
+for bit (and so vr_build's), whatever the mix of sizes, dtypes, caps and
+maxdims; clouds too large for the fused path, tiny clouds and bad clouds
+included."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1809_04424_b300 as vr
+import synth
+from test_gpu_parity import assert_same
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available()
+    return t
+
+
+def concat(clouds):
+    pts = np.concatenate([c.points for c in clouds], axis=0)
+    off = np.concatenate([[0], np.cumsum([c.n for c in clouds])]).astype(np.int64)
+    return pts, off
+
+
+def check_batch(torch, clouds, on_device=True):
+    pts, off = concat(clouds)
+    src = torch.from_numpy(pts).cuda() if on_device else pts
+    b = vr.vr_build_batch(src, off, [c.maxdim for c in clouds], [c.maxrad for c in clouds])
+    for i, c in enumerate(clouds):
+        st, view = b.get(i)
+        assert st == vr.VR_OK, (i, st)
+        g = {"gv": view.grade_values()}
+        for k in range(c.maxdim + 1):
+            g[k] = view.to_host(k)
+        assert_same(g, oracle.vr_build(c.points, c.maxdim, c.maxrad), c.maxdim)
+    return b
+
+
+def test_sphere_batch_int8(torch):
+    """64 clouds of the uneven sphere workload (n in [32, 512], cap 40)."""
+    b = check_batch(torch, synth.config4(64))
+    assert b.info()["n_failed"] == 0
+
+
+def test_mixed_float_batch(torch):
+    g = synth.rng(55)
+    clouds = []
+    for k in range(40):
+        n = int(g.integers(2, 300))
+        pts = synth.gaussian_mixture(n, 16, g)
+        clouds.append(synth.Cloud(pts, int(g.integers(0, 3)), float(g.uniform(4, 9))))
+    check_batch(torch, clouds)
+
+
+def test_batch_with_fallback_and_tiny_clouds(torch):
+    g = synth.rng(66)
+    clouds = [synth.Cloud(np.zeros((1, 3), np.int8), 2, math.inf),
+              synth.Cloud(g.integers(-127, 128, size=(1300, 3)).astype(np.int8), 2, 12.0),  # single-cloud path
+              synth.Cloud(g.integers(-5, 6, size=(40, 3)).astype(np.int8), 1, math.inf),
+              synth.Cloud(np.full((30, 3), 4, np.int8), 2, math.inf)]                      # all ties
+    check_batch(torch, clouds)
+
+
+def test_batch_int32_and_host_input(torch):
+    g = synth.rng(77)
+    clouds = [synth.Cloud(g.integers(-1000, 1000, size=(int(n), 4)).astype(np.int32), 2, 700.0)
+              for n in g.integers(10, 200, size=20)]
+    check_batch(torch, clouds, on_device=False)
+
+
+def test_bad_cloud_fails_alone(torch):
+    good = synth.gaussian_mixture(50, 3, synth.rng(1))
+    bad = good.copy()
+    bad[3, 1] = np.nan
+    clouds = [synth.Cloud(good, 2, 5.0), synth.Cloud(bad, 2, 5.0), synth.Cloud(good, 1, 5.0)]
+    pts, off = concat(clouds)
+    b = vr.vr_build_batch(torch.from_numpy(pts).cuda(), off, 2, 5.0)
+    assert b.get(0)[0] == vr.VR_OK and b.get(2)[0] == vr.VR_OK
+    assert b.get(1)[0] == vr.VR_ERR_ARG and b.get(1)[1] is None
+    assert b.info()["n_failed"] == 1
