@@ -161,6 +161,80 @@ def run_reference(args):
     return 0
 
 
+def run_batch_bench(args):
+    """Batched clouds/s: all clouds of the uneven sphere workload in one
+    vr_build_batch call per step, against the per-cloud path (one vr_build per
+    cloud, plain launches, same GPU) timed on a sample of the same clouds."""
+    import ctypes
+    import torch
+    import paper_1809_04424_b300 as vr
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    clouds = synth.config4(args.n_clouds)
+    pts = np.concatenate([c.points for c in clouds], axis=0)
+    off = np.concatenate([[0], np.cumsum([c.n for c in clouds])]).astype(np.int64)
+    dev = torch.from_numpy(pts).cuda()
+    L = vr.lib()
+    W = max(args.warmup, 3)
+    for _ in range(W):
+        b = vr.vr_build_batch(dev, off, 2, 40.0)
+        tot = b.info()["total_simplices"]
+        del b
+    torch.cuda.synchronize()
+    L.vr_profile_reset()
+    L.vr_profile_enable(1)
+    launches0 = L.vr_launch_count()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            b = vr.vr_build_batch(dev, off, 2, 40.0)
+            del b
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+    L.vr_profile_enable(0)
+    launches = L.vr_launch_count() - launches0
+    phases = {}
+    for i in range(L.vr_profile_phases()):
+        nm, ms, calls, nl = ctypes.c_char_p(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        L.vr_profile_phase(i, ctypes.byref(nm), ctypes.byref(ms), ctypes.byref(calls), ctypes.byref(nl))
+        phases[nm.value.decode()] = round(ms.value / max(calls.value, 1), 4)
+    batched = args.n_clouds * args.steps / el
+    # per-cloud path on a sample
+    sample = clouds[: min(len(clouds), 256)]
+    devs = [torch.from_numpy(c.points).cuda() for c in sample]
+    for c, dp in list(zip(sample, devs))[:8]:
+        vr.vr_build(dp, 2, 40.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c, dp in zip(sample, devs):
+        x = vr.vr_build(dp, 2, 40.0)
+        del x
+    torch.cuda.synchronize()
+    per_cloud = len(sample) / (time.perf_counter() - t0)
+    # e2e: host points in, all outputs of every cloud stay on the device
+    host = torch.from_numpy(pts).pin_memory()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b = vr.vr_build_batch(host.numpy(), off, 2, 40.0)
+        del b
+    torch.cuda.synchronize()
+    e2e = args.n_clouds * args.steps / (time.perf_counter() - t0)
+    line = {"metric": "batched clouds/s", "value": batched, "unit": "clouds/s", "n_gpus": world,
+            "steps": args.steps, "warmup": W, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"{args.n_clouds} sphere clouds n~U[32,512] d=3 int8 (scale 100, noise 0.02), "
+                                   "cap 40, maxdim 2", "simplices_per_step": tot,
+                       "l2": "inputs and outputs larger than L2 per step"},
+            "simplices_per_s": tot * args.steps / el,
+            "per_cloud_path": {"value": per_cloud, "unit": "clouds/s", "sample_clouds": len(sample),
+                               "speedup_batched": batched / per_cloud},
+            "e2e": {"value": e2e, "unit": "clouds/s", "h2d_bytes_per_step": int(pts.nbytes), "d2h_bytes_per_step": 0},
+            "gpu_launches": launches, "phases_ms": phases, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -170,9 +244,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="length of the CPU-oracle baseline sample (0 skips it)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--config", default="torus", choices=sorted(WORKLOADS),
+    ap.add_argument("--config", default="torus", choices=sorted(WORKLOADS) + ["batch"],
                     help="workload (default: the headline torus cloud)")
+    ap.add_argument("--n-clouds", type=int, default=4096, help="clouds of the batch workload")
     args = ap.parse_args()
+    if args.config == "batch" and args.impl != "reference":
+        return run_batch_bench(args)
     if args.impl == "reference":
         return run_reference(args)
 
