@@ -28,7 +28,7 @@ vr_status cuda_status(cudaError_t e, const char *what, const char *file, int lin
 
 // Pool memory stays reserved between builds, so repeated calls do not go
 // back to the driver for every workspace.
-static void keep_pool_warm() {
+void keep_pool_warm() {
   static thread_local int done_dev = -1;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return; }

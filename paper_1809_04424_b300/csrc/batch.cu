@@ -771,6 +771,7 @@ vr_status vr_build_batch(const void *points, const int64_t *offsets, int32_t n_c
     }
     c.fallback = fused_smem(c.n, d) > FUSED_SMEM ? 1 : 0;
   }
+  keep_pool_warm();
   cudaStream_t s = (cudaStream_t)stream;
   vr_batch *b = new (std::nothrow) vr_batch();
   if (!b) { set_error("host allocation failed"); return VR_ERR_OOM; }
