@@ -170,6 +170,39 @@ VR_API vr_status vr_batch_info(const vr_batch *b, int32_t *n_clouds,
                                int64_t *total_simplices, int32_t *n_failed);
 VR_API void vr_batch_free(vr_batch *b);
 
+/* ---- Serving: continuous batching of requests.
+ * A server owns worker threads and CUDA streams on one device.  Requests
+ * (one cloud each) are queued by vr_serve_submit, which copies the points
+ * (host or device memory) before returning.  Waiting requests of one
+ * (dtype, d) class are formed into micro-batches while earlier ones run; a
+ * batch's clouds are admitted by their exact output size against the memory
+ * budget left by the batches in flight (the rest wait for the next batch),
+ * and up to n_streams batches overlap on the device.  Clouds too large for
+ * the batch kernels are built one at a time on a stream of their own.  Every
+ * result equals vr_build's for the same request. */
+typedef struct vr_server vr_server;
+typedef struct vr_server_opts {
+  int64_t mem_budget_bytes; /* output bytes in flight (<= 0: 8 GiB)          */
+  int32_t max_queue;        /* waiting requests before VR_ERR_BUSY (<= 0: 65536) */
+  int32_t n_streams;        /* batches in flight (<= 0: 3)                  */
+  int32_t max_batch_clouds; /* clouds per micro-batch (<= 0: 512)           */
+  int32_t device;           /* CUDA device (< 0: the current one)           */
+} vr_server_opts;
+VR_API vr_status vr_server_create(const vr_server_opts *opts, vr_server **out);
+/* Queue one request; *ticket identifies it.  VR_ERR_BUSY when the queue is
+ * full; argument errors as in vr_build. */
+VR_API vr_status vr_serve_submit(vr_server *srv, const void *points, int32_t n,
+                                 int32_t d, vr_dtype dtype, int32_t maxdim,
+                                 double maxrad, uint64_t *ticket);
+/* Wait up to timeout_us for a ticket: VR_OK with *out (owned by the caller,
+ * release with vr_complex_free), VR_ERR_TIMEOUT if not ready, or the
+ * request's own error.  A ticket is delivered once. */
+VR_API vr_status vr_serve_poll(vr_server *srv, uint64_t ticket,
+                               int64_t timeout_us, vr_complex **out);
+/* Finish the work in flight and release the server (undelivered results are
+ * freed). */
+VR_API vr_status vr_server_destroy(vr_server *srv);
+
 /* Measurement support (no counterpart in the paper's API; its Sec. 4 profiles
  * with Julia's sampling profiler).  When enabled, every build records a CUDA
  * event pair around each phase on its own stream; once the build's work is

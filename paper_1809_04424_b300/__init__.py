@@ -309,3 +309,85 @@ def vr_batch_free(handle) -> None:
     L = lib()
     _set_batch_types(L)
     L.vr_batch_free(ctypes.c_void_p(handle))
+
+
+# ---------------------------------------------------------------- serving
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_queue", ctypes.c_int32),
+                ("n_streams", ctypes.c_int32), ("max_batch_clouds", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+def _set_server_types(L):
+    if getattr(L, "_server_types", False):
+        return
+    vp = ctypes.c_void_p
+    L.vr_server_create.argtypes = [ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
+    L.vr_server_create.restype = ctypes.c_int
+    L.vr_serve_submit.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int, ctypes.c_int32,
+                                  ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]
+    L.vr_serve_submit.restype = ctypes.c_int
+    L.vr_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(vp)]
+    L.vr_serve_poll.restype = ctypes.c_int
+    L.vr_server_destroy.argtypes = [vp]
+    L.vr_server_destroy.restype = ctypes.c_int
+    L._server_types = True
+
+
+class Server:
+    """A continuous-batching request server (vr_server_*)."""
+
+    def __init__(self, mem_budget_bytes=0, max_queue=0, n_streams=0, max_batch_clouds=0, device=-1):
+        L = lib()
+        _set_server_types(L)
+        o = ServerOpts(mem_budget_bytes, max_queue, n_streams, max_batch_clouds, device)
+        h = ctypes.c_void_p()
+        _check(L.vr_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h.value
+
+    def submit(self, points: np.ndarray, maxdim: int, maxrad: float) -> int:
+        """Queue one cloud (numpy array, copied before return); returns its
+        ticket.  Raises VRError (VR_ERR_BUSY when the queue is full)."""
+        return vr_serve_submit(self.handle, points, maxdim, maxrad)
+
+    def poll(self, ticket: int, timeout_us: int = 10_000_000) -> Complex:
+        return vr_serve_poll(self.handle, ticket, timeout_us)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            vr_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vr_server_create(**kw) -> Server:
+    return Server(**kw)
+
+
+def vr_serve_submit(handle, points, maxdim, maxrad) -> int:
+    L = lib()
+    _set_server_types(L)
+    p = np.ascontiguousarray(points)
+    t = ctypes.c_uint64()
+    _check(L.vr_serve_submit(ctypes.c_void_p(handle), ctypes.c_void_p(p.ctypes.data), p.shape[0], p.shape[1],
+                             _dtype_code(p.dtype), int(maxdim), float(maxrad), ctypes.byref(t)))
+    return t.value
+
+
+def vr_serve_poll(handle, ticket, timeout_us=10_000_000) -> Complex:
+    L = lib()
+    _set_server_types(L)
+    h = ctypes.c_void_p()
+    _check(L.vr_serve_poll(ctypes.c_void_p(handle), ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(h)))
+    return Complex(h.value)
+
+
+def vr_server_destroy(handle) -> None:
+    L = lib()
+    _set_server_types(L)
+    L.vr_server_destroy(ctypes.c_void_p(handle))

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "complex.h"
+#include "jobs.h"
 #include "kernels.cuh"
 #include "prof.h"
 
@@ -522,14 +523,7 @@ __global__ void __launch_bounds__(BT) k_batch_build(const TIn *pts, int d, Cloud
 
 // ================================================================== host
 
-struct vr_batch {
-  int32_t n_clouds = 0;
-  cudaStream_t stream = nullptr;
-  std::vector<void *> allocs;              // arenas owned by the batch
-  std::vector<vr_complex *> views;         // one per cloud (views or owned fallbacks)
-  std::vector<vr_status> status;           // per cloud
-  int64_t total_simplices = 0;
-};
+#include <memory>
 
 namespace vr {
 
@@ -568,161 +562,331 @@ static void thresholds_host(double r2, double crel, float *a_keep, float *a_drop
 
 static int bitlen64(uint64_t v) { return v ? 64 - __builtin_clzll(v) : 0; }
 
-// Shared memory of one fused cloud: bitmap (4 B/word), u16 prefix counts,
-// per-row arrays, row pointers, points.
-static size_t fused_smem(int n, int d) { return smem_layout(n, d).bytes; }
+// Shared memory of one fused cloud.
+size_t fused_smem(int n, int d) { return smem_layout(n, d).bytes; }
+bool fused_fits(int n, int d) { return fused_smem(n, d) <= FUSED_SMEM; }
 
-template <bool F, typename TIn>
-static vr_status run_batch(const TIn *dpts, int d, vr_dtype dtype, std::vector<CloudDesc> &hd, cudaStream_t s,
-                           vr_batch *b) {
-  const int nc = (int)hd.size();
-  int nmax = 1;
-  for (auto &c : hd)
-    if (!c.fallback) nmax = std::max(nmax, c.n);
-  const int Wmax = (nmax + 31) / 32;
-  std::vector<int32_t> order(nc);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hd[x].n > hd[y].n; });
+// Fill a cloud descriptor from its request; false (with the error set) on a
+// bad argument.
+vr_status make_desc(CloudDesc &c, int64_t pt, int64_t n, int d, vr_dtype dtype, int maxdim, double maxrad) {
+  memset(&c, 0, sizeof(c));
+  if (n < 1 || n > VR_MAX_POINTS) { set_error("cloud with %lld points", (long long)n); return VR_ERR_RANGE; }
+  if (maxdim < 0) { set_error("maxdim < 0"); return VR_ERR_ARG; }
+  if (maxdim > VR_MAX_DIM_SIMPLEX) { set_error("maxdim above 2 is not offered"); return VR_ERR_UNSUPPORTED; }
+  if (std::isnan(maxrad) || maxrad < 0) { set_error("maxrad must be >= 0 and not NaN"); return VR_ERR_ARG; }
+  c.pt = pt;
+  c.n = (int32_t)n;
+  c.maxdim = maxdim;
+  c.maxrad = maxrad;
+  const double r2 = maxrad * maxrad;
+  c.keep_all = std::isinf(r2) ? 1 : 0;
+  c.r2 = r2;
+  if (dtype == VR_F32) {
+    if (!c.keep_all && r2 >= 1e38) c.keep_all = 1;
+    if (!c.keep_all) thresholds_host(r2, (d + 5) * std::ldexp(1.0, -24), &c.a_keep, &c.a_drop);
+    c.kbits = 31;
+  } else {
+    uint64_t bound = dtype == VR_I8 ? (uint64_t)d * 255ull * 255ull : INT_KEY_LIMIT - 1;
+    if (!c.keep_all) {
+      const double f = std::floor(r2);
+      c.r2i = f >= 18446744073709551615.0 ? ~0ull : (uint64_t)f;
+      bound = std::min(bound, c.r2i);
+    }
+    c.kbits = std::max(1, bitlen64(bound));
+  }
+  c.fallback = fused_fits(c.n, d) ? 0 : 1;
+  return VR_OK;
+}
 
+// Output arenas of one batch, shared by the per-cloud results through
+// reference counting; released (stream-ordered on `stream`) with the last.
+struct Arenas {
+  std::vector<void *> ptrs;
+  cudaStream_t stream = nullptr;
+  ~Arenas() {
+    for (void *p : ptrs) cudaFreeAsync(p, stream);
+    cudaGetLastError();
+  }
+};
+
+// Bytes of output a fused cloud writes.
+int64_t cloud_out_bytes(const CloudDesc &c) {
+  return c.E * (8 + 4 + 8 + 8 + 8) + c.T * (12 + 4 + 12 + 8) + c.n * 8 + 16;
+}
+
+// One batch in three asynchronous steps, each ending with an event:
+// size -> build (with memory admission) -> finish.
+struct BatchJob {
+  cudaStream_t s = nullptr;
+  int d = 0;
+  vr_dtype dtype = VR_I8;
+  const void *dpts = nullptr;
+  std::vector<CloudDesc> hd;
+  CloudDesc *hpin = nullptr;   // optional pinned mirror of hd (async copies)
   std::vector<void *> ws;
-  CloudDesc *dd;
-  int32_t *dorder;
-  int *cursor;
-  VR_TRY(dalloc(ws, &dd, nc, s));
-  VR_TRY(dalloc(ws, &dorder, nc, s));
-  VR_TRY(dalloc(ws, &cursor, 2, s));
-  VR_CUDA(cudaMemcpyAsync(dd, hd.data(), sizeof(CloudDesc) * nc, cudaMemcpyHostToDevice, s));
-  VR_CUDA(cudaMemcpyAsync(dorder, order.data(), sizeof(int32_t) * nc, cudaMemcpyHostToDevice, s));
-  VR_CUDA(cudaMemsetAsync(cursor, 0, 2 * sizeof(int), s));
+  CloudDesc *dd = nullptr;
+  int32_t *dorder = nullptr;
+  int *cursor = nullptr;
+  std::shared_ptr<Arenas> ar;
+  BatchOut o{};
+  int64_t out_bytes = 0;       // admitted output bytes
+  cudaEvent_t ev = nullptr;
+  int dev = 0;
 
-  int dev = 0, nsm = 0;
-  VR_CUDA(cudaGetDevice(&dev));
-  VR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const size_t xbytes = (size_t)nmax * d * 4;
-  Prof prof(s);
-  // ---- sizing
-  {
-    const size_t smem = al16((size_t)nmax * Wmax * 4) + al16(xbytes);
+  ~BatchJob() {
+    free_all(ws, s);
+    if (ev) cudaEventDestroy(ev);
+  }
+  CloudDesc *host_descs() { return hpin ? hpin : hd.data(); }
+
+  template <bool F, typename TIn>
+  vr_status launch_size() {
+    const int nc = (int)hd.size();
+    int nmax = 1;
+    for (auto &c : hd)
+      if (!c.fallback) nmax = std::max(nmax, c.n);
+    const int Wmax = (nmax + 31) / 32;
+    std::vector<int32_t> order(nc);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hd[x].n > hd[y].n; });
+    VR_TRY(dalloc(ws, &dd, nc, s));
+    VR_TRY(dalloc(ws, &dorder, nc, s));
+    VR_TRY(dalloc(ws, &cursor, 2, s));
+    if (hpin) memcpy(hpin, hd.data(), sizeof(CloudDesc) * nc);
+    VR_CUDA(cudaMemcpyAsync(dd, host_descs(), sizeof(CloudDesc) * nc, cudaMemcpyHostToDevice, s));
+    VR_CUDA(cudaMemcpyAsync(dorder, order.data(), sizeof(int32_t) * nc, cudaMemcpyHostToDevice, s));
+    VR_CUDA(cudaMemsetAsync(cursor, 0, 2 * sizeof(int), s));
+    int nsm = 0;
+    VR_CUDA(cudaGetDevice(&dev));
+    VR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const size_t smem = al16((size_t)nmax * Wmax * 4) + al16((size_t)nmax * d * 4);
     VR_CUDA(cudaFuncSetAttribute(k_batch_size<F, TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per = 0;
     VR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_size<F, TIn>, BT, smem));
     const int grid = std::max(1, std::min(nc, nsm * std::max(per, 1)));
-    prof.begin("batch_size");
-    k_batch_size<F, TIn><<<grid, BT, smem, s>>>(dpts, d, dd, dorder, nc, cursor, nmax);
+    k_batch_size<F, TIn><<<grid, BT, smem, s>>>((const TIn *)dpts, d, dd, dorder, nc, cursor, nmax);
     count_launch();
     VR_CUDA(cudaGetLastError());
-    prof.end();
+    VR_CUDA(cudaMemcpyAsync(host_descs(), dd, sizeof(CloudDesc) * nc, cudaMemcpyDeviceToHost, s));
+    if (!ev) VR_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    VR_CUDA(cudaEventRecord(ev, s));
+    return VR_OK;
   }
-  VR_CUDA(cudaMemcpyAsync(hd.data(), dd, sizeof(CloudDesc) * nc, cudaMemcpyDeviceToHost, s));
-  VR_CUDA(cudaStreamSynchronize(s));
 
-  // ---- exact arenas
-  int64_t Etot = 0, Ttot = 0, Vtot = 0, Gtot = 0, Ctot = 0, Ktot = 0, Emax = 0, Tmax = 0;
-  for (auto &c : hd) {
-    if (c.fallback || c.flags) continue;
-    c.eo = Etot;
-    c.to = Ttot;
-    c.vo = Vtot;
-    c.go = Gtot;
-    c.co = Ctot;
-    c.ko = Ktot;
-    Etot += c.E;
-    Ttot += c.T;
-    Vtot += c.n;
-    Gtot += c.E + 1;
-    Ctot += c.E + 1;
-    Ktot += c.maxdim >= 2 ? c.T + 1 : 0;
-    Emax = std::max(Emax, c.E);
-    Tmax = std::max(Tmax, c.T);
-  }
-  BatchOut o{};
-  VR_TRY(dalloc(b->allocs, &o.everts, 2 * Etot, s));
-  VR_TRY(dalloc(b->allocs, &o.egrade, Etot, s));
-  VR_TRY(dalloc(b->allocs, &o.erow, 2 * Etot, s));
-  VR_TRY(dalloc(b->allocs, &o.ecol, Ctot, s));
-  VR_TRY(dalloc(b->allocs, &o.tverts, 3 * Ttot, s));
-  VR_TRY(dalloc(b->allocs, &o.tgrade, Ttot, s));
-  VR_TRY(dalloc(b->allocs, &o.trow, 3 * Ttot, s));
-  VR_TRY(dalloc(b->allocs, &o.tcol, Ktot, s));
-  VR_TRY(dalloc(b->allocs, &o.vverts, Vtot, s));
-  VR_TRY(dalloc(b->allocs, &o.vgrade, Vtot, s));
-  VR_TRY(dalloc(b->allocs, &o.gval, Gtot, s));
-
-  const ScratchLayout SL = scratch_layout(Emax, Tmax, F);
-  const size_t smem = fused_smem(nmax, d);
-  VR_CUDA(cudaFuncSetAttribute(k_batch_build<F, TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per = 0;
-  VR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_build<F, TIn>, BT, smem));
-  const int grid = std::max(1, std::min(nc, nsm * std::max(per, 1)));
-  unsigned char *scratch;
-  VR_TRY(dalloc(ws, &scratch, (int64_t)grid * SL.bytes, s));
-  VR_CUDA(cudaMemcpyAsync(dd, hd.data(), sizeof(CloudDesc) * nc, cudaMemcpyHostToDevice, s));
-  prof.begin("batch_build");
-  k_batch_build<F, TIn><<<grid, BT, smem, s>>>(dpts, d, dd, dorder, nc, cursor + 1, nmax, scratch, SL, o);
-  count_launch();
-  VR_CUDA(cudaGetLastError());
-  prof.end();
-  VR_CUDA(cudaMemcpyAsync(hd.data(), dd, sizeof(CloudDesc) * nc, cudaMemcpyDeviceToHost, s));
-  VR_CUDA(cudaStreamSynchronize(s));
-  free_all(ws, s);
-
-  // ---- per-cloud views; clouds the fused path declined go the single-cloud way
-  for (int ci = 0; ci < nc; ++ci) {
-    CloudDesc &c = hd[ci];
-    vr_complex *v = nullptr;
-    vr_status st = VR_OK;
-    if (c.flags && !(c.flags & F_OVERFLOW)) {
-      st = flags_to_status(c.flags);
-    } else if (c.fallback) {
-      v = new vr_complex();
-      v->device = dev;
-      const size_t es = dtype == VR_I8 ? 1 : 4;
-      st = build_cloud((const unsigned char *)dpts + (size_t)c.pt * d * es, c.n, d, dtype, c.maxdim, c.maxrad, s, v);
-      if (st != VR_OK) {
-        for (void *p : v->allocs) cudaFreeAsync(p, s);
-        delete v;
-        v = nullptr;
-      } else {
-        v->owned = true;
+  // After the sizing event.  Admits clouds in order while their output fits
+  // `budget` bytes (the first cloud always fits); the others are marked
+  // deferred (fallback = 2) and returned in `deferred`.
+  template <bool F, typename TIn>
+  vr_status launch_build(int64_t budget, std::vector<int> *deferred) {
+    const int nc = (int)hd.size();
+    if (hpin) memcpy(hd.data(), hpin, sizeof(CloudDesc) * nc);
+    int64_t Etot = 0, Ttot = 0, Vtot = 0, Gtot = 0, Ctot = 0, Ktot = 0, Emax = 0, Tmax = 0;
+    int nmax = 1;
+    bool any = false;
+    for (int ci = 0; ci < nc; ++ci) {
+      CloudDesc &c = hd[ci];
+      if (c.fallback || c.flags) continue;
+      const int64_t ob = cloud_out_bytes(c);
+      if (deferred && any && out_bytes + ob > budget) {
+        c.fallback = 2;
+        deferred->push_back(ci);
+        continue;
       }
-    } else {
-      v = new vr_complex();
-      v->owned = false;
-      v->device = dev;
-      v->n = c.n;
-      v->d = d;
-      v->maxdim = c.maxdim;
-      v->stream = s;
-      v->count[0] = c.n;
-      v->count[1] = c.maxdim >= 1 ? c.E : 0;
-      v->count[2] = c.maxdim >= 2 ? c.T : 0;
-      v->verts[0] = o.vverts + c.vo;
-      v->grade[0] = o.vgrade + c.vo;
-      v->verts[1] = o.everts + 2 * c.eo;
-      v->grade[1] = o.egrade + c.eo;
-      v->colptr[1] = o.ecol + c.co;
-      v->rowidx[1] = o.erow + 2 * c.eo;
-      if (c.maxdim >= 2) {
-        v->verts[2] = o.tverts + 3 * c.to;
-        v->grade[2] = o.tgrade + c.to;
-        v->colptr[2] = o.tcol + c.ko;
-        v->rowidx[2] = o.trow + 3 * c.to;
-      }
-      v->grade_value = o.gval + c.go;
-      v->ngrades = c.ngrades;
-      v->stats.kept_edges = c.E;
-      v->stats.triangles = c.T;
-      v->stats.ngrades = c.ngrades;
+      any = true;
+      out_bytes += ob;
+      c.eo = Etot;
+      c.to = Ttot;
+      c.vo = Vtot;
+      c.go = Gtot;
+      c.co = Ctot;
+      c.ko = Ktot;
+      Etot += c.E;
+      Ttot += c.T;
+      Vtot += c.n;
+      Gtot += c.E + 1;
+      Ctot += c.E + 1;
+      Ktot += c.maxdim >= 2 ? c.T + 1 : 0;
+      Emax = std::max(Emax, c.E);
+      Tmax = std::max(Tmax, c.T);
+      nmax = std::max(nmax, c.n);
     }
-    if (v) v->in_batch = true;
-    b->views[ci] = v;
-    b->status[ci] = st;
-    if (v) b->total_simplices += v->count[0] + v->count[1] + v->count[2];
+    ar = std::make_shared<Arenas>();
+    ar->stream = s;
+    VR_TRY(dalloc(ar->ptrs, &o.everts, 2 * Etot, s));
+    VR_TRY(dalloc(ar->ptrs, &o.egrade, Etot, s));
+    VR_TRY(dalloc(ar->ptrs, &o.erow, 2 * Etot, s));
+    VR_TRY(dalloc(ar->ptrs, &o.ecol, Ctot, s));
+    VR_TRY(dalloc(ar->ptrs, &o.tverts, 3 * Ttot, s));
+    VR_TRY(dalloc(ar->ptrs, &o.tgrade, Ttot, s));
+    VR_TRY(dalloc(ar->ptrs, &o.trow, 3 * Ttot, s));
+    VR_TRY(dalloc(ar->ptrs, &o.tcol, Ktot, s));
+    VR_TRY(dalloc(ar->ptrs, &o.vverts, Vtot, s));
+    VR_TRY(dalloc(ar->ptrs, &o.vgrade, Vtot, s));
+    VR_TRY(dalloc(ar->ptrs, &o.gval, Gtot, s));
+    if (!any) {
+      VR_CUDA(cudaEventRecord(ev, s));
+      return VR_OK;
+    }
+    const ScratchLayout SL = scratch_layout(Emax, Tmax, F);
+    const size_t smem = fused_smem(nmax, d);
+    VR_CUDA(cudaFuncSetAttribute(k_batch_build<F, TIn>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per = 0, nsm = 0;
+    VR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    VR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_build<F, TIn>, BT, smem));
+    const int grid = std::max(1, std::min(nc, nsm * std::max(per, 1)));
+    unsigned char *scratch;
+    VR_TRY(dalloc(ws, &scratch, (int64_t)grid * SL.bytes, s));
+    if (hpin) memcpy(hpin, hd.data(), sizeof(CloudDesc) * nc);
+    VR_CUDA(cudaMemcpyAsync(dd, host_descs(), sizeof(CloudDesc) * nc, cudaMemcpyHostToDevice, s));
+    k_batch_build<F, TIn><<<grid, BT, smem, s>>>((const TIn *)dpts, d, dd, dorder, nc, cursor + 1, nmax, scratch,
+                                                 SL, o);
+    count_launch();
+    VR_CUDA(cudaGetLastError());
+    VR_CUDA(cudaMemcpyAsync(host_descs(), dd, sizeof(CloudDesc) * nc, cudaMemcpyDeviceToHost, s));
+    VR_CUDA(cudaEventRecord(ev, s));
+    return VR_OK;
   }
-  return VR_OK;
+
+  vr_status size_async() {
+    if (dtype == VR_F32) return launch_size<true, float>();
+    if (dtype == VR_I8) return launch_size<false, int8_t>();
+    return launch_size<false, int32_t>();
+  }
+  vr_status build_async(int64_t budget, std::vector<int> *deferred) {
+    if (dtype == VR_F32) return launch_build<true, float>(budget, deferred);
+    if (dtype == VR_I8) return launch_build<false, int8_t>(budget, deferred);
+    return launch_build<false, int32_t>(budget, deferred);
+  }
+
+  // After the build event: one result per cloud (views sharing the arenas;
+  // clouds the fused path declined are built by the single-cloud path here,
+  // synchronously on the job's stream).  Deferred clouds get no result.
+  void finish(std::vector<vr_complex *> &views, std::vector<vr_status> &status) {
+    const int nc = (int)hd.size();
+    if (hpin) memcpy(hd.data(), hpin, sizeof(CloudDesc) * nc);
+    views.assign(nc, nullptr);
+    status.assign(nc, VR_OK);
+    for (int ci = 0; ci < nc; ++ci) {
+      CloudDesc &c = hd[ci];
+      if (c.fallback == 2) continue;
+      vr_complex *v = nullptr;
+      vr_status st = VR_OK;
+      if (c.flags && !(c.flags & F_OVERFLOW)) {
+        st = flags_to_status(c.flags);
+      } else if (c.fallback) {
+        v = new vr_complex();
+        v->device = dev;
+        const size_t es = dtype == VR_I8 ? 1 : 4;
+        st = build_cloud((const unsigned char *)dpts + (size_t)c.pt * d * es, c.n, d, dtype, c.maxdim, c.maxrad, s, v);
+        if (st != VR_OK) {
+          for (void *p : v->allocs) cudaFreeAsync(p, s);
+          delete v;
+          v = nullptr;
+        }
+      } else {
+        v = new vr_complex();
+        v->owned = false;
+        v->arena = ar;
+        v->device = dev;
+        v->n = c.n;
+        v->d = d;
+        v->maxdim = c.maxdim;
+        v->stream = s;
+        v->count[0] = c.n;
+        v->count[1] = c.maxdim >= 1 ? c.E : 0;
+        v->count[2] = c.maxdim >= 2 ? c.T : 0;
+        v->verts[0] = o.vverts + c.vo;
+        v->grade[0] = o.vgrade + c.vo;
+        v->verts[1] = o.everts + 2 * c.eo;
+        v->grade[1] = o.egrade + c.eo;
+        v->colptr[1] = o.ecol + c.co;
+        v->rowidx[1] = o.erow + 2 * c.eo;
+        if (c.maxdim >= 2) {
+          v->verts[2] = o.tverts + 3 * c.to;
+          v->grade[2] = o.tgrade + c.to;
+          v->colptr[2] = o.tcol + c.ko;
+          v->rowidx[2] = o.trow + 3 * c.to;
+        }
+        v->grade_value = o.gval + c.go;
+        v->ngrades = c.ngrades;
+        v->stats.kept_edges = c.E;
+        v->stats.triangles = c.T;
+        v->stats.ngrades = c.ngrades;
+      }
+      views[ci] = v;
+      status[ci] = st;
+    }
+    free_all(ws, s);
+  }
+};
+
+std::unique_ptr<BatchJob> new_batch_job() { return std::unique_ptr<BatchJob>(new BatchJob()); }
+
+// ---- asynchronous job interface (jobs.h)
+struct Job {
+  BatchJob b;
+};
+
+vr_status check_cloud_args(int64_t n, int d, vr_dtype dtype, int maxdim, double maxrad) {
+  if (dtype != VR_I8 && dtype != VR_I32 && dtype != VR_F32) { set_error("unknown dtype"); return VR_ERR_ARG; }
+  if (d < 1) { set_error("d = %d must be >= 1", d); return VR_ERR_ARG; }
+  CloudDesc c;
+  return make_desc(c, 0, n, d, dtype, maxdim, maxrad);
 }
 
+Job *job_create(cudaStream_t s, const void *dpts, int d, vr_dtype dtype, const std::vector<JobCloud> &clouds,
+                vr_status *err) {
+  Job *j = new Job();
+  j->b.s = s;
+  j->b.d = d;
+  j->b.dtype = dtype;
+  j->b.dpts = dpts;
+  j->b.hd.resize(clouds.size());
+  for (size_t i = 0; i < clouds.size(); ++i) {
+    const JobCloud &c = clouds[i];
+    const vr_status st = make_desc(j->b.hd[i], c.pt, c.n, d, dtype, c.maxdim, c.maxrad);
+    if (st != VR_OK) {
+      *err = st;
+      delete j;
+      return nullptr;
+    }
+  }
+  *err = VR_OK;
+  return j;
+}
+vr_status job_size_async(Job *j) { return j->b.size_async(); }
+vr_status job_build_async(Job *j, int64_t budget, std::vector<int> *deferred) {
+  return j->b.build_async(budget, deferred);
+}
+bool job_ready(Job *j) {
+  const cudaError_t e = cudaEventQuery(j->b.ev);
+  if (e == cudaErrorNotReady) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+int64_t job_out_bytes(Job *j) { return j->b.out_bytes; }
+void job_finish(Job *j, std::vector<vr_complex *> &results, std::vector<vr_status> &status, bool detach) {
+  j->b.finish(results, status);
+  if (detach) {
+    if (j->b.ar) j->b.ar->stream = nullptr;
+    for (vr_complex *v : results)
+      if (v) v->stream = nullptr;
+  }
+}
+void job_destroy(Job *j) { delete j; }
+
 }  // namespace vr
+
+struct vr_batch {
+  int32_t n_clouds = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<void *> allocs;              // the input copy, if any
+  std::vector<vr_complex *> views;         // one per cloud
+  std::vector<vr_status> status;           // per cloud
+  int64_t total_simplices = 0;
+};
 
 // ================================================================ C ABI
 
@@ -739,53 +903,23 @@ vr_status vr_build_batch(const void *points, const int64_t *offsets, int32_t n_c
   if (d < 1) { set_error("d = %d must be >= 1", d); return VR_ERR_ARG; }
   if (dtype != VR_I8 && dtype != VR_I32 && dtype != VR_F32) { set_error("unknown dtype"); return VR_ERR_ARG; }
   if (offsets[0] != 0) { set_error("offsets[0] must be 0"); return VR_ERR_ARG; }
-  std::vector<CloudDesc> hd(n_clouds);
-  const double crel = (d + 5) * std::ldexp(1.0, -24);
-  for (int i = 0; i < n_clouds; ++i) {
-    CloudDesc &c = hd[i];
-    memset(&c, 0, sizeof(c));
-    const int64_t n = offsets[i + 1] - offsets[i];
-    if (n < 1 || n > VR_MAX_POINTS) { set_error("cloud %d has %lld points", i, (long long)n); return VR_ERR_RANGE; }
-    c.pt = offsets[i];
-    c.n = (int32_t)n;
-    c.maxdim = maxdim ? maxdim[i] : 2;
-    if (c.maxdim < 0) { set_error("cloud %d: maxdim < 0", i); return VR_ERR_ARG; }
-    if (c.maxdim > VR_MAX_DIM_SIMPLEX) { set_error("cloud %d: maxdim above 2", i); return VR_ERR_UNSUPPORTED; }
-    c.maxrad = maxrad ? maxrad[i] : INFINITY;
-    if (std::isnan(c.maxrad) || c.maxrad < 0) { set_error("cloud %d: bad maxrad", i); return VR_ERR_ARG; }
-    const double r2 = c.maxrad * c.maxrad;
-    c.keep_all = std::isinf(r2) ? 1 : 0;
-    c.r2 = r2;
-    if (dtype == VR_F32) {
-      if (!c.keep_all && r2 >= 1e38) c.keep_all = 1;
-      if (!c.keep_all) thresholds_host(r2, crel, &c.a_keep, &c.a_drop);
-      c.kbits = 31;
-    } else {
-      uint64_t bound = dtype == VR_I8 ? (uint64_t)d * 255ull * 255ull : INT_KEY_LIMIT - 1;
-      if (!c.keep_all) {
-        const double f = std::floor(r2);
-        c.r2i = f >= 18446744073709551615.0 ? ~0ull : (uint64_t)f;
-        bound = std::min(bound, c.r2i);
-      }
-      c.kbits = std::max(1, bitlen64(bound));
-    }
-    c.fallback = fused_smem(c.n, d) > FUSED_SMEM ? 1 : 0;
-  }
+  auto job = new_batch_job();
+  job->hd.resize(n_clouds);
+  for (int i = 0; i < n_clouds; ++i)
+    VR_TRY(make_desc(job->hd[i], offsets[i], offsets[i + 1] - offsets[i], d, dtype, maxdim ? maxdim[i] : 2,
+                     maxrad ? maxrad[i] : INFINITY));
   keep_pool_warm();
   cudaStream_t s = (cudaStream_t)stream;
   vr_batch *b = new (std::nothrow) vr_batch();
   if (!b) { set_error("host allocation failed"); return VR_ERR_OOM; }
   b->n_clouds = n_clouds;
   b->stream = s;
-  b->views.assign(n_clouds, nullptr);
-  b->status.assign(n_clouds, VR_OK);
-  // Input: device pointer as is; host input copied in once.
   const size_t es = dtype == VR_I8 ? 1 : 4;
   const size_t bytes = (size_t)offsets[n_clouds] * d * es;
   const void *dpts = points;
   cudaPointerAttributes pa;
-  bool on_dev = cudaPointerGetAttributes(&pa, points) == cudaSuccess &&
-                (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+  const bool on_dev = cudaPointerGetAttributes(&pa, points) == cudaSuccess &&
+                      (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
   cudaGetLastError();
   if (!on_dev) {
     void *p = nullptr;
@@ -799,14 +933,24 @@ vr_status vr_build_batch(const void *points, const int64_t *offsets, int32_t n_c
     cudaMemcpyAsync(p, points, bytes, cudaMemcpyHostToDevice, s);
     dpts = p;
   }
-  vr_status st;
-  if (dtype == VR_F32) st = run_batch<true, float>((const float *)dpts, d, dtype, hd, s, b);
-  else if (dtype == VR_I8) st = run_batch<false, int8_t>((const int8_t *)dpts, d, dtype, hd, s, b);
-  else st = run_batch<false, int32_t>((const int32_t *)dpts, d, dtype, hd, s, b);
+  job->s = s;
+  job->d = d;
+  job->dtype = dtype;
+  job->dpts = dpts;
+  vr_status st = job->size_async();
+  if (st == VR_OK && cudaStreamSynchronize(s) != cudaSuccess) st = cuda_status(cudaGetLastError(), "sync", __FILE__, __LINE__);
+  if (st == VR_OK) st = job->build_async(INT64_MAX, nullptr);
+  if (st == VR_OK && cudaStreamSynchronize(s) != cudaSuccess) st = cuda_status(cudaGetLastError(), "sync", __FILE__, __LINE__);
   if (st != VR_OK) {
     vr_batch_free(b);
     return st;
   }
+  job->finish(b->views, b->status);
+  for (vr_complex *v : b->views)
+    if (v) {
+      v->in_batch = true;
+      b->total_simplices += v->count[0] + v->count[1] + v->count[2];
+    }
   *out = b;
   return VR_OK;
 }

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <vector>
 
 #include "../../include/vr.h"
@@ -20,6 +21,7 @@ struct vr_complex {
   int64_t ngrades = 0;
   vr_build_stats stats{};
   std::vector<void *> allocs;   // device allocations owned by this result
+  std::shared_ptr<void> arena;  // shared batch arenas this result views
   bool owned = true;            // false for views into a batch's arenas
   bool in_batch = false;        // owned by a vr_batch: vr_complex_free ignores it
 };
