@@ -623,6 +623,7 @@ struct BatchJob {
   const void *dpts = nullptr;
   std::vector<CloudDesc> hd;
   CloudDesc *hpin = nullptr;   // optional pinned mirror of hd (async copies)
+  int32_t *hord = nullptr;     // optional pinned work-list order
   std::vector<void *> ws;
   CloudDesc *dd = nullptr;
   int32_t *dorder = nullptr;
@@ -649,12 +650,17 @@ struct BatchJob {
     std::vector<int32_t> order(nc);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hd[x].n > hd[y].n; });
+    int32_t *ord = order.data();
+    if (hord) {
+      memcpy(hord, order.data(), sizeof(int32_t) * nc);
+      ord = hord;
+    }
     VR_TRY(dalloc(ws, &dd, nc, s));
     VR_TRY(dalloc(ws, &dorder, nc, s));
     VR_TRY(dalloc(ws, &cursor, 2, s));
     if (hpin) memcpy(hpin, hd.data(), sizeof(CloudDesc) * nc);
     VR_CUDA(cudaMemcpyAsync(dd, host_descs(), sizeof(CloudDesc) * nc, cudaMemcpyHostToDevice, s));
-    VR_CUDA(cudaMemcpyAsync(dorder, order.data(), sizeof(int32_t) * nc, cudaMemcpyHostToDevice, s));
+    VR_CUDA(cudaMemcpyAsync(dorder, ord, sizeof(int32_t) * nc, cudaMemcpyHostToDevice, s));
     VR_CUDA(cudaMemsetAsync(cursor, 0, 2 * sizeof(int), s));
     int nsm = 0;
     VR_CUDA(cudaGetDevice(&dev));
@@ -834,9 +840,15 @@ vr_status check_cloud_args(int64_t n, int d, vr_dtype dtype, int maxdim, double 
   return make_desc(c, 0, n, d, dtype, maxdim, maxrad);
 }
 
+size_t job_pinned_bytes(size_t n_clouds) { return n_clouds * (sizeof(CloudDesc) + sizeof(int32_t)) + 64; }
+
 Job *job_create(cudaStream_t s, const void *dpts, int d, vr_dtype dtype, const std::vector<JobCloud> &clouds,
-                vr_status *err) {
+                void *pinned, vr_status *err) {
   Job *j = new Job();
+  if (pinned) {
+    j->b.hpin = (CloudDesc *)pinned;
+    j->b.hord = (int32_t *)((char *)pinned + clouds.size() * sizeof(CloudDesc));
+  }
   j->b.s = s;
   j->b.d = d;
   j->b.dtype = dtype;

@@ -18,8 +18,12 @@ struct JobCloud {
 struct Job;  // one batch: size -> build -> finish, each step ending on an event
 
 // Validate and describe the clouds; on error returns NULL with *err set.
+// `pinned` (optional, job_pinned_bytes(n) bytes of page-locked host memory
+// that outlives the job) makes every host<->device copy of the job
+// asynchronous; without it the copies of per-cloud sizes block.
 Job *job_create(cudaStream_t s, const void *dpts, int d, vr_dtype dtype, const std::vector<JobCloud> &clouds,
-                vr_status *err);
+                void *pinned, vr_status *err);
+size_t job_pinned_bytes(size_t n_clouds);
 vr_status job_size_async(Job *j);
 // Admits clouds while their exact output bytes fit `budget` (the first
 // always); the indices of the others are appended to `deferred`.

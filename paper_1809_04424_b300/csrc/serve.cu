@@ -53,6 +53,8 @@ struct Slot {
   size_t hcap = 0;
   void *dbuf = nullptr;            // device copy of the points
   size_t dcap = 0;
+  unsigned char *pdesc = nullptr;  // pinned per-cloud descriptors of the job
+  size_t pcap = 0;
   vr::Job *job = nullptr;
   int state = 0;                   // 0 idle, 1 sizing, 2 building
   std::vector<Req> members;
@@ -152,7 +154,8 @@ void launch_slot(vr_server *S, Slot &sl, std::vector<Req> &batch) {
   }
   cudaMemcpyAsync(sl.dbuf, sl.hbuf, bytes, cudaMemcpyHostToDevice, sl.s);
   vr_status st;
-  sl.job = job_create(sl.s, sl.dbuf, d, dt, jc, &st);
+  if (!grow_pinned(&sl.pdesc, &sl.pcap, job_pinned_bytes(jc.size()))) return fail_members(S, sl, VR_ERR_OOM);
+  sl.job = job_create(sl.s, sl.dbuf, d, dt, jc, sl.pdesc, &st);
   if (!sl.job) return fail_members(S, sl, st);
   st = job_size_async(sl.job);
   if (st != VR_OK) {
@@ -380,6 +383,7 @@ vr_status vr_server_destroy(vr_server *S) {
     if (sl.dbuf) cudaFreeAsync(sl.dbuf, sl.s);
     if (sl.s) cudaStreamSynchronize(sl.s);
     if (sl.hbuf) cudaFreeHost(sl.hbuf);
+    if (sl.pdesc) cudaFreeHost(sl.pdesc);
   }
   cudaDeviceSynchronize();
   for (auto &sl : S->slots)

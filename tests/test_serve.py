@@ -11,7 +11,7 @@ import paper_1809_04424_b300 as vr
 import synth
 from test_gpu_parity import assert_same
 
-pytestmark = pytest.mark.gpu
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(600)]
 
 
 @pytest.fixture(scope="module")
@@ -59,7 +59,7 @@ def test_mixed_stream_equals_alone(torch):
     srv = vr.Server(n_streams=3, max_batch_clouds=64)
     tickets = [srv.submit(c.points, c.maxdim, c.maxrad) for c in reqs]
     for c, t in zip(reqs, tickets):
-        got = result_dict(srv.poll(t, 60_000_000), c.maxdim)
+        got = result_dict(srv.poll(t, 20_000_000), c.maxdim)
         same(got, alone(torch, c), c.maxdim)
     for c in reqs[:12]:  # and the oracle, for a sample
         got = alone(torch, c)
@@ -72,7 +72,7 @@ def test_small_memory_budget_defers_but_completes(torch):
     srv = vr.Server(mem_budget_bytes=2 << 20, n_streams=2, max_batch_clouds=32)
     tickets = [srv.submit(c.points, c.maxdim, c.maxrad) for c in reqs]
     for c, t in zip(reqs, tickets):
-        same(result_dict(srv.poll(t, 60_000_000), c.maxdim), alone(torch, c), c.maxdim)
+        same(result_dict(srv.poll(t, 20_000_000), c.maxdim), alone(torch, c), c.maxdim)
     srv.close()
 
 
@@ -111,7 +111,7 @@ def test_queue_full_is_busy_and_accepted_complete():
     assert busy > 0
     ref = None
     for t in tickets:
-        r = srv.poll(t, 60_000_000).counts()[0]
+        r = srv.poll(t, 20_000_000).counts()[0]
         ref = ref or r
         assert r == ref
     srv.close()
