@@ -235,6 +235,117 @@ def run_batch_bench(args):
     return 0
 
 
+def _open_loop(submit_fn, poll_fn, reqs, arrivals, n_pollers=16):
+    """Submit request i at arrivals[i] (seconds from start) and record when
+    its result is back.  Returns (latencies in s, wall time of the run)."""
+    import threading
+    N = len(reqs)
+    tickets = [None] * N
+    ready = [threading.Event() for _ in range(N)]
+    done = [0.0] * N
+    t_start = time.perf_counter() + 0.05
+
+    def submitter():
+        for i, r in enumerate(reqs):
+            dt = t_start + arrivals[i] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = submit_fn(r)
+            ready[i].set()
+
+    def poller(k):
+        for i in range(k, N, n_pollers):
+            ready[i].wait()
+            poll_fn(tickets[i])
+            done[i] = time.perf_counter()
+
+    th = [threading.Thread(target=submitter)] + [threading.Thread(target=poller, args=(k,)) for k in range(n_pollers)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    lat = np.array([done[i] - (t_start + arrivals[i]) for i in range(N)])
+    return lat, max(done) - t_start
+
+
+def run_serve_bench(args):
+    """Serving: a Poisson stream of mixed requests (n log-uniform in
+    [50, 5000]; half int8 d=3 torus/sphere, half float32 d=16 mixtures;
+    maxdim in {1, 2}; per-request cap) through the continuous-batching server
+    at 0.8x its measured capacity: p50/p99 latency and clouds/s, against the
+    per-cloud path (one vr_build per request, FIFO) on the same arrivals."""
+    import torch
+    import paper_1809_04424_b300 as vr
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    N = args.n_requests
+    _, reqs = synth.config5(N)
+    srv = vr.Server(n_streams=3, max_batch_clouds=256, n_large_workers=4)
+    submit = lambda r: srv.submit(r.points, r.maxdim, r.maxrad)
+    poll = lambda t: srv.poll(t, 120_000_000)
+    for r in reqs[:64]:  # warm-up
+        poll(submit(r))
+    # capacity, closed loop
+    C = min(N, 4000)
+    t0 = time.perf_counter()
+    ts = [submit(r) for r in reqs[:C]]
+    for t in ts:
+        poll(t)
+    cap = C / (time.perf_counter() - t0)
+    lam = 0.8 * cap
+    g = synth.rng(1809 + 50)
+    arrivals = np.cumsum(g.exponential(1.0 / lam, size=N))
+    with Clocks(local) as clk:
+        lat, wall = _open_loop(submit, poll, reqs, arrivals)
+    sweep = {}
+    for f in (0.5, 1.0):
+        M = min(N, 4000)
+        a = np.cumsum(synth.rng(1809 + 51).exponential(1.0 / (f * cap), size=M))
+        l2, w2 = _open_loop(submit, poll, reqs[:M], a)
+        sweep[str(f)] = {"p50_ms": 1e3 * float(np.percentile(l2, 50)), "p99_ms": 1e3 * float(np.percentile(l2, 99)),
+                         "clouds_per_s": M / w2}
+    srv.close()
+    # per-cloud path: one vr_build per request in arrival order, one worker
+    M = min(N, 2000)
+    devq = []
+    import threading
+    lock = threading.Lock()
+
+    def per_submit(r):
+        return r
+
+    results = {}
+
+    def per_poll(r):
+        with lock:  # a single FIFO worker: plain launches, one cloud at a time
+            x = vr.vr_build(r.points, r.maxdim, r.maxrad)
+            del x
+    t0 = time.perf_counter()
+    for r in reqs[:200]:
+        per_poll(r)
+    per_cap = 200 / (time.perf_counter() - t0)
+    a = np.cumsum(synth.rng(1809 + 52).exponential(1.0 / lam, size=M))
+    lp, wp = _open_loop(per_submit, per_poll, reqs[:M], a, n_pollers=1)
+    line = {"metric": "served clouds/s", "value": N / wall, "unit": "clouds/s", "n_gpus": world, "steps": N,
+            "warmup": 64, "ms_per_step": 1e3 * wall / N, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "mixed int64/f64", "data": "synthetic",
+            "config": {"workload": f"Poisson stream of {N} requests, n log-uniform [50,5000], half int8 d=3 "
+                                   "torus/sphere, half f32 d=16 Gaussian mixtures, maxdim {1,2}, per-request cap",
+                       "arrival_rate_per_s": lam, "capacity_closed_loop": cap},
+            "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99)),
+                           "mean": 1e3 * float(lat.mean())},
+            "rate_sweep": sweep,
+            "per_cloud_path": {"capacity_clouds_per_s": per_cap, "requests": M,
+                               "p50_ms": 1e3 * float(np.percentile(lp, 50)),
+                               "p99_ms": 1e3 * float(np.percentile(lp, 99)), "clouds_per_s": M / wp},
+            "e2e": {"value": N / wall, "unit": "clouds/s", "h2d_bytes_per_step": int(np.mean([r.points.nbytes for r in reqs])),
+                    "d2h_bytes_per_step": 0},
+            "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -244,12 +355,15 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="length of the CPU-oracle baseline sample (0 skips it)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--config", default="torus", choices=sorted(WORKLOADS) + ["batch"],
+    ap.add_argument("--config", default="torus", choices=sorted(WORKLOADS) + ["batch", "serve"],
                     help="workload (default: the headline torus cloud)")
     ap.add_argument("--n-clouds", type=int, default=4096, help="clouds of the batch workload")
+    ap.add_argument("--n-requests", type=int, default=20000, help="requests of the serving workload")
     args = ap.parse_args()
     if args.config == "batch" and args.impl != "reference":
         return run_batch_bench(args)
+    if args.config == "serve" and args.impl != "reference":
+        return run_serve_bench(args)
     if args.impl == "reference":
         return run_reference(args)
 

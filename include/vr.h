@@ -178,7 +178,8 @@ VR_API void vr_batch_free(vr_batch *b);
  * batch's clouds are admitted by their exact output size against the memory
  * budget left by the batches in flight (the rest wait for the next batch),
  * and up to n_streams batches overlap on the device.  Clouds too large for
- * the batch kernels are built one at a time on a stream of their own.  Every
+ * the batch kernels are built by n_large_workers threads, each on a stream
+ * of its own.  Every
  * result equals vr_build's for the same request. */
 typedef struct vr_server vr_server;
 typedef struct vr_server_opts {
@@ -187,6 +188,7 @@ typedef struct vr_server_opts {
   int32_t n_streams;        /* batches in flight (<= 0: 3)                  */
   int32_t max_batch_clouds; /* clouds per micro-batch (<= 0: 512)           */
   int32_t device;           /* CUDA device (< 0: the current one)           */
+  int32_t n_large_workers;  /* threads for clouds too large to batch (<= 0: 4) */
 } vr_server_opts;
 VR_API vr_status vr_server_create(const vr_server_opts *opts, vr_server **out);
 /* Queue one request; *ticket identifies it.  VR_ERR_BUSY when the queue is

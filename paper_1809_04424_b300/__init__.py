@@ -315,7 +315,8 @@ def vr_batch_free(handle) -> None:
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_queue", ctypes.c_int32),
-                ("n_streams", ctypes.c_int32), ("max_batch_clouds", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("n_streams", ctypes.c_int32), ("max_batch_clouds", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("n_large_workers", ctypes.c_int32)]
 
 
 def _set_server_types(L):
@@ -337,10 +338,11 @@ def _set_server_types(L):
 class Server:
     """A continuous-batching request server (vr_server_*)."""
 
-    def __init__(self, mem_budget_bytes=0, max_queue=0, n_streams=0, max_batch_clouds=0, device=-1):
+    def __init__(self, mem_budget_bytes=0, max_queue=0, n_streams=0, max_batch_clouds=0, device=-1,
+                 n_large_workers=0):
         L = lib()
         _set_server_types(L)
-        o = ServerOpts(mem_budget_bytes, max_queue, n_streams, max_batch_clouds, device)
+        o = ServerOpts(mem_budget_bytes, max_queue, n_streams, max_batch_clouds, device, n_large_workers)
         h = ctypes.c_void_p()
         _check(L.vr_server_create(ctypes.byref(o), ctypes.byref(h)))
         self.handle = h.value

@@ -12,8 +12,8 @@
 //     launches the build; when that completes it hands each request its own
 //     result.  Requests that arrive while batches run join the next batch,
 //     so their work overlaps on the device with the batches in flight.
-//   * the large-cloud worker builds requests too large for the batch kernels
-//     one by one through vr_build on its own stream.
+//   * n_large_workers threads build requests too large for the batch kernels
+//     through vr_build, each on a stream of its own, so they overlap too.
 // Results are vr_complex objects owned by the caller after poll (free with
 // vr_complex_free); a batch's shared output arenas are released with the last
 // of its results.
@@ -75,8 +75,9 @@ struct vr_server {
   int64_t queued = 0;
   bool stop = false;
   std::vector<Slot> slots;
-  cudaStream_t big_stream = nullptr;
-  std::thread batch_thr, big_thr;
+  std::vector<cudaStream_t> big_streams;
+  std::thread batch_thr;
+  std::vector<std::thread> big_thr;
 };
 
 namespace {
@@ -241,8 +242,9 @@ void batch_worker(vr_server *S) {
   }
 }
 
-void big_worker(vr_server *S) {
+void big_worker(vr_server *S, int k) {
   cudaSetDevice(S->device);
+  cudaStream_t bs = S->big_streams[k];
   for (;;) {
     Req r;
     {
@@ -254,9 +256,9 @@ void big_worker(vr_server *S) {
       --S->queued;
     }
     vr_complex *c = nullptr;
-    const vr_status st = vr_build(r.pts.data(), r.n, r.d, r.dtype, r.maxdim, r.maxrad, S->big_stream, &c);
+    const vr_status st = vr_build(r.pts.data(), r.n, r.d, r.dtype, r.maxdim, r.maxrad, bs, &c);
     if (c) {  // outlive the server's stream: later copies and frees use the legacy stream
-      cudaStreamSynchronize(S->big_stream);
+      cudaStreamSynchronize(bs);
       c->stream = nullptr;
     }
     deliver(S, r.ticket, st, c);
@@ -277,12 +279,14 @@ vr_status vr_server_create(const vr_server_opts *opts, vr_server **out) {
   o.max_queue = 65536;
   o.n_streams = 3;
   o.max_batch_clouds = 512;
+  o.n_large_workers = 4;
   o.device = -1;
   if (opts) {
     if (opts->mem_budget_bytes > 0) o.mem_budget_bytes = opts->mem_budget_bytes;
     if (opts->max_queue > 0) o.max_queue = opts->max_queue;
     if (opts->n_streams > 0) o.n_streams = opts->n_streams;
     if (opts->max_batch_clouds > 0) o.max_batch_clouds = opts->max_batch_clouds;
+    if (opts->n_large_workers > 0) o.n_large_workers = opts->n_large_workers;
     o.device = opts->device;
   }
   S->opts = o;
@@ -299,12 +303,14 @@ vr_status vr_server_create(const vr_server_opts *opts, vr_server **out) {
       delete S;
       return cuda_status(cudaGetLastError(), "cudaStreamCreate", __FILE__, __LINE__);
     }
-  if (cudaStreamCreateWithFlags(&S->big_stream, cudaStreamNonBlocking) != cudaSuccess) {
-    delete S;
-    return cuda_status(cudaGetLastError(), "cudaStreamCreate", __FILE__, __LINE__);
-  }
+  S->big_streams.resize(o.n_large_workers);
+  for (auto &bs : S->big_streams)
+    if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) {
+      delete S;
+      return cuda_status(cudaGetLastError(), "cudaStreamCreate", __FILE__, __LINE__);
+    }
   S->batch_thr = std::thread(batch_worker, S);
-  S->big_thr = std::thread(big_worker, S);
+  for (int k = 0; k < o.n_large_workers; ++k) S->big_thr.emplace_back(big_worker, S, k);
   *out = S;
   return VR_OK;
 }
@@ -375,7 +381,8 @@ vr_status vr_server_destroy(vr_server *S) {
   S->cv_work.notify_all();
   S->cv_big.notify_all();
   if (S->batch_thr.joinable()) S->batch_thr.join();
-  if (S->big_thr.joinable()) S->big_thr.join();
+  for (auto &t : S->big_thr)
+    if (t.joinable()) t.join();
   for (auto &kv : S->done)
     if (kv.second.c) vr_complex_free(kv.second.c);
   S->done.clear();
@@ -388,7 +395,8 @@ vr_status vr_server_destroy(vr_server *S) {
   cudaDeviceSynchronize();
   for (auto &sl : S->slots)
     if (sl.s) cudaStreamDestroy(sl.s);
-  if (S->big_stream) cudaStreamDestroy(S->big_stream);
+  for (auto bs : S->big_streams)
+    if (bs) cudaStreamDestroy(bs);
   cudaGetLastError();
   delete S;
   return VR_OK;

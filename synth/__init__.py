@@ -150,7 +150,7 @@ def config5_request(g: np.random.Generator) -> Cloud:
     """One serving request: n log-uniform in [50, 5000]; half int8 d=3 (torus
     scale 30 or sphere scale 100), half float32 Gaussian mixtures at d=16;
     maxdim uniform in {1, 2}; cap at the pairwise-d^2 quantile
-    q = clamp(k/n, 0.01, 0.15) with k ~ U[20, 100] (estimated from 20000
+    q = clamp(k/n, 0.01, 0.15) with k ~ U[20, 100] (estimated from 4000
     sampled pairs)."""
     n = int(round(math.exp(g.uniform(math.log(50), math.log(5000)))))
     kind = g.integers(0, 4)
@@ -162,7 +162,7 @@ def config5_request(g: np.random.Generator) -> Cloud:
         p = gaussian_mixture(n, 16, g)
     maxdim = int(g.integers(1, 3))
     q = min(max(g.uniform(20, 100) / n, 0.01), 0.15)
-    d2 = _sampled_pair_d2(p, g, 20000)
+    d2 = _sampled_pair_d2(p, g, 4000)
     cap2 = float(np.quantile(d2, q))
     if p.dtype == np.int8:
         cap2 = float(math.floor(cap2))
