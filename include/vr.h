@@ -205,6 +205,21 @@ VR_API vr_status vr_serve_poll(vr_server *srv, uint64_t ticket,
  * freed). */
 VR_API vr_status vr_server_destroy(vr_server *srv);
 
+/* Distance tiles: 0 = automatic (tensor-core Gram tiles for int8 input and
+ * for float input with d <= 64, CUDA cores otherwise), 1 = the same, 2 = CUDA
+ * cores always.  Process-wide; results are identical either way. */
+VR_API vr_status vr_set_gram_path(int32_t mode);
+
+/* Validation of the float Gram-tile error bound (no counterpart in the
+ * paper): for device float points (n <= 8192, d <= 64) compute every pair's
+ * tensor-core value and canonical FP64 value and return the worst
+ * |d2_tc - d2_fp64| / (|y_i|^2 + |y_j|^2) observed, and the ratio beta the
+ * build's cap test assumes (pairs within beta of the cap are decided with the
+ * exact value).  Synchronous; for tests. */
+VR_API vr_status vr_gram_error_check(const float *points, int32_t n, int32_t d,
+                                     vr_stream_t stream, double *worst_ratio,
+                                     double *beta_ratio);
+
 /* Measurement support (no counterpart in the paper's API; its Sec. 4 profiles
  * with Julia's sampling profiler).  When enabled, every build records a CUDA
  * event pair around each phase on its own stream; once the build's work is

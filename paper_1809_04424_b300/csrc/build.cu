@@ -94,6 +94,10 @@ static void launch_dist(const void *X, int n, int d, int W, const Cap &cap, uint
   k_dist_bitmap<F, DR><<<grid, 256, 0, s>>>(X, n, d, W, cap, adj, st);
 }
 
+bool gram_tc_eligible(vr_dtype dtype, int d);
+vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, uint32_t *adj, DevStatus *st,
+                         cudaStream_t s, unsigned int *worst_bits);
+
 template <bool F>
 static void dist_dispatch(const void *X, int n, int d, int W, const Cap &cap, uint32_t *adj, DevStatus *st,
                           cudaStream_t s) {
@@ -158,8 +162,12 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   prof.end();
 
   prof.begin("distance");
-  dist_dispatch<F>(X, n, d, W, cap, adj, st, s);
-  count_launch();
+  if (gram_tc_eligible(dtype, d)) {
+    VR_TRY(gram_bitmap_tc(X, n, d, F, cap, adj, st, s, nullptr));  // tensor-core Gram tiles
+  } else {
+    dist_dispatch<F>(X, n, d, W, cap, adj, st, s);
+    count_launch();
+  }
   VR_CUDA(cudaGetLastError());
   prof.end();
   prof.begin("row_counts");

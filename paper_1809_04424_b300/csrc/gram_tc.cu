@@ -1,0 +1,470 @@
+// gram_tc.cu -- the kept-edge bitmap from Gram tiles on the tensor cores.
+//
+// d^2(i,j) = |y_i|^2 + |y_j|^2 - 2 <y_i, y_j>, y = x - c (c a common centre:
+// distances do not change).  One CTA per 128x128 tile of the pair matrix
+// (upper triangle of tiles): TMA brings the two 128-row operand tiles (bf16,
+// 64 coordinates, 128-byte swizzle) into shared memory, one thread issues
+// tcgen05.mma (kind::f16, bf16 x bf16 -> fp32 accumulator in TMEM), and four
+// warps read the accumulator back with tcgen05.ld, one pair row per thread.
+//
+// int8 inputs: coordinates are exact in bf16, their products exact in fp32
+// and every partial sum stays below 2^24, so the squared distances are
+// exact integers and the cap test is exact.
+// float inputs: y is split as hi + lo (two bf16 values, ~16 significant
+// bits) and the Gram is hi.hi + hi.lo + lo.hi (three MMAs into one
+// accumulator).  The computed d^2 is within beta = 4e-4 (|y_i|^2 + |y_j|^2) of
+// the canonical FP64 value (bound below); pairs whose value is within beta of
+// the cap get the exact canonical value (integer emulation of the FP64
+// sequence), so the bitmap is exact.
+//
+// Bound, per pair, with S = |y_i| + |y_j|, eta = 1.01 * 2^-16 (split plus
+// centring error per coordinate, relative): representation 2 eta S^2; dropped
+// lo.lo term 2 * 2^-16 S^2/4; fp32 accumulation of 3K = 192 products, taken as
+// 192 * 2^-22 per term (truncating adders allowed) * S^2/4 * 1.1 * 2; norms
+// K * 2^-24 S^2; final subtraction 3 * 2^-23 S^2 -- in all below 7e-5 S^2 <=
+// 1.4e-4 (|y_i|^2 + |y_j|^2), so beta has more than 2x margin; a test measures
+// the observed error against beta on adversarial inputs.
+//
+// Every wait (TMA and MMA completion) is bounded; on a timeout the kernel
+// raises F_TIMEOUT, releases its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "complex.h"
+#include "kernels.cuh"
+#include "prof.h"
+
+namespace vr {
+
+constexpr int TC_TILE = 128;        // rows (and columns) of a pair tile
+constexpr int TC_K = 64;            // coordinates per operand row (padded)
+constexpr int TC_ROW_BYTES = TC_K * 2;
+constexpr int TC_OPERAND_BYTES = TC_TILE * TC_ROW_BYTES;  // 16 KB
+constexpr uint32_t TC_TMEM_COLS = 128;
+constexpr long TC_WAIT_LIMIT = 1l << 22;
+constexpr float TC_BETA = 4e-4f;
+
+// ------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long it = 0; it < TC_WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major bf16 tile written by TMA with
+// 128-byte swizzle: start address, leading offset (unused with this swizzle,
+// 16 B), stride offset 1024 B (8 rows of 128 B), descriptor version 1,
+// layout type 2 (128-byte swizzle).
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3fff);
+  d |= (uint64_t)1 << 16;                 // leading byte offset 16 B (>> 4)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // version
+  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D fp32, A and B bf16, both K-major, N = 128, M = 128.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_TILE >> 3) << 17) |
+                              ((uint32_t)(TC_TILE >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// ----------------------------------------------------------------- kernels
+
+// Operand preparation: y = x - c, hi = bf16(y), lo = bf16(y - hi) (float), or
+// hi = x exactly (int8); rows padded to 64 coordinates and to whole tiles.
+// norm = |hi + lo|^2 in fp32 (fma in coordinate order).
+template <bool F>
+__global__ void k_gram_prep(const void *Xv, int n, int d, int npad, const float *centre, __nv_bfloat16 *Xh,
+                            __nv_bfloat16 *Xl, float *norm) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int k = 0; k < TC_K; ++k) {
+      float hi = 0.f, lo = 0.f;
+      if (i < n && k < d) {
+        if constexpr (F) {
+          const float y = __fsub_rn(((const float *)Xv)[(int64_t)i * d + k], centre[k]);
+          const __nv_bfloat16 h = __float2bfloat16_rn(y);
+          hi = __bfloat162float(h);
+          lo = __bfloat162float(__float2bfloat16_rn(__fsub_rn(y, hi)));
+        } else {
+          hi = (float)((const int32_t *)Xv)[(int64_t)i * d + k];
+        }
+      }
+      Xh[(int64_t)i * TC_K + k] = __float2bfloat16_rn(hi);
+      if constexpr (F) Xl[(int64_t)i * TC_K + k] = __float2bfloat16_rn(lo);
+      const float xt = hi + lo;
+      acc = __fmaf_rn(xt, xt, acc);
+    }
+    norm[i] = acc;
+  }
+}
+
+// Centre = mean of the points (fp32, one CTA per coordinate chunk; the exact
+// centre does not matter, only that i and j share it).
+__global__ void k_gram_centre(const float *X, int n, int d, float *centre) {
+  for (int k = blockIdx.x; k < d; k += gridDim.x) {
+    float s = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += X[(int64_t)i * d + k];
+    s = warp_sum(s);
+    __shared__ float sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+      centre[k] = t / (float)n;
+    }
+    __syncthreads();
+  }
+}
+
+struct TcSmem {
+  uint32_t ah, bh, al, bl, bar_tma, bar_mma, tslot;
+};
+
+// One CTA (128 threads) per upper-triangle tile pair (ti <= tj).  validate:
+// compute the canonical value of every pair and record the worst observed
+// |d2_tc - d2_fp64| / (|y_i|^2 + |y_j|^2) (float only; for the bound test).
+template <bool F>
+__global__ void __launch_bounds__(128) k_gram_bitmap_tc(const __grid_constant__ CUtensorMap tmh,
+                                                        const __grid_constant__ CUtensorMap tml, const void *Xv,
+                                                        int n, int d, int W, int nt, Cap cap, const float *norm,
+                                                        uint32_t *adj, DevStatus *st, int validate,
+                                                        unsigned int *worst_bits) {
+  extern __shared__ unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // Tile pair from the linear block index.
+  int ti = 0, rem = blockIdx.x;
+  while (rem >= nt - ti) {
+    rem -= nt - ti;
+    ++ti;
+  }
+  const int tj = ti + rem;
+
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023) & ~1023u;  // 128-byte swizzle wants 1024-byte alignment
+  TcSmem S;
+  S.ah = base;
+  S.bh = base + TC_OPERAND_BYTES;
+  S.al = base + 2 * TC_OPERAND_BYTES;
+  S.bl = base + 3 * TC_OPERAND_BYTES;
+  S.bar_tma = base + 4 * TC_OPERAND_BYTES;
+  S.bar_mma = S.bar_tma + 8;
+  S.tslot = S.bar_tma + 16;
+  uint32_t *tslot_ptr = (uint32_t *)(smem_raw + (S.tslot - raw));
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(S.tslot),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 32) {
+    mbar_init(S.bar_tma, 1);
+    mbar_init(S.bar_mma, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *(volatile uint32_t *)tslot_ptr;
+
+  if (threadIdx.x == 0) {
+    const uint32_t bytes = (F ? 4 : 2) * TC_OPERAND_BYTES;
+    mbar_expect_tx(S.bar_tma, bytes);
+    tma_load_2d(S.ah, &tmh, 0, ti * TC_TILE, S.bar_tma);
+    tma_load_2d(S.bh, &tmh, 0, tj * TC_TILE, S.bar_tma);
+    if (F) {
+      tma_load_2d(S.al, &tml, 0, ti * TC_TILE, S.bar_tma);
+      tma_load_2d(S.bl, &tml, 0, tj * TC_TILE, S.bar_tma);
+    }
+    if (mbar_wait(S.bar_tma, 0)) {
+      tc_fence_after();
+      uint32_t acc = 0;
+      const uint32_t As[3] = {S.ah, S.ah, S.al}, Bs[3] = {S.bh, S.bl, S.bh};
+      const int nprod = F ? 3 : 1;
+      for (int p = 0; p < nprod; ++p)
+        for (int k = 0; k < TC_K / 16; ++k) {
+          umma_bf16(tmem, umma_desc_sw128(As[p] + 32 * k), umma_desc_sw128(Bs[p] + 32 * k), acc);
+          acc = 1;
+        }
+      umma_commit(S.bar_mma);
+    } else {
+      raise_flag(st, F_TIMEOUT);
+      mbar_arrive(S.bar_mma);  // release the other threads; nothing was issued
+    }
+  }
+  const bool ok = mbar_wait(S.bar_mma, 0);
+  tc_fence_after();
+  if (!ok && lane == 0) raise_flag(st, F_TIMEOUT);
+
+  if (ok && !(*(volatile int32_t *)&st->flags & F_TIMEOUT)) {
+    const int i = ti * TC_TILE + warp * 32 + lane;  // this thread's pair row
+    const float ni = i < n ? norm[i] : 0.f;
+    const bool diag = ti == tj;
+    unsigned int worst = 0;
+    for (int c0 = 0; c0 < TC_TILE; c0 += 32) {
+      float g[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, g);
+      uint32_t rowword = 0, mirror = 0;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int j = tj * TC_TILE + c0 + c;
+        bool kept = false;
+        if (i < n && j < n && i != j) {
+          const float nj = norm[j];
+          const float d2 = __fsub_rn(__fadd_rn(ni, nj), 2.f * g[c]);
+          if constexpr (F) {
+            const float beta = TC_BETA * (ni + nj) + 1e-30f;
+            if (cap.keep_all) kept = true;
+            else if ((double)d2 + (double)beta <= cap.r2) kept = true;
+            else if ((double)d2 - (double)beta > cap.r2) kept = false;
+            else kept = d2_canonical((const float *)Xv + (int64_t)i * d, (const float *)Xv + (int64_t)j * d, d) <= cap.r2;
+            if (validate) {
+              const double f = d2_canonical((const float *)Xv + (int64_t)i * d, (const float *)Xv + (int64_t)j * d, d);
+              const float r = (float)(fabs((double)d2 - f) / ((double)ni + (double)nj + 1e-30));
+              worst = max(worst, __float_as_uint(r));
+            }
+          } else {
+            const uint64_t v = (uint64_t)(int64_t)d2;  // exact: every term is an integer below 2^24
+            kept = cap.keep_all || v <= cap.r2i;
+          }
+        }
+        rowword |= (uint32_t)kept << c;
+        const uint32_t b = __ballot_sync(0xffffffffu, kept);
+        if (lane == c) mirror = b;
+      }
+      // Padded columns of the last tile map past the row's W words: skip them.
+      const int wr = (tj * TC_TILE + c0) / 32, wm = (ti * TC_TILE + warp * 32) / 32;
+      if (i < n && wr < W) adj[(int64_t)i * W + wr] = rowword;
+      const int jrow = tj * TC_TILE + c0 + lane;
+      if (!diag && jrow < n && wm < W) adj[(int64_t)jrow * W + wm] = mirror;
+    }
+    if (validate && worst) atomicMax(worst_bits, worst);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+  }
+}
+
+// ----------------------------------------------------------------- host
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+static vr_status make_map(CUtensorMap *m, void *base, int npad) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available");
+    return VR_ERR_CUDA;
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)TC_K, (cuuint64_t)npad};
+  const cuuint64_t strides[1] = {(cuuint64_t)TC_ROW_BYTES};
+  const cuuint32_t box[2] = {(cuuint32_t)TC_K, (cuuint32_t)TC_TILE};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return VR_ERR_CUDA;
+  }
+  return VR_OK;
+}
+
+static int g_gram_mode = 0;  // 0 auto, 1 tensor cores where eligible, 2 CUDA cores
+
+bool gram_tc_eligible(vr_dtype dtype, int d) {
+  if (g_gram_mode == 2) return false;
+  return d <= TC_K && (dtype == VR_I8 || dtype == VR_F32);
+}
+
+// Bitmap of kept pairs on the tensor cores.  X is the staged point array
+// (int32 for int8 input, float for float input).  `worst_bits` non-null
+// turns on validation (float only).
+vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, uint32_t *adj, DevStatus *st,
+                         cudaStream_t s, unsigned int *worst_bits) {
+  const int W = (n + 31) / 32;
+  const int nt = (n + TC_TILE - 1) / TC_TILE;
+  const int npad = nt * TC_TILE;
+  __nv_bfloat16 *Xh = nullptr, *Xl = nullptr;
+  float *norm = nullptr, *centre = nullptr;
+  auto fail = [&](cudaError_t e) {
+    cudaGetLastError();
+    if (Xh) cudaFreeAsync(Xh, s);
+    if (Xl) cudaFreeAsync(Xl, s);
+    if (norm) cudaFreeAsync(norm, s);
+    if (centre) cudaFreeAsync(centre, s);
+    return cuda_status(e, "gram_bitmap_tc", __FILE__, __LINE__);
+  };
+  cudaError_t e;
+  if ((e = cudaMallocAsync((void **)&Xh, (size_t)npad * TC_ROW_BYTES, s)) != cudaSuccess) return fail(e);
+  if ((e = cudaMallocAsync((void **)&Xl, (size_t)npad * TC_ROW_BYTES, s)) != cudaSuccess) return fail(e);
+  if ((e = cudaMallocAsync((void **)&norm, (size_t)npad * 4, s)) != cudaSuccess) return fail(e);
+  if ((e = cudaMallocAsync((void **)&centre, (size_t)TC_K * 4, s)) != cudaSuccess) return fail(e);
+  CUtensorMap mh, ml;
+  vr_status vs = make_map(&mh, Xh, npad);
+  if (vs == VR_OK) vs = make_map(&ml, Xl, npad);
+  if (vs != VR_OK) {
+    fail(cudaSuccess);
+    return vs;
+  }
+  if (F) {
+    k_gram_centre<<<d, 256, 0, s>>>((const float *)X, n, d, centre);
+    k_gram_prep<true><<<(npad + 255) / 256, 256, 0, s>>>(X, n, d, npad, centre, Xh, Xl, norm);
+  } else {
+    k_gram_prep<false><<<(npad + 255) / 256, 256, 0, s>>>(X, n, d, npad, centre, Xh, Xl, norm);
+  }
+  count_launch(F ? 2 : 1);
+  const size_t smem = 4 * TC_OPERAND_BYTES + 1024 + 64;
+  const int ntiles = nt * (nt + 1) / 2;
+  if (F) {
+    if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      return fail(e);
+    k_gram_bitmap_tc<true><<<ntiles, 128, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st,
+                                                     worst_bits ? 1 : 0, worst_bits);
+  } else {
+    if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+      return fail(e);
+    k_gram_bitmap_tc<false><<<ntiles, 128, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st, 0, nullptr);
+  }
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+  cudaFreeAsync(Xh, s);
+  cudaFreeAsync(Xl, s);
+  cudaFreeAsync(norm, s);
+  cudaFreeAsync(centre, s);
+  return VR_OK;
+}
+
+}  // namespace vr
+
+extern "C" {
+
+vr_status vr_set_gram_path(int32_t mode) {
+  if (mode < 0 || mode > 2) {
+    vr::set_error("gram path mode %d outside 0..2", mode);
+    return VR_ERR_ARG;
+  }
+  vr::g_gram_mode = mode;
+  return VR_OK;
+}
+
+}  // extern "C"
+
+extern "C" vr_status vr_gram_error_check(const float *points, int32_t n, int32_t d, vr_stream_t stream,
+                                         double *worst_ratio, double *beta_ratio) {
+  using namespace vr;
+  if (!points || !worst_ratio || n < 2 || n > VR_MAX_POINTS || d < 1 || d > TC_K) {
+    set_error("bad argument (n in [2, 8192], 1 <= d <= 64, device float points)");
+    return VR_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int W = (n + 31) / 32;
+  uint32_t *adj = nullptr;
+  DevStatus *st = nullptr;
+  unsigned int *worst = nullptr;
+  VR_CUDA(cudaMallocAsync((void **)&adj, (size_t)n * W * 4, s));
+  VR_CUDA(cudaMallocAsync((void **)&st, sizeof(DevStatus), s));
+  VR_CUDA(cudaMallocAsync((void **)&worst, 4, s));
+  VR_CUDA(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
+  VR_CUDA(cudaMemsetAsync(worst, 0, 4, s));
+  Cap cap{};
+  cap.keep_all = 1;
+  vr_status r = gram_bitmap_tc(points, n, d, true, cap, adj, st, s, worst);
+  unsigned int wb = 0;
+  int32_t flags = 0;
+  if (r == VR_OK) {
+    VR_CUDA(cudaMemcpyAsync(&wb, worst, 4, cudaMemcpyDeviceToHost, s));
+    VR_CUDA(cudaMemcpyAsync(&flags, &st->flags, 4, cudaMemcpyDeviceToHost, s));
+    VR_CUDA(cudaStreamSynchronize(s));
+  }
+  cudaFreeAsync(adj, s);
+  cudaFreeAsync(st, s);
+  cudaFreeAsync(worst, s);
+  if (r != VR_OK) return r;
+  if (flags) return flags_to_status(flags);
+  float w;
+  memcpy(&w, &wb, 4);
+  *worst_ratio = w;
+  if (beta_ratio) *beta_ratio = TC_BETA;
+  return VR_OK;
+}
