@@ -94,7 +94,7 @@ static void launch_dist(const void *X, int n, int d, int W, const Cap &cap, uint
   k_dist_bitmap<F, DR><<<grid, 256, 0, s>>>(X, n, d, W, cap, adj, st);
 }
 
-bool gram_tc_eligible(vr_dtype dtype, int d);
+bool gram_tc_eligible(vr_dtype dtype, int n, int d);
 vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, uint32_t *adj, DevStatus *st,
                          cudaStream_t s, unsigned int *worst_bits);
 
@@ -132,7 +132,13 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   }
   if (F && !cap.keep_all) {
     if (r2 >= 1e38) cap.keep_all = 1;  // beyond any fp32 first-pass value of valid input
-    else f32_thresholds(r2, cap.crel, &cap.a_keep, &cap.a_drop);
+    else {
+      f32_thresholds(r2, cap.crel, &cap.a_keep, &cap.a_drop);
+      cap.r2f_dn = (float)r2;
+      if ((double)cap.r2f_dn > r2) cap.r2f_dn = std::nextafter(cap.r2f_dn, -INFINITY);
+      cap.r2f_up = (float)r2;
+      if ((double)cap.r2f_up < r2) cap.r2f_up = std::nextafter(cap.r2f_up, INFINITY);
+    }
   }
 
   DevStatus *st;
@@ -162,7 +168,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   prof.end();
 
   prof.begin("distance");
-  if (gram_tc_eligible(dtype, d)) {
+  const bool tc = gram_tc_eligible(dtype, n, d);
+  if (tc) {
     VR_TRY(gram_bitmap_tc(X, n, d, F, cap, adj, st, s, nullptr));  // tensor-core Gram tiles
   } else {
     dist_dispatch<F>(X, n, d, W, cap, adj, st, s);
@@ -181,6 +188,19 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
 
   // ---- sync 1: kept-edge count and value errors.
   VR_TRY(read_status(st, hst, s));
+  if (tc && (hst->flags & F_OVERFLOW)) {
+    // The Gram tiles' near-cap list overflowed (pathological clustering at
+    // the cap): rebuild the bitmap exactly on the CUDA cores.
+    VR_CUDA(cudaMemsetAsync(&st->flags, 0, sizeof(int32_t), s));
+    dist_dispatch<F>(X, n, d, W, cap, adj, st, s);
+    count_launch();
+    k_rows<<<(n + 7) / 8, 256, 0, s>>>(adj, n, W, adjpre, deg, up);
+    count_launch();
+    VR_TRY((scan_exclusive<int32_t, int32_t>(deg, nbr_ptr, n, bs_small, s)));
+    VR_TRY((scan_exclusive<int32_t, int64_t>(up, lex_ptr, n, bs_small, s)));
+    VR_CUDA(cudaMemcpyAsync(&st->E, lex_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    VR_TRY(read_status(st, hst, s));
+  }
   const int64_t E = hst->E;
   if (E > INT32_MAX) {
     set_error("%lld edges exceed the 2^31-1 limit of one dimension", (long long)E);

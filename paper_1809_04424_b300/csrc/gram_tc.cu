@@ -13,9 +13,12 @@
 // float inputs: y is split as hi + lo (two bf16 values, ~16 significant
 // bits) and the Gram is hi.hi + hi.lo + lo.hi (three MMAs into one
 // accumulator).  The computed d^2 is within beta = 4e-4 (|y_i|^2 + |y_j|^2) of
-// the canonical FP64 value (bound below); pairs whose value is within beta of
-// the cap get the exact canonical value (integer emulation of the FP64
-// sequence), so the bitmap is exact.
+// the canonical FP64 value (bound below).  The tile compares fp32 d^2 -/+ beta
+// with the floats just below / above r^2 (their few roundings, < 1e-6
+// (|y_i|^2 + |y_j|^2), sit inside beta's margin); pairs left in between go to
+// a list that k_band_patch decides with the exact canonical value (integer
+// emulation of the FP64 sequence), so the bitmap is exact.  A list overflow
+// makes the host redo the bitmap on the CUDA cores.
 //
 // Bound, per pair, with S = |y_i| + |y_j|, eta = 1.01 * 2^-16 (split plus
 // centring error per coordinate, relative): representation 2 eta S^2; dropped
@@ -42,6 +45,7 @@ constexpr int TC_K = 64;            // coordinates per operand row (padded)
 constexpr int TC_ROW_BYTES = TC_K * 2;
 constexpr int TC_OPERAND_BYTES = TC_TILE * TC_ROW_BYTES;  // 16 KB
 constexpr uint32_t TC_TMEM_COLS = 128;
+constexpr int TC_THREADS = 256;     // 8 warps: two per TMEM lane quarter, each half the columns
 constexpr long TC_WAIT_LIMIT = 1l << 22;
 constexpr float TC_BETA = 4e-4f;
 
@@ -133,47 +137,70 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // hi = x exactly (int8); rows padded to 64 coordinates and to whole tiles.
 // norm = |hi + lo|^2 in fp32 (fma in coordinate order).
 template <bool F>
+// One warp per padded row: lane l owns coordinates 2l and 2l+1 (bf16x2
+// stores, coalesced), |y_i|^2 by a warp sum of the split values.
 __global__ void k_gram_prep(const void *Xv, int n, int d, int npad, const float *centre, __nv_bfloat16 *Xh,
                             __nv_bfloat16 *Xl, float *norm) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
-    float acc = 0.f;
-    for (int k = 0; k < TC_K; ++k) {
-      float hi = 0.f, lo = 0.f;
+  const int lane = threadIdx.x & 31;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < npad; i += (gridDim.x * blockDim.x) >> 5) {
+    float hi[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * lane + h;
       if (i < n && k < d) {
         if constexpr (F) {
           const float y = __fsub_rn(((const float *)Xv)[(int64_t)i * d + k], centre[k]);
-          const __nv_bfloat16 h = __float2bfloat16_rn(y);
-          hi = __bfloat162float(h);
-          lo = __bfloat162float(__float2bfloat16_rn(__fsub_rn(y, hi)));
+          hi[h] = __bfloat162float(__float2bfloat16_rn(y));
+          lo[h] = __bfloat162float(__float2bfloat16_rn(__fsub_rn(y, hi[h])));
         } else {
-          hi = (float)((const int32_t *)Xv)[(int64_t)i * d + k];
+          hi[h] = (float)((const int32_t *)Xv)[(int64_t)i * d + k];
         }
       }
-      Xh[(int64_t)i * TC_K + k] = __float2bfloat16_rn(hi);
-      if constexpr (F) Xl[(int64_t)i * TC_K + k] = __float2bfloat16_rn(lo);
-      const float xt = hi + lo;
-      acc = __fmaf_rn(xt, xt, acc);
     }
-    norm[i] = acc;
+    ((__nv_bfloat162 *)(Xh + (int64_t)i * TC_K))[lane] = __floats2bfloat162_rn(hi[0], hi[1]);
+    if constexpr (F) ((__nv_bfloat162 *)(Xl + (int64_t)i * TC_K))[lane] = __floats2bfloat162_rn(lo[0], lo[1]);
+    const float x0 = hi[0] + lo[0], x1 = hi[1] + lo[1];
+    const float acc = warp_sum(__fmaf_rn(x1, x1, x0 * x0));
+    if (lane == 0) norm[i] = acc;
   }
 }
 
-// Centre = mean of the points (fp32, one CTA per coordinate chunk; the exact
-// centre does not matter, only that i and j share it).
-__global__ void k_gram_centre(const float *X, int n, int d, float *centre) {
-  for (int k = blockIdx.x; k < d; k += gridDim.x) {
-    float s = 0.f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += X[(int64_t)i * d + k];
-    s = warp_sum(s);
-    __shared__ float sh[32];
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float t = 0.f;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-      centre[k] = t / (float)n;
+// Exact decision of the pairs the Gram tiles left within beta of the cap:
+// the canonical FP64 value (hardware FP64: the list is a small fraction of
+// the pairs), bits ORed into both rows.
+__global__ void k_band_patch(const float *X, int d, int W, double r2, const uint64_t *band, const DevStatus *st,
+                             uint64_t band_cap, uint32_t *adj) {
+  const uint64_t cnt = min((unsigned long long)st->band_count, (unsigned long long)band_cap);
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < cnt; t += (uint64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(band[t] >> 32), j = (int)(band[t] & 0xffffffffu);
+    if (d2_f64(X + (int64_t)i * d, X + (int64_t)j * d, d) <= r2) {
+      atomicOr(&adj[(int64_t)i * W + (j >> 5)], 1u << (j & 31));
+      atomicOr(&adj[(int64_t)j * W + (i >> 5)], 1u << (i & 31));
     }
-    __syncthreads();
+  }
+}
+
+// Centre c = mean of up to 256 evenly spaced points (one CTA).  Any c gives
+// the same distances; one near the middle of the cloud keeps |y|, and with it
+// the width of the near-cap band, small.
+constexpr int TC_CENTRE_SAMPLE = 256;
+__global__ void __launch_bounds__(1024) k_gram_centre(const float *X, int n, int d, float *centre) {
+  __shared__ float part[32][TC_K];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = min(n, TC_CENTRE_SAMPLE);
+  float a0 = 0.f, a1 = 0.f;
+  for (int s = warp; s < m; s += 32) {
+    const int64_t r = (int64_t)s * n / m;
+    if (lane < d) a0 += X[r * d + lane];
+    if (lane + 32 < d) a1 += X[r * d + lane + 32];
+  }
+  part[warp][lane] = a0;
+  part[warp][lane + 32] = a1;
+  __syncthreads();
+  if (threadIdx.x < d) {
+    float t = 0.f;
+    for (int w = 0; w < 32; ++w) t += part[w][threadIdx.x];
+    centre[threadIdx.x] = t / (float)m;
   }
 }
 
@@ -181,15 +208,16 @@ struct TcSmem {
   uint32_t ah, bh, al, bl, bar_tma, bar_mma, tslot;
 };
 
-// One CTA (128 threads) per upper-triangle tile pair (ti <= tj).  validate:
-// compute the canonical value of every pair and record the worst observed
-// |d2_tc - d2_fp64| / (|y_i|^2 + |y_j|^2) (float only; for the bound test).
-template <bool F>
-__global__ void __launch_bounds__(128) k_gram_bitmap_tc(const __grid_constant__ CUtensorMap tmh,
+// One CTA (TC_THREADS) per upper-triangle tile pair (ti <= tj).  Float
+// pairs within beta of the cap are appended to `band` (decided exactly by
+// k_band_patch); VALIDATE instead computes the canonical value of every pair
+// and records the worst observed |d2_tc - d2_fp64| / (|y_i|^2 + |y_j|^2).
+template <bool F, bool VALIDATE>
+__global__ void __launch_bounds__(TC_THREADS) k_gram_bitmap_tc(const __grid_constant__ CUtensorMap tmh,
                                                         const __grid_constant__ CUtensorMap tml, const void *Xv,
                                                         int n, int d, int W, int nt, Cap cap, const float *norm,
-                                                        uint32_t *adj, DevStatus *st, int validate,
-                                                        unsigned int *worst_bits) {
+                                                        uint32_t *adj, DevStatus *st, uint64_t *band,
+                                                        uint64_t band_cap, unsigned int *worst_bits) {
   extern __shared__ unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // Tile pair from the linear block index.
@@ -258,28 +286,30 @@ __global__ void __launch_bounds__(128) k_gram_bitmap_tc(const __grid_constant__ 
   if (!ok && lane == 0) raise_flag(st, F_TIMEOUT);
 
   if (ok && !(*(volatile int32_t *)&st->flags & F_TIMEOUT)) {
-    const int i = ti * TC_TILE + warp * 32 + lane;  // this thread's pair row
+    // Warp w reads TMEM lanes 32 (w % 4) .. +31 (the lane quarter its warp
+    // index allows) and columns 64 (w / 4) .. +63.
+    const int q = warp & 3, half = warp >> 2;
+    const int i = ti * TC_TILE + q * 32 + lane;  // this thread's pair row
     const float ni = i < n ? norm[i] : 0.f;
     const bool diag = ti == tj;
     unsigned int worst = 0;
-    for (int c0 = 0; c0 < TC_TILE; c0 += 32) {
+    for (int c0 = half * (TC_TILE / 2); c0 < (half + 1) * (TC_TILE / 2); c0 += 32) {
       float g[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, g);
+      tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, g);
       uint32_t rowword = 0, mirror = 0;
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int j = tj * TC_TILE + c0 + c;
-        bool kept = false;
+        bool kept = false, in_band = false;
         if (i < n && j < n && i != j) {
           const float nj = norm[j];
           const float d2 = __fsub_rn(__fadd_rn(ni, nj), 2.f * g[c]);
           if constexpr (F) {
-            const float beta = TC_BETA * (ni + nj) + 1e-30f;
-            if (cap.keep_all) kept = true;
-            else if ((double)d2 + (double)beta <= cap.r2) kept = true;
-            else if ((double)d2 - (double)beta > cap.r2) kept = false;
-            else kept = d2_canonical((const float *)Xv + (int64_t)i * d, (const float *)Xv + (int64_t)j * d, d) <= cap.r2;
-            if (validate) {
+            const float beta = TC_BETA * (ni + nj);
+            if (cap.keep_all || __fadd_rn(d2, beta) <= cap.r2f_dn) kept = true;
+            else if (__fsub_rn(d2, beta) > cap.r2f_up) kept = false;
+            else in_band = i < j;  // a diagonal tile sees the pair twice: record it once
+            if constexpr (VALIDATE) {
               const double f = d2_canonical((const float *)Xv + (int64_t)i * d, (const float *)Xv + (int64_t)j * d, d);
               const float r = (float)(fabs((double)d2 - f) / ((double)ni + (double)nj + 1e-30));
               worst = max(worst, __float_as_uint(r));
@@ -289,17 +319,29 @@ __global__ void __launch_bounds__(128) k_gram_bitmap_tc(const __grid_constant__ 
             kept = cap.keep_all || v <= cap.r2i;
           }
         }
+        if constexpr (F && !VALIDATE) {
+          const uint32_t bm = __ballot_sync(0xffffffffu, in_band);
+          if (bm) {
+            uint64_t at = 0;
+            if (lane == __ffs(bm) - 1) at = atomicAdd((unsigned long long *)&st->band_count, (unsigned long long)__popc(bm));
+            at = __shfl_sync(0xffffffffu, at, __ffs(bm) - 1) + __popc(bm & lanemask_lt());
+            if (in_band) {
+              if (at < band_cap) band[at] = ((uint64_t)i << 32) | (uint32_t)j;
+              else raise_flag(st, F_OVERFLOW);
+            }
+          }
+        }
         rowword |= (uint32_t)kept << c;
         const uint32_t b = __ballot_sync(0xffffffffu, kept);
         if (lane == c) mirror = b;
       }
       // Padded columns of the last tile map past the row's W words: skip them.
-      const int wr = (tj * TC_TILE + c0) / 32, wm = (ti * TC_TILE + warp * 32) / 32;
+      const int wr = (tj * TC_TILE + c0) / 32, wm = (ti * TC_TILE + q * 32) / 32;
       if (i < n && wr < W) adj[(int64_t)i * W + wr] = rowword;
       const int jrow = tj * TC_TILE + c0 + lane;
       if (!diag && jrow < n && wm < W) adj[(int64_t)jrow * W + wm] = mirror;
     }
-    if (validate && worst) atomicMax(worst_bits, worst);
+    if (VALIDATE && worst) atomicMax(worst_bits, worst);
   }
   tc_fence_before();
   __syncthreads();
@@ -350,9 +392,14 @@ static vr_status make_map(CUtensorMap *m, void *base, int npad) {
 
 static int g_gram_mode = 0;  // 0 auto, 1 tensor cores where eligible, 2 CUDA cores
 
-bool gram_tc_eligible(vr_dtype dtype, int d) {
+// Tensor-core tiles pay off once there are enough 128x128 tiles to fill the
+// GPU (two per SM); mode 1 forces them wherever they apply.
+bool gram_tc_eligible(vr_dtype dtype, int n, int d) {
   if (g_gram_mode == 2) return false;
-  return d <= TC_K && (dtype == VR_I8 || dtype == VR_F32);
+  if (!(d <= TC_K && (dtype == VR_I8 || dtype == VR_F32))) return false;
+  if (g_gram_mode == 1) return true;
+  const int nt = (n + TC_TILE - 1) / TC_TILE;
+  return nt * (nt + 1) / 2 >= 2 * 148;
 }
 
 // Bitmap of kept pairs on the tensor cores.  X is the staged point array
@@ -365,12 +412,14 @@ vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, ui
   const int npad = nt * TC_TILE;
   __nv_bfloat16 *Xh = nullptr, *Xl = nullptr;
   float *norm = nullptr, *centre = nullptr;
+  uint64_t *band = nullptr;
   auto fail = [&](cudaError_t e) {
     cudaGetLastError();
     if (Xh) cudaFreeAsync(Xh, s);
     if (Xl) cudaFreeAsync(Xl, s);
     if (norm) cudaFreeAsync(norm, s);
     if (centre) cudaFreeAsync(centre, s);
+    if (band) cudaFreeAsync(band, s);
     return cuda_status(e, "gram_bitmap_tc", __FILE__, __LINE__);
   };
   cudaError_t e;
@@ -386,28 +435,44 @@ vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, ui
     return vs;
   }
   if (F) {
-    k_gram_centre<<<d, 256, 0, s>>>((const float *)X, n, d, centre);
-    k_gram_prep<true><<<(npad + 255) / 256, 256, 0, s>>>(X, n, d, npad, centre, Xh, Xl, norm);
+    k_gram_centre<<<1, 1024, 0, s>>>((const float *)X, n, d, centre);
+    k_gram_prep<true><<<(npad + 7) / 8, 256, 0, s>>>(X, n, d, npad, centre, Xh, Xl, norm);
   } else {
-    k_gram_prep<false><<<(npad + 255) / 256, 256, 0, s>>>(X, n, d, npad, centre, Xh, Xl, norm);
+    k_gram_prep<false><<<(npad + 7) / 8, 256, 0, s>>>(X, n, d, npad, centre, Xh, Xl, norm);
   }
   count_launch(F ? 2 : 1);
   const size_t smem = 4 * TC_OPERAND_BYTES + 1024 + 64;
   const int ntiles = nt * (nt + 1) / 2;
-  if (F) {
-    if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
-      return fail(e);
-    k_gram_bitmap_tc<true><<<ntiles, 128, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st,
-                                                     worst_bits ? 1 : 0, worst_bits);
-  } else {
-    if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const uint64_t npairs = (uint64_t)n * (n - 1) / 2;
+  const uint64_t band_cap = std::min<uint64_t>(npairs, std::max<uint64_t>(1u << 20, npairs / 16));
+  if (F && !worst_bits) {
+    if ((e = cudaMallocAsync((void **)&band, band_cap * 8, s)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemsetAsync(&st->band_count, 0, 8, s)) != cudaSuccess) return fail(e);
+  }
+  if (F && worst_bits) {
+    if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
       return fail(e);
-    k_gram_bitmap_tc<false><<<ntiles, 128, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st, 0, nullptr);
+    k_gram_bitmap_tc<true, true><<<ntiles, TC_THREADS, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st, nullptr, 0,
+                                                           worst_bits);
+  } else if (F) {
+    if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+      return fail(e);
+    k_gram_bitmap_tc<true, false><<<ntiles, TC_THREADS, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st, band,
+                                                            band_cap, nullptr);
+    k_band_patch<<<148 * 4, 256, 0, s>>>((const float *)X, d, W, cap.r2, band, st, band_cap, adj);
+    count_launch();
+  } else {
+    if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+      return fail(e);
+    k_gram_bitmap_tc<false, false><<<ntiles, TC_THREADS, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st, nullptr, 0,
+                                                             nullptr);
   }
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+  if (band) cudaFreeAsync(band, s);
   cudaFreeAsync(Xh, s);
   cudaFreeAsync(Xl, s);
   cudaFreeAsync(norm, s);

@@ -32,6 +32,8 @@ struct Cap {
   double crel;      // float inputs: relative bound of the fp32 first pass
   float a_keep;     // float inputs: fp32 value at or below which a pair is certainly kept
   float a_drop;     // float inputs: fp32 value at or above which a pair is certainly dropped
+  float r2f_dn;     // float inputs: largest float <= r2
+  float r2f_up;     // float inputs: smallest float >= r2
 };
 
 // Absolute slack of the fp32 bound: covers underflow of tiny squares.

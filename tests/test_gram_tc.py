@@ -69,3 +69,21 @@ def test_float_gram_error_within_quarter_beta(torch, seed, scale, d):
     assert L.vr_gram_error_check(ctypes.c_void_p(dev.data_ptr()), 600, d, None, ctypes.byref(worst),
                                  ctypes.byref(beta)) == 0, vr.vr_last_error()
     assert 0 <= worst.value <= beta.value / 4, (worst.value, beta.value)
+
+
+def test_band_list_overflow_falls_back_exactly(torch):
+    """Two tight clusters 100 apart with the cap at exactly 100: every one of
+    the 1050^2 cross pairs lies within beta of the cap, more than the near-cap
+    list holds, so the build redoes the bitmap on the CUDA cores and still
+    gives the oracle's complex."""
+    g = synth.rng(77)
+    a = g.normal(size=(1050, 4)) * 1e-3
+    b = g.normal(size=(1050, 4)) * 1e-3
+    b[:, 0] += 100.0
+    pts = np.concatenate([a, b]).astype(np.float32)
+    try:
+        set_path(1)
+        gc = gpu_build(torch, pts, 1, 100.0)
+    finally:
+        set_path(0)
+    assert_same(gc, oracle.vr_build(pts, 1, 100.0), 1)
