@@ -44,7 +44,7 @@ WORKLOADS = {
 }
 METRIC = "VR simplices/s"
 
-# Algorithmic bytes per unit of each phase (see DESIGN.md "Roofline").
+# Algorithmic bytes per unit of each phase.
 #   tri_emit:  36 B written per triangle (verts 12, grade 4, rowidx 12, colptr 8)
 #   edge_sort: 8 B read + 8 B written per key per pass
 #   edge_grades: keys 8 read, flags 4+4, outputs 8+4+8+8, CSR scatter 8 per edge
@@ -484,17 +484,20 @@ def main():
     n, d = cloud.n, cloud.d
     Wd = (n + 31) // 32
     per_launch_bytes = {
-        "tri_sort.scatter": 16 * T,        # read + write one 8 B key
-        "tri_sort.hist": 8 * T,            # read one 8 B key
+        "tri_sort.pass": 16 * T,           # one digit pass: read + write one 8 B key
+        "tri_sort.hist": 8 * T,            # all-digit histogram: read one 8 B key
         "tri_final": 44 * T,               # read key 8 B, write verts 12 + grade 4 + rowidx 12 + colptr 8
         "tri_lex_gen": 8 * T,              # write one 8 B key
         "tri_emit": 36 * T,                # write verts 12 + grade 4 + rowidx 12 + colptr 8
-        "edge_sort.scatter": 16 * E,
+        "edge_sort.pass": 16 * E,
         "edge_sort.hist": 8 * E,
         "distance": cloud.points.nbytes + 4 * n * Wd,  # read points, write the bitmap
         "edge_keys": 8 * E,
     }
-    single = {k: v for k, v in phases.items() if k in per_launch_bytes}
+    # Regions of one kernel (a sort's digit passes: several launches of the
+    # same kernel, timed per launch).
+    single = {k: v for k, v in phases.items() if k in per_launch_bytes
+              and (v["launches_per_call"] == 1 or k.endswith(".pass"))}
     roof = None
     if single:
         dom = max(single, key=lambda k: single[k]["ms_per_call"])

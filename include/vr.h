@@ -260,6 +260,24 @@ VR_API int64_t vr_launch_count(void);
 VR_API vr_status vr_sort_keys_noalloc(uint64_t *keys, int64_t n, int32_t bit_lo,
                                       int32_t nbits, vr_stream_t stream);
 
+/* The builder's multi-CTA sort, exposed as a primitive (the paper orders
+ * simplices by (grade, lexicographic position); this is the stable sort that
+ * realises it on packed keys).  Stable LSD radix sort, in place, of n
+ * caller-owned 64-bit keys (DEVICE memory) on bits [bit_lo, bit_lo + nbits),
+ * ascending; keys equal on those bits keep their input order; bits outside
+ * the range never take part.
+ *   - One histogram pass over all digits, then one launch per 8-bit digit;
+ *     tiles of 4096 keys find their output offsets by looking back over
+ *     earlier tiles' published counts (bounded waits).
+ *   - Workspace (n keys + about 2 KB per tile) comes from the stream-ordered
+ *     pool of the current device and is released before return.
+ *   - Synchronous: returns once the sort on `stream` has finished.
+ *   - n < 0, NULL keys with n > 0, or a bit range outside [0, 64): VR_ERR_ARG;
+ *     n >= 2^31: VR_ERR_RANGE; no memory: VR_ERR_OOM; a bounded wait that gave
+ *     up: VR_ERR_TIMEOUT (keys then unspecified). */
+VR_API vr_status vr_sort_keys(uint64_t *keys, int64_t n, int32_t bit_lo, int32_t nbits,
+                              vr_stream_t stream);
+
 /* Message for the last failing call on this thread ("" if none). */
 VR_API const char *vr_last_error(void);
 VR_API const char *vr_status_string(vr_status s);

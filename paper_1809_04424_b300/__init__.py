@@ -231,6 +231,29 @@ def vr_complex_free(handle) -> None:
 
 # ---------------------------------------------------------------- batches
 
+def _sort_call(fn, keys, bit_lo, nbits, stream):
+    """keys: a CUDA uint64/int64 tensor (contiguous), sorted in place."""
+    if not (hasattr(keys, "is_cuda") and keys.is_cuda and keys.is_contiguous() and keys.element_size() == 8):
+        raise TypeError("keys must be a contiguous 8-byte CUDA tensor")
+    L = lib()
+    f = getattr(L, fn)
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    s = stream if stream is not None else _current_stream()
+    _check(f(ctypes.c_void_p(keys.data_ptr()), keys.numel(), bit_lo, nbits, ctypes.c_void_p(s)))
+    return keys
+
+
+def vr_sort_keys(keys, bit_lo: int, nbits: int, stream=None):
+    """Stable radix sort of 64-bit keys in place on bits [bit_lo, bit_lo + nbits)."""
+    return _sort_call("vr_sort_keys", keys, bit_lo, nbits, stream)
+
+
+def vr_sort_keys_noalloc(keys, bit_lo: int, nbits: int, stream=None):
+    """The same sort, one CTA, no allocation (at most 131072 keys)."""
+    return _sort_call("vr_sort_keys_noalloc", keys, bit_lo, nbits, stream)
+
+
 class Batch:
     """Owner of one ``vr_batch*``: per-cloud results as non-owning views."""
 

@@ -213,12 +213,10 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   int32_t *everts, *egrade, *erow;
   int64_t *ecol, *bs_e;
   double *gval, *d64 = nullptr, *d64_lex = nullptr;
-  const int64_t nt = rs_tiles(E);
   VR_TRY(ws.alloc(&keys, E));
   VR_TRY(ws.alloc(&rs.tkeys, E));
-  VR_TRY(ws.alloc(&rs.hist, (int64_t)RS_BINS * nt));
-  VR_TRY(ws.alloc(&rs.off, (int64_t)RS_BINS * nt + 1));
-  VR_TRY(ws.alloc(&rs.bs, scan_tmp_slots((int64_t)RS_BINS * nt)));
+  VR_TRY(ws.alloc(&rs.meta, rs_meta_bytes(E)));
+  rs.err = &st->flags;
   VR_TRY(ws.alloc(&flag, E));
   VR_TRY(ws.alloc(&gex, E + 1));
   VR_TRY(ws.alloc(&bs_e, scan_tmp_slots(E)));
@@ -252,8 +250,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       kbits = std::max(1, bitlen(bound));
     }
     prof.begin("edge_sort");
-    static const char *const etag[3] = {"edge_sort.hist", "edge_sort.scan", "edge_sort.scatter"};
-    VR_TRY(radix_sort(keys, nullptr, E, KEY_SHIFT, kbits, rs, s, &prof, etag));
+    static const char *const etag[2] = {"edge_sort.hist", "edge_sort.pass"};
+    VR_TRY(radix_sort(keys, E, KEY_SHIFT, kbits, rs, s, &prof, etag));
     prof.end();
 
     if (F) {
@@ -353,12 +351,10 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       // Lex-order generation, stable sort on the grade bits, final write.
       uint64_t *tk;
       RadixScratch trs{};
-      const int64_t tnt = rs_tiles(T);
       VR_TRY(ws.alloc(&tk, T));
       VR_TRY(ws.alloc(&trs.tkeys, T));
-      VR_TRY(ws.alloc(&trs.hist, (int64_t)RS_BINS * tnt));
-      VR_TRY(ws.alloc(&trs.off, (int64_t)RS_BINS * tnt + 1));
-      VR_TRY(ws.alloc(&trs.bs, scan_tmp_slots((int64_t)RS_BINS * tnt)));
+      VR_TRY(ws.alloc(&trs.meta, rs_meta_bytes(T)));
+      trs.err = &st->flags;
       prof.begin("tri_lex_gen");
       k_lex_tri_gen<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr, nbr_ord, deg,
                                                              up, lex_ptr, toff, T, tk, st);
@@ -366,8 +362,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_CUDA(cudaGetLastError());
       prof.end();
       prof.begin("tri_grade_sort");
-      static const char *const ttag[3] = {"tri_sort.hist", "tri_sort.scan", "tri_sort.scatter"};
-      VR_TRY(radix_sort(tk, nullptr, T, LEX_SHIFT, std::max(1, bitlen((uint64_t)(ngrades - 1))), trs, s, &prof,
+      static const char *const ttag[2] = {"tri_sort.hist", "tri_sort.pass"};
+      VR_TRY(radix_sort(tk, T, LEX_SHIFT, std::max(1, bitlen((uint64_t)(ngrades - 1))), trs, s, &prof,
                         ttag));
       prof.end();
       prof.begin("tri_final");

@@ -119,8 +119,9 @@ __device__ T block_excl_scan(T v, T *sh, T *total) {
 
 // ------------------------------------------------------------------ scans
 // out[i] = sum_{j<i} in[j] for i in [0, L]; out[L] = total.  L is known on the
-// host.  Three launches for long arrays (chunk sums, one-CTA scan of the
-// sums, chunk scans with offsets), one for short ones.
+// host.  One launch for one chunk; two for up to SCAN_SELF_MAX chunks (chunk
+// sums, then chunk scans that add up the sums before them themselves); three
+// beyond (a one-CTA scan of the chunk sums in between).
 
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 16;
@@ -155,11 +156,24 @@ static __global__ void __launch_bounds__(1024) k_scan_sums(int64_t *bs, int64_t 
   if (threadIdx.x == 0) bs[nb] = carry;
 }
 
+constexpr int64_t SCAN_SELF_MAX = 2048;
+
+// self_off: bs holds raw chunk sums; the CTA adds up those before its chunk.
 template <typename TI, typename TO>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(const TI *in, int64_t L, const int64_t *bs, TO *out) {
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(const TI *in, int64_t L, const int64_t *bs, TO *out,
+                                                             int self_off) {
   __shared__ int64_t buf[SCAN_CHUNK];
   __shared__ int64_t sh[33];
+  __shared__ int64_t off_sh;
   const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
+  if (self_off) {
+    int64_t a = 0;
+    for (int64_t q = threadIdx.x; q < (int64_t)blockIdx.x; q += SCAN_THREADS) a += bs[q];
+    int64_t tot;
+    block_excl_scan<int64_t>(a, sh, &tot);
+    if (threadIdx.x == 0) off_sh = tot;
+    __syncthreads();
+  }
   for (int t = threadIdx.x; t < SCAN_CHUNK; t += SCAN_THREADS) {
     int64_t i = base + t;
     buf[t] = i < L ? (int64_t)in[i] : 0;
@@ -174,7 +188,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(const TI *in, int64
   }
   __syncthreads();
   int64_t tot;
-  const int64_t off = bs ? bs[blockIdx.x] : 0;
+  const int64_t off = !bs ? 0 : self_off ? off_sh : bs[blockIdx.x];
   int64_t pre = block_excl_scan<int64_t>(s, sh, &tot) + off;
 #pragma unroll
   for (int q = 0; q < SCAN_ITEMS; ++q) buf[threadIdx.x * SCAN_ITEMS + q] = pre + loc[q];
@@ -193,13 +207,17 @@ template <typename TI, typename TO>
 inline vr_status scan_exclusive(const TI *in, TO *out, int64_t L, int64_t *bs, cudaStream_t s) {
   int64_t nb = (L + SCAN_CHUNK - 1) / SCAN_CHUNK;
   if (nb <= 1) {
-    k_scan_final<TI, TO><<<1, SCAN_THREADS, 0, s>>>(in, L, nullptr, out);
+    k_scan_final<TI, TO><<<1, SCAN_THREADS, 0, s>>>(in, L, nullptr, out, 0);
     count_launch(1);
+  } else if (nb <= SCAN_SELF_MAX) {
+    count_launch(2);
+    k_scan_reduce<TI><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, L, bs);
+    k_scan_final<TI, TO><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, L, bs, out, 1);
   } else {
     count_launch(3);
     k_scan_reduce<TI><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, L, bs);
     k_scan_sums<<<1, 1024, 0, s>>>(bs, nb);
-    k_scan_final<TI, TO><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, L, bs, out);
+    k_scan_final<TI, TO><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, L, bs, out, 0);
   }
   VR_CUDA(cudaGetLastError());
   return VR_OK;
@@ -218,25 +236,38 @@ constexpr int RS_ITEMS = 16;                    // keys per lane
 constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 4096 keys per tile
 constexpr int RS_BINS = 256;
 
-__device__ __forceinline__ uint32_t digit_of(uint64_t k, int shift) { return (uint32_t)(k >> shift) & 0xffu; }
+__device__ __forceinline__ uint32_t digit_of(uint64_t k, int shift, uint32_t mask) {
+  return (uint32_t)(k >> shift) & mask;
+}
+// Mask of digit p of a sort on nbits bits: the last digit may be narrower, so
+// bits above the sorted range never take part.
+__host__ __device__ inline uint32_t digit_mask(int nbits, int p) {
+  const int b = nbits - 8 * p;
+  return b >= 8 ? 0xffu : (1u << b) - 1u;
+}
 
 // Rank the keys of one tile (positions [t0, t0 + cnt) of src).  On return
 // rank[q] holds, for the lane's q-th key, its position among equal digits in
 // the tile, and sh_cnt[d] the tile's count of digit d.  Keys are read by warp
 // w at t0 + w*512 + q*32 + lane.
-__device__ __forceinline__ void tile_rank(const uint64_t *src, int64_t t0, int64_t cnt, int shift,
+__device__ __forceinline__ void tile_rank(const uint64_t *src, int64_t t0, int64_t cnt, int shift, uint32_t mask,
                                           uint64_t (&key)[RS_ITEMS], uint32_t (&rank)[RS_ITEMS],
                                           uint32_t (*sh_wcnt)[RS_BINS], uint32_t *sh_cnt) {
   const int w = threadIdx.x >> 5, l = lane_id();
   for (int b = threadIdx.x; b < RS_WARPS * RS_BINS; b += RS_THREADS) (&sh_wcnt[0][0])[b] = 0;
   __syncthreads();
   const uint32_t lt = lanemask_lt();
+  // All loads first (16 in flight per lane), then the ranking rounds.
+#pragma unroll
+  for (int q = 0; q < RS_ITEMS; ++q) {
+    const int64_t idx = (int64_t)w * (32 * RS_ITEMS) + q * 32 + l;
+    key[q] = idx < cnt ? src[t0 + idx] : ~0ull;
+  }
 #pragma unroll
   for (int q = 0; q < RS_ITEMS; ++q) {
     int64_t idx = (int64_t)w * (32 * RS_ITEMS) + q * 32 + l;
     bool ok = idx < cnt;
-    key[q] = ok ? src[t0 + idx] : ~0ull;
-    uint32_t dg = ok ? digit_of(key[q], shift) : RS_BINS;  // sentinel for empty lanes
+    uint32_t dg = ok ? digit_of(key[q], shift, mask) : RS_BINS;  // sentinel for empty lanes
     uint32_t peers = __match_any_sync(0xffffffffu, dg);
     uint32_t before = ok ? sh_wcnt[w][dg] : 0;
     rank[q] = before + __popc(peers & lt);
@@ -260,48 +291,127 @@ __device__ __forceinline__ void tile_rank(const uint64_t *src, int64_t t0, int64
 #pragma unroll
   for (int q = 0; q < RS_ITEMS; ++q) {
     int64_t idx = (int64_t)w * (32 * RS_ITEMS) + q * 32 + l;
-    if (idx < cnt) rank[q] += sh_wcnt[w][digit_of(key[q], shift)];
+    if (idx < cnt) rank[q] += sh_wcnt[w][digit_of(key[q], shift, mask)];
   }
 }
 
-// Multi-CTA pass, step 1: per-tile digit histogram, digit-major layout
-// hist[d * ntiles + tile].
-static __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *src, int64_t n, int shift, int64_t ntiles,
-                                                        int64_t *hist) {
-  __shared__ uint32_t h[RS_BINS];
-  for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) h[b] = 0;
+// Multi-CTA sort ("onesweep" shape: one digit histogram pass over all
+// digits, then one launch per digit pass).
+//
+// k_rs_hist_all: hist[p][d] = number of keys whose pass-p digit is d, for all
+// passes in one read of the keys (warp-aggregated shared atomics).
+constexpr int RS_MAX_PASSES = 8;
+static __global__ void __launch_bounds__(RS_THREADS) k_rs_hist_all(const uint64_t *src, int64_t n, int bit_lo,
+                                                                   int nbits, uint32_t *hist) {
+  const int passes = (nbits + 7) / 8;
+  __shared__ uint32_t h[RS_MAX_PASSES][RS_BINS];
+  for (int b = threadIdx.x; b < RS_MAX_PASSES * RS_BINS; b += RS_THREADS) (&h[0][0])[b] = 0;
   __syncthreads();
-  const int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
-  for (int t = threadIdx.x; t < RS_TILE; t += RS_THREADS) {
-    int64_t i = t0 + t;
-    if (i < n) atomicAdd(&h[digit_of(src[i], shift)], 1u);
+  const uint32_t lt = lanemask_lt();
+  // One tile per CTA and pass through the grid; a lane loads its 16 keys
+  // (coalesced, all in flight) before counting them.
+  for (int64_t t0 = (int64_t)blockIdx.x * RS_TILE; t0 < n; t0 += (int64_t)gridDim.x * RS_TILE) {
+    uint64_t k[RS_ITEMS];
+#pragma unroll
+    for (int q = 0; q < RS_ITEMS; ++q) {
+      const int64_t i = t0 + q * RS_THREADS + threadIdx.x;
+      k[q] = i < n ? src[i] : 0;
+    }
+    for (int p = 0; p < passes; ++p) {
+      const int shift = bit_lo + 8 * p;
+      const uint32_t mask = digit_mask(nbits, p);
+#pragma unroll
+      for (int q = 0; q < RS_ITEMS; ++q) {
+        const bool ok = t0 + q * RS_THREADS + threadIdx.x < n;
+        const uint32_t dg = ok ? digit_of(k[q], shift, mask) : RS_BINS;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        if (ok && (peers & lt) == 0) atomicAdd(&h[p][dg], (uint32_t)__popc(peers));
+      }
+    }
   }
   __syncthreads();
-  for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) hist[(int64_t)b * ntiles + blockIdx.x] = h[b];
+  for (int b = threadIdx.x; b < passes * RS_BINS; b += RS_THREADS) {
+    const uint32_t v = (&h[0][0])[b];
+    if (v) atomicAdd(&hist[b], v);
+  }
 }
 
-// Multi-CTA pass, step 3: stable scatter using the scanned histogram.
-static __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *src, const uint32_t *vsrc, uint64_t *dst,
-                                                           uint32_t *vdst, int64_t n, int shift, int64_t ntiles,
-                                                           const int64_t *off) {
+// Per-(tile, digit) status word of a pass: tag in the top byte (2p + 1: the
+// tile's own count is published; 2p + 2: the inclusive count over tiles
+// 0..t is published; anything else: not yet), value below.  Tags are
+// pass-specific, so one clearing serves every pass of a sort.
+constexpr long RS_WAIT_LIMIT = 1l << 24;
+__device__ __forceinline__ void rs_publish(uint64_t *w, uint32_t tag, uint64_t v) {
+  *(volatile uint64_t *)w = ((uint64_t)tag << 56) | v;
+}
+
+// One digit pass.  CTAs claim tiles in order (atomic ticket), so every
+// earlier tile belongs to a CTA that is already running; a CTA ranks its tile
+// (stable), publishes its per-digit counts, adds up earlier tiles' counts by
+// looking back until an inclusive count is found (bounded spin: a timeout
+// raises F_TIMEOUT in *err), publishes its own inclusive counts, and writes
+// the keys out digit run by digit run through shared memory.
+static __global__ void __launch_bounds__(RS_THREADS, 3) k_rs_onesweep(const uint64_t *src, uint64_t *dst, int64_t n,
+                                                                   int shift, uint32_t mask, int pass, const uint32_t *hist,
+                                                                   uint64_t *status, uint32_t *ticket,
+                                                                   int32_t *err) {
   __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
   __shared__ uint32_t cnt[RS_BINS];
-  __shared__ int64_t base[RS_BINS];
-  const int64_t t0 = (int64_t)blockIdx.x * RS_TILE;
+  __shared__ uint32_t lpre[RS_BINS];
+  __shared__ int64_t gbase[RS_BINS];
+  __shared__ uint64_t skey[RS_TILE];
+  __shared__ int64_t sh[33];
+  __shared__ int64_t tile_sh;
+  if (threadIdx.x == 0) tile_sh = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const int64_t t = tile_sh;
+  const int64_t t0 = t * RS_TILE;
   const int64_t c = n - t0 < RS_TILE ? n - t0 : RS_TILE;
   uint64_t key[RS_ITEMS];
   uint32_t rank[RS_ITEMS];
-  for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) base[b] = off[(int64_t)b * ntiles + blockIdx.x];
-  tile_rank(src, t0, c, shift, key, rank, wcnt, cnt);
+  tile_rank(src, t0, c, shift, mask, key, rank, wcnt, cnt);
+
+  const int b = threadIdx.x;  // RS_THREADS == RS_BINS: one digit per thread
+  const uint64_t v = cnt[b];
+  const uint32_t tag_agg = 2 * pass + 1, tag_inc = 2 * pass + 2;
+  uint64_t excl = 0;
+  if (t == 0) {
+    rs_publish(&status[b], tag_inc, v);
+  } else {
+    rs_publish(&status[t * RS_BINS + b], tag_agg, v);
+    int64_t k = t - 1;
+    long spins = 0;
+    while (k >= 0) {
+      const uint64_t w = *(volatile const uint64_t *)&status[k * RS_BINS + b];
+      const uint32_t tag = (uint32_t)(w >> 56);
+      if (tag == tag_inc || tag == tag_agg) {
+        excl += w & ((1ull << 56) - 1);
+        if (tag == tag_inc) break;
+        --k;
+      } else if (++spins > RS_WAIT_LIMIT) {
+        atomicOr(err, F_TIMEOUT);
+        break;
+      }
+    }
+    rs_publish(&status[t * RS_BINS + b], tag_inc, excl + v);
+  }
+  // Global start of this tile's run of digit b, and b's start inside the tile.
+  const int64_t dpre = block_excl_scan<int64_t>((int64_t)hist[b], sh, (int64_t *)nullptr);
+  const int64_t lp = block_excl_scan<int64_t>(v, sh, (int64_t *)nullptr);
+  gbase[b] = dpre + (int64_t)excl;
+  lpre[b] = (uint32_t)lp;
+  __syncthreads();
   const int w = threadIdx.x >> 5, l = lane_id();
 #pragma unroll
   for (int q = 0; q < RS_ITEMS; ++q) {
-    int64_t idx = (int64_t)w * (32 * RS_ITEMS) + q * 32 + l;
-    if (idx < c) {
-      int64_t p = base[digit_of(key[q], shift)] + rank[q];
-      dst[p] = key[q];
-      if (vsrc) vdst[p] = vsrc[t0 + idx];
-    }
+    const int idx = w * (32 * RS_ITEMS) + q * 32 + l;
+    if (idx < c) skey[lpre[digit_of(key[q], shift, mask)] + rank[q]] = key[q];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < c; i += RS_THREADS) {
+    const uint64_t k = skey[i];
+    const uint32_t d = digit_of(k, shift, mask);
+    dst[gbase[d] + (i - (int64_t)lpre[d])] = k;
   }
 }
 
@@ -319,9 +429,10 @@ static __device__ void cta_radix_sort_global(uint64_t *keys, uint32_t *vals, uin
   const int passes = (nbits + 7) / 8;
   for (int p = 0; p < passes; ++p) {
     const int shift = bit_lo + 8 * p;
+    const uint32_t mask = digit_mask(nbits, p);
     for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) cnt[b] = 0;
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < n; i += RS_THREADS) atomicAdd(&cnt[digit_of(src[i], shift)], 1u);
+    for (int64_t i = threadIdx.x; i < n; i += RS_THREADS) atomicAdd(&cnt[digit_of(src[i], shift, mask)], 1u);
     __syncthreads();
     {
       int64_t v = threadIdx.x < RS_BINS ? (int64_t)cnt[threadIdx.x] : 0;
@@ -333,13 +444,13 @@ static __device__ void cta_radix_sort_global(uint64_t *keys, uint32_t *vals, uin
       int64_t c = n - t0 < RS_TILE ? n - t0 : RS_TILE;
       uint64_t key[RS_ITEMS];
       uint32_t rank[RS_ITEMS];
-      tile_rank(src, t0, c, shift, key, rank, wcnt, cnt);
+      tile_rank(src, t0, c, shift, mask, key, rank, wcnt, cnt);
       const int w = threadIdx.x >> 5, l = lane_id();
 #pragma unroll
       for (int q = 0; q < RS_ITEMS; ++q) {
         int64_t idx = (int64_t)w * (32 * RS_ITEMS) + q * 32 + l;
         if (idx < c) {
-          int64_t pos = base[digit_of(key[q], shift)] + rank[q];
+          int64_t pos = base[digit_of(key[q], shift, mask)] + rank[q];
           dst[pos] = key[q];
           if (vs) vd[pos] = vs[t0 + idx];
         }
@@ -366,52 +477,51 @@ static __global__ void __launch_bounds__(RS_THREADS) k_rs_single(uint64_t *keys,
   cta_radix_sort_global(keys, vals, tkeys, tvals, n, bit_lo, nbits);
 }
 
-// Scratch for radix_sort: temporaries of n keys/vals, histogram and offsets
-// of 256 * ntiles int64 each, scan sums.  The sorted result ends in `keys`.
+// Scratch for radix_sort: a temporary of n keys and rs_meta_bytes(n) bytes
+// (all-digit histogram, tile tickets, per-tile status words).  The sorted
+// result ends in `keys`.  `err`: device flags word for a timed-out wait.
 struct RadixScratch {
   uint64_t *tkeys;
-  uint32_t *tvals;
-  int64_t *hist;
-  int64_t *off;
-  int64_t *bs;
+  uint8_t *meta;
+  int32_t *err;
 };
 inline int64_t rs_tiles(int64_t n) { return (n + RS_TILE - 1) / RS_TILE; }
+constexpr int64_t RS_META_HEAD = RS_MAX_PASSES * RS_BINS * 4 + 256;
+inline int64_t rs_meta_bytes(int64_t n) { return RS_META_HEAD + rs_tiles(n) * RS_BINS * 8; }
 
-// `prof`/`tag`: optional per-kernel timing ("<tag>.hist", ".scan", ".scatter").
-inline vr_status radix_sort(uint64_t *keys, uint32_t *vals, int64_t n, int bit_lo, int nbits, const RadixScratch &sc,
+// `prof`/`tag`: optional per-kernel timing ("<tag>.hist", ".pass").
+inline vr_status radix_sort(uint64_t *keys, int64_t n, int bit_lo, int nbits, const RadixScratch &sc,
                             cudaStream_t s, Prof *prof = nullptr, const char *const *tag = nullptr) {
   if (n <= 1 || nbits <= 0) return VR_OK;
   if (n <= 2 * RS_TILE) {
-    k_rs_single<<<1, RS_THREADS, 0, s>>>(keys, vals, sc.tkeys, sc.tvals, n, bit_lo, nbits);
+    k_rs_single<<<1, RS_THREADS, 0, s>>>(keys, nullptr, sc.tkeys, nullptr, n, bit_lo, nbits);
     count_launch(1);
     VR_CUDA(cudaGetLastError());
     return VR_OK;
   }
   const int64_t nt = rs_tiles(n);
-  uint64_t *src = keys, *dst = sc.tkeys;
-  uint32_t *vs = vals, *vd = vals ? sc.tvals : nullptr;
   const int passes = (nbits + 7) / 8;
+  uint32_t *hist = (uint32_t *)sc.meta;
+  uint32_t *ticket = (uint32_t *)(sc.meta + RS_MAX_PASSES * RS_BINS * 4);
+  uint64_t *status = (uint64_t *)(sc.meta + RS_META_HEAD);
+  int tk_ = prof ? prof->begin(tag[0]) : -1;
+  VR_CUDA(cudaMemsetAsync(sc.meta, 0, (size_t)rs_meta_bytes(n), s));
+  const unsigned hg = (unsigned)(nt < 148 * 8 ? nt : 148 * 8);
+  k_rs_hist_all<<<hg, RS_THREADS, 0, s>>>(keys, n, bit_lo, nbits, hist);
+  count_launch(1);
+  if (prof) prof->end(tk_);
+  uint64_t *src = keys, *dst = sc.tkeys;
   for (int p = 0; p < passes; ++p) {
-    const int shift = bit_lo + 8 * p;
-    int tk_ = prof ? prof->begin(tag[0]) : -1;
-    k_rs_hist<<<(unsigned)nt, RS_THREADS, 0, s>>>(src, n, shift, nt, sc.hist);
-    count_launch(1);
-    if (prof) prof->end(tk_);
     tk_ = prof ? prof->begin(tag[1]) : -1;
-    VR_TRY((scan_exclusive<int64_t, int64_t>(sc.hist, sc.off, RS_BINS * nt, sc.bs, s)));
-    if (prof) prof->end(tk_);
-    tk_ = prof ? prof->begin(tag[2]) : -1;
-    k_rs_scatter<<<(unsigned)nt, RS_THREADS, 0, s>>>(src, vs, dst, vd, n, shift, nt, sc.off);
+    k_rs_onesweep<<<(unsigned)nt, RS_THREADS, 0, s>>>(src, dst, n, bit_lo + 8 * p, digit_mask(nbits, p), p,
+                                                       hist + p * RS_BINS, status,
+                                                       ticket + p, sc.err);
     count_launch(1);
     if (prof) prof->end(tk_);
     VR_CUDA(cudaGetLastError());
     uint64_t *tk = src; src = dst; dst = tk;
-    uint32_t *tv = vs; vs = vd; vd = tv;
   }
-  if (passes & 1) {
-    VR_CUDA(cudaMemcpyAsync(keys, src, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
-    if (vals) VR_CUDA(cudaMemcpyAsync(vals, vs, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
-  }
+  if (passes & 1) VR_CUDA(cudaMemcpyAsync(keys, src, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
   return VR_OK;
 }
 

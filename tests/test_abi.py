@@ -74,3 +74,16 @@ def test_null_arguments():
     assert vr.lib().vr_build(None, 4, 3, vr.VR_I8, 2, 1.0, None, ctypes.byref(h)) == vr.VR_ERR_ARG
     assert vr.lib().vr_complex_dim(None, 0, None) == vr.VR_ERR_ARG
     assert vr.vr_status_string(vr.VR_ERR_RANGE) == "VR_ERR_RANGE"
+
+
+@pytest.mark.parametrize("fn", ["vr_sort_keys", "vr_sort_keys_noalloc"])
+@pytest.mark.parametrize("n,lo,nb,status", [(-1, 0, 8, vr.VR_ERR_ARG), (4, -1, 8, vr.VR_ERR_ARG),
+                                            (4, 60, 5, vr.VR_ERR_ARG), (4, 0, -2, vr.VR_ERR_ARG)])
+def test_sort_argument_checks(fn, n, lo, nb, status):
+    """Bad sort arguments are rejected before any CUDA call."""
+    f = getattr(vr.lib(), fn)
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    buf = np.zeros(8, np.uint64)
+    assert f(ctypes.c_void_p(buf.ctypes.data), n, lo, nb, None) == status
+    assert f(None, 4, 0, 8, None) == vr.VR_ERR_ARG
