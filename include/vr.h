@@ -222,12 +222,17 @@ VR_API vr_status vr_gram_error_check(const float *points, int32_t n, int32_t d,
 
 /* Measurement support (no counterpart in the paper's API; its Sec. 4 profiles
  * with Julia's sampling profiler).  When enabled, every build records a CUDA
- * event pair around each phase on its own stream; once the build's work is
- * done the elapsed times are added to a process-wide table of
- * (phase name, total ms, builds, kernel launches).  Enabling adds one stream
- * synchronisation at the end of each build.  vr_launch_count() is the number
+ * event pair around each phase on its own stream (events from a reused
+ * pool); the elapsed times are added to a process-wide table of
+ * (phase name, total ms, calls, kernel launches) when the table is next read
+ * (vr_profile_phases / vr_profile_phase / vr_profile_reset wait for the
+ * recorded events).  A profiled build adds event records, no
+ * synchronisation.  vr_launch_count() is the number
  * of kernels this library has launched in the process (always counted). */
 VR_API void vr_profile_enable(int32_t on);
+/* Time only the phases named in `names` (comma-separated, e.g.
+ * "tri_final,tri_sort.pass"); NULL or "" times every phase. */
+VR_API void vr_profile_select(const char *names);
 VR_API void vr_profile_reset(void);
 VR_API int32_t vr_profile_phases(void);
 VR_API vr_status vr_profile_phase(int32_t i, const char **name, double *total_ms,

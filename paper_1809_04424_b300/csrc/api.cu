@@ -199,8 +199,7 @@ struct PhaseTotal {
 static std::mutex g_prof_mu;
 static std::vector<PhaseTotal> g_prof;
 
-void profile_add(const char *name, double ms, int64_t launches) {
-  std::lock_guard<std::mutex> lk(g_prof_mu);
+static void profile_add(const char *name, double ms, int64_t launches) {
   for (auto &p : g_prof)
     if (p.name == name) {
       p.ms += ms;
@@ -210,23 +209,90 @@ void profile_add(const char *name, double ms, int64_t launches) {
     }
   g_prof.push_back({name, ms, 1, launches});
 }
+
+static std::vector<std::string> g_filter;
+std::vector<std::string> profile_filter() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  return g_filter;
+}
+
+static std::vector<cudaEvent_t> g_event_pool;
+static std::vector<ProfRec> g_pending;
+
+cudaEvent_t profile_event() {
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_event_pool.empty()) {
+      cudaEvent_t e = g_event_pool.back();
+      g_event_pool.pop_back();
+      return e;
+    }
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    e = nullptr;
+  }
+  return e;
+}
+
+// Read every pending record into the table (waits for its events); with
+// g_prof_mu held.
+static void resolve_pending_locked() {
+  for (auto &r : g_pending) {
+    float ms = 0.f;
+    if (r.a && r.b && cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess)
+      profile_add(r.name, ms, r.launches);
+    if (r.a) g_event_pool.push_back(r.a);
+    if (r.b) g_event_pool.push_back(r.b);
+  }
+  cudaGetLastError();
+  g_pending.clear();
+}
+
+void profile_defer(std::vector<ProfRec> &recs) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_pending.insert(g_pending.end(), recs.begin(), recs.end());
+  if (g_pending.size() > 16384) resolve_pending_locked();  // bound the list
+}
 }  // namespace vr
 
 extern "C" {
 void vr_profile_enable(int32_t on) { vr::g_profile_on.store(on ? 1 : 0); }
 
+void vr_profile_select(const char *names) {
+  std::vector<std::string> f;
+  if (names) {
+    std::string cur;
+    for (const char *c = names;; ++c) {
+      if (*c == ',' || *c == 0) {
+        if (!cur.empty()) f.push_back(cur);
+        cur.clear();
+        if (!*c) break;
+      } else {
+        cur.push_back(*c);
+      }
+    }
+  }
+  std::lock_guard<std::mutex> lk(vr::g_prof_mu);
+  vr::g_filter = f;
+}
+
 void vr_profile_reset(void) {
   std::lock_guard<std::mutex> lk(vr::g_prof_mu);
+  vr::resolve_pending_locked();
   vr::g_prof.clear();
 }
 
 int32_t vr_profile_phases(void) {
   std::lock_guard<std::mutex> lk(vr::g_prof_mu);
+  vr::resolve_pending_locked();
   return (int32_t)vr::g_prof.size();
 }
 
 vr_status vr_profile_phase(int32_t i, const char **name, double *total_ms, int64_t *calls, int64_t *launches) {
   std::lock_guard<std::mutex> lk(vr::g_prof_mu);
+  vr::resolve_pending_locked();
   if (i < 0 || i >= (int32_t)vr::g_prof.size() || !name || !total_ms || !calls || !launches) {
     vr::set_error("profile phase index out of range or NULL argument");
     return VR_ERR_ARG;

@@ -17,17 +17,43 @@
 namespace vr {
 
 // Stream-ordered allocations that are released together (on scope exit for
-// workspaces; handed over to the result for outputs).
+// workspaces; handed over to the result for outputs).  Between begin() and
+// commit() alloc() only records the request; commit() makes one allocation
+// and carves it (256-byte aligned pieces), so a group of arrays costs one
+// allocator call.
 struct Arena {
   cudaStream_t s;
   std::vector<void *> ptrs;
+  bool grouping = false;
+  std::vector<std::pair<void **, size_t>> pend;
   explicit Arena(cudaStream_t st) : s(st) {}
   ~Arena() {
     for (void *p : ptrs) cudaFreeAsync(p, s);
   }
+  void begin() { grouping = true; }
+  vr_status commit() {
+    grouping = false;
+    if (pend.empty()) return VR_OK;
+    size_t total = 0;
+    for (auto &q : pend) total += (q.second + 255) & ~(size_t)255;
+    char *base = nullptr;
+    VR_TRY(alloc(&base, (int64_t)total));
+    size_t at = 0;
+    for (auto &q : pend) {
+      *q.first = base + at;
+      at += (q.second + 255) & ~(size_t)255;
+    }
+    pend.clear();
+    return VR_OK;
+  }
   template <typename T>
   vr_status alloc(T **p, int64_t count) {
     size_t bytes = sizeof(T) * (size_t)std::max<int64_t>(count, 1);
+    if (grouping) {
+      *p = nullptr;
+      pend.push_back({(void **)p, bytes});
+      return VR_OK;
+    }
     cudaError_t e = cudaMallocAsync((void **)p, bytes, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -146,6 +172,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   uint32_t *adj;
   int32_t *adjpre, *deg, *up, *nbr_ptr;
   int64_t *lex_ptr, *bs_small;
+  ws.begin();
   VR_TRY(ws.alloc(&st, 1));
   VR_TRY(F ? ws.alloc((float **)&X, nd) : ws.alloc((int32_t **)&X, nd));
   VR_TRY(ws.alloc(&adj, (int64_t)n * W));
@@ -155,6 +182,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(ws.alloc(&nbr_ptr, n + 1));
   VR_TRY(ws.alloc(&lex_ptr, n + 1));
   VR_TRY(ws.alloc(&bs_small, scan_tmp_slots(n)));
+  VR_TRY(ws.commit());
   VR_CUDA(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
 
   // Stage: convert to the working element type and check values.
@@ -213,26 +241,60 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   int32_t *everts, *egrade, *erow;
   int64_t *ecol, *bs_e;
   double *gval, *d64 = nullptr, *d64_lex = nullptr;
+  // Every E-sized array of the rest of the build: one workspace block and one
+  // output block.
+  ws.begin();
+  out.begin();
   VR_TRY(ws.alloc(&keys, E));
   VR_TRY(ws.alloc(&rs.tkeys, E));
   VR_TRY(ws.alloc(&rs.meta, rs_meta_bytes(E)));
-  rs.err = &st->flags;
   VR_TRY(ws.alloc(&flag, E));
   VR_TRY(ws.alloc(&gex, E + 1));
   VR_TRY(ws.alloc(&bs_e, scan_tmp_slots(E)));
   VR_TRY(ws.alloc(&nbr_ord, 2 * E));
+  int32_t *eidx = nullptr;  // dense (i, j) -> order index table for small clouds
+  if (n <= DENSE_MAX_N && maxdim >= 2) VR_TRY(ws.alloc(&eidx, (int64_t)n * n));
   VR_TRY(ws.alloc(&gstart, E + 2));
   VR_TRY(out.alloc(&everts, 2 * E));
   VR_TRY(out.alloc(&egrade, E));
   VR_TRY(out.alloc(&ecol, E + 1));
   VR_TRY(out.alloc(&erow, 2 * E));
   VR_TRY(out.alloc(&gval, E + 1));
+  if (F && E > 0) VR_TRY(ws.alloc(&d64_lex, E));
+  int32_t *split = nullptr, *gbeg = nullptr, *midq = nullptr, *bigq = nullptr;
+  uint64_t *k1 = nullptr, *k2 = nullptr, *gk = nullptr;
+  uint32_t *v1 = nullptr, *v2 = nullptr;
+  double *gd = nullptr;
+  if (F && E > 0) {
+    VR_TRY(ws.alloc(&d64, E));
+    VR_TRY(ws.alloc(&split, E));
+    VR_TRY(ws.alloc(&gbeg, E + 1));
+    VR_TRY(ws.alloc(&midq, E));
+    VR_TRY(ws.alloc(&bigq, E));
+    VR_TRY(ws.alloc(&k1, E));
+    VR_TRY(ws.alloc(&k2, E));
+    VR_TRY(ws.alloc(&gk, E));
+    VR_TRY(ws.alloc(&v1, E));
+    VR_TRY(ws.alloc(&v2, E));
+    VR_TRY(ws.alloc(&gd, E));
+  }
+  int32_t *tcnt = nullptr, *tsmallq = nullptr, *tmidq = nullptr, *tbigq = nullptr;
+  int64_t *toff = nullptr;
+  if (maxdim >= 2 && E > 0) {
+    VR_TRY(ws.alloc(&tcnt, E));
+    VR_TRY(ws.alloc(&toff, E + 1));
+    VR_TRY(ws.alloc(&tsmallq, E + 1));
+    VR_TRY(ws.alloc(&tmidq, E + 1));
+    VR_TRY(ws.alloc(&tbigq, E + 1));
+  }
+  VR_TRY(ws.commit());
+  VR_TRY(out.commit());
+  rs.err = &st->flags;
 
   const unsigned ge = grid_for(E, 256);
   if (E > 0) {
     prof.begin("edge_keys");
     if constexpr (F) {
-      VR_TRY(ws.alloc(&d64_lex, E));
       k_edge_keys_f32<<<(n + 7) / 8, 256, 0, s>>>((const float *)X, n, d, W, adj, lex_ptr, keys, d64_lex, st);
     } else {
       k_edge_keys<F><<<(n + 7) / 8, 256, 0, s>>>(X, n, d, W, adj, lex_ptr, keys);
@@ -255,15 +317,6 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     prof.end();
 
     if (F) {
-      int32_t *split, *gbeg, *midq, *bigq;
-      uint64_t *k1, *k2, *gk;
-      uint32_t *v1, *v2;
-      double *gd;
-      VR_TRY(ws.alloc(&d64, E));
-      VR_TRY(ws.alloc(&split, E));
-      VR_TRY(ws.alloc(&gbeg, E + 1));
-      VR_TRY(ws.alloc(&midq, E));
-      VR_TRY(ws.alloc(&bigq, E));
       prof.begin("fp64_repair");
       count_launch(6);
       int tkf = prof.begin("fp64_values");
@@ -276,12 +329,6 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       k_repair_small<<<ge, 256, 0, s>>>(gbeg, gex + E, keys, d64, midq, bigq, st);
       VR_CUDA(cudaGetLastError());
       k_repair_mid<<<296, 256, 0, s>>>(gbeg, midq, st, keys, d64);
-      VR_TRY(ws.alloc(&k1, E));
-      VR_TRY(ws.alloc(&k2, E));
-      VR_TRY(ws.alloc(&gk, E));
-      VR_TRY(ws.alloc(&v1, E));
-      VR_TRY(ws.alloc(&v2, E));
-      VR_TRY(ws.alloc(&gd, E));
       k_repair_big<<<1, RS_THREADS, 0, s>>>(gbeg, bigq, st, keys, d64, k1, v1, k2, v2, gk, gd);
       VR_CUDA(cudaGetLastError());
       prof.end(tkr);
@@ -292,7 +339,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int32_t>(flag, gex, E, bs_e, s)));
     k_edge_emit<F><<<ge, 256, 0, s>>>(keys, d64, E, flag, gex, adj, adjpre, W, nbr_ptr, everts, egrade, ecol, erow,
-                                      gval, gstart, nbr_ord, st);
+                                      gval, gstart, nbr_ord, eidx, n, st);
     VR_CUDA(cudaGetLastError());
     prof.end();
   } else {
@@ -302,14 +349,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_CUDA(cudaMemcpyAsync(ecol, &zero64, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   }
 
-  int32_t *tcnt = nullptr, *tsmallq = nullptr, *tmidq = nullptr, *tbigq = nullptr;
-  int64_t *toff = nullptr;
   if (maxdim >= 2 && E > 0) {
-    VR_TRY(ws.alloc(&tcnt, E));
-    VR_TRY(ws.alloc(&toff, E + 1));
-    VR_TRY(ws.alloc(&tsmallq, E + 1));
-    VR_TRY(ws.alloc(&tmidq, E + 1));
-    VR_TRY(ws.alloc(&tbigq, E + 1));
     prof.begin("tri_count");
     k_tri_count<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, E, adj, adjpre, W, nbr_ptr, nbr_ord, deg, up,
                                                            lex_ptr, st, tcnt);
@@ -330,34 +370,57 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     return VR_ERR_RANGE;
   }
 
-  // Vertices.
+  // Vertex and triangle outputs (one block) and the T-sized workspace.
+  const bool lexm = T > 0 && lex_mode(E, ngrades);
+  const bool bigfix = T > 0 && !lexm && hst->big_seg_count > 0;
   int32_t *vverts, *vgrade;
-  VR_TRY(out.alloc(&vverts, n));
-  VR_TRY(out.alloc(&vgrade, n));
-  k_vertices<<<grid_for(n, 256), 256, 0, s>>>(n, vverts, vgrade);
-  count_launch();
-  VR_CUDA(cudaGetLastError());
-
   int32_t *tverts = nullptr, *tgrade = nullptr, *trow = nullptr;
   int64_t *tcol = nullptr;
+  uint64_t *tk = nullptr, *tk1 = nullptr, *tk2 = nullptr;
+  uint32_t *tv1 = nullptr, *tv2 = nullptr;
+  int32_t *rtmp = nullptr;
+  RadixScratch trs{};
+  out.begin();
+  ws.begin();
+  VR_TRY(out.alloc(&vverts, n));
+  VR_TRY(out.alloc(&vgrade, n));
   if (maxdim >= 2) {
     VR_TRY(out.alloc(&tverts, 3 * T));
     VR_TRY(out.alloc(&tgrade, T));
     VR_TRY(out.alloc(&tcol, T + 1));
     VR_TRY(out.alloc(&trow, 3 * T));
-    const int64_t tlast = 3 * T;
-    VR_CUDA(cudaMemcpyAsync(tcol + T, &tlast, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    if (T > 0 && lex_mode(E, ngrades)) {
+  }
+  if (lexm) {
+    VR_TRY(ws.alloc(&tk, T));
+    VR_TRY(ws.alloc(&trs.tkeys, T));
+    VR_TRY(ws.alloc(&trs.meta, rs_meta_bytes(T)));
+  }
+  if (bigfix) {
+    VR_TRY(ws.alloc(&tk1, T));
+    VR_TRY(ws.alloc(&tk2, T));
+    VR_TRY(ws.alloc(&tv1, T));
+    VR_TRY(ws.alloc(&tv2, T));
+    VR_TRY(ws.alloc(&rtmp, 3 * T));
+  }
+  VR_TRY(out.commit());
+  VR_TRY(ws.commit());
+  trs.err = &st->flags;
+  // Vertices (and the triangles' closing colptr entry 3T).
+  k_vertices<<<grid_for(n, 256), 256, 0, s>>>(n, vverts, vgrade, tcol, T);
+  count_launch();
+  VR_CUDA(cudaGetLastError());
+
+  if (maxdim >= 2) {
+    if (lexm) {
       // Lex-order generation, stable sort on the grade bits, final write.
-      uint64_t *tk;
-      RadixScratch trs{};
-      VR_TRY(ws.alloc(&tk, T));
-      VR_TRY(ws.alloc(&trs.tkeys, T));
-      VR_TRY(ws.alloc(&trs.meta, rs_meta_bytes(T)));
-      trs.err = &st->flags;
       prof.begin("tri_lex_gen");
-      k_lex_tri_gen<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr, nbr_ord, deg,
-                                                             up, lex_ptr, toff, T, tk, st);
+      const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, W, n};
+      if (eidx)
+        k_lex_tri_gen<true><<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr,
+                                                                     nbr_ord, deg, up, lex_ptr, toff, T, tk, ex, st);
+      else
+        k_lex_tri_gen<false><<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr,
+                                                                      nbr_ord, deg, up, lex_ptr, toff, T, tk, ex, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();
@@ -367,7 +430,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
                         ttag));
       prof.end();
       prof.begin("tri_final");
-      k_tri_final<<<grid_for(T, 256), 256, 0, s>>>(tk, T, adj, adjpre, W, nbr_ptr, nbr_ord, tverts, tgrade, tcol, trow);
+      if (eidx) k_tri_final<true><<<grid_for((T + 3) / 4, 256), 256, 0, s>>>(tk, T, ex, tverts, tgrade, tcol, trow);
+      else k_tri_final<false><<<grid_for((T + 3) / 4, 256), 256, 0, s>>>(tk, T, ex, tverts, tgrade, tcol, trow);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();
@@ -395,17 +459,9 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
         count_launch();
         VR_CUDA(cudaGetLastError());
       }
-      if (hst->big_seg_count > 0) {
-        uint64_t *k1, *k2;
-        uint32_t *v1, *v2;
-        int32_t *rtmp;
-        VR_TRY(ws.alloc(&k1, T));
-        VR_TRY(ws.alloc(&k2, T));
-        VR_TRY(ws.alloc(&v1, T));
-        VR_TRY(ws.alloc(&v2, T));
-        VR_TRY(ws.alloc(&rtmp, 3 * T));
+      if (bigfix) {
         k_tri_fix_big<<<(unsigned)std::min<int64_t>(hst->big_seg_count, 148 * 2), RS_THREADS, 0, s>>>(
-            gstart, toff, tbigq, st, tverts, trow, k1, v1, k2, v2, rtmp);
+            gstart, toff, tbigq, st, tverts, trow, tk1, tv1, tk2, tv2, rtmp);
         count_launch();
         VR_CUDA(cudaGetLastError());
       }

@@ -675,7 +675,8 @@ template <bool F>
 __global__ void k_edge_emit(const uint64_t *keys, const double *d64, int64_t E, const int32_t *flag,
                             const int32_t *gex, const uint32_t *adj, const int32_t *adjpre, int W,
                             const int32_t *nbr_ptr, int32_t *verts, int32_t *grade, int64_t *colptr, int32_t *rowidx,
-                            double *gval, int32_t *gstart, int32_t *nbr_ord, DevStatus *st) {
+                            double *gval, int32_t *gstart, int32_t *nbr_ord, int32_t *eidx, int n,
+                            DevStatus *st) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = keys[k];
     const int i = key_i(key), j = key_j(key);
@@ -692,6 +693,7 @@ __global__ void k_edge_emit(const uint64_t *keys, const double *d64, int64_t E, 
     }
     nbr_ord[nbr_ptr[i] + bit_rank(adj + (int64_t)i * W, adjpre + (int64_t)i * W, j)] = (int32_t)k;
     nbr_ord[nbr_ptr[j] + bit_rank(adj + (int64_t)j * W, adjpre + (int64_t)j * W, i)] = (int32_t)k;
+    if (eidx) eidx[(int64_t)i * n + j] = (int32_t)k;  // dense order-index table (i < j), small n only
     if (k == E - 1) {
       colptr[E] = 2 * E;
       gstart[g + 1] = (int32_t)E;
@@ -704,7 +706,8 @@ __global__ void k_edge_emit(const uint64_t *keys, const double *d64, int64_t E, 
   }
 }
 
-static __global__ void k_vertices(int n, int32_t *verts, int32_t *grade) {
+static __global__ void k_vertices(int n, int32_t *verts, int32_t *grade, int64_t *tcol, int64_t T) {
+  if (tcol && blockIdx.x == 0 && threadIdx.x == 0) tcol[T] = 3 * T;  // closing colptr entry of dimension 2
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     verts[v] = v;
     grade[v] = 0;
@@ -740,6 +743,23 @@ __device__ __forceinline__ int64_t lex_pos(int a, int b, const uint32_t *adj, co
                                            const int32_t *deg, const int32_t *up, const int64_t *lex_ptr) {
   return lex_ptr[a] + bit_rank(adj + (int64_t)a * W, adjpre + (int64_t)a * W, b) - (deg[a] - up[a]);
 }
+
+// Order index of kept edge (a, b), a < b: from the dense table when there is
+// one (n <= DENSE_MAX_N), else through the neighbour CSR.
+constexpr int DENSE_MAX_N = 4096;
+struct EdgeIndex {
+  const uint32_t *adj;
+  const int32_t *adjpre;
+  const int32_t *nbr_ptr;
+  const int32_t *nbr_ord;
+  const int32_t *eidx;
+  int W, n;
+  template <bool DENSE>
+  __device__ __forceinline__ int32_t ord(int a, int b) const {
+    if constexpr (DENSE) return eidx[(int64_t)a * n + b];
+    else return nbr_ord[nbr_ptr[a] + bit_rank(adj + (int64_t)a * W, adjpre + (int64_t)a * W, b)];
+  }
+};
 
 static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts, int64_t E, const uint32_t *adj,
                                                           const int32_t *adjpre, int W, const int32_t *nbr_ptr,
@@ -790,12 +810,14 @@ static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts,
 // ascending, land at toff[lex position of (a, b)]; the key carries the
 // triangle's grade (largest of its three edge grades).  Coalesced chunked
 // stores as in k_tri_emit.
+template <bool DENSE>
 static __global__ void __launch_bounds__(256) k_lex_tri_gen(const int32_t *everts, const int32_t *egrade, int64_t E,
                                                             const uint32_t *adj, const int32_t *adjpre, int W,
                                                             const int32_t *nbr_ptr, const int32_t *nbr_ord,
                                                             const int32_t *deg, const int32_t *up,
                                                             const int64_t *lex_ptr, const int64_t *toff,
-                                                            int64_t T, uint64_t *tkeys, DevStatus *st) {
+                                                            int64_t T, uint64_t *tkeys, EdgeIndex ex,
+                                                            DevStatus *st) {
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
@@ -827,9 +849,15 @@ static __global__ void __launch_bounds__(256) k_lex_tri_gen(const int32_t *evert
           const int bit = __fns(ovm, 0, q - oex + 1);
           const int ww = w0 + owner;
           const int cv = ww * 32 + bit;
-          const uint32_t below = (1u << bit) - 1u;
-          const int32_t gac = egrade[oa[pa[ww] + __popc(ra[ww] & below)]];
-          const int32_t gbc = egrade[ob[pb[ww] + __popc(rb[ww] & below)]];
+          int32_t gac, gbc;
+          if constexpr (DENSE) {
+            gac = egrade[ex.ord<true>(a, cv)];
+            gbc = egrade[ex.ord<true>(b, cv)];
+          } else {
+            const uint32_t below = (1u << bit) - 1u;
+            gac = egrade[oa[pa[ww] + __popc(ra[ww] & below)]];
+            gbc = egrade[ob[pb[ww] + __popc(rb[ww] & below)]];
+          }
           const int32_t g = max(gab, max(gac, gbc));
           if (t + q < T) tkeys[t + q] = ((uint64_t)g << LEX_SHIFT) | lex3(a, b, cv);
           else raise_flag(st, F_INTERNAL);  // never write past the key array
@@ -842,28 +870,51 @@ static __global__ void __launch_bounds__(256) k_lex_tri_gen(const int32_t *evert
 
 // Final write of lex-mode triangles, sorted by (grade, a, b, c): verts,
 // grade, colptr and the boundary column (order indices of the three faces,
-// ascending), one thread per triangle so stores are coalesced.
-static __global__ void k_tri_final(const uint64_t *tkeys, int64_t T, const uint32_t *adj, const int32_t *adjpre,
-                                   int W, const int32_t *nbr_ptr, const int32_t *nbr_ord, int32_t *tverts,
-                                   int32_t *tgrade, int64_t *tcolptr, int32_t *trow) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T; p += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t k = tkeys[p];
-    const int a = (int)((k >> (2 * ID_BITS)) & ID_MASK), b = (int)((k >> ID_BITS) & ID_MASK), c = (int)(k & ID_MASK);
-    const int32_t *ra = adjpre + (int64_t)a * W, *rb = adjpre + (int64_t)b * W;
-    const uint32_t *wa = adj + (int64_t)a * W, *wb = adj + (int64_t)b * W;
-    int32_t o0 = nbr_ord[nbr_ptr[a] + bit_rank(wa, ra, b)];  // (a, b)
-    int32_t o1 = nbr_ord[nbr_ptr[a] + bit_rank(wa, ra, c)];  // (a, c)
-    int32_t o2 = nbr_ord[nbr_ptr[b] + bit_rank(wb, rb, c)];  // (b, c)
-    int32_t lo = min(o0, min(o1, o2)), hi = max(o0, max(o1, o2));
-    int32_t mid = o0 + o1 + o2 - lo - hi;
-    tverts[3 * p] = a;
-    tverts[3 * p + 1] = b;
-    tverts[3 * p + 2] = c;
-    tgrade[p] = (int32_t)(k >> LEX_SHIFT);
+// ascending).  Four consecutive triangles per thread, written with 16-byte
+// stores (the output arrays start 16-byte aligned); a scalar tail.
+__device__ __forceinline__ void tri_final_one(uint64_t k, const EdgeIndex &ex, int32_t *v, int32_t *r, int32_t &g,
+                                              bool dense) {
+  const int a = (int)((k >> (2 * ID_BITS)) & ID_MASK), b = (int)((k >> ID_BITS) & ID_MASK), c = (int)(k & ID_MASK);
+  const int32_t o0 = dense ? ex.ord<true>(a, b) : ex.ord<false>(a, b);
+  const int32_t o1 = dense ? ex.ord<true>(a, c) : ex.ord<false>(a, c);
+  const int32_t o2 = dense ? ex.ord<true>(b, c) : ex.ord<false>(b, c);
+  const int32_t lo = min(o0, min(o1, o2)), hi = max(o0, max(o1, o2));
+  v[0] = a; v[1] = b; v[2] = c;
+  r[0] = lo; r[1] = o0 + o1 + o2 - lo - hi; r[2] = hi;
+  g = (int32_t)(k >> LEX_SHIFT);
+}
+
+template <bool DENSE>
+static __global__ void __launch_bounds__(256) k_tri_final(const uint64_t *tkeys, int64_t T, EdgeIndex ex,
+                                                          int32_t *tverts, int32_t *tgrade, int64_t *tcolptr,
+                                                          int32_t *trow) {
+  const int64_t T4 = T / 4, stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < T4; q += stride) {
+    const ulonglong2 k01 = ((const ulonglong2 *)tkeys)[2 * q], k23 = ((const ulonglong2 *)tkeys)[2 * q + 1];
+    int32_t v[12], r[12], g[4];
+    tri_final_one(k01.x, ex, v, r, g[0], DENSE);
+    tri_final_one(k01.y, ex, v + 3, r + 3, g[1], DENSE);
+    tri_final_one(k23.x, ex, v + 6, r + 6, g[2], DENSE);
+    tri_final_one(k23.y, ex, v + 9, r + 9, g[3], DENSE);
+    int4 *tv = (int4 *)(tverts + 12 * q), *tr = (int4 *)(trow + 12 * q);
+    tv[0] = make_int4(v[0], v[1], v[2], v[3]);
+    tv[1] = make_int4(v[4], v[5], v[6], v[7]);
+    tv[2] = make_int4(v[8], v[9], v[10], v[11]);
+    tr[0] = make_int4(r[0], r[1], r[2], r[3]);
+    tr[1] = make_int4(r[4], r[5], r[6], r[7]);
+    tr[2] = make_int4(r[8], r[9], r[10], r[11]);
+    ((int4 *)tgrade)[q] = make_int4(g[0], g[1], g[2], g[3]);
+    const long long c0 = 12 * q;
+    ((longlong2 *)tcolptr)[2 * q] = make_longlong2(c0, c0 + 3);
+    ((longlong2 *)tcolptr)[2 * q + 1] = make_longlong2(c0 + 6, c0 + 9);
+  }
+  for (int64_t p = 4 * T4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T; p += stride) {
+    int32_t v[3], r[3], g;
+    tri_final_one(tkeys[p], ex, v, r, g, DENSE);
+    tverts[3 * p] = v[0]; tverts[3 * p + 1] = v[1]; tverts[3 * p + 2] = v[2];
+    trow[3 * p] = r[0]; trow[3 * p + 1] = r[1]; trow[3 * p + 2] = r[2];
+    tgrade[p] = g;
     tcolptr[p] = 3 * p;
-    trow[3 * p] = lo;
-    trow[3 * p + 1] = mid;
-    trow[3 * p + 2] = hi;
   }
 }
 

@@ -159,10 +159,14 @@ static __global__ void __launch_bounds__(1024) k_scan_sums(int64_t *bs, int64_t 
 constexpr int64_t SCAN_SELF_MAX = 2048;
 
 // self_off: bs holds raw chunk sums; the CTA adds up those before its chunk.
+// Shared-memory slot of chunk element t: one pad word per SCAN_ITEMS so that a
+// thread's run of SCAN_ITEMS consecutive elements does not sit in one bank.
+__device__ __forceinline__ int scan_slot(int t) { return t + t / SCAN_ITEMS; }
+
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(const TI *in, int64_t L, const int64_t *bs, TO *out,
                                                              int self_off) {
-  __shared__ int64_t buf[SCAN_CHUNK];
+  __shared__ int64_t buf[SCAN_CHUNK + SCAN_CHUNK / SCAN_ITEMS];
   __shared__ int64_t sh[33];
   __shared__ int64_t off_sh;
   const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
@@ -176,7 +180,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(const TI *in, int64
   }
   for (int t = threadIdx.x; t < SCAN_CHUNK; t += SCAN_THREADS) {
     int64_t i = base + t;
-    buf[t] = i < L ? (int64_t)in[i] : 0;
+    buf[scan_slot(t)] = i < L ? (int64_t)in[i] : 0;
   }
   __syncthreads();
   int64_t loc[SCAN_ITEMS];
@@ -184,18 +188,18 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(const TI *in, int64
 #pragma unroll
   for (int q = 0; q < SCAN_ITEMS; ++q) {
     loc[q] = s;
-    s += buf[threadIdx.x * SCAN_ITEMS + q];
+    s += buf[scan_slot(threadIdx.x * SCAN_ITEMS + q)];
   }
   __syncthreads();
   int64_t tot;
   const int64_t off = !bs ? 0 : self_off ? off_sh : bs[blockIdx.x];
   int64_t pre = block_excl_scan<int64_t>(s, sh, &tot) + off;
 #pragma unroll
-  for (int q = 0; q < SCAN_ITEMS; ++q) buf[threadIdx.x * SCAN_ITEMS + q] = pre + loc[q];
+  for (int q = 0; q < SCAN_ITEMS; ++q) buf[scan_slot(threadIdx.x * SCAN_ITEMS + q)] = pre + loc[q];
   __syncthreads();
   for (int t = threadIdx.x; t < SCAN_CHUNK; t += SCAN_THREADS) {
     int64_t i = base + t;
-    if (i < L) out[i] = (TO)buf[t];
+    if (i < L) out[i] = (TO)buf[scan_slot(t)];
   }
   if (threadIdx.x == 0 && base + SCAN_CHUNK >= L) out[L] = (TO)(off + tot);
 }
@@ -246,6 +250,19 @@ __host__ __device__ inline uint32_t digit_mask(int nbits, int p) {
   return b >= 8 ? 0xffu : (1u << b) - 1u;
 }
 
+// Lanes of the warp holding the same 9-bit value v (v <= 256; 256 marks an
+// empty lane): one ballot per bit, full-rate votes instead of match.any.
+__device__ __forceinline__ uint32_t warp_peers9(uint32_t v) {
+  uint32_t m = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    const bool bit = (v >> b) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+    m &= bit ? bal : ~bal;
+  }
+  return m;
+}
+
 // Rank the keys of one tile (positions [t0, t0 + cnt) of src).  On return
 // rank[q] holds, for the lane's q-th key, its position among equal digits in
 // the tile, and sh_cnt[d] the tile's count of digit d.  Keys are read by warp
@@ -268,7 +285,7 @@ __device__ __forceinline__ void tile_rank(const uint64_t *src, int64_t t0, int64
     int64_t idx = (int64_t)w * (32 * RS_ITEMS) + q * 32 + l;
     bool ok = idx < cnt;
     uint32_t dg = ok ? digit_of(key[q], shift, mask) : RS_BINS;  // sentinel for empty lanes
-    uint32_t peers = __match_any_sync(0xffffffffu, dg);
+    uint32_t peers = warp_peers9(dg);
     uint32_t before = ok ? sh_wcnt[w][dg] : 0;
     rank[q] = before + __popc(peers & lt);
     __syncwarp();
@@ -324,7 +341,7 @@ static __global__ void __launch_bounds__(RS_THREADS) k_rs_hist_all(const uint64_
       for (int q = 0; q < RS_ITEMS; ++q) {
         const bool ok = t0 + q * RS_THREADS + threadIdx.x < n;
         const uint32_t dg = ok ? digit_of(k[q], shift, mask) : RS_BINS;
-        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        const uint32_t peers = warp_peers9(dg);
         if (ok && (peers & lt) == 0) atomicAdd(&h[p][dg], (uint32_t)__popc(peers));
       }
     }

@@ -143,6 +143,16 @@ def test_max_size_sampled(torch):
     check(torch, pts, 2, 9.0)
 
 
+@pytest.mark.parametrize("n", [4096, 4097])
+def test_dense_edge_table_boundary(torch, n):
+    """Lex-order triangles on both sides of the dense edge-index table's size
+    limit (4096 points: table; 4097: neighbour CSR)."""
+    g = synth.rng(4096 + n)
+    pts = g.integers(-20, 21, size=(n, 3)).astype(np.int8)
+    c = check(torch, pts, 2, 4.0)
+    assert len(c[2]["grade"]) > 10000
+
+
 def test_value_errors(torch):
     bad = np.zeros((5, 2), np.float32)
     bad[2, 1] = np.nan
