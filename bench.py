@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -67,6 +68,37 @@ def roofline_bytes(cloud, E, T):
     }
 
 
+def sources_hash():
+    """sha1 prefix over the CUDA sources and the C header (the key under which
+    ncu traffic figures are recorded)."""
+    import glob
+    import hashlib
+    h = hashlib.sha1()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1809_04424_b300", "csrc", "*"))) + \
+            [os.path.join(ROOT, "include", "vr.h")]:
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(region, workload):
+    """DRAM bytes per launch (read + write) of `region` on `workload` from a
+    profile summary's 'traffic:' line, if it was taken on the current
+    sources; else None."""
+    import glob
+    cur = sources_hash()
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        with open(f) as fh:
+            for line in fh:
+                if not line.startswith("traffic:"):
+                    continue
+                kv = dict(x.split("=", 1) for x in line.split()[1:] if "=" in x)
+                if kv.get("region") == region and kv.get("workload") == workload and kv.get("sources") == cur:
+                    return int(kv["bytes_per_launch"])
+    return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -77,16 +109,91 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the run."""
+    """SM clock and throttle-reason samples taken DURING the timed region:
+    NVML polled from a thread about every millisecond (reads only), else
+    nvidia-smi at 20 ms."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+            "hw_thermal_slowdown": 0x40, "hw_power_brake_slowdown": 0x80}
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.p = None
+        self.nv = None
+        self.samples = []
+        self.max_mhz = None
+        self.out = ""
+
+    def _nvml_handle(self):
+        """NVML through ctypes on the driver's libnvidia-ml (queries only)."""
+        import ctypes
+        import torch
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        want = ""
+        try:
+            want = str(torch.cuda.get_device_properties(self.gpu).uuid).replace("GPU-", "")
+        except Exception:
+            pass
+        cnt = ctypes.c_uint()
+        lib.nvmlDeviceGetCount_v2(ctypes.byref(cnt))
+        pick = None
+        for i in range(cnt.value):
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(i, ctypes.byref(h)) != 0:
+                continue
+            buf = ctypes.create_string_buffer(96)
+            lib.nvmlDeviceGetUUID(h, buf, 96)
+            if want and want in buf.value.decode():
+                pick = h
+                break
+        if pick is None:
+            pick = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(self.gpu, ctypes.byref(pick)) != 0:
+                raise RuntimeError("no NVML handle")
+        reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+        def clock(kind_max=False):
+            v = ctypes.c_uint()
+            f = lib.nvmlDeviceGetMaxClockInfo if kind_max else lib.nvmlDeviceGetClockInfo
+            if f(pick, 1, ctypes.byref(v)) != 0:  # 1 = NVML_CLOCK_SM
+                raise RuntimeError("clock query failed")
+            return float(v.value)
+
+        def reasons():
+            v = ctypes.c_ulonglong()
+            reasons_fn(pick, ctypes.byref(v))
+            return int(v.value)
+
+        return clock, reasons
 
     def __enter__(self):
+        try:
+            clock, reasons = self._nvml_handle()
+            self.nv = (clock, reasons)
+            self.max_mhz = clock(True)
+            self.stop = threading.Event()
+
+            def poll():
+                while not self.stop.is_set():
+                    try:
+                        self.samples.append((clock(), reasons()))
+                    except Exception:
+                        pass
+                    time.sleep(0.001)
+
+            self.th = threading.Thread(target=poll, daemon=True)
+            self.th.start()
+            t0 = time.time()
+            while not self.samples and time.time() - t0 < 2:  # start with one sample in hand
+                time.sleep(0.0005)
+            return self
+        except Exception:
+            self.nv = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "20"],
@@ -96,7 +203,14 @@ class Clocks:
         return self
 
     def __exit__(self, *a):
-        self.out = ""
+        if self.nv is not None:
+            try:
+                self.samples.append((self.nv[0](), self.nv[1]()))
+            except Exception:
+                pass
+            self.stop.set()
+            self.th.join(timeout=2)
+            return False
         if self.p:
             self.p.terminate()
             try:
@@ -106,6 +220,14 @@ class Clocks:
         return False
 
     def summary(self):
+        if self.nv is not None and self.samples:
+            reasons = set()
+            for _, r in self.samples:
+                for nm, bit in self.BITS.items():
+                    if r & bit:
+                        reasons.add(nm)
+            return {"sm_mhz": statistics.median(c for c, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                    "reasons": sorted(reasons), "samples": len(self.samples), "source": "nvml"}
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in (self.out or "").splitlines():
@@ -123,7 +245,7 @@ class Clocks:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": "nvidia-smi"}
 
 
 def dist_env():
@@ -530,7 +652,7 @@ def main():
             tp["ms_per_call"] / max(tp["launches_per_call"], 1)
         ach = per_launch_bytes[dom] / (per_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "peak_source": src,
+                "frac": ach / hbm, "traffic": recorded_traffic(dom, args.config), "peak_source": src,
                 "algorithmic_bytes_per_launch": per_launch_bytes[dom],
                 "launch_ms": per_launch_ms, "launches_timed": tp["calls"]}
 
