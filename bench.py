@@ -42,6 +42,8 @@ WORKLOADS = {
     "plain64": ("uniform int32 n=64 d=3 in [-100,100], no cap, maxdim 2", lambda: synth.config1(), "int64"),
     "gauss32": ("8-Gaussian mixture n=4000 d=32 float32, cap at 5th-pct d^2, maxdim 2",
                 lambda: synth.config3(), "f64"),
+    "worldmap": ("WorldMap-shaped n=7322 d=3 float32 on the unit sphere (7 blobs + uniform), cap 0.15, maxdim 2",
+                 lambda: synth.worldmap(), "f64"),
 }
 METRIC = "VR simplices/s"
 

@@ -178,6 +178,26 @@ def config5(n_requests: int = 20000, rate_per_s: float = 1000.0, seed: int = 180
 
 # ----------------------------------------------------------------- test clouds
 
+def worldmap(n: int = 7322, maxdim: int = 2, seed: int = 1809 + 6) -> Cloud:
+    """WorldMap-shaped single cloud: n = 7322 float32 points on the unit
+    sphere, cap 0.15 (the paper's WorldMap run).  The city coordinates are
+    not available; the stand-in clusters like land masses: 70 % of the points
+    from 7 blobs (centres uniform on the sphere, N(0, 0.25^2) offsets,
+    projected back to the sphere), 30 % uniform on the sphere."""
+    g = rng(seed)
+    k = 7
+    centres = g.normal(size=(k, 3))
+    centres /= np.linalg.norm(centres, axis=1, keepdims=True)
+    m = int(round(0.7 * n))
+    lab = g.integers(0, k, size=m)
+    a = centres[lab] + g.normal(scale=0.25, size=(m, 3))
+    b = g.normal(size=(n - m, 3))
+    p = np.concatenate([a, b])
+    p /= np.linalg.norm(p, axis=1, keepdims=True)
+    p = p[g.permutation(n)]
+    return Cloud(p.astype(np.float32), maxdim, 0.15)
+
+
 def random_cloud(n: int, d: int, dtype, seed: int, lo=-100, hi=100) -> np.ndarray:
     g = rng(seed)
     if np.dtype(dtype) == np.float32:

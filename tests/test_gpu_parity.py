@@ -153,6 +153,15 @@ def test_dense_edge_table_boundary(torch, n):
     assert len(c[2]["grade"]) > 10000
 
 
+def test_worldmap_shaped_cloud(torch):
+    """The WorldMap-shaped single cloud (n = 7322 float32 on the unit sphere,
+    cap 0.15): 280,777 edges and 5,878,554 triangles, in full."""
+    c = synth.worldmap()
+    g = check(torch, c.points, 2, c.maxrad)
+    assert g["counts"] == [7322, 280777, 5878554]
+    assert g["stats"]["max_rel_dist_err"] <= 1e-6
+
+
 def test_value_errors(torch):
     bad = np.zeros((5, 2), np.float32)
     bad[2, 1] = np.nan
