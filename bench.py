@@ -44,7 +44,25 @@ WORKLOADS = {
                 lambda: synth.config3(), "f64"),
     "worldmap": ("WorldMap-shaped n=7322 d=3 float32 on the unit sphere (7 blobs + uniform), cap 0.15, maxdim 2",
                  lambda: synth.worldmap(), "f64"),
+    "hiv": ("HIV-shaped 1088x1088 int32 Hamming distance matrix (9 subtypes), cap at its 10th percentile, maxdim 2",
+            lambda: synth.hiv(), "int64"),
 }
+
+
+def oracle_build(cloud):
+    import oracle
+    if isinstance(cloud, synth.Matrix):
+        return oracle.vr_build_dmat(cloud.points, cloud.maxdim, cloud.maxrad)
+    return oracle.vr_build(cloud.points, cloud.maxdim, cloud.maxrad)
+
+
+def gpu_build(cloud, src, **kw):
+    import paper_1809_04424_b300 as vr
+    if isinstance(cloud, synth.Matrix):
+        if "d" in kw:
+            kw.pop("d")
+        return vr.vr_build_dmat(src, cloud.maxdim, cloud.maxrad, **kw)
+    return vr.vr_build(src, cloud.maxdim, cloud.maxrad, **kw)
 METRIC = "VR simplices/s"
 
 # Algorithmic bytes per unit of each phase.
@@ -264,7 +282,7 @@ def oracle_rate(cloud, seconds: float):
     reps, t0 = 0, time.perf_counter()
     simp = 0
     while True:
-        cx = oracle.vr_build(cloud.points, cloud.maxdim, cloud.maxrad)
+        cx = oracle_build(cloud)
         simp += sum(d.count for d in cx.dims)
         reps += 1
         el = time.perf_counter() - t0
@@ -282,11 +300,11 @@ def run_reference(args):
     WORKLOAD, make, dtype_name = WORKLOADS[args.config]
     cloud = make()
     for _ in range(args.warmup):
-        oracle.vr_build(cloud.points, cloud.maxdim, cloud.maxrad)
+        oracle_build(cloud)
     t0 = time.perf_counter()
     simp = 0
     for _ in range(args.steps):
-        cx = oracle.vr_build(cloud.points, cloud.maxdim, cloud.maxrad)
+        cx = oracle_build(cloud)
         simp += sum(d.count for d in cx.dims)
     el = time.perf_counter() - t0
     v = simp / el
@@ -528,8 +546,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step():
-        c = vr.vr_build(pts_dev, cloud.maxdim, cloud.maxrad)
-        return c
+        return gpu_build(cloud, pts_dev)
 
     for _ in range(W):
         c = step()
@@ -603,7 +620,7 @@ def main():
 
     # ---- e2e: host (pinned) points in, every output array back to pinned host.
     host_pts = torch.from_numpy(cloud.points).pin_memory()
-    c0 = vr.vr_build(pts_dev, cloud.maxdim, cloud.maxrad)
+    c0 = gpu_build(cloud, pts_dev)
     cnt, _ = c0.counts()
     del c0
     bufs = []
@@ -618,7 +635,7 @@ def main():
 
     def e2e_step():
         nonlocal gv
-        c = vr.vr_build(host_pts.data_ptr(), cloud.maxdim, cloud.maxrad, n=cloud.n, d=cloud.d,
+        c = gpu_build(cloud, host_pts.data_ptr(), n=cloud.n, d=cloud.d,
                         dtype=cloud.dtype_code)
         for k in range(3):
             b = bufs[k]

@@ -118,6 +118,26 @@ VR_API vr_status vr_build(const void *points, int32_t n, int32_t d, vr_dtype dty
                    int32_t maxdim, double maxrad, vr_stream_t stream,
                    vr_complex **out);
 
+/* Build the filtered complex of a square symmetric matrix of edge values
+ * (Sec. 3: Eirene takes a point cloud or a square symmetric matrix, typically
+ * of pairwise distances, e.g. Hamming distances between sequences).
+ *   D       n x n row-major, VR_I32 or VR_F32 (else VR_ERR_ARG), device or
+ *           host memory (detected and copied in on `stream`).  Borrowed until
+ *           the call returns.
+ *   n       1 .. VR_MAX_POINTS, else VR_ERR_RANGE.
+ *   maxdim  0 .. 2 as for vr_build.
+ *   maxrad  inclusive cap on the VALUE (keep D[i][j] <= maxrad, no squaring);
+ *           +INFINITY keeps every pair.
+ * Edges come from the strict upper triangle (i < j); the diagonal is ignored
+ * (vertices at grade 0).  Grades rank the values themselves: dense rank over
+ * {0} U {kept values}; grade_values() returns the values.  Every entry must
+ * be finite and non-negative and D[i][j] == D[j][i] exactly (-0 counts as
+ * 0); otherwise VR_ERR_ARG, found on the device.  Other behaviour as vr_build
+ * (ownership, sizes, errors); the build statistics' near-tie and distance
+ * error fields are 0 (the keys are the exact values). */
+VR_API vr_status vr_build_dmat(const void *D, int32_t n, vr_dtype dtype, int32_t maxdim,
+                               double maxrad, vr_stream_t stream, vr_complex **out);
+
 /* Fill `view` for dimension k (0 <= k <= maxdim, else VR_ERR_ARG). */
 VR_API vr_status vr_complex_dim(const vr_complex *c, int32_t k, vr_dim_view *view);
 

@@ -68,6 +68,9 @@ def _open(path):
                               ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                               ctypes.POINTER(_Complex)]
     lib.vro_build.restype = ctypes.c_int
+    lib.vro_build_dmat.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.c_double, ctypes.c_void_p]
+    lib.vro_build_dmat.restype = ctypes.c_int
     lib.vro_free.argtypes = [ctypes.POINTER(_Complex)]
     lib.vro_pair_d2.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                 ctypes.c_int32, ctypes.c_int32]
@@ -168,6 +171,33 @@ def vr_build(points: np.ndarray, maxdim: int, maxrad: float = float("inf"),
     rc = lib.vro_build(pts.ctypes.data, n, d, _dtype_code(pts), maxdim, float(maxrad), ctypes.byref(c))
     if rc:
         raise OracleError(rc)
+    return _wrap(lib, c, n, maxdim, keep_handle)
+
+
+def vr_build_dmat(D: np.ndarray, maxdim: int, maxrad: float = float("inf"),
+                  keep_handle: bool = False) -> Complex:
+    """Build the filtered complex of a square symmetric (n, n) matrix of edge
+    values (int32 or float32): edges from the strict upper triangle, kept iff
+    value <= maxrad, grades ranking the values."""
+    lib = _load()
+    m = np.ascontiguousarray(D)
+    if m.ndim != 2 or m.shape[0] != m.shape[1]:
+        raise ValueError("D must be (n, n)")
+    if m.dtype == np.int32:
+        code = 2
+    elif m.dtype == np.float32:
+        code = 3
+    else:
+        raise ValueError("D must be int32 or float32")
+    n = m.shape[0]
+    c = _Complex()
+    rc = lib.vro_build_dmat(m.ctypes.data, n, code, maxdim, float(maxrad), ctypes.byref(c))
+    if rc:
+        raise OracleError(rc)
+    return _wrap(lib, c, n, maxdim, keep_handle)
+
+
+def _wrap(lib, c, n, maxdim, keep_handle):
     cx = Complex(n=n, maxdim=maxdim)
     for k in range(maxdim + 1):
         cnt = c.count[k]

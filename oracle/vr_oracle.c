@@ -160,63 +160,15 @@ void vro_free(vro_complex *c) {
 
 void vro_free_buf(void *p) { free(p); }
 
-int vro_build(const void *pts, int32_t n, int32_t d, int32_t dtype,
-              int32_t maxdim, double maxrad, vro_complex *out) {
-  if (!out) return ERR_ARG;
-  clear(out);
-  if (!pts || n < 1 || d < 1) return ERR_ARG;
-  if (dtype != VRO_I8 && dtype != VRO_I32 && dtype != VRO_F32) return ERR_ARG;
-  if (maxdim < 0) return ERR_ARG;
-  if (maxdim > VRO_MAXDIM) return ERR_UNSUPPORTED;
-  if (isnan(maxrad) || maxrad < 0.0) return ERR_ARG;
-  const int is_float = (dtype == VRO_F32);
-  if (is_float)
-    for (int64_t t = 0; t < (int64_t)n * d; ++t)
-      if (!isfinite(((const float *)pts)[t])) return ERR_ARG;
-
-  out->n = n;
-  out->d = d;
-  out->maxdim = maxdim;
-
-  /* Step 6: vertices in id order, all at grade 0. */
-  out->count[0] = n;
-  out->verts[0] = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
-  out->grade[0] = (int32_t *)calloc((size_t)n, sizeof(int32_t));
-  if (!out->verts[0] || !out->grade[0]) { vro_free(out); return ERR_OOM; }
-  for (int32_t v = 0; v < n; ++v) out->verts[0][v] = v;
-
-  /* Steps 1-2: every pair i<j, its squared distance, kept iff d^2 <= r^2.
-   * Float: r2 = fl(maxrad*maxrad).  Integer: r2i = floor(fl(maxrad*maxrad)),
-   * which for an integer d^2 is the same test. */
-  const double r2 = maxrad * maxrad;
-  const int keep_all = isinf(r2);
-  u128 r2i = 0;
-  int keep_all_int = keep_all;
-  if (!is_float && !keep_all) {
-    double f = floor(r2);
-    if (f >= 3.0e38) keep_all_int = 1; else r2i = (u128)f;
-  }
-  int64_t npairs = (int64_t)n * (n - 1) / 2;
-  int32_t *ei = (int32_t *)malloc(sizeof(int32_t) * (size_t)(npairs + 1));
-  int32_t *ej = (int32_t *)malloc(sizeof(int32_t) * (size_t)(npairs + 1));
-  u128 *di = is_float ? NULL : (u128 *)malloc(sizeof(u128) * (size_t)(npairs + 1));
-  double *df = is_float ? (double *)malloc(sizeof(double) * (size_t)(npairs + 1)) : NULL;
+/* Steps 3-7 from the kept pairs (ei[t] < ej[t], value di[t] (integer) or
+ * df[t] (float), t < m, in (i, j) order).  Takes ownership of the four
+ * arrays. */
+static int finish_build(vro_complex *out, int32_t n, int32_t maxdim, int is_float, int32_t *ei, int32_t *ej,
+                        u128 *di, double *df, int64_t m) {
   int32_t *eg = NULL;
-  if (!ei || !ej || (!di && !df)) goto oom_pairs;
-  int64_t m = 0;
-  for (int32_t i = 0; i < n; ++i)
-    for (int32_t j = i + 1; j < n; ++j) {
-      if (is_float) {
-        double v = d2_f32((const float *)pts, d, i, j);
-        if (keep_all || v <= r2) { ei[m] = i; ej[m] = j; df[m] = v; ++m; }
-      } else {
-        u128 v = d2_int(pts, d, dtype, i, j);
-        if (keep_all_int || v <= r2i) { ei[m] = i; ej[m] = j; di[m] = v; ++m; }
-      }
-    }
-
-  /* Step 3: grade of an edge = rank of its d^2 in the sorted distinct set
-   * {0} U {kept d^2}; grade_value[g] = the g-th member. */
+  /* Step 3: grade of an edge = rank of its value (d^2 for points) in the
+   * sorted distinct set {0} U {kept values}; grade_value[g] = the g-th
+   * member. */
   eg = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m + 1));
   int64_t ng = 0;
   if (!eg) goto oom_pairs;
@@ -340,6 +292,128 @@ oom_pairs:
   free(eg); free(ei); free(ej); free(di); free(df);
   vro_free(out);
   return ERR_OOM;
+}
+
+int vro_build(const void *pts, int32_t n, int32_t d, int32_t dtype,
+              int32_t maxdim, double maxrad, vro_complex *out) {
+  if (!out) return ERR_ARG;
+  clear(out);
+  if (!pts || n < 1 || d < 1) return ERR_ARG;
+  if (dtype != VRO_I8 && dtype != VRO_I32 && dtype != VRO_F32) return ERR_ARG;
+  if (maxdim < 0) return ERR_ARG;
+  if (maxdim > VRO_MAXDIM) return ERR_UNSUPPORTED;
+  if (isnan(maxrad) || maxrad < 0.0) return ERR_ARG;
+  const int is_float = (dtype == VRO_F32);
+  if (is_float)
+    for (int64_t t = 0; t < (int64_t)n * d; ++t)
+      if (!isfinite(((const float *)pts)[t])) return ERR_ARG;
+
+  out->n = n;
+  out->d = d;
+  out->maxdim = maxdim;
+
+  /* Step 6: vertices in id order, all at grade 0. */
+  out->count[0] = n;
+  out->verts[0] = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  out->grade[0] = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+  if (!out->verts[0] || !out->grade[0]) { vro_free(out); return ERR_OOM; }
+  for (int32_t v = 0; v < n; ++v) out->verts[0][v] = v;
+
+  /* Steps 1-2: every pair i<j, its squared distance, kept iff d^2 <= r^2.
+   * Float: r2 = fl(maxrad*maxrad).  Integer: r2i = floor(fl(maxrad*maxrad)),
+   * which for an integer d^2 is the same test. */
+  const double r2 = maxrad * maxrad;
+  const int keep_all = isinf(r2);
+  u128 r2i = 0;
+  int keep_all_int = keep_all;
+  if (!is_float && !keep_all) {
+    double f = floor(r2);
+    if (f >= 3.0e38) keep_all_int = 1; else r2i = (u128)f;
+  }
+  int64_t npairs = (int64_t)n * (n - 1) / 2;
+  int32_t *ei = (int32_t *)malloc(sizeof(int32_t) * (size_t)(npairs + 1));
+  int32_t *ej = (int32_t *)malloc(sizeof(int32_t) * (size_t)(npairs + 1));
+  u128 *di = is_float ? NULL : (u128 *)malloc(sizeof(u128) * (size_t)(npairs + 1));
+  double *df = is_float ? (double *)malloc(sizeof(double) * (size_t)(npairs + 1)) : NULL;
+  if (!ei || !ej || (!di && !df)) goto oom_pairs;
+  int64_t m = 0;
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t j = i + 1; j < n; ++j) {
+      if (is_float) {
+        double v = d2_f32((const float *)pts, d, i, j);
+        if (keep_all || v <= r2) { ei[m] = i; ej[m] = j; df[m] = v; ++m; }
+      } else {
+        u128 v = d2_int(pts, d, dtype, i, j);
+        if (keep_all_int || v <= r2i) { ei[m] = i; ej[m] = j; di[m] = v; ++m; }
+      }
+    }
+
+  return finish_build(out, n, maxdim, is_float, ei, ej, di, df, m);
+
+oom_pairs:
+  free(ei); free(ej); free(di); free(df);
+  vro_free(out);
+  return ERR_OOM;
+}
+
+/* Distance-matrix input (the paper's Sec. 3: Eirene also takes a square
+ * symmetric matrix, typically of pairwise distances).  Readings: the strict
+ * upper triangle D[i][j], i < j, gives the edge values; the matrix must be
+ * exactly symmetric with finite non-negative entries; the diagonal is
+ * ignored (vertices at grade 0); an edge is kept iff D[i][j] <= maxrad; the
+ * grades rank the values themselves (no squaring), grade_value[g] = the g-th
+ * distinct value of {0} U {kept values}. */
+int vro_build_dmat(const void *D, int32_t n, int32_t dtype, int32_t maxdim, double maxrad, vro_complex *out) {
+  if (!out) return ERR_ARG;
+  clear(out);
+  if (!D || n < 1) return ERR_ARG;
+  if (dtype != VRO_I32 && dtype != VRO_F32) return ERR_ARG;
+  if (maxdim < 0) return ERR_ARG;
+  if (maxdim > VRO_MAXDIM) return ERR_UNSUPPORTED;
+  if (isnan(maxrad) || maxrad < 0.0) return ERR_ARG;
+  const int is_float = (dtype == VRO_F32);
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t j = 0; j < n; ++j) {
+      if (is_float) {
+        const float v = ((const float *)D)[(int64_t)i * n + j], w = ((const float *)D)[(int64_t)j * n + i];
+        if (!isfinite(v) || v < 0.0f || v != w) return ERR_ARG;
+      } else {
+        const int32_t v = ((const int32_t *)D)[(int64_t)i * n + j], w = ((const int32_t *)D)[(int64_t)j * n + i];
+        if (v < 0 || v != w) return ERR_ARG;
+      }
+    }
+  out->n = n;
+  out->d = 0;
+  out->maxdim = maxdim;
+  out->count[0] = n;
+  out->verts[0] = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  out->grade[0] = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+  if (!out->verts[0] || !out->grade[0]) { vro_free(out); return ERR_OOM; }
+  for (int32_t v = 0; v < n; ++v) out->verts[0][v] = v;
+  const int64_t npairs = (int64_t)n * (n - 1) / 2;
+  int32_t *ei = (int32_t *)malloc(sizeof(int32_t) * (size_t)(npairs + 1));
+  int32_t *ej = (int32_t *)malloc(sizeof(int32_t) * (size_t)(npairs + 1));
+  u128 *di = is_float ? NULL : (u128 *)malloc(sizeof(u128) * (size_t)(npairs + 1));
+  double *df = is_float ? (double *)malloc(sizeof(double) * (size_t)(npairs + 1)) : NULL;
+  if (!ei || !ej || (!di && !df)) {
+    free(ei); free(ej); free(di); free(df);
+    vro_free(out);
+    return ERR_OOM;
+  }
+  int64_t m = 0;
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t j = i + 1; j < n; ++j) {
+      const double v = is_float ? (double)((const float *)D)[(int64_t)i * n + j]
+                                : (double)((const int32_t *)D)[(int64_t)i * n + j];
+      if (v <= maxrad) {
+        ei[m] = i;
+        ej[m] = j;
+        if (is_float) df[m] = v;
+        else di[m] = (u128)((const int32_t *)D)[(int64_t)i * n + j];
+        ++m;
+      }
+    }
+  return finish_build(out, n, maxdim, is_float, ei, ej, di, df, m);
 }
 
 /* ------------------------------------------------------------------ step 8 */

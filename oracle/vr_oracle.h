@@ -58,6 +58,12 @@ int vro_build(const void *pts, int32_t n, int32_t d, int32_t dtype,
               int32_t maxdim, double maxrad, vro_complex *out);
 void vro_free(vro_complex *c);
 
+/* The same complex from a square symmetric n x n matrix of edge values
+ * (host, row-major, VRO_I32 or VRO_F32): the strict upper triangle gives the
+ * edges, kept iff value <= maxrad; grades rank the values (no squaring).
+ * Asymmetric, negative or non-finite entries: a bad-argument code. */
+int vro_build_dmat(const void *D, int32_t n, int32_t dtype, int32_t maxdim, double maxrad, vro_complex *out);
+
 /* Squared distance of one pair, as step 1 defines it (integer: exact, as a
  * double that is exact below 2^53; float: canonical FP64 sequence). */
 double vro_pair_d2(const void *pts, int32_t d, int32_t dtype, int32_t i,

@@ -181,6 +181,34 @@ def vr_build(points, maxdim: int, maxrad: float = float("inf"), stream=None, n=N
     return Complex(h.value)
 
 
+def vr_build_dmat(D, maxdim: int, maxrad: float = float("inf"), stream=None, n=None, dtype=None) -> Complex:
+    """Build the filtered complex of a square symmetric (n, n) matrix of edge
+    values (int32 or float32; CUDA tensor, numpy array, or raw pointer with
+    n and dtype).  The cap applies to the values themselves."""
+    if hasattr(D, "data_ptr"):
+        if not D.is_contiguous():
+            raise ValueError("D must be contiguous")
+        ptr, n0, code = D.data_ptr(), D.shape[0], _dtype_code(D.dtype)
+        if D.dim() != 2 or D.shape[1] != n0:
+            raise ValueError("D must be (n, n)")
+    elif isinstance(D, np.ndarray):
+        keep = np.ascontiguousarray(D)
+        if keep.ndim != 2 or keep.shape[0] != keep.shape[1]:
+            raise ValueError("D must be (n, n)")
+        ptr, n0, code = keep.ctypes.data, keep.shape[0], _dtype_code(keep.dtype)
+    else:
+        ptr, n0, code = int(D), n, dtype
+    L = lib()
+    L.vr_build_dmat.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int, ctypes.c_int32, ctypes.c_double,
+                                ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    L.vr_build_dmat.restype = ctypes.c_int
+    h = ctypes.c_void_p()
+    s = _current_stream() if stream is None else stream
+    _check(L.vr_build_dmat(ctypes.c_void_p(ptr), int(n0), code, int(maxdim), float(maxrad), ctypes.c_void_p(s),
+                           ctypes.byref(h)))
+    return Complex(h.value)
+
+
 def vr_complex_dim(handle, k: int) -> DimView:
     v = DimView()
     _check(lib().vr_complex_dim(ctypes.c_void_p(handle), k, ctypes.byref(v)))

@@ -117,6 +117,46 @@ vr_status vr_build(const void *points, int32_t n, int32_t d, vr_dtype dtype, int
   return VR_OK;
 }
 
+vr_status vr_build_dmat(const void *D, int32_t n, vr_dtype dtype, int32_t maxdim, double maxrad,
+                        vr_stream_t stream, vr_complex **out) {
+  g_err[0] = 0;
+  if (!out) { set_error("out is NULL"); return VR_ERR_ARG; }
+  *out = nullptr;
+  if (!D) { set_error("D is NULL"); return VR_ERR_ARG; }
+  if (dtype != VR_I32 && dtype != VR_F32) { set_error("matrix dtype %d: VR_I32 or VR_F32", (int)dtype); return VR_ERR_ARG; }
+  if (n < 1 || n > VR_MAX_POINTS) { set_error("n = %d outside [1, %d]", n, VR_MAX_POINTS); return VR_ERR_RANGE; }
+  if (maxdim < 0) { set_error("maxdim = %d is negative", maxdim); return VR_ERR_ARG; }
+  if (maxdim > VR_MAX_DIM_SIMPLEX) { set_error("maxdim = %d above %d is not offered", maxdim, VR_MAX_DIM_SIMPLEX); return VR_ERR_UNSUPPORTED; }
+  if (std::isnan(maxrad) || maxrad < 0.0) { set_error("maxrad must be >= 0 and not NaN"); return VR_ERR_ARG; }
+  keep_pool_warm();
+  cudaStream_t s = (cudaStream_t)stream;
+  vr_complex *res = new (std::nothrow) vr_complex();
+  if (!res) { set_error("host allocation failed"); return VR_ERR_OOM; }
+  cudaGetDevice(&res->device);
+  const void *dm = D;
+  void *staged = nullptr;
+  const size_t bytes = (size_t)n * n * 4;
+  if (!is_device_pointer(D)) {
+    if (cudaMallocAsync(&staged, bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      delete res;
+      set_error("device allocation for the matrix copy failed");
+      return VR_ERR_OOM;
+    }
+    cudaMemcpyAsync(staged, D, bytes, cudaMemcpyHostToDevice, s);
+    dm = staged;
+  }
+  vr_status st = build_dmat(dm, n, dtype, maxdim, maxrad, s, res);
+  if (staged) cudaFreeAsync(staged, s);
+  if (st != VR_OK) {
+    for (void *p : res->allocs) cudaFreeAsync(p, s);
+    delete res;
+    return st;
+  }
+  *out = res;
+  return VR_OK;
+}
+
 vr_status vr_complex_dim(const vr_complex *c, int32_t k, vr_dim_view *v) {
   if (!c || !v) { set_error("NULL argument"); return VR_ERR_ARG; }
   if (k < 0 || k > c->maxdim) { set_error("dimension %d outside [0, %d]", k, c->maxdim); return VR_ERR_ARG; }

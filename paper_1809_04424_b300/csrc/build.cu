@@ -134,8 +134,10 @@ static void dist_dispatch(const void *X, int n, int d, int W, const Cap &cap, ui
 }
 
 template <bool F>
+// `dmat` non-null: the edge values come from that n x n device matrix
+// (dtype VR_I32 or VR_F32 = its element type; d and dpts unused, F false).
 static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dtype, int32_t maxdim, double maxrad,
-                            cudaStream_t s, vr_complex *res) {
+                            cudaStream_t s, vr_complex *res, const void *dmat = nullptr) {
   DevStatus *hst = pinned_status();
   if (!hst) {
     set_error("pinned host status buffer allocation failed");
@@ -167,6 +169,25 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     }
   }
 
+  // Matrix input: keep iff key <= capkey (int: floor(maxrad); float: the
+  // bits of the largest float <= maxrad).
+  const bool dmf = dmat && dtype == VR_F32;
+  int dm_keep_all = std::isinf(maxrad) ? 1 : 0;
+  uint32_t capkey = 0;
+  if (dmat && !dm_keep_all) {
+    if (dmf) {
+      if (maxrad >= 3.4028234663852886e38) dm_keep_all = 1;
+      else {
+        float f = (float)maxrad;
+        if ((double)f > maxrad) f = std::nextafter(f, -INFINITY);
+        memcpy(&capkey, &f, 4);
+      }
+    } else {
+      const double f = std::floor(maxrad);
+      capkey = f >= 2147483647.0 ? 0x7fffffffu : (uint32_t)f;
+    }
+  }
+
   DevStatus *st;
   void *X;
   uint32_t *adj;
@@ -188,7 +209,11 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   // Stage: convert to the working element type and check values.
   prof.begin("stage");
   const unsigned gs = grid_for(nd, 256, 148 * 8);
-  if (dtype == VR_I8) k_stage<int8_t, false><<<gs, 256, 0, s>>>((const int8_t *)dpts, nd, (int32_t *)X, st);
+  if (dmat) {
+    const int nb = (n + 31) / 32;
+    if (dmf) k_dmat_check<true><<<nb * nb, 256, 0, s>>>(dmat, n, st);
+    else k_dmat_check<false><<<nb * nb, 256, 0, s>>>(dmat, n, st);
+  } else if (dtype == VR_I8) k_stage<int8_t, false><<<gs, 256, 0, s>>>((const int8_t *)dpts, nd, (int32_t *)X, st);
   else if (dtype == VR_I32) k_stage<int32_t, false><<<gs, 256, 0, s>>>((const int32_t *)dpts, nd, (int32_t *)X, st);
   else k_stage<float, true><<<gs, 256, 0, s>>>((const float *)dpts, nd, (float *)X, st);
   count_launch();
@@ -196,8 +221,12 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   prof.end();
 
   prof.begin("distance");
-  const bool tc = gram_tc_eligible(dtype, n, d);
-  if (tc) {
+  const bool tc = !dmat && gram_tc_eligible(dtype, n, d);
+  if (dmat) {
+    if (dmf) k_dmat_bitmap<true><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, dm_keep_all, capkey, adj);
+    else k_dmat_bitmap<false><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, dm_keep_all, capkey, adj);
+    count_launch();
+  } else if (tc) {
     VR_TRY(gram_bitmap_tc(X, n, d, F, cap, adj, st, s, nullptr));  // tensor-core Gram tiles
   } else {
     dist_dispatch<F>(X, n, d, W, cap, adj, st, s);
@@ -296,6 +325,9 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     prof.begin("edge_keys");
     if constexpr (F) {
       k_edge_keys_f32<<<(n + 7) / 8, 256, 0, s>>>((const float *)X, n, d, W, adj, lex_ptr, keys, d64_lex, st);
+    } else if (dmat) {
+      if (dmf) k_dmat_keys<true><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, adj, lex_ptr, keys);
+      else k_dmat_keys<false><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, adj, lex_ptr, keys);
     } else {
       k_edge_keys<F><<<(n + 7) / 8, 256, 0, s>>>(X, n, d, W, adj, lex_ptr, keys);
     }
@@ -306,6 +338,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     // alone yields (distance, i, j).
     int kbits;
     if (F) kbits = 31;
+    else if (dmat) kbits = dm_keep_all ? 31 : std::max(1, bitlen(capkey));
     else {
       uint64_t bound = dtype == VR_I8 ? (uint64_t)d * 255ull * 255ull : INT_KEY_LIMIT - 1;
       if (!cap.keep_all) bound = std::min(bound, cap.r2i);
@@ -339,7 +372,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int32_t>(flag, gex, E, bs_e, s)));
     k_edge_emit<F><<<ge, 256, 0, s>>>(keys, d64, E, flag, gex, adj, adjpre, W, nbr_ptr, everts, egrade, ecol, erow,
-                                      gval, gstart, nbr_ord, eidx, n, st);
+                                      gval, gstart, nbr_ord, eidx, n, dmf ? 1 : 0, st);
     VR_CUDA(cudaGetLastError());
     prof.end();
   } else {
@@ -500,6 +533,11 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   res->stats.max_rel_dist_err = F ? mre : 0.0;
   out.release_to(res->allocs);
   return VR_OK;
+}
+
+vr_status build_dmat(const void *D, int32_t n, vr_dtype dtype, int32_t maxdim, double maxrad, cudaStream_t s,
+                     vr_complex *res) {
+  return build_impl<false>(nullptr, n, 0, dtype, maxdim, maxrad, s, res, D);
 }
 
 vr_status build_cloud(const void *dpts, int32_t n, int32_t d, vr_dtype dtype, int32_t maxdim, double maxrad,

@@ -29,6 +29,8 @@ struct vr_complex {
 namespace vr {
 // Keep stream-ordered pool memory reserved between calls (once per device).
 void keep_pool_warm();
+vr_status build_dmat(const void *D, int32_t n, vr_dtype dtype, int32_t maxdim, double maxrad, cudaStream_t s,
+                     vr_complex *res);
 vr_status build_cloud(const void *dpts, int32_t n, int32_t d, vr_dtype dtype, int32_t maxdim, double maxrad,
                       cudaStream_t s, vr_complex *res);
 }

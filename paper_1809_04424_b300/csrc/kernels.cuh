@@ -383,6 +383,98 @@ __global__ void __launch_bounds__(256) k_edge_keys(const void *Xv, int n, int d,
   }
 }
 
+// ------------------------------------------------- distance-matrix input
+// A square symmetric n x n matrix of edge values (int32, or float32 whose
+// keys are the bits of the value: order-preserving for non-negative floats,
+// -0 folded onto +0).  The strict upper triangle gives the edges.
+
+template <bool F>
+__device__ __forceinline__ uint32_t dmat_key(const void *Dv, int64_t idx) {
+  if constexpr (F) return __float_as_uint(((const float *)Dv)[idx]) & 0x7fffffffu;
+  else return (uint32_t)((const int32_t *)Dv)[idx];
+}
+
+// Value checks on 32 x 32 tiles: finite, non-negative, D[i][j] == D[j][i].
+template <bool F>
+static __global__ void __launch_bounds__(256) k_dmat_check(const void *Dv, int n, DevStatus *st) {
+  __shared__ float tf[32][33];
+  __shared__ int32_t ti[32][33];
+  const int nb = (n + 31) / 32;
+  const int bi = blockIdx.x / nb, bj = blockIdx.x % nb;
+  if (bi > bj) return;  // the tile pair (bi, bj) and its transpose, once
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  // Load the transposed tile D[bj*32 + r][bi*32 + c].
+  for (int r = ty; r < 32; r += 8) {
+    const int gi = bj * 32 + r, gj = bi * 32 + tx;
+    if (gi < n && gj < n) {
+      if constexpr (F) tf[r][tx] = ((const float *)Dv)[(int64_t)gi * n + gj];
+      else ti[r][tx] = ((const int32_t *)Dv)[(int64_t)gi * n + gj];
+    }
+  }
+  __syncthreads();
+  bool bad = false, nonfinite = false;
+  for (int r = ty; r < 32; r += 8) {
+    const int gi = bi * 32 + r, gj = bj * 32 + tx;
+    if (gi < n && gj < n) {
+      if constexpr (F) {
+        const float v = ((const float *)Dv)[(int64_t)gi * n + gj];
+        if (!isfinite(v)) nonfinite = true;
+        else if (v < 0.0f || v != tf[tx][r]) bad = true;
+      } else {
+        const int32_t v = ((const int32_t *)Dv)[(int64_t)gi * n + gj];
+        if (v < 0 || v != ti[tx][r]) bad = true;
+      }
+    }
+  }
+  if (__any_sync(0xffffffffu, nonfinite) && tx == 0) raise_flag(st, F_NONFINITE);
+  if (__any_sync(0xffffffffu, bad) && tx == 0) raise_flag(st, F_DMAT);
+}
+
+// Kept-edge bitmap: warp per row, one ballot per 32 columns (the matrix is
+// symmetric, so rows give both halves).  keep iff key <= capkey (or all).
+template <bool F>
+static __global__ void __launch_bounds__(256) k_dmat_bitmap(const void *Dv, int n, int W, int keep_all,
+                                                            uint32_t capkey, uint32_t *adj) {
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5), l = lane_id();
+  if (i >= n) return;
+  for (int w = 0; w < W; ++w) {
+    const int j = w * 32 + l;
+    bool keep = false;
+    if (j < n && j != i) keep = keep_all || dmat_key<F>(Dv, (int64_t)i * n + j) <= capkey;
+    const uint32_t b = __ballot_sync(0xffffffffu, keep);
+    if (l == 0) adj[(int64_t)i * W + w] = b;
+  }
+}
+
+// Edge keys in lexicographic order, warp per row (the walk of k_edge_keys
+// with the matrix entry as the value).
+template <bool F>
+static __global__ void __launch_bounds__(256) k_dmat_keys(const void *Dv, int n, int W, const uint32_t *adj,
+                                                          const int64_t *lex_ptr, uint64_t *keys) {
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int l = lane_id();
+  if (i >= n) return;
+  const uint32_t *row = adj + (int64_t)i * W;
+  int64_t t = lex_ptr[i];
+  for (int w0 = (i + 1) >> 5; w0 < W; w0 += 32) {
+    const int w = w0 + l;
+    const uint32_t word = w < W ? row[w] & above_mask(i, w) : 0u;
+    const BitChunk r = bit_round(word);
+    for (int q0 = 0; q0 < r.tot; q0 += 32) {
+      const int q = q0 + l;
+      const int ow = bit_owner(r, q);
+      const uint32_t om = __shfl_sync(0xffffffffu, word, ow);
+      const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
+      if (q < r.tot) {
+        const int j = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
+        const uint64_t dk = dmat_key<F>(Dv, (int64_t)i * n + j);
+        keys[t + q] = (dk << KEY_SHIFT) | ((uint64_t)i << ID_BITS) | (uint64_t)j;
+      }
+    }
+    t += r.tot;
+  }
+}
+
 // Float edge keys, in lexicographic order: warp per row i, 32 candidates per
 // chunk (one per lane).  The chunk's 32 candidate rows are staged through
 // shared memory 32 coordinates at a time with coalesced loads; each lane then
@@ -676,7 +768,7 @@ __global__ void k_edge_emit(const uint64_t *keys, const double *d64, int64_t E, 
                             const int32_t *gex, const uint32_t *adj, const int32_t *adjpre, int W,
                             const int32_t *nbr_ptr, int32_t *verts, int32_t *grade, int64_t *colptr, int32_t *rowidx,
                             double *gval, int32_t *gstart, int32_t *nbr_ord, int32_t *eidx, int n,
-                            DevStatus *st) {
+                            int key_f32, DevStatus *st) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = keys[k];
     const int i = key_i(key), j = key_j(key);
@@ -688,7 +780,8 @@ __global__ void k_edge_emit(const uint64_t *keys, const double *d64, int64_t E, 
     colptr[k] = 2 * k;
     grade[k] = g;
     if (flag[k]) {
-      gval[g] = F ? d64[k] : (double)(key >> KEY_SHIFT);
+      gval[g] = F ? d64[k]
+                  : key_f32 ? (double)__uint_as_float((uint32_t)(key >> KEY_SHIFT)) : (double)(key >> KEY_SHIFT);
       gstart[g] = (int32_t)k;
     }
     nbr_ord[nbr_ptr[i] + bit_rank(adj + (int64_t)i * W, adjpre + (int64_t)i * W, j)] = (int32_t)k;

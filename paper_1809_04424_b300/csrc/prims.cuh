@@ -38,6 +38,7 @@ enum : int32_t {
   F_INTERNAL = 8,    // invariant violated                    -> VR_ERR_INTERNAL
   F_TIMEOUT = 16,    // a bounded wait gave up                -> VR_ERR_TIMEOUT
   F_OVERFLOW = 32,   // an output arena was too small         -> retried by host
+  F_DMAT = 64,       // distance matrix asymmetric or negative -> VR_ERR_ARG
 };
 
 // Device-resident status and counters of one build (read back at sync points).
@@ -63,7 +64,8 @@ __device__ __forceinline__ void raise_flag(DevStatus *st, int32_t f) { atomicOr(
 
 inline vr_status flags_to_status(int32_t f) {
   if (f & F_INTERNAL) { set_error("internal invariant violated on the device"); return VR_ERR_INTERNAL; }
-  if (f & F_NONFINITE) { set_error("non-finite float coordinate"); return VR_ERR_ARG; }
+  if (f & F_NONFINITE) { set_error("non-finite float value"); return VR_ERR_ARG; }
+  if (f & F_DMAT) { set_error("distance matrix is not symmetric or has a negative entry"); return VR_ERR_ARG; }
   if (f & F_F32_RANGE) { set_error("float coordinate magnitude above 2^50"); return VR_ERR_RANGE; }
   if (f & F_INT_KEY) { set_error("integer squared distance of a kept edge is >= 2^38"); return VR_ERR_RANGE; }
   if (f & F_TIMEOUT) { set_error("a bounded device wait timed out"); return VR_ERR_TIMEOUT; }

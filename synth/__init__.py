@@ -41,6 +41,26 @@ class Cloud:
                 np.dtype(np.float32): F32}[self.points.dtype]
 
 
+@dataclass
+class Matrix:
+    """A square symmetric matrix of edge values as the input."""
+    points: np.ndarray   # (n, n) int32 / float32, row-major
+    maxdim: int
+    maxrad: float
+
+    @property
+    def n(self) -> int:
+        return self.points.shape[0]
+
+    @property
+    def d(self) -> int:
+        return 0
+
+    @property
+    def dtype_code(self) -> int:
+        return {np.dtype(np.int32): I32, np.dtype(np.float32): F32}[self.points.dtype]
+
+
 def rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(seed))
 
@@ -196,6 +216,40 @@ def worldmap(n: int = 7322, maxdim: int = 2, seed: int = 1809 + 6) -> Cloud:
     p /= np.linalg.norm(p, axis=1, keepdims=True)
     p = p[g.permutation(n)]
     return Cloud(p.astype(np.float32), maxdim, 0.15)
+
+
+def hamming_matrix(n: int = 1088, L: int = 1000, n_types: int = 9, seed: int = 1809 + 7):
+    """HIV-shaped distance matrix: Hamming distances (int32) between n
+    sequences of length L over 4 letters with subtype structure -- a random
+    root, n_types subtypes each differing from it at 15 % of sites, each
+    sequence differing from its subtype at 5 % of sites.  The paper's 1088
+    HIV genomic sequences are not available."""
+    g = rng(seed)
+    root = g.integers(0, 4, size=L)
+    types = np.repeat(root[None, :], n_types, axis=0)
+    mut = g.random((n_types, L)) < 0.15
+    types[mut] = (types[mut] + g.integers(1, 4, size=mut.sum())) % 4
+    lab = g.integers(0, n_types, size=n)
+    seqs = types[lab].copy()
+    mut = g.random((n, L)) < 0.05
+    seqs[mut] = (seqs[mut] + g.integers(1, 4, size=mut.sum())) % 4
+    D = np.zeros((n, n), np.int32)
+    for i in range(n):
+        D[i] = (seqs != seqs[i]).sum(1)
+    return D
+
+
+def hiv(maxdim: int = 2) -> Matrix:
+    """HIV-shaped workload: the 1088 x 1088 Hamming matrix, cap at its 10th
+    percentile (59,846 edges, 2,106,840 triangles, 51 grades)."""
+    D = hamming_matrix()
+    return Matrix(D, maxdim, hamming_cap(D, 0.1))
+
+
+def hamming_cap(D: np.ndarray, q: float) -> float:
+    """The q-quantile of the strict-upper-triangle values (an integer)."""
+    iu = np.triu_indices(D.shape[0], 1)
+    return float(np.quantile(D[iu], q, method="lower"))
 
 
 def random_cloud(n: int, d: int, dtype, seed: int, lo=-100, hi=100) -> np.ndarray:

@@ -36,6 +36,8 @@ MUTANTS = [
     ("reduction never adds", "owner[low[j]] = j; }", "}"),
     ("pivot rows not killed", "killed[lowk1[j]] = 1;", ""),
     ("bar endpoints swapped", "b[nb] = gb; e[nb] = gd;", "b[nb] = gd; e[nb] = gb;"),
+    ("matrix cap strict", "      if (v <= maxrad) {", "      if (v < maxrad) {"),
+    ("matrix values squared", "if (is_float) df[m] = v;", "if (is_float) df[m] = v * v;"),
 ]
 
 
@@ -44,6 +46,8 @@ def _pins():
     import test_oracle_pins as P
     for s in range(6):
         yield lambda s=s: P.test_brute_force_tiny(s)
+    for s in range(4):
+        yield lambda s=s: P.test_dmat_brute_force_tiny(s)
     yield P.test_sortperm_worked_example
     yield P.test_cap_is_inclusive
     yield P.test_float_distance_within_fp64_bound

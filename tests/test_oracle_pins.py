@@ -329,3 +329,94 @@ def test_errors():
     bad[1, 1] = np.inf
     with pytest.raises(oracle.OracleError):
         oracle.vr_build(bad, 2)
+
+
+# ------------------------------------------------ distance-matrix input (Sec. 3)
+
+def brute_force_dmat(D, maxrad):
+    """Every subset of a tiny matrix's vertices enumerated directly: edges
+    (i < j) with D[i][j] <= maxrad, grades ranking the values themselves."""
+    n = D.shape[0]
+    val = {(i, j): (float(D[i, j]) if D.dtype == np.float32 else int(D[i, j]))
+           for i, j in itertools.combinations(range(n), 2)}
+    kept = {e: v for e, v in val.items() if v <= maxrad}
+    values = sorted(set([0] + list(kept.values())))
+    gidx = {v: g for g, v in enumerate(values)}
+    eg = {e: gidx[v] for e, v in kept.items()}
+    edges = sorted(kept, key=lambda e: (eg[e], e[0], e[1]))
+    ordr = {e: t for t, e in enumerate(edges)}
+    tris = sorted((max(eg[(a, b)], eg[(a, c)], eg[(b, c)]), a, b, c)
+                  for a, b, c in itertools.combinations(range(n), 3)
+                  if (a, b) in kept and (a, c) in kept and (b, c) in kept)
+    return values, edges, [eg[e] for e in edges], ordr, tris
+
+
+def random_symmetric(n, dtype, g, hi):
+    a = g.integers(0, hi, size=(n, n))
+    m = np.triu(a, 1)
+    m = m + m.T
+    if dtype == np.float32:
+        m = (m * 0.25).astype(np.float32)   # quarter steps: ties, exact in fp32
+    return m.astype(dtype)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_dmat_brute_force_tiny(seed):
+    """n <= 9 symmetric matrices with many tied values: simplices, grades,
+    order, boundary and grade values equal direct enumeration."""
+    g = synth.rng(900 + seed)
+    n = int(g.integers(1, 10))
+    dtype = np.int32 if seed % 2 else np.float32
+    D = random_symmetric(n, dtype, g, 6)
+    cap = [math.inf, 2.0, 0.75, 4.0][seed % 4]
+    values, edges, grades, ordr, tris = brute_force_dmat(D, cap)
+    cx = oracle.vr_build_dmat(D, 2, cap)
+    assert cx.grade_value.tolist() == [float(v) for v in values]
+    assert [tuple(x) for x in cx.dims[1].verts.tolist()] == edges
+    assert cx.dims[1].grade.tolist() == grades
+    assert [tuple(x) for x in cx.dims[2].verts.tolist()] == [t[1:] for t in tris]
+    assert cx.dims[2].grade.tolist() == [t[0] for t in tris]
+    rows = []
+    for _, a, b, c in tris:
+        rows += sorted([ordr[(b, c)], ordr[(a, c)], ordr[(a, b)]])
+    assert cx.dims[2].rowidx.tolist() == rows
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.float32])
+def test_dmat_of_squared_distances_equals_point_build(dtype):
+    """A matrix holding a cloud's squared distances, capped at r^2, gives the
+    point build capped at r (integer d^2 below 2^24, exact in float32)."""
+    p = synth.random_cloud(70, 3, np.int32, seed=41, lo=-60, hi=60)
+    D = ((p[:, None, :].astype(np.int64) - p[None, :, :]) ** 2).sum(-1).astype(dtype)
+    a = oracle.vr_build(p, 2, 30.0)
+    b = oracle.vr_build_dmat(D, 2, 900.0)
+    for k in range(3):
+        for f in ("verts", "grade", "colptr", "rowidx"):
+            x, y = getattr(a.dims[k], f), getattr(b.dims[k], f)
+            assert (x is None and y is None) or np.array_equal(x, y), (k, f)
+    assert np.array_equal(a.grade_value, b.grade_value)
+
+
+def test_dmat_hamming_cube():
+    """Hamming distances of {0,1}^3: the cube graph at cap 1 has 12 edges and
+    no triangle; at cap 2 every pair but the 4 antipodal ones is an edge."""
+    v = np.array(list(itertools.product([0, 1], repeat=3)))
+    D = (v[:, None, :] != v[None, :, :]).sum(-1).astype(np.int32)
+    c1 = oracle.vr_build_dmat(D, 2, 1.0)
+    assert [c1.dims[k].count for k in range(3)] == [8, 12, 0]
+    assert c1.grade_value.tolist() == [0.0, 1.0]
+    c2 = oracle.vr_build_dmat(D, 2, 2.0)
+    assert c2.dims[1].count == 28 - 4
+    assert c2.grade_value.tolist() == [0.0, 1.0, 2.0]
+
+
+def test_dmat_rejects_invalid_matrices():
+    D = np.array([[0, 1], [2, 0]], np.int32)
+    with pytest.raises(oracle.OracleError):
+        oracle.vr_build_dmat(D, 1)
+    with pytest.raises(oracle.OracleError):
+        oracle.vr_build_dmat(np.array([[0, -1], [-1, 0]], np.int32), 1)
+    with pytest.raises(oracle.OracleError):
+        oracle.vr_build_dmat(np.array([[0, np.nan], [np.nan, 0]], np.float32), 1)
+    ok = oracle.vr_build_dmat(np.array([[0.0, -0.0], [0.0, 0.0]], np.float32), 1)
+    assert ok.dims[1].grade.tolist() == [0]
