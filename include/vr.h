@@ -138,6 +138,29 @@ VR_API vr_status vr_build(const void *points, int32_t n, int32_t d, vr_dtype dty
 VR_API vr_status vr_build_dmat(const void *D, int32_t n, vr_dtype dtype, int32_t maxdim,
                                double maxrad, vr_stream_t stream, vr_complex **out);
 
+/* Persistence barcode of dimension `dim` (0 <= dim <= maxdim) of a built
+ * complex, computed on the device (Algorithm 1 over F2 and the pivot/bar
+ * rule of Fig. 4: a pivot (s, j) of the reduced boundary matrix is the bar
+ * [grade(s), grade(j)); a positive simplex never killed is [grade, inf)).
+ * The persistence pairs of every dimension are computed on the first call
+ * and kept on the complex; the bars of each dimension on their first request.
+ *   - Bars: first the finite ones in the order of the killing simplex, then
+ *     the infinite ones in the order of the born simplex; zero-length bars
+ *     are dropped; grades are the complex's integer filtration grades.
+ *     `dim` = maxdim reports the top dimension's positive simplices (the
+ *     complex is the maxdim skeleton, nothing kills them).
+ *   - *nbars receives the count.  Synchronous on `stream` (NULL: the
+ *     complex's stream).  Results of vr_build_batch views: VR_ERR_UNSUPPORTED.
+ * vr_complex_bars gives device pointers (int32 birth and death grades, death
+ * -1 for an infinite bar), valid until vr_complex_free; _to_host copies them
+ * into caller buffers of nbars entries each.  Both need a prior
+ * vr_complex_barcode of that dimension, else VR_ERR_ARG. */
+VR_API vr_status vr_complex_barcode(vr_complex *c, int32_t dim, vr_stream_t stream, int64_t *nbars);
+VR_API vr_status vr_complex_bars(const vr_complex *c, int32_t dim, const int32_t **birth,
+                                 const int32_t **death, int64_t *nbars);
+VR_API vr_status vr_complex_bars_to_host(const vr_complex *c, int32_t dim, int32_t *birth,
+                                         int32_t *death);
+
 /* Fill `view` for dimension k (0 <= k <= maxdim, else VR_ERR_ARG). */
 VR_API vr_status vr_complex_dim(const vr_complex *c, int32_t k, vr_dim_view *view);
 

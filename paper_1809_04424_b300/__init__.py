@@ -150,6 +150,24 @@ class Complex:
     def to_host(self, k: int) -> dict:
         return vr_complex_to_host(self.handle, k)
 
+    def barcode(self, dim: int, stream=None) -> np.ndarray:
+        """Bars of dimension `dim` as an (m, 2) int64 array of [birth, death)
+        grades (death -1: infinite), computed on the device."""
+        L = lib()
+        L.vr_complex_barcode.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_int64)]
+        L.vr_complex_barcode.restype = ctypes.c_int
+        L.vr_complex_bars_to_host.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+        L.vr_complex_bars_to_host.restype = ctypes.c_int
+        nb = ctypes.c_int64()
+        _check(L.vr_complex_barcode(ctypes.c_void_p(self.handle), int(dim), ctypes.c_void_p(stream or 0),
+                                    ctypes.byref(nb)))
+        b = np.zeros(nb.value, np.int32)
+        d = np.zeros(nb.value, np.int32)
+        _check(L.vr_complex_bars_to_host(ctypes.c_void_p(self.handle), int(dim), ctypes.c_void_p(b.ctypes.data),
+                                         ctypes.c_void_p(d.ctypes.data)))
+        return np.stack([b, d], axis=1).astype(np.int64) if nb.value else np.zeros((0, 2), np.int64)
+
     def grade_values(self) -> np.ndarray:
         return vr_complex_grade_values_to_host(self.handle)
 

@@ -210,8 +210,43 @@ vr_status vr_complex_grade_values_to_host(const vr_complex *c, double *values) {
   return VR_OK;
 }
 
+vr_status vr_complex_barcode(vr_complex *c, int32_t dim, vr_stream_t stream, int64_t *nbars) {
+  g_err[0] = 0;
+  if (!c || !nbars) { set_error("NULL argument"); return VR_ERR_ARG; }
+  if (dim < 0 || dim > c->maxdim) { set_error("dimension %d outside [0, %d]", dim, c->maxdim); return VR_ERR_ARG; }
+  if (c->in_batch || !c->owned) {
+    set_error("barcodes are computed on results of vr_build / vr_build_dmat / vr_serve_poll");
+    return VR_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+  return vr::complex_barcode(c, dim, s, nbars);
+}
+
+vr_status vr_complex_bars(const vr_complex *c, int32_t dim, const int32_t **birth, const int32_t **death,
+                          int64_t *nbars) {
+  if (!c || !birth || !death || !nbars) { set_error("NULL argument"); return VR_ERR_ARG; }
+  if (dim < 0 || dim > 2 || c->nbars[dim] < 0) { set_error("no barcode of dimension %d computed", dim); return VR_ERR_ARG; }
+  *birth = c->bar_birth[dim];
+  *death = c->bar_death[dim];
+  *nbars = c->nbars[dim];
+  return VR_OK;
+}
+
+vr_status vr_complex_bars_to_host(const vr_complex *c, int32_t dim, int32_t *birth, int32_t *death) {
+  if (!c || !birth || !death) { set_error("NULL argument"); return VR_ERR_ARG; }
+  if (dim < 0 || dim > 2 || c->nbars[dim] < 0) { set_error("no barcode of dimension %d computed", dim); return VR_ERR_ARG; }
+  const int64_t m = c->nbars[dim];
+  if (m) {
+    VR_CUDA(cudaMemcpyAsync(birth, c->bar_birth[dim], sizeof(int32_t) * m, cudaMemcpyDeviceToHost, c->stream));
+    VR_CUDA(cudaMemcpyAsync(death, c->bar_death[dim], sizeof(int32_t) * m, cudaMemcpyDeviceToHost, c->stream));
+  }
+  VR_CUDA(cudaStreamSynchronize(c->stream));
+  return VR_OK;
+}
+
 void vr_complex_free(vr_complex *c) {
   if (!c || c->in_batch) return;
+  for (void *p : c->bar_allocs) cudaFreeAsync(p, c->stream);
   if (c->owned)
     for (void *p : c->allocs) cudaFreeAsync(p, c->stream);
   cudaGetLastError();

@@ -1,0 +1,539 @@
+// barcode.cu -- persistence barcodes of a built complex on the GPU.
+//
+// The reduction of the filtered boundary matrix over F2 (Algorithm 1; the
+// pivot/bar rule of Fig. 4's caption) pairs simplices (s, j): s of
+// dimension k is the low of the reduced column j of dimension k+1, and
+// [grade(s), grade(j)) is a bar.  The pairing does not depend on which
+// left-to-right column additions reach the reduced form, so it is computed
+// here by two parallel routes that reach the same pairs:
+//
+//  * dimension 0 (vertices x edges): the reduced column of edge j is
+//    {root(A), root(B)} when j joins components A and B (roots = the
+//    smallest vertex id, the oldest vertex), so j kills max(root(A),
+//    root(B)); edges inside one component reduce to zero.  The killing edges
+//    are the minimum spanning forest under the edge order (Boruvka rounds,
+//    order index as the unique weight); one CTA then replays the forest
+//    edges in order with a union-find to name the killed vertices.
+//  * dimension 1 (edges x triangles): the coboundary matrix (the boundary
+//    matrix transposed with both orders reversed; the cohomology variant of
+//    the same reduction) is reduced instead.  Columns are the edges outside
+//    the forest (forest edges reduce to zero there: clearing), youngest
+//    first; a column lists the triangles containing the edge, its pivot is
+//    the oldest.  Rounds: every pivot's owner is the youngest column holding
+//    it; every other column holding that pivot adds the owner's column (a
+//    left-to-right addition in the reversed order).  The rounds stop when all
+//    pivots differ.  Column sums go to a growing pool.
+//
+// Bars are listed in the order of the killing simplex, then the essential
+// (never killed) positive simplices in their own order; zero-length bars are
+// dropped.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <vector>
+
+#include "complex.h"
+#include "prims.cuh"
+#include "prof.h"
+
+namespace vr {
+
+constexpr int BC_THREADS = 256;
+
+static unsigned bc_grid(int64_t work) {
+  const int64_t g = (work + BC_THREADS - 1) / BC_THREADS;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 148 * 16));
+}
+
+// ------------------------------------------------------------ dimension 0
+
+static __global__ void k_bv_init(int n, int32_t *comp, int32_t *best) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    comp[v] = v;
+    best[v] = INT_MAX;
+  }
+}
+
+// Each component's lightest (oldest) edge to another component.
+static __global__ void k_bv_choose(const int32_t *everts, int64_t E, const int32_t *comp, int32_t *best) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < E; j += (int64_t)gridDim.x * blockDim.x) {
+    const int ca = comp[everts[2 * j]], cb = comp[everts[2 * j + 1]];
+    if (ca != cb) {
+      atomicMin(&best[ca], (int32_t)j);
+      atomicMin(&best[cb], (int32_t)j);
+    }
+  }
+}
+
+// Root c hooks onto the component across its chosen edge (a mutual choice
+// keeps the smaller root); the edge joins the forest.  Reads comp, writes next.
+static __global__ void k_bv_hook(const int32_t *everts, int n, const int32_t *comp, const int32_t *best,
+                                 int32_t *next, uint8_t *msf, int32_t *changed) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    int32_t to = comp[c];
+    if (to == c && best[c] != INT_MAX) {
+      const int32_t j = best[c];
+      msf[j] = 1;
+      const int ca = comp[everts[2 * j]], cb = comp[everts[2 * j + 1]];
+      const int other = ca == c ? cb : ca;
+      if (!(best[other] == j && c < other)) to = other;
+      *changed = 1;
+    }
+    next[c] = to;
+  }
+}
+
+// comp[v] = the root reached through next (a forest: hooks never close a cycle).
+static __global__ void k_bv_jump(int n, const int32_t *next, int32_t *comp, int32_t *best) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    int r = next[v];
+    for (int guard = 0; next[r] != r && guard < 8192; ++guard) r = next[r];
+    comp[v] = r;
+    best[v] = INT_MAX;
+  }
+}
+
+// Replay the forest edges in filtration order (one thread; n <= 8192 vertices
+// in shared memory): edge j joining roots ra, rb kills max(ra, rb).
+static __global__ void __launch_bounds__(32) k_elder(const int32_t *everts, const int32_t *fedges, const int64_t *nf,
+                                                     int n, int32_t *killed_by_edge) {
+  __shared__ int32_t parent[VR_MAX_POINTS];
+  for (int v = threadIdx.x; v < n; v += 32) parent[v] = v;
+  __syncwarp();
+  if (threadIdx.x != 0) return;
+  const int m = (int)*nf;
+  for (int q = 0; q < m; ++q) {
+    const int32_t j = fedges[q];
+    int a = everts[2 * j], b = everts[2 * j + 1];
+    while (parent[a] != a) { parent[a] = parent[parent[a]]; a = parent[a]; }
+    while (parent[b] != b) { parent[b] = parent[parent[b]]; b = parent[b]; }
+    const int s = max(a, b), r = min(a, b);
+    parent[s] = r;
+    killed_by_edge[j] = s;
+  }
+}
+
+static __global__ void k_u8_to_i32(const uint8_t *f, int64_t L, int32_t *o) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L; q += (int64_t)gridDim.x * blockDim.x)
+    o[q] = f[q];
+}
+
+// Indices q with flag[q] set, in order (pos = exclusive scan of flag).
+static __global__ void k_compact_idx(const int32_t *flag, const int64_t *pos, int64_t L, int32_t *out) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L; q += (int64_t)gridDim.x * blockDim.x)
+    if (flag[q]) out[pos[q]] = (int32_t)q;
+}
+
+// ------------------------------------------------------------ dimension 1
+
+// Coboundary entries (face edge, triangle) in triangle order.
+static __global__ void k_cob_keys(const int32_t *trow, int64_t T, uint64_t *keys, int32_t *cnt) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < 3 * T; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t e = (uint32_t)trow[p];
+    keys[p] = ((uint64_t)e << 32) | (uint64_t)(p / 3);
+    atomicAdd(&cnt[e], 1);
+  }
+}
+
+static __global__ void k_cob_cols(const uint64_t *keys, int64_t L, int32_t *pool) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < L; p += (int64_t)gridDim.x * blockDim.x)
+    pool[p] = (int32_t)(uint32_t)keys[p];
+}
+
+// Columns of the reduction: edges outside the forest with their coface list.
+static __global__ void k_col_init(int64_t E, const uint8_t *msf, const int32_t *cptr, int64_t *coff, int32_t *clen) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    coff[e] = cptr[e];
+    clen[e] = msf[e] ? 0 : cptr[e + 1] - cptr[e];
+  }
+}
+
+// Owner of each pivot this round: the youngest column (largest edge index).
+static __global__ void k_own(int64_t E, const int64_t *coff, const int32_t *clen, const int32_t *pool,
+                             uint64_t round, unsigned long long *owner) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x)
+    if (clen[e] > 0) atomicMax(&owner[pool[coff[e]]], (round << 32) | (unsigned long long)e);
+}
+
+// Every non-owner adds its pivot owner's column: symmetric difference of two
+// ascending lists into fresh pool space (a column that finds no space keeps
+// its value and raises *overflow; the host grows the pool).
+static __global__ void k_add(int64_t E, int64_t *coff, int32_t *clen, int32_t *pool, int64_t cap,
+                             unsigned long long *top, const unsigned long long *owner, int32_t *changed,
+                             int32_t *overflow) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t la = clen[e];
+    if (la == 0) continue;
+    const int64_t oa = coff[e];
+    const int64_t o = (int64_t)(owner[pool[oa]] & 0xffffffffull);
+    if (o == e) continue;
+    *changed = 1;
+    const int64_t ob = coff[o];
+    const int32_t lb = clen[o];
+    const int64_t at = (int64_t)atomicAdd(top, (unsigned long long)(la + lb));
+    if (at + la + lb > cap) {
+      *overflow = 1;
+      continue;
+    }
+    int32_t x = 0, y = 0, k = 0;
+    while (x < la || y < lb) {
+      const int32_t u = x < la ? pool[oa + x] : INT_MAX, v = y < lb ? pool[ob + y] : INT_MAX;
+      if (u < v) { pool[at + k++] = u; ++x; }
+      else if (v < u) { pool[at + k++] = v; ++y; }
+      else { ++x; ++y; }  // equal rows cancel over F2
+    }
+    coff[e] = at;
+    clen[e] = k;
+  }
+}
+
+// Move the live columns to the front of a new pool.
+static __global__ void k_compact(int64_t E, const int64_t *coff, const int32_t *clen, const int64_t *noff,
+                                 const int32_t *pool, int32_t *npool, int64_t *coff_out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t l = clen[e];
+    const int64_t src = coff[e], dst = noff[e];
+    for (int32_t q = 0; q < l; ++q) npool[dst + q] = pool[src + q];
+    coff_out[e] = dst;
+  }
+}
+
+static __global__ void k_pairs1(int64_t E, const int64_t *coff, const int32_t *clen, const int32_t *pool,
+                                int32_t *pair_tri, int32_t *pair_edge) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    if (clen[e] > 0) {
+      const int32_t t = pool[coff[e]];
+      pair_tri[t] = (int32_t)e;
+      pair_edge[e] = t;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ bars
+
+// Bar candidates of one dimension in output order: finite bars indexed by
+// the killing simplex (m1 candidates), then essential ones (m0 candidates).
+struct BarSrc {
+  int dim, maxdim;
+  int64_t m0, m1;                 // simplices of dimension dim / dim+1
+  const int32_t *g0, *g1;         // their grades
+  const int32_t *killer_of;       // dim 0: killed vertex per edge; dim 1: edge per triangle (-1 none)
+  const uint8_t *neg0;            // dim 1: forest edges (zero in the edge reduction)
+  const int32_t *paired0;         // dim >= 1: the dim-simplex's killer (-1 none); dim 0: killed flag array
+};
+
+__device__ __forceinline__ bool bar_at(const BarSrc &b, int64_t q, int32_t &birth, int32_t &death) {
+  if (q < b.m1) {  // finite bar killed by simplex q of dimension dim+1
+    const int32_t s = b.killer_of[q];
+    if (s < 0) return false;
+    birth = b.g0[s];
+    death = b.g1[q];
+    return birth != death;
+  }
+  const int64_t s = q - b.m1;  // essential: positive and never killed
+  if (b.dim >= 1 && b.neg0 && b.neg0[s]) return false;
+  if (b.paired0 && b.paired0[s] >= 0) return false;
+  birth = b.g0[s];
+  death = -1;
+  return true;
+}
+
+static __global__ void k_bar_flags(BarSrc b, int32_t *flag) {
+  const int64_t L = b.m1 + b.m0;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L; q += (int64_t)gridDim.x * blockDim.x) {
+    int32_t x, y;
+    flag[q] = bar_at(b, q, x, y) ? 1 : 0;
+  }
+}
+
+static __global__ void k_bar_write(BarSrc b, const int64_t *pos, int32_t *birth, int32_t *death) {
+  const int64_t L = b.m1 + b.m0;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L; q += (int64_t)gridDim.x * blockDim.x) {
+    int32_t x, y;
+    if (bar_at(b, q, x, y)) {
+      birth[pos[q]] = x;
+      death[pos[q]] = y;
+    }
+  }
+}
+
+// dim 0 helper: per vertex, whether some forest edge killed it (-1 = never).
+static __global__ void k_killed_vertices(int64_t E, const int32_t *killed_by_edge, int32_t *vkill) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < E; j += (int64_t)gridDim.x * blockDim.x)
+    if (killed_by_edge[j] >= 0) vkill[killed_by_edge[j]] = (int32_t)j;
+}
+
+// ------------------------------------------------------------------ host
+
+struct Dev {
+  cudaStream_t s;
+  std::vector<void *> tmp;
+  explicit Dev(cudaStream_t st) : s(st) {}
+  ~Dev() {
+    for (void *p : tmp) cudaFreeAsync(p, s);
+  }
+  void release(void *p) {
+    for (auto &q : tmp)
+      if (q == p) {
+        cudaFreeAsync(p, s);
+        q = tmp.back();
+        tmp.pop_back();
+        return;
+      }
+  }
+  template <typename T>
+  vr_status get(T **p, int64_t count, bool keep = false, std::vector<void *> *owner = nullptr) {
+    const size_t bytes = sizeof(T) * (size_t)std::max<int64_t>(count, 1);
+    cudaError_t e = cudaMallocAsync((void **)p, bytes, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("barcode: device allocation of %zu bytes failed", bytes);
+      return e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA;
+    }
+    if (keep) owner->push_back(*p);
+    else tmp.push_back(*p);
+    return VR_OK;
+  }
+};
+
+static vr_status read_i32(const int32_t *d, int32_t *h, cudaStream_t s) {
+  VR_CUDA(cudaMemcpyAsync(h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  VR_CUDA(cudaStreamSynchronize(s));
+  return VR_OK;
+}
+
+// Pairs of dimension 0 (killed vertex per edge) and, for maxdim 2, of
+// dimension 1 (edge per triangle and triangle per edge).  Kept on the complex.
+static vr_status compute_pairs(vr_complex *c, cudaStream_t s) {
+  Dev dv(s);
+  Prof prof(s);
+  const int n = c->n;
+  const int64_t E = c->maxdim >= 1 ? c->count[1] : 0;
+  const int64_t T = c->maxdim >= 2 ? c->count[2] : 0;
+  int32_t *killed_by_edge = nullptr, *vkill = nullptr;
+  uint8_t *msf = nullptr;
+  int32_t *pair_tri = nullptr, *pair_edge = nullptr;
+  VR_TRY(dv.get(&killed_by_edge, E, true, &c->bar_allocs));
+  VR_TRY(dv.get(&vkill, n, true, &c->bar_allocs));
+  VR_TRY(dv.get(&msf, E, true, &c->bar_allocs));
+  VR_CUDA(cudaMemsetAsync(killed_by_edge, 0xff, sizeof(int32_t) * std::max<int64_t>(E, 1), s));
+  VR_CUDA(cudaMemsetAsync(vkill, 0xff, sizeof(int32_t) * n, s));
+  VR_CUDA(cudaMemsetAsync(msf, 0, std::max<int64_t>(E, 1), s));
+  int32_t *hflag = nullptr;
+  VR_CUDA(cudaMallocHost((void **)&hflag, sizeof(int32_t)));
+  struct HostFree {
+    int32_t *p;
+    ~HostFree() { cudaFreeHost(p); }
+  } hf{hflag};
+
+  if (E > 0) {
+    // Boruvka rounds for the spanning forest.
+    prof.begin("bars.forest");
+    int32_t *comp, *best, *next, *changed;
+    VR_TRY(dv.get(&comp, n));
+    VR_TRY(dv.get(&best, n));
+    VR_TRY(dv.get(&next, n));
+    VR_TRY(dv.get(&changed, 1));
+    k_bv_init<<<bc_grid(n), BC_THREADS, 0, s>>>(n, comp, best);
+    count_launch();
+    for (int round = 0; round < 64; ++round) {
+      VR_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), s));
+      k_bv_choose<<<bc_grid(E), BC_THREADS, 0, s>>>(c->verts[1], E, comp, best);
+      k_bv_hook<<<bc_grid(n), BC_THREADS, 0, s>>>(c->verts[1], n, comp, best, next, msf, changed);
+      k_bv_jump<<<bc_grid(n), BC_THREADS, 0, s>>>(n, next, comp, best);
+      count_launch(3);
+      VR_CUDA(cudaGetLastError());
+      VR_TRY(read_i32(changed, hflag, s));
+      if (!*hflag) break;
+    }
+    prof.end();
+    // Forest edges in order, then the elder rule.
+    prof.begin("bars.elder");
+    int32_t *flag, *fedges;
+    int64_t *bs;
+    VR_TRY(dv.get(&flag, E));
+    VR_TRY(dv.get(&fedges, n));
+    int64_t *fpos;
+    VR_TRY(dv.get(&fpos, E + 1));
+    VR_TRY(dv.get(&bs, scan_tmp_slots(E)));
+    k_u8_to_i32<<<bc_grid(E), BC_THREADS, 0, s>>>(msf, E, flag);
+    count_launch();
+    VR_TRY((scan_exclusive<int32_t, int64_t>(flag, fpos, E, bs, s)));
+    k_compact_idx<<<bc_grid(E), BC_THREADS, 0, s>>>(flag, fpos, E, fedges);
+    count_launch();
+    k_elder<<<1, 32, 0, s>>>(c->verts[1], fedges, fpos + E, n, killed_by_edge);
+    k_killed_vertices<<<bc_grid(E), BC_THREADS, 0, s>>>(E, killed_by_edge, vkill);
+    count_launch(2);
+    VR_CUDA(cudaGetLastError());
+    prof.end();
+  }
+
+  if (T > 0) {
+    prof.begin("bars.coboundary");
+    VR_TRY(dv.get(&pair_tri, T, true, &c->bar_allocs));
+    VR_TRY(dv.get(&pair_edge, E, true, &c->bar_allocs));
+    VR_CUDA(cudaMemsetAsync(pair_tri, 0xff, sizeof(int32_t) * T, s));
+    VR_CUDA(cudaMemsetAsync(pair_edge, 0xff, sizeof(int32_t) * E, s));
+    // Coboundary lists: (edge, triangle) entries sorted by edge, stable in t.
+    const int64_t L = 3 * T;
+    uint64_t *keys;
+    int32_t *cnt, *cptr;
+    RadixScratch rs{};
+    int32_t *sflags;
+    VR_TRY(dv.get(&keys, L));
+    VR_TRY(dv.get(&rs.tkeys, L));
+    VR_TRY(dv.get(&rs.meta, rs_meta_bytes(L)));
+    VR_TRY(dv.get(&sflags, 1));
+    VR_CUDA(cudaMemsetAsync(sflags, 0, sizeof(int32_t), s));
+    rs.err = sflags;
+    VR_TRY(dv.get(&cnt, E));
+    VR_TRY(dv.get(&cptr, E + 1));
+    VR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * E, s));
+    k_cob_keys<<<bc_grid(L), BC_THREADS, 0, s>>>(c->rowidx[2], T, keys, cnt);
+    count_launch();
+    int ebits = 1;
+    while ((1ll << ebits) < E) ++ebits;
+    VR_TRY(radix_sort(keys, L, 32, ebits, rs, s));
+    int64_t *bs;
+    VR_TRY(dv.get(&bs, scan_tmp_slots(E)));
+    VR_TRY((scan_exclusive<int32_t, int32_t>(cnt, cptr, E, bs, s)));
+    // The pool: the initial columns, then room for column sums.
+    int64_t cap = std::max<int64_t>(4 * L, 1 << 20);
+    int32_t *pool;
+    VR_TRY(dv.get(&pool, cap));
+    k_cob_cols<<<bc_grid(L), BC_THREADS, 0, s>>>(keys, L, pool);
+    count_launch();
+    int64_t *coff;
+    int32_t *clen;
+    unsigned long long *owner, *top;
+    int32_t *changed, *overflow;
+    VR_TRY(dv.get(&coff, E));
+    VR_TRY(dv.get(&clen, E));
+    VR_TRY(dv.get(&owner, T));
+    VR_TRY(dv.get(&top, 1));
+    VR_TRY(dv.get(&changed, 2));
+    overflow = changed + 1;
+    VR_CUDA(cudaMemsetAsync(owner, 0, sizeof(unsigned long long) * T, s));
+    const unsigned long long top0 = (unsigned long long)L;
+    VR_CUDA(cudaMemcpyAsync(top, &top0, sizeof(top0), cudaMemcpyHostToDevice, s));
+    k_col_init<<<bc_grid(E), BC_THREADS, 0, s>>>(E, msf, cptr, coff, clen);
+    count_launch();
+    VR_CUDA(cudaGetLastError());
+    prof.end();
+
+    prof.begin("bars.reduce");
+    int32_t hcf[2];
+    unsigned long long htop = 0;
+    for (uint64_t round = 1;; ++round) {
+      if (round > (uint64_t)T + 2) {
+        set_error("barcode: the column reduction did not settle");
+        return VR_ERR_INTERNAL;
+      }
+      VR_CUDA(cudaMemsetAsync(changed, 0, 2 * sizeof(int32_t), s));
+      k_own<<<bc_grid(E), BC_THREADS, 0, s>>>(E, coff, clen, pool, round, owner);
+      k_add<<<bc_grid(E), BC_THREADS, 0, s>>>(E, coff, clen, pool, cap, top, owner, changed, overflow);
+      count_launch(2);
+      VR_CUDA(cudaGetLastError());
+      VR_CUDA(cudaMemcpyAsync(hcf, changed, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      VR_CUDA(cudaMemcpyAsync(&htop, top, sizeof(htop), cudaMemcpyDeviceToHost, s));
+      VR_CUDA(cudaStreamSynchronize(s));
+      if (!hcf[0]) break;
+      if (hcf[1] || htop > (unsigned long long)cap / 2) {
+        // Compact the live columns into a pool twice the live size (and at
+        // least as large as before).
+        int32_t *lens32 = clen;
+        int64_t *noff, *nbs;
+        VR_TRY(dv.get(&noff, E + 1));
+        VR_TRY(dv.get(&nbs, scan_tmp_slots(E)));
+        VR_TRY((scan_exclusive<int32_t, int64_t>(lens32, noff, E, nbs, s)));
+        int64_t live = 0;
+        VR_CUDA(cudaMemcpyAsync(&live, noff + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        VR_CUDA(cudaStreamSynchronize(s));
+        const int64_t ncap = std::max<int64_t>(cap, 4 * live + (1 << 20));
+        int32_t *npool;
+        int64_t *ncoff;
+        VR_TRY(dv.get(&npool, ncap));
+        VR_TRY(dv.get(&ncoff, E));
+        k_compact<<<bc_grid(E), BC_THREADS, 0, s>>>(E, coff, clen, noff, pool, npool, ncoff);
+        count_launch();
+        VR_CUDA(cudaGetLastError());
+        dv.release(pool);
+        dv.release(coff);
+        dv.release(noff);
+        dv.release(nbs);
+        pool = npool;
+        coff = ncoff;
+        cap = ncap;
+        const unsigned long long t0 = (unsigned long long)live;
+        VR_CUDA(cudaMemcpyAsync(top, &t0, sizeof(t0), cudaMemcpyHostToDevice, s));
+      }
+    }
+    k_pairs1<<<bc_grid(E), BC_THREADS, 0, s>>>(E, coff, clen, pool, pair_tri, pair_edge);
+    count_launch();
+    VR_CUDA(cudaGetLastError());
+    int32_t hs = 0;
+    VR_TRY(read_i32(sflags, &hs, s));
+    VR_TRY(flags_to_status(hs));
+    prof.end();
+  }
+  c->killed_by_edge = killed_by_edge;
+  c->vkill = vkill;
+  c->msf = msf;
+  c->pair_tri = pair_tri;
+  c->pair_edge = pair_edge;
+  c->pairs_done = true;
+  VR_CUDA(cudaStreamSynchronize(s));
+  return VR_OK;
+}
+
+vr_status complex_barcode(vr_complex *c, int dim, cudaStream_t s, int64_t *nbars) {
+  if (!c->pairs_done) VR_TRY(compute_pairs(c, s));
+  if (c->nbars[dim] >= 0) {
+    *nbars = c->nbars[dim];
+    return VR_OK;
+  }
+  BarSrc b{};
+  b.dim = dim;
+  b.maxdim = c->maxdim;
+  b.m0 = c->count[dim];
+  b.g0 = c->grade[dim];
+  if (dim < c->maxdim) {
+    b.m1 = c->count[dim + 1];
+    b.g1 = c->grade[dim + 1];
+    b.killer_of = dim == 0 ? c->killed_by_edge : c->pair_tri;
+  }
+  if (dim == 0) b.paired0 = c->maxdim >= 1 ? c->vkill : nullptr;
+  if (dim == 1) {
+    b.neg0 = c->msf;
+    b.paired0 = c->maxdim >= 2 ? c->pair_edge : nullptr;
+  }
+  if (dim == 2) b.paired0 = c->pair_tri;
+  Dev dv(s);
+  const int64_t L = b.m0 + b.m1;
+  int32_t *flag;
+  int64_t *pos, *bs;
+  VR_TRY(dv.get(&flag, L));
+  VR_TRY(dv.get(&pos, L + 1));
+  VR_TRY(dv.get(&bs, scan_tmp_slots(L)));
+  k_bar_flags<<<bc_grid(L), BC_THREADS, 0, s>>>(b, flag);
+  count_launch();
+  VR_TRY((scan_exclusive<int32_t, int64_t>(flag, pos, L, bs, s)));
+  int64_t nb = 0;
+  VR_CUDA(cudaMemcpyAsync(&nb, pos + L, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  VR_CUDA(cudaStreamSynchronize(s));
+  int32_t *birth, *death;
+  VR_TRY(dv.get(&birth, nb, true, &c->bar_allocs));
+  VR_TRY(dv.get(&death, nb, true, &c->bar_allocs));
+  k_bar_write<<<bc_grid(L), BC_THREADS, 0, s>>>(b, pos, birth, death);
+  count_launch();
+  VR_CUDA(cudaGetLastError());
+  VR_CUDA(cudaStreamSynchronize(s));
+  c->bar_birth[dim] = birth;
+  c->bar_death[dim] = death;
+  c->nbars[dim] = nb;
+  *nbars = nb;
+  return VR_OK;
+}
+
+}  // namespace vr

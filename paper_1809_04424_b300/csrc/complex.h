@@ -24,6 +24,18 @@ struct vr_complex {
   std::shared_ptr<void> arena;  // shared batch arenas this result views
   bool owned = true;            // false for views into a batch's arenas
   bool in_batch = false;        // owned by a vr_batch: vr_complex_free ignores it
+  // Persistence pairs and bars (vr_complex_barcode), device arrays owned by
+  // this object whatever `owned` says.
+  std::vector<void *> bar_allocs;
+  bool pairs_done = false;
+  int32_t *killed_by_edge = nullptr;  // dim 0: vertex killed by each edge (-1: none)
+  int32_t *vkill = nullptr;           // per vertex: its killing edge (-1: never)
+  uint8_t *msf = nullptr;             // per edge: in the spanning forest (zero column of D1)
+  int32_t *pair_tri = nullptr;        // per triangle: the edge it kills (-1: none)
+  int32_t *pair_edge = nullptr;       // per edge: the triangle killing it (-1: none)
+  int64_t nbars[3] = {-1, -1, -1};
+  int32_t *bar_birth[3] = {nullptr, nullptr, nullptr};
+  int32_t *bar_death[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace vr {
@@ -31,6 +43,7 @@ namespace vr {
 void keep_pool_warm();
 vr_status build_dmat(const void *D, int32_t n, vr_dtype dtype, int32_t maxdim, double maxrad, cudaStream_t s,
                      vr_complex *res);
+vr_status complex_barcode(vr_complex *c, int dim, cudaStream_t s, int64_t *nbars);
 vr_status build_cloud(const void *dpts, int32_t n, int32_t d, vr_dtype dtype, int32_t maxdim, double maxrad,
                       cudaStream_t s, vr_complex *res);
 }
