@@ -19,10 +19,12 @@
 //    the same reduction) is reduced instead.  Columns are the edges outside
 //    the forest (forest edges reduce to zero there: clearing), youngest
 //    first; a column lists the triangles containing the edge, its pivot is
-//    the oldest.  Rounds: every pivot's owner is the youngest column holding
-//    it; every other column holding that pivot adds the owner's column (a
-//    left-to-right addition in the reversed order).  The rounds stop when all
-//    pivots differ.  Column sums go to a growing pool.
+//    the oldest.  Columns are taken in processing order in batches: each
+//    column of a batch adds final columns owning its pivot (every addition
+//    uses a final column, as in the sequential algorithm), then one CTA
+//    finalises the longest prefix of the batch whose pivots differ; the
+//    first column whose pivot repeats a younger one adds that (now final)
+//    column on the next pass.  Column sums go to a growing pool.
 //
 // Bars are listed in the order of the killing simplex, then the essential
 // (never killed) positive simplices in their own order; zero-length bars are
@@ -149,43 +151,201 @@ static __global__ void k_col_init(int64_t E, const uint8_t *msf, const int32_t *
   }
 }
 
-// Owner of each pivot this round: the youngest column (largest edge index).
-static __global__ void k_own(int64_t E, const int64_t *coff, const int32_t *clen, const int32_t *pool,
-                             uint64_t round, unsigned long long *owner) {
+// Active columns (outside the forest, with cofaces), ascending edge order.
+static __global__ void k_active_flags(int64_t E, const int32_t *clen, int32_t *flag) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x)
-    if (clen[e] > 0) atomicMax(&owner[pool[coff[e]]], (round << 32) | (unsigned long long)e);
+    flag[e] = clen[e] > 0;
 }
 
-// Every non-owner adds its pivot owner's column: symmetric difference of two
-// ascending lists into fresh pool space (a column that finds no space keeps
-// its value and raises *overflow; the host grows the pool).
-static __global__ void k_add(int64_t E, int64_t *coff, int32_t *clen, int32_t *pool, int64_t cap,
-                             unsigned long long *top, const unsigned long long *owner, int32_t *changed,
-                             int32_t *overflow) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t la = clen[e];
-    if (la == 0) continue;
-    const int64_t oa = coff[e];
-    const int64_t o = (int64_t)(owner[pool[oa]] & 0xffffffffull);
-    if (o == e) continue;
-    *changed = 1;
-    const int64_t ob = coff[o];
-    const int32_t lb = clen[o];
-    const int64_t at = (int64_t)atomicAdd(top, (unsigned long long)(la + lb));
-    if (at + la + lb > cap) {
-      *overflow = 1;
-      continue;
-    }
-    int32_t x = 0, y = 0, k = 0;
-    while (x < la || y < lb) {
-      const int32_t u = x < la ? pool[oa + x] : INT_MAX, v = y < lb ? pool[ob + y] : INT_MAX;
-      if (u < v) { pool[at + k++] = u; ++x; }
-      else if (v < u) { pool[at + k++] = v; ++y; }
-      else { ++x; ++y; }  // equal rows cancel over F2
-    }
-    coff[e] = at;
-    clen[e] = k;
+constexpr int BC_BATCH = 1024;
+
+// Symmetric difference of two ascending lists A (la) and B (lb) into out by
+// one CTA of BC_THREADS threads, in merge-path tiles of BC_TILE merged
+// entries: both slices of a tile are staged in shared memory (coalesced),
+// each thread merges BC_PER consecutive entries (A first on ties, so an
+// entry present in both lists is an A entry directly followed by the equal B
+// entry), drops the entries that cancel, and a block scan places the rest.
+// Returns the output length (to every thread).
+constexpr int BC_PER = 16;
+constexpr int BC_TILE = BC_THREADS * BC_PER;
+
+struct SymdiffSmem {
+  int32_t a[BC_TILE], b[BC_TILE];
+  int64_t sh[33];
+  int64_t split[BC_THREADS + 1];  // A entries before each tile boundary of a group of tiles
+};
+
+// Entries of A before merged position d (A first on ties).
+__device__ __forceinline__ int64_t merge_split(const int32_t *A, int64_t la, const int32_t *B, int64_t lb, int64_t d) {
+  int64_t lo = d - lb > 0 ? d - lb : 0, hi = d < la ? d : la;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (A[mid] <= B[d - mid - 1]) lo = mid + 1;
+    else hi = mid;
   }
+  return lo;
+}
+
+__device__ int64_t cta_symdiff(const int32_t *A, int64_t la, const int32_t *B, int64_t lb, int32_t *out,
+                               SymdiffSmem &S) {
+  int64_t written = 0;
+  const int64_t L = la + lb;
+  for (int64_t g0 = 0; g0 < L; g0 += (int64_t)BC_TILE * BC_THREADS) {
+    // The boundaries of up to BC_THREADS tiles, one binary search per thread.
+    {
+      const int64_t d = g0 + (int64_t)threadIdx.x * BC_TILE;
+      S.split[threadIdx.x] = merge_split(A, la, B, lb, d < L ? d : L);
+      if (threadIdx.x == 0) {
+        const int64_t dl = g0 + (int64_t)BC_THREADS * BC_TILE;
+        S.split[BC_THREADS] = merge_split(A, la, B, lb, dl < L ? dl : L);
+      }
+    }
+    __syncthreads();
+    for (int t = 0; t < BC_THREADS; ++t) {
+      const int64_t d0 = g0 + (int64_t)t * BC_TILE;
+      if (d0 >= L) break;
+      const int64_t d1 = d0 + BC_TILE < L ? d0 + BC_TILE : L;
+      const int64_t a0 = S.split[t], a1 = S.split[t + 1];  // split[t + 1] was taken at d1
+      const int64_t b0 = d0 - a0, b1 = d1 - a1;
+      const int na = (int)(a1 - a0), nb = (int)(b1 - b0);
+      for (int q = threadIdx.x; q < na; q += BC_THREADS) S.a[q] = A[a0 + q];
+      for (int q = threadIdx.x; q < nb; q += BC_THREADS) S.b[q] = B[b0 + q];
+      const int32_t prevA = a0 > 0 ? A[a0 - 1] : -1;    // last A entry before the tile
+      const int32_t nextB = b1 < lb ? B[b1] : INT_MAX;  // first B entry after the tile
+      __syncthreads();
+      // This thread's merged positions [p0, p1) of the tile.
+      const int p0 = threadIdx.x * BC_PER, p1 = min(p0 + BC_PER, na + nb);
+      int32_t keep[BC_PER];
+      int nk = 0;
+      if (p0 < p1) {
+        int lo = p0 - nb > 0 ? p0 - nb : 0, hi = p0 < na ? p0 : na;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (S.a[mid] <= S.b[p0 - mid - 1]) lo = mid + 1;
+          else hi = mid;
+        }
+        int ia = lo, ib = p0 - lo;
+#pragma unroll
+        for (int r = 0; r < BC_PER; ++r) {
+          if (p0 + r >= p1) break;
+          const bool takeA = ib >= nb || (ia < na && S.a[ia] <= S.b[ib]);
+          if (takeA) {
+            const int32_t x = S.a[ia];
+            const int32_t nextb = ib < nb ? S.b[ib] : nextB;
+            if (nextb != x) keep[nk++] = x;
+            ++ia;
+          } else {
+            const int32_t y = S.b[ib];
+            const int32_t preva = ia > 0 ? S.a[ia - 1] : prevA;
+            if (preva != y) keep[nk++] = y;
+            ++ib;
+          }
+        }
+      }
+      int64_t tot;
+      const int64_t off = block_excl_scan<int64_t>((int64_t)nk, S.sh, &tot);
+#pragma unroll
+      for (int q = 0; q < BC_PER; ++q)
+        if (q < nk) out[written + off + q] = keep[q];
+      written += tot;
+      __syncthreads();
+    }
+  }
+  return written;
+}
+
+// Reduce the non-final columns of batch positions [p0, p1) (position p is
+// edge act[P-1-p]: youngest first) against final columns, one CTA per
+// column: while the pivot has a final owner, add that column (into fresh
+// pool space).  No pool space: *overflow, the column keeps its last value.
+static __global__ void __launch_bounds__(BC_THREADS) k_batch_reduce(const int32_t *act, int64_t P, int64_t p0,
+                                                                    int64_t p1, int64_t *coff, int32_t *clen,
+                                                                    int32_t *pool, int64_t cap,
+                                                                    unsigned long long *top,
+                                                                    const int32_t *final_owner, const uint8_t *fin,
+                                                                    int32_t *overflow) {
+  __shared__ SymdiffSmem S;
+  __shared__ int64_t s_o, s_at;
+  const int64_t p = p0 + blockIdx.x;
+  if (p >= p1) return;
+  const int64_t e = act[P - 1 - p];
+  if (fin[e]) return;
+  int64_t la = clen[e], oa = coff[e];
+  bool moved = false;
+  while (la > 0) {
+    if (threadIdx.x == 0) {
+      const int32_t o = final_owner[pool[oa]];
+      s_o = o;
+      s_at = -1;
+      if (o >= 0) {
+        const int64_t need = la + clen[o];
+        const int64_t at = (int64_t)atomicAdd(top, (unsigned long long)need);
+        if (at + need > cap) *overflow = 1;
+        else s_at = at;
+      }
+    }
+    __syncthreads();
+    const int64_t o = s_o, at = s_at;
+    __syncthreads();
+    if (o < 0 || at < 0) break;
+    const int64_t k = cta_symdiff(pool + oa, la, pool + coff[o], clen[o], pool + at, S);
+    oa = at;
+    la = k;
+    moved = true;
+  }
+  if (moved && threadIdx.x == 0) {
+    coff[e] = oa;
+    clen[e] = (int32_t)la;
+  }
+}
+
+// One CTA: finalise the longest prefix of the batch's non-final columns whose
+// pivots differ from every younger non-final column's (empty columns are
+// final at once).  *remaining = the batch's non-final columns afterwards.
+static __global__ void __launch_bounds__(BC_BATCH) k_batch_finalize(const int32_t *act, int64_t P, int64_t p0,
+                                                                    int64_t p1, const int64_t *coff,
+                                                                    const int32_t *clen, const int32_t *pool,
+                                                                    int32_t *final_owner, uint8_t *fin,
+                                                                    const int32_t *overflow, int32_t *remaining) {
+  __shared__ int32_t piv[BC_BATCH];
+  __shared__ int32_t first_conflict;
+  __shared__ int32_t left;
+  const int i = threadIdx.x;
+  const int64_t p = p0 + i;
+  const bool mine = p < p1;
+  const int64_t e = mine ? act[P - 1 - p] : -1;
+  const bool open = mine && !fin[e];
+  piv[i] = open && clen[e] > 0 ? pool[coff[e]] : -1;
+  if (i == 0) {
+    first_conflict = BC_BATCH;
+    left = 0;
+  }
+  __syncthreads();
+  if (*overflow) {  // a column could not finish its additions: no finalising this pass
+    if (open) atomicAdd(&left, 1);
+    __syncthreads();
+    if (i == 0) *remaining = left;
+    return;
+  }
+  bool conflict = false;
+  if (piv[i] >= 0)
+    for (int j = 0; j < i; ++j)
+      if (piv[j] == piv[i]) {
+        conflict = true;
+        break;
+      }
+  if (conflict) atomicMin(&first_conflict, i);
+  __syncthreads();
+  if (open) {
+    if (i < first_conflict) {
+      if (piv[i] >= 0) final_owner[piv[i]] = (int32_t)e;
+      fin[e] = 1;
+    } else {
+      atomicAdd(&left, 1);
+    }
+  }
+  __syncthreads();
+  if (i == 0) *remaining = left;
 }
 
 // Move the live columns to the front of a new pool.
@@ -406,15 +566,12 @@ static vr_status compute_pairs(vr_complex *c, cudaStream_t s) {
     count_launch();
     int64_t *coff;
     int32_t *clen;
-    unsigned long long *owner, *top;
-    int32_t *changed, *overflow;
+    unsigned long long *top;
+    int32_t *overflow;
     VR_TRY(dv.get(&coff, E));
     VR_TRY(dv.get(&clen, E));
-    VR_TRY(dv.get(&owner, T));
     VR_TRY(dv.get(&top, 1));
-    VR_TRY(dv.get(&changed, 2));
-    overflow = changed + 1;
-    VR_CUDA(cudaMemsetAsync(owner, 0, sizeof(unsigned long long) * T, s));
+    VR_TRY(dv.get(&overflow, 1));
     const unsigned long long top0 = (unsigned long long)L;
     VR_CUDA(cudaMemcpyAsync(top, &top0, sizeof(top0), cudaMemcpyHostToDevice, s));
     k_col_init<<<bc_grid(E), BC_THREADS, 0, s>>>(E, msf, cptr, coff, clen);
@@ -423,50 +580,81 @@ static vr_status compute_pairs(vr_complex *c, cudaStream_t s) {
     prof.end();
 
     prof.begin("bars.reduce");
-    int32_t hcf[2];
+    // Active columns in ascending edge order; processing takes them from the
+    // youngest.
+    int32_t *aflag, *act, *final_owner, *rem;
+    int64_t *apos, *abs_;
+    uint8_t *fin;
+    VR_TRY(dv.get(&aflag, E));
+    VR_TRY(dv.get(&apos, E + 1));
+    VR_TRY(dv.get(&abs_, scan_tmp_slots(E)));
+    VR_TRY(dv.get(&act, E));
+    VR_TRY(dv.get(&final_owner, T));
+    VR_TRY(dv.get(&fin, E));
+    VR_TRY(dv.get(&rem, 1));
+    VR_CUDA(cudaMemsetAsync(final_owner, 0xff, sizeof(int32_t) * T, s));
+    VR_CUDA(cudaMemsetAsync(fin, 0, E, s));
+    k_active_flags<<<bc_grid(E), BC_THREADS, 0, s>>>(E, clen, aflag);
+    count_launch();
+    VR_TRY((scan_exclusive<int32_t, int64_t>(aflag, apos, E, abs_, s)));
+    k_compact_idx<<<bc_grid(E), BC_THREADS, 0, s>>>(aflag, apos, E, act);
+    count_launch();
+    int64_t P = 0;
+    VR_CUDA(cudaMemcpyAsync(&P, apos + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    VR_CUDA(cudaStreamSynchronize(s));
+    int32_t hrem[2];
     unsigned long long htop = 0;
-    for (uint64_t round = 1;; ++round) {
-      if (round > (uint64_t)T + 2) {
-        set_error("barcode: the column reduction did not settle");
-        return VR_ERR_INTERNAL;
-      }
-      VR_CUDA(cudaMemsetAsync(changed, 0, 2 * sizeof(int32_t), s));
-      k_own<<<bc_grid(E), BC_THREADS, 0, s>>>(E, coff, clen, pool, round, owner);
-      k_add<<<bc_grid(E), BC_THREADS, 0, s>>>(E, coff, clen, pool, cap, top, owner, changed, overflow);
-      count_launch(2);
-      VR_CUDA(cudaGetLastError());
-      VR_CUDA(cudaMemcpyAsync(hcf, changed, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      VR_CUDA(cudaMemcpyAsync(&htop, top, sizeof(htop), cudaMemcpyDeviceToHost, s));
-      VR_CUDA(cudaStreamSynchronize(s));
-      if (!hcf[0]) break;
-      if (hcf[1] || htop > (unsigned long long)cap / 2) {
-        // Compact the live columns into a pool twice the live size (and at
-        // least as large as before).
-        int32_t *lens32 = clen;
-        int64_t *noff, *nbs;
-        VR_TRY(dv.get(&noff, E + 1));
-        VR_TRY(dv.get(&nbs, scan_tmp_slots(E)));
-        VR_TRY((scan_exclusive<int32_t, int64_t>(lens32, noff, E, nbs, s)));
-        int64_t live = 0;
-        VR_CUDA(cudaMemcpyAsync(&live, noff + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        VR_CUDA(cudaStreamSynchronize(s));
-        const int64_t ncap = std::max<int64_t>(cap, 4 * live + (1 << 20));
-        int32_t *npool;
-        int64_t *ncoff;
-        VR_TRY(dv.get(&npool, ncap));
-        VR_TRY(dv.get(&ncoff, E));
-        k_compact<<<bc_grid(E), BC_THREADS, 0, s>>>(E, coff, clen, noff, pool, npool, ncoff);
-        count_launch();
+    for (int64_t p0 = 0; p0 < P; p0 += BC_BATCH) {
+      const int64_t p1 = std::min<int64_t>(P, p0 + BC_BATCH);
+      for (int64_t pass = 0;; ++pass) {
+        if (pass > BC_BATCH + 8) {
+          set_error("barcode: a batch of the column reduction did not settle");
+          return VR_ERR_INTERNAL;
+        }
+        VR_CUDA(cudaMemsetAsync(overflow, 0, sizeof(int32_t), s));
+        // Two passes per check: a pass on a settled batch does nothing.
+        for (int k = 0; k < 2; ++k) {
+          k_batch_reduce<<<(unsigned)(p1 - p0), BC_THREADS, 0, s>>>(act, P, p0, p1, coff, clen, pool, cap, top,
+                                                                    final_owner, fin, overflow);
+          k_batch_finalize<<<1, BC_BATCH, 0, s>>>(act, P, p0, p1, coff, clen, pool, final_owner, fin, overflow,
+                                                  rem);
+          count_launch(2);
+        }
         VR_CUDA(cudaGetLastError());
-        dv.release(pool);
-        dv.release(coff);
-        dv.release(noff);
-        dv.release(nbs);
-        pool = npool;
-        coff = ncoff;
-        cap = ncap;
-        const unsigned long long t0 = (unsigned long long)live;
-        VR_CUDA(cudaMemcpyAsync(top, &t0, sizeof(t0), cudaMemcpyHostToDevice, s));
+        VR_CUDA(cudaMemcpyAsync(hrem, rem, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        VR_CUDA(cudaMemcpyAsync(hrem + 1, overflow, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        VR_CUDA(cudaMemcpyAsync(&htop, top, sizeof(htop), cudaMemcpyDeviceToHost, s));
+        VR_CUDA(cudaStreamSynchronize(s));
+        if (hrem[1] || htop > (unsigned long long)cap / 2) {
+          // Compact the live columns into a pool four times the live size (and
+          // at least as large as before).
+          int64_t *noff, *nbs;
+          VR_TRY(dv.get(&noff, E + 1));
+          VR_TRY(dv.get(&nbs, scan_tmp_slots(E)));
+          VR_TRY((scan_exclusive<int32_t, int64_t>(clen, noff, E, nbs, s)));
+          int64_t live = 0;
+          VR_CUDA(cudaMemcpyAsync(&live, noff + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+          VR_CUDA(cudaStreamSynchronize(s));
+          const int64_t ncap = std::max<int64_t>(cap, 4 * live + (1 << 20));
+          int32_t *npool;
+          int64_t *ncoff;
+          VR_TRY(dv.get(&npool, ncap));
+          VR_TRY(dv.get(&ncoff, E));
+          k_compact<<<bc_grid(E), BC_THREADS, 0, s>>>(E, coff, clen, noff, pool, npool, ncoff);
+          count_launch();
+          VR_CUDA(cudaGetLastError());
+          dv.release(pool);
+          dv.release(coff);
+          dv.release(noff);
+          dv.release(nbs);
+          pool = npool;
+          coff = ncoff;
+          cap = ncap;
+          const unsigned long long t0 = (unsigned long long)live;
+          VR_CUDA(cudaMemcpyAsync(top, &t0, sizeof(t0), cudaMemcpyHostToDevice, s));
+          continue;
+        }
+        if (hrem[0] == 0) break;
       }
     }
     k_pairs1<<<bc_grid(E), BC_THREADS, 0, s>>>(E, coff, clen, pool, pair_tri, pair_edge);
