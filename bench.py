@@ -505,6 +505,85 @@ def run_serve_bench(args):
     return 0
 
 
+def run_bars_bench(args):
+    """One step = build the complex and compute its barcodes in every
+    dimension on the device (GPU reduction of the boundary matrix)."""
+    import ctypes
+    import torch
+    import paper_1809_04424_b300 as vr
+    WORKLOAD, make, dtype_name = WORKLOADS[args.config]
+    cloud = make()
+    L = vr.lib()
+    src = torch.from_numpy(cloud.points).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    W = max(args.warmup, 3)
+
+    def step():
+        c = gpu_build(cloud, src)
+        nb = [len(c.barcode(k)) for k in range(cloud.maxdim + 1)]
+        return c, nb
+
+    for _ in range(W):
+        c, nbars = step()
+        counts = c.counts()[0]
+        del c
+    torch.cuda.synchronize()
+    L.vr_profile_select(None)
+    L.vr_profile_reset()
+    L.vr_profile_enable(1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(0) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record()
+            c, _ = step()
+            ev[k][1].record()
+            del c
+        torch.cuda.synchronize()
+    L.vr_profile_enable(0)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    phases = {}
+    for i in range(L.vr_profile_phases()):
+        nm, t, calls, nl = ctypes.c_char_p(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        L.vr_profile_phase(i, ctypes.byref(nm), ctypes.byref(t), ctypes.byref(calls), ctypes.byref(nl))
+        if nm.value.decode().startswith("bars."):
+            phases[nm.value.decode()] = round(t.value / max(calls.value, 1), 3)
+    simplices = sum(counts)
+    cpu = None
+    if args.cpu_seconds > 0:
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            cx = oracle_build_keep(cloud)
+            for k in range(cloud.maxdim + 1):
+                cx.barcode(k)
+            reps += 1
+            if time.perf_counter() - t0 >= args.cpu_seconds:
+                break
+        el = time.perf_counter() - t0
+        cpu = {"value": simplices * reps / el, "unit": "simplices/s", "cores": 1, "kind": "oracle",
+               "sample": f"{reps} build(s) + barcodes of the workload in {el:.1f} s, single-threaded "
+                         "(column algorithm in homology)"}
+    line = {"metric": "VR simplices/s, build + barcodes of every dimension", "value": simplices * args.steps / (ms / 1e3),
+            "unit": "simplices/s", "n_gpus": 1, "steps": args.steps, "warmup": W,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype_name, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "counts": counts, "bars_per_dim": nbars,
+                       "l2": "flushed between steps (256 MB write)"},
+            "e2e": None, "gpu_launches": None, "roofline": None,
+            "roofline_note": "the reduction is latency-bound on chains of column additions; see bars phases",
+            "bars_phases_ms": phases, "clocks": clk.summary(), "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def oracle_build_keep(cloud):
+    import oracle
+    if isinstance(cloud, synth.Matrix):
+        return oracle.vr_build_dmat(cloud.points, cloud.maxdim, cloud.maxrad, keep_handle=True)
+    return oracle.vr_build(cloud.points, cloud.maxdim, cloud.maxrad, keep_handle=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -518,7 +597,11 @@ def main():
                     help="workload (default: the headline torus cloud)")
     ap.add_argument("--n-clouds", type=int, default=4096, help="clouds of the batch workload")
     ap.add_argument("--n-requests", type=int, default=20000, help="requests of the serving workload")
+    ap.add_argument("--bars", action="store_true",
+                    help="time build + persistence barcodes of every dimension (the reduction step)")
     args = ap.parse_args()
+    if args.bars and args.impl != "reference":
+        return run_bars_bench(args)
     if args.config == "batch" and args.impl != "reference":
         return run_batch_bench(args)
     if args.config == "serve" and args.impl != "reference":
