@@ -31,7 +31,7 @@ _LIB = os.path.join(_BUILD, "libvr_oracle.so")
 _CFLAGS = ["-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
 
 I8, I32, F32 = 1, 2, 3
-MAXDIM = 2
+MAXDIM = 3
 
 
 def build(force: bool = False) -> str:

@@ -133,7 +133,7 @@ int vro_dense_rank(const double *values, int64_t m, int64_t *rank) {
 
 /* ---------------------------------------------------------------- steps 4-5 */
 
-typedef struct { int32_t g, a, b, c; } simp;
+typedef struct { int32_t g, a, b, c, d; } simp;
 
 static int cmp_simp(const void *x, const void *y) {
   const simp *p = (const simp *)x, *q = (const simp *)y;
@@ -141,7 +141,13 @@ static int cmp_simp(const void *x, const void *y) {
   if (p->a != q->a) return p->a < q->a ? -1 : 1;
   if (p->b != q->b) return p->b < q->b ? -1 : 1;
   if (p->c != q->c) return p->c < q->c ? -1 : 1;
+  if (p->d != q->d) return p->d < q->d ? -1 : 1;
   return 0;
+}
+
+static int cmp_i64pair(const void *x, const void *y) {
+  const int64_t *p = (const int64_t *)x, *q = (const int64_t *)y;
+  return p[0] < q[0] ? -1 : p[0] > q[0];
 }
 
 static void clear(vro_complex *c) { memset(c, 0, sizeof(*c)); }
@@ -198,7 +204,7 @@ static int finish_build(vro_complex *out, int32_t n, int32_t maxdim, int is_floa
     /* Step 4: edges in (grade, i, j) order. */
     simp *es = (simp *)malloc(sizeof(simp) * (size_t)(m + 1));
     if (!es) goto oom_pairs;
-    for (int64_t t = 0; t < m; ++t) { es[t].g = eg[t]; es[t].a = ei[t]; es[t].b = ej[t]; es[t].c = 0; }
+    for (int64_t t = 0; t < m; ++t) { es[t].g = eg[t]; es[t].a = ei[t]; es[t].b = ej[t]; es[t].c = 0; es[t].d = 0; }
     qsort(es, (size_t)m, sizeof(simp), cmp_simp);
     out->count[1] = m;
     out->verts[1] = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * m + 1));
@@ -246,7 +252,7 @@ static int finish_build(vro_complex *out, int32_t n, int32_t maxdim, int is_floa
           int32_t g = es[t].g;
           if (es[oik].g > g) g = es[oik].g;
           if (es[ojk].g > g) g = es[ojk].g;
-          ts[T].g = g; ts[T].a = i; ts[T].b = j; ts[T].c = k;
+          ts[T].g = g; ts[T].a = i; ts[T].b = j; ts[T].c = k; ts[T].d = 0;
           ++T;
         }
       }
@@ -278,6 +284,83 @@ static int finish_build(vro_complex *out, int32_t n, int32_t maxdim, int is_floa
         out->rowidx[2][3 * t + 2] = r[2];
       }
       out->colptr[2][T] = 3 * T;
+
+      if (maxdim >= 3) {
+        /* Tetrahedra (a,b,c,d), a<b<c<d: present iff all six edges are kept;
+         * grade = the largest edge grade (= the largest face grade). */
+        int64_t *lexkey = (int64_t *)malloc(sizeof(int64_t) * (size_t)(T + 1));
+        int64_t *lexord = (int64_t *)malloc(sizeof(int64_t) * (size_t)(T + 1));
+        int64_t qcap = 1024, Q = 0;
+        simp *qs = (simp *)malloc(sizeof(simp) * (size_t)qcap);
+        if (!lexkey || !lexord || !qs) { free(lexkey); free(lexord); free(qs); free(ts); free(ord); free(es); goto oom_pairs; }
+        /* Order index of a triangle from its vertices: triangles sorted by
+         * their lexicographic key, searched by bisection. */
+        for (int64_t t = 0; t < T; ++t) lexord[t] = t;
+        const int64_t nn = n;
+        for (int64_t t = 0; t < T; ++t) lexkey[t] = ((int64_t)ts[t].a * nn + ts[t].b) * nn + ts[t].c;
+        /* insertion into lexicographic order via qsort on (key, index) pairs */
+        int64_t *pairs = (int64_t *)malloc(sizeof(int64_t) * 2 * (size_t)(T + 1));
+        if (!pairs) { free(lexkey); free(lexord); free(qs); free(ts); free(ord); free(es); goto oom_pairs; }
+        for (int64_t t = 0; t < T; ++t) { pairs[2 * t] = lexkey[t]; pairs[2 * t + 1] = t; }
+        qsort(pairs, (size_t)T, 2 * sizeof(int64_t), cmp_i64pair);
+        for (int64_t t = 0; t < T; ++t) { lexkey[t] = pairs[2 * t]; lexord[t] = pairs[2 * t + 1]; }
+        free(pairs);
+        for (int64_t t = 0; t < T; ++t) {
+          const int32_t a = ts[t].a, b = ts[t].b, c = ts[t].c;
+          for (int32_t dv = c + 1; dv < n; ++dv) {
+            const int32_t oad = ord[(int64_t)a * n + dv], obd = ord[(int64_t)b * n + dv], ocd = ord[(int64_t)c * n + dv];
+            if (oad < 0 || obd < 0 || ocd < 0) continue;
+            if (Q == qcap) {
+              qcap *= 2;
+              simp *nq = (simp *)realloc(qs, sizeof(simp) * (size_t)qcap);
+              if (!nq) { free(lexkey); free(lexord); free(qs); free(ts); free(ord); free(es); goto oom_pairs; }
+              qs = nq;
+            }
+            int32_t g = ts[t].g;
+            if (es[oad].g > g) g = es[oad].g;
+            if (es[obd].g > g) g = es[obd].g;
+            if (es[ocd].g > g) g = es[ocd].g;
+            qs[Q].g = g; qs[Q].a = a; qs[Q].b = b; qs[Q].c = c; qs[Q].d = dv;
+            ++Q;
+          }
+        }
+        qsort(qs, (size_t)Q, sizeof(simp), cmp_simp);
+        out->count[3] = Q;
+        out->verts[3] = (int32_t *)malloc(sizeof(int32_t) * (size_t)(4 * Q + 1));
+        out->grade[3] = (int32_t *)malloc(sizeof(int32_t) * (size_t)(Q + 1));
+        out->colptr[3] = (int64_t *)malloc(sizeof(int64_t) * (size_t)(Q + 1));
+        out->rowidx[3] = (int32_t *)malloc(sizeof(int32_t) * (size_t)(4 * Q + 1));
+        if (!out->verts[3] || !out->grade[3] || !out->colptr[3] || !out->rowidx[3]) {
+          free(lexkey); free(lexord); free(qs); free(ts); free(ord); free(es); goto oom_pairs;
+        }
+        for (int64_t t = 0; t < Q; ++t) {
+          const int32_t a = qs[t].a, b = qs[t].b, c = qs[t].c, dv = qs[t].d;
+          out->verts[3][4 * t] = a;
+          out->verts[3][4 * t + 1] = b;
+          out->verts[3][4 * t + 2] = c;
+          out->verts[3][4 * t + 3] = dv;
+          out->grade[3][t] = qs[t].g;
+          /* Step 7, dimension 3: the faces (b,c,d), (a,c,d), (a,b,d), (a,b,c)
+           * as triangle order indices, listed ascending. */
+          int64_t fk[4] = {((int64_t)b * nn + c) * nn + dv, ((int64_t)a * nn + c) * nn + dv,
+                           ((int64_t)a * nn + b) * nn + dv, ((int64_t)a * nn + b) * nn + c};
+          int32_t r[4];
+          for (int x = 0; x < 4; ++x) {
+            int64_t lo = 0, hi = T;
+            while (lo < hi) { int64_t mid = (lo + hi) / 2; if (lexkey[mid] < fk[x]) lo = mid + 1; else hi = mid; }
+            r[x] = (int32_t)lexord[lo];
+          }
+          for (int x = 0; x < 4; ++x)
+            for (int y = x + 1; y < 4; ++y)
+              if (r[y] < r[x]) { int32_t sw = r[x]; r[x] = r[y]; r[y] = sw; }
+          out->colptr[3][t] = 4 * t;
+          for (int x = 0; x < 4; ++x) out->rowidx[3][4 * t + x] = r[x];
+        }
+        out->colptr[3][Q] = 4 * Q;
+        free(lexkey);
+        free(lexord);
+        free(qs);
+      }
       free(ts);
       free(ord);
     }

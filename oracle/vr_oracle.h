@@ -39,7 +39,7 @@ extern "C" {
 #define VRO_I32 2
 #define VRO_F32 3
 
-#define VRO_MAXDIM 2
+#define VRO_MAXDIM 3
 
 typedef struct {
   int32_t n, d, maxdim;

@@ -37,6 +37,9 @@ MUTANTS = [
     ("pivot rows not killed", "killed[lowk1[j]] = 1;", ""),
     ("bar endpoints swapped", "b[nb] = gb; e[nb] = gd;", "b[nb] = gd; e[nb] = gb;"),
     ("matrix cap strict", "      if (v <= maxrad) {", "      if (v < maxrad) {"),
+    ("tetrahedron apex skipped", "for (int32_t dv = c + 1; dv < n; ++dv)", "for (int32_t dv = c + 2; dv < n; ++dv)"),
+    ("tetrahedron grade ignores one edge", "            if (es[ocd].g > g) g = es[ocd].g;\n", ""),
+    ("tetrahedron face wrong", "((int64_t)a * nn + c) * nn + dv,", "((int64_t)a * nn + b) * nn + dv,"),
     ("matrix values squared", "if (is_float) df[m] = v;", "if (is_float) df[m] = v * v;"),
 ]
 
@@ -48,6 +51,8 @@ def _pins():
         yield lambda s=s: P.test_brute_force_tiny(s)
     for s in range(4):
         yield lambda s=s: P.test_dmat_brute_force_tiny(s)
+    for s in range(3):
+        yield lambda s=s: P.test_tetrahedra_brute_force_tiny(s)
     yield P.test_sortperm_worked_example
     yield P.test_cap_is_inclusive
     yield P.test_float_distance_within_fp64_bound

@@ -320,7 +320,7 @@ def test_integer_distance_exact_at_extremes():
 def test_errors():
     pts = np.zeros((3, 2), np.float32)
     with pytest.raises(oracle.OracleError):
-        oracle.vr_build(pts, 3)
+        oracle.vr_build(pts, 4)
     with pytest.raises(oracle.OracleError):
         oracle.vr_build(pts, 2, -1.0)
     with pytest.raises(oracle.OracleError):
@@ -420,3 +420,69 @@ def test_dmat_rejects_invalid_matrices():
         oracle.vr_build_dmat(np.array([[0, np.nan], [np.nan, 0]], np.float32), 1)
     ok = oracle.vr_build_dmat(np.array([[0.0, -0.0], [0.0, 0.0]], np.float32), 1)
     assert ok.dims[1].grade.tolist() == [0]
+
+
+# ------------------------------------------------------------- tetrahedra
+
+def brute_tetra(points, maxrad):
+    """Tetrahedra of a tiny cloud by direct enumeration of 4-subsets: grade =
+    largest edge grade, order (grade, a, b, c, d), faces as triangle order
+    indices, ascending."""
+    values, edges, grades, ordr, tris = brute_force(points, 2, maxrad)
+    eg = dict(zip(edges, grades))
+    tord = {t[1:]: i for i, t in enumerate(tris)}
+    n = points.shape[0]
+    tets = sorted((max(eg[(a, b)], eg[(a, c)], eg[(a, d)], eg[(b, c)], eg[(b, d)], eg[(c, d)]), a, b, c, d)
+                  for a, b, c, d in itertools.combinations(range(n), 4)
+                  if all(e in eg for e in itertools.combinations((a, b, c, d), 2)))
+    rows = []
+    for _, a, b, c, d in tets:
+        rows += sorted([tord[(b, c, d)], tord[(a, c, d)], tord[(a, b, d)], tord[(a, b, c)]])
+    return tets, rows
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_tetrahedra_brute_force_tiny(seed):
+    g = synth.rng(1300 + seed)
+    n = int(g.integers(4, 11))
+    dtype = [np.int8, np.int32, np.float32][seed % 3]
+    pts = synth.random_cloud(n, 3, dtype, seed=1400 + seed, lo=-5, hi=5)
+    cap = [math.inf, 4.0, 6.0][seed % 3]
+    tets, rows = brute_tetra(pts, cap)
+    cx = oracle.vr_build(pts, 3, cap)
+    d3 = cx.dims[3]
+    assert d3.count == len(tets)
+    assert [tuple(x) for x in d3.verts.tolist()] == [t[1:] for t in tets]
+    assert d3.grade.tolist() == [t[0] for t in tets]
+    assert d3.colptr.tolist() == [4 * t for t in range(len(tets) + 1)]
+    assert d3.rowidx.tolist() == rows
+
+
+def test_counts_without_cap_dim3():
+    """No cap: C(n, 4) tetrahedra."""
+    pts = synth.random_cloud(11, 3, np.int32, seed=5)
+    cx = oracle.vr_build(pts, 3)
+    assert [cx.dims[k].count for k in range(4)] == [math.comb(11, k + 1) for k in range(4)]
+
+
+def test_boundary_of_4_simplex():
+    """The five standard basis vectors of R^5 are pairwise at d^2 = 2: the
+    3-skeleton of the 4-simplex is a 3-sphere -- bars H0 4x[0,1) + [0,inf),
+    H1 and H2 none, H3 [1,inf)."""
+    pts = np.eye(5, dtype=np.int32)
+    cx = oracle.vr_build(pts, 3, keep_handle=True)
+    assert [cx.dims[k].count for k in range(4)] == [5, 10, 10, 5]
+    assert sorted(map(tuple, cx.barcode(0).tolist())) == [(0, -1), (0, 1), (0, 1), (0, 1), (0, 1)]
+    assert cx.barcode(1).tolist() == []
+    assert cx.barcode(2).tolist() == []
+    assert cx.barcode(3).tolist() == [[1, -1]]
+
+
+@pytest.mark.parametrize("seed,dtype,n,cap", [(31, np.int8, 18, 50.0), (32, np.float32, 16, 70.0)])
+def test_euler_characteristic_every_grade_dim3(seed, dtype, n, cap):
+    pts = synth.random_cloud(n, 3, dtype, seed=seed, lo=-60, hi=60)
+    cx = oracle.vr_build(pts, 3, cap, keep_handle=True)
+    for g in range(len(cx.grade_value)):
+        chi = sum((-1) ** k * int((cx.dims[k].grade <= g).sum()) for k in range(4))
+        b = oracle.betti(cx, g)
+        assert chi == b[0] - b[1] + b[2] - b[3], g
