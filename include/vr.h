@@ -67,7 +67,9 @@ typedef enum vr_dtype { VR_I8 = 1, VR_I32 = 2, VR_F32 = 3 } vr_dtype;
 
 /* Limits.  Vertex ids travel in 13-bit fields of 64-bit sort keys. */
 #define VR_MAX_POINTS 8192
-#define VR_MAX_DIM_SIMPLEX 2
+#define VR_MAX_DIM_SIMPLEX 3
+/* vr_build_batch and the server build up to triangles. */
+#define VR_MAX_DIM_BATCH 2
 /* Integer squared distances of kept edges must be below 2^38. */
 #define VR_MAX_INT_D2_BITS 38
 /* |float coordinate| must not exceed 2^50 (fp32 squares stay finite). */
@@ -102,7 +104,9 @@ typedef struct vr_build_stats {
  *           `stream`).  Borrowed: it must stay valid until the call returns.
  *   n       1 .. VR_MAX_POINTS, else VR_ERR_RANGE.
  *   d       >= 1, else VR_ERR_ARG.
- *   maxdim  top simplex dimension, 0 .. 2; 3 and above give VR_ERR_UNSUPPORTED.
+ *   maxdim  top simplex dimension, 0 .. 3 (3: tetrahedra, whose boundary
+ *           columns list the order indices of their four triangles); above
+ *           3 gives VR_ERR_UNSUPPORTED.
  *   maxrad  inclusive radius cap (keep |x_i - x_j| <= maxrad).  +INFINITY
  *           keeps every pair.  NaN or negative gives VR_ERR_ARG.  Integer
  *           inputs keep d^2 <= floor(fl(maxrad*maxrad)); float inputs keep
@@ -125,7 +129,7 @@ VR_API vr_status vr_build(const void *points, int32_t n, int32_t d, vr_dtype dty
  *           host memory (detected and copied in on `stream`).  Borrowed until
  *           the call returns.
  *   n       1 .. VR_MAX_POINTS, else VR_ERR_RANGE.
- *   maxdim  0 .. 2 as for vr_build.
+ *   maxdim  0 .. 3 as for vr_build.
  *   maxrad  inclusive cap on the VALUE (keep D[i][j] <= maxrad, no squaring);
  *           +INFINITY keeps every pair.
  * Edges come from the strict upper triangle (i < j); the diagonal is ignored
@@ -169,8 +173,8 @@ VR_API vr_status vr_complex_dim(const vr_complex *c, int32_t k, vr_dim_view *vie
 VR_API vr_status vr_complex_grade_values(const vr_complex *c, const double **values,
                                   int64_t *ngrades);
 
-/* Host-side sizes: counts[k] for k = 0..2 (0 above maxdim) and maxdim. */
-VR_API vr_status vr_complex_counts(const vr_complex *c, int64_t counts[3],
+/* Host-side sizes: counts[k] for k = 0..3 (0 above maxdim) and maxdim. */
+VR_API vr_status vr_complex_counts(const vr_complex *c, int64_t counts[VR_MAX_DIM_SIMPLEX + 1],
                             int32_t *maxdim);
 
 VR_API vr_status vr_complex_stats(const vr_complex *c, vr_build_stats *stats);

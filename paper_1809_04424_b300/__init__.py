@@ -240,10 +240,10 @@ def vr_complex_grade_values(handle):
 
 
 def vr_complex_counts(handle):
-    c = (ctypes.c_int64 * 3)()
+    c = (ctypes.c_int64 * 4)()
     m = ctypes.c_int32()
     _check(lib().vr_complex_counts(ctypes.c_void_p(handle), c, ctypes.byref(m)))
-    return [c[0], c[1], c[2]], m.value
+    return [c[k] for k in range(max(3, m.value + 1))], m.value
 
 
 def vr_complex_stats(handle) -> dict:

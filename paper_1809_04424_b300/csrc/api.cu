@@ -176,9 +176,9 @@ vr_status vr_complex_grade_values(const vr_complex *c, const double **values, in
   return VR_OK;
 }
 
-vr_status vr_complex_counts(const vr_complex *c, int64_t counts[3], int32_t *maxdim) {
+vr_status vr_complex_counts(const vr_complex *c, int64_t counts[VR_MAX_DIM_SIMPLEX + 1], int32_t *maxdim) {
   if (!c || !counts) { set_error("NULL argument"); return VR_ERR_ARG; }
-  for (int k = 0; k < 3; ++k) counts[k] = c->count[k];
+  for (int k = 0; k <= VR_MAX_DIM_SIMPLEX; ++k) counts[k] = c->count[k];
   if (maxdim) *maxdim = c->maxdim;
   return VR_OK;
 }
@@ -225,7 +225,7 @@ vr_status vr_complex_barcode(vr_complex *c, int32_t dim, vr_stream_t stream, int
 vr_status vr_complex_bars(const vr_complex *c, int32_t dim, const int32_t **birth, const int32_t **death,
                           int64_t *nbars) {
   if (!c || !birth || !death || !nbars) { set_error("NULL argument"); return VR_ERR_ARG; }
-  if (dim < 0 || dim > 2 || c->nbars[dim] < 0) { set_error("no barcode of dimension %d computed", dim); return VR_ERR_ARG; }
+  if (dim < 0 || dim > 3 || c->nbars[dim] < 0) { set_error("no barcode of dimension %d computed", dim); return VR_ERR_ARG; }
   *birth = c->bar_birth[dim];
   *death = c->bar_death[dim];
   *nbars = c->nbars[dim];
@@ -234,7 +234,7 @@ vr_status vr_complex_bars(const vr_complex *c, int32_t dim, const int32_t **birt
 
 vr_status vr_complex_bars_to_host(const vr_complex *c, int32_t dim, int32_t *birth, int32_t *death) {
   if (!c || !birth || !death) { set_error("NULL argument"); return VR_ERR_ARG; }
-  if (dim < 0 || dim > 2 || c->nbars[dim] < 0) { set_error("no barcode of dimension %d computed", dim); return VR_ERR_ARG; }
+  if (dim < 0 || dim > 3 || c->nbars[dim] < 0) { set_error("no barcode of dimension %d computed", dim); return VR_ERR_ARG; }
   const int64_t m = c->nbars[dim];
   if (m) {
     VR_CUDA(cudaMemcpyAsync(birth, c->bar_birth[dim], sizeof(int32_t) * m, cudaMemcpyDeviceToHost, c->stream));

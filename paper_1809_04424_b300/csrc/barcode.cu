@@ -129,11 +129,13 @@ static __global__ void k_compact_idx(const int32_t *flag, const int64_t *pos, in
 
 // ------------------------------------------------------------ dimension 1
 
-// Coboundary entries (face edge, triangle) in triangle order.
-static __global__ void k_cob_keys(const int32_t *trow, int64_t T, uint64_t *keys, int32_t *cnt) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < 3 * T; p += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t e = (uint32_t)trow[p];
-    keys[p] = ((uint64_t)e << 32) | (uint64_t)(p / 3);
+// Coboundary entries (face, coface) in coface order; `faces` faces per
+// coface in its boundary column.
+static __global__ void k_cob_keys(const int32_t *rows, int64_t T, int faces, uint64_t *keys, int32_t *cnt) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < faces * T;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t e = (uint32_t)rows[p];
+    keys[p] = ((uint64_t)e << 32) | (uint64_t)(p / faces);
     atomicAdd(&cnt[e], 1);
   }
 }
@@ -143,11 +145,15 @@ static __global__ void k_cob_cols(const uint64_t *keys, int64_t L, int32_t *pool
     pool[p] = (int32_t)(uint32_t)keys[p];
 }
 
-// Columns of the reduction: edges outside the forest with their coface list.
-static __global__ void k_col_init(int64_t E, const uint8_t *msf, const int32_t *cptr, int64_t *coff, int32_t *clen) {
+// Columns of the reduction: the positive simplices (not killing one of the
+// dimension below: neg8 != 0 / neg32 >= 0 mark the negative ones) with their
+// coface list.
+static __global__ void k_col_init(int64_t E, const uint8_t *neg8, const int32_t *neg32, const int32_t *cptr,
+                                  int64_t *coff, int32_t *clen) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    const bool neg = (neg8 && neg8[e]) || (neg32 && neg32[e] >= 0);
     coff[e] = cptr[e];
-    clen[e] = msf[e] ? 0 : cptr[e + 1] - cptr[e];
+    clen[e] = neg ? 0 : cptr[e + 1] - cptr[e];
   }
 }
 
@@ -378,9 +384,10 @@ struct BarSrc {
   int dim, maxdim;
   int64_t m0, m1;                 // simplices of dimension dim / dim+1
   const int32_t *g0, *g1;         // their grades
-  const int32_t *killer_of;       // dim 0: killed vertex per edge; dim 1: edge per triangle (-1 none)
-  const uint8_t *neg0;            // dim 1: forest edges (zero in the edge reduction)
-  const int32_t *paired0;         // dim >= 1: the dim-simplex's killer (-1 none); dim 0: killed flag array
+  const int32_t *killer_of;       // per (dim+1)-simplex: the dim-simplex it kills (-1: none)
+  const uint8_t *neg8;            // negative dim-simplices (they kill one of dimension dim-1) ...
+  const int32_t *neg32;           // ... as a flag array or as a partner array (>= 0)
+  const int32_t *kill;            // per dim-simplex: the (dim+1)-simplex killing it (-1: none)
 };
 
 __device__ __forceinline__ bool bar_at(const BarSrc &b, int64_t q, int32_t &birth, int32_t &death) {
@@ -392,8 +399,9 @@ __device__ __forceinline__ bool bar_at(const BarSrc &b, int64_t q, int32_t &birt
     return birth != death;
   }
   const int64_t s = q - b.m1;  // essential: positive and never killed
-  if (b.dim >= 1 && b.neg0 && b.neg0[s]) return false;
-  if (b.paired0 && b.paired0[s] >= 0) return false;
+  if (b.neg8 && b.neg8[s]) return false;
+  if (b.neg32 && b.neg32[s] >= 0) return false;
+  if (b.kill && b.kill[s] >= 0) return false;
   birth = b.g0[s];
   death = -1;
   return true;
@@ -463,80 +471,23 @@ static vr_status read_i32(const int32_t *d, int32_t *h, cudaStream_t s) {
   return VR_OK;
 }
 
-// Pairs of dimension 0 (killed vertex per edge) and, for maxdim 2, of
-// dimension 1 (edge per triangle and triangle per edge).  Kept on the complex.
-static vr_status compute_pairs(vr_complex *c, cudaStream_t s) {
-  Dev dv(s);
-  Prof prof(s);
-  const int n = c->n;
-  const int64_t E = c->maxdim >= 1 ? c->count[1] : 0;
-  const int64_t T = c->maxdim >= 2 ? c->count[2] : 0;
-  int32_t *killed_by_edge = nullptr, *vkill = nullptr;
-  uint8_t *msf = nullptr;
-  int32_t *pair_tri = nullptr, *pair_edge = nullptr;
-  VR_TRY(dv.get(&killed_by_edge, E, true, &c->bar_allocs));
-  VR_TRY(dv.get(&vkill, n, true, &c->bar_allocs));
-  VR_TRY(dv.get(&msf, E, true, &c->bar_allocs));
-  VR_CUDA(cudaMemsetAsync(killed_by_edge, 0xff, sizeof(int32_t) * std::max<int64_t>(E, 1), s));
-  VR_CUDA(cudaMemsetAsync(vkill, 0xff, sizeof(int32_t) * n, s));
-  VR_CUDA(cudaMemsetAsync(msf, 0, std::max<int64_t>(E, 1), s));
-  int32_t *hflag = nullptr;
-  VR_CUDA(cudaMallocHost((void **)&hflag, sizeof(int32_t)));
-  struct HostFree {
-    int32_t *p;
-    ~HostFree() { cudaFreeHost(p); }
-  } hf{hflag};
-
-  if (E > 0) {
-    // Boruvka rounds for the spanning forest.
-    prof.begin("bars.forest");
-    int32_t *comp, *best, *next, *changed;
-    VR_TRY(dv.get(&comp, n));
-    VR_TRY(dv.get(&best, n));
-    VR_TRY(dv.get(&next, n));
-    VR_TRY(dv.get(&changed, 1));
-    k_bv_init<<<bc_grid(n), BC_THREADS, 0, s>>>(n, comp, best);
-    count_launch();
-    for (int round = 0; round < 64; ++round) {
-      VR_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), s));
-      k_bv_choose<<<bc_grid(E), BC_THREADS, 0, s>>>(c->verts[1], E, comp, best);
-      k_bv_hook<<<bc_grid(n), BC_THREADS, 0, s>>>(c->verts[1], n, comp, best, next, msf, changed);
-      k_bv_jump<<<bc_grid(n), BC_THREADS, 0, s>>>(n, next, comp, best);
-      count_launch(3);
-      VR_CUDA(cudaGetLastError());
-      VR_TRY(read_i32(changed, hflag, s));
-      if (!*hflag) break;
-    }
-    prof.end();
-    // Forest edges in order, then the elder rule.
-    prof.begin("bars.elder");
-    int32_t *flag, *fedges;
-    int64_t *bs;
-    VR_TRY(dv.get(&flag, E));
-    VR_TRY(dv.get(&fedges, n));
-    int64_t *fpos;
-    VR_TRY(dv.get(&fpos, E + 1));
-    VR_TRY(dv.get(&bs, scan_tmp_slots(E)));
-    k_u8_to_i32<<<bc_grid(E), BC_THREADS, 0, s>>>(msf, E, flag);
-    count_launch();
-    VR_TRY((scan_exclusive<int32_t, int64_t>(flag, fpos, E, bs, s)));
-    k_compact_idx<<<bc_grid(E), BC_THREADS, 0, s>>>(flag, fpos, E, fedges);
-    count_launch();
-    k_elder<<<1, 32, 0, s>>>(c->verts[1], fedges, fpos + E, n, killed_by_edge);
-    k_killed_vertices<<<bc_grid(E), BC_THREADS, 0, s>>>(E, killed_by_edge, vkill);
-    count_launch(2);
-    VR_CUDA(cudaGetLastError());
-    prof.end();
-  }
-
-  if (T > 0) {
-    prof.begin("bars.coboundary");
+// Pairs of dimension k (k-simplices x (k+1)-simplices) by the batch-ordered
+// coboundary reduction.  E = number of k-simplices (columns), T = number of
+// (k+1)-simplices (rows); a column is cleared when its k-simplex is negative
+// (neg8[s] != 0 or neg32[s] >= 0: it kills a (k-1)-simplex).  Outputs, kept
+// on the complex: pair_tri[j] = the k-simplex the (k+1)-simplex j kills,
+// pair_edge[s] = the (k+1)-simplex killing s (-1: none).
+static vr_status reduce_cohomology(vr_complex *c, int k, cudaStream_t s, Dev &dv, Prof &prof, const uint8_t *neg8,
+                                   const int32_t *neg32, int32_t *&pair_tri, int32_t *&pair_edge) {
+  const int64_t E = c->count[k], T = c->count[k + 1];
+  {
+    prof.begin(k == 1 ? "bars.coboundary" : "bars.coboundary2");
     VR_TRY(dv.get(&pair_tri, T, true, &c->bar_allocs));
     VR_TRY(dv.get(&pair_edge, E, true, &c->bar_allocs));
     VR_CUDA(cudaMemsetAsync(pair_tri, 0xff, sizeof(int32_t) * T, s));
     VR_CUDA(cudaMemsetAsync(pair_edge, 0xff, sizeof(int32_t) * E, s));
     // Coboundary lists: (edge, triangle) entries sorted by edge, stable in t.
-    const int64_t L = 3 * T;
+    const int64_t L = (int64_t)(k + 2) * T;
     uint64_t *keys;
     int32_t *cnt, *cptr;
     RadixScratch rs{};
@@ -550,7 +501,7 @@ static vr_status compute_pairs(vr_complex *c, cudaStream_t s) {
     VR_TRY(dv.get(&cnt, E));
     VR_TRY(dv.get(&cptr, E + 1));
     VR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * E, s));
-    k_cob_keys<<<bc_grid(L), BC_THREADS, 0, s>>>(c->rowidx[2], T, keys, cnt);
+    k_cob_keys<<<bc_grid(L), BC_THREADS, 0, s>>>(c->rowidx[k + 1], T, k + 2, keys, cnt);
     count_launch();
     int ebits = 1;
     while ((1ll << ebits) < E) ++ebits;
@@ -574,12 +525,12 @@ static vr_status compute_pairs(vr_complex *c, cudaStream_t s) {
     VR_TRY(dv.get(&overflow, 1));
     const unsigned long long top0 = (unsigned long long)L;
     VR_CUDA(cudaMemcpyAsync(top, &top0, sizeof(top0), cudaMemcpyHostToDevice, s));
-    k_col_init<<<bc_grid(E), BC_THREADS, 0, s>>>(E, msf, cptr, coff, clen);
+    k_col_init<<<bc_grid(E), BC_THREADS, 0, s>>>(E, neg8, neg32, cptr, coff, clen);
     count_launch();
     VR_CUDA(cudaGetLastError());
     prof.end();
 
-    prof.begin("bars.reduce");
+    prof.begin(k == 1 ? "bars.reduce" : "bars.reduce2");
     // Active columns in ascending edge order; processing takes them from the
     // youngest.
     int32_t *aflag, *act, *final_owner, *rem;
@@ -665,6 +616,81 @@ static vr_status compute_pairs(vr_complex *c, cudaStream_t s) {
     VR_TRY(flags_to_status(hs));
     prof.end();
   }
+  return VR_OK;
+}
+
+// Pairs of dimension 0 (killed vertex per edge) and, for maxdim 2, of
+// dimension 1 (edge per triangle and triangle per edge).  Kept on the complex.
+static vr_status compute_pairs(vr_complex *c, cudaStream_t s) {
+  Dev dv(s);
+  Prof prof(s);
+  const int n = c->n;
+  const int64_t E = c->maxdim >= 1 ? c->count[1] : 0;
+  const int64_t T = c->maxdim >= 2 ? c->count[2] : 0;
+  int32_t *killed_by_edge = nullptr, *vkill = nullptr;
+  uint8_t *msf = nullptr;
+  int32_t *pair_tri = nullptr, *pair_edge = nullptr;
+  VR_TRY(dv.get(&killed_by_edge, E, true, &c->bar_allocs));
+  VR_TRY(dv.get(&vkill, n, true, &c->bar_allocs));
+  VR_TRY(dv.get(&msf, E, true, &c->bar_allocs));
+  VR_CUDA(cudaMemsetAsync(killed_by_edge, 0xff, sizeof(int32_t) * std::max<int64_t>(E, 1), s));
+  VR_CUDA(cudaMemsetAsync(vkill, 0xff, sizeof(int32_t) * n, s));
+  VR_CUDA(cudaMemsetAsync(msf, 0, std::max<int64_t>(E, 1), s));
+  int32_t *hflag = nullptr;
+  VR_CUDA(cudaMallocHost((void **)&hflag, sizeof(int32_t)));
+  struct HostFree {
+    int32_t *p;
+    ~HostFree() { cudaFreeHost(p); }
+  } hf{hflag};
+
+  if (E > 0) {
+    // Boruvka rounds for the spanning forest.
+    prof.begin("bars.forest");
+    int32_t *comp, *best, *next, *changed;
+    VR_TRY(dv.get(&comp, n));
+    VR_TRY(dv.get(&best, n));
+    VR_TRY(dv.get(&next, n));
+    VR_TRY(dv.get(&changed, 1));
+    k_bv_init<<<bc_grid(n), BC_THREADS, 0, s>>>(n, comp, best);
+    count_launch();
+    for (int round = 0; round < 64; ++round) {
+      VR_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), s));
+      k_bv_choose<<<bc_grid(E), BC_THREADS, 0, s>>>(c->verts[1], E, comp, best);
+      k_bv_hook<<<bc_grid(n), BC_THREADS, 0, s>>>(c->verts[1], n, comp, best, next, msf, changed);
+      k_bv_jump<<<bc_grid(n), BC_THREADS, 0, s>>>(n, next, comp, best);
+      count_launch(3);
+      VR_CUDA(cudaGetLastError());
+      VR_TRY(read_i32(changed, hflag, s));
+      if (!*hflag) break;
+    }
+    prof.end();
+    // Forest edges in order, then the elder rule.
+    prof.begin("bars.elder");
+    int32_t *flag, *fedges;
+    int64_t *bs;
+    VR_TRY(dv.get(&flag, E));
+    VR_TRY(dv.get(&fedges, n));
+    int64_t *fpos;
+    VR_TRY(dv.get(&fpos, E + 1));
+    VR_TRY(dv.get(&bs, scan_tmp_slots(E)));
+    k_u8_to_i32<<<bc_grid(E), BC_THREADS, 0, s>>>(msf, E, flag);
+    count_launch();
+    VR_TRY((scan_exclusive<int32_t, int64_t>(flag, fpos, E, bs, s)));
+    k_compact_idx<<<bc_grid(E), BC_THREADS, 0, s>>>(flag, fpos, E, fedges);
+    count_launch();
+    k_elder<<<1, 32, 0, s>>>(c->verts[1], fedges, fpos + E, n, killed_by_edge);
+    k_killed_vertices<<<bc_grid(E), BC_THREADS, 0, s>>>(E, killed_by_edge, vkill);
+    count_launch(2);
+    VR_CUDA(cudaGetLastError());
+    prof.end();
+  }
+
+  if (T > 0) VR_TRY(reduce_cohomology(c, 1, s, dv, prof, msf, nullptr, pair_tri, pair_edge));
+  int32_t *pair_tet = nullptr, *pair_tri2 = nullptr;
+  if (c->maxdim >= 3 && c->count[3] > 0 && T > 0)
+    VR_TRY(reduce_cohomology(c, 2, s, dv, prof, nullptr, pair_tri, pair_tet, pair_tri2));
+  c->pair_tet = pair_tet;
+  c->pair_tri2 = pair_tri2;
   c->killed_by_edge = killed_by_edge;
   c->vkill = vkill;
   c->msf = msf;
@@ -687,16 +713,22 @@ vr_status complex_barcode(vr_complex *c, int dim, cudaStream_t s, int64_t *nbars
   b.m0 = c->count[dim];
   b.g0 = c->grade[dim];
   if (dim < c->maxdim) {
-    b.m1 = c->count[dim + 1];
-    b.g1 = c->grade[dim + 1];
-    b.killer_of = dim == 0 ? c->killed_by_edge : c->pair_tri;
+    b.killer_of = dim == 0 ? c->killed_by_edge : dim == 1 ? c->pair_tri : c->pair_tet;
+    if (b.killer_of) {
+      b.m1 = c->count[dim + 1];
+      b.g1 = c->grade[dim + 1];
+    }
   }
-  if (dim == 0) b.paired0 = c->maxdim >= 1 ? c->vkill : nullptr;
+  if (dim == 0) b.kill = c->maxdim >= 1 ? c->vkill : nullptr;
   if (dim == 1) {
-    b.neg0 = c->msf;
-    b.paired0 = c->maxdim >= 2 ? c->pair_edge : nullptr;
+    b.neg8 = c->msf;
+    b.kill = c->maxdim >= 2 ? c->pair_edge : nullptr;
   }
-  if (dim == 2) b.paired0 = c->pair_tri;
+  if (dim == 2) {
+    b.neg32 = c->pair_tri;
+    b.kill = c->maxdim >= 3 ? c->pair_tri2 : nullptr;
+  }
+  if (dim == 3) b.neg32 = c->pair_tet;
   Dev dv(s);
   const int64_t L = b.m0 + b.m1;
   int32_t *flag;

@@ -572,7 +572,7 @@ vr_status make_desc(CloudDesc &c, int64_t pt, int64_t n, int d, vr_dtype dtype, 
   memset(&c, 0, sizeof(c));
   if (n < 1 || n > VR_MAX_POINTS) { set_error("cloud with %lld points", (long long)n); return VR_ERR_RANGE; }
   if (maxdim < 0) { set_error("maxdim < 0"); return VR_ERR_ARG; }
-  if (maxdim > VR_MAX_DIM_SIMPLEX) { set_error("maxdim above 2 is not offered"); return VR_ERR_UNSUPPORTED; }
+  if (maxdim > VR_MAX_DIM_BATCH) { set_error("maxdim above 2 is not offered for batches"); return VR_ERR_UNSUPPORTED; }
   if (std::isnan(maxrad) || maxrad < 0) { set_error("maxrad must be >= 0 and not NaN"); return VR_ERR_ARG; }
   c.pt = pt;
   c.n = (int32_t)n;

@@ -385,11 +385,12 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   if (maxdim >= 2 && E > 0) {
     prof.begin("tri_count");
     k_tri_count<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, E, adj, adjpre, W, nbr_ptr, nbr_ord, deg, up,
-                                                           lex_ptr, st, tcnt);
+                                                           lex_ptr, st, tcnt, maxdim >= 3 ? 1 : 0);
     count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int64_t>(tcnt, toff, E, bs_e, s)));
     VR_CUDA(cudaMemcpyAsync(&st->T, toff + E, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    k_tri_groups<<<grid_for(E + 1, 256), 256, 0, s>>>(gstart, tcnt, toff, tsmallq, tmidq, tbigq, st);
+    k_tri_groups<<<grid_for(E + 1, 256), 256, 0, s>>>(gstart, tcnt, toff, tsmallq, tmidq, tbigq, st,
+                                                      maxdim >= 3 ? 1 : 0);
     VR_CUDA(cudaGetLastError());
     prof.end();
   }
@@ -404,7 +405,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   }
 
   // Vertex and triangle outputs (one block) and the T-sized workspace.
-  const bool lexm = T > 0 && lex_mode(E, ngrades);
+  const bool lexm = T > 0 && lex_mode(E, ngrades, maxdim >= 3 ? 1 : 0);
+  const bool tets = maxdim >= 3 && T > 0;
   const bool bigfix = T > 0 && !lexm && hst->big_seg_count > 0;
   int32_t *vverts, *vgrade;
   int32_t *tverts = nullptr, *tgrade = nullptr, *trow = nullptr;
@@ -423,10 +425,20 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_TRY(out.alloc(&tcol, T + 1));
     VR_TRY(out.alloc(&trow, 3 * T));
   }
+  uint64_t *tk_lex = nullptr;  // tetrahedra: the triangles' keys in lexicographic order
+  int32_t *ordidx = nullptr, *cnt4 = nullptr;
+  int64_t *off4 = nullptr, *bs_t = nullptr;
   if (lexm) {
     VR_TRY(ws.alloc(&tk, T));
     VR_TRY(ws.alloc(&trs.tkeys, T));
     VR_TRY(ws.alloc(&trs.meta, rs_meta_bytes(T)));
+  }
+  if (tets) {
+    VR_TRY(ws.alloc(&tk_lex, T));
+    VR_TRY(ws.alloc(&ordidx, T));
+    VR_TRY(ws.alloc(&cnt4, T));
+    VR_TRY(ws.alloc(&off4, T + 1));
+    VR_TRY(ws.alloc(&bs_t, scan_tmp_slots(T)));
   }
   if (bigfix) {
     VR_TRY(ws.alloc(&tk1, T));
@@ -456,6 +468,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
                                                                       nbr_ord, deg, up, lex_ptr, toff, T, tk, ex, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
+      if (tets) VR_CUDA(cudaMemcpyAsync(tk_lex, tk, sizeof(uint64_t) * T, cudaMemcpyDeviceToDevice, s));
       prof.end();
       prof.begin("tri_grade_sort");
       static const char *const ttag[2] = {"tri_sort.hist", "tri_sort.pass"};
@@ -502,6 +515,74 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     }
   }
 
+  // Tetrahedra (maxdim 3): lexicographic generation from the lexicographic
+  // triangle list, stable sort on the grade bits, final write.
+  int64_t T4 = 0;
+  int32_t *qverts = nullptr, *qgrade = nullptr, *qrow = nullptr;
+  int64_t *qcol = nullptr;
+  if (maxdim >= 3) {
+    if (tets) {
+      prof.begin("tet_count");
+      k_tri_ordidx<<<grid_for(T, 256), 256, 0, s>>>(tk, T, tk_lex, ordidx);
+      k_tet_count<<<grid_for(T, 8, 148 * 32), 256, 0, s>>>(tk_lex, T, adj, W, cnt4);
+      count_launch(2);
+      VR_TRY((scan_exclusive<int32_t, int64_t>(cnt4, off4, T, bs_t, s)));
+      VR_CUDA(cudaGetLastError());
+      prof.end();
+      // ---- sync 3: tetrahedron count.
+      VR_CUDA(cudaMemcpyAsync(&hst->T, off4 + T, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      VR_CUDA(cudaStreamSynchronize(s));
+      T4 = hst->T;
+      if (T4 > INT32_MAX) {
+        set_error("%lld tetrahedra exceed the 2^31-1 limit of one dimension", (long long)T4);
+        return VR_ERR_RANGE;
+      }
+    }
+    uint64_t *keys4 = nullptr, *lex4 = nullptr;
+    RadixScratch qrs{};
+    out.begin();
+    ws.begin();
+    VR_TRY(out.alloc(&qverts, 4 * T4));
+    VR_TRY(out.alloc(&qgrade, T4));
+    VR_TRY(out.alloc(&qcol, T4 + 1));
+    VR_TRY(out.alloc(&qrow, 4 * T4));
+    if (T4 > 0) {
+      VR_TRY(ws.alloc(&keys4, T4));
+      VR_TRY(ws.alloc(&lex4, T4));
+      VR_TRY(ws.alloc(&qrs.tkeys, T4));
+      VR_TRY(ws.alloc(&qrs.meta, rs_meta_bytes(T4)));
+    }
+    VR_TRY(out.commit());
+    VR_TRY(ws.commit());
+    qrs.err = &st->flags;
+    if (T4 == 0) {
+      VR_CUDA(cudaMemsetAsync(qcol, 0, sizeof(int64_t), s));
+    } else {
+      prof.begin("tet_gen");
+      const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, W, n};
+      if (eidx)
+        k_tet_gen<true><<<grid_for(T, 8, 148 * 32), 256, 0, s>>>(tk_lex, T, adj, W, tgrade, ordidx, egrade, ex, off4,
+                                                                 T4, keys4, lex4, st);
+      else
+        k_tet_gen<false><<<grid_for(T, 8, 148 * 32), 256, 0, s>>>(tk_lex, T, adj, W, tgrade, ordidx, egrade, ex,
+                                                                  off4, T4, keys4, lex4, st);
+      count_launch();
+      VR_CUDA(cudaGetLastError());
+      prof.end();
+      prof.begin("tet_grade_sort");
+      VR_TRY(radix_sort(keys4, T4, 32, std::max(1, bitlen((uint64_t)(ngrades - 1))), qrs, s));
+      prof.end();
+      prof.begin("tet_final");
+      k_tet_final<<<grid_for(T4, 256), 256, 0, s>>>(keys4, T4, lex4, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr,
+                                                    ordidx, qverts, qgrade, qcol, qrow);
+      count_launch();
+      VR_CUDA(cudaGetLastError());
+      prof.end();
+    }
+    // Value errors raised by the tetrahedron kernels (internal checks).
+    VR_TRY(read_status(st, hst, s));
+  }
+
   // Hand the outputs to the result.
   res->n = n;
   res->d = d;
@@ -520,6 +601,11 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   res->grade[2] = tgrade;
   res->colptr[2] = tcol;
   res->rowidx[2] = trow;
+  res->count[3] = maxdim >= 3 ? T4 : 0;
+  res->verts[3] = qverts;
+  res->grade[3] = qgrade;
+  res->colptr[3] = qcol;
+  res->rowidx[3] = qrow;
   res->grade_value = gval;
   res->ngrades = ngrades;
   res->stats.kept_edges = E;

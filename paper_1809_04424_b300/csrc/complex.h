@@ -12,11 +12,11 @@ struct vr_complex {
   int32_t n = 0, d = 0, maxdim = 0;
   cudaStream_t stream = nullptr;
   int device = 0;
-  int64_t count[3] = {0, 0, 0};
-  int32_t *verts[3] = {nullptr, nullptr, nullptr};
-  int32_t *grade[3] = {nullptr, nullptr, nullptr};
-  int64_t *colptr[3] = {nullptr, nullptr, nullptr};
-  int32_t *rowidx[3] = {nullptr, nullptr, nullptr};
+  int64_t count[4] = {0, 0, 0, 0};
+  int32_t *verts[4] = {nullptr, nullptr, nullptr, nullptr};
+  int32_t *grade[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t *colptr[4] = {nullptr, nullptr, nullptr, nullptr};
+  int32_t *rowidx[4] = {nullptr, nullptr, nullptr, nullptr};
   double *grade_value = nullptr;
   int64_t ngrades = 0;
   vr_build_stats stats{};
@@ -33,9 +33,11 @@ struct vr_complex {
   uint8_t *msf = nullptr;             // per edge: in the spanning forest (zero column of D1)
   int32_t *pair_tri = nullptr;        // per triangle: the edge it kills (-1: none)
   int32_t *pair_edge = nullptr;       // per edge: the triangle killing it (-1: none)
-  int64_t nbars[3] = {-1, -1, -1};
-  int32_t *bar_birth[3] = {nullptr, nullptr, nullptr};
-  int32_t *bar_death[3] = {nullptr, nullptr, nullptr};
+  int32_t *pair_tet = nullptr;        // per tetrahedron: the triangle it kills (-1: none)
+  int32_t *pair_tri2 = nullptr;       // per triangle: the tetrahedron killing it (-1: none)
+  int64_t nbars[4] = {-1, -1, -1, -1};
+  int32_t *bar_birth[4] = {nullptr, nullptr, nullptr, nullptr};
+  int32_t *bar_death[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace vr {

@@ -828,8 +828,11 @@ __device__ __forceinline__ uint64_t lex3(int a, int b, int c) {
   return ((uint64_t)a << (2 * ID_BITS)) | ((uint64_t)b << ID_BITS) | (uint64_t)c;
 }
 
-__host__ __device__ __forceinline__ bool lex_mode(int64_t E, int64_t ngrades) {
-  return (E - (ngrades - 1)) * 20 > E;  // more than 5% of edges share a grade
+// Triangles in lexicographic order + a sort on the grade bits: chosen when
+// more than 5% of edges share a grade, and always for tetrahedra (which are
+// generated from the lexicographic triangle list).
+__host__ __device__ __forceinline__ bool lex_mode(int64_t E, int64_t ngrades, int force = 0) {
+  return force || (E - (ngrades - 1)) * 20 > E;
 }
 
 __device__ __forceinline__ int64_t lex_pos(int a, int b, const uint32_t *adj, const int32_t *adjpre, int W,
@@ -858,10 +861,10 @@ static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts,
                                                           const int32_t *adjpre, int W, const int32_t *nbr_ptr,
                                                           const int32_t *nbr_ord, const int32_t *deg,
                                                           const int32_t *up, const int64_t *lex_ptr,
-                                                          const DevStatus *st, int32_t *tcnt) {
+                                                          const DevStatus *st, int32_t *tcnt, int force_lex) {
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
-  const bool lexm = lex_mode(E, st->ngrades);
+  const bool lexm = lex_mode(E, st->ngrades, force_lex);
   for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
     const int a = everts[2 * e], b = everts[2 * e + 1];
     const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
@@ -1090,9 +1093,9 @@ constexpr int TRI_SMALL = 1024;
 constexpr int TRI_MID = 8192;
 
 static __global__ void k_tri_groups(const int32_t *gstart, const int32_t *tcnt, const int64_t *toff, int32_t *smallq,
-                                    int32_t *midq, int32_t *bigq, DevStatus *st) {
+                                    int32_t *midq, int32_t *bigq, DevStatus *st, int force_lex) {
   const int64_t ngrades = st->ngrades;
-  if (lex_mode(st->E, ngrades)) return;  // lex mode needs no merge
+  if (lex_mode(st->E, ngrades, force_lex)) return;  // lex mode needs no merge
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngrades; g += (int64_t)gridDim.x * blockDim.x) {
     const int32_t b = gstart[g], e = gstart[g + 1];
     if (e - b < 2) continue;
@@ -1194,6 +1197,157 @@ static __global__ void __launch_bounds__(RS_THREADS) k_tri_fix_big(const int32_t
       trow[3 * p + 2] = R[3 * v + 2];
     }
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- tetrahedra
+// Tetrahedron (a,b,c,d), a<b<c<d: present iff its six edges are kept; grade =
+// the largest edge grade.  Generated from the triangles in lexicographic
+// order: triangle (a,b,c) at lexicographic position t takes the apexes d > c
+// of N(a) & N(b) & N(c), so the tetrahedra come out in lexicographic order;
+// a stable sort on the grade gives (grade, lex).  Faces are found through the
+// triangles' apex lists: the triangles whose first edge is (x,y) occupy
+// positions toff[lex_pos(x,y)] .. toff[lex_pos(x,y)+1] of the lexicographic
+// list, apexes ascending.
+
+constexpr uint64_t LEX3_MASK = (1ull << LEX_SHIFT) - 1;
+
+__device__ __forceinline__ void lex3_unpack(uint64_t k, int &a, int &b, int &c) {
+  a = (int)((k >> (2 * ID_BITS)) & ID_MASK);
+  b = (int)((k >> ID_BITS) & ID_MASK);
+  c = (int)(k & ID_MASK);
+}
+
+// Order index of each triangle by lexicographic position: the sorted
+// triangle p has key (grade, lex3); its lexicographic position is found by
+// bisection in the lexicographic key list.
+static __global__ void k_tri_ordidx(const uint64_t *tk, int64_t T, const uint64_t *tk_lex, int32_t *ordidx) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t x = tk[p] & LEX3_MASK;
+    int64_t lo = 0, hi = T;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((tk_lex[mid] & LEX3_MASK) < x) lo = mid + 1;
+      else hi = mid;
+    }
+    ordidx[lo] = (int32_t)p;
+  }
+}
+
+// Tetrahedra per lexicographic triangle (warp per triangle).
+static __global__ void __launch_bounds__(256) k_tet_count(const uint64_t *tk_lex, int64_t T, const uint32_t *adj,
+                                                          int W, int32_t *cnt4) {
+  const int l = lane_id();
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  for (int64_t t = blockIdx.x * 8 + (threadIdx.x >> 5); t < T; t += nwarps) {
+    int a, b, c;
+    lex3_unpack(tk_lex[t], a, b, c);
+    const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W, *rc = adj + (int64_t)c * W;
+    int n4 = 0;
+    for (int w = (c >> 5) + l; w < W; w += 32) n4 += __popc(ra[w] & rb[w] & rc[w] & above_mask(c, w));
+    n4 = warp_sum(n4);
+    if (l == 0) cnt4[t] = n4;
+  }
+}
+
+// Keys (grade << 32 | lexicographic position q) and the packed vertices of
+// each tetrahedron at q.
+template <bool DENSE>
+static __global__ void __launch_bounds__(256) k_tet_gen(const uint64_t *tk_lex, int64_t T, const uint32_t *adj,
+                                                        int W, const int32_t *tgrade, const int32_t *ordidx,
+                                                        const int32_t *egrade, EdgeIndex ex, const int64_t *off4,
+                                                        int64_t T4, uint64_t *keys4, uint64_t *lex4, DevStatus *st) {
+  const int l = lane_id();
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  for (int64_t t = blockIdx.x * 8 + (threadIdx.x >> 5); t < T; t += nwarps) {
+    const uint64_t k3 = tk_lex[t] & LEX3_MASK;
+    int a, b, c;
+    lex3_unpack(k3, a, b, c);
+    const int32_t g3 = tgrade[ordidx[t]];
+    const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W, *rc = adj + (int64_t)c * W;
+    int64_t q0 = off4[t];
+    for (int w0 = c >> 5; w0 < W; w0 += 32) {
+      const int w = w0 + l;
+      const uint32_t vm = w < W ? (ra[w] & rb[w] & rc[w] & above_mask(c, w)) : 0u;
+      const BitChunk r = bit_round(vm);
+      for (int qq0 = 0; qq0 < r.tot; qq0 += 32) {
+        const int qq = qq0 + l;
+        const int ow = bit_owner(r, qq);
+        const uint32_t om = __shfl_sync(0xffffffffu, vm, ow);
+        const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
+        if (qq < r.tot) {
+          const int d = (w0 + ow) * 32 + __fns(om, 0, qq - oex + 1);
+          int32_t g = g3;
+          g = max(g, egrade[ex.ord<DENSE>(a, d)]);
+          g = max(g, egrade[ex.ord<DENSE>(b, d)]);
+          g = max(g, egrade[ex.ord<DENSE>(c, d)]);
+          const int64_t q = q0 + qq;
+          if (q < T4) {
+            keys4[q] = ((uint64_t)(uint32_t)g << 32) | (uint64_t)q;
+            lex4[q] = (k3 << ID_BITS) | (uint64_t)d;
+          } else {
+            raise_flag(st, F_INTERNAL);  // never write past the key arrays
+          }
+        }
+      }
+      q0 += r.tot;
+    }
+  }
+}
+
+// Lexicographic position of triangle (x,y,z), x<y<z, all edges kept.
+__device__ __forceinline__ int64_t tri_lexpos(int x, int y, int z, const uint64_t *tk_lex, const int64_t *toff,
+                                              const uint32_t *adj, const int32_t *adjpre, int W, const int32_t *deg,
+                                              const int32_t *up, const int64_t *lex_ptr) {
+  const int64_t lp = lex_pos(x, y, adj, adjpre, W, deg, up, lex_ptr);
+  int64_t lo = toff[lp], hi = toff[lp + 1];
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int)(tk_lex[mid] & ID_MASK) < z) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Final write of the tetrahedra in (grade, lex) order: vertices, grade,
+// colptr and the boundary column (order indices of the four triangles,
+// ascending); thread p also closes colptr at T4.
+static __global__ void k_tet_final(const uint64_t *keys4, int64_t T4, const uint64_t *lex4, const uint64_t *tk_lex,
+                                   const int64_t *toff, const uint32_t *adj, const int32_t *adjpre, int W,
+                                   const int32_t *deg, const int32_t *up, const int64_t *lex_ptr,
+                                   const int32_t *ordidx, int32_t *verts, int32_t *grade, int64_t *colptr,
+                                   int32_t *rowidx) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T4; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = keys4[p];
+    const uint64_t v = lex4[key & 0xffffffffull];
+    const int d = (int)(v & ID_MASK);
+    int a, b, c;
+    lex3_unpack(v >> ID_BITS, a, b, c);
+    int32_t r[4];
+    r[0] = ordidx[tri_lexpos(b, c, d, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr)];
+    r[1] = ordidx[tri_lexpos(a, c, d, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr)];
+    r[2] = ordidx[tri_lexpos(a, b, d, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr)];
+    r[3] = ordidx[tri_lexpos(a, b, c, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr)];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 3 - x; ++y)
+        if (r[y] > r[y + 1]) {
+          const int32_t sw = r[y];
+          r[y] = r[y + 1];
+          r[y + 1] = sw;
+        }
+    verts[4 * p] = a;
+    verts[4 * p + 1] = b;
+    verts[4 * p + 2] = c;
+    verts[4 * p + 3] = d;
+    grade[p] = (int32_t)(key >> 32);
+    colptr[p] = 4 * p;
+    rowidx[4 * p] = r[0];
+    rowidx[4 * p + 1] = r[1];
+    rowidx[4 * p + 2] = r[2];
+    rowidx[4 * p + 3] = r[3];
+    if (p == T4 - 1) colptr[T4] = 4 * T4;
   }
 }
 

@@ -54,7 +54,7 @@ def test_library_targets_sm_103a():
 
 @pytest.mark.parametrize("args,status", [
     (dict(n=0), vr.VR_ERR_RANGE), (dict(n=8193), vr.VR_ERR_RANGE), (dict(d=0), vr.VR_ERR_ARG),
-    (dict(maxdim=3), vr.VR_ERR_UNSUPPORTED), (dict(maxdim=-1), vr.VR_ERR_ARG),
+    (dict(maxdim=4), vr.VR_ERR_UNSUPPORTED), (dict(maxdim=-1), vr.VR_ERR_ARG),
     (dict(maxrad=-1.0), vr.VR_ERR_ARG), (dict(maxrad=math.nan), vr.VR_ERR_ARG), (dict(dtype=9), vr.VR_ERR_ARG)])
 def test_host_argument_checks(args, status):
     """These are rejected before any CUDA call, so they run without a GPU."""
