@@ -44,6 +44,8 @@ WORKLOADS = {
                 lambda: synth.config3(), "f64"),
     "worldmap": ("WorldMap-shaped n=7322 d=3 float32 on the unit sphere (7 blobs + uniform), cap 0.15, maxdim 2",
                  lambda: synth.worldmap(), "f64"),
+    "torus3": ("torus n=1000 d=3 int8 (scale 30, noise 0.05), cap at 15th-pct d^2, maxdim 3 (tetrahedra)",
+               lambda: synth.Cloud(synth.config2().points, 3, synth.config2().maxrad), "int64"),
     "hiv": ("HIV-shaped 1088x1088 int32 Hamming distance matrix (9 subtypes), cap at its 10th percentile, maxdim 2",
             lambda: synth.hiv(), "int64"),
 }
@@ -71,7 +73,7 @@ METRIC = "VR simplices/s"
 #   edge_grades: keys 8 read, flags 4+4, outputs 8+4+8+8, CSR scatter 8 per edge
 
 
-def roofline_bytes(cloud, E, T):
+def roofline_bytes(cloud, E, T, T4=0):
     """Algorithmic bytes of one launch of each single-kernel phase."""
     n = cloud.n
     Wd = (n + 31) // 32
@@ -85,6 +87,7 @@ def roofline_bytes(cloud, E, T):
         "edge_sort.hist": 8 * E,
         "distance": cloud.points.nbytes + 4 * n * Wd,  # read points, write the bitmap
         "edge_keys": 8 * E,
+        "tet_final": 52 * T4,               # read key 8 + lex 8; write verts 16, grade 4, colptr 8, rowidx 16
     }
 
 
@@ -661,7 +664,7 @@ def main():
     torch.cuda.synchronize()
     L.vr_profile_enable(0)
     phases = read_phases()
-    per_launch_bytes = roofline_bytes(cloud, counts[1], counts[2])
+    per_launch_bytes = roofline_bytes(cloud, counts[1], counts[2], counts[3] if len(counts) > 3 else 0)
     # Regions of one kernel (a sort's digit passes: several launches of the
     # same kernel, each timed).
     single = {k: v for k, v in phases.items() if k in per_launch_bytes
