@@ -322,18 +322,6 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
 
   const unsigned ge = grid_for(E, 256);
   if (E > 0) {
-    prof.begin("edge_keys");
-    if constexpr (F) {
-      k_edge_keys_f32<<<(n + 7) / 8, 256, 0, s>>>((const float *)X, n, d, W, adj, lex_ptr, keys, d64_lex, st);
-    } else if (dmat) {
-      if (dmf) k_dmat_keys<true><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, adj, lex_ptr, keys);
-      else k_dmat_keys<false><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, adj, lex_ptr, keys);
-    } else {
-      k_edge_keys<F><<<(n + 7) / 8, 256, 0, s>>>(X, n, d, W, adj, lex_ptr, keys);
-    }
-    count_launch();
-    VR_CUDA(cudaGetLastError());
-    prof.end();
     // Keys arrive in (i, j) order, so a stable sort on the distance bits
     // alone yields (distance, i, j).
     int kbits;
@@ -344,9 +332,25 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       if (!cap.keep_all) bound = std::min(bound, cap.r2i);
       kbits = std::max(1, bitlen(bound));
     }
+    // The key generator also counts the sort's digit histogram.
+    KeyHist ekh;
+    VR_TRY(radix_prepare(E, KEY_SHIFT, kbits, rs, s, &ekh));
+    prof.begin("edge_keys");
+    if constexpr (F) {
+      k_edge_keys_f32<<<(n + 7) / 8, 256, 0, s>>>((const float *)X, n, d, W, adj, lex_ptr, keys, d64_lex, st,
+                                                   ekh);
+    } else if (dmat) {
+      if (dmf) k_dmat_keys<true><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, adj, lex_ptr, keys, ekh);
+      else k_dmat_keys<false><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, adj, lex_ptr, keys, ekh);
+    } else {
+      k_edge_keys<F><<<(n + 7) / 8, 256, 0, s>>>(X, n, d, W, adj, lex_ptr, keys, ekh);
+    }
+    count_launch();
+    VR_CUDA(cudaGetLastError());
+    prof.end();
     prof.begin("edge_sort");
     static const char *const etag[2] = {"edge_sort.hist", "edge_sort.pass"};
-    VR_TRY(radix_sort(keys, E, KEY_SHIFT, kbits, rs, s, &prof, etag));
+    VR_TRY(radix_sort(keys, E, KEY_SHIFT, kbits, rs, s, &prof, etag, true));
     prof.end();
 
     if (F) {
@@ -458,6 +462,9 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   if (maxdim >= 2) {
     if (lexm) {
       // Lex-order generation, stable sort on the grade bits, final write.
+      const int gbits = std::max(1, bitlen((uint64_t)(ngrades - 1)));
+      // (The triangle generator is latency-bound: counting the sort's
+      // histogram inside it cost more than the sort's own histogram pass.)
       prof.begin("tri_lex_gen");
       const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, W, n};
       if (eidx)
@@ -472,8 +479,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       prof.end();
       prof.begin("tri_grade_sort");
       static const char *const ttag[2] = {"tri_sort.hist", "tri_sort.pass"};
-      VR_TRY(radix_sort(tk, T, LEX_SHIFT, std::max(1, bitlen((uint64_t)(ngrades - 1))), trs, s, &prof,
-                        ttag));
+      VR_TRY(radix_sort(tk, T, LEX_SHIFT, gbits, trs, s, &prof, ttag));
       prof.end();
       prof.begin("tri_final");
       if (eidx) k_tri_final<true><<<grid_for((T + 3) / 4, 256), 256, 0, s>>>(tk, T, ex, tverts, tgrade, tcol, trow);
@@ -558,6 +564,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     if (T4 == 0) {
       VR_CUDA(cudaMemsetAsync(qcol, 0, sizeof(int64_t), s));
     } else {
+      const int gbits = std::max(1, bitlen((uint64_t)(ngrades - 1)));
       prof.begin("tet_gen");
       const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, W, n};
       if (eidx)
@@ -570,7 +577,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_CUDA(cudaGetLastError());
       prof.end();
       prof.begin("tet_grade_sort");
-      VR_TRY(radix_sort(keys4, T4, 32, std::max(1, bitlen((uint64_t)(ngrades - 1))), qrs, s));
+      VR_TRY(radix_sort(keys4, T4, 32, gbits, qrs, s));
       prof.end();
       prof.begin("tet_final");
       k_tet_final<<<grid_for(T4, 256), 256, 0, s>>>(keys4, T4, lex4, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr,

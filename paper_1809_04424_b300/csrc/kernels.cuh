@@ -354,15 +354,16 @@ __device__ __forceinline__ int32_t bit_rank(const uint32_t *adj_row, const int32
 // position lex_ptr[i] + (rank of j in row i) - (neighbours <= i).
 template <bool F>
 __global__ void __launch_bounds__(256) k_edge_keys(const void *Xv, int n, int d, int W, const uint32_t *adj,
-                                                   const int64_t *lex_ptr, uint64_t *keys) {
+                                                   const int64_t *lex_ptr, uint64_t *keys, KeyHist kh) {
   using T = typename std::conditional<F, float, int32_t>::type;
+  __shared__ KeyHistSmem hs;
+  khist_init(hs, kh);
   const T *X = (const T *)Xv;
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int l = lane_id();
-  if (i >= n) return;
   const uint32_t *row = adj + (int64_t)i * W;
-  int64_t t = lex_ptr[i];
-  for (int w0 = (i + 1) >> 5; w0 < W; w0 += 32) {
+  int64_t t = i < n ? lex_ptr[i] : 0;
+  for (int w0 = (i + 1) >> 5; i < n && w0 < W; w0 += 32) {
     const int w = w0 + l;
     const uint32_t word = w < W ? row[w] & above_mask(i, w) : 0u;
     const BitChunk r = bit_round(word);
@@ -371,16 +372,20 @@ __global__ void __launch_bounds__(256) k_edge_keys(const void *Xv, int n, int d,
       const int ow = bit_owner(r, q);
       const uint32_t om = __shfl_sync(0xffffffffu, word, ow);
       const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
+      uint64_t key = 0;
       if (q < r.tot) {
         const int j = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
         uint64_t dk;
         if constexpr (F) dk = (uint64_t)__float_as_uint(d2_f32(X + (int64_t)i * d, X + (int64_t)j * d, d));
         else dk = d2_int(X + (int64_t)i * d, X + (int64_t)j * d, d);
-        keys[t + q] = (dk << KEY_SHIFT) | ((uint64_t)i << ID_BITS) | (uint64_t)j;
+        key = (dk << KEY_SHIFT) | ((uint64_t)i << ID_BITS) | (uint64_t)j;
+        keys[t + q] = key;
       }
+      khist_add(hs, kh, key, q < r.tot);
     }
     t += r.tot;
   }
+  khist_flush(hs, kh);
 }
 
 // ------------------------------------------------- distance-matrix input
@@ -450,13 +455,14 @@ static __global__ void __launch_bounds__(256) k_dmat_bitmap(const void *Dv, int 
 // with the matrix entry as the value).
 template <bool F>
 static __global__ void __launch_bounds__(256) k_dmat_keys(const void *Dv, int n, int W, const uint32_t *adj,
-                                                          const int64_t *lex_ptr, uint64_t *keys) {
+                                                          const int64_t *lex_ptr, uint64_t *keys, KeyHist kh) {
+  __shared__ KeyHistSmem hs;
+  khist_init(hs, kh);
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int l = lane_id();
-  if (i >= n) return;
   const uint32_t *row = adj + (int64_t)i * W;
-  int64_t t = lex_ptr[i];
-  for (int w0 = (i + 1) >> 5; w0 < W; w0 += 32) {
+  int64_t t = i < n ? lex_ptr[i] : 0;
+  for (int w0 = (i + 1) >> 5; i < n && w0 < W; w0 += 32) {
     const int w = w0 + l;
     const uint32_t word = w < W ? row[w] & above_mask(i, w) : 0u;
     const BitChunk r = bit_round(word);
@@ -465,14 +471,18 @@ static __global__ void __launch_bounds__(256) k_dmat_keys(const void *Dv, int n,
       const int ow = bit_owner(r, q);
       const uint32_t om = __shfl_sync(0xffffffffu, word, ow);
       const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
+      uint64_t key = 0;
       if (q < r.tot) {
         const int j = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
         const uint64_t dk = dmat_key<F>(Dv, (int64_t)i * n + j);
-        keys[t + q] = (dk << KEY_SHIFT) | ((uint64_t)i << ID_BITS) | (uint64_t)j;
+        key = (dk << KEY_SHIFT) | ((uint64_t)i << ID_BITS) | (uint64_t)j;
+        keys[t + q] = key;
       }
+      khist_add(hs, kh, key, q < r.tot);
     }
     t += r.tot;
   }
+  khist_flush(hs, kh);
 }
 
 // Float edge keys, in lexicographic order: warp per row i, 32 candidates per
@@ -517,17 +527,19 @@ __device__ __forceinline__ double soft_value(const SoftAcc &s) {
 
 static __global__ void __launch_bounds__(256) k_edge_keys_f32(const float *X, int n, int d, int W,
                                                               const uint32_t *adj, const int64_t *lex_ptr,
-                                                              uint64_t *keys, double *d64_lex, DevStatus *st) {
+                                                              uint64_t *keys, double *d64_lex, DevStatus *st,
+                                                              KeyHist kh) {
   __shared__ float tile[8][32][33];
   __shared__ float rowi[8][32];
+  __shared__ KeyHistSmem hs;
+  khist_init(hs, kh);
   const int wid = threadIdx.x >> 5;
   const int i = blockIdx.x * 8 + wid;
   const int l = lane_id();
-  if (i >= n) return;
   const uint32_t *row = adj + (int64_t)i * W;
-  int64_t t = lex_ptr[i];
+  int64_t t = i < n ? lex_ptr[i] : 0;
   float worst = 0.f;
-  for (int w0 = (i + 1) >> 5; w0 < W; w0 += 32) {
+  for (int w0 = (i + 1) >> 5; i < n && w0 < W; w0 += 32) {
     const int w = w0 + l;
     const uint32_t word = w < W ? row[w] & above_mask(i, w) : 0u;
     const BitChunk r = bit_round(word);
@@ -556,19 +568,23 @@ static __global__ void __launch_bounds__(256) k_edge_keys_f32(const float *X, in
         }
         __syncwarp();
       }
+      uint64_t key = 0;
       if (has) {
         const double f = acc.ok ? soft_value(acc) : d2_f64(X + (int64_t)i * d, X + (int64_t)j * d, d);
         d64_lex[t + q] = f;
-        keys[t + q] = ((uint64_t)__float_as_uint(__double2float_rn(f)) << KEY_SHIFT) |
-                      ((uint64_t)i << ID_BITS) | (uint64_t)j;
+        key = ((uint64_t)__float_as_uint(__double2float_rn(f)) << KEY_SHIFT) | ((uint64_t)i << ID_BITS) |
+              (uint64_t)j;
+        keys[t + q] = key;
         if (f > 0.0) {
           const float ff = (float)f, sf = sqrtf(ff);
           worst = fmaxf(worst, fabsf((float)((double)a - f)) / (sf * (sqrtf(a) + sf)));
         }
       }
+      khist_add(hs, kh, key, has);
     }
     t += r.tot;
   }
+  khist_flush(hs, kh);
   worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 16));
   worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 8));
   worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 4));

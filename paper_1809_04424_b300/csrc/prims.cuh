@@ -496,6 +496,45 @@ static __global__ void __launch_bounds__(RS_THREADS) k_rs_single(uint64_t *keys,
   cta_radix_sort_global(keys, vals, tkeys, tvals, n, bit_lo, nbits);
 }
 
+// All-digit histogram of the keys a kernel writes, counted per CTA in shared
+// memory (warp-aggregated) and added to the sort's global histogram at the
+// end, so that radix_sort(..., hist_ready) needs no histogram pass.  g null:
+// off (a kernel parameter, so uniform over the block).
+struct KeyHist {
+  uint32_t *g;
+  int bit_lo, nbits;
+};
+using KeyHistSmem = uint32_t[RS_MAX_PASSES][RS_BINS];
+
+__device__ __forceinline__ void khist_init(KeyHistSmem &h, const KeyHist &kh) {
+  if (!kh.g) return;
+  for (int b = threadIdx.x; b < RS_MAX_PASSES * RS_BINS; b += blockDim.x) (&h[0][0])[b] = 0;
+  __syncthreads();
+}
+
+// Called by all 32 lanes of a warp together.
+__device__ __forceinline__ void khist_add(KeyHistSmem &h, const KeyHist &kh, uint64_t key, bool valid) {
+  if (!kh.g) return;
+  const uint32_t lt = lanemask_lt();
+  const int passes = (kh.nbits + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    const uint32_t dg = valid ? digit_of(key, kh.bit_lo + 8 * p, digit_mask(kh.nbits, p)) : RS_BINS;
+    const uint32_t peers = warp_peers9(dg);
+    if (valid && (peers & lt) == 0) atomicAdd(&h[p][dg], (uint32_t)__popc(peers));
+  }
+}
+
+// Called by every thread of the block after its last khist_add.
+__device__ __forceinline__ void khist_flush(KeyHistSmem &h, const KeyHist &kh) {
+  if (!kh.g) return;
+  __syncthreads();
+  const int n = ((kh.nbits + 7) / 8) * RS_BINS;
+  for (int b = threadIdx.x; b < n; b += blockDim.x) {
+    const uint32_t v = (&h[0][0])[b];
+    if (v) atomicAdd(&kh.g[b], v);
+  }
+}
+
 // Scratch for radix_sort: a temporary of n keys and rs_meta_bytes(n) bytes
 // (all-digit histogram, tile tickets, per-tile status words).  The sorted
 // result ends in `keys`.  `err`: device flags word for a timed-out wait.
@@ -508,9 +547,22 @@ inline int64_t rs_tiles(int64_t n) { return (n + RS_TILE - 1) / RS_TILE; }
 constexpr int64_t RS_META_HEAD = RS_MAX_PASSES * RS_BINS * 4 + 256;
 inline int64_t rs_meta_bytes(int64_t n) { return RS_META_HEAD + rs_tiles(n) * RS_BINS * 8; }
 
+// Clear the sort's scratch and return the histogram for a key generator to
+// fill (KeyHist with g null when the sort will not use it: one-CTA sizes).
+inline vr_status radix_prepare(int64_t n, int bit_lo, int nbits, const RadixScratch &sc, cudaStream_t s,
+                               KeyHist *kh) {
+  *kh = KeyHist{nullptr, bit_lo, nbits};
+  if (n <= 2 * RS_TILE || nbits <= 0) return VR_OK;
+  VR_CUDA(cudaMemsetAsync(sc.meta, 0, (size_t)rs_meta_bytes(n), s));
+  kh->g = (uint32_t *)sc.meta;
+  return VR_OK;
+}
+
 // `prof`/`tag`: optional per-kernel timing ("<tag>.hist", ".pass").
+// hist_ready: radix_prepare was called and a generator filled the histogram.
 inline vr_status radix_sort(uint64_t *keys, int64_t n, int bit_lo, int nbits, const RadixScratch &sc,
-                            cudaStream_t s, Prof *prof = nullptr, const char *const *tag = nullptr) {
+                            cudaStream_t s, Prof *prof = nullptr, const char *const *tag = nullptr,
+                            bool hist_ready = false) {
   if (n <= 1 || nbits <= 0) return VR_OK;
   if (n <= 2 * RS_TILE) {
     k_rs_single<<<1, RS_THREADS, 0, s>>>(keys, nullptr, sc.tkeys, nullptr, n, bit_lo, nbits);
@@ -523,12 +575,15 @@ inline vr_status radix_sort(uint64_t *keys, int64_t n, int bit_lo, int nbits, co
   uint32_t *hist = (uint32_t *)sc.meta;
   uint32_t *ticket = (uint32_t *)(sc.meta + RS_MAX_PASSES * RS_BINS * 4);
   uint64_t *status = (uint64_t *)(sc.meta + RS_META_HEAD);
-  int tk_ = prof ? prof->begin(tag[0]) : -1;
-  VR_CUDA(cudaMemsetAsync(sc.meta, 0, (size_t)rs_meta_bytes(n), s));
-  const unsigned hg = (unsigned)(nt < 148 * 8 ? nt : 148 * 8);
-  k_rs_hist_all<<<hg, RS_THREADS, 0, s>>>(keys, n, bit_lo, nbits, hist);
-  count_launch(1);
-  if (prof) prof->end(tk_);
+  int tk_ = -1;
+  if (!hist_ready) {
+    tk_ = prof ? prof->begin(tag[0]) : -1;
+    VR_CUDA(cudaMemsetAsync(sc.meta, 0, (size_t)rs_meta_bytes(n), s));
+    const unsigned hg = (unsigned)(nt < 148 * 8 ? nt : 148 * 8);
+    k_rs_hist_all<<<hg, RS_THREADS, 0, s>>>(keys, n, bit_lo, nbits, hist);
+    count_launch(1);
+    if (prof) prof->end(tk_);
+  }
   uint64_t *src = keys, *dst = sc.tkeys;
   for (int p = 0; p < passes; ++p) {
     tk_ = prof ? prof->begin(tag[1]) : -1;
