@@ -281,8 +281,11 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(ws.alloc(&gex, E + 1));
   VR_TRY(ws.alloc(&bs_e, scan_tmp_slots(E)));
   VR_TRY(ws.alloc(&nbr_ord, 2 * E));
-  int32_t *eidx = nullptr;  // dense (i, j) -> order index table for small clouds
-  if (n <= DENSE_MAX_N && maxdim >= 2) VR_TRY(ws.alloc(&eidx, (int64_t)n * n));
+  int32_t *eidx = nullptr, *egd = nullptr;  // dense (i, j) -> order index / grade tables for small clouds
+  if (n <= DENSE_MAX_N && maxdim >= 2) {
+    VR_TRY(ws.alloc(&eidx, (int64_t)n * n));
+    VR_TRY(ws.alloc(&egd, (int64_t)n * n));
+  }
   VR_TRY(ws.alloc(&gstart, E + 2));
   VR_TRY(out.alloc(&everts, 2 * E));
   VR_TRY(out.alloc(&egrade, E));
@@ -376,7 +379,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int32_t>(flag, gex, E, bs_e, s)));
     k_edge_emit<F><<<ge, 256, 0, s>>>(keys, d64, E, flag, gex, adj, adjpre, W, nbr_ptr, everts, egrade, ecol, erow,
-                                      gval, gstart, nbr_ord, eidx, n, dmf ? 1 : 0, st);
+                                      gval, gstart, nbr_ord, eidx, egd, n, dmf ? 1 : 0, st);
     VR_CUDA(cudaGetLastError());
     prof.end();
   } else {
@@ -466,7 +469,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       // (The triangle generator is latency-bound: counting the sort's
       // histogram inside it cost more than the sort's own histogram pass.)
       prof.begin("tri_lex_gen");
-      const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, W, n};
+      const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
       if (eidx)
         k_lex_tri_gen<true><<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr,
                                                                      nbr_ord, deg, up, lex_ptr, toff, T, tk, ex, st);
@@ -566,7 +569,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     } else {
       const int gbits = std::max(1, bitlen((uint64_t)(ngrades - 1)));
       prof.begin("tet_gen");
-      const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, W, n};
+      const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
       if (eidx)
         k_tet_gen<true><<<grid_for(T, 8, 148 * 32), 256, 0, s>>>(tk_lex, T, adj, W, tgrade, ordidx, egrade, ex, off4,
                                                                  T4, keys4, lex4, st);

@@ -783,7 +783,7 @@ template <bool F>
 __global__ void k_edge_emit(const uint64_t *keys, const double *d64, int64_t E, const int32_t *flag,
                             const int32_t *gex, const uint32_t *adj, const int32_t *adjpre, int W,
                             const int32_t *nbr_ptr, int32_t *verts, int32_t *grade, int64_t *colptr, int32_t *rowidx,
-                            double *gval, int32_t *gstart, int32_t *nbr_ord, int32_t *eidx, int n,
+                            double *gval, int32_t *gstart, int32_t *nbr_ord, int32_t *eidx, int32_t *egd, int n,
                             int key_f32, DevStatus *st) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = keys[k];
@@ -802,7 +802,10 @@ __global__ void k_edge_emit(const uint64_t *keys, const double *d64, int64_t E, 
     }
     nbr_ord[nbr_ptr[i] + bit_rank(adj + (int64_t)i * W, adjpre + (int64_t)i * W, j)] = (int32_t)k;
     nbr_ord[nbr_ptr[j] + bit_rank(adj + (int64_t)j * W, adjpre + (int64_t)j * W, i)] = (int32_t)k;
-    if (eidx) eidx[(int64_t)i * n + j] = (int32_t)k;  // dense order-index table (i < j), small n only
+    if (eidx) {  // dense order-index and grade tables (i < j), small n only
+      eidx[(int64_t)i * n + j] = (int32_t)k;
+      egd[(int64_t)i * n + j] = g;
+    }
     if (k == E - 1) {
       colptr[E] = 2 * E;
       gstart[g + 1] = (int32_t)E;
@@ -865,11 +868,18 @@ struct EdgeIndex {
   const int32_t *nbr_ptr;
   const int32_t *nbr_ord;
   const int32_t *eidx;
+  const int32_t *egd;     // dense (a, b) -> grade table (with eidx)
+  const int32_t *egrade;  // grade by order index
   int W, n;
   template <bool DENSE>
   __device__ __forceinline__ int32_t ord(int a, int b) const {
     if constexpr (DENSE) return eidx[(int64_t)a * n + b];
     else return nbr_ord[nbr_ptr[a] + bit_rank(adj + (int64_t)a * W, adjpre + (int64_t)a * W, b)];
+  }
+  template <bool DENSE>
+  __device__ __forceinline__ int32_t grade(int a, int b) const {
+    if constexpr (DENSE) return egd[(int64_t)a * n + b];
+    else return egrade[ord<false>(a, b)];
   }
 };
 
@@ -963,8 +973,8 @@ static __global__ void __launch_bounds__(256) k_lex_tri_gen(const int32_t *evert
           const int cv = ww * 32 + bit;
           int32_t gac, gbc;
           if constexpr (DENSE) {
-            gac = egrade[ex.ord<true>(a, cv)];
-            gbc = egrade[ex.ord<true>(b, cv)];
+            gac = ex.grade<true>(a, cv);
+            gbc = ex.grade<true>(b, cv);
           } else {
             const uint32_t below = (1u << bit) - 1u;
             gac = egrade[oa[pa[ww] + __popc(ra[ww] & below)]];
@@ -1294,9 +1304,9 @@ static __global__ void __launch_bounds__(256) k_tet_gen(const uint64_t *tk_lex, 
         if (qq < r.tot) {
           const int d = (w0 + ow) * 32 + __fns(om, 0, qq - oex + 1);
           int32_t g = g3;
-          g = max(g, egrade[ex.ord<DENSE>(a, d)]);
-          g = max(g, egrade[ex.ord<DENSE>(b, d)]);
-          g = max(g, egrade[ex.ord<DENSE>(c, d)]);
+          g = max(g, ex.grade<DENSE>(a, d));
+          g = max(g, ex.grade<DENSE>(b, d));
+          g = max(g, ex.grade<DENSE>(c, d));
           const int64_t q = q0 + qq;
           if (q < T4) {
             keys4[q] = ((uint64_t)(uint32_t)g << 32) | (uint64_t)q;
