@@ -278,6 +278,65 @@ def dist_env():
     return world, rank, local
 
 
+class Ranks:
+    """One process per GPU (torchrun env).  The work shards by independent
+    units (replicas of a cloud, clouds of a batch, requests of a stream) with
+    no data-path collective: a barrier around the timed region and a max of
+    the ranks' times are the only communication.  backend: "nccl" on GPUs,
+    "gloo" for the host-only tests."""
+
+    def __init__(self, backend="nccl"):
+        self.world, self.rank, self.local = dist_env()
+        self.dist = None
+        self.backend = backend
+        if self.world > 1:
+            import torch.distributed as dist
+            if not dist.is_initialized():
+                dist.init_process_group(backend)
+            self.dist = dist
+
+    def shard(self, n_units):
+        """This rank's contiguous share [lo, hi) of n_units (sizes differ by
+        at most one)."""
+        q, r = divmod(n_units, self.world)
+        lo = self.rank * q + min(self.rank, r)
+        return lo, lo + q + (1 if self.rank < r else 0)
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def max(self, x: float) -> float:
+        """The largest x over the ranks (a rank's time: the job ends with the
+        slowest)."""
+        if not self.dist:
+            return float(x)
+        import torch
+        dev = "cuda" if self.backend == "nccl" else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.dist:
+            return float(x)
+        import torch
+        dev = "cuda" if self.backend == "nccl" else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def whole_job_rate(units_all_ranks: float, slowest_seconds: float) -> float:
+    """Units processed by every rank together over the slowest rank's time."""
+    return units_all_ranks / slowest_seconds
+
+
 def oracle_rate(cloud, seconds: float):
     """Time the oracle as it stands on full builds of the workload."""
     import oracle
@@ -332,7 +391,9 @@ def run_batch_bench(args):
     import paper_1809_04424_b300 as vr
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
-    clouds = synth.config4(args.n_clouds)
+    ranks = Ranks()
+    lo, hi = ranks.shard(args.n_clouds)  # this rank's clouds of the batch
+    clouds = synth.config4(args.n_clouds)[lo:hi]
     pts = np.concatenate([c.points for c in clouds], axis=0)
     off = np.concatenate([[0], np.cumsum([c.n for c in clouds])]).astype(np.int64)
     dev = torch.from_numpy(pts).cuda()
@@ -346,13 +407,14 @@ def run_batch_bench(args):
     L.vr_profile_reset()
     L.vr_profile_enable(1)
     launches0 = L.vr_launch_count()
+    ranks.barrier()
     with Clocks(local) as clk:
         t0 = time.perf_counter()
         for _ in range(args.steps):
             b = vr.vr_build_batch(dev, off, 2, 40.0)
             del b
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
+        el = ranks.max(time.perf_counter() - t0)
     L.vr_profile_enable(0)
     launches = L.vr_launch_count() - launches0
     phases = {}
@@ -360,7 +422,8 @@ def run_batch_bench(args):
         nm, ms, calls, nl = ctypes.c_char_p(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
         L.vr_profile_phase(i, ctypes.byref(nm), ctypes.byref(ms), ctypes.byref(calls), ctypes.byref(nl))
         phases[nm.value.decode()] = round(ms.value / max(calls.value, 1), 4)
-    batched = args.n_clouds * args.steps / el
+    batched = whole_job_rate(args.n_clouds * args.steps, el)
+    tot = ranks.sum(tot)
     # per-cloud path on a sample
     sample = clouds[: min(len(clouds), 256)]
     devs = [torch.from_numpy(c.points).cuda() for c in sample]
@@ -382,6 +445,7 @@ def run_batch_bench(args):
     torch.cuda.synchronize()
     e2e = args.n_clouds * args.steps / (time.perf_counter() - t0)
     line = {"metric": "batched clouds/s", "value": batched, "unit": "clouds/s", "n_gpus": world,
+            "scaling_note": "clouds sharded across ranks, no collective on the data path",
             "steps": args.steps, "warmup": W, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": f"{args.n_clouds} sphere clouds n~U[32,512] d=3 int8 (scale 100, noise 0.02), "
@@ -394,6 +458,7 @@ def run_batch_bench(args):
             "gpu_launches": launches, "phases_ms": phases, "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    ranks.close()
     return 0
 
 
@@ -440,8 +505,11 @@ def run_serve_bench(args):
     import paper_1809_04424_b300 as vr
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
-    N = args.n_requests
-    _, reqs = synth.config5(N)
+    ranks = Ranks()
+    _, reqs_all = synth.config5(args.n_requests)
+    lo, hi = ranks.shard(args.n_requests)  # this rank's share of the stream
+    reqs = reqs_all[lo:hi]
+    N = len(reqs)
     srv = vr.Server(n_streams=3, max_batch_clouds=256, n_large_workers=4)
     submit = lambda r: srv.submit(r.points, r.maxdim, r.maxrad)
     poll = lambda t: srv.poll(t, 120_000_000)
@@ -457,8 +525,10 @@ def run_serve_bench(args):
     lam = 0.8 * cap
     g = synth.rng(1809 + 50)
     arrivals = np.cumsum(g.exponential(1.0 / lam, size=N))
+    ranks.barrier()
     with Clocks(local) as clk:
         lat, wall = _open_loop(submit, poll, reqs, arrivals)
+    wall_all = ranks.max(wall)
     sweep = {}
     for f in (0.5, 1.0):
         M = min(N, 4000)
@@ -488,7 +558,8 @@ def run_serve_bench(args):
     per_cap = 200 / (time.perf_counter() - t0)
     a = np.cumsum(synth.rng(1809 + 52).exponential(1.0 / lam, size=M))
     lp, wp = _open_loop(per_submit, per_poll, reqs[:M], a, n_pollers=1)
-    line = {"metric": "served clouds/s", "value": N / wall, "unit": "clouds/s", "n_gpus": world, "steps": N,
+    line = {"metric": "served clouds/s", "value": whole_job_rate(args.n_requests, wall_all), "unit": "clouds/s",
+            "n_gpus": world, "steps": N,
             "warmup": 64, "ms_per_step": 1e3 * wall / N, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "mixed int64/f64", "data": "synthetic",
             "config": {"workload": f"Poisson stream of {N} requests, n log-uniform [50,5000], half int8 d=3 "
@@ -505,6 +576,7 @@ def run_serve_bench(args):
             "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    ranks.close()
     return 0
 
 
@@ -618,10 +690,7 @@ def main():
     world, rank, local = dist_env()
     assert torch.cuda.is_available(), "bench needs a CUDA device"
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    ranks = Ranks()
     W = max(args.warmup, 3)
     L = vr.lib()
 
@@ -677,8 +746,7 @@ def main():
     L.vr_profile_select(dom.encode() if dom else b"-")
     L.vr_profile_reset()
     L.vr_profile_enable(1)
-    if dist:
-        dist.barrier()
+    ranks.barrier()
     torch.cuda.synchronize()
     launches0 = L.vr_launch_count()
     with Clocks(local) as clk:
@@ -691,15 +759,10 @@ def main():
         torch.cuda.synchronize()
     launches = L.vr_launch_count() - launches0
     L.vr_profile_enable(0)
-    if dist:
-        dist.barrier()
+    ranks.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = simplices * args.steps * world / (total_ms / 1e3)
+    total_ms = ranks.max(sum(step_ms))
+    value = whole_job_rate(simplices * args.steps * world, total_ms / 1e3)
 
     timed_phases = read_phases()
     L.vr_profile_select(None)
@@ -783,8 +846,7 @@ def main():
                                 "sample": f"{reps} full builds of the workload in {el:.1f} s, single-threaded"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
+    ranks.close()
     return 0
 
 
