@@ -287,7 +287,7 @@ __device__ __forceinline__ void tile_rank(const uint64_t *src, int64_t t0, int64
     int64_t idx = (int64_t)w * (32 * RS_ITEMS) + q * 32 + l;
     bool ok = idx < cnt;
     uint32_t dg = ok ? digit_of(key[q], shift, mask) : RS_BINS;  // sentinel for empty lanes
-    uint32_t peers = warp_peers9(dg);
+    uint32_t peers = __match_any_sync(0xffffffffu, dg);
     uint32_t before = ok ? sh_wcnt[w][dg] : 0;
     rank[q] = before + __popc(peers & lt);
     __syncwarp();
@@ -410,6 +410,8 @@ static __global__ void __launch_bounds__(RS_THREADS, 3) k_rs_onesweep(const uint
       } else if (++spins > RS_WAIT_LIMIT) {
         atomicOr(err, F_TIMEOUT);
         break;
+      } else {
+        __nanosleep(64);  // yield issue slots to the warps still ranking
       }
     }
     rs_publish(&status[t * RS_BINS + b], tag_inc, excl + v);
