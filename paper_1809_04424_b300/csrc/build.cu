@@ -192,7 +192,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   void *X;
   uint32_t *adj;
   int32_t *adjpre, *deg, *up, *nbr_ptr;
-  int64_t *lex_ptr, *bs_small;
+  int64_t *lex_ptr;
   ws.begin();
   VR_TRY(ws.alloc(&st, 1));
   VR_TRY(F ? ws.alloc((float **)&X, nd) : ws.alloc((int32_t **)&X, nd));
@@ -202,7 +202,6 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(ws.alloc(&up, n));
   VR_TRY(ws.alloc(&nbr_ptr, n + 1));
   VR_TRY(ws.alloc(&lex_ptr, n + 1));
-  VR_TRY(ws.alloc(&bs_small, scan_tmp_slots(n)));
   VR_TRY(ws.commit());
   VR_CUDA(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
 
@@ -235,12 +234,9 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_CUDA(cudaGetLastError());
   prof.end();
   prof.begin("row_counts");
-  k_rows<<<(n + 7) / 8, 256, 0, s>>>(adj, n, W, adjpre, deg, up);
+  k_rows_scan<<<(n + 7) / 8, 256, 0, s>>>(adj, n, W, adjpre, deg, up, nbr_ptr, lex_ptr, st);
   count_launch();
   VR_CUDA(cudaGetLastError());
-  VR_TRY((scan_exclusive<int32_t, int32_t>(deg, nbr_ptr, n, bs_small, s)));
-  VR_TRY((scan_exclusive<int32_t, int64_t>(up, lex_ptr, n, bs_small, s)));
-  VR_CUDA(cudaMemcpyAsync(&st->E, lex_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
   prof.end();
 
   // ---- sync 1: kept-edge count and value errors.
@@ -251,11 +247,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_CUDA(cudaMemsetAsync(&st->flags, 0, sizeof(int32_t), s));
     dist_dispatch<F>(X, n, d, W, cap, adj, st, s);
     count_launch();
-    k_rows<<<(n + 7) / 8, 256, 0, s>>>(adj, n, W, adjpre, deg, up);
+    k_rows_scan<<<(n + 7) / 8, 256, 0, s>>>(adj, n, W, adjpre, deg, up, nbr_ptr, lex_ptr, st);
     count_launch();
-    VR_TRY((scan_exclusive<int32_t, int32_t>(deg, nbr_ptr, n, bs_small, s)));
-    VR_TRY((scan_exclusive<int32_t, int64_t>(up, lex_ptr, n, bs_small, s)));
-    VR_CUDA(cudaMemcpyAsync(&st->E, lex_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     VR_TRY(read_status(st, hst, s));
   }
   const int64_t E = hst->E;

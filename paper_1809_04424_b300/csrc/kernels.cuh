@@ -282,31 +282,85 @@ __global__ void __launch_bounds__(256) k_dist_bitmap(const void *Xv, int n, int 
 // ------------------------------------------------------------- row counts
 // One warp per row: degree, number of neighbours above the row id, and the
 // exclusive prefix popcount of the row's words.
-static __global__ void __launch_bounds__(256) k_rows(const uint32_t *adj, int n, int W, int32_t *adjpre, int32_t *deg,
-                                              int32_t *up) {
+// Row counts and both scans in one launch: every CTA does its rows; the last CTA
+// to finish (ticket after a fence; no CTA waits for another) scans deg and up
+// (n <= 8192) into nbr_ptr and lex_ptr and stores the edge count in st->E.
+static __global__ void __launch_bounds__(256) k_rows_scan(const uint32_t *adj, int n, int W, int32_t *adjpre,
+                                                          int32_t *deg, int32_t *up, int32_t *nbr_ptr,
+                                                          int64_t *lex_ptr, DevStatus *st) {
+  __shared__ int64_t sh[33];
+  __shared__ unsigned int ticket;
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int l = lane_id();
-  if (i >= n) return;
-  int carry = 0, upc = 0;
-  for (int w0 = 0; w0 < W; w0 += 32) {
-    const int w = w0 + l;
-    uint32_t word = w < W ? adj[(int64_t)i * W + w] : 0u;
-    int c = __popc(word);
-    int inc = warp_incl_scan(c);
-    if (w < W) adjpre[(int64_t)i * W + w] = carry + inc - c;
-    carry += __shfl_sync(0xffffffffu, inc, 31);
-    // bits j > i inside this word
-    uint32_t m;
-    const int lo = w * 32;
-    if (lo > i) m = 0xffffffffu;
-    else if (lo + 31 <= i) m = 0u;
-    else m = ~((2u << (i & 31)) - 1u);
-    upc += __popc(word & m);
+  if (i < n) {
+    int carry = 0, upc = 0;
+    for (int w0 = 0; w0 < W; w0 += 32) {
+      const int w = w0 + l;
+      const uint32_t word = w < W ? adj[(int64_t)i * W + w] : 0u;
+      const int c = __popc(word);
+      const int inc = warp_incl_scan(c);
+      if (w < W) adjpre[(int64_t)i * W + w] = carry + inc - c;
+      carry += __shfl_sync(0xffffffffu, inc, 31);
+      uint32_t m;
+      const int lo = w * 32;
+      if (lo > i) m = 0xffffffffu;
+      else if (lo + 31 <= i) m = 0u;
+      else m = ~((2u << (i & 31)) - 1u);
+      upc += __popc(word & m);
+    }
+    upc = warp_sum(upc);
+    if (l == 0) {
+      deg[i] = carry;
+      up[i] = upc;
+    }
   }
-  upc = warp_sum(upc);
-  if (l == 0) {
-    deg[i] = carry;
-    up[i] = upc;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(&st->rows_done, 1u);
+  __syncthreads();
+  if (ticket != gridDim.x - 1) return;
+  __threadfence();
+  // Last CTA: chunks of 2048 entries staged in shared memory (coalesced,
+  // bypassing L1 for the other CTAs' writes), 8 consecutive per thread.
+  constexpr int PER = 8, CH = 256 * PER;
+  __shared__ int32_t cd[CH], cu[CH];
+  int64_t base_d = 0, base_u = 0;
+  for (int c0 = 0; c0 < n; c0 += CH) {
+    for (int q = threadIdx.x; q < CH; q += 256) {
+      const int j = c0 + q;
+      cd[q] = j < n ? __ldcg(deg + j) : 0;
+      cu[q] = j < n ? __ldcg(up + j) : 0;
+    }
+    __syncthreads();
+    int64_t sd = 0, su = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      sd += cd[threadIdx.x * PER + q];
+      su += cu[threadIdx.x * PER + q];
+    }
+    int64_t td, tu;
+    const int64_t ed = block_excl_scan<int64_t>(sd, sh, &td);
+    const int64_t eu = block_excl_scan<int64_t>(su, sh, &tu);
+    int64_t rd = base_d + ed, ru = base_u + eu;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int j = c0 + threadIdx.x * PER + q;
+      if (j < n) {
+        nbr_ptr[j] = (int32_t)rd;
+        lex_ptr[j] = ru;
+      }
+      rd += cd[threadIdx.x * PER + q];
+      ru += cu[threadIdx.x * PER + q];
+    }
+    base_d += td;
+    base_u += tu;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    nbr_ptr[n] = (int32_t)base_d;
+    lex_ptr[n] = base_u;
+    st->E = base_u;
+    st->rows_done = 0;  // ready for another launch on the same status word
   }
 }
 
