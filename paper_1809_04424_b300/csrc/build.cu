@@ -259,7 +259,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
 
   uint64_t *keys;
   RadixScratch rs{};
-  int32_t *flag, *gex, *nbr_ord, *gstart;
+  int32_t *gex, *nbr_ord, *gstart;
   int32_t *everts, *egrade, *erow;
   int64_t *ecol, *bs_e;
   double *gval, *d64 = nullptr, *d64_lex = nullptr;
@@ -270,8 +270,9 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(ws.alloc(&keys, E));
   VR_TRY(ws.alloc(&rs.tkeys, E));
   VR_TRY(ws.alloc(&rs.meta, rs_meta_bytes(E)));
-  VR_TRY(ws.alloc(&flag, E));
   VR_TRY(ws.alloc(&gex, E + 1));
+  uint64_t *eg_lb;  // look-back status of the edge-grade tiles + their ticket
+  VR_TRY(ws.alloc(&eg_lb, (E + EG_TILE - 1) / EG_TILE + 1));
   VR_TRY(ws.alloc(&bs_e, scan_tmp_slots(E)));
   VR_TRY(ws.alloc(&nbr_ord, 2 * E));
   int32_t *eidx = nullptr, *egd = nullptr;  // dense (i, j) -> order index / grade tables for small clouds
@@ -368,11 +369,11 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       prof.end();
     }
     prof.begin("edge_grades");
-    k_edge_flags<F><<<ge, 256, 0, s>>>(keys, d64, E, flag);
-    count_launch(2);
-    VR_TRY((scan_exclusive<int32_t, int32_t>(flag, gex, E, bs_e, s)));
-    k_edge_emit<F><<<ge, 256, 0, s>>>(keys, d64, E, flag, gex, adj, adjpre, W, nbr_ptr, everts, egrade, ecol, erow,
-                                      gval, gstart, nbr_ord, eidx, egd, n, dmf ? 1 : 0, st);
+    const int64_t egt = (E + EG_TILE - 1) / EG_TILE;
+    VR_CUDA(cudaMemsetAsync(eg_lb, 0, sizeof(uint64_t) * (egt + 1), s));
+    k_edge_grades<F><<<(unsigned)egt, 256, 0, s>>>(keys, d64, E, adj, adjpre, W, nbr_ptr, everts, egrade, ecol, erow,
+                                                   gval, gstart, nbr_ord, eidx, egd, n, dmf ? 1 : 0, eg_lb, egt, st);
+    count_launch();
     VR_CUDA(cudaGetLastError());
     prof.end();
   } else {

@@ -820,45 +820,71 @@ static __global__ void __launch_bounds__(RS_THREADS) k_repair_big(const int32_t 
 // ------------------------------------------------------------ edge grades
 // flag[k] = 1 where the squared distance differs from the previous edge's
 // (or from 0 for k = 0): the dense rank is the running sum of flags.
+// Grades and edge outputs in one launch: tiles of EG_TILE sorted keys (one
+// per thread, so the scatter latency is spread over many CTAs) in
+// ticket order; a key starts a new grade when its distance differs from the
+// previous key's (the first distance > 0 also does: grade 0 is d = 0); the
+// block scan of those flags plus the earlier tiles' counts (look-back) is the
+// dense rank; then the outputs: verts, grade, colptr/rowidx ({i, j}), grade
+// values and group starts, the neighbour CSR scatter and the dense tables.  lb: the
+// tiles' zeroed status words followed by the ticket counter.
+constexpr int EG_TILE = 256;
 template <bool F>
-__global__ void k_edge_flags(const uint64_t *keys, const double *d64, int64_t E, int32_t *flag) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
-    int f;
-    if constexpr (F) f = k == 0 ? (d64[0] != 0.0) : (d64[k] != d64[k - 1]);
-    else f = k == 0 ? ((keys[0] >> KEY_SHIFT) != 0) : ((keys[k] >> KEY_SHIFT) != (keys[k - 1] >> KEY_SHIFT));
-    flag[k] = f;
+__global__ void __launch_bounds__(256) k_edge_grades(const uint64_t *keys, const double *d64, int64_t E,
+                                                     const uint32_t *adj, const int32_t *adjpre, int W,
+                                                     const int32_t *nbr_ptr, int32_t *verts, int32_t *grade,
+                                                     int64_t *colptr, int32_t *rowidx, double *gval, int32_t *gstart,
+                                                     int32_t *nbr_ord, int32_t *eidx, int32_t *egd, int n, int key_f32,
+                                                     uint64_t *lb, int64_t ntiles, DevStatus *st) {
+  constexpr int PER = EG_TILE / 256;
+  __shared__ int64_t sh[33];
+  __shared__ int64_t tile_sh, pre_sh;
+  if (threadIdx.x == 0) tile_sh = atomicAdd((unsigned long long *)&lb[ntiles], 1ull);
+  __syncthreads();
+  const int64_t tile = tile_sh, k0 = tile * EG_TILE;
+  // Flags of this thread's PER consecutive keys.
+  uint32_t fl = 0;
+  int cnt = 0;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int64_t k = k0 + threadIdx.x * PER + q;
+    if (k < E) {
+      bool f;
+      if constexpr (F) f = k == 0 ? (d64[0] != 0.0) : (d64[k] != d64[k - 1]);
+      else f = k == 0 ? ((keys[0] >> KEY_SHIFT) != 0) : ((keys[k] >> KEY_SHIFT) != (keys[k - 1] >> KEY_SHIFT));
+      fl |= (uint32_t)f << q;
+      cnt += f;
+    }
   }
-}
-
-// Edge outputs (verts, grade, CSC column = {i, j}), grade values, grade-group
-// starts, and the neighbour CSR scatter: entry (i -> j) sits at
-// nbr_ptr[i] + rank of j in row i, so each row lists neighbours ascending.
-template <bool F>
-__global__ void k_edge_emit(const uint64_t *keys, const double *d64, int64_t E, const int32_t *flag,
-                            const int32_t *gex, const uint32_t *adj, const int32_t *adjpre, int W,
-                            const int32_t *nbr_ptr, int32_t *verts, int32_t *grade, int64_t *colptr, int32_t *rowidx,
-                            double *gval, int32_t *gstart, int32_t *nbr_ord, int32_t *eidx, int32_t *egd, int n,
-                            int key_f32, DevStatus *st) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
+  int64_t tot;
+  const int64_t ex = block_excl_scan<int64_t>((int64_t)cnt, sh, &tot);
+  if (threadIdx.x == 0) pre_sh = tile_lookback(lb, tile, tot, &st->flags);
+  __syncthreads();
+  int64_t g = pre_sh + ex;  // grade before this thread's first key
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int64_t k = k0 + threadIdx.x * PER + q;
+    if (k >= E) break;
+    const bool f = (fl >> q) & 1u;
+    g += f;
     const uint64_t key = keys[k];
     const int i = key_i(key), j = key_j(key);
-    const int g = gex[k + 1];
     verts[2 * k] = i;
     verts[2 * k + 1] = j;
     rowidx[2 * k] = i;
     rowidx[2 * k + 1] = j;
     colptr[k] = 2 * k;
-    grade[k] = g;
-    if (flag[k]) {
+    grade[k] = (int32_t)g;
+    if (f) {
       gval[g] = F ? d64[k]
                   : key_f32 ? (double)__uint_as_float((uint32_t)(key >> KEY_SHIFT)) : (double)(key >> KEY_SHIFT);
       gstart[g] = (int32_t)k;
     }
     nbr_ord[nbr_ptr[i] + bit_rank(adj + (int64_t)i * W, adjpre + (int64_t)i * W, j)] = (int32_t)k;
     nbr_ord[nbr_ptr[j] + bit_rank(adj + (int64_t)j * W, adjpre + (int64_t)j * W, i)] = (int32_t)k;
-    if (eidx) {  // dense order-index and grade tables (i < j), small n only
+    if (eidx) {
       eidx[(int64_t)i * n + j] = (int32_t)k;
-      egd[(int64_t)i * n + j] = g;
+      egd[(int64_t)i * n + j] = (int32_t)g;
     }
     if (k == E - 1) {
       colptr[E] = 2 * E;

@@ -538,6 +538,38 @@ __device__ __forceinline__ void khist_flush(KeyHistSmem &h, const KeyHist &kh) {
   }
 }
 
+// Decoupled look-back over tiles taken in ticket order: returns the sum of
+// the totals of every earlier tile.  status: one zeroed word per tile (flag
+// in the top two bits: 1 = the tile's own total, 2 = the inclusive total;
+// value below).  Called by one thread of the tile; every earlier tile's CTA
+// is already running (ticket order), so the wait ends; it is bounded anyway
+// (F_TIMEOUT in *err).
+constexpr uint64_t LB_AGG = 1ull << 62, LB_INC = 2ull << 62, LB_VAL = (1ull << 62) - 1;
+__device__ __forceinline__ int64_t tile_lookback(uint64_t *status, int64_t tile, int64_t total, int32_t *err) {
+  if (tile == 0) {
+    *(volatile uint64_t *)&status[0] = LB_INC | (uint64_t)total;
+    return 0;
+  }
+  *(volatile uint64_t *)&status[tile] = LB_AGG | (uint64_t)total;
+  int64_t excl = 0, k = tile - 1;
+  long spins = 0;
+  while (k >= 0) {
+    const uint64_t w = *(volatile const uint64_t *)&status[k];
+    if (w & (LB_AGG | LB_INC)) {
+      excl += (int64_t)(w & LB_VAL);
+      if (w & LB_INC) break;
+      --k;
+    } else if (++spins > RS_WAIT_LIMIT) {
+      atomicOr(err, F_TIMEOUT);
+      break;
+    } else {
+      __nanosleep(32);
+    }
+  }
+  *(volatile uint64_t *)&status[tile] = LB_INC | (uint64_t)(excl + total);
+  return excl;
+}
+
 // Scratch for radix_sort: a temporary of n keys and rs_meta_bytes(n) bytes
 // (all-digit histogram, tile tickets, per-tile status words).  The sorted
 // result ends in `keys`.  `err`: device flags word for a timed-out wait.
