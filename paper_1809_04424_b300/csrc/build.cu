@@ -276,9 +276,11 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(ws.alloc(&bs_e, scan_tmp_slots(E)));
   VR_TRY(ws.alloc(&nbr_ord, 2 * E));
   int32_t *eidx = nullptr, *egd = nullptr;  // dense (i, j) -> order index / grade tables for small clouds
+  int32_t *elp = nullptr;                    // dense (i, j) -> lexicographic position (tetrahedra)
   if (n <= DENSE_MAX_N && maxdim >= 2) {
     VR_TRY(ws.alloc(&eidx, (int64_t)n * n));
     VR_TRY(ws.alloc(&egd, (int64_t)n * n));
+    if (maxdim >= 3) VR_TRY(ws.alloc(&elp, (int64_t)n * n));
   }
   VR_TRY(ws.alloc(&gstart, E + 2));
   VR_TRY(out.alloc(&everts, 2 * E));
@@ -335,12 +337,12 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     prof.begin("edge_keys");
     if constexpr (F) {
       k_edge_keys_f32<<<(n + 7) / 8, 256, 0, s>>>((const float *)X, n, d, W, adj, lex_ptr, keys, d64_lex, st,
-                                                   ekh);
+                                                   elp, ekh);
     } else if (dmat) {
-      if (dmf) k_dmat_keys<true><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, adj, lex_ptr, keys, ekh);
-      else k_dmat_keys<false><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, adj, lex_ptr, keys, ekh);
+      if (dmf) k_dmat_keys<true><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, adj, lex_ptr, keys, elp, ekh);
+      else k_dmat_keys<false><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, adj, lex_ptr, keys, elp, ekh);
     } else {
-      k_edge_keys<F><<<(n + 7) / 8, 256, 0, s>>>(X, n, d, W, adj, lex_ptr, keys, ekh);
+      k_edge_keys<F><<<(n + 7) / 8, 256, 0, s>>>(X, n, d, W, adj, lex_ptr, keys, elp, ekh);
     }
     count_launch();
     VR_CUDA(cudaGetLastError());
@@ -543,6 +545,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     }
     uint64_t *keys4 = nullptr, *lex4 = nullptr;
     RadixScratch qrs{};
+    const int qbits = std::max(1, bitlen((uint64_t)(ngrades - 1)));
+    const bool packed = qbits <= 64 - TET_PACK_SHIFT;  // the sorted keys carry the vertices
     out.begin();
     ws.begin();
     VR_TRY(out.alloc(&qverts, 4 * T4));
@@ -551,7 +555,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_TRY(out.alloc(&qrow, 4 * T4));
     if (T4 > 0) {
       VR_TRY(ws.alloc(&keys4, T4));
-      VR_TRY(ws.alloc(&lex4, T4));
+      if (!packed) VR_TRY(ws.alloc(&lex4, T4));
       VR_TRY(ws.alloc(&qrs.tkeys, T4));
       VR_TRY(ws.alloc(&qrs.meta, rs_meta_bytes(T4)));
     }
@@ -561,24 +565,23 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     if (T4 == 0) {
       VR_CUDA(cudaMemsetAsync(qcol, 0, sizeof(int64_t), s));
     } else {
-      const int gbits = std::max(1, bitlen((uint64_t)(ngrades - 1)));
       prof.begin("tet_gen");
       const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
       if (eidx)
         k_tet_gen<true><<<grid_for(T, 8, 148 * 32), 256, 0, s>>>(tk_lex, T, adj, W, tgrade, ordidx, egrade, ex, off4,
-                                                                 T4, keys4, lex4, st);
+                                                                 T4, keys4, lex4, packed ? 1 : 0, st);
       else
         k_tet_gen<false><<<grid_for(T, 8, 148 * 32), 256, 0, s>>>(tk_lex, T, adj, W, tgrade, ordidx, egrade, ex,
-                                                                  off4, T4, keys4, lex4, st);
+                                                                  off4, T4, keys4, lex4, packed ? 1 : 0, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();
       prof.begin("tet_grade_sort");
-      VR_TRY(radix_sort(keys4, T4, 32, gbits, qrs, s));
+      VR_TRY(radix_sort(keys4, T4, packed ? TET_PACK_SHIFT : 32, qbits, qrs, s));
       prof.end();
       prof.begin("tet_final");
       k_tet_final<<<grid_for(T4, 256), 256, 0, s>>>(keys4, T4, lex4, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr,
-                                                    ordidx, qverts, qgrade, qcol, qrow);
+                                                    ordidx, elp, n, packed ? 1 : 0, qverts, qgrade, qcol, qrow);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();

@@ -408,7 +408,8 @@ __device__ __forceinline__ int32_t bit_rank(const uint32_t *adj_row, const int32
 // position lex_ptr[i] + (rank of j in row i) - (neighbours <= i).
 template <bool F>
 __global__ void __launch_bounds__(256) k_edge_keys(const void *Xv, int n, int d, int W, const uint32_t *adj,
-                                                   const int64_t *lex_ptr, uint64_t *keys, KeyHist kh) {
+                                                   const int64_t *lex_ptr, uint64_t *keys, int32_t *elp,
+                                                   KeyHist kh) {
   using T = typename std::conditional<F, float, int32_t>::type;
   __shared__ KeyHistSmem hs;
   khist_init(hs, kh);
@@ -434,6 +435,7 @@ __global__ void __launch_bounds__(256) k_edge_keys(const void *Xv, int n, int d,
         else dk = d2_int(X + (int64_t)i * d, X + (int64_t)j * d, d);
         key = (dk << KEY_SHIFT) | ((uint64_t)i << ID_BITS) | (uint64_t)j;
         keys[t + q] = key;
+        if (elp) elp[(int64_t)i * n + j] = (int32_t)(t + q);  // lexicographic position (tetrahedra)
       }
       khist_add(hs, kh, key, q < r.tot);
     }
@@ -509,7 +511,8 @@ static __global__ void __launch_bounds__(256) k_dmat_bitmap(const void *Dv, int 
 // with the matrix entry as the value).
 template <bool F>
 static __global__ void __launch_bounds__(256) k_dmat_keys(const void *Dv, int n, int W, const uint32_t *adj,
-                                                          const int64_t *lex_ptr, uint64_t *keys, KeyHist kh) {
+                                                          const int64_t *lex_ptr, uint64_t *keys, int32_t *elp,
+                                                          KeyHist kh) {
   __shared__ KeyHistSmem hs;
   khist_init(hs, kh);
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -531,6 +534,7 @@ static __global__ void __launch_bounds__(256) k_dmat_keys(const void *Dv, int n,
         const uint64_t dk = dmat_key<F>(Dv, (int64_t)i * n + j);
         key = (dk << KEY_SHIFT) | ((uint64_t)i << ID_BITS) | (uint64_t)j;
         keys[t + q] = key;
+        if (elp) elp[(int64_t)i * n + j] = (int32_t)(t + q);  // lexicographic position (tetrahedra)
       }
       khist_add(hs, kh, key, q < r.tot);
     }
@@ -582,7 +586,7 @@ __device__ __forceinline__ double soft_value(const SoftAcc &s) {
 static __global__ void __launch_bounds__(256) k_edge_keys_f32(const float *X, int n, int d, int W,
                                                               const uint32_t *adj, const int64_t *lex_ptr,
                                                               uint64_t *keys, double *d64_lex, DevStatus *st,
-                                                              KeyHist kh) {
+                                                              int32_t *elp, KeyHist kh) {
   __shared__ float tile[8][32][33];
   __shared__ float rowi[8][32];
   __shared__ KeyHistSmem hs;
@@ -629,6 +633,7 @@ static __global__ void __launch_bounds__(256) k_edge_keys_f32(const float *X, in
         key = ((uint64_t)__float_as_uint(__double2float_rn(f)) << KEY_SHIFT) | ((uint64_t)i << ID_BITS) |
               (uint64_t)j;
         keys[t + q] = key;
+        if (elp) elp[(int64_t)i * n + j] = (int32_t)(t + q);
         if (f > 0.0) {
           const float ff = (float)f, sf = sqrtf(ff);
           worst = fmaxf(worst, fabsf((float)((double)a - f)) / (sf * (sqrtf(a) + sf)));
@@ -1356,13 +1361,16 @@ static __global__ void __launch_bounds__(256) k_tet_count(const uint64_t *tk_lex
   }
 }
 
-// Keys (grade << 32 | lexicographic position q) and the packed vertices of
-// each tetrahedron at q.
+// Keys in lexicographic order.  packed (grades below 2^12): grade << 52 |
+// a,b,c,d (13 bits each), so the sorted keys carry the vertices; otherwise
+// grade << 32 | lexicographic position q, with the packed vertices at lex4[q].
+constexpr int TET_PACK_SHIFT = 4 * ID_BITS;
 template <bool DENSE>
 static __global__ void __launch_bounds__(256) k_tet_gen(const uint64_t *tk_lex, int64_t T, const uint32_t *adj,
                                                         int W, const int32_t *tgrade, const int32_t *ordidx,
                                                         const int32_t *egrade, EdgeIndex ex, const int64_t *off4,
-                                                        int64_t T4, uint64_t *keys4, uint64_t *lex4, DevStatus *st) {
+                                                        int64_t T4, uint64_t *keys4, uint64_t *lex4, int packed,
+                                                        DevStatus *st) {
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   for (int64_t t = blockIdx.x * 8 + (threadIdx.x >> 5); t < T; t += nwarps) {
@@ -1389,8 +1397,13 @@ static __global__ void __launch_bounds__(256) k_tet_gen(const uint64_t *tk_lex, 
           g = max(g, ex.grade<DENSE>(c, d));
           const int64_t q = q0 + qq;
           if (q < T4) {
-            keys4[q] = ((uint64_t)(uint32_t)g << 32) | (uint64_t)q;
-            lex4[q] = (k3 << ID_BITS) | (uint64_t)d;
+            const uint64_t v4 = (k3 << ID_BITS) | (uint64_t)d;
+            if (packed) {
+              keys4[q] = ((uint64_t)(uint32_t)g << TET_PACK_SHIFT) | v4;
+            } else {
+              keys4[q] = ((uint64_t)(uint32_t)g << 32) | (uint64_t)q;
+              lex4[q] = v4;
+            }
           } else {
             raise_flag(st, F_INTERNAL);  // never write past the key arrays
           }
@@ -1404,8 +1417,8 @@ static __global__ void __launch_bounds__(256) k_tet_gen(const uint64_t *tk_lex, 
 // Lexicographic position of triangle (x,y,z), x<y<z, all edges kept.
 __device__ __forceinline__ int64_t tri_lexpos(int x, int y, int z, const uint64_t *tk_lex, const int64_t *toff,
                                               const uint32_t *adj, const int32_t *adjpre, int W, const int32_t *deg,
-                                              const int32_t *up, const int64_t *lex_ptr) {
-  const int64_t lp = lex_pos(x, y, adj, adjpre, W, deg, up, lex_ptr);
+                                              const int32_t *up, const int64_t *lex_ptr, const int32_t *elp, int n) {
+  const int64_t lp = elp ? (int64_t)elp[(int64_t)x * n + y] : lex_pos(x, y, adj, adjpre, W, deg, up, lex_ptr);
   int64_t lo = toff[lp], hi = toff[lp + 1];
   while (lo < hi) {
     const int64_t mid = (lo + hi) >> 1;
@@ -1421,19 +1434,19 @@ __device__ __forceinline__ int64_t tri_lexpos(int x, int y, int z, const uint64_
 static __global__ void k_tet_final(const uint64_t *keys4, int64_t T4, const uint64_t *lex4, const uint64_t *tk_lex,
                                    const int64_t *toff, const uint32_t *adj, const int32_t *adjpre, int W,
                                    const int32_t *deg, const int32_t *up, const int64_t *lex_ptr,
-                                   const int32_t *ordidx, int32_t *verts, int32_t *grade, int64_t *colptr,
-                                   int32_t *rowidx) {
+                                   const int32_t *ordidx, const int32_t *elp, int n, int packed, int32_t *verts,
+                                   int32_t *grade, int64_t *colptr, int32_t *rowidx) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T4; p += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = keys4[p];
-    const uint64_t v = lex4[key & 0xffffffffull];
+    const uint64_t v = packed ? key & ((1ull << TET_PACK_SHIFT) - 1) : lex4[key & 0xffffffffull];
     const int d = (int)(v & ID_MASK);
     int a, b, c;
     lex3_unpack(v >> ID_BITS, a, b, c);
     int32_t r[4];
-    r[0] = ordidx[tri_lexpos(b, c, d, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr)];
-    r[1] = ordidx[tri_lexpos(a, c, d, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr)];
-    r[2] = ordidx[tri_lexpos(a, b, d, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr)];
-    r[3] = ordidx[tri_lexpos(a, b, c, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr)];
+    r[0] = ordidx[tri_lexpos(b, c, d, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr, elp, n)];
+    r[1] = ordidx[tri_lexpos(a, c, d, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr, elp, n)];
+    r[2] = ordidx[tri_lexpos(a, b, d, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr, elp, n)];
+    r[3] = ordidx[tri_lexpos(a, b, c, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr, elp, n)];
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -1447,7 +1460,7 @@ static __global__ void k_tet_final(const uint64_t *keys4, int64_t T4, const uint
     verts[4 * p + 1] = b;
     verts[4 * p + 2] = c;
     verts[4 * p + 3] = d;
-    grade[p] = (int32_t)(key >> 32);
+    grade[p] = (int32_t)(packed ? key >> TET_PACK_SHIFT : key >> 32);
     colptr[p] = 4 * p;
     rowidx[4 * p] = r[0];
     rowidx[4 * p + 1] = r[1];

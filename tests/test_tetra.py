@@ -69,6 +69,15 @@ def test_float_ngon_and_lattice(torch):
     check(torch, pts, 1.5)
 
 
+def test_many_grades_unpacked_keys(torch):
+    """A float cloud with more than 2^12 distinct edge lengths: the
+    tetrahedron keys carry a lexicographic position instead of the vertices."""
+    g0 = synth.rng(77)
+    pts = g0.normal(size=(400, 3)).astype(np.float32)
+    g = check(torch, pts, 0.9, bars=False)
+    assert len(g["gv"]) > 4097 and g["counts"][3] > 1000
+
+
 def test_beyond_dense_table(torch):
     """n = 4500 (> 4096): edge indices through the neighbour CSR."""
     g0 = synth.rng(45)
