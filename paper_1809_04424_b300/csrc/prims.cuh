@@ -399,19 +399,35 @@ static __global__ void __launch_bounds__(RS_THREADS, 3) k_rs_onesweep(const uint
     rs_publish(&status[b], tag_inc, v);
   } else {
     rs_publish(&status[t * RS_BINS + b], tag_agg, v);
+    // Look back in windows of LB_WIN predecessors (loads issued together),
+    // consumed in order until an inclusive count; a word not yet published
+    // restarts the window there.
+    constexpr int LB_WIN = 8;
     int64_t k = t - 1;
     long spins = 0;
-    while (k >= 0) {
-      const uint64_t w = *(volatile const uint64_t *)&status[k * RS_BINS + b];
-      const uint32_t tag = (uint32_t)(w >> 56);
-      if (tag == tag_inc || tag == tag_agg) {
-        excl += w & ((1ull << 56) - 1);
-        if (tag == tag_inc) break;
-        --k;
-      } else if (++spins > RS_WAIT_LIMIT) {
-        atomicOr(err, F_TIMEOUT);
-        break;
-      } else {
+    bool done = false;
+    while (!done && k >= 0) {
+      uint64_t w[LB_WIN];
+#pragma unroll
+      for (int q = 0; q < LB_WIN; ++q)
+        w[q] = k - q >= 0 ? *(volatile const uint64_t *)&status[(k - q) * RS_BINS + b] : 0;
+      int used = 0;
+#pragma unroll
+      for (int q = 0; q < LB_WIN; ++q) {
+        if (done || used != q || k - q < 0) continue;
+        const uint32_t tag = (uint32_t)(w[q] >> 56);
+        if (tag == tag_inc || tag == tag_agg) {
+          excl += w[q] & ((1ull << 56) - 1);
+          ++used;
+          if (tag == tag_inc) done = true;
+        }
+      }
+      k -= used;
+      if (!done && used == 0) {
+        if (++spins > RS_WAIT_LIMIT) {
+          atomicOr(err, F_TIMEOUT);
+          break;
+        }
         __nanosleep(64);  // yield issue slots to the warps still ranking
       }
     }
