@@ -387,8 +387,13 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
 
   if (maxdim >= 2 && E > 0) {
     prof.begin("tri_count");
-    k_tri_count<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, E, adj, adjpre, W, nbr_ptr, nbr_ord, deg, up,
-                                                           lex_ptr, st, tcnt, maxdim >= 3 ? 1 : 0);
+    const EdgeIndex exc{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
+    if (eidx)
+      k_tri_count<true><<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, E, adj, adjpre, W, nbr_ptr, nbr_ord, deg,
+                                                                 up, lex_ptr, st, tcnt, maxdim >= 3 ? 1 : 0, exc);
+    else
+      k_tri_count<false><<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, E, adj, adjpre, W, nbr_ptr, nbr_ord, deg,
+                                                                  up, lex_ptr, st, tcnt, maxdim >= 3 ? 1 : 0, exc);
     count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int64_t>(tcnt, toff, E, bs_e, s)));
     VR_CUDA(cudaMemcpyAsync(&st->T, toff + E, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
@@ -488,8 +493,13 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       prof.end();
     } else if (T > 0) {
       prof.begin("tri_emit");
-      k_tri_emit<<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr, nbr_ord, toff,
-                                                          T, tverts, tgrade, tcol, trow, st);
+      // The emission keeps the neighbour-CSR lookups even with the dense
+      // table: its two lookups per candidate land in the rows' contiguous
+      // neighbour lists, while the table's are spread over n^2 entries
+      // (measured: 0.58 vs 0.65 ms on 19.8M triangles at n = 4000).
+      const EdgeIndex exm{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
+      k_tri_emit<false><<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr,
+                                                                 nbr_ord, toff, T, tverts, tgrade, tcol, trow, exm, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();

@@ -968,11 +968,13 @@ struct EdgeIndex {
   }
 };
 
+template <bool DENSE>
 static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts, int64_t E, const uint32_t *adj,
                                                           const int32_t *adjpre, int W, const int32_t *nbr_ptr,
                                                           const int32_t *nbr_ord, const int32_t *deg,
                                                           const int32_t *up, const int64_t *lex_ptr,
-                                                          const DevStatus *st, int32_t *tcnt, int force_lex) {
+                                                          const DevStatus *st, int32_t *tcnt, int force_lex,
+                                                          EdgeIndex ex) {
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   const bool lexm = lex_mode(E, st->ngrades, force_lex);
@@ -988,21 +990,28 @@ static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts,
       for (int w0 = 0; w0 < W; w0 += 32) {
         const int w = w0 + l;
         const uint32_t wa = w < W ? ra[w] : 0u, wb = w < W ? rb[w] : 0u;
-        const int32_t qa = w < W ? pa[w] : 0, qb = w < W ? pb[w] : 0;
+        const int32_t qa = !DENSE && w < W ? pa[w] : 0, qb = !DENSE && w < W ? pb[w] : 0;
         const uint32_t m = wa & wb;
         const BitChunk r = bit_round(m);
         for (int q0 = 0; q0 < r.tot; q0 += 32) {
           const int q = q0 + l;
           const int ow = bit_owner(r, q);
-          const uint32_t om = __shfl_sync(0xffffffffu, m, ow), owa = __shfl_sync(0xffffffffu, wa, ow),
-                         owb = __shfl_sync(0xffffffffu, wb, ow);
-          const int32_t oqa = __shfl_sync(0xffffffffu, qa, ow), oqb = __shfl_sync(0xffffffffu, qb, ow);
+          const uint32_t om = __shfl_sync(0xffffffffu, m, ow);
           const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
           bool ok = false;
-          if (q < r.tot) {
-            const int bit = __fns(om, 0, q - oex + 1);
-            const uint32_t below = (1u << bit) - 1u;
-            ok = oa[oqa + __popc(owa & below)] < (int32_t)e && ob[oqb + __popc(owb & below)] < (int32_t)e;
+          if constexpr (DENSE) {
+            if (q < r.tot) {
+              const int cv = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
+              ok = ex.ord<true>(min(a, cv), max(a, cv)) < (int32_t)e && ex.ord<true>(min(b, cv), max(b, cv)) < (int32_t)e;
+            }
+          } else {
+            const uint32_t owa = __shfl_sync(0xffffffffu, wa, ow), owb = __shfl_sync(0xffffffffu, wb, ow);
+            const int32_t oqa = __shfl_sync(0xffffffffu, qa, ow), oqb = __shfl_sync(0xffffffffu, qb, ow);
+            if (q < r.tot) {
+              const int bit = __fns(om, 0, q - oex + 1);
+              const uint32_t below = (1u << bit) - 1u;
+              ok = oa[oqa + __popc(owa & below)] < (int32_t)e && ob[oqb + __popc(owb & below)] < (int32_t)e;
+            }
           }
           cnt += __popc(__ballot_sync(0xffffffffu, ok));
         }
@@ -1130,12 +1139,15 @@ static __global__ void __launch_bounds__(256) k_tri_final(const uint64_t *tkeys,
 // lane q taking the round's q-th triangle, found by a 5-step search over the
 // lanes' prefix counts and __fns inside the owner's mask, so consecutive
 // lanes write consecutive output slots (coalesced stores).
+// DENSE: the two edge positions of a candidate come from the dense
+// order-index table (one load each) instead of bitmap rank + CSR.
+template <bool DENSE>
 static __global__ void __launch_bounds__(256) k_tri_emit(const int32_t *everts, const int32_t *egrade, int64_t E,
                                                          const uint32_t *adj, const int32_t *adjpre, int W,
                                                          const int32_t *nbr_ptr, const int32_t *nbr_ord,
                                                          const int64_t *toff, int64_t T, int32_t *tverts,
                                                          int32_t *tgrade, int64_t *tcolptr, int32_t *trow,
-                                                         DevStatus *st) {
+                                                         EdgeIndex ex, DevStatus *st) {
   const int l = lane_id();
   const uint32_t lt = lanemask_lt();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
@@ -1149,26 +1161,35 @@ static __global__ void __launch_bounds__(256) k_tri_emit(const int32_t *everts, 
     for (int w0 = 0; w0 < W; w0 += 32) {
       const int w = w0 + l;
       const uint32_t wa = w < W ? ra[w] : 0u, wb = w < W ? rb[w] : 0u;
-      const int32_t qa = w < W ? pa[w] : 0, qb = w < W ? pb[w] : 0;
+      const int32_t qa = !DENSE && w < W ? pa[w] : 0, qb = !DENSE && w < W ? pb[w] : 0;
       const uint32_t m = wa & wb;
       const BitChunk r = bit_round(m);
       for (int q0 = 0; q0 < r.tot; q0 += 32) {
         const int q = q0 + l;
         const int ow = bit_owner(r, q);
-        const uint32_t om = __shfl_sync(0xffffffffu, m, ow), owa = __shfl_sync(0xffffffffu, wa, ow),
-                       owb = __shfl_sync(0xffffffffu, wb, ow);
-        const int32_t oqa = __shfl_sync(0xffffffffu, qa, ow), oqb = __shfl_sync(0xffffffffu, qb, ow);
+        const uint32_t om = __shfl_sync(0xffffffffu, m, ow);
         const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
         bool ok = false;
         int cv = 0;
         int32_t oac = 0, obc = 0;
-        if (q < r.tot) {
-          const int bit = __fns(om, 0, q - oex + 1);
-          const uint32_t below = (1u << bit) - 1u;
-          cv = (w0 + ow) * 32 + bit;
-          oac = oa[oqa + __popc(owa & below)];
-          obc = ob[oqb + __popc(owb & below)];
-          ok = oac < (int32_t)e && obc < (int32_t)e;
+        if constexpr (DENSE) {
+          if (q < r.tot) {
+            cv = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
+            oac = ex.ord<true>(min(a, cv), max(a, cv));
+            obc = ex.ord<true>(min(b, cv), max(b, cv));
+            ok = oac < (int32_t)e && obc < (int32_t)e;
+          }
+        } else {
+          const uint32_t owa = __shfl_sync(0xffffffffu, wa, ow), owb = __shfl_sync(0xffffffffu, wb, ow);
+          const int32_t oqa = __shfl_sync(0xffffffffu, qa, ow), oqb = __shfl_sync(0xffffffffu, qb, ow);
+          if (q < r.tot) {
+            const int bit = __fns(om, 0, q - oex + 1);
+            const uint32_t below = (1u << bit) - 1u;
+            cv = (w0 + ow) * 32 + bit;
+            oac = oa[oqa + __popc(owa & below)];
+            obc = ob[oqb + __popc(owb & below)];
+            ok = oac < (int32_t)e && obc < (int32_t)e;
+          }
         }
         const uint32_t bal = __ballot_sync(0xffffffffu, ok);
         if (ok && t + __popc(bal & lt) >= T) {  // never write past the outputs
