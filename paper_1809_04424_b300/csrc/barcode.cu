@@ -172,14 +172,18 @@ constexpr int BC_BATCH = 1024;
 // entry present in both lists is an A entry directly followed by the equal B
 // entry), drops the entries that cancel, and a block scan places the rest.
 // Returns the output length (to every thread).
+// A column's chain of additions is serial, so one column gets a whole
+// 1024-thread CTA (the longest chains decide the reduction's time).
+constexpr int BR_THREADS = 1024;
 constexpr int BC_PER = 16;
-constexpr int BC_TILE = BC_THREADS * BC_PER;
+constexpr int BC_TILE = BR_THREADS * BC_PER;
 
 struct SymdiffSmem {
   int32_t a[BC_TILE], b[BC_TILE];
   int64_t sh[33];
-  int64_t split[BC_THREADS + 1];  // A entries before each tile boundary of a group of tiles
+  int64_t split[BR_THREADS + 1];  // A entries before each tile boundary of a group of tiles
 };
+constexpr size_t BR_SMEM = sizeof(SymdiffSmem) + 64;
 
 // Entries of A before merged position d (A first on ties).
 __device__ __forceinline__ int64_t merge_split(const int32_t *A, int64_t la, const int32_t *B, int64_t lb, int64_t d) {
@@ -196,33 +200,34 @@ __device__ int64_t cta_symdiff(const int32_t *A, int64_t la, const int32_t *B, i
                                SymdiffSmem &S) {
   int64_t written = 0;
   const int64_t L = la + lb;
-  for (int64_t g0 = 0; g0 < L; g0 += (int64_t)BC_TILE * BC_THREADS) {
-    // The boundaries of up to BC_THREADS tiles, one binary search per thread.
+  for (int64_t g0 = 0; g0 < L; g0 += (int64_t)BC_TILE * BR_THREADS) {
+    // The boundaries of up to BR_THREADS tiles, one binary search per thread.
     {
       const int64_t d = g0 + (int64_t)threadIdx.x * BC_TILE;
       S.split[threadIdx.x] = merge_split(A, la, B, lb, d < L ? d : L);
       if (threadIdx.x == 0) {
-        const int64_t dl = g0 + (int64_t)BC_THREADS * BC_TILE;
-        S.split[BC_THREADS] = merge_split(A, la, B, lb, dl < L ? dl : L);
+        const int64_t dl = g0 + (int64_t)BR_THREADS * BC_TILE;
+        S.split[BR_THREADS] = merge_split(A, la, B, lb, dl < L ? dl : L);
       }
     }
     __syncthreads();
-    for (int t = 0; t < BC_THREADS; ++t) {
+    for (int t = 0; t < BR_THREADS; ++t) {
       const int64_t d0 = g0 + (int64_t)t * BC_TILE;
       if (d0 >= L) break;
       const int64_t d1 = d0 + BC_TILE < L ? d0 + BC_TILE : L;
       const int64_t a0 = S.split[t], a1 = S.split[t + 1];  // split[t + 1] was taken at d1
       const int64_t b0 = d0 - a0, b1 = d1 - a1;
       const int na = (int)(a1 - a0), nb = (int)(b1 - b0);
-      for (int q = threadIdx.x; q < na; q += BC_THREADS) S.a[q] = A[a0 + q];
-      for (int q = threadIdx.x; q < nb; q += BC_THREADS) S.b[q] = B[b0 + q];
+      for (int q = threadIdx.x; q < na; q += BR_THREADS) S.a[q] = A[a0 + q];
+      for (int q = threadIdx.x; q < nb; q += BR_THREADS) S.b[q] = B[b0 + q];
       const int32_t prevA = a0 > 0 ? A[a0 - 1] : -1;    // last A entry before the tile
       const int32_t nextB = b1 < lb ? B[b1] : INT_MAX;  // first B entry after the tile
       __syncthreads();
-      // This thread's merged positions [p0, p1) of the tile.
+      // This thread's merged positions [p0, p1) of the tile: one pass counts
+      // the entries that survive, a block scan places them, a second pass
+      // writes them (no per-thread buffer).
       const int p0 = threadIdx.x * BC_PER, p1 = min(p0 + BC_PER, na + nb);
-      int32_t keep[BC_PER];
-      int nk = 0;
+      int ia0 = 0, ib0 = 0;
       if (p0 < p1) {
         int lo = p0 - nb > 0 ? p0 - nb : 0, hi = p0 < na ? p0 : na;
         while (lo < hi) {
@@ -230,29 +235,43 @@ __device__ int64_t cta_symdiff(const int32_t *A, int64_t la, const int32_t *B, i
           if (S.a[mid] <= S.b[p0 - mid - 1]) lo = mid + 1;
           else hi = mid;
         }
-        int ia = lo, ib = p0 - lo;
-#pragma unroll
-        for (int r = 0; r < BC_PER; ++r) {
-          if (p0 + r >= p1) break;
+        ia0 = lo;
+        ib0 = p0 - lo;
+      }
+      int nk = 0;
+      {
+        int ia = ia0, ib = ib0;
+        for (int p = p0; p < p1; ++p) {
           const bool takeA = ib >= nb || (ia < na && S.a[ia] <= S.b[ib]);
           if (takeA) {
             const int32_t x = S.a[ia];
-            const int32_t nextb = ib < nb ? S.b[ib] : nextB;
-            if (nextb != x) keep[nk++] = x;
+            nk += (ib < nb ? S.b[ib] : nextB) != x;
             ++ia;
           } else {
             const int32_t y = S.b[ib];
-            const int32_t preva = ia > 0 ? S.a[ia - 1] : prevA;
-            if (preva != y) keep[nk++] = y;
+            nk += (ia > 0 ? S.a[ia - 1] : prevA) != y;
             ++ib;
           }
         }
       }
       int64_t tot;
       const int64_t off = block_excl_scan<int64_t>((int64_t)nk, S.sh, &tot);
-#pragma unroll
-      for (int q = 0; q < BC_PER; ++q)
-        if (q < nk) out[written + off + q] = keep[q];
+      {
+        int ia = ia0, ib = ib0;
+        int32_t *o = out + written + off;
+        for (int p = p0; p < p1; ++p) {
+          const bool takeA = ib >= nb || (ia < na && S.a[ia] <= S.b[ib]);
+          if (takeA) {
+            const int32_t x = S.a[ia];
+            if ((ib < nb ? S.b[ib] : nextB) != x) *o++ = x;
+            ++ia;
+          } else {
+            const int32_t y = S.b[ib];
+            if ((ia > 0 ? S.a[ia - 1] : prevA) != y) *o++ = y;
+            ++ib;
+          }
+        }
+      }
       written += tot;
       __syncthreads();
     }
@@ -264,13 +283,14 @@ __device__ int64_t cta_symdiff(const int32_t *A, int64_t la, const int32_t *B, i
 // edge act[P-1-p]: youngest first) against final columns, one CTA per
 // column: while the pivot has a final owner, add that column (into fresh
 // pool space).  No pool space: *overflow, the column keeps its last value.
-static __global__ void __launch_bounds__(BC_THREADS) k_batch_reduce(const int32_t *act, int64_t P, int64_t p0,
+static __global__ void __launch_bounds__(BR_THREADS) k_batch_reduce(const int32_t *act, int64_t P, int64_t p0,
                                                                     int64_t p1, int64_t *coff, int32_t *clen,
                                                                     int32_t *pool, int64_t cap,
                                                                     unsigned long long *top,
                                                                     const int32_t *final_owner, const uint8_t *fin,
                                                                     int32_t *overflow) {
-  __shared__ SymdiffSmem S;
+  extern __shared__ __align__(16) unsigned char br_smem[];
+  SymdiffSmem &S = *reinterpret_cast<SymdiffSmem *>(br_smem);
   __shared__ int64_t s_o, s_at;
   const int64_t p = p0 + blockIdx.x;
   if (p >= p1) return;
@@ -531,6 +551,7 @@ static vr_status reduce_cohomology(vr_complex *c, int k, cudaStream_t s, Dev &dv
     prof.end();
 
     prof.begin(k == 1 ? "bars.reduce" : "bars.reduce2");
+    VR_CUDA(cudaFuncSetAttribute(k_batch_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BR_SMEM));
     // Active columns in ascending edge order; processing takes them from the
     // youngest.
     int32_t *aflag, *act, *final_owner, *rem;
@@ -565,7 +586,7 @@ static vr_status reduce_cohomology(vr_complex *c, int k, cudaStream_t s, Dev &dv
         VR_CUDA(cudaMemsetAsync(overflow, 0, sizeof(int32_t), s));
         // Two passes per check: a pass on a settled batch does nothing.
         for (int k = 0; k < 2; ++k) {
-          k_batch_reduce<<<(unsigned)(p1 - p0), BC_THREADS, 0, s>>>(act, P, p0, p1, coff, clen, pool, cap, top,
+          k_batch_reduce<<<(unsigned)(p1 - p0), BR_THREADS, BR_SMEM, s>>>(act, P, p0, p1, coff, clen, pool, cap, top,
                                                                     final_owner, fin, overflow);
           k_batch_finalize<<<1, BC_BATCH, 0, s>>>(act, P, p0, p1, coff, clen, pool, final_owner, fin, overflow,
                                                   rem);
