@@ -7,7 +7,9 @@
 // neighbour CSR -> triangle counts -> scan -> tie groups -> [sync 2: triangle
 // count] -> triangle emission -> tie-group merge.  Only sizes cross to the host.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "complex.h"
@@ -76,20 +78,80 @@ static unsigned grid_for(int64_t work, int threads, int cap_ctas = 148 * 16) {
 
 static int bitlen(uint64_t v) { return v ? 64 - __builtin_clzll(v) : 0; }
 
-// Read the status word back (pinned buffer, stream sync).
-static vr_status read_status(const DevStatus *dst, DevStatus *host, cudaStream_t s) {
-  VR_CUDA(cudaMemcpyAsync(host, dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
-  VR_CUDA(cudaStreamSynchronize(s));
-  return flags_to_status(host->flags);
+// Host mirror of the status word in mapped pinned memory.  At a sync point
+// k_publish (one warp, launched behind the segment's last kernel) copies the
+// status into it and then writes a fresh sequence number, which the host
+// polls: no copy-engine transfer and no stream synchronisation between the
+// segment's end and the host's next launch.
+struct HostStatus {
+  DevStatus st;
+  uint64_t seq;
+};
+struct StatusMirror {
+  HostStatus *h, *d;  // host and device addresses of one mapped buffer
+  uint64_t next;      // last sequence number handed out
+};
+
+static StatusMirror *status_mirror() {
+  thread_local StatusMirror m{nullptr, nullptr, 0};
+  if (!m.h) {
+    HostStatus *h = nullptr;
+    if (cudaHostAlloc((void **)&h, sizeof(HostStatus), cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    if (cudaHostGetDevicePointer((void **)&m.d, h, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeHost(h);
+      return nullptr;
+    }
+    memset(h, 0, sizeof(HostStatus));
+    m.h = h;
+  }
+  return &m;
 }
 
-static DevStatus *pinned_status() {
-  thread_local DevStatus *p = nullptr;
-  if (!p && cudaMallocHost((void **)&p, sizeof(DevStatus)) != cudaSuccess) {
-    cudaGetLastError();
-    p = nullptr;
+// Copy the status word (and, if t_src is set, *t_src into its T field) to the
+// host mirror, then publish seq.
+static __global__ void k_publish(const DevStatus *st, const int64_t *t_src, HostStatus *h, uint64_t seq) {
+  pdl_entry();
+  constexpr int NW = (int)(sizeof(DevStatus) / 4);
+  static_assert(sizeof(DevStatus) % 4 == 0 && NW <= 32, "one warp copies the status word");
+  const uint32_t *src = (const uint32_t *)st;
+  if (threadIdx.x < NW) ((volatile uint32_t *)&h->st)[threadIdx.x] = __ldcg(src + threadIdx.x);
+  __syncwarp();
+  if (threadIdx.x == 0 && t_src) *(volatile int64_t *)&h->st.T = __ldcg(t_src);
+  __threadfence_system();
+  __syncwarp();
+  if (threadIdx.x == 0) {
+    __threadfence_system();
+    *(volatile uint64_t *)&h->seq = seq;
   }
-  return p;
+}
+
+// Sync point: publish the status word and wait for it on the host.  The wait
+// asks the stream for errors every 1024 polls, so a failed kernel ends it.
+static vr_status read_status(const DevStatus *dst, StatusMirror *m, cudaStream_t s, const int64_t *t_src = nullptr) {
+  const uint64_t seq = ++m->next;
+  launch_dep(k_publish, 1, 32, 0, s, dst, t_src, m->d, seq);
+  count_launch();
+  VR_CUDA(cudaGetLastError());
+  const volatile uint64_t *p = &m->h->seq;
+  for (uint64_t k = 1; *p != seq; ++k) {
+    if ((k & 1023) == 0) {
+      const cudaError_t e = cudaStreamQuery(s);
+      if (e == cudaSuccess && *p != seq) {
+        set_error("the status word was not published");
+        return VR_ERR_INTERNAL;
+      }
+      if (e != cudaSuccess && e != cudaErrorNotReady) return cuda_status(e, "status wait", __FILE__, __LINE__);
+    }
+#if defined(__x86_64__)
+    __builtin_ia32_pause();
+#endif
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
+  return flags_to_status(m->h->st.flags);
 }
 
 // fp32 thresholds of the cap test: a_keep = largest float a with
@@ -117,7 +179,7 @@ static void launch_dist(const void *X, int n, int d, int W, const Cap &cap, uint
                         cudaStream_t s) {
   const int B = (n + 31) / 32;
   dim3 grid(B, (B + 7) / 8);
-  k_dist_bitmap<F, DR><<<grid, 256, 0, s>>>(X, n, d, W, cap, adj, st);
+  launch_dep(k_dist_bitmap<F, DR>, grid, 256, 0, s, X, n, d, W, cap, adj, st);
 }
 
 bool gram_tc_eligible(vr_dtype dtype, int n, int d);
@@ -138,11 +200,12 @@ template <bool F>
 // (dtype VR_I32 or VR_F32 = its element type; d and dpts unused, F false).
 static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dtype, int32_t maxdim, double maxrad,
                             cudaStream_t s, vr_complex *res, const void *dmat = nullptr) {
-  DevStatus *hst = pinned_status();
-  if (!hst) {
-    set_error("pinned host status buffer allocation failed");
+  StatusMirror *sm = status_mirror();
+  if (!sm) {
+    set_error("mapped host status buffer allocation failed");
     return VR_ERR_OOM;
   }
+  const DevStatus *hst = &sm->h->st;
   Arena ws(s), out(s);
   Prof prof(s);
   const int W = (n + 31) / 32;
@@ -193,8 +256,17 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   uint32_t *adj;
   int32_t *adjpre, *deg, *up, *nbr_ptr;
   int64_t *lex_ptr;
+  // The edge sort's scratch (digit histogram, tile status) and the edge-grade
+  // look-back words, sized for every possible edge, follow the status word
+  // in one block, so that a single memset clears all three up front.
+  const int64_t E_ub = (int64_t)n * (n - 1) / 2;
+  const int64_t eg_words = (E_ub + EG_TILE - 1) / EG_TILE + 1;
+  RadixScratch rs{};
+  uint64_t *eg_lb;  // look-back status of the edge-grade tiles + their ticket
   ws.begin();
   VR_TRY(ws.alloc(&st, 1));
+  VR_TRY(ws.alloc(&rs.meta, rs_meta_bytes(E_ub)));
+  VR_TRY(ws.alloc(&eg_lb, eg_words));
   VR_TRY(F ? ws.alloc((float **)&X, nd) : ws.alloc((int32_t **)&X, nd));
   VR_TRY(ws.alloc(&adj, (int64_t)n * W));
   VR_TRY(ws.alloc(&adjpre, (int64_t)n * W));
@@ -203,18 +275,22 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(ws.alloc(&nbr_ptr, n + 1));
   VR_TRY(ws.alloc(&lex_ptr, n + 1));
   VR_TRY(ws.commit());
-  VR_CUDA(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
+  VR_CUDA(cudaMemsetAsync(st, 0, (size_t)((char *)(eg_lb + eg_words) - (char *)st), s));
 
   // Stage: convert to the working element type and check values.
   prof.begin("stage");
   const unsigned gs = grid_for(nd, 256, 148 * 8);
   if (dmat) {
     const int nb = (n + 31) / 32;
-    if (dmf) k_dmat_check<true><<<nb * nb, 256, 0, s>>>(dmat, n, st);
-    else k_dmat_check<false><<<nb * nb, 256, 0, s>>>(dmat, n, st);
-  } else if (dtype == VR_I8) k_stage<int8_t, false><<<gs, 256, 0, s>>>((const int8_t *)dpts, nd, (int32_t *)X, st);
-  else if (dtype == VR_I32) k_stage<int32_t, false><<<gs, 256, 0, s>>>((const int32_t *)dpts, nd, (int32_t *)X, st);
-  else k_stage<float, true><<<gs, 256, 0, s>>>((const float *)dpts, nd, (float *)X, st);
+    if (dmf) launch_dep(k_dmat_check<true>, nb * nb, 256, 0, s, dmat, n, st);
+    else launch_dep(k_dmat_check<false>, nb * nb, 256, 0, s, dmat, n, st);
+  } else if (dtype == VR_I8) {
+    launch_dep(k_stage<int8_t, false>, gs, 256, 0, s, (const int8_t *)dpts, nd, (int32_t *)X, st);
+  } else if (dtype == VR_I32) {
+    launch_dep(k_stage<int32_t, false>, gs, 256, 0, s, (const int32_t *)dpts, nd, (int32_t *)X, st);
+  } else {
+    launch_dep(k_stage<float, true>, gs, 256, 0, s, (const float *)dpts, nd, (float *)X, st);
+  }
   count_launch();
   VR_CUDA(cudaGetLastError());
   prof.end();
@@ -222,8 +298,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   prof.begin("distance");
   const bool tc = !dmat && gram_tc_eligible(dtype, n, d);
   if (dmat) {
-    if (dmf) k_dmat_bitmap<true><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, dm_keep_all, capkey, adj);
-    else k_dmat_bitmap<false><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, dm_keep_all, capkey, adj);
+    if (dmf) launch_dep(k_dmat_bitmap<true>, (n + 7) / 8, 256, 0, s, dmat, n, W, dm_keep_all, capkey, adj);
+    else launch_dep(k_dmat_bitmap<false>, (n + 7) / 8, 256, 0, s, dmat, n, W, dm_keep_all, capkey, adj);
     count_launch();
   } else if (tc) {
     VR_TRY(gram_bitmap_tc(X, n, d, F, cap, adj, st, s, nullptr));  // tensor-core Gram tiles
@@ -234,22 +310,22 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_CUDA(cudaGetLastError());
   prof.end();
   prof.begin("row_counts");
-  k_rows_scan<<<(n + 7) / 8, 256, 0, s>>>(adj, n, W, adjpre, deg, up, nbr_ptr, lex_ptr, st);
+  launch_dep(k_rows_scan, (n + 7) / 8, 256, 0, s, adj, n, W, adjpre, deg, up, nbr_ptr, lex_ptr, st);
   count_launch();
   VR_CUDA(cudaGetLastError());
   prof.end();
 
   // ---- sync 1: kept-edge count and value errors.
-  VR_TRY(read_status(st, hst, s));
+  VR_TRY(read_status(st, sm, s));
   if (tc && (hst->flags & F_OVERFLOW)) {
     // The Gram tiles' near-cap list overflowed (pathological clustering at
     // the cap): rebuild the bitmap exactly on the CUDA cores.
     VR_CUDA(cudaMemsetAsync(&st->flags, 0, sizeof(int32_t), s));
     dist_dispatch<F>(X, n, d, W, cap, adj, st, s);
     count_launch();
-    k_rows_scan<<<(n + 7) / 8, 256, 0, s>>>(adj, n, W, adjpre, deg, up, nbr_ptr, lex_ptr, st);
+    launch_dep(k_rows_scan, (n + 7) / 8, 256, 0, s, adj, n, W, adjpre, deg, up, nbr_ptr, lex_ptr, st);
     count_launch();
-    VR_TRY(read_status(st, hst, s));
+    VR_TRY(read_status(st, sm, s));
   }
   const int64_t E = hst->E;
   if (E > INT32_MAX) {
@@ -258,7 +334,6 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   }
 
   uint64_t *keys;
-  RadixScratch rs{};
   int32_t *gex, *nbr_ord, *gstart;
   int32_t *everts, *egrade, *erow;
   int64_t *ecol, *bs_e;
@@ -269,10 +344,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   out.begin();
   VR_TRY(ws.alloc(&keys, E));
   VR_TRY(ws.alloc(&rs.tkeys, E));
-  VR_TRY(ws.alloc(&rs.meta, rs_meta_bytes(E)));
   VR_TRY(ws.alloc(&gex, E + 1));
-  uint64_t *eg_lb;  // look-back status of the edge-grade tiles + their ticket
-  VR_TRY(ws.alloc(&eg_lb, (E + EG_TILE - 1) / EG_TILE + 1));
   VR_TRY(ws.alloc(&bs_e, scan_tmp_slots(E)));
   VR_TRY(ws.alloc(&nbr_ord, 2 * E));
   int32_t *eidx = nullptr, *egd = nullptr;  // dense (i, j) -> order index / grade tables for small clouds
@@ -333,48 +405,47 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     }
     // The key generator also counts the sort's digit histogram.
     KeyHist ekh;
-    VR_TRY(radix_prepare(E, KEY_SHIFT, kbits, rs, s, &ekh));
+    VR_TRY(radix_prepare(E, KEY_SHIFT, kbits, rs, s, &ekh, true));
     prof.begin("edge_keys");
     if constexpr (F) {
-      k_edge_keys_f32<<<(n + 7) / 8, 256, 0, s>>>((const float *)X, n, d, W, adj, lex_ptr, keys, d64_lex, st,
-                                                   elp, ekh);
+      launch_dep(k_edge_keys_f32, (n + 7) / 8, 256, 0, s, (const float *)X, n, d, W, adj, lex_ptr, keys, d64_lex, st,
+                 elp, ekh);
     } else if (dmat) {
-      if (dmf) k_dmat_keys<true><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, adj, lex_ptr, keys, elp, ekh);
-      else k_dmat_keys<false><<<(n + 7) / 8, 256, 0, s>>>(dmat, n, W, adj, lex_ptr, keys, elp, ekh);
+      if (dmf) launch_dep(k_dmat_keys<true>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, elp, ekh);
+      else launch_dep(k_dmat_keys<false>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, elp, ekh);
     } else {
-      k_edge_keys<F><<<(n + 7) / 8, 256, 0, s>>>(X, n, d, W, adj, lex_ptr, keys, elp, ekh);
+      launch_dep(k_edge_keys<F>, (n + 7) / 8, 256, 0, s, X, n, d, W, adj, lex_ptr, keys, elp, ekh);
     }
     count_launch();
     VR_CUDA(cudaGetLastError());
     prof.end();
     prof.begin("edge_sort");
     static const char *const etag[2] = {"edge_sort.hist", "edge_sort.pass"};
-    VR_TRY(radix_sort(keys, E, KEY_SHIFT, kbits, rs, s, &prof, etag, true));
+    VR_TRY(radix_sort(keys, E, KEY_SHIFT, kbits, rs, s, &prof, etag, RS_PREP_HIST));
     prof.end();
 
     if (F) {
       prof.begin("fp64_repair");
       count_launch(6);
       int tkf = prof.begin("fp64_values");
-      k_f64_gather<<<ge, 256, 0, s>>>(keys, E, d64_lex, adj, adjpre, W, deg, up, lex_ptr, d64, split);
+      launch_dep(k_f64_gather, ge, 256, 0, s, keys, E, d64_lex, adj, adjpre, W, deg, up, lex_ptr, d64, split);
       prof.end(tkf);
       VR_TRY((scan_exclusive<int32_t, int32_t>(split, gex, E, bs_e, s)));
-      k_group_starts<<<ge, 256, 0, s>>>(split, gex, E, gbeg);
+      launch_dep(k_group_starts, ge, 256, 0, s, split, gex, E, gbeg);
       // Group count is gex[E]; launch over the E upper bound, threads skip.
       int tkr = prof.begin("fp64_regroup");
-      k_repair_small<<<ge, 256, 0, s>>>(gbeg, gex + E, keys, d64, midq, bigq, st);
+      launch_dep(k_repair_small, ge, 256, 0, s, gbeg, gex + E, keys, d64, midq, bigq, st);
       VR_CUDA(cudaGetLastError());
-      k_repair_mid<<<296, 256, 0, s>>>(gbeg, midq, st, keys, d64);
-      k_repair_big<<<1, RS_THREADS, 0, s>>>(gbeg, bigq, st, keys, d64, k1, v1, k2, v2, gk, gd);
+      launch_dep(k_repair_mid, 296, 256, 0, s, gbeg, midq, st, keys, d64);
+      launch_dep(k_repair_big, 1, RS_THREADS, 0, s, gbeg, bigq, st, keys, d64, k1, v1, k2, v2, gk, gd);
       VR_CUDA(cudaGetLastError());
       prof.end(tkr);
       prof.end();
     }
     prof.begin("edge_grades");
     const int64_t egt = (E + EG_TILE - 1) / EG_TILE;
-    VR_CUDA(cudaMemsetAsync(eg_lb, 0, sizeof(uint64_t) * (egt + 1), s));
-    k_edge_grades<F><<<(unsigned)egt, 256, 0, s>>>(keys, d64, E, adj, adjpre, W, nbr_ptr, everts, egrade, ecol, erow,
-                                                   gval, gstart, nbr_ord, eidx, egd, n, dmf ? 1 : 0, eg_lb, egt, st);
+    launch_dep(k_edge_grades<F>, (unsigned)egt, 256, 0, s, keys, d64, E, adj, adjpre, W, nbr_ptr, everts, egrade, ecol,
+               erow, gval, gstart, nbr_ord, eidx, egd, n, dmf ? 1 : 0, eg_lb, egt, st);
     count_launch();
     VR_CUDA(cudaGetLastError());
     prof.end();
@@ -389,22 +460,21 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     prof.begin("tri_count");
     const EdgeIndex exc{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
     if (eidx)
-      k_tri_count<true><<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, E, adj, adjpre, W, nbr_ptr, nbr_ord, deg,
-                                                                 up, lex_ptr, st, tcnt, maxdim >= 3 ? 1 : 0, exc);
+      launch_dep(k_tri_count<true>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, E, adj, adjpre, W, nbr_ptr, nbr_ord,
+                 deg, up, lex_ptr, st, tcnt, maxdim >= 3 ? 1 : 0, exc);
     else
-      k_tri_count<false><<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, E, adj, adjpre, W, nbr_ptr, nbr_ord, deg,
-                                                                  up, lex_ptr, st, tcnt, maxdim >= 3 ? 1 : 0, exc);
+      launch_dep(k_tri_count<false>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, E, adj, adjpre, W, nbr_ptr, nbr_ord,
+                 deg, up, lex_ptr, st, tcnt, maxdim >= 3 ? 1 : 0, exc);
     count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int64_t>(tcnt, toff, E, bs_e, s)));
-    VR_CUDA(cudaMemcpyAsync(&st->T, toff + E, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    k_tri_groups<<<grid_for(E + 1, 256), 256, 0, s>>>(gstart, tcnt, toff, tsmallq, tmidq, tbigq, st,
-                                                      maxdim >= 3 ? 1 : 0);
+    launch_dep(k_tri_groups, grid_for(E + 1, 256), 256, 0, s, gstart, tcnt, toff, tsmallq, tmidq, tbigq, st,
+               maxdim >= 3 ? 1 : 0);
     VR_CUDA(cudaGetLastError());
     prof.end();
   }
 
   // ---- sync 2: grade count, triangle count, tie-group sizes.
-  VR_TRY(read_status(st, hst, s));
+  VR_TRY(read_status(st, sm, s));
   const int64_t ngrades = E > 0 ? hst->ngrades : 1;
   const int64_t T = (maxdim >= 2 && E > 0) ? hst->T : 0;
   if (T > INT32_MAX) {
@@ -458,8 +528,11 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(out.commit());
   VR_TRY(ws.commit());
   trs.err = &st->flags;
-  // Vertices (and the triangles' closing colptr entry 3T).
-  k_vertices<<<grid_for(n, 256), 256, 0, s>>>(n, vverts, vgrade, tcol, T);
+  // Vertices (and the triangles' closing colptr entry 3T); the same launch
+  // clears the triangle sort's scratch.
+  const int64_t tz_words = lexm ? rs_meta_bytes(T) / 8 : 0;
+  launch_dep(k_vertices, grid_for(std::max<int64_t>(n, tz_words), 256), 256, 0, s, n, vverts, vgrade, tcol, T,
+             (uint64_t *)trs.meta, tz_words);
   count_launch();
   VR_CUDA(cudaGetLastError());
 
@@ -472,22 +545,23 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       prof.begin("tri_lex_gen");
       const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
       if (eidx)
-        k_lex_tri_gen<true><<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr,
-                                                                     nbr_ord, deg, up, lex_ptr, toff, T, tk, ex, st);
+        launch_dep(k_lex_tri_gen<true>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, egrade, E, adj, adjpre, W, nbr_ptr,
+                   nbr_ord, deg, up, lex_ptr, toff, T, tk, ex, st);
       else
-        k_lex_tri_gen<false><<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr,
-                                                                      nbr_ord, deg, up, lex_ptr, toff, T, tk, ex, st);
+        launch_dep(k_lex_tri_gen<false>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, egrade, E, adj, adjpre, W,
+                   nbr_ptr, nbr_ord, deg, up, lex_ptr, toff, T, tk, ex, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
       if (tets) VR_CUDA(cudaMemcpyAsync(tk_lex, tk, sizeof(uint64_t) * T, cudaMemcpyDeviceToDevice, s));
       prof.end();
       prof.begin("tri_grade_sort");
       static const char *const ttag[2] = {"tri_sort.hist", "tri_sort.pass"};
-      VR_TRY(radix_sort(tk, T, LEX_SHIFT, gbits, trs, s, &prof, ttag));
+      VR_TRY(radix_sort(tk, T, LEX_SHIFT, gbits, trs, s, &prof, ttag, RS_PREP_ZEROED));
       prof.end();
       prof.begin("tri_final");
-      if (eidx) k_tri_final<true><<<grid_for((T + 3) / 4, 256), 256, 0, s>>>(tk, T, ex, tverts, tgrade, tcol, trow);
-      else k_tri_final<false><<<grid_for((T + 3) / 4, 256), 256, 0, s>>>(tk, T, ex, tverts, tgrade, tcol, trow);
+      if (eidx) launch_dep(k_tri_final<true>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, ex, tverts, tgrade, tcol,
+                           trow);
+      else launch_dep(k_tri_final<false>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, ex, tverts, tgrade, tcol, trow);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();
@@ -498,16 +572,16 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       // neighbour lists, while the table's are spread over n^2 entries
       // (measured: 0.58 vs 0.65 ms on 19.8M triangles at n = 4000).
       const EdgeIndex exm{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
-      k_tri_emit<false><<<grid_for(E, 8, 148 * 32), 256, 0, s>>>(everts, egrade, E, adj, adjpre, W, nbr_ptr,
-                                                                 nbr_ord, toff, T, tverts, tgrade, tcol, trow, exm, st);
+      launch_dep(k_tri_emit<false>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, egrade, E, adj, adjpre, W, nbr_ptr,
+                 nbr_ord, toff, T, tverts, tgrade, tcol, trow, exm, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();
       prof.begin("tri_tie_merge");
       if (hst->small_seg_count > 0) {
         const size_t smem = (size_t)TRI_SMALL * (8 + 4 + 12);
-        k_tri_fix_smem<TRI_SMALL><<<std::min(hst->small_seg_count, 148 * 8), 256, smem, s>>>(
-            gstart, toff, tsmallq, &st->small_seg_count, tverts, trow);
+        launch_dep(k_tri_fix_smem<TRI_SMALL>, std::min(hst->small_seg_count, 148 * 8), 256, smem, s, gstart, toff,
+                   tsmallq, &st->small_seg_count, tverts, trow);
         count_launch();
         VR_CUDA(cudaGetLastError());
       }
@@ -515,14 +589,14 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
         const size_t smem = (size_t)TRI_MID * (8 + 4 + 12);
         VR_CUDA(cudaFuncSetAttribute(k_tri_fix_smem<TRI_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-        k_tri_fix_smem<TRI_MID><<<std::min(hst->mid_seg_count, 148), 512, smem, s>>>(
-            gstart, toff, tmidq, &st->mid_seg_count, tverts, trow);
+        launch_dep(k_tri_fix_smem<TRI_MID>, std::min(hst->mid_seg_count, 148), 512, smem, s, gstart, toff, tmidq,
+                   &st->mid_seg_count, tverts, trow);
         count_launch();
         VR_CUDA(cudaGetLastError());
       }
       if (bigfix) {
-        k_tri_fix_big<<<(unsigned)std::min<int64_t>(hst->big_seg_count, 148 * 2), RS_THREADS, 0, s>>>(
-            gstart, toff, tbigq, st, tverts, trow, tk1, tv1, tk2, tv2, rtmp);
+        launch_dep(k_tri_fix_big, (unsigned)std::min<int64_t>(hst->big_seg_count, 148 * 2), RS_THREADS, 0, s, gstart,
+                   toff, tbigq, st, tverts, trow, tk1, tv1, tk2, tv2, rtmp);
         count_launch();
         VR_CUDA(cudaGetLastError());
       }
@@ -538,15 +612,14 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   if (maxdim >= 3) {
     if (tets) {
       prof.begin("tet_count");
-      k_tri_ordidx<<<grid_for(T, 256), 256, 0, s>>>(tk, T, tk_lex, ordidx);
-      k_tet_count<<<grid_for(T, 8, 148 * 32), 256, 0, s>>>(tk_lex, T, adj, W, cnt4);
+      launch_dep(k_tri_ordidx, grid_for(T, 256), 256, 0, s, tk, T, tk_lex, ordidx);
+      launch_dep(k_tet_count, grid_for(T, 8, 148 * 32), 256, 0, s, tk_lex, T, adj, W, cnt4);
       count_launch(2);
       VR_TRY((scan_exclusive<int32_t, int64_t>(cnt4, off4, T, bs_t, s)));
       VR_CUDA(cudaGetLastError());
       prof.end();
       // ---- sync 3: tetrahedron count.
-      VR_CUDA(cudaMemcpyAsync(&hst->T, off4 + T, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-      VR_CUDA(cudaStreamSynchronize(s));
+      VR_TRY(read_status(st, sm, s, off4 + T));
       T4 = hst->T;
       if (T4 > INT32_MAX) {
         set_error("%lld tetrahedra exceed the 2^31-1 limit of one dimension", (long long)T4);
@@ -578,11 +651,11 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       prof.begin("tet_gen");
       const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
       if (eidx)
-        k_tet_gen<true><<<grid_for(T, 8, 148 * 32), 256, 0, s>>>(tk_lex, T, adj, W, tgrade, ordidx, egrade, ex, off4,
-                                                                 T4, keys4, lex4, packed ? 1 : 0, st);
+        launch_dep(k_tet_gen<true>, grid_for(T, 8, 148 * 32), 256, 0, s, tk_lex, T, adj, W, tgrade, ordidx, egrade, ex,
+                   off4, T4, keys4, lex4, packed ? 1 : 0, st);
       else
-        k_tet_gen<false><<<grid_for(T, 8, 148 * 32), 256, 0, s>>>(tk_lex, T, adj, W, tgrade, ordidx, egrade, ex,
-                                                                  off4, T4, keys4, lex4, packed ? 1 : 0, st);
+        launch_dep(k_tet_gen<false>, grid_for(T, 8, 148 * 32), 256, 0, s, tk_lex, T, adj, W, tgrade, ordidx, egrade, ex,
+                   off4, T4, keys4, lex4, packed ? 1 : 0, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();
@@ -590,14 +663,14 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_TRY(radix_sort(keys4, T4, packed ? TET_PACK_SHIFT : 32, qbits, qrs, s));
       prof.end();
       prof.begin("tet_final");
-      k_tet_final<<<grid_for(T4, 256), 256, 0, s>>>(keys4, T4, lex4, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr,
-                                                    ordidx, elp, n, packed ? 1 : 0, qverts, qgrade, qcol, qrow);
+      launch_dep(k_tet_final, grid_for(T4, 256), 256, 0, s, keys4, T4, lex4, tk_lex, toff, adj, adjpre, W, deg, up,
+                 lex_ptr, ordidx, elp, n, packed ? 1 : 0, qverts, qgrade, qcol, qrow);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();
     }
     // Value errors raised by the tetrahedron kernels (internal checks).
-    VR_TRY(read_status(st, hst, s));
+    VR_TRY(read_status(st, sm, s));
   }
 
   // Hand the outputs to the result.

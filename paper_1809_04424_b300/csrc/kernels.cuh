@@ -189,6 +189,7 @@ __device__ __forceinline__ double f32_hi(float a, double crel) { return (double)
 template <typename TIn, bool F>
 __global__ void k_stage(const TIn *in, int64_t count, typename std::conditional<F, float, int32_t>::type *X,
                         DevStatus *st) {
+  pdl_entry();
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
     if constexpr (F) {
       float v = (float)in[t];
@@ -212,6 +213,7 @@ __global__ void k_stage(const TIn *in, int64_t count, typename std::conditional<
 template <bool F, int DR>
 __global__ void __launch_bounds__(256) k_dist_bitmap(const void *Xv, int n, int d, int W, Cap cap, uint32_t *adj,
                                                      DevStatus *st) {
+  pdl_entry();
   using T = typename std::conditional<F, float, int32_t>::type;
   const T *X = (const T *)Xv;
   const int bj = blockIdx.x;
@@ -288,6 +290,7 @@ __global__ void __launch_bounds__(256) k_dist_bitmap(const void *Xv, int n, int 
 static __global__ void __launch_bounds__(256) k_rows_scan(const uint32_t *adj, int n, int W, int32_t *adjpre,
                                                           int32_t *deg, int32_t *up, int32_t *nbr_ptr,
                                                           int64_t *lex_ptr, DevStatus *st) {
+  pdl_entry();
   __shared__ int64_t sh[33];
   __shared__ unsigned int ticket;
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -410,6 +413,7 @@ template <bool F>
 __global__ void __launch_bounds__(256) k_edge_keys(const void *Xv, int n, int d, int W, const uint32_t *adj,
                                                    const int64_t *lex_ptr, uint64_t *keys, int32_t *elp,
                                                    KeyHist kh) {
+  pdl_entry();
   using T = typename std::conditional<F, float, int32_t>::type;
   __shared__ KeyHistSmem hs;
   khist_init(hs, kh);
@@ -458,6 +462,7 @@ __device__ __forceinline__ uint32_t dmat_key(const void *Dv, int64_t idx) {
 // Value checks on 32 x 32 tiles: finite, non-negative, D[i][j] == D[j][i].
 template <bool F>
 static __global__ void __launch_bounds__(256) k_dmat_check(const void *Dv, int n, DevStatus *st) {
+  pdl_entry();
   __shared__ float tf[32][33];
   __shared__ int32_t ti[32][33];
   const int nb = (n + 31) / 32;
@@ -496,6 +501,7 @@ static __global__ void __launch_bounds__(256) k_dmat_check(const void *Dv, int n
 template <bool F>
 static __global__ void __launch_bounds__(256) k_dmat_bitmap(const void *Dv, int n, int W, int keep_all,
                                                             uint32_t capkey, uint32_t *adj) {
+  pdl_entry();
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5), l = lane_id();
   if (i >= n) return;
   for (int w = 0; w < W; ++w) {
@@ -513,6 +519,7 @@ template <bool F>
 static __global__ void __launch_bounds__(256) k_dmat_keys(const void *Dv, int n, int W, const uint32_t *adj,
                                                           const int64_t *lex_ptr, uint64_t *keys, int32_t *elp,
                                                           KeyHist kh) {
+  pdl_entry();
   __shared__ KeyHistSmem hs;
   khist_init(hs, kh);
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -587,6 +594,7 @@ static __global__ void __launch_bounds__(256) k_edge_keys_f32(const float *X, in
                                                               const uint32_t *adj, const int64_t *lex_ptr,
                                                               uint64_t *keys, double *d64_lex, DevStatus *st,
                                                               int32_t *elp, KeyHist kh) {
+  pdl_entry();
   __shared__ float tile[8][32][33];
   __shared__ float rowi[8][32];
   __shared__ KeyHistSmem hs;
@@ -670,6 +678,7 @@ __device__ __forceinline__ int key_j(uint64_t k) { return (int)(k & ID_MASK); }
 static __global__ void k_f64_gather(const uint64_t *keys, int64_t E, const double *d64_lex, const uint32_t *adj,
                                     const int32_t *adjpre, int W, const int32_t *deg, const int32_t *up,
                                     const int64_t *lex_ptr, double *d64, int32_t *split) {
+  pdl_entry();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = keys[k];
     const int i = (int)((key >> ID_BITS) & ID_MASK), j = (int)(key & ID_MASK);
@@ -681,6 +690,7 @@ static __global__ void k_f64_gather(const uint64_t *keys, int64_t E, const doubl
 
 // Group starts from the exclusive scan of split: gbeg[gid] = k.
 static __global__ void k_group_starts(const int32_t *split, const int32_t *gex, int64_t E, int32_t *gbeg) {
+  pdl_entry();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x)
     if (split[k]) gbeg[gex[k]] = (int32_t)k;
   if (blockIdx.x == 0 && threadIdx.x == 0) gbeg[gex[E]] = (int32_t)E;
@@ -697,6 +707,7 @@ constexpr int REPAIR_MID = 2048;
 // groups are queued for the CTA kernels.
 static __global__ void k_repair_small(const int32_t *gbeg, const int32_t *ngroups_ptr, uint64_t *keys, double *d64,
                                int32_t *midq, int32_t *bigq, DevStatus *st) {
+  pdl_entry();
   const int64_t ngroups = *ngroups_ptr;
   int64_t nt = 0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
@@ -734,6 +745,7 @@ static __global__ void k_repair_small(const int32_t *gbeg, const int32_t *ngroup
 // (FP64 bits, i<<13|j) packed as two words; val = position in the group.
 static __global__ void __launch_bounds__(256) k_repair_mid(const int32_t *gbeg, const int32_t *midq, const DevStatus *st,
                                                     uint64_t *keys, double *d64) {
+  pdl_entry();
   __shared__ uint64_t hi[REPAIR_MID];
   __shared__ uint32_t lo[REPAIR_MID];
   __shared__ uint32_t val[REPAIR_MID];
@@ -795,6 +807,7 @@ static __global__ void __launch_bounds__(RS_THREADS) k_repair_big(const int32_t 
                                                            const DevStatus *st, uint64_t *keys, double *d64,
                                                            uint64_t *k1, uint32_t *v1, uint64_t *k2, uint32_t *v2,
                                                            uint64_t *gk, double *gd) {
+  pdl_entry();
   const int nq = (int)st->big_grp_count;
   for (int q = 0; q < nq; ++q) {
     const int g = bigq[q];
@@ -841,6 +854,7 @@ __global__ void __launch_bounds__(256) k_edge_grades(const uint64_t *keys, const
                                                      int64_t *colptr, int32_t *rowidx, double *gval, int32_t *gstart,
                                                      int32_t *nbr_ord, int32_t *eidx, int32_t *egd, int n, int key_f32,
                                                      uint64_t *lb, int64_t ntiles, DevStatus *st) {
+  pdl_entry();
   constexpr int PER = EG_TILE / 256;
   __shared__ int64_t sh[33];
   __shared__ int64_t tile_sh, pre_sh;
@@ -903,12 +917,18 @@ __global__ void __launch_bounds__(256) k_edge_grades(const uint64_t *keys, const
   }
 }
 
-static __global__ void k_vertices(int n, int32_t *verts, int32_t *grade, int64_t *tcol, int64_t T) {
+// Also clears `zero_words` words at `zero` (the triangle sort's scratch), so
+// that no memset sits between the build's dependent launches.
+static __global__ void k_vertices(int n, int32_t *verts, int32_t *grade, int64_t *tcol, int64_t T, uint64_t *zero,
+                                  int64_t zero_words) {
+  pdl_entry();
   if (tcol && blockIdx.x == 0 && threadIdx.x == 0) tcol[T] = 3 * T;  // closing colptr entry of dimension 2
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-    verts[v] = v;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
+    verts[v] = (int32_t)v;
     grade[v] = 0;
   }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < zero_words; i += stride) zero[i] = 0;
 }
 
 // -------------------------------------------------------------- triangles
@@ -975,6 +995,7 @@ static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts,
                                                           const int32_t *up, const int64_t *lex_ptr,
                                                           const DevStatus *st, int32_t *tcnt, int force_lex,
                                                           EdgeIndex ex) {
+  pdl_entry();
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   const bool lexm = lex_mode(E, st->ngrades, force_lex);
@@ -1034,6 +1055,7 @@ static __global__ void __launch_bounds__(256) k_lex_tri_gen(const int32_t *evert
                                                             const int64_t *lex_ptr, const int64_t *toff,
                                                             int64_t T, uint64_t *tkeys, EdgeIndex ex,
                                                             DevStatus *st) {
+  pdl_entry();
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
@@ -1104,6 +1126,7 @@ template <bool DENSE>
 static __global__ void __launch_bounds__(256) k_tri_final(const uint64_t *tkeys, int64_t T, EdgeIndex ex,
                                                           int32_t *tverts, int32_t *tgrade, int64_t *tcolptr,
                                                           int32_t *trow) {
+  pdl_entry();
   const int64_t T4 = T / 4, stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < T4; q += stride) {
     const ulonglong2 k01 = ((const ulonglong2 *)tkeys)[2 * q], k23 = ((const ulonglong2 *)tkeys)[2 * q + 1];
@@ -1148,6 +1171,7 @@ static __global__ void __launch_bounds__(256) k_tri_emit(const int32_t *everts, 
                                                          const int64_t *toff, int64_t T, int32_t *tverts,
                                                          int32_t *tgrade, int64_t *tcolptr, int32_t *trow,
                                                          EdgeIndex ex, DevStatus *st) {
+  pdl_entry();
   const int l = lane_id();
   const uint32_t lt = lanemask_lt();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
@@ -1226,6 +1250,8 @@ constexpr int TRI_MID = 8192;
 
 static __global__ void k_tri_groups(const int32_t *gstart, const int32_t *tcnt, const int64_t *toff, int32_t *smallq,
                                     int32_t *midq, int32_t *bigq, DevStatus *st, int force_lex) {
+  pdl_entry();
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->T = toff[st->E];  // triangle count
   const int64_t ngrades = st->ngrades;
   if (lex_mode(st->E, ngrades, force_lex)) return;  // lex mode needs no merge
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngrades; g += (int64_t)gridDim.x * blockDim.x) {
@@ -1254,6 +1280,7 @@ static __global__ void k_tri_groups(const int32_t *gstart, const int32_t *tcnt, 
 template <int CAP>
 static __global__ void k_tri_fix_smem(const int32_t *gstart, const int64_t *toff, const int32_t *queue,
                                       const int32_t *count, int32_t *tverts, int32_t *trow) {
+  pdl_entry();
   extern __shared__ unsigned char smem[];
   uint64_t *key = (uint64_t *)smem;              // CAP
   uint32_t *val = (uint32_t *)(key + CAP);       // CAP
@@ -1299,6 +1326,7 @@ static __global__ void __launch_bounds__(RS_THREADS) k_tri_fix_big(const int32_t
                                                                    int32_t *tverts, int32_t *trow, uint64_t *k1,
                                                                    uint32_t *v1, uint64_t *k2, uint32_t *v2,
                                                                    int32_t *rtmp) {
+  pdl_entry();
   const int nq = (int)st->big_seg_count;
   for (int q = blockIdx.x; q < nq; q += gridDim.x) {
     const int g = bigq[q];
@@ -1354,6 +1382,7 @@ __device__ __forceinline__ void lex3_unpack(uint64_t k, int &a, int &b, int &c) 
 // triangle p has key (grade, lex3); its lexicographic position is found by
 // bisection in the lexicographic key list.
 static __global__ void k_tri_ordidx(const uint64_t *tk, int64_t T, const uint64_t *tk_lex, int32_t *ordidx) {
+  pdl_entry();
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T; p += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t x = tk[p] & LEX3_MASK;
     int64_t lo = 0, hi = T;
@@ -1369,6 +1398,7 @@ static __global__ void k_tri_ordidx(const uint64_t *tk, int64_t T, const uint64_
 // Tetrahedra per lexicographic triangle (warp per triangle).
 static __global__ void __launch_bounds__(256) k_tet_count(const uint64_t *tk_lex, int64_t T, const uint32_t *adj,
                                                           int W, int32_t *cnt4) {
+  pdl_entry();
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   for (int64_t t = blockIdx.x * 8 + (threadIdx.x >> 5); t < T; t += nwarps) {
@@ -1392,6 +1422,7 @@ static __global__ void __launch_bounds__(256) k_tet_gen(const uint64_t *tk_lex, 
                                                         const int32_t *egrade, EdgeIndex ex, const int64_t *off4,
                                                         int64_t T4, uint64_t *keys4, uint64_t *lex4, int packed,
                                                         DevStatus *st) {
+  pdl_entry();
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   for (int64_t t = blockIdx.x * 8 + (threadIdx.x >> 5); t < T; t += nwarps) {
@@ -1457,6 +1488,7 @@ static __global__ void k_tet_final(const uint64_t *keys4, int64_t T4, const uint
                                    const int32_t *deg, const int32_t *up, const int64_t *lex_ptr,
                                    const int32_t *ordidx, const int32_t *elp, int n, int packed, int32_t *verts,
                                    int32_t *grade, int64_t *colptr, int32_t *rowidx) {
+  pdl_entry();
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T4; p += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = keys4[p];
     const uint64_t v = packed ? key & ((1ull << TET_PACK_SHIFT) - 1) : lex4[key & 0xffffffffull];
