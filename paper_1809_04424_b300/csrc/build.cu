@@ -343,6 +343,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   ws.begin();
   out.begin();
   VR_TRY(ws.alloc(&keys, E));
+  uint32_t *lexe;  // kept edges in lexicographic order, (i << 13) | j
+  VR_TRY(ws.alloc(&lexe, E));
   VR_TRY(ws.alloc(&rs.tkeys, E));
   VR_TRY(ws.alloc(&gex, E + 1));
   VR_TRY(ws.alloc(&bs_e, scan_tmp_slots(E)));
@@ -408,13 +410,13 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_TRY(radix_prepare(E, KEY_SHIFT, kbits, rs, s, &ekh, true));
     prof.begin("edge_keys");
     if constexpr (F) {
-      launch_dep(k_edge_keys_f32, (n + 7) / 8, 256, 0, s, (const float *)X, n, d, W, adj, lex_ptr, keys, d64_lex, st,
-                 elp, ekh);
+      launch_dep(k_edge_keys_f32, (n + 7) / 8, 256, 0, s, (const float *)X, n, d, W, adj, lex_ptr, keys, lexe,
+                 d64_lex, st, elp, ekh);
     } else if (dmat) {
-      if (dmf) launch_dep(k_dmat_keys<true>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, elp, ekh);
-      else launch_dep(k_dmat_keys<false>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, elp, ekh);
+      if (dmf) launch_dep(k_dmat_keys<true>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, lexe, elp, ekh);
+      else launch_dep(k_dmat_keys<false>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, lexe, elp, ekh);
     } else {
-      launch_dep(k_edge_keys<F>, (n + 7) / 8, 256, 0, s, X, n, d, W, adj, lex_ptr, keys, elp, ekh);
+      launch_dep(k_edge_keys<F>, (n + 7) / 8, 256, 0, s, X, n, d, W, adj, lex_ptr, keys, lexe, elp, ekh);
     }
     count_launch();
     VR_CUDA(cudaGetLastError());
@@ -460,11 +462,11 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     prof.begin("tri_count");
     const EdgeIndex exc{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
     if (eidx)
-      launch_dep(k_tri_count<true>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, E, adj, adjpre, W, nbr_ptr, nbr_ord,
-                 deg, up, lex_ptr, st, tcnt, maxdim >= 3 ? 1 : 0, exc);
+      launch_dep(k_tri_count<true>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
+                 nbr_ord, st, tcnt, maxdim >= 3 ? 1 : 0, exc);
     else
-      launch_dep(k_tri_count<false>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, E, adj, adjpre, W, nbr_ptr, nbr_ord,
-                 deg, up, lex_ptr, st, tcnt, maxdim >= 3 ? 1 : 0, exc);
+      launch_dep(k_tri_count<false>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
+                 nbr_ord, st, tcnt, maxdim >= 3 ? 1 : 0, exc);
     count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int64_t>(tcnt, toff, E, bs_e, s)));
     launch_dep(k_tri_groups, grid_for(E + 1, 256), 256, 0, s, gstart, tcnt, toff, tsmallq, tmidq, tbigq, st,
@@ -545,26 +547,40 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       prof.begin("tri_lex_gen");
       const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
       if (eidx)
-        launch_dep(k_lex_tri_gen<true>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, egrade, E, adj, adjpre, W, nbr_ptr,
-                   nbr_ord, deg, up, lex_ptr, toff, T, tk, ex, st);
+        launch_dep(k_lex_tri_gen<true>, grid_for(E, 8, 148 * 32), 256, 0, s, lexe, egrade, E, adj, adjpre, W, nbr_ptr,
+                   nbr_ord, toff, T, tk, ex, st);
       else
-        launch_dep(k_lex_tri_gen<false>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, egrade, E, adj, adjpre, W,
-                   nbr_ptr, nbr_ord, deg, up, lex_ptr, toff, T, tk, ex, st);
+        launch_dep(k_lex_tri_gen<false>, grid_for(E, 8, 148 * 32), 256, 0, s, lexe, egrade, E, adj, adjpre, W, nbr_ptr,
+                   nbr_ord, toff, T, tk, ex, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
       if (tets) VR_CUDA(cudaMemcpyAsync(tk_lex, tk, sizeof(uint64_t) * T, cudaMemcpyDeviceToDevice, s));
       prof.end();
       prof.begin("tri_grade_sort");
-      static const char *const ttag[2] = {"tri_sort.hist", "tri_sort.pass"};
-      VR_TRY(radix_sort(tk, T, LEX_SHIFT, gbits, trs, s, &prof, ttag, RS_PREP_ZEROED));
-      prof.end();
-      prof.begin("tri_final");
-      if (eidx) launch_dep(k_tri_final<true>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, ex, tverts, tgrade, tcol,
-                           trow);
-      else launch_dep(k_tri_final<false>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, ex, tverts, tgrade, tcol, trow);
-      count_launch();
-      VR_CUDA(cudaGetLastError());
-      prof.end();
+      static const char *const ttag[3] = {"tri_sort.hist", "tri_sort.pass", "tri_final"};
+      if (!tets && radix_sort_fuses(T, gbits)) {
+        // The sort's last pass writes the final arrays (the sorted keys are
+        // needed by nothing else).
+        if (eidx) {
+          const TriOut<true> o{ex, tverts, tgrade, trow, tcol};
+          VR_TRY(radix_sort(tk, T, LEX_SHIFT, gbits, trs, s, &prof, ttag, RS_PREP_ZEROED, &o));
+        } else {
+          const TriOut<false> o{ex, tverts, tgrade, trow, tcol};
+          VR_TRY(radix_sort(tk, T, LEX_SHIFT, gbits, trs, s, &prof, ttag, RS_PREP_ZEROED, &o));
+        }
+        prof.end();
+      } else {
+        VR_TRY(radix_sort(tk, T, LEX_SHIFT, gbits, trs, s, &prof, ttag, RS_PREP_ZEROED));
+        prof.end();
+        prof.begin("tri_final");
+        if (eidx)
+          launch_dep(k_tri_final<true>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, ex, tverts, tgrade, tcol, trow);
+        else
+          launch_dep(k_tri_final<false>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, ex, tverts, tgrade, tcol, trow);
+        count_launch();
+        VR_CUDA(cudaGetLastError());
+        prof.end();
+      }
     } else if (T > 0) {
       prof.begin("tri_emit");
       // The emission keeps the neighbour-CSR lookups even with the dense

@@ -411,8 +411,8 @@ __device__ __forceinline__ int32_t bit_rank(const uint32_t *adj_row, const int32
 // position lex_ptr[i] + (rank of j in row i) - (neighbours <= i).
 template <bool F>
 __global__ void __launch_bounds__(256) k_edge_keys(const void *Xv, int n, int d, int W, const uint32_t *adj,
-                                                   const int64_t *lex_ptr, uint64_t *keys, int32_t *elp,
-                                                   KeyHist kh) {
+                                                   const int64_t *lex_ptr, uint64_t *keys, uint32_t *lexe,
+                                                   int32_t *elp, KeyHist kh) {
   pdl_entry();
   using T = typename std::conditional<F, float, int32_t>::type;
   __shared__ KeyHistSmem hs;
@@ -439,6 +439,7 @@ __global__ void __launch_bounds__(256) k_edge_keys(const void *Xv, int n, int d,
         else dk = d2_int(X + (int64_t)i * d, X + (int64_t)j * d, d);
         key = (dk << KEY_SHIFT) | ((uint64_t)i << ID_BITS) | (uint64_t)j;
         keys[t + q] = key;
+        lexe[t + q] = ((uint32_t)i << ID_BITS) | (uint32_t)j;
         if (elp) elp[(int64_t)i * n + j] = (int32_t)(t + q);  // lexicographic position (tetrahedra)
       }
       khist_add(hs, kh, key, q < r.tot);
@@ -517,8 +518,8 @@ static __global__ void __launch_bounds__(256) k_dmat_bitmap(const void *Dv, int 
 // with the matrix entry as the value).
 template <bool F>
 static __global__ void __launch_bounds__(256) k_dmat_keys(const void *Dv, int n, int W, const uint32_t *adj,
-                                                          const int64_t *lex_ptr, uint64_t *keys, int32_t *elp,
-                                                          KeyHist kh) {
+                                                          const int64_t *lex_ptr, uint64_t *keys, uint32_t *lexe,
+                                                          int32_t *elp, KeyHist kh) {
   pdl_entry();
   __shared__ KeyHistSmem hs;
   khist_init(hs, kh);
@@ -541,6 +542,7 @@ static __global__ void __launch_bounds__(256) k_dmat_keys(const void *Dv, int n,
         const uint64_t dk = dmat_key<F>(Dv, (int64_t)i * n + j);
         key = (dk << KEY_SHIFT) | ((uint64_t)i << ID_BITS) | (uint64_t)j;
         keys[t + q] = key;
+        lexe[t + q] = ((uint32_t)i << ID_BITS) | (uint32_t)j;
         if (elp) elp[(int64_t)i * n + j] = (int32_t)(t + q);  // lexicographic position (tetrahedra)
       }
       khist_add(hs, kh, key, q < r.tot);
@@ -592,8 +594,8 @@ __device__ __forceinline__ double soft_value(const SoftAcc &s) {
 
 static __global__ void __launch_bounds__(256) k_edge_keys_f32(const float *X, int n, int d, int W,
                                                               const uint32_t *adj, const int64_t *lex_ptr,
-                                                              uint64_t *keys, double *d64_lex, DevStatus *st,
-                                                              int32_t *elp, KeyHist kh) {
+                                                              uint64_t *keys, uint32_t *lexe, double *d64_lex,
+                                                              DevStatus *st, int32_t *elp, KeyHist kh) {
   pdl_entry();
   __shared__ float tile[8][32][33];
   __shared__ float rowi[8][32];
@@ -641,6 +643,7 @@ static __global__ void __launch_bounds__(256) k_edge_keys_f32(const float *X, in
         key = ((uint64_t)__float_as_uint(__double2float_rn(f)) << KEY_SHIFT) | ((uint64_t)i << ID_BITS) |
               (uint64_t)j;
         keys[t + q] = key;
+        lexe[t + q] = ((uint32_t)i << ID_BITS) | (uint32_t)j;
         if (elp) elp[(int64_t)i * n + j] = (int32_t)(t + q);
         if (f > 0.0) {
           const float ff = (float)f, sf = sqrtf(ff);
@@ -989,10 +992,9 @@ struct EdgeIndex {
 };
 
 template <bool DENSE>
-static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts, int64_t E, const uint32_t *adj,
-                                                          const int32_t *adjpre, int W, const int32_t *nbr_ptr,
-                                                          const int32_t *nbr_ord, const int32_t *deg,
-                                                          const int32_t *up, const int64_t *lex_ptr,
+static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts, const uint32_t *lexe, int64_t E,
+                                                          const uint32_t *adj, const int32_t *adjpre, int W,
+                                                          const int32_t *nbr_ptr, const int32_t *nbr_ord,
                                                           const DevStatus *st, int32_t *tcnt, int force_lex,
                                                           EdgeIndex ex) {
   pdl_entry();
@@ -1000,7 +1002,17 @@ static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts,
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   const bool lexm = lex_mode(E, st->ngrades, force_lex);
   for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
-    const int a = everts[2 * e], b = everts[2 * e + 1];
+    // Lex mode: e runs over the edges in lexicographic order (the count of
+    // edge e lands at e); max-edge mode: in filtration order.
+    int a, b;
+    if (lexm) {
+      const uint32_t ab = lexe[e];
+      a = (int)(ab >> ID_BITS);
+      b = (int)(ab & ID_MASK);
+    } else {
+      a = everts[2 * e];
+      b = everts[2 * e + 1];
+    }
     const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
     int cnt = 0;
     if (lexm) {
@@ -1039,32 +1051,31 @@ static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts,
       }
     }
     if (lexm) cnt = warp_sum(cnt);  // max-edge lanes already hold the warp total
-    if (l == 0) tcnt[lexm ? lex_pos(a, b, adj, adjpre, W, deg, up, lex_ptr) : e] = cnt;
+    if (l == 0) tcnt[e] = cnt;
   }
 }
 
-// Lex-order generation: warp per edge (a, b); its triangles (a, b, c), c > b
-// ascending, land at toff[lex position of (a, b)]; the key carries the
-// triangle's grade (largest of its three edge grades).  Coalesced chunked
-// stores as in k_tri_emit.
+// Lex-order generation: warp per edge (a, b), taken in lexicographic order
+// (lexe); its triangles (a, b, c), c > b ascending, land at toff[e]; the key
+// carries the triangle's grade (largest of its three edge grades).
+// Coalesced chunked stores as in k_tri_emit.
 template <bool DENSE>
-static __global__ void __launch_bounds__(256) k_lex_tri_gen(const int32_t *everts, const int32_t *egrade, int64_t E,
+static __global__ void __launch_bounds__(256) k_lex_tri_gen(const uint32_t *lexe, const int32_t *egrade, int64_t E,
                                                             const uint32_t *adj, const int32_t *adjpre, int W,
                                                             const int32_t *nbr_ptr, const int32_t *nbr_ord,
-                                                            const int32_t *deg, const int32_t *up,
-                                                            const int64_t *lex_ptr, const int64_t *toff,
-                                                            int64_t T, uint64_t *tkeys, EdgeIndex ex,
-                                                            DevStatus *st) {
+                                                            const int64_t *toff, int64_t T, uint64_t *tkeys,
+                                                            EdgeIndex ex, DevStatus *st) {
   pdl_entry();
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
-    const int a = everts[2 * e], b = everts[2 * e + 1];
-    const int32_t gab = egrade[e];
+    const uint32_t ab = lexe[e];
+    const int a = (int)(ab >> ID_BITS), b = (int)(ab & ID_MASK);
+    int64_t t = toff[e];
+    const int32_t gab = ex.grade<DENSE>(a, b);
     const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
     const int32_t *pa = adjpre + (int64_t)a * W, *pb = adjpre + (int64_t)b * W;
     const int32_t *oa = nbr_ord + nbr_ptr[a], *ob = nbr_ord + nbr_ptr[b];
-    int64_t t = toff[lex_pos(a, b, adj, adjpre, W, deg, up, lex_ptr)];
     for (int w0 = (b >> 5); w0 < W; w0 += 32) {
       const int w = w0 + l;
       const uint32_t vm = w < W ? (ra[w] & rb[w] & above_mask(b, w)) : 0u;
@@ -1121,6 +1132,23 @@ __device__ __forceinline__ void tri_final_one(uint64_t k, const EdgeIndex &ex, i
   r[0] = lo; r[1] = o0 + o1 + o2 - lo - hi; r[2] = hi;
   g = (int32_t)(k >> LEX_SHIFT);
 }
+
+// The same write as the last pass of the grade sort: the triangle with key k
+// lands at its sorted position p, so the sorted keys are never stored.
+template <bool DENSE>
+struct TriOut {
+  EdgeIndex ex;
+  int32_t *tverts, *tgrade, *trow;
+  int64_t *tcol;
+  __device__ __forceinline__ void operator()(int64_t p, uint64_t k) const {
+    int32_t v[3], r[3], g;
+    tri_final_one(k, ex, v, r, g, DENSE);
+    tverts[3 * p] = v[0]; tverts[3 * p + 1] = v[1]; tverts[3 * p + 2] = v[2];
+    trow[3 * p] = r[0]; trow[3 * p + 1] = r[1]; trow[3 * p + 2] = r[2];
+    tgrade[p] = g;
+    tcol[p] = 3 * p;
+  }
+};
 
 template <bool DENSE>
 static __global__ void __launch_bounds__(256) k_tri_final(const uint64_t *tkeys, int64_t T, EdgeIndex ex,
