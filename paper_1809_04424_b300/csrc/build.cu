@@ -557,30 +557,17 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       if (tets) VR_CUDA(cudaMemcpyAsync(tk_lex, tk, sizeof(uint64_t) * T, cudaMemcpyDeviceToDevice, s));
       prof.end();
       prof.begin("tri_grade_sort");
-      static const char *const ttag[3] = {"tri_sort.hist", "tri_sort.pass", "tri_final"};
-      if (!tets && radix_sort_fuses(T, gbits)) {
-        // The sort's last pass writes the final arrays (the sorted keys are
-        // needed by nothing else).
-        if (eidx) {
-          const TriOut<true> o{ex, tverts, tgrade, trow, tcol};
-          VR_TRY(radix_sort(tk, T, LEX_SHIFT, gbits, trs, s, &prof, ttag, RS_PREP_ZEROED, &o));
-        } else {
-          const TriOut<false> o{ex, tverts, tgrade, trow, tcol};
-          VR_TRY(radix_sort(tk, T, LEX_SHIFT, gbits, trs, s, &prof, ttag, RS_PREP_ZEROED, &o));
-        }
-        prof.end();
-      } else {
-        VR_TRY(radix_sort(tk, T, LEX_SHIFT, gbits, trs, s, &prof, ttag, RS_PREP_ZEROED));
-        prof.end();
-        prof.begin("tri_final");
-        if (eidx)
-          launch_dep(k_tri_final<true>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, ex, tverts, tgrade, tcol, trow);
-        else
-          launch_dep(k_tri_final<false>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, ex, tverts, tgrade, tcol, trow);
-        count_launch();
-        VR_CUDA(cudaGetLastError());
-        prof.end();
-      }
+      static const char *const ttag[2] = {"tri_sort.hist", "tri_sort.pass"};
+      VR_TRY(radix_sort(tk, T, LEX_SHIFT, gbits, trs, s, &prof, ttag, RS_PREP_ZEROED));
+      prof.end();
+      prof.begin("tri_final");
+      if (eidx)
+        launch_dep(k_tri_final<true>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, ex, tverts, tgrade, tcol, trow);
+      else
+        launch_dep(k_tri_final<false>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, ex, tverts, tgrade, tcol, trow);
+      count_launch();
+      VR_CUDA(cudaGetLastError());
+      prof.end();
     } else if (T > 0) {
       prof.begin("tri_emit");
       // The emission keeps the neighbour-CSR lookups even with the dense

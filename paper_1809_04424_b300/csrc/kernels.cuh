@@ -1133,23 +1133,6 @@ __device__ __forceinline__ void tri_final_one(uint64_t k, const EdgeIndex &ex, i
   g = (int32_t)(k >> LEX_SHIFT);
 }
 
-// The same write as the last pass of the grade sort: the triangle with key k
-// lands at its sorted position p, so the sorted keys are never stored.
-template <bool DENSE>
-struct TriOut {
-  EdgeIndex ex;
-  int32_t *tverts, *tgrade, *trow;
-  int64_t *tcol;
-  __device__ __forceinline__ void operator()(int64_t p, uint64_t k) const {
-    int32_t v[3], r[3], g;
-    tri_final_one(k, ex, v, r, g, DENSE);
-    tverts[3 * p] = v[0]; tverts[3 * p + 1] = v[1]; tverts[3 * p + 2] = v[2];
-    trow[3 * p] = r[0]; trow[3 * p + 1] = r[1]; trow[3 * p + 2] = r[2];
-    tgrade[p] = g;
-    tcol[p] = 3 * p;
-  }
-};
-
 template <bool DENSE>
 static __global__ void __launch_bounds__(256) k_tri_final(const uint64_t *tkeys, int64_t T, EdgeIndex ex,
                                                           int32_t *tverts, int32_t *tgrade, int64_t *tcolptr,

@@ -388,22 +388,13 @@ __device__ __forceinline__ void rs_publish(uint64_t *w, uint32_t tag, uint64_t v
   *(volatile uint64_t *)w = ((uint64_t)tag << 56) | v;
 }
 
-// Output of a digit pass: the key at its sorted position.  A sort's last
-// pass may take another functor with the same call (the key's final
-// position and the key) that writes the caller's outputs instead.
-struct KeyOut {
-  uint64_t *dst;
-  __device__ __forceinline__ void operator()(int64_t pos, uint64_t key) const { dst[pos] = key; }
-};
-
 // One digit pass.  CTAs claim tiles in order (atomic ticket), so every
 // earlier tile belongs to a CTA that is already running; a CTA ranks its tile
 // (stable), publishes its per-digit counts, adds up earlier tiles' counts by
 // looking back until an inclusive count is found (bounded spin: a timeout
 // raises F_TIMEOUT in *err), publishes its own inclusive counts, and writes
 // the keys out digit run by digit run through shared memory.
-template <class Out>
-static __global__ void __launch_bounds__(RS_THREADS, 3) k_rs_onesweep(const uint64_t *src, Out out, int64_t n,
+static __global__ void __launch_bounds__(RS_THREADS, 3) k_rs_onesweep(const uint64_t *src, uint64_t *dst, int64_t n,
                                                                    int shift, uint32_t mask, int pass, const uint32_t *hist,
                                                                    uint64_t *status, uint32_t *ticket,
                                                                    int32_t *err) {
@@ -479,11 +470,10 @@ static __global__ void __launch_bounds__(RS_THREADS, 3) k_rs_onesweep(const uint
     if (idx < c) skey[lpre[digit_of(key[q], shift, mask)] + rank[q]] = key[q];
   }
   __syncthreads();
-#pragma unroll 4
   for (int i = threadIdx.x; i < c; i += RS_THREADS) {
     const uint64_t k = skey[i];
     const uint32_t d = digit_of(k, shift, mask);
-    out(gbase[d] + (i - (int64_t)lpre[d]), k);
+    dst[gbase[d] + (i - (int64_t)lpre[d])] = k;
   }
 }
 
@@ -646,21 +636,11 @@ inline vr_status radix_prepare(int64_t n, int bit_lo, int nbits, const RadixScra
 // the histogram.
 enum RsPrep { RS_PREP_NONE, RS_PREP_ZEROED, RS_PREP_HIST };
 
-// `prof`/`tag`: optional per-kernel timing (tag[0]: histogram, tag[1]: a
-// digit pass, tag[2]: the last pass when `last` is set).
-// `last`: output functor of the last pass (see KeyOut); with it the sorted
-// keys are not stored, and the caller must use the multi-CTA path
-// (n > 2 * RS_TILE, which radix_sort_fuses reports).
-inline bool radix_sort_fuses(int64_t n, int nbits) { return n > 2 * RS_TILE && nbits > 0; }
-template <class Last = KeyOut>
+// `prof`/`tag`: optional per-kernel timing ("<tag>.hist", ".pass").
 inline vr_status radix_sort(uint64_t *keys, int64_t n, int bit_lo, int nbits, const RadixScratch &sc,
                             cudaStream_t s, Prof *prof = nullptr, const char *const *tag = nullptr,
-                            RsPrep prep = RS_PREP_NONE, const Last *last = nullptr) {
+                            RsPrep prep = RS_PREP_NONE) {
   if (n <= 1 || nbits <= 0) return VR_OK;
-  if (last && !radix_sort_fuses(n, nbits)) {
-    set_error("radix_sort: a last-pass output needs the multi-CTA sort");
-    return VR_ERR_INTERNAL;
-  }
   if (n <= 2 * RS_TILE) {
     launch_dep(k_rs_single, 1, RS_THREADS, 0, s, keys, nullptr, sc.tkeys, nullptr, n, bit_lo, nbits);
     count_launch(1);
@@ -683,23 +663,15 @@ inline vr_status radix_sort(uint64_t *keys, int64_t n, int bit_lo, int nbits, co
   }
   uint64_t *src = keys, *dst = sc.tkeys;
   for (int p = 0; p < passes; ++p) {
-    const bool fused = last && p == passes - 1;
-    tk_ = prof ? prof->begin(tag[fused ? 2 : 1]) : -1;
-    const int shift = bit_lo + 8 * p;
-    const uint32_t mask = digit_mask(nbits, p);
-    const uint32_t *hp = hist + p * RS_BINS;
-    if (fused)
-      launch_dep(k_rs_onesweep<Last>, (unsigned)nt, RS_THREADS, 0, s, src, *last, n, shift, mask, p, hp, status,
-                 ticket + p, sc.err);
-    else
-      launch_dep(k_rs_onesweep<KeyOut>, (unsigned)nt, RS_THREADS, 0, s, src, KeyOut{dst}, n, shift, mask, p, hp,
-                 status, ticket + p, sc.err);
+    tk_ = prof ? prof->begin(tag[1]) : -1;
+    launch_dep(k_rs_onesweep, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, bit_lo + 8 * p, digit_mask(nbits, p), p,
+               hist + p * RS_BINS, status, ticket + p, sc.err);
     count_launch(1);
     if (prof) prof->end(tk_);
     VR_CUDA(cudaGetLastError());
     uint64_t *tk = src; src = dst; dst = tk;
   }
-  if (!last && (passes & 1)) VR_CUDA(cudaMemcpyAsync(keys, src, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+  if (passes & 1) VR_CUDA(cudaMemcpyAsync(keys, src, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
   return VR_OK;
 }
 
