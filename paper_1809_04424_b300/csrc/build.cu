@@ -129,13 +129,19 @@ static __global__ void k_publish(const DevStatus *st, const int64_t *t_src, Host
   }
 }
 
-// Sync point: publish the status word and wait for it on the host.  The wait
-// asks the stream for errors every 1024 polls, so a failed kernel ends it.
-static vr_status read_status(const DevStatus *dst, StatusMirror *m, cudaStream_t s, const int64_t *t_src = nullptr) {
-  const uint64_t seq = ++m->next;
-  launch_dep(k_publish, 1, 32, 0, s, dst, t_src, m->d, seq);
+// Sync point, in two halves: publish_status enqueues the copy (work
+// enqueued after it overlaps the host's wait); wait_status polls for it.  The
+// wait asks the stream for errors every 1024 polls, so a failed kernel ends it.
+static vr_status publish_status(const DevStatus *dst, StatusMirror *m, cudaStream_t s,
+                                const int64_t *t_src = nullptr) {
+  launch_dep(k_publish, 1, 32, 0, s, dst, t_src, m->d, ++m->next);
   count_launch();
   VR_CUDA(cudaGetLastError());
+  return VR_OK;
+}
+
+static vr_status wait_status(StatusMirror *m, cudaStream_t s) {
+  const uint64_t seq = m->next;
   const volatile uint64_t *p = &m->h->seq;
   for (uint64_t k = 1; *p != seq; ++k) {
     if ((k & 1023) == 0) {
@@ -152,6 +158,11 @@ static vr_status read_status(const DevStatus *dst, StatusMirror *m, cudaStream_t
   }
   std::atomic_thread_fence(std::memory_order_acquire);
   return flags_to_status(m->h->st.flags);
+}
+
+static vr_status read_status(const DevStatus *dst, StatusMirror *m, cudaStream_t s, const int64_t *t_src = nullptr) {
+  VR_TRY(publish_status(dst, m, s, t_src));
+  return wait_status(m, s);
 }
 
 // fp32 thresholds of the cap test: a_keep = largest float a with
@@ -185,6 +196,12 @@ static void launch_dist(const void *X, int n, int d, int W, const Cap &cap, uint
 bool gram_tc_eligible(vr_dtype dtype, int n, int d);
 vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, uint32_t *adj, DevStatus *st,
                          cudaStream_t s, unsigned int *worst_bits);
+
+// Largest all-pairs count for which the edge keys are generated before the
+// host knows the kept-edge count (the key buffers then hold every pair: at
+// most 1M keys, n <= 1448).  Larger clouds gain nothing from it (their key
+// generation dwarfs the host's wait; measured 1% slower at n = 4000).
+constexpr int64_t EARLY_KEYS_MAX = int64_t(1) << 20;
 
 template <bool F>
 static void dist_dispatch(const void *X, int n, int d, int W, const Cap &cap, uint32_t *adj, DevStatus *st,
@@ -274,8 +291,54 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(ws.alloc(&up, n));
   VR_TRY(ws.alloc(&nbr_ptr, n + 1));
   VR_TRY(ws.alloc(&lex_ptr, n + 1));
+  // Clouds whose every possible edge fits EARLY_KEYS_MAX: the edge-key
+  // buffers are sized for all pairs, so the key generator runs between the
+  // status publish and the host's wait (the GPU works while the host reads
+  // the edge count and allocates).
+  const bool early_keys = E_ub <= EARLY_KEYS_MAX;
+  uint64_t *keys = nullptr;
+  uint32_t *lexe = nullptr;  // kept edges in lexicographic order, (i << 13) | j
+  double *d64_lex = nullptr;
+  int32_t *elp = nullptr;    // dense (i, j) -> lexicographic position (tetrahedra)
+  const bool want_elp = n <= DENSE_MAX_N && maxdim >= 3;
+  if (early_keys) {
+    VR_TRY(ws.alloc(&keys, E_ub));
+    VR_TRY(ws.alloc(&lexe, E_ub));
+    if (F) VR_TRY(ws.alloc(&d64_lex, E_ub));
+    if (want_elp) VR_TRY(ws.alloc(&elp, (int64_t)n * n));
+  }
   VR_TRY(ws.commit());
   VR_CUDA(cudaMemsetAsync(st, 0, (size_t)((char *)(eg_lb + eg_words) - (char *)st), s));
+
+  // Edge keys in (i, j) order: a stable sort on the distance bits alone then
+  // yields (distance, i, j).  The generator also counts the sort's digit
+  // histogram (into rs.meta, cleared above).
+  int kbits;
+  if (F) kbits = 31;
+  else if (dmat) kbits = dm_keep_all ? 31 : std::max(1, bitlen(capkey));
+  else {
+    uint64_t bound = dtype == VR_I8 ? (uint64_t)d * 255ull * 255ull : INT_KEY_LIMIT - 1;
+    if (!cap.keep_all) bound = std::min(bound, cap.r2i);
+    kbits = std::max(1, bitlen(bound));
+  }
+  KeyHist ekh{};
+  auto edge_keys = [&](int64_t ecap) -> vr_status {
+    VR_TRY(radix_prepare(ecap, KEY_SHIFT, kbits, rs, s, &ekh, true));
+    prof.begin("edge_keys");
+    if constexpr (F) {
+      launch_dep(k_edge_keys_f32, (n + 7) / 8, 256, 0, s, (const float *)X, n, d, W, adj, lex_ptr, keys, lexe,
+                 d64_lex, st, elp, ekh);
+    } else if (dmat) {
+      if (dmf) launch_dep(k_dmat_keys<true>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, lexe, elp, ekh);
+      else launch_dep(k_dmat_keys<false>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, lexe, elp, ekh);
+    } else {
+      launch_dep(k_edge_keys<F>, (n + 7) / 8, 256, 0, s, X, n, d, W, adj, lex_ptr, keys, lexe, elp, ekh);
+    }
+    count_launch();
+    VR_CUDA(cudaGetLastError());
+    prof.end();
+    return VR_OK;
+  };
 
   // Stage: convert to the working element type and check values.
   prof.begin("stage");
@@ -316,16 +379,25 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   prof.end();
 
   // ---- sync 1: kept-edge count and value errors.
-  VR_TRY(read_status(st, sm, s));
+  VR_TRY(publish_status(st, sm, s));
+  if (early_keys) VR_TRY(edge_keys(E_ub));
+  VR_TRY(wait_status(sm, s));
   if (tc && (hst->flags & F_OVERFLOW)) {
     // The Gram tiles' near-cap list overflowed (pathological clustering at
-    // the cap): rebuild the bitmap exactly on the CUDA cores.
+    // the cap): rebuild the bitmap exactly on the CUDA cores (and the early
+    // keys, after clearing the histogram they added to; unreachable while
+    // the list holds at least EARLY_KEYS_MAX pairs, kept for safety).
     VR_CUDA(cudaMemsetAsync(&st->flags, 0, sizeof(int32_t), s));
     dist_dispatch<F>(X, n, d, W, cap, adj, st, s);
     count_launch();
     launch_dep(k_rows_scan, (n + 7) / 8, 256, 0, s, adj, n, W, adjpre, deg, up, nbr_ptr, lex_ptr, st);
     count_launch();
-    VR_TRY(read_status(st, sm, s));
+    VR_TRY(publish_status(st, sm, s));
+    if (early_keys) {
+      VR_CUDA(cudaMemsetAsync(rs.meta, 0, (size_t)RS_META_HEAD, s));
+      VR_TRY(edge_keys(E_ub));
+    }
+    VR_TRY(wait_status(sm, s));
   }
   const int64_t E = hst->E;
   if (E > INT32_MAX) {
@@ -333,28 +405,28 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     return VR_ERR_RANGE;
   }
 
-  uint64_t *keys;
   int32_t *gex, *nbr_ord, *gstart;
   int32_t *everts, *egrade, *erow;
   int64_t *ecol, *bs_e;
-  double *gval, *d64 = nullptr, *d64_lex = nullptr;
+  double *gval, *d64 = nullptr;
   // Every E-sized array of the rest of the build: one workspace block and one
   // output block.
   ws.begin();
   out.begin();
-  VR_TRY(ws.alloc(&keys, E));
-  uint32_t *lexe;  // kept edges in lexicographic order, (i << 13) | j
-  VR_TRY(ws.alloc(&lexe, E));
+  if (!early_keys) {
+    VR_TRY(ws.alloc(&keys, E));
+    VR_TRY(ws.alloc(&lexe, E));
+    if (F && E > 0) VR_TRY(ws.alloc(&d64_lex, E));
+    if (want_elp) VR_TRY(ws.alloc(&elp, (int64_t)n * n));
+  }
   VR_TRY(ws.alloc(&rs.tkeys, E));
   VR_TRY(ws.alloc(&gex, E + 1));
   VR_TRY(ws.alloc(&bs_e, scan_tmp_slots(E)));
   VR_TRY(ws.alloc(&nbr_ord, 2 * E));
   int32_t *eidx = nullptr, *egd = nullptr;  // dense (i, j) -> order index / grade tables for small clouds
-  int32_t *elp = nullptr;                    // dense (i, j) -> lexicographic position (tetrahedra)
   if (n <= DENSE_MAX_N && maxdim >= 2) {
     VR_TRY(ws.alloc(&eidx, (int64_t)n * n));
     VR_TRY(ws.alloc(&egd, (int64_t)n * n));
-    if (maxdim >= 3) VR_TRY(ws.alloc(&elp, (int64_t)n * n));
   }
   VR_TRY(ws.alloc(&gstart, E + 2));
   VR_TRY(out.alloc(&everts, 2 * E));
@@ -362,7 +434,6 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(out.alloc(&ecol, E + 1));
   VR_TRY(out.alloc(&erow, 2 * E));
   VR_TRY(out.alloc(&gval, E + 1));
-  if (F && E > 0) VR_TRY(ws.alloc(&d64_lex, E));
   int32_t *split = nullptr, *gbeg = nullptr, *midq = nullptr, *bigq = nullptr;
   uint64_t *k1 = nullptr, *k2 = nullptr, *gk = nullptr;
   uint32_t *v1 = nullptr, *v2 = nullptr;
@@ -395,32 +466,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
 
   const unsigned ge = grid_for(E, 256);
   if (E > 0) {
-    // Keys arrive in (i, j) order, so a stable sort on the distance bits
-    // alone yields (distance, i, j).
-    int kbits;
-    if (F) kbits = 31;
-    else if (dmat) kbits = dm_keep_all ? 31 : std::max(1, bitlen(capkey));
-    else {
-      uint64_t bound = dtype == VR_I8 ? (uint64_t)d * 255ull * 255ull : INT_KEY_LIMIT - 1;
-      if (!cap.keep_all) bound = std::min(bound, cap.r2i);
-      kbits = std::max(1, bitlen(bound));
-    }
-    // The key generator also counts the sort's digit histogram.
-    KeyHist ekh;
-    VR_TRY(radix_prepare(E, KEY_SHIFT, kbits, rs, s, &ekh, true));
-    prof.begin("edge_keys");
-    if constexpr (F) {
-      launch_dep(k_edge_keys_f32, (n + 7) / 8, 256, 0, s, (const float *)X, n, d, W, adj, lex_ptr, keys, lexe,
-                 d64_lex, st, elp, ekh);
-    } else if (dmat) {
-      if (dmf) launch_dep(k_dmat_keys<true>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, lexe, elp, ekh);
-      else launch_dep(k_dmat_keys<false>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, lexe, elp, ekh);
-    } else {
-      launch_dep(k_edge_keys<F>, (n + 7) / 8, 256, 0, s, X, n, d, W, adj, lex_ptr, keys, lexe, elp, ekh);
-    }
-    count_launch();
-    VR_CUDA(cudaGetLastError());
-    prof.end();
+    if (!early_keys) VR_TRY(edge_keys(E));
     prof.begin("edge_sort");
     static const char *const etag[2] = {"edge_sort.hist", "edge_sort.pass"};
     VR_TRY(radix_sort(keys, E, KEY_SHIFT, kbits, rs, s, &prof, etag, RS_PREP_HIST));
