@@ -321,13 +321,17 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     if (!cap.keep_all) bound = std::min(bound, cap.r2i);
     kbits = std::max(1, bitlen(bound));
   }
+  // Float keys: the lexicographic edge list first, then the keys over it (the
+  // sort's histogram then comes from its own pass).
   KeyHist ekh{};
   auto edge_keys = [&](int64_t ecap) -> vr_status {
-    VR_TRY(radix_prepare(ecap, KEY_SHIFT, kbits, rs, s, &ekh, true));
+    if (!F) VR_TRY(radix_prepare(ecap, KEY_SHIFT, kbits, rs, s, &ekh, true));
     prof.begin("edge_keys");
     if constexpr (F) {
-      launch_dep(k_edge_keys_f32, (n + 7) / 8, 256, 0, s, (const float *)X, n, d, W, adj, lex_ptr, keys, lexe,
-                 d64_lex, st, elp, ekh);
+      launch_dep(k_lex_edges, (n + 7) / 8, 256, 0, s, n, W, adj, lex_ptr, lexe, elp);
+      launch_dep(k_edge_keys_f32, grid_for((ecap + 31) / 32, EKF_WARPS, 148 * 16), EKF_WARPS * 32, 0, s,
+                 (const float *)X, d, lexe, keys, d64_lex, st);
+      count_launch();
     } else if (dmat) {
       if (dmf) launch_dep(k_dmat_keys<true>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, lexe, elp, ekh);
       else launch_dep(k_dmat_keys<false>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, lexe, elp, ekh);
@@ -469,7 +473,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     if (!early_keys) VR_TRY(edge_keys(E));
     prof.begin("edge_sort");
     static const char *const etag[2] = {"edge_sort.hist", "edge_sort.pass"};
-    VR_TRY(radix_sort(keys, E, KEY_SHIFT, kbits, rs, s, &prof, etag, RS_PREP_HIST));
+    VR_TRY(radix_sort(keys, E, KEY_SHIFT, kbits, rs, s, &prof, etag, F ? RS_PREP_ZEROED : RS_PREP_HIST));
     prof.end();
 
     if (F) {

@@ -566,12 +566,6 @@ static __global__ void __launch_bounds__(256) k_dmat_keys(const void *Dv, int n,
   khist_flush(hs, kh);
 }
 
-// Float edge keys, in lexicographic order: warp per row i, 32 candidates per
-// chunk (one per lane).  The chunk's 32 candidate rows are staged through
-// shared memory 32 coordinates at a time with coalesced loads; each lane then
-// walks its row in coordinate order evaluating the canonical FP64 sum (integer
-// emulation, hardware FP64 only on the rare inexact case) and the fp32 first
-// pass for the error statistic.  Key = RN32(FP64 value) bits, i, j.
 struct SoftAcc {
   uint64_t M;
   int E;
@@ -606,22 +600,18 @@ __device__ __forceinline__ double soft_value(const SoftAcc &s) {
   return __longlong_as_double((long long)(((uint64_t)(s.E + 52 + 1023) << 52) | (s.M & ((1ull << 52) - 1))));
 }
 
-static __global__ void __launch_bounds__(256) k_edge_keys_f32(const float *X, int n, int d, int W,
-                                                              const uint32_t *adj, const int64_t *lex_ptr,
-                                                              uint64_t *keys, uint32_t *lexe, double *d64_lex,
-                                                              DevStatus *st, int32_t *elp, KeyHist kh) {
+// Kept edges (i, j), i < j, in lexicographic order: warp per row i, every
+// kept j > i in ascending j at lex_ptr[i] + k (and its position in the dense
+// table elp, when given).
+static __global__ void __launch_bounds__(256) k_lex_edges(int n, int W, const uint32_t *adj, const int64_t *lex_ptr,
+                                                          uint32_t *lexe, int32_t *elp) {
   pdl_entry();
-  __shared__ float tile[8][32][33];
-  __shared__ float rowi[8][32];
-  __shared__ KeyHistSmem hs;
-  khist_init(hs, kh);
-  const int wid = threadIdx.x >> 5;
-  const int i = blockIdx.x * 8 + wid;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int l = lane_id();
+  if (i >= n) return;  // whole warps
   const uint32_t *row = adj + (int64_t)i * W;
-  int64_t t = i < n ? lex_ptr[i] : 0;
-  float worst = 0.f;
-  for (int w0 = (i + 1) >> 5; i < n && w0 < W; w0 += 32) {
+  int64_t t = lex_ptr[i];
+  for (int w0 = (i + 1) >> 5; w0 < W; w0 += 32) {
     const int w = w0 + l;
     const uint32_t word = w < W ? row[w] & above_mask(i, w) : 0u;
     const BitChunk r = bit_round(word);
@@ -630,45 +620,79 @@ static __global__ void __launch_bounds__(256) k_edge_keys_f32(const float *X, in
       const int ow = bit_owner(r, q);
       const uint32_t om = __shfl_sync(0xffffffffu, word, ow);
       const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
-      const bool has = q < r.tot;
-      const int j = has ? (w0 + ow) * 32 + __fns(om, 0, q - oex + 1) : i;
-      SoftAcc acc{0, 0, true};
-      float a = 0.f;
-      for (int k0 = 0; k0 < d; k0 += 32) {
-        const int kn = min(32, d - k0);
-        rowi[wid][l] = l < kn ? X[(int64_t)i * d + k0 + l] : 0.f;
-        for (int rr = 0; rr < 32; ++rr) {
-          const int jr = __shfl_sync(0xffffffffu, j, rr);
-          tile[wid][rr][l] = l < kn ? X[(int64_t)jr * d + k0 + l] : 0.f;
-        }
-        __syncwarp();
-        for (int k = 0; k < kn; ++k) {
-          const float xv = rowi[wid][k], yv = tile[wid][l][k];
-          const float tt = __fsub_rn(xv, yv);
-          a = __fmaf_rn(tt, tt, a);
-          if (acc.ok) soft_step(acc, xv, yv);
-        }
-        __syncwarp();
-      }
-      uint64_t key = 0;
-      if (has) {
-        const double f = acc.ok ? soft_value(acc) : d2_f64(X + (int64_t)i * d, X + (int64_t)j * d, d);
-        d64_lex[t + q] = f;
-        key = ((uint64_t)__float_as_uint(__double2float_rn(f)) << KEY_SHIFT) | ((uint64_t)i << ID_BITS) |
-              (uint64_t)j;
-        keys[t + q] = key;
+      if (q < r.tot) {
+        const int j = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
         lexe[t + q] = ((uint32_t)i << ID_BITS) | (uint32_t)j;
         if (elp) elp[(int64_t)i * n + j] = (int32_t)(t + q);
-        if (f > 0.0) {
-          const float ff = (float)f, sf = sqrtf(ff);
-          worst = fmaxf(worst, fabsf((float)((double)a - f)) / (sf * (sqrtf(a) + sf)));
-        }
       }
-      khist_add(hs, kh, key, has);
     }
     t += r.tot;
   }
-  khist_flush(hs, kh);
+}
+
+// Float edge keys over the lexicographic edge list: warp per 32 consecutive
+// kept edges (lane l takes position 32c + l), so every warp has the same work
+// whatever the rows' degrees (warp per row left the densest rows' warps
+// running long after the rest).  Both endpoints' coordinates are staged
+// through shared memory 32 at a time with coalesced loads, all of a stage's
+// loads in flight; each lane then walks its pair in coordinate order,
+// evaluating the canonical FP64 sum (integer emulation, hardware FP64 only on
+// the rare inexact case) and the fp32 first pass for the error statistic.
+// Key = RN32(FP64 value) bits, i, j.  E comes from the status word (the
+// launch may precede the host's read of it).
+constexpr int EKF_WARPS = 4;
+static __global__ void __launch_bounds__(EKF_WARPS * 32) k_edge_keys_f32(const float *X, int d, const uint32_t *lexe,
+                                                                         uint64_t *keys, double *d64_lex,
+                                                                         DevStatus *st) {
+  pdl_entry();
+  __shared__ float ti[EKF_WARPS][32][33], tj[EKF_WARPS][32][33];
+  const int wid = threadIdx.x >> 5, l = lane_id();
+  const int64_t E = st->E, nch = (E + 31) / 32;
+  float worst = 0.f;
+  for (int64_t c = (int64_t)blockIdx.x * EKF_WARPS + wid; c < nch; c += (int64_t)gridDim.x * EKF_WARPS) {
+    const int64_t t = c * 32 + l;
+    const bool has = t < E;
+    const uint32_t ab = lexe[has ? t : c * 32];  // idle lanes repeat the chunk's first pair
+    const int i = (int)(ab >> ID_BITS), j = (int)(ab & ID_MASK);
+    SoftAcc acc{0, 0, true};
+    float a = 0.f;
+    for (int k0 = 0; k0 < d; k0 += 32) {
+      const int kn = min(32, d - k0);
+      float v[32];
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) {
+        const int jr = __shfl_sync(0xffffffffu, j, rr);
+        v[rr] = l < kn ? __ldg(X + (int64_t)jr * d + k0 + l) : 0.f;
+      }
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) tj[wid][rr][l] = v[rr];
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) {
+        const int ir = __shfl_sync(0xffffffffu, i, rr);
+        v[rr] = l < kn ? __ldg(X + (int64_t)ir * d + k0 + l) : 0.f;
+      }
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) ti[wid][rr][l] = v[rr];
+      __syncwarp();
+      for (int k = 0; k < kn; ++k) {
+        const float xv = ti[wid][l][k], yv = tj[wid][l][k];
+        const float tt = __fsub_rn(xv, yv);
+        a = __fmaf_rn(tt, tt, a);
+        if (acc.ok) soft_step(acc, xv, yv);
+      }
+      __syncwarp();
+    }
+    if (has) {
+      const double f = acc.ok ? soft_value(acc) : d2_f64(X + (int64_t)i * d, X + (int64_t)j * d, d);
+      d64_lex[t] = f;
+      keys[t] = ((uint64_t)__float_as_uint(__double2float_rn(f)) << KEY_SHIFT) | ((uint64_t)i << ID_BITS) |
+                (uint64_t)j;
+      if (f > 0.0) {
+        const float ff = (float)f, sf = sqrtf(ff);
+        worst = fmaxf(worst, fabsf((float)((double)a - f)) / (sf * (sqrtf(a) + sf)));
+      }
+    }
+  }
   worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 16));
   worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 8));
   worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 4));
