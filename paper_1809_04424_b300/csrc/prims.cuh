@@ -637,9 +637,12 @@ inline vr_status radix_prepare(int64_t n, int bit_lo, int nbits, const RadixScra
 enum RsPrep { RS_PREP_NONE, RS_PREP_ZEROED, RS_PREP_HIST };
 
 // `prof`/`tag`: optional per-kernel timing ("<tag>.hist", ".pass").
+// `sorted`: if given, receives the buffer holding the result (keys or
+// sc.tkeys) and an odd pass count costs no copy back into keys.
 inline vr_status radix_sort(uint64_t *keys, int64_t n, int bit_lo, int nbits, const RadixScratch &sc,
                             cudaStream_t s, Prof *prof = nullptr, const char *const *tag = nullptr,
-                            RsPrep prep = RS_PREP_NONE) {
+                            RsPrep prep = RS_PREP_NONE, uint64_t **sorted = nullptr) {
+  if (sorted) *sorted = keys;
   if (n <= 1 || nbits <= 0) return VR_OK;
   if (n <= 2 * RS_TILE) {
     launch_dep(k_rs_single, 1, RS_THREADS, 0, s, keys, nullptr, sc.tkeys, nullptr, n, bit_lo, nbits);
@@ -671,7 +674,8 @@ inline vr_status radix_sort(uint64_t *keys, int64_t n, int bit_lo, int nbits, co
     VR_CUDA(cudaGetLastError());
     uint64_t *tk = src; src = dst; dst = tk;
   }
-  if (passes & 1) VR_CUDA(cudaMemcpyAsync(keys, src, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+  if (sorted) *sorted = src;
+  else if (passes & 1) VR_CUDA(cudaMemcpyAsync(keys, src, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
   return VR_OK;
 }
 
