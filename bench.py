@@ -73,8 +73,11 @@ METRIC = "VR simplices/s"
 #   edge_grades: keys 8 read, flags 4+4, outputs 8+4+8+8, CSR scatter 8 per edge
 
 
-def roofline_bytes(cloud, E, T, T4=0):
+def roofline_bytes(cloud, E, T, T4=0, ngrades=0):
     """Algorithmic bytes of one launch of each single-kernel phase."""
+    # Tetrahedron keys carry the packed vertices when the grades fit 12 bits;
+    # otherwise the final write also reads an 8 B vertex record.
+    tet_read = 8 if (ngrades - 1).bit_length() <= 12 else 16
     n = cloud.n
     Wd = (n + 31) // 32
     return {
@@ -87,7 +90,7 @@ def roofline_bytes(cloud, E, T, T4=0):
         "edge_sort.hist": 8 * E,
         "distance": cloud.points.nbytes + 4 * n * Wd,  # read points, write the bitmap
         "edge_keys": 8 * E,
-        "tet_final": 52 * T4,               # read key 8 + lex 8; write verts 16, grade 4, colptr 8, rowidx 16
+        "tet_final": (tet_read + 36) * T4,  # read key (+ vertex record); write verts 16, grade 4, colptr 8, rowidx 16
     }
 
 
@@ -706,6 +709,7 @@ def main():
     for _ in range(W):
         c = step()
         counts = c.counts()[0]
+        ngrades = c.stats()["ngrades"]
         del c
     torch.cuda.synchronize()
     simplices = sum(counts)
@@ -733,7 +737,7 @@ def main():
     torch.cuda.synchronize()
     L.vr_profile_enable(0)
     phases = read_phases()
-    per_launch_bytes = roofline_bytes(cloud, counts[1], counts[2], counts[3] if len(counts) > 3 else 0)
+    per_launch_bytes = roofline_bytes(cloud, counts[1], counts[2], counts[3] if len(counts) > 3 else 0, ngrades)
     # Regions of one kernel (a sort's digit passes: several launches of the
     # same kernel, each timed).
     single = {k: v for k, v in phases.items() if k in per_launch_bytes
