@@ -1157,8 +1157,7 @@ static __global__ void __launch_bounds__(256) k_lex_tri_gen(const uint32_t *lexe
 
 // Final write of lex-mode triangles, sorted by (grade, a, b, c): verts,
 // grade, colptr and the boundary column (order indices of the three faces,
-// ascending).  Four consecutive triangles per thread, written with 16-byte
-// stores (the output arrays start 16-byte aligned); a scalar tail.
+// ascending).  The output arrays start 16-byte aligned; a scalar tail.
 __device__ __forceinline__ void tri_final_one(uint64_t k, const EdgeIndex &ex, int32_t *v, int32_t *r, int32_t &g,
                                               bool dense) {
   const int a = (int)((k >> (2 * ID_BITS)) & ID_MASK), b = (int)((k >> ID_BITS) & ID_MASK), c = (int)(k & ID_MASK);
@@ -1171,32 +1170,53 @@ __device__ __forceinline__ void tri_final_one(uint64_t k, const EdgeIndex &ex, i
   g = (int32_t)(k >> LEX_SHIFT);
 }
 
+// A warp takes 128 consecutive sorted triangles: lane l the pairs at 2l and
+// 64 + 2l (16-byte key loads, consecutive lanes on consecutive addresses).
+// Grades and colptr go out directly (8- and 16-byte stores, coalesced); the
+// vertices and boundary rows (12 bytes per triangle) are staged in shared
+// memory and written as 16-byte words by consecutive lanes, so every store
+// instruction covers whole sectors (the kernel is bound by L1 sector
+// throughput: the three order lookups per triangle are scattered).
 template <bool DENSE>
 static __global__ void __launch_bounds__(256) k_tri_final(const uint64_t *tkeys, int64_t T, EdgeIndex ex,
                                                           int32_t *tverts, int32_t *tgrade, int64_t *tcolptr,
                                                           int32_t *trow) {
   pdl_entry();
-  const int64_t T4 = T / 4, stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < T4; q += stride) {
-    const ulonglong2 k01 = ((const ulonglong2 *)tkeys)[2 * q], k23 = ((const ulonglong2 *)tkeys)[2 * q + 1];
+  __shared__ int4 sv[8][96], sr[8][96];  // per warp: 128 triangles x 3 ints
+  const int wid = threadIdx.x >> 5, l = lane_id();
+  int32_t *svi = (int32_t *)sv[wid], *sri = (int32_t *)sr[wid];
+  const int64_t nch = T / 128;
+  for (int64_t ch = blockIdx.x * 8 + wid; ch < nch; ch += (int64_t)gridDim.x * 8) {
+    const int64_t base = ch * 128;
+    const ulonglong2 kA = ((const ulonglong2 *)(tkeys + base))[l], kB = ((const ulonglong2 *)(tkeys + base))[32 + l];
     int32_t v[12], r[12], g[4];
-    tri_final_one(k01.x, ex, v, r, g[0], DENSE);
-    tri_final_one(k01.y, ex, v + 3, r + 3, g[1], DENSE);
-    tri_final_one(k23.x, ex, v + 6, r + 6, g[2], DENSE);
-    tri_final_one(k23.y, ex, v + 9, r + 9, g[3], DENSE);
-    int4 *tv = (int4 *)(tverts + 12 * q), *tr = (int4 *)(trow + 12 * q);
-    tv[0] = make_int4(v[0], v[1], v[2], v[3]);
-    tv[1] = make_int4(v[4], v[5], v[6], v[7]);
-    tv[2] = make_int4(v[8], v[9], v[10], v[11]);
-    tr[0] = make_int4(r[0], r[1], r[2], r[3]);
-    tr[1] = make_int4(r[4], r[5], r[6], r[7]);
-    tr[2] = make_int4(r[8], r[9], r[10], r[11]);
-    ((int4 *)tgrade)[q] = make_int4(g[0], g[1], g[2], g[3]);
-    const long long c0 = 12 * q;
-    ((longlong2 *)tcolptr)[2 * q] = make_longlong2(c0, c0 + 3);
-    ((longlong2 *)tcolptr)[2 * q + 1] = make_longlong2(c0 + 6, c0 + 9);
+    tri_final_one(kA.x, ex, v, r, g[0], DENSE);
+    tri_final_one(kA.y, ex, v + 3, r + 3, g[1], DENSE);
+    tri_final_one(kB.x, ex, v + 6, r + 6, g[2], DENSE);
+    tri_final_one(kB.y, ex, v + 9, r + 9, g[3], DENSE);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      svi[6 * l + k] = v[k];
+      sri[6 * l + k] = r[k];
+      svi[192 + 6 * l + k] = v[6 + k];
+      sri[192 + 6 * l + k] = r[6 + k];
+    }
+    ((int2 *)(tgrade + base))[l] = make_int2(g[0], g[1]);
+    ((int2 *)(tgrade + base + 64))[l] = make_int2(g[2], g[3]);
+    const long long c0 = 3 * (base + 2 * l), c1 = c0 + 192;
+    ((longlong2 *)(tcolptr + base))[l] = make_longlong2(c0, c0 + 3);
+    ((longlong2 *)(tcolptr + base + 64))[l] = make_longlong2(c1, c1 + 3);
+    __syncwarp();
+    int4 *gv = (int4 *)(tverts + 3 * base), *gr = (int4 *)(trow + 3 * base);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      gv[32 * k + l] = sv[wid][32 * k + l];
+      gr[32 * k + l] = sr[wid][32 * k + l];
+    }
+    __syncwarp();
   }
-  for (int64_t p = 4 * T4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T; p += stride) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = nch * 128 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T; p += stride) {
     int32_t v[3], r[3], g;
     tri_final_one(tkeys[p], ex, v, r, g, DENSE);
     tverts[3 * p] = v[0]; tverts[3 * p + 1] = v[1]; tverts[3 * p + 2] = v[2];
