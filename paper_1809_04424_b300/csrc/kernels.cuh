@@ -1578,16 +1578,12 @@ static __global__ void k_tet_final(const uint64_t *keys4, int64_t T4, const uint
           r[y] = r[y + 1];
           r[y + 1] = sw;
         }
-    verts[4 * p] = a;
-    verts[4 * p + 1] = b;
-    verts[4 * p + 2] = c;
-    verts[4 * p + 3] = d;
+    // One 16-byte store each (the arrays start 16-byte aligned): consecutive
+    // lanes then cover whole sectors.
+    ((int4 *)verts)[p] = make_int4(a, b, c, d);
     grade[p] = (int32_t)(packed ? key >> TET_PACK_SHIFT : key >> 32);
     colptr[p] = 4 * p;
-    rowidx[4 * p] = r[0];
-    rowidx[4 * p + 1] = r[1];
-    rowidx[4 * p + 2] = r[2];
-    rowidx[4 * p + 3] = r[3];
+    ((int4 *)rowidx)[p] = make_int4(r[0], r[1], r[2], r[3]);
     if (p == T4 - 1) colptr[T4] = 4 * T4;
   }
 }
