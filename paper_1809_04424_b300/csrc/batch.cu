@@ -63,7 +63,7 @@ struct BatchOut {
 // Per-CTA scratch slice layout (bytes from the slice base), sized from the
 // batch's largest E and T.
 struct ScratchLayout {
-  int64_t keys, tkeys, d64lex, d64, flag, gex, nbr_ord, gstart, tcnt, toff, tk, tk2, bytes;
+  int64_t keys, tkeys, d64lex, d64, flag, gex, nbr_ord, nbr_gr, gstart, tcnt, toff, tk, tk2, bytes;
 };
 
 static ScratchLayout scratch_layout(int64_t Emax, int64_t Tmax, bool F) {
@@ -82,6 +82,7 @@ static ScratchLayout scratch_layout(int64_t Emax, int64_t Tmax, bool F) {
   L.flag = take(4 * E1);
   L.gex = take(4 * E1);
   L.nbr_ord = take(8 * E1);
+  L.nbr_gr = take(8 * E1);
   L.gstart = take(4 * E1);
   L.tcnt = take(4 * E1);
   L.toff = take(8 * E1);
@@ -286,6 +287,7 @@ __global__ void __launch_bounds__(BT) k_batch_build(const TIn *pts, int d, Cloud
   double *d64lex = (double *)(base + SL.d64lex), *d64 = (double *)(base + SL.d64);
   int32_t *flag = (int32_t *)(base + SL.flag), *gex = (int32_t *)(base + SL.gex);
   int32_t *nbr_ord = (int32_t *)(base + SL.nbr_ord), *gstart = (int32_t *)(base + SL.gstart);
+  int32_t *nbr_gr = (int32_t *)(base + SL.nbr_gr);  // the CSR's edge grades, beside nbr_ord
   int32_t *tcnt = (int32_t *)(base + SL.tcnt);
   int64_t *toff = (int64_t *)(base + SL.toff);
   uint64_t *tk = (uint64_t *)(base + SL.tk), *tk2 = (uint64_t *)(base + SL.tk2);
@@ -429,8 +431,12 @@ __global__ void __launch_bounds__(BT) k_batch_build(const TIn *pts, int d, Cloud
         out.gval[c.go + g] = v;
         gstart[g] = (int32_t)k;
       }
-      nbr_ord[nptr[i] + rank16(adj + i * W, pre + i * W, j)] = (int32_t)k;
-      nbr_ord[nptr[j] + rank16(adj + j * W, pre + j * W, i)] = (int32_t)k;
+      const int32_t si = nptr[i] + rank16(adj + i * W, pre + i * W, j);
+      const int32_t sj = nptr[j] + rank16(adj + j * W, pre + j * W, i);
+      nbr_ord[si] = (int32_t)k;
+      nbr_ord[sj] = (int32_t)k;
+      nbr_gr[si] = g;
+      nbr_gr[sj] = g;
       if (k == E - 1) ngr = g + 1;
     }
     if (threadIdx.x == 0) {
@@ -447,13 +453,29 @@ __global__ void __launch_bounds__(BT) k_batch_build(const TIn *pts, int d, Cloud
     const int64_t T = c.T;
     if (c.maxdim >= 2) {
       if (threadIdx.x == 0) out.tcol[c.ko + T] = 3 * T;
-      // Lex counts: triangle (a, b, c'), a < b < c', counted at its first edge.
-      for (int64_t e = wid; e < E; e += BWARPS) {
-        const int a = out.everts[2 * (c.eo + e)], b = out.everts[2 * (c.eo + e) + 1];
-        int cnt = 0;
-        for (int w = (b >> 5) + l; w < W; w += 32) cnt += __popc(adj[a * W + w] & adj[b * W + w] & above_mask(b, w));
-        cnt = warp_sum(cnt);
-        if (l == 0) tcnt[lptr[a] + rank16(adj + a * W, pre + a * W, b) - (deg[a] - up[a])] = cnt;
+      // Lex counts: triangle (a, b, c'), a < b < c', counted at its first
+      // edge.  Warp per row a, lane per kept b > a (lexicographic position
+      // lptr[a] + rank), all from the shared-memory bitmap.
+      for (int a = wid; a < n; a += BWARPS) {
+        int64_t e = lptr[a];
+        for (int w0 = (a + 1) >> 5; w0 < W; w0 += 32) {
+          const int w = w0 + l;
+          const uint32_t word = w < W ? adj[a * W + w] & above_mask(a, w) : 0u;
+          const BitChunk r = bit_round(word);
+          for (int q0 = 0; q0 < r.tot; q0 += 32) {
+            const int q = q0 + l;
+            const int ow = bit_owner(r, q);
+            const uint32_t om = __shfl_sync(0xffffffffu, word, ow);
+            const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
+            if (q < r.tot) {
+              const int b = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
+              int cnt = 0;
+              for (int x = b >> 5; x < W; ++x) cnt += __popc(adj[a * W + x] & adj[b * W + x] & above_mask(b, x));
+              tcnt[e + q] = cnt;
+            }
+          }
+          e += r.tot;
+        }
       }
       __syncthreads();
       cta_scan<int32_t, int64_t>(tcnt, toff, E);
@@ -461,29 +483,42 @@ __global__ void __launch_bounds__(BT) k_batch_build(const TIn *pts, int d, Cloud
         if (threadIdx.x == 0) c.flags |= F_INTERNAL;
         continue;
       }
-      // Keys grade << 39 | (a, b, c').
-      for (int64_t e = wid; e < E; e += BWARPS) {
-        const int a = out.everts[2 * (c.eo + e)], b = out.everts[2 * (c.eo + e) + 1];
-        const int32_t gab = out.egrade[c.eo + e];
-        const int32_t *oa = nbr_ord + nptr[a], *ob = nbr_ord + nptr[b];
-        int64_t t = toff[lptr[a] + rank16(adj + a * W, pre + a * W, b) - (deg[a] - up[a])];
-        for (int w0 = b >> 5; w0 < W; w0 += 32) {
+      // Keys grade << 39 | (a, b, c'): warp per row a, lane per kept b > a
+      // (lexicographic position lptr[a] + rank); each lane walks its edge's
+      // triangles (c' ascending) itself, the two other grades read from the
+      // CSR's grade copy, so the lanes' loads overlap instead of one edge's
+      // few triangles holding the whole warp.
+      for (int a = wid; a < n; a += BWARPS) {
+        const int32_t *ga = nbr_gr + nptr[a];
+        int64_t e = lptr[a];
+        for (int w0 = (a + 1) >> 5; w0 < W; w0 += 32) {
           const int w = w0 + l;
-          const uint32_t vm = w < W ? (adj[a * W + w] & adj[b * W + w] & above_mask(b, w)) : 0u;
-          const BitChunk r = bit_round(vm);
+          const uint32_t word = w < W ? adj[a * W + w] & above_mask(a, w) : 0u;
+          const BitChunk r = bit_round(word);
           for (int q0 = 0; q0 < r.tot; q0 += 32) {
             const int q = q0 + l;
             const int ow = bit_owner(r, q);
-            const uint32_t om = __shfl_sync(0xffffffffu, vm, ow);
+            const uint32_t om = __shfl_sync(0xffffffffu, word, ow);
             const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
             if (q < r.tot) {
-              const int cv = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
-              const int32_t gac = out.egrade[c.eo + oa[rank16(adj + a * W, pre + a * W, cv)]];
-              const int32_t gbc = out.egrade[c.eo + ob[rank16(adj + b * W, pre + b * W, cv)]];
-              if (t + q < T) tk[t + q] = ((uint64_t)max(gab, max(gac, gbc)) << LEX_SHIFT) | lex3(a, b, cv);
+              const int b = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
+              const int32_t gab = ga[rank16(adj + a * W, pre + a * W, b)];
+              const int32_t *gb = nbr_gr + nptr[b];
+              int64_t t = toff[e + q];
+              for (int x = b >> 5; x < W; ++x) {
+                uint32_t m = adj[a * W + x] & adj[b * W + x] & above_mask(b, x);
+                while (m) {
+                  const int cv = x * 32 + __ffs(m) - 1;
+                  m &= m - 1;
+                  const int32_t gac = ga[rank16(adj + a * W, pre + a * W, cv)];
+                  const int32_t gbc = gb[rank16(adj + b * W, pre + b * W, cv)];
+                  if (t < T) tk[t] = ((uint64_t)max(gab, max(gac, gbc)) << LEX_SHIFT) | lex3(a, b, cv);
+                  ++t;
+                }
+              }
             }
           }
-          t += r.tot;
+          e += r.tot;
         }
       }
       __syncthreads();
