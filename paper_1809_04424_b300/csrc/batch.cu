@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "complex.h"
@@ -145,8 +146,11 @@ __device__ __forceinline__ int32_t rank16(const uint32_t *row, const uint16_t *p
 }
 
 // Stage points, bitmap (warp per 32x32 block of the upper triangle, ballot
-// rows, lane-accumulated mirrored columns), all in shared memory.
-template <bool F>
+// rows, lane-accumulated mirrored columns), all in shared memory.  I8 (int8
+// source, d <= 4): the lane's column point sits in registers, the block's
+// row points are broadcast by shuffles and the distance is 32-bit integer
+// arithmetic (d^2 <= 4 * 255^2, far below the key limit).
+template <bool F, bool I8 = false>
 __device__ void cta_bitmap(const void *pts, const CloudDesc &c, int d, void *Xs, uint32_t *adj, int32_t *flags) {
   using T = typename std::conditional<F, float, int32_t>::type;
   const int n = c.n, W = (n + 31) / 32;
@@ -170,10 +174,29 @@ __device__ void cta_bitmap(const void *pts, const CloudDesc &c, int d, void *Xs,
     uint32_t myrow = 0, mycol = 0;
     bool over = false;
     const int rows = min(32, n - bi * 32);
+    constexpr int DR = I8 ? 4 : 1;
+    T xj[DR], xr[DR];
+    if constexpr (I8) {
+      const int ir = bi * 32 + l;
+#pragma unroll
+      for (int k = 0; k < DR; ++k) {
+        xj[k] = (jv && k < d) ? X[j * d + k] : T(0);
+        xr[k] = (ir < n && k < d) ? X[ir * d + k] : T(0);
+      }
+    }
     for (int r = 0; r < rows; ++r) {
       const int i = bi * 32 + r;
       bool kept = false;
-      if (jv && j != i) {
+      if constexpr (I8 && !F) {
+        // All lanes shuffle (the row point of lane r), then decide.
+        int32_t v = 0;
+#pragma unroll
+        for (int k = 0; k < DR; ++k) {
+          const int32_t t = __shfl_sync(0xffffffffu, (int32_t)xr[k], r) - (int32_t)xj[k];
+          v += t * t;
+        }
+        if (jv && j != i) kept = c.keep_all || (uint64_t)v <= c.r2i;
+      } else if (jv && j != i) {
         if constexpr (F) {
           const float a = d2_f32(X + i * d, X + j * d, d);
           if (c.keep_all || a <= c.a_keep) kept = true;
@@ -229,7 +252,12 @@ __global__ void __launch_bounds__(BT) k_batch_size(const TIn *pts, int d, CloudD
     if (threadIdx.x == 0) flags = 0;
     __syncthreads();
     if constexpr (!F) cta_stage_int<TIn>(pts, c, d, (int32_t *)Xs);
-    cta_bitmap<F>(pts, c, d, Xs, adj, &flags);
+    if constexpr (std::is_same<TIn, int8_t>::value) {
+      if (d <= 4) cta_bitmap<F, true>(pts, c, d, Xs, adj, &flags);
+      else cta_bitmap<F>(pts, c, d, Xs, adj, &flags);
+    } else {
+      cta_bitmap<F>(pts, c, d, Xs, adj, &flags);
+    }
     const int n = c.n, W = (n + 31) / 32;
     const int wid = threadIdx.x >> 5, l = lane_id();
     // E: upper-triangle bits; 3T: sum over edges (a < b) of |N(a) & N(b)|.
@@ -304,7 +332,12 @@ __global__ void __launch_bounds__(BT) k_batch_build(const TIn *pts, int d, Cloud
     __syncthreads();
     const int n = c.n, W = (n + 31) / 32;
     if constexpr (!F) cta_stage_int<TIn>(pts, c, d, (int32_t *)Xs);
-    cta_bitmap<F>(pts, c, d, Xs, adj, &flags);
+    if constexpr (std::is_same<TIn, int8_t>::value) {
+      if (d <= 4) cta_bitmap<F, true>(pts, c, d, Xs, adj, &flags);
+      else cta_bitmap<F>(pts, c, d, Xs, adj, &flags);
+    } else {
+      cta_bitmap<F>(pts, c, d, Xs, adj, &flags);
+    }
     using TX = typename std::conditional<F, float, int32_t>::type;
     const TX *X = (const TX *)Xs;
 
