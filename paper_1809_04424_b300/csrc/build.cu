@@ -197,6 +197,11 @@ bool gram_tc_eligible(vr_dtype dtype, int n, int d);
 vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, uint32_t *adj, DevStatus *st,
                          cudaStream_t s, unsigned int *worst_bits);
 
+// Largest kept-edge count for which the lexicographic triangle keys are
+// generated before the host knows T (their buffer then holds the bound
+// (sqrt 2 / 3) E^(3/2): at most 22M keys).
+constexpr int64_t EARLY_TRI_MAX_E = int64_t(1) << 17;
+
 // Largest all-pairs count for which the edge keys are generated before the
 // host knows the kept-edge count (the key buffers then hold every pair: at
 // most 1M keys, n <= 1448).  Larger clouds gain nothing from it (their key
@@ -457,6 +462,14 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   }
   int32_t *tcnt = nullptr, *tsmallq = nullptr, *tmidq = nullptr, *tbigq = nullptr;
   int64_t *toff = nullptr;
+  // Small complexes (maxdim 2, E <= EARLY_TRI_MAX_E): the lexicographic
+  // triangle keys get a buffer sized by the bound on the triangles of a graph
+  // with E edges, T <= (sqrt 2 / 3) E^(3/2), so the generator can be enqueued
+  // before the host reads T (it returns at once in max-edge mode).
+  const bool early_tri = maxdim == 2 && E > 0 && E <= EARLY_TRI_MAX_E;
+  const int64_t T_cap = early_tri ? (int64_t)std::ceil(std::sqrt(2.0) / 3.0 * std::pow((double)E, 1.5)) + 1 : 0;
+  uint64_t *tk = nullptr;
+  if (early_tri) VR_TRY(ws.alloc(&tk, T_cap));
   if (maxdim >= 2 && E > 0) {
     VR_TRY(ws.alloc(&tcnt, E));
     VR_TRY(ws.alloc(&toff, E + 1));
@@ -533,7 +546,23 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   }
 
   // ---- sync 2: grade count, triangle count, tie-group sizes.
-  VR_TRY(read_status(st, sm, s));
+  VR_TRY(publish_status(st, sm, s));
+  auto lex_tri_gen = [&](int64_t tcap) -> vr_status {
+    prof.begin("tri_lex_gen");
+    const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
+    if (eidx)
+      launch_dep(k_lex_tri_gen<true>, grid_for(E, 8, 148 * 32), 256, 0, s, lexe, egrade, E, adj, adjpre, W, nbr_ptr,
+                 nbr_ord, toff, tcap, tk, ex, st, force_lex);
+    else
+      launch_dep(k_lex_tri_gen<false>, grid_for(E, 8, 148 * 32), 256, 0, s, lexe, egrade, E, adj, adjpre, W, nbr_ptr,
+                 nbr_ord, toff, tcap, tk, ex, st, force_lex);
+    count_launch();
+    VR_CUDA(cudaGetLastError());
+    prof.end();
+    return VR_OK;
+  };
+  if (early_tri) VR_TRY(lex_tri_gen(T_cap));
+  VR_TRY(wait_status(sm, s));
   const int64_t ngrades = E > 0 ? hst->ngrades : 1;
   const int64_t T = (maxdim >= 2 && E > 0) ? hst->T : 0;
   if (T > INT32_MAX) {
@@ -548,7 +577,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   int32_t *vverts, *vgrade;
   int32_t *tverts = nullptr, *tgrade = nullptr, *trow = nullptr;
   int64_t *tcol = nullptr;
-  uint64_t *tk = nullptr, *tk1 = nullptr, *tk2 = nullptr;
+  uint64_t *tk1 = nullptr, *tk2 = nullptr;
   uint32_t *tv1 = nullptr, *tv2 = nullptr;
   int32_t *rtmp = nullptr;
   RadixScratch trs{};
@@ -566,7 +595,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   int32_t *ordidx = nullptr, *cnt4 = nullptr;
   int64_t *off4 = nullptr, *bs_t = nullptr;
   if (lexm) {
-    VR_TRY(ws.alloc(&tk, T));
+    if (!early_tri) VR_TRY(ws.alloc(&tk, T));
     VR_TRY(ws.alloc(&trs.tkeys, T));
     VR_TRY(ws.alloc(&trs.meta, rs_meta_bytes(T)));
   }
@@ -601,18 +630,9 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       const int gbits = std::max(1, bitlen((uint64_t)(ngrades - 1)));
       // (The triangle generator is latency-bound: counting the sort's
       // histogram inside it cost more than the sort's own histogram pass.)
-      prof.begin("tri_lex_gen");
+      if (!early_tri) VR_TRY(lex_tri_gen(T));
       const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
-      if (eidx)
-        launch_dep(k_lex_tri_gen<true>, grid_for(E, 8, 148 * 32), 256, 0, s, lexe, egrade, E, adj, adjpre, W, nbr_ptr,
-                   nbr_ord, toff, T, tk, ex, st);
-      else
-        launch_dep(k_lex_tri_gen<false>, grid_for(E, 8, 148 * 32), 256, 0, s, lexe, egrade, E, adj, adjpre, W, nbr_ptr,
-                   nbr_ord, toff, T, tk, ex, st);
-      count_launch();
-      VR_CUDA(cudaGetLastError());
       if (tets) VR_CUDA(cudaMemcpyAsync(tk_lex, tk, sizeof(uint64_t) * T, cudaMemcpyDeviceToDevice, s));
-      prof.end();
       prof.begin("tri_grade_sort");
       static const char *const ttag[2] = {"tri_sort.hist", "tri_sort.pass"};
       uint64_t *tks = tk;  // the sorted keys: tk or the sort's other buffer

@@ -1096,14 +1096,16 @@ static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts,
 // Lex-order generation: warp per edge (a, b), taken in lexicographic order
 // (lexe); its triangles (a, b, c), c > b ascending, land at toff[e]; the key
 // carries the triangle's grade (largest of its three edge grades).
-// Coalesced chunked stores as in k_tri_emit.
+// Coalesced chunked stores as in k_tri_emit.  T: the key buffer's capacity
+// (at least the triangle count).
 template <bool DENSE>
 static __global__ void __launch_bounds__(256) k_lex_tri_gen(const uint32_t *lexe, const int32_t *egrade, int64_t E,
                                                             const uint32_t *adj, const int32_t *adjpre, int W,
                                                             const int32_t *nbr_ptr, const int32_t *nbr_ord,
                                                             const int64_t *toff, int64_t T, uint64_t *tkeys,
-                                                            EdgeIndex ex, DevStatus *st) {
+                                                            EdgeIndex ex, DevStatus *st, int force_lex) {
   pdl_entry();
+  if (!lex_mode(E, st->ngrades, force_lex)) return;  // max-edge order (a launch ahead of the host's decision)
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
