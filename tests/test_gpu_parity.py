@@ -153,6 +153,16 @@ def test_dense_edge_table_boundary(torch, n):
     assert len(c[2]["grade"]) > 10000
 
 
+def test_lex_mode_beyond_early_triangle_limit(torch):
+    """Tie-heavy integer cloud with about 199k kept edges (more than 2^17) and
+    8.8M triangles: lex order with the triangle keys allocated after the
+    triangle count is read (not from the all-graphs bound), in full."""
+    g = synth.rng(1800)
+    pts = g.integers(-12, 13, size=(1800, 3)).astype(np.int8)
+    c = check(torch, pts, 2, 9.0)
+    assert len(c[1]["grade"]) > (1 << 17)
+
+
 def test_worldmap_shaped_cloud(torch):
     """The WorldMap-shaped single cloud (n = 7322 float32 on the unit sphere,
     cap 0.15): 280,777 edges and 5,878,554 triangles, in full."""

@@ -1,0 +1,54 @@
+"""Host-side sizing rules of the build, checked on CPU.
+
+The build sizes the lexicographic triangle-key buffer of small complexes
+before it knows the triangle count, from the bound on the number of triangles
+of a graph with E edges, T <= (sqrt 2 / 3) E^(3/2) (a consequence of the
+Kruskal-Katona theorem; complete graphs approach it).  These tests check the
+capacity formula the build uses against exact triangle counts."""
+import math
+
+import numpy as np
+import pytest
+
+
+def capacity(E):
+    """The build's buffer capacity for E kept edges."""
+    return math.ceil(math.sqrt(2.0) / 3.0 * E ** 1.5) + 1
+
+
+def triangles(adj):
+    a = adj.astype(np.int64)
+    return int(np.trace(a @ a @ a)) // 6
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 10, 40, 120])
+def test_complete_graphs(n):
+    adj = np.ones((n, n), dtype=np.int64) - np.eye(n, dtype=np.int64)
+    E = n * (n - 1) // 2
+    T = n * (n - 1) * (n - 2) // 6
+    assert triangles(adj) == T
+    assert T <= capacity(E)
+    # the bound is tight up to lower-order terms
+    assert T >= 0.7 * (math.sqrt(2.0) / 3.0) * E ** 1.5 or n < 10
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_and_clustered_graphs(seed):
+    g = np.random.default_rng(seed)
+    n = int(g.integers(20, 200))
+    p = float(g.uniform(0.05, 0.9))
+    m = g.random((n, n)) < p
+    adj = np.triu(m, 1)
+    # a dense block (clique) inside makes the count lopsided
+    k = int(g.integers(3, n // 2))
+    adj[:k, :k] = True
+    adj = np.triu(adj, 1)
+    adj = (adj | adj.T).astype(np.int64)
+    E = int(adj.sum()) // 2
+    assert triangles(adj) <= capacity(E)
+
+
+def test_small_cases():
+    assert capacity(0) == 1
+    assert capacity(1) >= 1
+    assert capacity(3) >= 1  # one triangle
