@@ -190,7 +190,7 @@ static void launch_dist(const void *X, int n, int d, int W, const Cap &cap, uint
                         cudaStream_t s) {
   const int B = (n + 31) / 32;
   dim3 grid(B, (B + 7) / 8);
-  launch_dep(k_dist_bitmap<F, DR>, grid, 256, 0, s, X, n, d, W, cap, adj, st);
+  launch_dep(k_dist_bitmap<F, DR>, grid, 256, 0, s, X, n, d, W, cap, adj, st, (int32_t *)nullptr);
 }
 
 bool gram_tc_eligible(vr_dtype dtype, int n, int d);
@@ -289,7 +289,10 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(ws.alloc(&st, 1));
   VR_TRY(ws.alloc(&rs.meta, rs_meta_bytes(E_ub)));
   VR_TRY(ws.alloc(&eg_lb, eg_words));
-  VR_TRY(F ? ws.alloc((float **)&X, nd) : ws.alloc((int32_t **)&X, nd));
+  // Staged points: int32 input is used in place (the build only reads it
+  // before it returns); int8 and float are converted (and floats checked).
+  const bool in_place = !dmat && dtype == VR_I32;
+  if (!in_place) VR_TRY(F ? ws.alloc((float **)&X, nd) : ws.alloc((int32_t **)&X, nd));
   VR_TRY(ws.alloc(&adj, (int64_t)n * W));
   VR_TRY(ws.alloc(&adjpre, (int64_t)n * W));
   VR_TRY(ws.alloc(&deg, n));
@@ -349,32 +352,41 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     return VR_OK;
   };
 
-  // Stage: convert to the working element type and check values.
+  // Stage: convert to the working element type and check values (int8
+  // with d <= 4 on the CUDA-core path: the distance kernel stages as it
+  // loads; int32: in place).
+  const bool tc = !dmat && gram_tc_eligible(dtype, n, d);
+  const bool fused8 = !dmat && !tc && dtype == VR_I8 && d <= 4;
+  if (in_place) X = (void *)dpts;
   prof.begin("stage");
   const unsigned gs = grid_for(nd, 256, 148 * 8);
   if (dmat) {
     const int nb = (n + 31) / 32;
     if (dmf) launch_dep(k_dmat_check<true>, nb * nb, 256, 0, s, dmat, n, st);
     else launch_dep(k_dmat_check<false>, nb * nb, 256, 0, s, dmat, n, st);
-  } else if (dtype == VR_I8) {
+    count_launch();
+  } else if (dtype == VR_I8 && !fused8) {
     launch_dep(k_stage<int8_t, false>, gs, 256, 0, s, (const int8_t *)dpts, nd, (int32_t *)X, st);
-  } else if (dtype == VR_I32) {
-    launch_dep(k_stage<int32_t, false>, gs, 256, 0, s, (const int32_t *)dpts, nd, (int32_t *)X, st);
-  } else {
+    count_launch();
+  } else if (F) {
     launch_dep(k_stage<float, true>, gs, 256, 0, s, (const float *)dpts, nd, (float *)X, st);
+    count_launch();
   }
-  count_launch();
   VR_CUDA(cudaGetLastError());
   prof.end();
 
   prof.begin("distance");
-  const bool tc = !dmat && gram_tc_eligible(dtype, n, d);
   if (dmat) {
     if (dmf) launch_dep(k_dmat_bitmap<true>, (n + 7) / 8, 256, 0, s, dmat, n, W, dm_keep_all, capkey, adj);
     else launch_dep(k_dmat_bitmap<false>, (n + 7) / 8, 256, 0, s, dmat, n, W, dm_keep_all, capkey, adj);
     count_launch();
   } else if (tc) {
     VR_TRY(gram_bitmap_tc(X, n, d, F, cap, adj, st, s, nullptr));  // tensor-core Gram tiles
+  } else if (fused8) {
+    const int B = (n + 31) / 32;
+    launch_dep(k_dist_bitmap<false, 4, true>, dim3(B, (B + 7) / 8), 256, 0, s, dpts, n, d, W, cap, adj, st,
+               (int32_t *)X);
+    count_launch();
   } else {
     dist_dispatch<F>(X, n, d, W, cap, adj, st, s);
     count_launch();

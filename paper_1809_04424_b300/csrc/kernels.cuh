@@ -210,12 +210,20 @@ __global__ void k_stage(const TIn *in, int64_t count, typename std::conditional<
 // column word for the mirrored block, so both halves are written without
 // atomics.  grid = (B, ceil(B/8)), 8 warps per CTA.
 
-template <bool F, int DR>
+// STAGE8 (int8 input, d <= 4): Xv is the raw int8 input, converted as it is
+// loaded, and the warps of the diagonal blocks also write the staged int32
+// copy Xout (each row once) that the edge-key kernel reads: no staging launch.
+template <bool F, int DR, bool STAGE8 = false>
 __global__ void __launch_bounds__(256) k_dist_bitmap(const void *Xv, int n, int d, int W, Cap cap, uint32_t *adj,
-                                                     DevStatus *st) {
+                                                     DevStatus *st, int32_t *Xout = nullptr) {
   pdl_entry();
   using T = typename std::conditional<F, float, int32_t>::type;
+  static_assert(!STAGE8 || (!F && DR > 0 && DR <= 4), "fused staging: int8 input, d <= 4");
   const T *X = (const T *)Xv;
+  auto ld = [&](int64_t idx) -> T {
+    if constexpr (STAGE8) return (T)((const int8_t *)Xv)[idx];
+    else return X[idx];
+  };
   const int bj = blockIdx.x;
   const int bi = blockIdx.y * 8 + (threadIdx.x >> 5);
   const int l = lane_id();
@@ -225,7 +233,7 @@ __global__ void __launch_bounds__(256) k_dist_bitmap(const void *Xv, int n, int 
   T xj[DR > 0 ? DR : 1];
   if constexpr (DR > 0) {
 #pragma unroll
-    for (int k = 0; k < DR; ++k) xj[k] = (jv && k < d) ? X[(int64_t)j * d + k] : T(0);
+    for (int k = 0; k < DR; ++k) xj[k] = (jv && k < d) ? ld((int64_t)j * d + k) : T(0);
   }
   const T *pj = X + (int64_t)(jv ? j : 0) * d;
   uint32_t myrow = 0, mycol = 0;
@@ -238,7 +246,14 @@ __global__ void __launch_bounds__(256) k_dist_bitmap(const void *Xv, int n, int 
   if constexpr (SHFL) {
     const int ir = bi * 32 + l;
 #pragma unroll
-    for (int k = 0; k < DR; ++k) xr[k] = (ir < n && k < d) ? X[(int64_t)ir * d + k] : T(0);
+    for (int k = 0; k < DR; ++k) xr[k] = (ir < n && k < d) ? ld((int64_t)ir * d + k) : T(0);
+    if constexpr (STAGE8) {
+      if (bi == bj && ir < n) {
+#pragma unroll
+        for (int k = 0; k < DR; ++k)
+          if (k < d) Xout[(int64_t)ir * d + k] = (int32_t)xr[k];
+      }
+    }
   }
   for (int r = 0; r < rows; ++r) {
     const int i = bi * 32 + r;
