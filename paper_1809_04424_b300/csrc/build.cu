@@ -197,6 +197,10 @@ bool gram_tc_eligible(vr_dtype dtype, int n, int d);
 vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, uint32_t *adj, DevStatus *st,
                          cudaStream_t s, unsigned int *worst_bits);
 
+// Largest size of the tetrahedron stage's per-edge prefix table (E * W
+// 16-bit counts); beyond it the face positions come from bisections.
+constexpr int64_t TET_PRE_MAX_BYTES = int64_t(1) << 28;
+
 // Largest kept-edge count for which the lexicographic triangle keys are
 // generated before the host knows T (their buffer then holds the bound
 // (sqrt 2 / 3) E^(3/2): at most 22M keys).
@@ -611,6 +615,12 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_TRY(ws.alloc(&trs.tkeys, T));
     VR_TRY(ws.alloc(&trs.meta, rs_meta_bytes(T)));
   }
+  // Tetrahedra: per lexicographic edge, word-wise prefix counts of the common
+  // neighbours (face positions by popcount instead of bisection) while the
+  // table stays under TET_PRE_MAX_BYTES.
+  uint16_t *tpre = nullptr;
+  const bool use_tpre = tets && (double)E * W * 2 <= (double)TET_PRE_MAX_BYTES;
+  if (use_tpre) VR_TRY(ws.alloc(&tpre, E * W));
   if (tets) {
     VR_TRY(ws.alloc(&tk_lex, T));
     VR_TRY(ws.alloc(&ordidx, T));
@@ -709,6 +719,10 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       launch_dep(k_tri_ordidx, grid_for(T, 256), 256, 0, s, tk, T, tk_lex, ordidx);
       launch_dep(k_tet_count, grid_for(T, 8, 148 * 32), 256, 0, s, tk_lex, T, adj, W, cnt4);
       count_launch(2);
+      if (tpre) {
+        launch_dep(k_lex_pre, grid_for(E, 8, 148 * 32), 256, 0, s, lexe, E, adj, W, tpre);
+        count_launch();
+      }
       VR_TRY((scan_exclusive<int32_t, int64_t>(cnt4, off4, T, bs_t, s)));
       VR_CUDA(cudaGetLastError());
       prof.end();
@@ -758,7 +772,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       prof.end();
       prof.begin("tet_final");
       launch_dep(k_tet_final, grid_for(T4, 256), 256, 0, s, keys4, T4, lex4, tk_lex, toff, adj, adjpre, W, deg, up,
-                 lex_ptr, ordidx, elp, n, packed ? 1 : 0, qverts, qgrade, qcol, qrow);
+                 lex_ptr, ordidx, elp, n, packed ? 1 : 0, tpre, qverts, qgrade, qcol, qrow);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();
