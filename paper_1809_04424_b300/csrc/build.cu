@@ -716,13 +716,14 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   if (maxdim >= 3) {
     if (tets) {
       prof.begin("tet_count");
-      launch_dep(k_tri_ordidx, grid_for(T, 256), 256, 0, s, tk, T, tk_lex, ordidx);
-      launch_dep(k_tet_count, grid_for(T, 8, 148 * 32), 256, 0, s, tk_lex, T, adj, W, cnt4);
-      count_launch(2);
       if (tpre) {
         launch_dep(k_lex_pre, grid_for(E, 8, 148 * 32), 256, 0, s, lexe, E, adj, W, tpre);
         count_launch();
       }
+      launch_dep(k_tri_ordidx, grid_for(T, 256), 256, 0, s, tk, T, tk_lex, ordidx, toff, adj, adjpre, W, deg, up,
+                 lex_ptr, elp, n, tpre);
+      launch_dep(k_tet_count, grid_for(T, 8, 148 * 32), 256, 0, s, tk_lex, T, adj, W, cnt4);
+      count_launch(2);
       VR_TRY((scan_exclusive<int32_t, int64_t>(cnt4, off4, T, bs_t, s)));
       VR_CUDA(cudaGetLastError());
       prof.end();

@@ -1464,18 +1464,76 @@ __device__ __forceinline__ void lex3_unpack(uint64_t k, int &a, int &b, int &c) 
   c = (int)(k & ID_MASK);
 }
 
+// Per lexicographic edge e = (x, y): word by word, the number of common
+// neighbours above y in the words below (16-bit: n <= 8192).  A triangle
+// (x, y, z)'s rank among edge e's triangles (z ascending) is then one read
+// of this table plus a popcount, instead of a bisection in the triangle keys.
+static __global__ void __launch_bounds__(256) k_lex_pre(const uint32_t *lexe, int64_t E, const uint32_t *adj, int W,
+                                                        uint16_t *pre) {
+  pdl_entry();
+  const int l = lane_id();
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
+    const uint32_t ab = lexe[e];
+    const int x = (int)(ab >> ID_BITS), y = (int)(ab & ID_MASK);
+    const uint32_t *rx = adj + (int64_t)x * W, *ry = adj + (int64_t)y * W;
+    int carry = 0;
+    for (int w0 = 0; w0 < W; w0 += 32) {
+      const int w = w0 + l;
+      const int c = w < W ? __popc(rx[w] & ry[w] & above_mask(y, w)) : 0;
+      const int inc = warp_incl_scan(c);
+      if (w < W) pre[e * W + w] = (uint16_t)(carry + inc - c);
+      carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+}
+
+// Lexicographic position of triangle (x,y,z), x<y<z, all edges kept: the
+// first edge's triangle offset plus z's rank among that edge's triangles
+// (from the prefix table when given, else a bisection in the keys).
+__device__ __forceinline__ int64_t tri_lexpos(int x, int y, int z, const uint64_t *tk_lex, const int64_t *toff,
+                                              const uint32_t *adj, const int32_t *adjpre, int W, const int32_t *deg,
+                                              const int32_t *up, const int64_t *lex_ptr, const int32_t *elp, int n,
+                                              const uint16_t *pre) {
+  const int64_t lp = elp ? (int64_t)elp[(int64_t)x * n + y] : lex_pos(x, y, adj, adjpre, W, deg, up, lex_ptr);
+  if (pre) {
+    const int w = z >> 5;
+    const uint32_t m = adj[(int64_t)x * W + w] & adj[(int64_t)y * W + w] & above_mask(y, w) & ((1u << (z & 31)) - 1u);
+    return toff[lp] + pre[lp * W + w] + __popc(m);
+  }
+  int64_t lo = toff[lp], hi = toff[lp + 1];
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int)(tk_lex[mid] & ID_MASK) < z) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // Order index of each triangle by lexicographic position: the sorted
-// triangle p has key (grade, lex3); its lexicographic position is found by
-// bisection in the lexicographic key list.
-static __global__ void k_tri_ordidx(const uint64_t *tk, int64_t T, const uint64_t *tk_lex, int32_t *ordidx) {
+// triangle p has key (grade, lex3); its lexicographic position comes from the
+// per-edge prefix table when there is one, else by bisection in the
+// lexicographic key list.
+static __global__ void k_tri_ordidx(const uint64_t *tk, int64_t T, const uint64_t *tk_lex, int32_t *ordidx,
+                                    const int64_t *toff, const uint32_t *adj, const int32_t *adjpre, int W,
+                                    const int32_t *deg, const int32_t *up, const int64_t *lex_ptr, const int32_t *elp,
+                                    int n, const uint16_t *pre) {
   pdl_entry();
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T; p += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t x = tk[p] & LEX3_MASK;
-    int64_t lo = 0, hi = T;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if ((tk_lex[mid] & LEX3_MASK) < x) lo = mid + 1;
-      else hi = mid;
+    int64_t lo;
+    if (pre) {
+      int a, b, c;
+      lex3_unpack(x, a, b, c);
+      lo = tri_lexpos(a, b, c, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr, elp, n, pre);
+    } else {
+      int64_t hi = T;
+      lo = 0;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((tk_lex[mid] & LEX3_MASK) < x) lo = mid + 1;
+        else hi = mid;
+      }
     }
     ordidx[lo] = (int32_t)p;
   }
@@ -1550,52 +1608,6 @@ static __global__ void __launch_bounds__(256) k_tet_gen(const uint64_t *tk_lex, 
       q0 += r.tot;
     }
   }
-}
-
-// Per lexicographic edge e = (x, y): word by word, the number of common
-// neighbours above y in the words below (16-bit: n <= 8192).  A triangle
-// (x, y, z)'s rank among edge e's triangles (z ascending) is then one read
-// of this table plus a popcount, instead of a bisection in the triangle keys.
-static __global__ void __launch_bounds__(256) k_lex_pre(const uint32_t *lexe, int64_t E, const uint32_t *adj, int W,
-                                                        uint16_t *pre) {
-  pdl_entry();
-  const int l = lane_id();
-  const int64_t nwarps = (int64_t)gridDim.x * 8;
-  for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
-    const uint32_t ab = lexe[e];
-    const int x = (int)(ab >> ID_BITS), y = (int)(ab & ID_MASK);
-    const uint32_t *rx = adj + (int64_t)x * W, *ry = adj + (int64_t)y * W;
-    int carry = 0;
-    for (int w0 = 0; w0 < W; w0 += 32) {
-      const int w = w0 + l;
-      const int c = w < W ? __popc(rx[w] & ry[w] & above_mask(y, w)) : 0;
-      const int inc = warp_incl_scan(c);
-      if (w < W) pre[e * W + w] = (uint16_t)(carry + inc - c);
-      carry += __shfl_sync(0xffffffffu, inc, 31);
-    }
-  }
-}
-
-// Lexicographic position of triangle (x,y,z), x<y<z, all edges kept: the
-// first edge's triangle offset plus z's rank among that edge's triangles
-// (from the prefix table when given, else a bisection in the keys).
-__device__ __forceinline__ int64_t tri_lexpos(int x, int y, int z, const uint64_t *tk_lex, const int64_t *toff,
-                                              const uint32_t *adj, const int32_t *adjpre, int W, const int32_t *deg,
-                                              const int32_t *up, const int64_t *lex_ptr, const int32_t *elp, int n,
-                                              const uint16_t *pre) {
-  const int64_t lp = elp ? (int64_t)elp[(int64_t)x * n + y] : lex_pos(x, y, adj, adjpre, W, deg, up, lex_ptr);
-  if (pre) {
-    const int w = z >> 5;
-    const uint32_t m = adj[(int64_t)x * W + w] & adj[(int64_t)y * W + w] & above_mask(y, w) & ((1u << (z & 31)) - 1u);
-    return toff[lp] + pre[lp * W + w] + __popc(m);
-  }
-  int64_t lo = toff[lp], hi = toff[lp + 1];
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if ((int)(tk_lex[mid] & ID_MASK) < z) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
 }
 
 // Final write of the tetrahedra in (grade, lex) order: vertices, grade,
