@@ -252,6 +252,12 @@ VR_API vr_status vr_serve_poll(vr_server *srv, uint64_t ticket,
  * freed). */
 VR_API vr_status vr_server_destroy(vr_server *srv);
 
+/* Barcode reduction: a working column reaching min_entries entries continues
+ * as a bitset over its rows (each later addition then costs the added
+ * column's length); negative: never, 0: always.  Default 4096.  Process-wide;
+ * the bars are identical either way. */
+VR_API vr_status vr_set_barcode_dense_min(int64_t min_entries);
+
 /* Distance tiles: 0 = automatic (tensor-core Gram tiles for int8 input and
  * for float input with d <= 64, CUDA cores otherwise), 1 = the same, 2 = CUDA
  * cores always.  Process-wide; results are identical either way. */

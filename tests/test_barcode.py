@@ -44,6 +44,30 @@ def test_random_clouds(torch, n, dtype, cap):
         check_bars(torch, pts, maxdim, cap)
 
 
+def set_dense_min(m):
+    import ctypes
+    L = vr.lib()
+    L.vr_set_barcode_dense_min.argtypes = [ctypes.c_int64]
+    L.vr_set_barcode_dense_min.restype = ctypes.c_int
+    assert L.vr_set_barcode_dense_min(m) == 0
+
+
+@pytest.mark.parametrize("dense_min", [0, 1, 64, -1])
+def test_dense_column_continuation(torch, dense_min):
+    """Working columns continued as bitsets (from the first entry, from
+    short lengths, never) give the oracle's bars: the addition order and the
+    pairs do not depend on the column's representation."""
+    try:
+        set_dense_min(dense_min)
+        c = synth.config2(n=300)
+        check_bars(torch, c.points, 2, c.maxrad)
+        pts = synth.random_cloud(120, 3, np.int8, seed=120)
+        check_bars(torch, pts, 2, 25.0)
+        check_bars(torch, synth.circle_samples(150, 3), 2, 0.6)
+    finally:
+        set_dense_min(4096)
+
+
 def test_torus_small(torch):
     """A torus: one H0 class, two long H1 classes, many ties."""
     c = synth.config2(n=300)
