@@ -194,7 +194,7 @@ __device__ __forceinline__ int64_t merge_split(const int32_t *A, int64_t la, con
   int64_t lo = d - lb > 0 ? d - lb : 0, hi = d < la ? d : la;
   while (lo < hi) {
     const int64_t mid = (lo + hi) >> 1;
-    if (A[mid] <= B[d - mid - 1]) lo = mid + 1;
+    if (__ldcg(A + mid) <= __ldcg(B + (d - mid - 1))) lo = mid + 1;
     else hi = mid;
   }
   return lo;
@@ -222,10 +222,10 @@ __device__ int64_t cta_symdiff(const int32_t *A, int64_t la, const int32_t *B, i
       const int64_t a0 = S.split[t], a1 = S.split[t + 1];  // split[t + 1] was taken at d1
       const int64_t b0 = d0 - a0, b1 = d1 - a1;
       const int na = (int)(a1 - a0), nb = (int)(b1 - b0);
-      for (int q = threadIdx.x; q < na; q += BR_THREADS) S.a[q] = A[a0 + q];
-      for (int q = threadIdx.x; q < nb; q += BR_THREADS) S.b[q] = B[b0 + q];
-      const int32_t prevA = a0 > 0 ? A[a0 - 1] : -1;    // last A entry before the tile
-      const int32_t nextB = b1 < lb ? B[b1] : INT_MAX;  // first B entry after the tile
+      for (int q = threadIdx.x; q < na; q += BR_THREADS) S.a[q] = __ldcg(A + a0 + q);
+      for (int q = threadIdx.x; q < nb; q += BR_THREADS) S.b[q] = __ldcg(B + b0 + q);
+      const int32_t prevA = a0 > 0 ? __ldcg(A + a0 - 1) : -1;    // last A entry before the tile
+      const int32_t nextB = b1 < lb ? __ldcg(B + b1) : INT_MAX;  // first B entry after the tile
       __syncthreads();
       // This thread's merged positions [p0, p1) of the tile: one pass counts
       // the entries that survive, a block scan places them, a second pass
@@ -315,134 +315,134 @@ __device__ int32_t bits_first_from(const uint32_t *bs, int64_t WT, int32_t from,
 // fresh pool space at the end.  (Long-lived working columns meet many short
 // final columns: on the n = 1000 torus the merges moved 950M entries for
 // 1.25M entries added.)
-static __global__ void __launch_bounds__(BR_THREADS) k_batch_reduce(const int32_t *act, int64_t P, int64_t p0,
-                                                                    int64_t p1, int64_t *coff, int32_t *clen,
-                                                                    int32_t *pool, int64_t cap,
-                                                                    unsigned long long *top,
-                                                                    const int32_t *final_owner, const uint8_t *fin,
-                                                                    int32_t *overflow, int64_t nrows, uint32_t *bits,
-                                                                    int nslots, int *slot_ctr, int64_t dense_min) {
-  extern __shared__ __align__(16) unsigned char br_smem[];
-  SymdiffSmem &S = *reinterpret_cast<SymdiffSmem *>(br_smem);
-  __shared__ int64_t s_o, s_at;
+__device__ void batch_reduce_phase(const int32_t *act, int64_t P, int64_t p0, int64_t p1, int64_t *coff,
+                                   int32_t *clen, int32_t *pool, int64_t cap, unsigned long long *top,
+                                   const int32_t *final_owner, const uint8_t *fin, int32_t *overflow, int64_t nrows,
+                                   uint32_t *bits, int nslots, int *slot_ctr, int64_t dense_min, SymdiffSmem &S) {
+  __shared__ int64_t s_o, s_at, s_p;
   __shared__ int s_slot, s_piv;
-  const int64_t p = p0 + blockIdx.x;
-  if (p >= p1) return;
-  const int64_t e = act[P - 1 - p];
-  if (fin[e]) return;
-  int64_t la = clen[e], oa = coff[e];
-  bool moved = false;
-  while (la > 0) {
-    if (threadIdx.x == 0) {
-      const int32_t o = final_owner[pool[oa]];
-      s_o = o;
-      s_at = -1;
-      s_slot = -1;
-      if (o >= 0) {
-        bool dense = false;
-        if (bits && dense_min >= 0 && la >= dense_min) {
-          const int sl = atomicAdd(slot_ctr, 1);
-          if (sl < nslots) {
-            s_slot = sl;
-            dense = true;
-          }
-        }
-        if (!dense) {
-          const int64_t need = la + clen[o];
-          const int64_t at = (int64_t)atomicAdd(top, (unsigned long long)need);
-          if (at + need > cap) *overflow = 1;
-          else s_at = at;
-        }
-      }
-    }
+  // The grid's CTAs take the batch's columns by ticket (slot_ctr[1]).
+  for (;;) {
+    if (threadIdx.x == 0) s_p = p0 + (int64_t)atomicAdd(slot_ctr + 1, 1);
     __syncthreads();
-    const int64_t o = s_o, at = s_at;
-    const int slot = s_slot;
+    const int64_t p = s_p;
     __syncthreads();
-    if (o < 0) break;
-    if (slot >= 0) {
-      // Dense continuation of this column's chain.
-      const int64_t WT = (nrows + 31) / 32;
-      uint32_t *bs = bits + (size_t)slot * WT;
-      for (int64_t w = threadIdx.x; w < WT; w += BR_THREADS) bs[w] = 0u;
-      __syncthreads();
-      for (int64_t i = threadIdx.x; i < la; i += BR_THREADS) {
-        const int32_t x = pool[oa + i];
-        atomicOr(bs + (x >> 5), 1u << (x & 31));
-      }
-      __syncthreads();
-      int32_t piv = pool[oa];
-      int64_t oo = o;
-      for (;;) {
-        const int64_t ob = coff[oo], lb = clen[oo];
-        for (int64_t i = threadIdx.x; i < lb; i += BR_THREADS) {
-          const int32_t x = pool[ob + i];
-          atomicXor(bs + (x >> 5), 1u << (x & 31));
-        }
-        __syncthreads();
-        piv = bits_first_from(bs, WT, piv, &s_piv);
-        if (piv == INT_MAX) break;
-        if (threadIdx.x == 0) s_o = final_owner[piv];
-        __syncthreads();
-        oo = s_o;
-        __syncthreads();
-        if (oo < 0) break;
-      }
-      // Back to a sorted list: per-thread runs of words, counted, placed.
-      const int64_t per = (WT + BR_THREADS - 1) / BR_THREADS;
-      const int64_t w0 = (int64_t)threadIdx.x * per, w1 = w0 + per < WT ? w0 + per : WT;
-      int64_t cnt = 0;
-      for (int64_t w = w0; w < w1; ++w) cnt += __popc(__ldcg(bs + w));
-      int64_t tot;
-      const int64_t off = block_excl_scan<int64_t>(cnt, S.sh, &tot);
+    if (p >= p1) return;
+    const int64_t e = act[P - 1 - p];
+    if (__ldcg(fin + e)) continue;
+    int64_t la = __ldcg(clen + e), oa = __ldcg(coff + e);
+    bool moved = false;
+    while (la > 0) {
       if (threadIdx.x == 0) {
+        const int32_t o = __ldcg(final_owner + __ldcg(pool + oa));
+        s_o = o;
         s_at = -1;
-        if (tot > 0) {
-          const int64_t a2 = (int64_t)atomicAdd(top, (unsigned long long)tot);
-          if (a2 + tot > cap) *overflow = 1;
-          else s_at = a2;
+        s_slot = -1;
+        if (o >= 0) {
+          bool dense = false;
+          if (bits && dense_min >= 0 && la >= dense_min) {
+            const int sl = atomicAdd(slot_ctr, 1);
+            if (sl < nslots) {
+              s_slot = sl;
+              dense = true;
+            }
+          }
+          if (!dense) {
+            const int64_t need = la + __ldcg(clen + o);
+            const int64_t at = (int64_t)atomicAdd(top, (unsigned long long)need);
+            if (at + need > cap) *overflow = 1;
+            else s_at = at;
+          }
         }
       }
       __syncthreads();
-      const int64_t a2 = s_at;
-      if (tot == 0) {
-        la = 0;
-        moved = true;
-      } else if (a2 >= 0) {
-        int32_t *out = pool + a2 + off;
-        for (int64_t w = w0; w < w1; ++w) {
-          uint32_t v = __ldcg(bs + w);
-          while (v) {
-            *out++ = (int32_t)(w * 32 + __ffs(v) - 1);
-            v &= v - 1;
+      const int64_t o = s_o, at = s_at;
+      const int slot = s_slot;
+      __syncthreads();
+      if (o < 0) break;
+      if (slot >= 0) {
+        // Dense continuation of this column's chain.
+        const int64_t WT = (nrows + 31) / 32;
+        uint32_t *bs = bits + (size_t)slot * WT;
+        for (int64_t w = threadIdx.x; w < WT; w += BR_THREADS) bs[w] = 0u;
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < la; i += BR_THREADS) {
+          const int32_t x = __ldcg(pool + oa + i);
+          atomicOr(bs + (x >> 5), 1u << (x & 31));
+        }
+        __syncthreads();
+        int32_t piv = __ldcg(pool + oa);
+        int64_t oo = o;
+        for (;;) {
+          const int64_t ob = __ldcg(coff + oo), lb = __ldcg(clen + oo);
+          for (int64_t i = threadIdx.x; i < lb; i += BR_THREADS) {
+            const int32_t x = __ldcg(pool + ob + i);
+            atomicXor(bs + (x >> 5), 1u << (x & 31));
+          }
+          __syncthreads();
+          piv = bits_first_from(bs, WT, piv, &s_piv);
+          if (piv == INT_MAX) break;
+          if (threadIdx.x == 0) s_o = __ldcg(final_owner + piv);
+          __syncthreads();
+          oo = s_o;
+          __syncthreads();
+          if (oo < 0) break;
+        }
+        // Back to a sorted list: per-thread runs of words, counted, placed.
+        const int64_t per = (WT + BR_THREADS - 1) / BR_THREADS;
+        const int64_t w0 = (int64_t)threadIdx.x * per, w1 = w0 + per < WT ? w0 + per : WT;
+        int64_t cnt = 0;
+        for (int64_t w = w0; w < w1; ++w) cnt += __popc(__ldcg(bs + w));
+        int64_t tot;
+        const int64_t off = block_excl_scan<int64_t>(cnt, S.sh, &tot);
+        if (threadIdx.x == 0) {
+          s_at = -1;
+          if (tot > 0) {
+            const int64_t a2 = (int64_t)atomicAdd(top, (unsigned long long)tot);
+            if (a2 + tot > cap) *overflow = 1;
+            else s_at = a2;
           }
         }
-        oa = a2;
-        la = tot;
-        moved = true;
+        __syncthreads();
+        const int64_t a2 = s_at;
+        if (tot == 0) {
+          la = 0;
+          moved = true;
+        } else if (a2 >= 0) {
+          int32_t *out = pool + a2 + off;
+          for (int64_t w = w0; w < w1; ++w) {
+            uint32_t v = __ldcg(bs + w);
+            while (v) {
+              *out++ = (int32_t)(w * 32 + __ffs(v) - 1);
+              v &= v - 1;
+            }
+          }
+          oa = a2;
+          la = tot;
+          moved = true;
+        }
+        break;  // (no pool space: the column keeps its last list and comes back next pass)
       }
-      break;  // (no pool space: the column keeps its last list and comes back next pass)
+      if (at < 0) break;
+      const int64_t k = cta_symdiff(pool + oa, la, pool + __ldcg(coff + o), __ldcg(clen + o), pool + at, S);
+      oa = at;
+      la = k;
+      moved = true;
     }
-    if (at < 0) break;
-    const int64_t k = cta_symdiff(pool + oa, la, pool + coff[o], clen[o], pool + at, S);
-    oa = at;
-    la = k;
-    moved = true;
-  }
-  if (moved && threadIdx.x == 0) {
-    coff[e] = oa;
-    clen[e] = (int32_t)la;
+    if (moved && threadIdx.x == 0) {
+      coff[e] = oa;
+      clen[e] = (int32_t)la;
+    }
   }
 }
 
 // One CTA: finalise the longest prefix of the batch's non-final columns whose
 // pivots differ from every younger non-final column's (empty columns are
 // final at once).  *remaining = the batch's non-final columns afterwards.
-static __global__ void __launch_bounds__(BC_BATCH) k_batch_finalize(const int32_t *act, int64_t P, int64_t p0,
-                                                                    int64_t p1, const int64_t *coff,
-                                                                    const int32_t *clen, const int32_t *pool,
-                                                                    int32_t *final_owner, uint8_t *fin,
-                                                                    const int32_t *overflow, int32_t *remaining) {
+__device__ void batch_finalize_phase(const int32_t *act, int64_t P, int64_t p0, int64_t p1, const int64_t *coff,
+                                     const int32_t *clen, const int32_t *pool, int32_t *final_owner, uint8_t *fin,
+                                     const int32_t *overflow, int32_t *remaining) {
+  static_assert(BR_THREADS == BC_BATCH, "one thread per column of a batch");
   __shared__ int32_t piv[BC_BATCH];
   __shared__ int32_t first_conflict;
   __shared__ int32_t left;
@@ -450,14 +450,14 @@ static __global__ void __launch_bounds__(BC_BATCH) k_batch_finalize(const int32_
   const int64_t p = p0 + i;
   const bool mine = p < p1;
   const int64_t e = mine ? act[P - 1 - p] : -1;
-  const bool open = mine && !fin[e];
-  piv[i] = open && clen[e] > 0 ? pool[coff[e]] : -1;
+  const bool open = mine && !__ldcg(fin + e);
+  piv[i] = open && __ldcg(clen + e) > 0 ? __ldcg(pool + __ldcg(coff + e)) : -1;
   if (i == 0) {
     first_conflict = BC_BATCH;
     left = 0;
   }
   __syncthreads();
-  if (*overflow) {  // a column could not finish its additions: no finalising this pass
+  if (__ldcg(overflow)) {  // a column could not finish its additions: no finalising this pass
     if (open) atomicAdd(&left, 1);
     __syncthreads();
     if (i == 0) *remaining = left;
@@ -482,6 +482,90 @@ static __global__ void __launch_bounds__(BC_BATCH) k_batch_finalize(const int32_
   }
   __syncthreads();
   if (i == 0) *remaining = left;
+}
+
+// Grid-wide barrier of a co-resident grid (cooperative launch): arrival
+// count and generation in global memory; the wait is bounded (F_TIMEOUT in
+// *err, then every CTA leaves the reduction).  Every thread fences its writes
+// first; data other CTAs write during the launch is read through L2 (__ldcg).
+constexpr long BAR_WAIT_LIMIT = 1l << 26;
+__device__ bool grid_barrier(unsigned int *bar, int32_t *err) {
+  __threadfence();
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    volatile unsigned int *gen = bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long spins = 0;
+      while (*gen == g) {
+        if (++spins > BAR_WAIT_LIMIT) {
+          atomicOr(err, F_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = *(volatile int32_t *)err == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The whole column reduction from batch position *cursor on, in one launch
+// of co-resident CTAs: per batch, passes of (every CTA reduces columns by
+// ticket; CTA 0 finalises the longest conflict-free prefix) until the batch
+// has no open column.  It returns to the host, with *cursor at the batch to
+// redo or take next, when the pool is over half full or an addition found no
+// room (the host compacts the pool and relaunches), or when a batch does not
+// settle (*cursor = -1).  ctr: [0] bitset slots, [1] column tickets,
+// [2..3] barrier, [4] stop.
+static __global__ void __launch_bounds__(BR_THREADS) k_reduce_all(const int32_t *act, int64_t P, int64_t *cursor,
+                                                                  int64_t *coff, int32_t *clen, int32_t *pool,
+                                                                  int64_t cap, unsigned long long *top,
+                                                                  int32_t *final_owner, uint8_t *fin,
+                                                                  int32_t *overflow, int32_t *remaining,
+                                                                  int64_t nrows, uint32_t *bits, int nslots,
+                                                                  unsigned int *ctr, int64_t dense_min, int32_t *err) {
+  extern __shared__ __align__(16) unsigned char br_smem[];
+  SymdiffSmem &S = *reinterpret_cast<SymdiffSmem *>(br_smem);
+  int *slot_ctr = (int *)ctr;
+  unsigned int *bar = ctr + 2;
+  for (int64_t p0 = *(volatile int64_t *)cursor; p0 < P; p0 += BC_BATCH) {
+    const int64_t p1 = p0 + BC_BATCH < P ? p0 + BC_BATCH : P;
+    for (int64_t pass = 0;; ++pass) {
+      batch_reduce_phase(act, P, p0, p1, coff, clen, pool, cap, top, final_owner, fin, overflow, nrows, bits, nslots,
+                         slot_ctr, dense_min, S);
+      if (!grid_barrier(bar, err)) return;
+      if (blockIdx.x == 0) {
+        batch_finalize_phase(act, P, p0, p1, coff, clen, pool, final_owner, fin, overflow, remaining);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          slot_ctr[0] = 0;
+          slot_ctr[1] = 0;
+          const bool full = *(volatile int32_t *)overflow != 0 ||
+                            *(volatile unsigned long long *)top > (unsigned long long)cap / 2;
+          const bool settled = *(volatile int32_t *)remaining == 0;
+          // leave for the host: compaction (redo this batch if unsettled, else
+          // start at the next), or a batch that does not settle
+          if (full) *cursor = settled ? p1 : p0;
+          else if (!settled && pass > BC_BATCH + 8) *cursor = -1;
+          else *cursor = settled ? p1 : p0;
+          ctr[4] = (full || (!settled && pass > BC_BATCH + 8)) ? 1u : 0u;
+        }
+      }
+      if (!grid_barrier(bar, err)) return;
+      const int64_t cur = *(volatile int64_t *)cursor;
+      if (*(volatile unsigned int *)(ctr + 4) != 0) return;
+      if (cur != p0) break;  // settled: next batch
+    }
+  }
 }
 
 // Move the live columns to the front of a new pool.
@@ -661,7 +745,6 @@ static vr_status reduce_cohomology(vr_complex *c, int k, cudaStream_t s, Dev &dv
     prof.end();
 
     prof.begin(k == 1 ? "bars.reduce" : "bars.reduce2");
-    VR_CUDA(cudaFuncSetAttribute(k_batch_reduce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BR_SMEM));
     // Active columns in ascending edge order; processing takes them from the
     // youngest.
     int32_t *aflag, *act, *final_owner, *rem;
@@ -690,68 +773,80 @@ static vr_status reduce_cohomology(vr_complex *c, int k, cudaStream_t s, Dev &dv
     const int64_t dense_min = g_dense_min;
     int nslots = 0;
     uint32_t *bits = nullptr;
-    int *slot_ctr = nullptr;
+    int *slot_ctr = nullptr;  // [0]: bitset slots taken, [1]: column tickets (per launch)
+    VR_TRY(dv.get(&slot_ctr, 2));
     if (dense_min >= 0 && T > 0) {
       nslots = (int)std::min<int64_t>(BC_BATCH, std::max<int64_t>(1, DENSE_BITS_MAX / (WT * 4)));
       VR_TRY(dv.get(&bits, (int64_t)nslots * WT));
-      VR_TRY(dv.get(&slot_ctr, 1));
     }
-    int32_t hrem[2];
-    unsigned long long htop = 0;
-    for (int64_t p0 = 0; p0 < P; p0 += BC_BATCH) {
-      const int64_t p1 = std::min<int64_t>(P, p0 + BC_BATCH);
-      for (int64_t pass = 0;; ++pass) {
-        if (pass > BC_BATCH + 8) {
-          set_error("barcode: a batch of the column reduction did not settle");
-          return VR_ERR_INTERNAL;
-        }
-        VR_CUDA(cudaMemsetAsync(overflow, 0, sizeof(int32_t), s));
-        // Two passes per check: a pass on a settled batch does nothing.
-        for (int k = 0; k < 2; ++k) {
-          if (slot_ctr) VR_CUDA(cudaMemsetAsync(slot_ctr, 0, sizeof(int), s));
-          k_batch_reduce<<<(unsigned)(p1 - p0), BR_THREADS, BR_SMEM, s>>>(act, P, p0, p1, coff, clen, pool, cap, top,
-                                                                    final_owner, fin, overflow, T, bits, nslots,
-                                                                    slot_ctr, dense_min);
-          k_batch_finalize<<<1, BC_BATCH, 0, s>>>(act, P, p0, p1, coff, clen, pool, final_owner, fin, overflow,
-                                                  rem);
-          count_launch(2);
-        }
-        VR_CUDA(cudaGetLastError());
-        VR_CUDA(cudaMemcpyAsync(hrem, rem, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        VR_CUDA(cudaMemcpyAsync(hrem + 1, overflow, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        VR_CUDA(cudaMemcpyAsync(&htop, top, sizeof(htop), cudaMemcpyDeviceToHost, s));
-        VR_CUDA(cudaStreamSynchronize(s));
-        if (hrem[1] || htop > (unsigned long long)cap / 2) {
-          // Compact the live columns into a pool four times the live size (and
-          // at least as large as before).
-          int64_t *noff, *nbs;
-          VR_TRY(dv.get(&noff, E + 1));
-          VR_TRY(dv.get(&nbs, scan_tmp_slots(E)));
-          VR_TRY((scan_exclusive<int32_t, int64_t>(clen, noff, E, nbs, s)));
-          int64_t live = 0;
-          VR_CUDA(cudaMemcpyAsync(&live, noff + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-          VR_CUDA(cudaStreamSynchronize(s));
-          const int64_t ncap = std::max<int64_t>(cap, 4 * live + (1 << 20));
-          int32_t *npool;
-          int64_t *ncoff;
-          VR_TRY(dv.get(&npool, ncap));
-          VR_TRY(dv.get(&ncoff, E));
-          k_compact<<<bc_grid(E), BC_THREADS, 0, s>>>(E, coff, clen, noff, pool, npool, ncoff);
-          count_launch();
-          VR_CUDA(cudaGetLastError());
-          dv.release(pool);
-          dv.release(coff);
-          dv.release(noff);
-          dv.release(nbs);
-          pool = npool;
-          coff = ncoff;
-          cap = ncap;
-          const unsigned long long t0 = (unsigned long long)live;
-          VR_CUDA(cudaMemcpyAsync(top, &t0, sizeof(t0), cudaMemcpyHostToDevice, s));
-          continue;
-        }
-        if (hrem[0] == 0) break;
+    int nsm = 0, dev = 0;
+    VR_CUDA(cudaGetDevice(&dev));
+    VR_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    // One cooperative launch reduces batch after batch; it comes back only
+    // to have the pool compacted (then it is launched again from *cursor).
+    int64_t *cursor;
+    unsigned int *ctr;
+    int32_t *rerr;
+    VR_TRY(dv.get(&cursor, 1));
+    VR_TRY(dv.get(&ctr, 5));
+    VR_TRY(dv.get(&rerr, 1));
+    VR_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int64_t), s));
+    VR_CUDA(cudaMemsetAsync(rerr, 0, sizeof(int32_t), s));
+    VR_CUDA(cudaFuncSetAttribute(k_reduce_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BR_SMEM));
+    int per = 0;
+    VR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_reduce_all, BR_THREADS, BR_SMEM));
+    const unsigned rgrid = (unsigned)std::max(1, nsm * std::max(per, 1));
+    for (int launch = 0;; ++launch) {
+      if (launch > 1 << 20) {
+        set_error("barcode: the column reduction did not finish");
+        return VR_ERR_INTERNAL;
       }
+      VR_CUDA(cudaMemsetAsync(overflow, 0, sizeof(int32_t), s));
+      VR_CUDA(cudaMemsetAsync(ctr, 0, 5 * sizeof(unsigned int), s));
+      int64_t a_P = P, a_cap = cap, a_T = T, a_dmin = dense_min;
+      int a_nslots = nslots;
+      void *args[] = {&act, &a_P, &cursor, &coff, &clen, &pool, &a_cap, &top, &final_owner, &fin, &overflow, &rem,
+                      &a_T, &bits, &a_nslots, &ctr, &a_dmin, &rerr};
+      VR_CUDA(cudaLaunchCooperativeKernel((const void *)k_reduce_all, dim3(rgrid), dim3(BR_THREADS), args, BR_SMEM, s));
+      count_launch();
+      int64_t hcur = 0;
+      int32_t herr = 0;
+      VR_CUDA(cudaMemcpyAsync(&hcur, cursor, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      VR_CUDA(cudaMemcpyAsync(&herr, rerr, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      VR_CUDA(cudaStreamSynchronize(s));
+      VR_TRY(flags_to_status(herr));
+      if (hcur < 0) {
+        set_error("barcode: a batch of the column reduction did not settle");
+        return VR_ERR_INTERNAL;
+      }
+      if (hcur >= P) break;
+      // The pool is over half full (or an addition found no room): compact
+      // the live columns into a pool four times the live size (and at least
+      // as large as before).
+      int64_t *noff, *nbs;
+      VR_TRY(dv.get(&noff, E + 1));
+      VR_TRY(dv.get(&nbs, scan_tmp_slots(E)));
+      VR_TRY((scan_exclusive<int32_t, int64_t>(clen, noff, E, nbs, s)));
+      int64_t live = 0;
+      VR_CUDA(cudaMemcpyAsync(&live, noff + E, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      VR_CUDA(cudaStreamSynchronize(s));
+      const int64_t ncap = std::max<int64_t>(cap, 4 * live + (1 << 20));
+      int32_t *npool;
+      int64_t *ncoff;
+      VR_TRY(dv.get(&npool, ncap));
+      VR_TRY(dv.get(&ncoff, E));
+      k_compact<<<bc_grid(E), BC_THREADS, 0, s>>>(E, coff, clen, noff, pool, npool, ncoff);
+      count_launch();
+      VR_CUDA(cudaGetLastError());
+      dv.release(pool);
+      dv.release(coff);
+      dv.release(noff);
+      dv.release(nbs);
+      pool = npool;
+      coff = ncoff;
+      cap = ncap;
+      const unsigned long long t0 = (unsigned long long)live;
+      VR_CUDA(cudaMemcpyAsync(top, &t0, sizeof(t0), cudaMemcpyHostToDevice, s));
     }
     k_pairs1<<<bc_grid(E), BC_THREADS, 0, s>>>(E, coff, clen, pool, pair_tri, pair_edge);
     count_launch();
