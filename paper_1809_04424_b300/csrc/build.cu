@@ -197,6 +197,9 @@ bool gram_tc_eligible(vr_dtype dtype, int n, int d);
 vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, uint32_t *adj, DevStatus *st,
                          cudaStream_t s, unsigned int *worst_bits);
 
+// Clouds above this size always take the lex triangle order.
+constexpr int LEX_FORCE_N = 4096;
+
 // Largest size of the tetrahedron stage's per-edge prefix table (E * W
 // 16-bit counts); beyond it the face positions come from bisections.
 constexpr int64_t TET_PRE_MAX_BYTES = int64_t(1) << 28;
@@ -538,12 +541,13 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   }
 
   // Triangle order: lex mode (generation by first edge, stable sort on the
-  // grade) is forced for tetrahedra and for clouds above DENSE_MAX_N points,
-  // where the max-edge enumeration's per-candidate order lookups go through
-  // the neighbour CSR (measured on the 7322-point WorldMap-shaped cloud:
-  // 0.88 ms in lex mode, 1.24 ms in max-edge mode).  Otherwise lex_mode
-  // decides by the share of tied grades.
-  const int force_lex = (maxdim >= 3 || n > DENSE_MAX_N) ? 1 : 0;
+  // grade) is forced for tetrahedra and for clouds above LEX_FORCE_N points,
+  // where the max-edge enumeration (each triangle a candidate at all three of
+  // its edges, two order lookups per candidate) costs more than the sort
+  // (measured on the 7322-point WorldMap-shaped cloud: 0.76 ms in lex mode,
+  // 1.19 ms in max-edge mode).  Otherwise lex_mode decides by the share of
+  // tied grades.
+  const int force_lex = (maxdim >= 3 || n > LEX_FORCE_N) ? 1 : 0;
   if (maxdim >= 2 && E > 0) {
     prof.begin("tri_count");
     const EdgeIndex exc{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};

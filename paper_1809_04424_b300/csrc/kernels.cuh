@@ -1022,7 +1022,7 @@ __device__ __forceinline__ int64_t lex_pos(int a, int b, const uint32_t *adj, co
 
 // Order index of kept edge (a, b), a < b: from the dense table when there is
 // one (n <= DENSE_MAX_N), else through the neighbour CSR.
-constexpr int DENSE_MAX_N = 4096;
+constexpr int DENSE_MAX_N = 8192;  // every cloud (n <= 8192): two n x n int32 tables, at most 512 MB
 struct EdgeIndex {
   const uint32_t *adj;
   const int32_t *adjpre;

@@ -145,8 +145,8 @@ def test_max_size_sampled(torch):
 
 @pytest.mark.parametrize("n", [4096, 4097])
 def test_dense_edge_table_boundary(torch, n):
-    """Lex-order triangles on both sides of the dense edge-index table's size
-    limit (4096 points: table; 4097: neighbour CSR)."""
+    """Lex-order triangles on both sides of 4096 points (above it the lex
+    order is forced; the dense edge tables serve both)."""
     g = synth.rng(4096 + n)
     pts = g.integers(-20, 21, size=(n, 3)).astype(np.int8)
     c = check(torch, pts, 2, 4.0)
