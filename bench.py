@@ -385,6 +385,12 @@ def run_reference(args):
     return 0
 
 
+# Bytes of one cloud's descriptor in the batch path (struct CloudDesc of the
+# batch source: 14 eight-byte fields and 8 four-byte ones); the library sends it
+# to the device twice per batch and reads it back twice.
+CLOUD_DESC_BYTES = 144
+
+
 def run_batch_bench(args):
     """Batched clouds/s: all clouds of the uneven sphere workload in one
     vr_build_batch call per step, against the per-cloud path (one vr_build per
@@ -439,11 +445,13 @@ def run_batch_bench(args):
         del x
     torch.cuda.synchronize()
     per_cloud = len(sample) / (time.perf_counter() - t0)
-    # e2e: host points in, all outputs of every cloud stay on the device
+    # e2e: host points in, each cloud's descriptor back, the complexes stay on the device
     host = torch.from_numpy(pts).pin_memory()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         b = vr.vr_build_batch(host.numpy(), off, 2, 40.0)
+        if b.info()["n_failed"]:
+            raise RuntimeError("batch build failed on some clouds")
         del b
     torch.cuda.synchronize()
     e2e = args.n_clouds * args.steps / (time.perf_counter() - t0)
@@ -457,7 +465,11 @@ def run_batch_bench(args):
             "simplices_per_s": tot * args.steps / el,
             "per_cloud_path": {"value": per_cloud, "unit": "clouds/s", "sample_clouds": len(sample),
                                "speedup_batched": batched / per_cloud},
-            "e2e": {"value": e2e, "unit": "clouds/s", "h2d_bytes_per_step": int(pts.nbytes), "d2h_bytes_per_step": 0},
+            "e2e": {"value": e2e, "unit": "clouds/s",
+                    "h2d_bytes_per_step": int(pts.nbytes) + len(clouds) * (2 * CLOUD_DESC_BYTES + 4),
+                    "d2h_bytes_per_step": len(clouds) * 2 * CLOUD_DESC_BYTES,
+                    "read_back": "each cloud's descriptor (sizes, status, grade count) after the sizing pass "
+                                 "and after the build; the complexes stay on the device"},
             "gpu_launches": launches, "phases_ms": phases, "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -575,7 +587,9 @@ def run_serve_bench(args):
                                "p50_ms": 1e3 * float(np.percentile(lp, 50)),
                                "p99_ms": 1e3 * float(np.percentile(lp, 99)), "clouds_per_s": M / wp},
             "e2e": {"value": N / wall, "unit": "clouds/s", "h2d_bytes_per_step": int(np.mean([r.points.nbytes for r in reqs])),
-                    "d2h_bytes_per_step": 0},
+                    "d2h_bytes_per_step": 2 * CLOUD_DESC_BYTES,
+                    "read_back": "per request its descriptor (batched requests, twice) or the status word the "
+                                 "device writes to mapped host memory (large ones); the complexes stay on the device"},
             "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -52,3 +52,28 @@ def test_small_cases():
     assert capacity(0) == 1
     assert capacity(1) >= 1
     assert capacity(3) >= 1  # one triangle
+
+
+def test_cloud_descriptor_bytes():
+    """The batch bench counts the per-cloud descriptor the batch path copies
+    each way; its byte count must match the struct in the CUDA source (fields
+    of 4 and 8 bytes only, so no padding beyond a trailing pair)."""
+    import os
+    import re
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = open(os.path.join(root, "paper_1809_04424_b300", "csrc", "batch.cu")).read()
+    body = src[src.index("struct CloudDesc {"):]
+    body = body[: body.index("};")]
+    size = {"int64_t": 8, "uint64_t": 8, "double": 8, "int32_t": 4, "float": 4}
+    total = 0
+    for line in body.splitlines()[1:]:
+        line = line.split("//")[0].strip()
+        if not line:
+            continue
+        m = re.match(r"(\w+)\s+(.*);", line)
+        total += size[m.group(1)] * len(m.group(2).split(","))
+    assert total % 8 == 0
+    sys.path.insert(0, root)
+    import bench
+    assert bench.CLOUD_DESC_BYTES == total
