@@ -545,8 +545,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   // where the max-edge enumeration (each triangle a candidate at all three of
   // its edges, two order lookups per candidate) costs more than the sort
   // (measured on the 7322-point WorldMap-shaped cloud: 0.76 ms in lex mode,
-  // 1.19 ms in max-edge mode).  Otherwise lex_mode decides by the share of
-  // tied grades.
+  // 1.19 ms in max-edge mode).  Otherwise lex_mode decides by the edge count
+  // and the share of tied grades.
   const int force_lex = (maxdim >= 3 || n > LEX_FORCE_N) ? 1 : 0;
   if (maxdim >= 2 && E > 0) {
     prof.begin("tri_count");

@@ -1009,10 +1009,14 @@ __device__ __forceinline__ uint64_t lex3(int a, int b, int c) {
 }
 
 // Triangles in lexicographic order + a sort on the grade bits: chosen when
-// more than 5% of edges share a grade, and always for tetrahedra (which are
+// more than 5% of edges share a grade, from LEX_MIN_E kept edges on (the
+// max-edge enumeration checks every triangle at all three of its edges and
+// costs more than the sort there: on Gaussian-mixture clouds with d = 8 and 32
+// the two meet near 150k edges), and always for tetrahedra (which are
 // generated from the lexicographic triangle list).
+constexpr int64_t LEX_MIN_E = 1 << 17;
 __host__ __device__ __forceinline__ bool lex_mode(int64_t E, int64_t ngrades, int force = 0) {
-  return force || (E - (ngrades - 1)) * 20 > E;
+  return force || E >= LEX_MIN_E || (E - (ngrades - 1)) * 20 > E;
 }
 
 __device__ __forceinline__ int64_t lex_pos(int a, int b, const uint32_t *adj, const int32_t *adjpre, int W,

@@ -388,65 +388,128 @@ __device__ __forceinline__ void rs_publish(uint64_t *w, uint32_t tag, uint64_t v
   *(volatile uint64_t *)w = ((uint64_t)tag << 56) | v;
 }
 
+// Digit of key k in one pass: bits [sh, sh + 8) of the key under mask.  HI:
+// the digit lies in the upper word and sh counts from bit 32; otherwise a
+// funnel shift of the two words (a digit may straddle bit 32).
+template <bool HI>
+__device__ __forceinline__ uint32_t pass_digit(uint64_t k, int sh, uint32_t mask) {
+  const uint32_t lo = (uint32_t)k, hi = (uint32_t)(k >> 32);
+  return (HI ? hi >> sh : __funnelshift_r(lo, hi, sh)) & mask;
+}
+
 // One digit pass.  CTAs claim tiles in order (atomic ticket), so every
-// earlier tile belongs to a CTA that is already running; a CTA ranks its tile
-// (stable), publishes its per-digit counts, adds up earlier tiles' counts by
-// looking back until an inclusive count is found (bounded spin: a timeout
-// raises F_TIMEOUT in *err), publishes its own inclusive counts, and writes
-// the keys out digit run by digit run through shared memory.
-static __global__ void __launch_bounds__(RS_THREADS, 3) k_rs_onesweep(const uint64_t *src, uint64_t *dst, int64_t n,
-                                                                   int shift, uint32_t mask, int pass, const uint32_t *hist,
-                                                                   uint64_t *status, uint32_t *ticket,
-                                                                   int32_t *err) {
+// earlier tile belongs to a CTA that is already running.  A CTA ranks its
+// tile (stable: match.any peers and per-warp digit counters), publishes its
+// per-digit counts, places the keys digit run by digit run in shared memory,
+// adds up earlier tiles' counts by looking back until an inclusive count is
+// found (bounded spin: a timeout raises F_TIMEOUT in *err), publishes its own
+// inclusive counts and writes the runs out.  A ragged last tile is padded
+// with all-ones keys: they take the largest digit, rank after every real key
+// of it and are neither counted nor written.
+constexpr int OS_ITEMS = 16;                    // keys per lane
+constexpr int OS_TILE = RS_THREADS * OS_ITEMS;  // keys per tile
+constexpr int OS_MIN_BLOCKS = 4;                // resident CTAs per SM the registers are sized for
+template <bool HI>
+__global__ void __launch_bounds__(RS_THREADS, OS_MIN_BLOCKS) k_rs_onesweep(const uint64_t *src, uint64_t *dst, int64_t n,
+                                                               int sh, uint32_t mask, int pass,
+                                                               const uint32_t *hist, uint64_t *status,
+                                                               uint32_t *ticket, int32_t *err) {
   pdl_entry();
-  __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
-  __shared__ uint32_t cnt[RS_BINS];
-  __shared__ uint32_t lpre[RS_BINS];
-  __shared__ int64_t gbase[RS_BINS];
-  __shared__ uint64_t skey[RS_TILE];
-  __shared__ int64_t sh[33];
+  __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];  // per-warp digit counts, then each warp's run starts
+  __shared__ int64_t gofs[RS_BINS];             // global position of a run's slot 0 in skey
+  __shared__ uint64_t skey[OS_TILE];
+  __shared__ uint64_t scan_sh[33];
   __shared__ int64_t tile_sh;
+  const int w = threadIdx.x >> 5, l = lane_id();
+  for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
   if (threadIdx.x == 0) tile_sh = atomicAdd(ticket, 1u);
   __syncthreads();
   const int64_t t = tile_sh;
-  const int64_t t0 = t * RS_TILE;
-  const int64_t c = n - t0 < RS_TILE ? n - t0 : RS_TILE;
-  uint64_t key[RS_ITEMS];
-  uint32_t rank[RS_ITEMS];
-  tile_rank(src, t0, c, shift, mask, key, rank, wcnt, cnt);
+  const int64_t t0 = t * OS_TILE;
+  const int c = n - t0 < OS_TILE ? (int)(n - t0) : OS_TILE;
 
-  const int b = threadIdx.x;  // RS_THREADS == RS_BINS: one digit per thread
-  const uint64_t v = cnt[b];
+  // Rank: lane l of warp w holds keys w*32*OS_ITEMS + q*32 + l of the tile.
+  uint64_t key[OS_ITEMS];
+  uint32_t pk[OS_ITEMS];  // rank among the warp's keys of the digit | digit << 16
+  {
+    const uint64_t *p = src + t0 + w * (32 * OS_ITEMS) + l;
+    const int lim = c - (w * (32 * OS_ITEMS) + l);
+#pragma unroll
+    for (int q = 0; q < OS_ITEMS; ++q) key[q] = q * 32 < lim ? p[q * 32] : ~0ull;
+    const uint32_t lt = lanemask_lt();
+    uint32_t *wc = wcnt[w];
+#pragma unroll
+    for (int q = 0; q < OS_ITEMS; ++q) {
+      const uint32_t dg = pass_digit<HI>(key[q], sh, mask);
+      const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+      const uint32_t below = peers & lt;
+      const uint32_t before = wc[dg];
+      pk[q] = (before + __popc(below)) | (dg << 16);
+      __syncwarp();
+      if (below == 0) wc[dg] = before + __popc(peers);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+
+  // Per digit b (one per thread): the tile's count, published at once; the
+  // tile-local start of each warp's run of b.
+  const int b = threadIdx.x;  // RS_THREADS == RS_BINS
+  uint32_t v = 0;
+#pragma unroll
+  for (int ww = 0; ww < RS_WARPS; ++ww) v += wcnt[ww][b];
+  if (b == (int)mask) v -= OS_TILE - c;  // the padding
   const uint32_t tag_agg = 2 * pass + 1, tag_inc = 2 * pass + 2;
+  uint64_t *my = status + t * RS_BINS + b;
+  rs_publish(my, t == 0 ? tag_inc : tag_agg, v);
+  // One scan for both starts: the digit's start over all keys (from the
+  // histogram) in the high bits, its start inside the tile in the low 16.
+  const uint64_t both = block_excl_scan<uint64_t>(((uint64_t)hist[b] << 16) | v, scan_sh, (uint64_t *)nullptr);
+  const uint32_t lp = (uint32_t)(both & 0xffffu);
+  {
+    uint32_t run = lp;
+#pragma unroll
+    for (int ww = 0; ww < RS_WARPS; ++ww) {
+      const uint32_t x = wcnt[ww][b];
+      wcnt[ww][b] = run;
+      run += x;
+    }
+  }
+  __syncthreads();
+  {
+    const uint32_t *wc = wcnt[w];
+#pragma unroll
+    for (int q = 0; q < OS_ITEMS; ++q) skey[wc[pk[q] >> 16] + (pk[q] & 0xffffu)] = key[q];
+  }
+
+  // Look back in windows of LB_WIN predecessors (loads issued together),
+  // consumed in order until an inclusive count; a word not yet published
+  // restarts the window there.
   uint64_t excl = 0;
-  if (t == 0) {
-    rs_publish(&status[b], tag_inc, v);
-  } else {
-    rs_publish(&status[t * RS_BINS + b], tag_agg, v);
-    // Look back in windows of LB_WIN predecessors (loads issued together),
-    // consumed in order until an inclusive count; a word not yet published
-    // restarts the window there.
+  if (t > 0) {
     constexpr int LB_WIN = 8;
+    const uint64_t *pk0 = my - RS_BINS;  // tile t - 1
     int64_t k = t - 1;
     long spins = 0;
     bool done = false;
     while (!done && k >= 0) {
-      uint64_t w[LB_WIN];
+      uint64_t wv[LB_WIN];
 #pragma unroll
       for (int q = 0; q < LB_WIN; ++q)
-        w[q] = k - q >= 0 ? *(volatile const uint64_t *)&status[(k - q) * RS_BINS + b] : 0;
+        wv[q] = q <= k ? *(volatile const uint64_t *)(pk0 - q * RS_BINS) : 0;
       int used = 0;
 #pragma unroll
       for (int q = 0; q < LB_WIN; ++q) {
-        if (done || used != q || k - q < 0) continue;
-        const uint32_t tag = (uint32_t)(w[q] >> 56);
+        if (done || used != q || q > k) continue;
+        const uint32_t tag = (uint32_t)(wv[q] >> 56);
         if (tag == tag_inc || tag == tag_agg) {
-          excl += w[q] & ((1ull << 56) - 1);
+          excl += wv[q] & ((1ull << 56) - 1);
           ++used;
           if (tag == tag_inc) done = true;
         }
       }
       k -= used;
+      pk0 -= used * RS_BINS;
       if (!done && used == 0) {
         if (++spins > RS_WAIT_LIMIT) {
           atomicOr(err, F_TIMEOUT);
@@ -455,25 +518,14 @@ static __global__ void __launch_bounds__(RS_THREADS, 3) k_rs_onesweep(const uint
         __nanosleep(64);  // yield issue slots to the warps still ranking
       }
     }
-    rs_publish(&status[t * RS_BINS + b], tag_inc, excl + v);
+    rs_publish(my, tag_inc, excl + v);
   }
-  // Global start of this tile's run of digit b, and b's start inside the tile.
-  const int64_t dpre = block_excl_scan<int64_t>((int64_t)hist[b], sh, (int64_t *)nullptr);
-  const int64_t lp = block_excl_scan<int64_t>(v, sh, (int64_t *)nullptr);
-  gbase[b] = dpre + (int64_t)excl;
-  lpre[b] = (uint32_t)lp;
+  gofs[b] = (int64_t)(both >> 16) + (int64_t)excl - (int64_t)lp;
   __syncthreads();
-  const int w = threadIdx.x >> 5, l = lane_id();
-#pragma unroll
-  for (int q = 0; q < RS_ITEMS; ++q) {
-    const int idx = w * (32 * RS_ITEMS) + q * 32 + l;
-    if (idx < c) skey[lpre[digit_of(key[q], shift, mask)] + rank[q]] = key[q];
-  }
-  __syncthreads();
+  uint64_t *out = dst;
   for (int i = threadIdx.x; i < c; i += RS_THREADS) {
     const uint64_t k = skey[i];
-    const uint32_t d = digit_of(k, shift, mask);
-    dst[gbase[d] + (i - (int64_t)lpre[d])] = k;
+    out[gofs[pass_digit<HI>(k, sh, mask)] + i] = k;
   }
 }
 
@@ -615,7 +667,7 @@ struct RadixScratch {
   uint8_t *meta;
   int32_t *err;
 };
-inline int64_t rs_tiles(int64_t n) { return (n + RS_TILE - 1) / RS_TILE; }
+inline int64_t rs_tiles(int64_t n) { return (n + OS_TILE - 1) / OS_TILE; }  // tiles of a digit pass
 constexpr int64_t RS_META_HEAD = RS_MAX_PASSES * RS_BINS * 4 + 256;
 inline int64_t rs_meta_bytes(int64_t n) { return RS_META_HEAD + rs_tiles(n) * RS_BINS * 8; }
 
@@ -667,8 +719,13 @@ inline vr_status radix_sort(uint64_t *keys, int64_t n, int bit_lo, int nbits, co
   uint64_t *src = keys, *dst = sc.tkeys;
   for (int p = 0; p < passes; ++p) {
     tk_ = prof ? prof->begin(tag[1]) : -1;
-    launch_dep(k_rs_onesweep, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, bit_lo + 8 * p, digit_mask(nbits, p), p,
-               hist + p * RS_BINS, status, ticket + p, sc.err);
+    const int sh = bit_lo + 8 * p;
+    if (sh >= 32)
+      launch_dep(k_rs_onesweep<true>, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, sh - 32, digit_mask(nbits, p), p,
+                 hist + p * RS_BINS, status, ticket + p, sc.err);
+    else
+      launch_dep(k_rs_onesweep<false>, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, sh, digit_mask(nbits, p), p,
+                 hist + p * RS_BINS, status, ticket + p, sc.err);
     count_launch(1);
     if (prof) prof->end(tk_);
     VR_CUDA(cudaGetLastError());
