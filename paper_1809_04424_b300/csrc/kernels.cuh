@@ -1125,53 +1125,54 @@ static __global__ void __launch_bounds__(256) k_lex_tri_gen(const uint32_t *lexe
                                                             EdgeIndex ex, DevStatus *st, int force_lex) {
   pdl_entry();
   if (!lex_mode(E, st->ngrades, force_lex)) return;  // max-edge order (a launch ahead of the host's decision)
-  const int l = lane_id();
+  // Per warp: the third vertices of one 32-word chunk's candidates, in order
+  // (at most 32 x 32).  Each lane appends its word's set bits at its
+  // exclusive prefix; lane q then takes candidates q, q + 32, ...
+  __shared__ uint16_t cbuf[8][1024];
+  const int l = lane_id(), wid = threadIdx.x >> 5;
+  uint16_t *cb = cbuf[wid];
   const int64_t nwarps = (int64_t)gridDim.x * 8;
-  for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
+  for (int64_t e = blockIdx.x * 8 + wid; e < E; e += nwarps) {
     const uint32_t ab = lexe[e];
     const int a = (int)(ab >> ID_BITS), b = (int)(ab & ID_MASK);
-    int64_t t = toff[e];
-    const int32_t gab = ex.grade<DENSE>(a, b);
+    const int64_t t0 = toff[e];
+    uint64_t *out = tkeys + t0;
+    int64_t room = T - t0;  // keys that fit from out on
+    const uint64_t kab = lex3(a, b, 0);
     const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
     const int32_t *pa = adjpre + (int64_t)a * W, *pb = adjpre + (int64_t)b * W;
     const int32_t *oa = nbr_ord + nbr_ptr[a], *ob = nbr_ord + nbr_ptr[b];
+    const int32_t *ga = DENSE ? ex.egd + (int64_t)a * ex.n : nullptr;
+    const int32_t *gb = DENSE ? ex.egd + (int64_t)b * ex.n : nullptr;
+    const int32_t gab = ex.grade<DENSE>(a, b);
     for (int w0 = (b >> 5); w0 < W; w0 += 32) {
       const int w = w0 + l;
-      const uint32_t vm = w < W ? (ra[w] & rb[w] & above_mask(b, w)) : 0u;
+      uint32_t vm = w < W ? (ra[w] & rb[w] & above_mask(b, w)) : 0u;
       const int c = __popc(vm);
       const int inc = warp_incl_scan(c);
-      const int excl = inc - c;
       const int tot = __shfl_sync(0xffffffffu, inc, 31);
-      for (int q0 = 0; q0 < tot; q0 += 32) {
-        const int q = q0 + l;
-        int owner = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int cand = owner + step;
-          const int v = __shfl_sync(0xffffffffu, excl, cand & 31);
-          if (cand < 32 && v <= q) owner = cand;
+      if (tot == 0) continue;
+      for (int p = inc - c; vm; vm &= vm - 1) cb[p++] = (uint16_t)(w * 32 + __ffs(vm) - 1);
+      __syncwarp();
+      for (int q = l; q < tot; q += 32) {
+        const int cv = cb[q];
+        int32_t gac, gbc;
+        if constexpr (DENSE) {
+          gac = ga[cv];
+          gbc = gb[cv];
+        } else {
+          const int ww = cv >> 5;
+          const uint32_t below = (1u << (cv & 31)) - 1u;
+          gac = egrade[oa[pa[ww] + __popc(ra[ww] & below)]];
+          gbc = egrade[ob[pb[ww] + __popc(rb[ww] & below)]];
         }
-        const uint32_t ovm = __shfl_sync(0xffffffffu, vm, owner);
-        const int oex = __shfl_sync(0xffffffffu, excl, owner);
-        if (q < tot) {
-          const int bit = __fns(ovm, 0, q - oex + 1);
-          const int ww = w0 + owner;
-          const int cv = ww * 32 + bit;
-          int32_t gac, gbc;
-          if constexpr (DENSE) {
-            gac = ex.grade<true>(a, cv);
-            gbc = ex.grade<true>(b, cv);
-          } else {
-            const uint32_t below = (1u << bit) - 1u;
-            gac = egrade[oa[pa[ww] + __popc(ra[ww] & below)]];
-            gbc = egrade[ob[pb[ww] + __popc(rb[ww] & below)]];
-          }
-          const int32_t g = max(gab, max(gac, gbc));
-          if (t + q < T) tkeys[t + q] = ((uint64_t)g << LEX_SHIFT) | lex3(a, b, cv);
-          else raise_flag(st, F_INTERNAL);  // never write past the key array
-        }
+        const int32_t g = max(gab, max(gac, gbc));
+        if (q < room) out[q] = ((uint64_t)g << LEX_SHIFT) | kab | (uint64_t)cv;
+        else raise_flag(st, F_INTERNAL);  // never write past the key array
       }
-      t += tot;
+      __syncwarp();
+      out += tot;
+      room -= tot;
     }
   }
 }
