@@ -430,6 +430,21 @@ __device__ __forceinline__ int bit_owner(const BitChunk &r, int q) {
   return owner;
 }
 
+// Compaction of one round of per-lane masks m (lane l owns word w): the
+// columns w * 32 + bit of all set bits, in ascending order, land in the
+// warp's buffer cb (room for 32 x 32), each lane appending its own bits at its
+// exclusive prefix; returns the round's count.  The caller reads cb after a
+// __syncwarp and issues another before the buffer is reused.  Cheaper than
+// locating every candidate by search (bit_owner + __fns): a lane's loop runs
+// over its own set bits only.
+__device__ __forceinline__ int bit_compact(uint32_t m, int w, uint16_t *cb) {
+  const int c = __popc(m);
+  const int inc = warp_incl_scan(c);
+  for (int p = inc - c; m; m &= m - 1) cb[p++] = (uint16_t)(w * 32 + __ffs(m) - 1);
+  return __shfl_sync(0xffffffffu, inc, 31);
+}
+constexpr int CB_SLOTS = 1024;  // bit_compact buffer per warp
+
 __device__ __forceinline__ int32_t bit_rank(const uint32_t *adj_row, const int32_t *pre_row, int c) {
   const int w = c >> 5, b = c & 31;
   return pre_row[w] + __popc(adj_row[w] & ((1u << b) - 1u));
@@ -445,24 +460,24 @@ __global__ void __launch_bounds__(256) k_edge_keys(const void *Xv, int n, int d,
   pdl_entry();
   using T = typename std::conditional<F, float, int32_t>::type;
   __shared__ KeyHistSmem hs;
+  __shared__ uint16_t cbuf[8][CB_SLOTS];
   khist_init(hs, kh);
   const T *X = (const T *)Xv;
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int l = lane_id();
+  uint16_t *cb = cbuf[threadIdx.x >> 5];
   const uint32_t *row = adj + (int64_t)i * W;
   int64_t t = i < n ? lex_ptr[i] : 0;
   for (int w0 = (i + 1) >> 5; i < n && w0 < W; w0 += 32) {
     const int w = w0 + l;
     const uint32_t word = w < W ? row[w] & above_mask(i, w) : 0u;
-    const BitChunk r = bit_round(word);
-    for (int q0 = 0; q0 < r.tot; q0 += 32) {
+    const int tot = bit_compact(word, w, cb);
+    __syncwarp();
+    for (int q0 = 0; q0 < tot; q0 += 32) {
       const int q = q0 + l;
-      const int ow = bit_owner(r, q);
-      const uint32_t om = __shfl_sync(0xffffffffu, word, ow);
-      const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
       uint64_t key = 0;
-      if (q < r.tot) {
-        const int j = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
+      if (q < tot) {
+        const int j = cb[q];
         uint64_t dk;
         if constexpr (F) dk = (uint64_t)__float_as_uint(d2_f32(X + (int64_t)i * d, X + (int64_t)j * d, d));
         else dk = d2_int(X + (int64_t)i * d, X + (int64_t)j * d, d);
@@ -471,9 +486,10 @@ __global__ void __launch_bounds__(256) k_edge_keys(const void *Xv, int n, int d,
         lexe[t + q] = ((uint32_t)i << ID_BITS) | (uint32_t)j;
         if (elp) elp[(int64_t)i * n + j] = (int32_t)(t + q);  // lexicographic position (tetrahedra)
       }
-      khist_add(hs, kh, key, q < r.tot);
+      khist_add(hs, kh, key, q < tot);
     }
-    t += r.tot;
+    __syncwarp();
+    t += tot;
   }
   khist_flush(hs, kh);
 }
@@ -551,32 +567,33 @@ static __global__ void __launch_bounds__(256) k_dmat_keys(const void *Dv, int n,
                                                           int32_t *elp, KeyHist kh) {
   pdl_entry();
   __shared__ KeyHistSmem hs;
+  __shared__ uint16_t cbuf[8][CB_SLOTS];
   khist_init(hs, kh);
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int l = lane_id();
+  uint16_t *cb = cbuf[threadIdx.x >> 5];
   const uint32_t *row = adj + (int64_t)i * W;
   int64_t t = i < n ? lex_ptr[i] : 0;
   for (int w0 = (i + 1) >> 5; i < n && w0 < W; w0 += 32) {
     const int w = w0 + l;
     const uint32_t word = w < W ? row[w] & above_mask(i, w) : 0u;
-    const BitChunk r = bit_round(word);
-    for (int q0 = 0; q0 < r.tot; q0 += 32) {
+    const int tot = bit_compact(word, w, cb);
+    __syncwarp();
+    for (int q0 = 0; q0 < tot; q0 += 32) {
       const int q = q0 + l;
-      const int ow = bit_owner(r, q);
-      const uint32_t om = __shfl_sync(0xffffffffu, word, ow);
-      const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
       uint64_t key = 0;
-      if (q < r.tot) {
-        const int j = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
+      if (q < tot) {
+        const int j = cb[q];
         const uint64_t dk = dmat_key<F>(Dv, (int64_t)i * n + j);
         key = (dk << KEY_SHIFT) | ((uint64_t)i << ID_BITS) | (uint64_t)j;
         keys[t + q] = key;
         lexe[t + q] = ((uint32_t)i << ID_BITS) | (uint32_t)j;
         if (elp) elp[(int64_t)i * n + j] = (int32_t)(t + q);  // lexicographic position (tetrahedra)
       }
-      khist_add(hs, kh, key, q < r.tot);
+      khist_add(hs, kh, key, q < tot);
     }
-    t += r.tot;
+    __syncwarp();
+    t += tot;
   }
   khist_flush(hs, kh);
 }
@@ -621,27 +638,25 @@ __device__ __forceinline__ double soft_value(const SoftAcc &s) {
 static __global__ void __launch_bounds__(256) k_lex_edges(int n, int W, const uint32_t *adj, const int64_t *lex_ptr,
                                                           uint32_t *lexe, int32_t *elp) {
   pdl_entry();
+  __shared__ uint16_t cbuf[8][CB_SLOTS];
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int l = lane_id();
   if (i >= n) return;  // whole warps
+  uint16_t *cb = cbuf[threadIdx.x >> 5];
   const uint32_t *row = adj + (int64_t)i * W;
   int64_t t = lex_ptr[i];
   for (int w0 = (i + 1) >> 5; w0 < W; w0 += 32) {
     const int w = w0 + l;
     const uint32_t word = w < W ? row[w] & above_mask(i, w) : 0u;
-    const BitChunk r = bit_round(word);
-    for (int q0 = 0; q0 < r.tot; q0 += 32) {
-      const int q = q0 + l;
-      const int ow = bit_owner(r, q);
-      const uint32_t om = __shfl_sync(0xffffffffu, word, ow);
-      const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
-      if (q < r.tot) {
-        const int j = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
-        lexe[t + q] = ((uint32_t)i << ID_BITS) | (uint32_t)j;
-        if (elp) elp[(int64_t)i * n + j] = (int32_t)(t + q);
-      }
+    const int tot = bit_compact(word, w, cb);
+    __syncwarp();
+    for (int q = l; q < tot; q += 32) {
+      const int j = cb[q];
+      lexe[t + q] = ((uint32_t)i << ID_BITS) | (uint32_t)j;
+      if (elp) elp[(int64_t)i * n + j] = (int32_t)(t + q);
     }
-    t += r.tot;
+    __syncwarp();
+    t += tot;
   }
 }
 
@@ -1055,7 +1070,9 @@ static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts,
                                                           const DevStatus *st, int32_t *tcnt, int force_lex,
                                                           EdgeIndex ex) {
   pdl_entry();
+  __shared__ uint16_t cbuf[8][CB_SLOTS];
   const int l = lane_id();
+  uint16_t *cb = cbuf[threadIdx.x >> 5];
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   const bool lexm = lex_mode(E, st->ngrades, force_lex);
   for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
@@ -1079,32 +1096,25 @@ static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts,
       const int32_t *oa = nbr_ord + nbr_ptr[a], *ob = nbr_ord + nbr_ptr[b];
       for (int w0 = 0; w0 < W; w0 += 32) {
         const int w = w0 + l;
-        const uint32_t wa = w < W ? ra[w] : 0u, wb = w < W ? rb[w] : 0u;
-        const int32_t qa = !DENSE && w < W ? pa[w] : 0, qb = !DENSE && w < W ? pb[w] : 0;
-        const uint32_t m = wa & wb;
-        const BitChunk r = bit_round(m);
-        for (int q0 = 0; q0 < r.tot; q0 += 32) {
+        const uint32_t m = w < W ? ra[w] & rb[w] : 0u;
+        const int tot = bit_compact(m, w, cb);
+        __syncwarp();
+        for (int q0 = 0; q0 < tot; q0 += 32) {
           const int q = q0 + l;
-          const int ow = bit_owner(r, q);
-          const uint32_t om = __shfl_sync(0xffffffffu, m, ow);
-          const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
           bool ok = false;
-          if constexpr (DENSE) {
-            if (q < r.tot) {
-              const int cv = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
+          if (q < tot) {
+            const int cv = cb[q];
+            if constexpr (DENSE) {
               ok = ex.ord<true>(min(a, cv), max(a, cv)) < (int32_t)e && ex.ord<true>(min(b, cv), max(b, cv)) < (int32_t)e;
-            }
-          } else {
-            const uint32_t owa = __shfl_sync(0xffffffffu, wa, ow), owb = __shfl_sync(0xffffffffu, wb, ow);
-            const int32_t oqa = __shfl_sync(0xffffffffu, qa, ow), oqb = __shfl_sync(0xffffffffu, qb, ow);
-            if (q < r.tot) {
-              const int bit = __fns(om, 0, q - oex + 1);
-              const uint32_t below = (1u << bit) - 1u;
-              ok = oa[oqa + __popc(owa & below)] < (int32_t)e && ob[oqb + __popc(owb & below)] < (int32_t)e;
+            } else {
+              const int ww = cv >> 5;
+              const uint32_t below = (1u << (cv & 31)) - 1u;
+              ok = oa[pa[ww] + __popc(ra[ww] & below)] < (int32_t)e && ob[pb[ww] + __popc(rb[ww] & below)] < (int32_t)e;
             }
           }
           cnt += __popc(__ballot_sync(0xffffffffu, ok));
         }
+        __syncwarp();
       }
     }
     if (lexm) cnt = warp_sum(cnt);  // max-edge lanes already hold the warp total
@@ -1125,10 +1135,9 @@ static __global__ void __launch_bounds__(256) k_lex_tri_gen(const uint32_t *lexe
                                                             EdgeIndex ex, DevStatus *st, int force_lex) {
   pdl_entry();
   if (!lex_mode(E, st->ngrades, force_lex)) return;  // max-edge order (a launch ahead of the host's decision)
-  // Per warp: the third vertices of one 32-word chunk's candidates, in order
-  // (at most 32 x 32).  Each lane appends its word's set bits at its
-  // exclusive prefix; lane q then takes candidates q, q + 32, ...
-  __shared__ uint16_t cbuf[8][1024];
+  // Per warp: the third vertices of one 32-word chunk's candidates
+  // (bit_compact); lane q takes candidates q, q + 32, ...
+  __shared__ uint16_t cbuf[8][CB_SLOTS];
   const int l = lane_id(), wid = threadIdx.x >> 5;
   uint16_t *cb = cbuf[wid];
   const int64_t nwarps = (int64_t)gridDim.x * 8;
@@ -1147,12 +1156,9 @@ static __global__ void __launch_bounds__(256) k_lex_tri_gen(const uint32_t *lexe
     const int32_t gab = ex.grade<DENSE>(a, b);
     for (int w0 = (b >> 5); w0 < W; w0 += 32) {
       const int w = w0 + l;
-      uint32_t vm = w < W ? (ra[w] & rb[w] & above_mask(b, w)) : 0u;
-      const int c = __popc(vm);
-      const int inc = warp_incl_scan(c);
-      const int tot = __shfl_sync(0xffffffffu, inc, 31);
+      const uint32_t vm = w < W ? (ra[w] & rb[w] & above_mask(b, w)) : 0u;
+      const int tot = bit_compact(vm, w, cb);
       if (tot == 0) continue;
-      for (int p = inc - c; vm; vm &= vm - 1) cb[p++] = (uint16_t)(w * 32 + __ffs(vm) - 1);
       __syncwarp();
       for (int q = l; q < tot; q += 32) {
         const int cv = cb[q];
@@ -1248,11 +1254,10 @@ static __global__ void __launch_bounds__(256) k_tri_final(const uint64_t *tkeys,
   }
 }
 
-// Emission.  Each round (32 words, one per lane) the warp knows how many
-// triangles each lane's word holds; it then writes them in chunks of 32 with
-// lane q taking the round's q-th triangle, found by a 5-step search over the
-// lanes' prefix counts and __fns inside the owner's mask, so consecutive
-// lanes write consecutive output slots (coalesced stores).
+// Emission.  Each round (32 words, one per lane) the warp compacts the
+// candidates of its words (bit_compact) and checks them in chunks of 32, lane
+// q taking the round's q-th; the kept ones of a chunk take consecutive output
+// slots (ballot prefix), so stores are coalesced.
 // DENSE: the two edge positions of a candidate come from the dense
 // order-index table (one load each) instead of bitmap rank + CSR.
 template <bool DENSE>
@@ -1263,7 +1268,9 @@ static __global__ void __launch_bounds__(256) k_tri_emit(const int32_t *everts, 
                                                          int32_t *tgrade, int64_t *tcolptr, int32_t *trow,
                                                          EdgeIndex ex, DevStatus *st) {
   pdl_entry();
+  __shared__ uint16_t cbuf[8][CB_SLOTS];
   const int l = lane_id();
+  uint16_t *cb = cbuf[threadIdx.x >> 5];
   const uint32_t lt = lanemask_lt();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
@@ -1275,36 +1282,26 @@ static __global__ void __launch_bounds__(256) k_tri_emit(const int32_t *everts, 
     int64_t t = toff[e];
     for (int w0 = 0; w0 < W; w0 += 32) {
       const int w = w0 + l;
-      const uint32_t wa = w < W ? ra[w] : 0u, wb = w < W ? rb[w] : 0u;
-      const int32_t qa = !DENSE && w < W ? pa[w] : 0, qb = !DENSE && w < W ? pb[w] : 0;
-      const uint32_t m = wa & wb;
-      const BitChunk r = bit_round(m);
-      for (int q0 = 0; q0 < r.tot; q0 += 32) {
+      const uint32_t m = w < W ? ra[w] & rb[w] : 0u;
+      const int tot = bit_compact(m, w, cb);
+      __syncwarp();
+      for (int q0 = 0; q0 < tot; q0 += 32) {
         const int q = q0 + l;
-        const int ow = bit_owner(r, q);
-        const uint32_t om = __shfl_sync(0xffffffffu, m, ow);
-        const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
         bool ok = false;
         int cv = 0;
         int32_t oac = 0, obc = 0;
-        if constexpr (DENSE) {
-          if (q < r.tot) {
-            cv = (w0 + ow) * 32 + __fns(om, 0, q - oex + 1);
+        if (q < tot) {
+          cv = cb[q];
+          if constexpr (DENSE) {
             oac = ex.ord<true>(min(a, cv), max(a, cv));
             obc = ex.ord<true>(min(b, cv), max(b, cv));
-            ok = oac < (int32_t)e && obc < (int32_t)e;
+          } else {
+            const int ww = cv >> 5;
+            const uint32_t below = (1u << (cv & 31)) - 1u;
+            oac = oa[pa[ww] + __popc(ra[ww] & below)];
+            obc = ob[pb[ww] + __popc(rb[ww] & below)];
           }
-        } else {
-          const uint32_t owa = __shfl_sync(0xffffffffu, wa, ow), owb = __shfl_sync(0xffffffffu, wb, ow);
-          const int32_t oqa = __shfl_sync(0xffffffffu, qa, ow), oqb = __shfl_sync(0xffffffffu, qb, ow);
-          if (q < r.tot) {
-            const int bit = __fns(om, 0, q - oex + 1);
-            const uint32_t below = (1u << bit) - 1u;
-            cv = (w0 + ow) * 32 + bit;
-            oac = oa[oqa + __popc(owa & below)];
-            obc = ob[oqb + __popc(owb & below)];
-            ok = oac < (int32_t)e && obc < (int32_t)e;
-          }
+          ok = oac < (int32_t)e && obc < (int32_t)e;
         }
         const uint32_t bal = __ballot_sync(0xffffffffu, ok);
         if (ok && t + __popc(bal & lt) >= T) {  // never write past the outputs
@@ -1328,6 +1325,7 @@ static __global__ void __launch_bounds__(256) k_tri_emit(const int32_t *everts, 
         }
         t += __popc(bal);
       }
+      __syncwarp();
     }
   }
 }
@@ -1572,9 +1570,11 @@ static __global__ void __launch_bounds__(256) k_tet_gen(const uint64_t *tk_lex, 
                                                         int64_t T4, uint64_t *keys4, uint64_t *lex4, int packed,
                                                         DevStatus *st) {
   pdl_entry();
-  const int l = lane_id();
+  __shared__ uint16_t cbuf[8][CB_SLOTS];  // per warp: one chunk's fourth vertices (bit_compact)
+  const int l = lane_id(), wid = threadIdx.x >> 5;
+  uint16_t *cb = cbuf[wid];
   const int64_t nwarps = (int64_t)gridDim.x * 8;
-  for (int64_t t = blockIdx.x * 8 + (threadIdx.x >> 5); t < T; t += nwarps) {
+  for (int64_t t = blockIdx.x * 8 + wid; t < T; t += nwarps) {
     const uint64_t k3 = tk_lex[t] & LEX3_MASK;
     int a, b, c;
     lex3_unpack(k3, a, b, c);
@@ -1584,33 +1584,30 @@ static __global__ void __launch_bounds__(256) k_tet_gen(const uint64_t *tk_lex, 
     for (int w0 = c >> 5; w0 < W; w0 += 32) {
       const int w = w0 + l;
       const uint32_t vm = w < W ? (ra[w] & rb[w] & rc[w] & above_mask(c, w)) : 0u;
-      const BitChunk r = bit_round(vm);
-      for (int qq0 = 0; qq0 < r.tot; qq0 += 32) {
-        const int qq = qq0 + l;
-        const int ow = bit_owner(r, qq);
-        const uint32_t om = __shfl_sync(0xffffffffu, vm, ow);
-        const int oex = __shfl_sync(0xffffffffu, r.excl, ow);
-        if (qq < r.tot) {
-          const int d = (w0 + ow) * 32 + __fns(om, 0, qq - oex + 1);
-          int32_t g = g3;
-          g = max(g, ex.grade<DENSE>(a, d));
-          g = max(g, ex.grade<DENSE>(b, d));
-          g = max(g, ex.grade<DENSE>(c, d));
-          const int64_t q = q0 + qq;
-          if (q < T4) {
-            const uint64_t v4 = (k3 << ID_BITS) | (uint64_t)d;
-            if (packed) {
-              keys4[q] = ((uint64_t)(uint32_t)g << TET_PACK_SHIFT) | v4;
-            } else {
-              keys4[q] = ((uint64_t)(uint32_t)g << 32) | (uint64_t)q;
-              lex4[q] = v4;
-            }
+      const int tot = bit_compact(vm, w, cb);
+      if (tot == 0) continue;
+      __syncwarp();
+      for (int qq = l; qq < tot; qq += 32) {
+        const int d = cb[qq];
+        int32_t g = g3;
+        g = max(g, ex.grade<DENSE>(a, d));
+        g = max(g, ex.grade<DENSE>(b, d));
+        g = max(g, ex.grade<DENSE>(c, d));
+        const int64_t q = q0 + qq;
+        if (q < T4) {
+          const uint64_t v4 = (k3 << ID_BITS) | (uint64_t)d;
+          if (packed) {
+            keys4[q] = ((uint64_t)(uint32_t)g << TET_PACK_SHIFT) | v4;
           } else {
-            raise_flag(st, F_INTERNAL);  // never write past the key arrays
+            keys4[q] = ((uint64_t)(uint32_t)g << 32) | (uint64_t)q;
+            lex4[q] = v4;
           }
+        } else {
+          raise_flag(st, F_INTERNAL);  // never write past the key arrays
         }
       }
-      q0 += r.tot;
+      __syncwarp();
+      q0 += tot;
     }
   }
 }
