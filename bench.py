@@ -20,6 +20,7 @@ slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -132,6 +133,20 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6400.0, "fallback"
+
+
+class NoGC:
+    """The interpreter's cyclic garbage collector held off for a timed region
+    (collected first), so that no collection pause lands inside a step."""
+
+    def __enter__(self):
+        gc.collect()
+        gc.disable()
+        return self
+
+    def __exit__(self, *a):
+        gc.enable()
+        return False
 
 
 class Clocks:
@@ -417,7 +432,7 @@ def run_batch_bench(args):
     L.vr_profile_enable(1)
     launches0 = L.vr_launch_count()
     ranks.barrier()
-    with Clocks(local) as clk:
+    with NoGC(), Clocks(local) as clk:
         t0 = time.perf_counter()
         for _ in range(args.steps):
             b = vr.vr_build_batch(dev, off, 2, 40.0)
@@ -767,7 +782,7 @@ def main():
     ranks.barrier()
     torch.cuda.synchronize()
     launches0 = L.vr_launch_count()
-    with Clocks(local) as clk:
+    with NoGC(), Clocks(local) as clk:
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
@@ -820,11 +835,12 @@ def main():
         for _ in range(W):
             e2e_step()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
-        torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
+        with NoGC():
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                e2e_step()
+            torch.cuda.synchronize()
+            e2e_s = time.perf_counter() - t0
         d2h += gv.numel() * 8
         e2e_val = simplices * args.steps * world / e2e_s
 

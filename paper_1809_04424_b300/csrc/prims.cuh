@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(RS_THREADS, OS_MIN_BLOCKS) k_rs_onesweep(const
   // restarts the window there.
   uint64_t excl = 0;
   if (t > 0) {
-    constexpr int LB_WIN = 8;
+    constexpr int LB_WIN = 4;
     const uint64_t *pk0 = my - RS_BINS;  // tile t - 1
     int64_t k = t - 1;
     long spins = 0;
