@@ -1074,51 +1074,70 @@ static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts,
   const int l = lane_id();
   uint16_t *cb = cbuf[threadIdx.x >> 5];
   const int64_t nwarps = (int64_t)gridDim.x * 8;
-  const bool lexm = lex_mode(E, st->ngrades, force_lex);
-  for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
-    // Lex mode: e runs over the edges in lexicographic order (the count of
-    // edge e lands at e); max-edge mode: in filtration order.
-    int a, b;
-    if (lexm) {
-      const uint32_t ab = lexe[e];
-      a = (int)(ab >> ID_BITS);
-      b = (int)(ab & ID_MASK);
-    } else {
-      a = everts[2 * e];
-      b = everts[2 * e + 1];
-    }
-    const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
-    int cnt = 0;
-    if (lexm) {
-      for (int w = (b >> 5) + l; w < W; w += 32) cnt += __popc(ra[w] & rb[w] & above_mask(b, w));
-    } else {
-      const int32_t *pa = adjpre + (int64_t)a * W, *pb = adjpre + (int64_t)b * W;
-      const int32_t *oa = nbr_ord + nbr_ptr[a], *ob = nbr_ord + nbr_ptr[b];
-      for (int w0 = 0; w0 < W; w0 += 32) {
-        const int w = w0 + l;
-        const uint32_t m = w < W ? ra[w] & rb[w] : 0u;
-        const int tot = bit_compact(m, w, cb);
-        __syncwarp();
-        for (int q0 = 0; q0 < tot; q0 += 32) {
-          const int q = q0 + l;
-          bool ok = false;
-          if (q < tot) {
-            const int cv = cb[q];
-            if constexpr (DENSE) {
-              ok = ex.ord<true>(min(a, cv), max(a, cv)) < (int32_t)e && ex.ord<true>(min(b, cv), max(b, cv)) < (int32_t)e;
-            } else {
-              const int ww = cv >> 5;
-              const uint32_t below = (1u << (cv & 31)) - 1u;
-              ok = oa[pa[ww] + __popc(ra[ww] & below)] < (int32_t)e && ob[pb[ww] + __popc(rb[ww] & below)] < (int32_t)e;
-            }
-          }
-          cnt += __popc(__ballot_sync(0xffffffffu, ok));
-        }
-        __syncwarp();
+  if (lex_mode(E, st->ngrades, force_lex)) {
+    // Lex mode: edges in lexicographic order, the count of edge e (its
+    // triangles (a, b, c), c > b) at e: a popcount of the two rows above b.
+    // Four edges per warp at a time with all their first-round loads in
+    // flight together (one short dependent chain per edge otherwise leaves
+    // the kernel latency-bound).
+    constexpr int U = 4;
+    for (int64_t e0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * (int64_t)U; e0 < E; e0 += nwarps * U) {
+      int a[U], b[U], cnt[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t ab = e0 + u < E ? lexe[e0 + u] : 0u;
+        a[u] = (int)(ab >> ID_BITS);
+        b[u] = (int)(ab & ID_MASK);
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int w = (b[u] >> 5) + l;
+        cnt[u] = e0 + u < E && w < W
+                     ? __popc(adj[(int64_t)a[u] * W + w] & adj[(int64_t)b[u] * W + w] & above_mask(b[u], w))
+                     : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t *ra = adj + (int64_t)a[u] * W, *rb = adj + (int64_t)b[u] * W;
+        for (int w = (b[u] >> 5) + l + 32; e0 + u < E && w < W; w += 32) cnt[u] += __popc(ra[w] & rb[w]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) cnt[u] = warp_sum(cnt[u]);
+      if (l < U && e0 + l < E) tcnt[e0 + l] = l == 0 ? cnt[0] : l == 1 ? cnt[1] : l == 2 ? cnt[2] : cnt[3];
     }
-    if (lexm) cnt = warp_sum(cnt);  // max-edge lanes already hold the warp total
-    if (l == 0) tcnt[e] = cnt;
+    return;
+  }
+  // Max-edge mode: edges in filtration order; the count of edge e is the
+  // number of common neighbours c whose edges to a and b both come before e.
+  for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
+    const int a = everts[2 * e], b = everts[2 * e + 1];
+    const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
+    const int32_t *pa = adjpre + (int64_t)a * W, *pb = adjpre + (int64_t)b * W;
+    const int32_t *oa = nbr_ord + nbr_ptr[a], *ob = nbr_ord + nbr_ptr[b];
+    int cnt = 0;
+    for (int w0 = 0; w0 < W; w0 += 32) {
+      const int w = w0 + l;
+      const uint32_t m = w < W ? ra[w] & rb[w] : 0u;
+      const int tot = bit_compact(m, w, cb);
+      __syncwarp();
+      for (int q0 = 0; q0 < tot; q0 += 32) {
+        const int q = q0 + l;
+        bool ok = false;
+        if (q < tot) {
+          const int cv = cb[q];
+          if constexpr (DENSE) {
+            ok = ex.ord<true>(min(a, cv), max(a, cv)) < (int32_t)e && ex.ord<true>(min(b, cv), max(b, cv)) < (int32_t)e;
+          } else {
+            const int ww = cv >> 5;
+            const uint32_t below = (1u << (cv & 31)) - 1u;
+            ok = oa[pa[ww] + __popc(ra[ww] & below)] < (int32_t)e && ob[pb[ww] + __popc(rb[ww] & below)] < (int32_t)e;
+          }
+        }
+        cnt += __popc(__ballot_sync(0xffffffffu, ok));
+      }
+      __syncwarp();
+    }
+    if (l == 0) tcnt[e] = cnt;  // every lane holds the warp total
   }
 }
 
@@ -1548,14 +1567,29 @@ static __global__ void __launch_bounds__(256) k_tet_count(const uint64_t *tk_lex
   pdl_entry();
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
-  for (int64_t t = blockIdx.x * 8 + (threadIdx.x >> 5); t < T; t += nwarps) {
-    int a, b, c;
-    lex3_unpack(tk_lex[t], a, b, c);
-    const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W, *rc = adj + (int64_t)c * W;
-    int n4 = 0;
-    for (int w = (c >> 5) + l; w < W; w += 32) n4 += __popc(ra[w] & rb[w] & rc[w] & above_mask(c, w));
-    n4 = warp_sum(n4);
-    if (l == 0) cnt4[t] = n4;
+  // Four triangles per warp at a time, their first-round loads in flight
+  // together (as in k_tri_count's lex path).
+  constexpr int U = 4;
+  for (int64_t t0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * (int64_t)U; t0 < T; t0 += nwarps * U) {
+    int a[U], b[U], c[U], n4[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) lex3_unpack(t0 + u < T ? tk_lex[t0 + u] : 0ull, a[u], b[u], c[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int w = (c[u] >> 5) + l;
+      n4[u] = t0 + u < T && w < W
+                  ? __popc(adj[(int64_t)a[u] * W + w] & adj[(int64_t)b[u] * W + w] & adj[(int64_t)c[u] * W + w] &
+                           above_mask(c[u], w))
+                  : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t *ra = adj + (int64_t)a[u] * W, *rb = adj + (int64_t)b[u] * W, *rc = adj + (int64_t)c[u] * W;
+      for (int w = (c[u] >> 5) + l + 32; t0 + u < T && w < W; w += 32) n4[u] += __popc(ra[w] & rb[w] & rc[w]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) n4[u] = warp_sum(n4[u]);
+    if (l < U && t0 + l < T) cnt4[t0 + l] = l == 0 ? n4[0] : l == 1 ? n4[1] : l == 2 ? n4[2] : n4[3];
   }
 }
 
