@@ -546,7 +546,19 @@ static __device__ void cta_radix_sort_global(uint64_t *keys, uint32_t *vals, uin
     const uint32_t mask = digit_mask(nbits, p);
     for (int b = threadIdx.x; b < RS_BINS; b += RS_THREADS) cnt[b] = 0;
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < n; i += RS_THREADS) atomicAdd(&cnt[digit_of(src[i], shift, mask)], 1u);
+    // Eight loads in flight per thread before their counts (one dependent
+    // L2 round trip per key otherwise bounds small sorts).
+    for (int64_t i0 = 0; i0 < n; i0 += 8 * RS_THREADS) {
+      uint64_t k[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t i = i0 + u * RS_THREADS + threadIdx.x;
+        k[u] = i < n ? src[i] : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (i0 + u * RS_THREADS + threadIdx.x < n) atomicAdd(&cnt[digit_of(k[u], shift, mask)], 1u);
+    }
     __syncthreads();
     {
       int64_t v = threadIdx.x < RS_BINS ? (int64_t)cnt[threadIdx.x] : 0;
@@ -560,13 +572,19 @@ static __device__ void cta_radix_sort_global(uint64_t *keys, uint32_t *vals, uin
       uint32_t rank[RS_ITEMS];
       tile_rank(src, t0, c, shift, mask, key, rank, wcnt, cnt);
       const int w = threadIdx.x >> 5, l = lane_id();
+      uint32_t val[RS_ITEMS];
+#pragma unroll
+      for (int q = 0; q < RS_ITEMS; ++q) {
+        const int64_t idx = (int64_t)w * (32 * RS_ITEMS) + q * 32 + l;
+        val[q] = vs && idx < c ? vs[t0 + idx] : 0u;
+      }
 #pragma unroll
       for (int q = 0; q < RS_ITEMS; ++q) {
         int64_t idx = (int64_t)w * (32 * RS_ITEMS) + q * 32 + l;
         if (idx < c) {
           int64_t pos = base[digit_of(key[q], shift, mask)] + rank[q];
           dst[pos] = key[q];
-          if (vs) vd[pos] = vs[t0 + idx];
+          if (vs) vd[pos] = val[q];
         }
       }
       __syncthreads();
@@ -577,10 +595,24 @@ static __device__ void cta_radix_sort_global(uint64_t *keys, uint32_t *vals, uin
     uint32_t *tv = vs; vs = vd; vd = tv;
     __syncthreads();
   }
-  if (passes & 1) {  // result sits in the temporaries: copy back
-    for (int64_t i = threadIdx.x; i < n; i += RS_THREADS) {
-      keys[i] = tkeys[i];
-      if (vals) vals[i] = tvals[i];
+  if (passes & 1) {  // result sits in the temporaries: copy back, eight loads in flight per thread
+    for (int64_t i0 = 0; i0 < n; i0 += 8 * RS_THREADS) {
+      uint64_t k[8];
+      uint32_t v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t i = i0 + u * RS_THREADS + threadIdx.x;
+        k[u] = i < n ? tkeys[i] : 0ull;
+        v[u] = vals && i < n ? tvals[i] : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t i = i0 + u * RS_THREADS + threadIdx.x;
+        if (i < n) {
+          keys[i] = k[u];
+          if (vals) vals[i] = v[u];
+        }
+      }
     }
     __syncthreads();
   }
