@@ -548,15 +548,20 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   // 1.19 ms in max-edge mode).  Otherwise lex_mode decides by the edge count
   // and the share of tied grades.
   const int force_lex = (maxdim >= 3 || n > LEX_FORCE_N) ? 1 : 0;
+  // Lex-mode candidate walk: rows with fewer neighbours on average than
+  // bitmap words take their candidates from the lexicographic edge list (one
+  // bit test each) instead of walking the words above b (the 7322-point
+  // WorldMap-shaped cloud: 77 neighbours per point, 229 words per row).
+  const int sparse_rows = 2 * E < (int64_t)n * W ? 1 : 0;
   if (maxdim >= 2 && E > 0) {
     prof.begin("tri_count");
     const EdgeIndex exc{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
     if (eidx)
       launch_dep(k_tri_count<true>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
-                 nbr_ord, st, tcnt, force_lex, exc);
+                 nbr_ord, st, tcnt, force_lex, exc, (const int64_t *)lex_ptr, sparse_rows);
     else
       launch_dep(k_tri_count<false>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
-                 nbr_ord, st, tcnt, force_lex, exc);
+                 nbr_ord, st, tcnt, force_lex, exc, (const int64_t *)lex_ptr, sparse_rows);
     count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int64_t>(tcnt, toff, E, bs_e, s)));
     launch_dep(k_tri_groups, grid_for(E + 1, 256), 256, 0, s, gstart, tcnt, toff, tsmallq, tmidq, tbigq, st,
@@ -572,10 +577,10 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
     if (eidx)
       launch_dep(k_lex_tri_gen<true>, grid_for(E, 8, 148 * 32), 256, 0, s, lexe, egrade, E, adj, adjpre, W, nbr_ptr,
-                 nbr_ord, toff, tcap, tk, ex, st, force_lex);
+                 nbr_ord, toff, tcap, tk, ex, st, force_lex, (const int64_t *)lex_ptr, sparse_rows);
     else
       launch_dep(k_lex_tri_gen<false>, grid_for(E, 8, 148 * 32), 256, 0, s, lexe, egrade, E, adj, adjpre, W, nbr_ptr,
-                 nbr_ord, toff, tcap, tk, ex, st, force_lex);
+                 nbr_ord, toff, tcap, tk, ex, st, force_lex, (const int64_t *)lex_ptr, sparse_rows);
     count_launch();
     VR_CUDA(cudaGetLastError());
     prof.end();

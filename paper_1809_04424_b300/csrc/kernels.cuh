@@ -1068,12 +1068,35 @@ static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts,
                                                           const uint32_t *adj, const int32_t *adjpre, int W,
                                                           const int32_t *nbr_ptr, const int32_t *nbr_ord,
                                                           const DevStatus *st, int32_t *tcnt, int force_lex,
-                                                          EdgeIndex ex) {
+                                                          EdgeIndex ex, const int64_t *lex_ptr, int sparse) {
   pdl_entry();
   __shared__ uint16_t cbuf[8][CB_SLOTS];
   const int l = lane_id();
   uint16_t *cb = cbuf[threadIdx.x >> 5];
   const int64_t nwarps = (int64_t)gridDim.x * 8;
+  if (lex_mode(E, st->ngrades, force_lex) && sparse) {
+    // Lex mode on sparse rows (fewer neighbours than bitmap words): the
+    // candidates of edge e = (a, b) are a's neighbours above b, which are the
+    // lexicographic edges after e in row a; each is one bit test in row b.
+    for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
+      const uint32_t ab = lexe[e];
+      const int a = (int)(ab >> ID_BITS), b = (int)(ab & ID_MASK);
+      const int64_t end = lex_ptr[a + 1];
+      const uint32_t *rb = adj + (int64_t)b * W;
+      int cnt = 0;
+      for (int64_t q0 = e + 1; q0 < end; q0 += 32) {
+        const int64_t q = q0 + l;
+        bool ok = false;
+        if (q < end) {
+          const int c = (int)(lexe[q] & ID_MASK);
+          ok = (rb[c >> 5] >> (c & 31)) & 1u;
+        }
+        cnt += __popc(__ballot_sync(0xffffffffu, ok));
+      }
+      if (l == 0) tcnt[e] = cnt;
+    }
+    return;
+  }
   if (lex_mode(E, st->ngrades, force_lex)) {
     // Lex mode: edges in lexicographic order, the count of edge e (its
     // triangles (a, b, c), c > b) at e: a popcount of the two rows above b.
@@ -1151,9 +1174,45 @@ static __global__ void __launch_bounds__(256) k_lex_tri_gen(const uint32_t *lexe
                                                             const uint32_t *adj, const int32_t *adjpre, int W,
                                                             const int32_t *nbr_ptr, const int32_t *nbr_ord,
                                                             const int64_t *toff, int64_t T, uint64_t *tkeys,
-                                                            EdgeIndex ex, DevStatus *st, int force_lex) {
+                                                            EdgeIndex ex, DevStatus *st, int force_lex,
+                                                            const int64_t *lex_ptr, int sparse) {
   pdl_entry();
   if (!lex_mode(E, st->ngrades, force_lex)) return;  // max-edge order (a launch ahead of the host's decision)
+  if (sparse) {
+    // Sparse rows (as in k_tri_count): the candidates c of edge (a, b) are
+    // the lexicographic edges after it in row a, ascending; lane q tests the
+    // q-th in row b, and the kept ones of a round take consecutive slots.
+    const int l = lane_id();
+    const uint32_t lt = lanemask_lt();
+    const int64_t nwarps = (int64_t)gridDim.x * 8;
+    for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
+      const uint32_t ab = lexe[e];
+      const int a = (int)(ab >> ID_BITS), b = (int)(ab & ID_MASK);
+      const int64_t end = lex_ptr[a + 1];
+      const uint32_t *rb = adj + (int64_t)b * W;
+      int64_t t = toff[e];
+      const uint64_t kab = lex3(a, b, 0);
+      const int32_t gab = ex.grade<DENSE>(a, b);
+      for (int64_t q0 = e + 1; q0 < end; q0 += 32) {
+        const int64_t q = q0 + l;
+        bool ok = false;
+        int cv = 0;
+        if (q < end) {
+          cv = (int)(lexe[q] & ID_MASK);
+          ok = (rb[cv >> 5] >> (cv & 31)) & 1u;
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+          const int64_t p = t + __popc(bal & lt);
+          const int32_t g = max(gab, max(ex.grade<DENSE>(a, cv), ex.grade<DENSE>(b, cv)));
+          if (p < T) tkeys[p] = ((uint64_t)g << LEX_SHIFT) | kab | (uint64_t)cv;
+          else raise_flag(st, F_INTERNAL);  // never write past the key array
+        }
+        t += __popc(bal);
+      }
+    }
+    return;
+  }
   // Per warp: the third vertices of one 32-word chunk's candidates
   // (bit_compact); lane q takes candidates q, q + 32, ...
   __shared__ uint16_t cbuf[8][CB_SLOTS];

@@ -163,6 +163,19 @@ def test_lex_mode_beyond_early_triangle_limit(torch):
     assert len(c[1]["grade"]) > (1 << 17)
 
 
+@pytest.mark.parametrize("box,r,maxdim", [(15, 5.0, 2), (20, 4.0, 3)])
+def test_sparse_rows_lex_mode(torch, box, r, maxdim):
+    """Tie-heavy int8 clouds whose average degree (about 36 and 8) is below
+    the 79 bitmap words per row: lex order, with the candidates of each edge
+    taken from the lexicographic edge list (one bit test each), in full."""
+    g = synth.rng(1811)
+    pts = g.integers(-box, box + 1, size=(2500, 3)).astype(np.int8)
+    c = check(torch, pts, maxdim, r)
+    E = len(c[1]["grade"])
+    assert 2 * E < 2500 * ((2500 + 31) // 32)  # sparse rows
+    assert len(c[2]["grade"]) > 10000
+
+
 def test_worldmap_shaped_cloud(torch):
     """The WorldMap-shaped single cloud (n = 7322 float32 on the unit sphere,
     cap 0.15): 280,777 edges and 5,878,554 triangles, in full."""
