@@ -258,9 +258,11 @@ VR_API vr_status vr_server_destroy(vr_server *srv);
  * the bars are identical either way. */
 VR_API vr_status vr_set_barcode_dense_min(int64_t min_entries);
 
-/* Distance tiles: 0 = automatic (tensor-core Gram tiles for int8 input and
- * for float input with d <= 64, CUDA cores otherwise), 1 = the same, 2 = CUDA
- * cores always.  Process-wide; results are identical either way. */
+/* Distance tiles: 0 = automatic (tensor-core Gram tiles for int8 or float
+ * input with 16 < d <= 64 and enough 128-point tiles to fill the SMs twice,
+ * CUDA cores otherwise), 1 = tensor-core tiles whenever d <= 64 (int8 or
+ * float), 2 = CUDA cores always.  Process-wide; results are identical either
+ * way. */
 VR_API vr_status vr_set_gram_path(int32_t mode);
 
 /* Validation of the float Gram-tile error bound (no counterpart in the
