@@ -1724,8 +1724,23 @@ static __global__ void k_tet_final(const uint64_t *keys4, int64_t T4, const uint
     int32_t r[4];
     r[0] = ordidx[tri_lexpos(b, c, d, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr, elp, n, pre)];
     r[1] = ordidx[tri_lexpos(a, c, d, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr, elp, n, pre)];
-    r[2] = ordidx[tri_lexpos(a, b, d, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr, elp, n, pre)];
-    r[3] = ordidx[tri_lexpos(a, b, c, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr, elp, n, pre)];
+    if (pre && elp) {
+      // Faces (a, b, d) and (a, b, c) share their first edge: its position,
+      // triangle offset and the two rows' words above b, read once.
+      const int64_t lp = elp[(int64_t)a * n + b];
+      const int64_t base = toff[lp];
+      const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
+      const int wc = c >> 5, wd = d >> 5;
+      const uint32_t mc = ra[wc] & rb[wc] & above_mask(b, wc);
+      const uint32_t md = wd == wc ? mc : ra[wd] & rb[wd] & above_mask(b, wd);
+      const int64_t pc = base + pre[lp * W + wc] + __popc(mc & ((1u << (c & 31)) - 1u));
+      const int64_t pd = base + (wd == wc ? pre[lp * W + wc] : pre[lp * W + wd]) + __popc(md & ((1u << (d & 31)) - 1u));
+      r[2] = ordidx[pd];
+      r[3] = ordidx[pc];
+    } else {
+      r[2] = ordidx[tri_lexpos(a, b, d, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr, elp, n, pre)];
+      r[3] = ordidx[tri_lexpos(a, b, c, tk_lex, toff, adj, adjpre, W, deg, up, lex_ptr, elp, n, pre)];
+    }
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
