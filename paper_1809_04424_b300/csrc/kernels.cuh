@@ -1078,22 +1078,41 @@ static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts,
     // Lex mode on sparse rows (fewer neighbours than bitmap words): the
     // candidates of edge e = (a, b) are a's neighbours above b, which are the
     // lexicographic edges after e in row a; each is one bit test in row b.
-    for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
-      const uint32_t ab = lexe[e];
-      const int a = (int)(ab >> ID_BITS), b = (int)(ab & ID_MASK);
-      const int64_t end = lex_ptr[a + 1];
-      const uint32_t *rb = adj + (int64_t)b * W;
-      int cnt = 0;
-      for (int64_t q0 = e + 1; q0 < end; q0 += 32) {
-        const int64_t q = q0 + l;
-        bool ok = false;
-        if (q < end) {
-          const int c = (int)(lexe[q] & ID_MASK);
-          ok = (rb[c >> 5] >> (c & 31)) & 1u;
-        }
-        cnt += __popc(__ballot_sync(0xffffffffu, ok));
+    // Four edges per warp at a time, their first rounds' loads together.
+    constexpr int U = 4;
+    for (int64_t e0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * (int64_t)U; e0 < E; e0 += nwarps * U) {
+      int b[U], c[U], cnt[U];
+      int64_t end[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t ab = e0 + u < E ? lexe[e0 + u] : 0u;
+        b[u] = (int)(ab & ID_MASK);
+        end[u] = e0 + u < E ? lex_ptr[(ab >> ID_BITS) + 1] : 0;
       }
-      if (l == 0) tcnt[e] = cnt;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t q = e0 + u + 1 + l;
+        c[u] = q < end[u] ? (int)(lexe[q] & ID_MASK) : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const bool ok = c[u] >= 0 && ((adj[(int64_t)b[u] * W + (c[u] >> 5)] >> (c[u] & 31)) & 1u);
+        cnt[u] = __popc(__ballot_sync(0xffffffffu, ok));
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t *rb = adj + (int64_t)b[u] * W;
+        for (int64_t q0 = e0 + u + 1 + 32; q0 < end[u]; q0 += 32) {
+          const int64_t q = q0 + l;
+          bool ok = false;
+          if (q < end[u]) {
+            const int cv = (int)(lexe[q] & ID_MASK);
+            ok = (rb[cv >> 5] >> (cv & 31)) & 1u;
+          }
+          cnt[u] += __popc(__ballot_sync(0xffffffffu, ok));
+        }
+      }
+      if (l < U && e0 + l < E) tcnt[e0 + l] = l == 0 ? cnt[0] : l == 1 ? cnt[1] : l == 2 ? cnt[2] : cnt[3];
     }
     return;
   }
