@@ -406,10 +406,15 @@ __device__ __forceinline__ uint32_t pass_digit(uint64_t k, int sh, uint32_t mask
 // inclusive counts and writes the runs out.  A ragged last tile is padded
 // with all-ones keys: they take the largest digit, rank after every real key
 // of it and are neither counted nor written.
-constexpr int OS_ITEMS = 16;                    // keys per lane
-constexpr int OS_TILE = RS_THREADS * OS_ITEMS;  // keys per tile
-constexpr int OS_MIN_BLOCKS = 4;                // resident CTAs per SM the registers are sized for
-template <bool HI>
+// Tiles: OS_ITEMS keys per lane (4096 per tile, four CTAs per SM); sorts of
+// at most OS_SMALL_N keys take OS_SMALL_ITEMS per lane (1024 per tile, eight
+// CTAs per SM), so that a small sort spreads over more SMs.
+constexpr int OS_ITEMS = 16;
+constexpr int OS_TILE = RS_THREADS * OS_ITEMS;
+constexpr int OS_SMALL_ITEMS = 4;
+constexpr int OS_SMALL_TILE = RS_THREADS * OS_SMALL_ITEMS;
+constexpr int64_t OS_SMALL_N = 1 << 18;
+template <bool HI, int OS_ITEMS, int OS_MIN_BLOCKS>
 __global__ void __launch_bounds__(RS_THREADS, OS_MIN_BLOCKS) k_rs_onesweep(const uint64_t *src, uint64_t *dst, int64_t n,
                                                                int sh, uint32_t mask, int pass,
                                                                const uint32_t *hist, uint64_t *status,
@@ -417,6 +422,7 @@ __global__ void __launch_bounds__(RS_THREADS, OS_MIN_BLOCKS) k_rs_onesweep(const
   pdl_entry();
   __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];  // per-warp digit counts, then each warp's run starts
   __shared__ int64_t gofs[RS_BINS];             // global position of a run's slot 0 in skey
+  constexpr int OS_TILE = RS_THREADS * OS_ITEMS;
   __shared__ uint64_t skey[OS_TILE];
   __shared__ uint64_t scan_sh[33];
   __shared__ int64_t tile_sh;
@@ -699,9 +705,16 @@ struct RadixScratch {
   uint8_t *meta;
   int32_t *err;
 };
-inline int64_t rs_tiles(int64_t n) { return (n + OS_TILE - 1) / OS_TILE; }  // tiles of a digit pass
+inline int64_t rs_tiles(int64_t n) {  // tiles of a digit pass over n keys
+  return n <= OS_SMALL_N ? (n + OS_SMALL_TILE - 1) / OS_SMALL_TILE : (n + OS_TILE - 1) / OS_TILE;
+}
 constexpr int64_t RS_META_HEAD = RS_MAX_PASSES * RS_BINS * 4 + 256;
-inline int64_t rs_meta_bytes(int64_t n) { return RS_META_HEAD + rs_tiles(n) * RS_BINS * 8; }
+// Room for the status words of a sort of any m <= n keys, whichever tile size
+// m takes (callers size the scratch from an upper bound on the key count).
+inline int64_t rs_meta_bytes(int64_t n) {
+  const int64_t small = ((n < OS_SMALL_N ? n : OS_SMALL_N) + OS_SMALL_TILE - 1) / OS_SMALL_TILE;
+  return RS_META_HEAD + (small + (n + OS_TILE - 1) / OS_TILE) * RS_BINS * 8;
+}
 
 // Clear the sort's scratch (unless `zeroed`: the caller cleared at least
 // rs_meta_bytes(n) bytes of it) and return the histogram for a key generator
@@ -752,12 +765,22 @@ inline vr_status radix_sort(uint64_t *keys, int64_t n, int bit_lo, int nbits, co
   for (int p = 0; p < passes; ++p) {
     tk_ = prof ? prof->begin(tag[1]) : -1;
     const int sh = bit_lo + 8 * p;
-    if (sh >= 32)
-      launch_dep(k_rs_onesweep<true>, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, sh - 32, digit_mask(nbits, p), p,
-                 hist + p * RS_BINS, status, ticket + p, sc.err);
-    else
-      launch_dep(k_rs_onesweep<false>, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, sh, digit_mask(nbits, p), p,
-                 hist + p * RS_BINS, status, ticket + p, sc.err);
+    const uint32_t dm = digit_mask(nbits, p);
+    if (n <= OS_SMALL_N) {
+      if (sh >= 32)
+        launch_dep(k_rs_onesweep<true, OS_SMALL_ITEMS, 8>, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, sh - 32, dm, p,
+                   hist + p * RS_BINS, status, ticket + p, sc.err);
+      else
+        launch_dep(k_rs_onesweep<false, OS_SMALL_ITEMS, 8>, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, sh, dm, p,
+                   hist + p * RS_BINS, status, ticket + p, sc.err);
+    } else {
+      if (sh >= 32)
+        launch_dep(k_rs_onesweep<true, OS_ITEMS, 4>, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, sh - 32, dm, p,
+                   hist + p * RS_BINS, status, ticket + p, sc.err);
+      else
+        launch_dep(k_rs_onesweep<false, OS_ITEMS, 4>, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, sh, dm, p,
+                   hist + p * RS_BINS, status, ticket + p, sc.err);
+    }
     count_launch(1);
     if (prof) prof->end(tk_);
     VR_CUDA(cudaGetLastError());
