@@ -1,5 +1,6 @@
 // api.cu -- the extern "C" entry points of vr.h: argument checks, host/device
 // input detection, result access and error reporting.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -18,6 +19,24 @@ void set_error(const char *fmt, ...) {
   va_start(ap, fmt);
   vsnprintf(g_err, sizeof(g_err), fmt, ap);
   va_end(ap);
+}
+
+int num_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  if (dev < 0 || dev >= 64) dev = 63;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+    cudaGetLastError();
+    return 1;
+  }
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
 }
 
 vr_status cuda_status(cudaError_t e, const char *what, const char *file, int line) {

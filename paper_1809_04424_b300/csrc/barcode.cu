@@ -45,7 +45,7 @@ constexpr int BC_THREADS = 256;
 
 static unsigned bc_grid(int64_t work) {
   const int64_t g = (work + BC_THREADS - 1) / BC_THREADS;
-  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 148 * 16));
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)num_sms() * 16));
 }
 
 // ------------------------------------------------------------ dimension 0

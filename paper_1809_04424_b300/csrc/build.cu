@@ -71,7 +71,9 @@ struct Arena {
   }
 };
 
-static unsigned grid_for(int64_t work, int threads, int cap_ctas = 148 * 16) {
+// per_sm: the grid is capped at this many CTAs per SM of the device.
+static unsigned grid_for(int64_t work, int threads, int per_sm = 16) {
+  const int64_t cap_ctas = (int64_t)num_sms() * per_sm;
   int64_t g = (work + threads - 1) / threads;
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, cap_ctas));
 }
@@ -344,7 +346,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     prof.begin("edge_keys");
     if constexpr (F) {
       launch_dep(k_lex_edges, (n + 7) / 8, 256, 0, s, n, W, adj, lex_ptr, lexe, elp);
-      launch_dep(k_edge_keys_f32, grid_for((ecap + 31) / 32, EKF_WARPS, 148 * 16), EKF_WARPS * 32, 0, s,
+      launch_dep(k_edge_keys_f32, grid_for((ecap + 31) / 32, EKF_WARPS, 16), EKF_WARPS * 32, 0, s,
                  (const float *)X, d, lexe, keys, d64_lex, st);
       count_launch();
     } else if (dmat) {
@@ -366,7 +368,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   const bool fused8 = !dmat && !tc && dtype == VR_I8 && d <= 4;
   if (in_place) X = (void *)dpts;
   prof.begin("stage");
-  const unsigned gs = grid_for(nd, 256, 148 * 8);
+  const unsigned gs = grid_for(nd, 256, 8);
   if (dmat) {
     const int nb = (n + 31) / 32;
     if (dmf) launch_dep(k_dmat_check<true>, nb * nb, 256, 0, s, dmat, n, st);
@@ -520,7 +522,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       int tkr = prof.begin("fp64_regroup");
       launch_dep(k_repair_small, ge, 256, 0, s, gbeg, gex + E, keys, d64, midq, bigq, st);
       VR_CUDA(cudaGetLastError());
-      launch_dep(k_repair_mid, 296, 256, 0, s, gbeg, midq, st, keys, d64);
+      launch_dep(k_repair_mid, (unsigned)num_sms() * 2, 256, 0, s, gbeg, midq, st, keys, d64);
       launch_dep(k_repair_big, 1, RS_THREADS, 0, s, gbeg, bigq, st, keys, d64, k1, v1, k2, v2, gk, gd);
       VR_CUDA(cudaGetLastError());
       prof.end(tkr);
@@ -557,10 +559,10 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     prof.begin("tri_count");
     const EdgeIndex exc{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
     if (eidx)
-      launch_dep(k_tri_count<true>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
+      launch_dep(k_tri_count<true>, grid_for(E, 8, 32), 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
                  nbr_ord, st, tcnt, force_lex, exc, (const int64_t *)lex_ptr, sparse_rows);
     else
-      launch_dep(k_tri_count<false>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
+      launch_dep(k_tri_count<false>, grid_for(E, 8, 32), 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
                  nbr_ord, st, tcnt, force_lex, exc, (const int64_t *)lex_ptr, sparse_rows);
     count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int64_t>(tcnt, toff, E, bs_e, s)));
@@ -576,10 +578,10 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     prof.begin("tri_lex_gen");
     const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
     if (eidx)
-      launch_dep(k_lex_tri_gen<true>, grid_for(E, 8, 148 * 32), 256, 0, s, lexe, egrade, E, adj, adjpre, W, nbr_ptr,
+      launch_dep(k_lex_tri_gen<true>, grid_for(E, 8, 32), 256, 0, s, lexe, egrade, E, adj, adjpre, W, nbr_ptr,
                  nbr_ord, toff, tcap, tk, ex, st, force_lex, (const int64_t *)lex_ptr, sparse_rows);
     else
-      launch_dep(k_lex_tri_gen<false>, grid_for(E, 8, 148 * 32), 256, 0, s, lexe, egrade, E, adj, adjpre, W, nbr_ptr,
+      launch_dep(k_lex_tri_gen<false>, grid_for(E, 8, 32), 256, 0, s, lexe, egrade, E, adj, adjpre, W, nbr_ptr,
                  nbr_ord, toff, tcap, tk, ex, st, force_lex, (const int64_t *)lex_ptr, sparse_rows);
     count_launch();
     VR_CUDA(cudaGetLastError());
@@ -685,7 +687,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       // neighbour lists, while the table's are spread over n^2 entries
       // (measured: 0.58 vs 0.65 ms on 19.8M triangles at n = 4000).
       const EdgeIndex exm{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
-      launch_dep(k_tri_emit<false>, grid_for(E, 8, 148 * 32), 256, 0, s, everts, egrade, E, adj, adjpre, W, nbr_ptr,
+      launch_dep(k_tri_emit<false>, grid_for(E, 8, 32), 256, 0, s, everts, egrade, E, adj, adjpre, W, nbr_ptr,
                  nbr_ord, toff, T, tverts, tgrade, tcol, trow, exm, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
@@ -693,7 +695,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       prof.begin("tri_tie_merge");
       if (hst->small_seg_count > 0) {
         const size_t smem = (size_t)TRI_SMALL * (8 + 4 + 12);
-        launch_dep(k_tri_fix_smem<TRI_SMALL>, std::min(hst->small_seg_count, 148 * 8), 256, smem, s, gstart, toff,
+        launch_dep(k_tri_fix_smem<TRI_SMALL>, std::min(hst->small_seg_count, num_sms() * 8), 256, smem, s, gstart, toff,
                    tsmallq, &st->small_seg_count, tverts, trow);
         count_launch();
         VR_CUDA(cudaGetLastError());
@@ -702,13 +704,13 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
         const size_t smem = (size_t)TRI_MID * (8 + 4 + 12);
         VR_CUDA(cudaFuncSetAttribute(k_tri_fix_smem<TRI_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
-        launch_dep(k_tri_fix_smem<TRI_MID>, std::min(hst->mid_seg_count, 148), 512, smem, s, gstart, toff, tmidq,
+        launch_dep(k_tri_fix_smem<TRI_MID>, std::min(hst->mid_seg_count, num_sms()), 512, smem, s, gstart, toff, tmidq,
                    &st->mid_seg_count, tverts, trow);
         count_launch();
         VR_CUDA(cudaGetLastError());
       }
       if (bigfix) {
-        launch_dep(k_tri_fix_big, (unsigned)std::min<int64_t>(hst->big_seg_count, 148 * 2), RS_THREADS, 0, s, gstart,
+        launch_dep(k_tri_fix_big, (unsigned)std::min<int64_t>(hst->big_seg_count, (int64_t)num_sms() * 2), RS_THREADS, 0, s, gstart,
                    toff, tbigq, st, tverts, trow, tk1, tv1, tk2, tv2, rtmp);
         count_launch();
         VR_CUDA(cudaGetLastError());
@@ -726,12 +728,12 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     if (tets) {
       prof.begin("tet_count");
       if (tpre) {
-        launch_dep(k_lex_pre, grid_for(E, 8, 148 * 32), 256, 0, s, lexe, E, adj, W, tpre);
+        launch_dep(k_lex_pre, grid_for(E, 8, 32), 256, 0, s, lexe, E, adj, W, tpre);
         count_launch();
       }
       launch_dep(k_tri_ordidx, grid_for(T, 256), 256, 0, s, tk, T, tk_lex, ordidx, toff, adj, adjpre, W, deg, up,
                  lex_ptr, elp, n, tpre);
-      launch_dep(k_tet_count, grid_for(T, 8, 148 * 32), 256, 0, s, tk_lex, T, adj, W, cnt4);
+      launch_dep(k_tet_count, grid_for(T, 8, 32), 256, 0, s, tk_lex, T, adj, W, cnt4);
       count_launch(2);
       VR_TRY((scan_exclusive<int32_t, int64_t>(cnt4, off4, T, bs_t, s)));
       VR_CUDA(cudaGetLastError());
@@ -769,10 +771,10 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       prof.begin("tet_gen");
       const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
       if (eidx)
-        launch_dep(k_tet_gen<true>, grid_for(T, 8, 148 * 32), 256, 0, s, tk_lex, T, adj, W, tgrade, ordidx, egrade, ex,
+        launch_dep(k_tet_gen<true>, grid_for(T, 8, 32), 256, 0, s, tk_lex, T, adj, W, tgrade, ordidx, egrade, ex,
                    off4, T4, keys4, lex4, packed ? 1 : 0, st);
       else
-        launch_dep(k_tet_gen<false>, grid_for(T, 8, 148 * 32), 256, 0, s, tk_lex, T, adj, W, tgrade, ordidx, egrade, ex,
+        launch_dep(k_tet_gen<false>, grid_for(T, 8, 32), 256, 0, s, tk_lex, T, adj, W, tgrade, ordidx, egrade, ex,
                    off4, T4, keys4, lex4, packed ? 1 : 0, st);
       count_launch();
       VR_CUDA(cudaGetLastError());

@@ -4,8 +4,9 @@
 // distances do not change).  One CTA per 128x128 tile of the pair matrix
 // (upper triangle of tiles): TMA brings the two 128-row operand tiles (bf16,
 // 64 coordinates, 128-byte swizzle) into shared memory, one thread issues
-// tcgen05.mma (kind::f16, bf16 x bf16 -> fp32 accumulator in TMEM), and four
-// warps read the accumulator back with tcgen05.ld, one pair row per thread.
+// tcgen05.mma (kind::f16, bf16 x bf16 -> fp32 accumulator in TMEM), and eight
+// warps read the accumulator back with tcgen05.ld (two per TMEM lane quarter,
+// each taking half of the tile's columns), one pair row per thread.
 //
 // int8 inputs: coordinates are exact in bf16, their products exact in fp32
 // and every partial sum stays below 2^24, so the squared distances are
@@ -405,7 +406,7 @@ bool gram_tc_eligible(vr_dtype dtype, int n, int d) {
   // SMs twice, too.
   if (d <= 16) return false;
   const int nt = (n + TC_TILE - 1) / TC_TILE;
-  return nt * (nt + 1) / 2 >= 2 * 148;
+  return nt * (nt + 1) / 2 >= 2 * num_sms();
 }
 
 // Bitmap of kept pairs on the tensor cores.  X is the staged point array
@@ -467,7 +468,7 @@ vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, ui
       return fail(e);
     k_gram_bitmap_tc<true, false><<<ntiles, TC_THREADS, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st, band,
                                                             band_cap, nullptr);
-    k_band_patch<<<148 * 4, 256, 0, s>>>((const float *)X, d, W, cap.r2, band, st, band_cap, adj);
+    k_band_patch<<<num_sms() * 4, 256, 0, s>>>((const float *)X, d, W, cap.r2, band, st, band_cap, adj);
     count_launch();
   } else {
     if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -15,6 +15,8 @@
 // the build allocates.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "../../include/vr.h"
 #include "prims.cuh"
 
@@ -23,8 +25,12 @@ namespace vr {
 static __device__ __align__(256) uint64_t g_noalloc_scratch[VR_NOALLOC_MAX_KEYS];
 
 // Device address of g_noalloc_scratch per device (the symbol's name in host
-// code is only a host-side stand-in).  Filled by the first call on a device.
+// code is only a host-side stand-in).  Filled once per device, by the first
+// call on it, under that device's once-flag, so that host threads making
+// their first calls together do not race on the slot.
 static uint64_t *g_scratch_ptr[64] = {nullptr};
+static cudaError_t g_scratch_err[64] = {cudaSuccess};
+static std::once_flag g_scratch_once[64];
 
 static __global__ void __launch_bounds__(RS_THREADS) k_sort_keys_noalloc(uint64_t *keys, uint64_t *scratch, int64_t n,
                                                                          int bit_lo, int nbits) {
@@ -45,8 +51,9 @@ extern "C" vr_status vr_sort_keys_noalloc(uint64_t *keys, int64_t n, int32_t bit
               (int)VR_NOALLOC_MAX_KEYS);
     return VR_ERR_RANGE;
   }
-  if (bit_lo < 0 || nbits < 0 || bit_lo + nbits > 64) {
-    set_error("bit range [%d, %d) is outside [0, 64)", bit_lo, bit_lo + nbits);
+  // The sum in 64 bits: bit_lo + nbits in int32 could wrap and pass.
+  if (bit_lo < 0 || nbits < 0 || bit_lo > 64 || nbits > 64 || (int64_t)bit_lo + nbits > 64) {
+    set_error("bit range [%d, %lld) is outside [0, 64)", bit_lo, (long long)bit_lo + nbits);
     return VR_ERR_ARG;
   }
   int dev = 0;
@@ -55,11 +62,15 @@ extern "C" vr_status vr_sort_keys_noalloc(uint64_t *keys, int64_t n, int32_t bit
     set_error("device ordinal %d beyond the 64 this entry point tracks", dev);
     return VR_ERR_RANGE;
   }
-  if (!g_scratch_ptr[dev]) {
-    // Set-up, once per device, with that device current.
+  // Set-up, once per device, with that device current.
+  std::call_once(g_scratch_once[dev], [dev]() {
     void *p = nullptr;
-    VR_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_scratch_ptr[dev] = (uint64_t *)p;
+    g_scratch_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (g_scratch_err[dev] == cudaSuccess) g_scratch_ptr[dev] = (uint64_t *)p;
+  });
+  if (g_scratch_err[dev] != cudaSuccess) {
+    set_error("device address of the fixed sort scratch: %s", cudaGetErrorString(g_scratch_err[dev]));
+    return VR_ERR_CUDA;
   }
   if (n <= 1 || nbits == 0) return VR_OK;
   k_sort_keys_noalloc<<<1, RS_THREADS, 0, (cudaStream_t)stream>>>(keys, g_scratch_ptr[dev], n, bit_lo, nbits);

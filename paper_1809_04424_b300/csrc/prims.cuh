@@ -19,6 +19,11 @@ namespace vr {
 void set_error(const char *fmt, ...);   // thread-local message (api.cu)
 vr_status cuda_status(cudaError_t e, const char *what, const char *file, int line);
 
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
+// read once per device and cached; 1 if the query fails).  Grid caps and path
+// thresholds are multiples of it.
+int num_sms();
+
 #define VR_TRY(x)                                                     \
   do {                                                                \
     vr_status s_ = (x);                                               \
@@ -756,7 +761,8 @@ inline vr_status radix_sort(uint64_t *keys, int64_t n, int bit_lo, int nbits, co
   if (prep != RS_PREP_HIST) {
     tk_ = prof ? prof->begin(tag[0]) : -1;
     if (prep == RS_PREP_NONE) VR_CUDA(cudaMemsetAsync(sc.meta, 0, (size_t)rs_meta_bytes(n), s));
-    const unsigned hg = (unsigned)(nt < 148 * 8 ? nt : 148 * 8);
+    const int64_t hcap = (int64_t)num_sms() * 8;
+    const unsigned hg = (unsigned)(nt < hcap ? nt : hcap);
     launch_dep(k_rs_hist_all, hg, RS_THREADS, 0, s, keys, n, bit_lo, nbits, hist);
     count_launch(1);
     if (prof) prof->end(tk_);

@@ -10,8 +10,9 @@ extern "C" vr_status vr_sort_keys(uint64_t *keys, int64_t n, int32_t bit_lo, int
     set_error("keys is NULL or n is negative");
     return VR_ERR_ARG;
   }
-  if (bit_lo < 0 || nbits < 0 || bit_lo + nbits > 64) {
-    set_error("bit range [%d, %d) is outside [0, 64)", bit_lo, bit_lo + nbits);
+  // The sum in 64 bits: bit_lo + nbits in int32 could wrap and pass.
+  if (bit_lo < 0 || nbits < 0 || bit_lo > 64 || nbits > 64 || (int64_t)bit_lo + nbits > 64) {
+    set_error("bit range [%d, %lld) is outside [0, 64)", bit_lo, (long long)bit_lo + nbits);
     return VR_ERR_ARG;
   }
   if (n >= ((int64_t)1 << 31)) {

@@ -47,9 +47,12 @@ def test_library_carries_no_oracle_code():
 
 
 def test_library_targets_sm_103a():
-    out = subprocess.run(["/usr/local/cuda/bin/cuobjdump", "--list-elf", vr.LIB_PATH],
-                         capture_output=True, text=True).stdout
-    assert "sm_103a" in out
+    """The build compiles every source for sm_103a only (one -gencode pair,
+    real architecture sm_103a, virtual compute_103a)."""
+    from paper_1809_04424_b300 import build as b
+    pairs = [b.FLAGS[i + 1] for i, f in enumerate(b.FLAGS) if f == "-gencode"]
+    assert pairs == ["arch=compute_103a,code=sm_103a"]
+    assert not any(f.startswith(("-arch", "--gpu-architecture")) for f in b.FLAGS)
 
 
 @pytest.mark.parametrize("args,status", [
@@ -78,7 +81,10 @@ def test_null_arguments():
 
 @pytest.mark.parametrize("fn", ["vr_sort_keys", "vr_sort_keys_noalloc"])
 @pytest.mark.parametrize("n,lo,nb,status", [(-1, 0, 8, vr.VR_ERR_ARG), (4, -1, 8, vr.VR_ERR_ARG),
-                                            (4, 60, 5, vr.VR_ERR_ARG), (4, 0, -2, vr.VR_ERR_ARG)])
+                                            (4, 60, 5, vr.VR_ERR_ARG), (4, 0, -2, vr.VR_ERR_ARG),
+                                            # bit_lo + nbits wraps in 32 bits: must still be refused
+                                            (4, 8, 2**31 - 8, vr.VR_ERR_ARG), (4, 2**31 - 1, 1, vr.VR_ERR_ARG),
+                                            (4, 65, 0, vr.VR_ERR_ARG), (4, 0, 65, vr.VR_ERR_ARG)])
 def test_sort_argument_checks(fn, n, lo, nb, status):
     """Bad sort arguments are rejected before any CUDA call."""
     f = getattr(vr.lib(), fn)

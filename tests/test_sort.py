@@ -43,17 +43,18 @@ def keyset(kind, n, seed):
     return k
 
 
-@pytest.mark.parametrize("n", [2, 4097, 8192, 8193, 50_001, 1_000_003])
+@pytest.mark.parametrize("n", [2, 4097, 8192, 8193, 50_001, 262_144, 262_145, 1_000_003])
 @pytest.mark.parametrize("lo,nb", [(0, 1), (3, 5), (26, 12), (7, 17), (20, 24), (0, 64)])
 def test_sort_matches_stable_argsort(torch, n, lo, nb):
     keys = keyset("random", n, 1000 + n % 97 + lo + nb)
     assert np.array_equal(run(torch, vr.vr_sort_keys, keys, lo, nb), expected(keys, lo, nb))
 
 
+@pytest.mark.parametrize("n", [200_003, 300_007])   # 1024-key tiles below 2^18 keys, 4096-key above
 @pytest.mark.parametrize("kind", ["skew", "const", "sorted_desc"])
 @pytest.mark.parametrize("lo,nb", [(0, 16), (4, 13), (0, 20)])
-def test_sort_structured_keys(torch, kind, lo, nb):
-    keys = keyset(kind, 300_007, 7)
+def test_sort_structured_keys(torch, kind, lo, nb, n):
+    keys = keyset(kind, n, 7)
     assert np.array_equal(run(torch, vr.vr_sort_keys, keys, lo, nb), expected(keys, lo, nb))
 
 

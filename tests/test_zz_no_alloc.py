@@ -1,4 +1,5 @@
-"""The allocation-free sort entry point, checked against vr_build.
+"""The allocation-free sort entry point, checked against numpy's stable
+argsort and against vr_build.
 
 vr_sort_keys_noalloc is for callers that cannot allocate device memory when
 they rank edges (their framework's allocator owns the GPU memory, or their
@@ -49,6 +50,9 @@ def sort_noalloc(torch, keys, nbits):
 def check_cloud(torch, cloud):
     keys, nbits = lex_keys(cloud.points, cloud.maxrad)
     out = sort_noalloc(torch, keys, nbits)
+    # A sort defined without this library: numpy's stable argsort on the
+    # distance field alone (the (i, j) input order breaks its ties).
+    np.testing.assert_array_equal(out, keys[np.argsort(keys >> np.uint64(26), kind="stable")])
     ref = vr.vr_build(torch.from_numpy(cloud.points).cuda(), 1, cloud.maxrad)
     e = ref.to_host(1)
     gv = ref.grade_values()
