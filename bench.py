@@ -1,8 +1,10 @@
-"""Benchmark: VR filtered-complex build throughput (simplices/s) on one cloud.
+"""Benchmark: VR filtered-complex build throughput (simplices/s), with the
+batched and served forms nested in the same line.
 
-Workload (default): 1000 points on a torus (R=3, r=1) + N(0, 0.05^2) noise,
-scaled by 30 to an int8 grid, radius cap at the 15th-percentile pairwise
-squared distance, simplices up to dimension 2 (vertices, edges, triangles).
+Workload (default): 4000 points in R^32, float32, a mixture of 8 isotropic
+Gaussians (centres uniform in [-5, 5]^32, sigma 1), radius cap at the 5th
+percentile of pairwise squared distance, simplices up to dimension 2
+(vertices, edges, triangles: 19.76M triangles per build).
 
 One step = one complete vr_build (distances, cap, ranking, enumeration,
 (grade, lex) order, boundary CSC) from device-resident points; its result is
@@ -11,11 +13,20 @@ steps, outside the per-step events.  e2e repeats the step through the same
 C-ABI call with the points in pinned host memory and copies every output
 array back to pinned host memory inside the timed region.
 
+Nested in the default line (skip with --no-nested):
+  batched: 4096 uneven sphere clouds (n ~ U[32, 512], int8, maxdim 2) in one
+           vr_build_batch per step, against one vr_build per cloud on every
+           cloud, and the oracle run across clouds on all host cores;
+  served:  a Poisson stream of 20000 mixed requests through the continuous-
+           batching server at 0.8x its closed-loop capacity (p50/p99 latency,
+           clouds/s), against one vr_build per request in arrival order, and
+           the oracle across requests on all host cores on a bounded sample.
+
 --impl reference times the plain CPU oracle (the correctness reference) on
 the host cores on the same workload; it is a deliberately slow program.
 Multi-GPU (torchrun): the single-cloud build does not shard, so every rank
 builds its own replica ("replicas only"); value = all ranks' simplices / the
-slowest rank's time.
+slowest rank's time.  Batches and streams shard by cloud.
 """
 from __future__ import annotations
 
@@ -67,31 +78,41 @@ def gpu_build(cloud, src, **kw):
         return vr.vr_build_dmat(src, cloud.maxdim, cloud.maxrad, **kw)
     return vr.vr_build(src, cloud.maxdim, cloud.maxrad, **kw)
 METRIC = "VR simplices/s"
+DEFAULT_CONFIG = "gauss32"
 
-# Algorithmic bytes per unit of each phase.
-#   tri_emit:  36 B written per triangle (verts 12, grade 4, rowidx 12, colptr 8)
-#   edge_sort: 8 B read + 8 B written per key per pass
-#   edge_grades: keys 8 read, flags 4+4, outputs 8+4+8+8, CSR scatter 8 per edge
+
+def method_bytes_per_step(cloud, counts):
+    """Bytes the method must move per build: the input, 76 B per kept edge
+    (key 8 written + 8 read; outputs verts 8, grade 4, rowidx 8, colptr 8;
+    neighbour CSR 16 written + 16 read), 36 B per triangle (verts 12,
+    grade 4, rowidx 12, colptr 8) and 44 B per tetrahedron (verts 16, grade 4,
+    rowidx 16, colptr 8)."""
+    E = counts[1] if len(counts) > 1 else 0
+    T = counts[2] if len(counts) > 2 else 0
+    T4 = counts[3] if len(counts) > 3 else 0
+    return int(cloud.points.nbytes) + 76 * E + 36 * T + 44 * T4
 
 
 def roofline_bytes(cloud, E, T, T4=0, ngrades=0):
-    """Algorithmic bytes of one launch of each single-kernel phase."""
-    # Tetrahedron keys carry the packed vertices when the grades fit 12 bits;
-    # otherwise the final write also reads an 8 B vertex record.
+    """Per launch of each single-kernel phase: (method bytes, intermediate
+    bytes).  Method bytes are the per-unit figures of method_bytes_per_step
+    that the kernel moves; intermediates (sort keys, bitmaps) are listed
+    apart and never counted in `achieved`."""
     tet_read = 8 if (ngrades - 1).bit_length() <= 12 else 16
     n = cloud.n
     Wd = (n + 31) // 32
     return {
-        "tri_sort.pass": 16 * T,           # one digit pass: read + write one 8 B key
-        "tri_sort.hist": 8 * T,            # all-digit histogram: read one 8 B key
-        "tri_final": 44 * T,               # read key 8 B, write verts 12 + grade 4 + rowidx 12 + colptr 8
-        "tri_lex_gen": 8 * T,              # write one 8 B key
-        "tri_emit": 36 * T,                # write verts 12 + grade 4 + rowidx 12 + colptr 8
-        "edge_sort.pass": 16 * E,
-        "edge_sort.hist": 8 * E,
-        "distance": cloud.points.nbytes + 4 * n * Wd,  # read points, write the bitmap
-        "edge_keys": 8 * E,
-        "tet_final": (tet_read + 36) * T4,  # read key (+ vertex record); write verts 16, grade 4, colptr 8, rowidx 16
+        "tri_final": (36 * T, 8 * T),          # outputs 36 B; reads one 8 B key
+        "tri_emit": (36 * T, 0),               # outputs 36 B, emitted at their final position
+        "tri_lex_gen": (0, 8 * T),             # writes one 8 B key
+        "tri_gen": (0, 8 * T),                 # max-edge order: writes one 8 B key, already in order
+        "tri_sort.pass": (0, 16 * T),          # one digit pass over the keys
+        "tri_sort.hist": (0, 8 * T),
+        "edge_sort.pass": (16 * E, 0),         # the edge key: 8 B written + 8 B read
+        "edge_sort.hist": (0, 8 * E),
+        "edge_keys": (8 * E, 0),               # writes the edge key
+        "distance": (int(cloud.points.nbytes), 4 * n * Wd),  # reads the points, writes the bitmap
+        "tet_final": (44 * T4, tet_read * T4),
     }
 
 
@@ -355,6 +376,14 @@ def whole_job_rate(units_all_ranks: float, slowest_seconds: float) -> float:
     return units_all_ranks / slowest_seconds
 
 
+def host_cores():
+    """Cores this process may run on (the box's usable host cores)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
 def oracle_rate(cloud, seconds: float):
     """Time the oracle as it stands on full builds of the workload."""
     import oracle
@@ -369,6 +398,45 @@ def oracle_rate(cloud, seconds: float):
         if el >= seconds:
             break
     return simp / el, reps, el
+
+
+def oracle_parallel_rate(clouds, seconds: float, threads: int):
+    """The oracle as it stands, one whole build per cloud, clouds taken in
+    order by `threads` host threads (the C call releases the interpreter
+    lock, so the builds run in parallel).  Stops taking new clouds after
+    `seconds`; returns (clouds built, elapsed seconds, threads)."""
+    import ctypes
+    import oracle
+    oracle.build()
+    lib = oracle._load()
+    lock = threading.Lock()
+    state = {"next": 0, "done": 0}
+    t0 = time.perf_counter()
+
+    def worker():
+        while True:
+            with lock:
+                i = state["next"]
+                if i >= len(clouds) or time.perf_counter() - t0 > seconds:
+                    return
+                state["next"] += 1
+            c = clouds[i]
+            pts = np.ascontiguousarray(c.points)
+            out = oracle._Complex()
+            rc = lib.vro_build(pts.ctypes.data, c.n, c.d, oracle._dtype_code(pts), c.maxdim, float(c.maxrad),
+                               ctypes.byref(out))
+            if rc:
+                raise RuntimeError(f"oracle failed on cloud {i}: {rc}")
+            lib.vro_free(ctypes.byref(out))
+            with lock:
+                state["done"] += 1
+
+    th = [threading.Thread(target=worker) for _ in range(threads)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    return state["done"], time.perf_counter() - t0, threads
 
 
 def run_reference(args):
@@ -392,8 +460,9 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype_name, "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "n": cloud.n, "d": cloud.d, "maxdim": cloud.maxdim},
-            "cpu_baseline": {"value": v, "unit": "simplices/s", "cores": 1, "kind": "oracle",
+            "config": {"workload": WORKLOAD, "n": cloud.n, "d": cloud.d, "maxdim": cloud.maxdim,
+                       "maxrad": cloud.maxrad},
+            "cpu_baseline": {"value": v, "unit": "simplices/s", "cores": 1, "nproc": host_cores(), "kind": "oracle",
                              "sample": f"{args.steps} full builds of the workload, single-threaded C oracle"},
             "e2e": {"value": v, "unit": "simplices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -405,17 +474,18 @@ def run_reference(args):
 # to the device twice per batch and reads it back twice.
 CLOUD_DESC_BYTES = 144
 
+BATCH_WORKLOAD = "4096 sphere clouds n~U[32,512] d=3 int8 (scale 100, noise 0.02), cap 40, maxdim 2"
 
-def run_batch_bench(args):
+
+def batch_leg(args, ranks, local):
     """Batched clouds/s: all clouds of the uneven sphere workload in one
     vr_build_batch call per step, against the per-cloud path (one vr_build per
-    cloud, plain launches, same GPU) timed on a sample of the same clouds."""
+    cloud, plain launches, same GPU) on every cloud.  Returns the result
+    dict and this rank's clouds (for the CPU baseline)."""
     import ctypes
     import torch
     import paper_1809_04424_b300 as vr
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    ranks = Ranks()
+    world = ranks.world
     lo, hi = ranks.shard(args.n_clouds)  # this rank's clouds of the batch
     clouds = synth.config4(args.n_clouds)[lo:hi]
     pts = np.concatenate([c.points for c in clouds], axis=0)
@@ -425,71 +495,82 @@ def run_batch_bench(args):
     W = max(args.warmup, 3)
     for _ in range(W):
         b = vr.vr_build_batch(dev, off, 2, 40.0)
-        tot = b.info()["total_simplices"]
+        info = b.info()
+        tot = info["total_simplices"]
+        if info["n_failed"]:
+            raise RuntimeError("batch build failed on some clouds")
         del b
     torch.cuda.synchronize()
     L.vr_profile_reset()
     L.vr_profile_enable(1)
     launches0 = L.vr_launch_count()
+    steps = max(args.batch_steps, 1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stream = torch.cuda.current_stream()
     ranks.barrier()
+    torch.cuda.synchronize()
     with NoGC(), Clocks(local) as clk:
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for k in range(steps):
+            ev[k][0].record(stream)
             b = vr.vr_build_batch(dev, off, 2, 40.0)
+            ev[k][1].record(stream)
             del b
         torch.cuda.synchronize()
-        el = ranks.max(time.perf_counter() - t0)
+        wall = time.perf_counter() - t0
     L.vr_profile_enable(0)
     launches = L.vr_launch_count() - launches0
+    dev_ms = ranks.max(sum(a.elapsed_time(b) for a, b in ev))
     phases = {}
     for i in range(L.vr_profile_phases()):
         nm, ms, calls, nl = ctypes.c_char_p(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
         L.vr_profile_phase(i, ctypes.byref(nm), ctypes.byref(ms), ctypes.byref(calls), ctypes.byref(nl))
         phases[nm.value.decode()] = round(ms.value / max(calls.value, 1), 4)
-    batched = whole_job_rate(args.n_clouds * args.steps, el)
+    batched = whole_job_rate(args.n_clouds * steps, dev_ms / 1e3)
     tot = ranks.sum(tot)
-    # per-cloud path on a sample
-    sample = clouds[: min(len(clouds), 256)]
-    devs = [torch.from_numpy(c.points).cuda() for c in sample]
-    for c, dp in list(zip(sample, devs))[:8]:
+    # per-cloud path: one vr_build per cloud, every cloud of this rank
+    devs = [torch.from_numpy(c.points).cuda() for c in clouds]
+    for dp in devs[:16]:
         vr.vr_build(dp, 2, 40.0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for c, dp in zip(sample, devs):
+    for dp in devs:
         x = vr.vr_build(dp, 2, 40.0)
         del x
     torch.cuda.synchronize()
-    per_cloud = len(sample) / (time.perf_counter() - t0)
+    per_cloud = whole_job_rate(args.n_clouds, ranks.max(time.perf_counter() - t0))
     # e2e: host points in, each cloud's descriptor back, the complexes stay on the device
     host = torch.from_numpy(pts).pin_memory()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         b = vr.vr_build_batch(host.numpy(), off, 2, 40.0)
         if b.info()["n_failed"]:
             raise RuntimeError("batch build failed on some clouds")
         del b
     torch.cuda.synchronize()
-    e2e = args.n_clouds * args.steps / (time.perf_counter() - t0)
-    line = {"metric": "batched clouds/s", "value": batched, "unit": "clouds/s", "n_gpus": world,
-            "scaling_note": "clouds sharded across ranks, no collective on the data path",
-            "steps": args.steps, "warmup": W, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": f"{args.n_clouds} sphere clouds n~U[32,512] d=3 int8 (scale 100, noise 0.02), "
-                                   "cap 40, maxdim 2", "simplices_per_step": tot,
-                       "l2": "inputs and outputs larger than L2 per step"},
-            "simplices_per_s": tot * args.steps / el,
-            "per_cloud_path": {"value": per_cloud, "unit": "clouds/s", "sample_clouds": len(sample),
-                               "speedup_batched": batched / per_cloud},
-            "e2e": {"value": e2e, "unit": "clouds/s",
-                    "h2d_bytes_per_step": int(pts.nbytes) + len(clouds) * (2 * CLOUD_DESC_BYTES + 4),
-                    "d2h_bytes_per_step": len(clouds) * 2 * CLOUD_DESC_BYTES,
-                    "read_back": "each cloud's descriptor (sizes, status, grade count) after the sizing pass "
-                                 "and after the build; the complexes stay on the device"},
-            "gpu_launches": launches, "phases_ms": phases, "clocks": clk.summary()}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    ranks.close()
-    return 0
+    e2e = whole_job_rate(args.n_clouds * steps, ranks.max(time.perf_counter() - t0))
+    out = {"metric": "batched clouds/s", "value": batched, "unit": "clouds/s", "steps": steps, "warmup": W,
+           "ms_per_step": dev_ms / steps, "wall_ms_per_step": 1e3 * wall / steps,
+           "workload": BATCH_WORKLOAD, "clouds": args.n_clouds, "simplices_per_step": tot,
+           "simplices_per_s": tot * steps / (dev_ms / 1e3),
+           "l2": "inputs and outputs larger than L2 per step",
+           "per_cloud_path": {"value": per_cloud, "unit": "clouds/s", "clouds": args.n_clouds,
+                              "how": "one vr_build per cloud, plain launches, same GPU, every cloud"},
+           "speedup_vs_per_cloud": batched / per_cloud,
+           "e2e": {"value": e2e, "unit": "clouds/s",
+                   "h2d_bytes_per_step": int(pts.nbytes) + len(clouds) * (2 * CLOUD_DESC_BYTES + 4),
+                   "d2h_bytes_per_step": len(clouds) * 2 * CLOUD_DESC_BYTES,
+                   "read_back": "each cloud's descriptor (sizes, status, grade count); the complexes stay on "
+                                "the device"},
+           "gpu_launches": launches, "phases_ms": phases, "clocks": clk.summary()}
+    return out, clouds
+
+
+def cpu_batch_baseline(clouds, seconds, threads):
+    done, el, th = oracle_parallel_rate(clouds, seconds, threads)
+    return {"value": done / el, "unit": "clouds/s", "cores": th, "nproc": host_cores(), "kind": "oracle",
+            "sample": f"{done} of {len(clouds)} clouds in {el:.1f} s, one whole oracle build per cloud, "
+                      f"{th} host threads across clouds"}
 
 
 def _open_loop(submit_fn, poll_fn, reqs, arrivals, n_pollers=16):
@@ -525,19 +606,40 @@ def _open_loop(submit_fn, poll_fn, reqs, arrivals, n_pollers=16):
     return lat, max(done) - t_start
 
 
-def run_serve_bench(args):
+SERVE_WORKLOAD = ("Poisson stream of {N} requests, n log-uniform [50,5000], half int8 d=3 torus/sphere, "
+                  "half f32 d=16 Gaussian mixtures, maxdim {{1,2}}, per-request cap")
+
+
+def _gen_requests(n):
+    return synth.config5(n)[1]
+
+
+class RequestsAhead:
+    """The serving workload's requests drawn in a spawned process (about a
+    millisecond of numpy per request) while the GPU legs run."""
+
+    def __init__(self, n):
+        import multiprocessing as mp
+        self.pool = mp.get_context("spawn").Pool(1)
+        self.res = self.pool.apply_async(_gen_requests, (n,))
+
+    def get(self):
+        out = self.res.get()
+        self.pool.close()
+        self.pool.join()
+        return out
+
+
+def serve_leg(args, ranks, local, reqs_all):
     """Serving: a Poisson stream of mixed requests (n log-uniform in
     [50, 5000]; half int8 d=3 torus/sphere, half float32 d=16 mixtures;
     maxdim in {1, 2}; per-request cap) through the continuous-batching server
     at 0.8x its measured capacity: p50/p99 latency and clouds/s, against the
-    per-cloud path (one vr_build per request, FIFO) on the same arrivals."""
-    import torch
+    per-cloud path (one vr_build per request, FIFO) on the same arrival rate.
+    Returns the result dict and this rank's requests."""
     import paper_1809_04424_b300 as vr
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    ranks = Ranks()
-    _, reqs_all = synth.config5(args.n_requests)
-    lo, hi = ranks.shard(args.n_requests)  # this rank's share of the stream
+    world = ranks.world
+    lo, hi = ranks.shard(len(reqs_all))  # this rank's share of the stream
     reqs = reqs_all[lo:hi]
     N = len(reqs)
     srv = vr.Server(n_streams=3, max_batch_clouds=256, n_large_workers=4)
@@ -561,22 +663,16 @@ def run_serve_bench(args):
     wall_all = ranks.max(wall)
     sweep = {}
     for f in (0.5, 1.0):
-        M = min(N, 4000)
+        M = min(N, args.sweep_requests)
         a = np.cumsum(synth.rng(1809 + 51).exponential(1.0 / (f * cap), size=M))
         l2, w2 = _open_loop(submit, poll, reqs[:M], a)
         sweep[str(f)] = {"p50_ms": 1e3 * float(np.percentile(l2, 50)), "p99_ms": 1e3 * float(np.percentile(l2, 99)),
-                         "clouds_per_s": M / w2}
+                         "clouds_per_s": M / w2, "requests": M}
     srv.close()
     # per-cloud path: one vr_build per request in arrival order, one worker
     M = min(N, 2000)
-    devq = []
     import threading
     lock = threading.Lock()
-
-    def per_submit(r):
-        return r
-
-    results = {}
 
     def per_poll(r):
         with lock:  # a single FIFO worker: plain launches, one cloud at a time
@@ -587,25 +683,70 @@ def run_serve_bench(args):
         per_poll(r)
     per_cap = 200 / (time.perf_counter() - t0)
     a = np.cumsum(synth.rng(1809 + 52).exponential(1.0 / lam, size=M))
-    lp, wp = _open_loop(per_submit, per_poll, reqs[:M], a, n_pollers=1)
-    line = {"metric": "served clouds/s", "value": whole_job_rate(args.n_requests, wall_all), "unit": "clouds/s",
-            "n_gpus": world, "steps": N,
-            "warmup": 64, "ms_per_step": 1e3 * wall / N, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "mixed int64/f64", "data": "synthetic",
-            "config": {"workload": f"Poisson stream of {N} requests, n log-uniform [50,5000], half int8 d=3 "
-                                   "torus/sphere, half f32 d=16 Gaussian mixtures, maxdim {1,2}, per-request cap",
-                       "arrival_rate_per_s": lam, "capacity_closed_loop": cap},
-            "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99)),
-                           "mean": 1e3 * float(lat.mean())},
-            "rate_sweep": sweep,
-            "per_cloud_path": {"capacity_clouds_per_s": per_cap, "requests": M,
-                               "p50_ms": 1e3 * float(np.percentile(lp, 50)),
-                               "p99_ms": 1e3 * float(np.percentile(lp, 99)), "clouds_per_s": M / wp},
-            "e2e": {"value": N / wall, "unit": "clouds/s", "h2d_bytes_per_step": int(np.mean([r.points.nbytes for r in reqs])),
-                    "d2h_bytes_per_step": 2 * CLOUD_DESC_BYTES,
-                    "read_back": "per request its descriptor (batched requests, twice) or the status word the "
-                                 "device writes to mapped host memory (large ones); the complexes stay on the device"},
-            "clocks": clk.summary()}
+    lp, wp = _open_loop(lambda r: r, per_poll, reqs[:M], a, n_pollers=1)
+    out = {"metric": "served clouds/s", "value": whole_job_rate(len(reqs_all), wall_all), "unit": "clouds/s",
+           "requests": len(reqs_all), "workload": SERVE_WORKLOAD.format(N=len(reqs_all)),
+           "arrival_rate_per_s": lam, "capacity_closed_loop": cap,
+           "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99)),
+                          "mean": 1e3 * float(lat.mean())},
+           "rate_sweep": sweep,
+           "per_cloud_path": {"capacity_clouds_per_s": per_cap, "requests": M,
+                              "arrival_rate_per_s": lam,
+                              "p50_ms": 1e3 * float(np.percentile(lp, 50)),
+                              "p99_ms": 1e3 * float(np.percentile(lp, 99)), "clouds_per_s": M / wp,
+                              "how": "one vr_build per request, one FIFO worker, same arrival rate"},
+           "e2e": {"value": N / wall, "unit": "clouds/s",
+                   "h2d_bytes_per_step": int(np.mean([r.points.nbytes for r in reqs])),
+                   "d2h_bytes_per_step": 2 * CLOUD_DESC_BYTES,
+                   "read_back": "per request its descriptor (batched requests, twice) or the status word the "
+                                "device writes to mapped host memory (large ones); the complexes stay on the "
+                                "device"},
+           "clocks": clk.summary()}
+    return out, reqs
+
+
+def cpu_serve_baseline(reqs, seconds, threads):
+    done, el, th = oracle_parallel_rate(reqs, seconds, threads)
+    return {"value": done / el, "unit": "clouds/s", "cores": th, "nproc": host_cores(), "kind": "oracle",
+            "sample": f"the first {done} requests of the stream in arrival order in {el:.1f} s, one whole oracle "
+                      f"build per request, {th} host threads across requests"}
+
+
+def run_batch_bench(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    ranks = Ranks()
+    out, clouds = batch_leg(args, ranks, local)
+    line = {"metric": out["metric"], "value": out["value"], "unit": "clouds/s", "n_gpus": ranks.world,
+            "steps": out["steps"], "warmup": out["warmup"], "ms_per_step": out["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": out["workload"], "simplices_per_step": out["simplices_per_step"],
+                                            "l2": out["l2"]}}
+    line.update({k: v for k, v in out.items() if k not in line and k not in ("workload",)})
+    if rank == 0 and args.cpu_seconds > 0:
+        line["cpu_baseline"] = cpu_batch_baseline(clouds, args.cpu_seconds, host_cores())
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ranks.close()
+    return 0
+
+
+def run_serve_bench(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    ranks = Ranks()
+    reqs_all = synth.config5(args.n_requests)[1]
+    out, reqs = serve_leg(args, ranks, local, reqs_all)
+    line = {"metric": out["metric"], "value": out["value"], "unit": "clouds/s", "n_gpus": ranks.world,
+            "steps": len(reqs_all), "warmup": 64, "ms_per_step": 1e3 / out["value"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "mixed int64/f64", "data": "synthetic",
+            "config": {"workload": out["workload"], "arrival_rate_per_s": out["arrival_rate_per_s"],
+                       "capacity_closed_loop": out["capacity_closed_loop"]}}
+    line.update({k: v for k, v in out.items() if k not in line and k not in ("workload",)})
+    if rank == 0 and args.cpu_seconds > 0:
+        line["cpu_baseline"] = cpu_serve_baseline(reqs, args.cpu_seconds, host_cores())
     if rank == 0:
         print(json.dumps(line), flush=True)
     ranks.close()
@@ -691,38 +832,13 @@ def oracle_build_keep(cloud):
     return oracle.vr_build(cloud.points, cloud.maxdim, cloud.maxrad, keep_handle=True)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=10.0,
-                    help="length of the CPU-oracle baseline sample (0 skips it)")
-    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--config", default="torus", choices=sorted(WORKLOADS) + ["batch", "serve"],
-                    help="workload (default: the headline torus cloud)")
-    ap.add_argument("--n-clouds", type=int, default=4096, help="clouds of the batch workload")
-    ap.add_argument("--n-requests", type=int, default=20000, help="requests of the serving workload")
-    ap.add_argument("--bars", action="store_true",
-                    help="time build + persistence barcodes of every dimension (the reduction step)")
-    args = ap.parse_args()
-    if args.bars and args.impl != "reference":
-        return run_bars_bench(args)
-    if args.config == "batch" and args.impl != "reference":
-        return run_batch_bench(args)
-    if args.config == "serve" and args.impl != "reference":
-        return run_serve_bench(args)
-    if args.impl == "reference":
-        return run_reference(args)
-
+def single_cloud_leg(args, ranks, local):
+    """One vr_build per step of the chosen single-cloud workload; returns the
+    contract's line (without the CPU baseline) and the cloud."""
+    import ctypes
     import torch
     import paper_1809_04424_b300 as vr
-
-    world, rank, local = dist_env()
-    assert torch.cuda.is_available(), "bench needs a CUDA device"
-    torch.cuda.set_device(local)
-    ranks = Ranks()
+    world, rank = ranks.world, ranks.rank
     W = max(args.warmup, 3)
     L = vr.lib()
 
@@ -738,12 +854,12 @@ def main():
     for _ in range(W):
         c = step()
         counts = c.counts()[0]
-        ngrades = c.stats()["ngrades"]
+        st = c.stats()
+        ngrades = st["ngrades"]
         del c
     torch.cuda.synchronize()
     simplices = sum(counts)
 
-    import ctypes
     L.vr_profile_select.argtypes = [ctypes.c_char_p]
 
     def read_phases():
@@ -766,15 +882,18 @@ def main():
     torch.cuda.synchronize()
     L.vr_profile_enable(0)
     phases = read_phases()
-    per_launch_bytes = roofline_bytes(cloud, counts[1], counts[2], counts[3] if len(counts) > 3 else 0, ngrades)
-    # Regions of one kernel (a sort's digit passes: several launches of the
+    per_launch_bytes = roofline_bytes(cloud, counts[1] if len(counts) > 1 else 0,
+                                      counts[2] if len(counts) > 2 else 0,
+                                      counts[3] if len(counts) > 3 else 0, ngrades)
+    # The roofline kernel: the longest single-kernel region that moves bytes
+    # of the method's own (a sort's digit passes: several launches of the
     # same kernel, each timed).
-    single = {k: v for k, v in phases.items() if k in per_launch_bytes
+    single = {k: v for k, v in phases.items() if k in per_launch_bytes and per_launch_bytes[k][0] > 0
               and (v["launches_per_call"] == 1 or k.endswith(".pass"))}
     dom = max(single, key=lambda k: single[k]["ms_per_call"]) if single else None
 
     # ---- timed region: K steps, per-step CUDA events, L2 flushed between;
-    # inside it the library times only the dominant kernel's region.
+    # inside it the library times only the roofline kernel's region.
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     L.vr_profile_select(dom.encode() if dom else b"-")
     L.vr_profile_reset()
@@ -802,31 +921,24 @@ def main():
 
     # ---- e2e: host (pinned) points in, every output array back to pinned host.
     host_pts = torch.from_numpy(cloud.points).pin_memory()
-    c0 = gpu_build(cloud, pts_dev)
-    cnt, _ = c0.counts()
-    del c0
+    ndims = len(counts)
     bufs = []
-    for k in range(3):
-        m = cnt[k]
+    for k in range(ndims):
+        m = counts[k]
         bufs.append([torch.empty(m * (k + 1), dtype=torch.int32).pin_memory(),
                      torch.empty(m, dtype=torch.int32).pin_memory(),
                      torch.empty(m + 1, dtype=torch.int64).pin_memory() if k else None,
                      torch.empty(m * (k + 1), dtype=torch.int32).pin_memory() if k else None])
     d2h = sum(b.numel() * b.element_size() for bb in bufs for b in bb if b is not None)
-    gv = None
+    gv = torch.empty(ngrades, dtype=torch.float64).pin_memory()
 
     def e2e_step():
-        nonlocal gv
-        c = gpu_build(cloud, host_pts.data_ptr(), n=cloud.n, d=cloud.d,
-                        dtype=cloud.dtype_code)
-        for k in range(3):
+        c = gpu_build(cloud, host_pts.data_ptr(), n=cloud.n, d=cloud.d, dtype=cloud.dtype_code)
+        for k in range(ndims):
             b = bufs[k]
             p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
             rc = L.vr_complex_to_host(ctypes.c_void_p(c.handle), k, p(b[0]), p(b[1]), p(b[2]), p(b[3]))
             assert rc == 0, vr.vr_last_error()
-        _, ng = vr.vr_complex_grade_values(c.handle)
-        if gv is None:
-            gv = torch.empty(ng, dtype=torch.float64).pin_memory()
         L.vr_complex_grade_values_to_host(ctypes.c_void_p(c.handle), ctypes.c_void_p(gv.data_ptr()))
         del c
 
@@ -835,31 +947,41 @@ def main():
         for _ in range(W):
             e2e_step()
         torch.cuda.synchronize()
+        ranks.barrier()
         with NoGC():
             t0 = time.perf_counter()
             for _ in range(args.steps):
                 e2e_step()
             torch.cuda.synchronize()
-            e2e_s = time.perf_counter() - t0
+            e2e_s = ranks.max(time.perf_counter() - t0)
         d2h += gv.numel() * 8
         e2e_val = simplices * args.steps * world / e2e_s
 
     # ---- roofline of the dominant kernel: its region timed by the library's
-    # CUDA events on the build stream inside the timed region.
+    # CUDA events on the build stream inside the timed region; and the whole
+    # build against the bytes the method must move.
     hbm, src = peaks()
     roof = None
+    ms_step = total_ms / args.steps
+    build_bytes = method_bytes_per_step(cloud, counts)
     if dom and dom in timed_phases:
         tp = timed_phases[dom]
         per_launch_ms = tp["ms_per_call"] if dom.endswith(".pass") else \
             tp["ms_per_call"] / max(tp["launches_per_call"], 1)
-        ach = per_launch_bytes[dom] / (per_launch_ms / 1e3) / 1e9
+        alg, inter = per_launch_bytes[dom]
+        ach = alg / (per_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": recorded_traffic(dom, args.config), "peak_source": src,
-                "algorithmic_bytes_per_launch": per_launch_bytes[dom],
-                "launch_ms": per_launch_ms, "launches_timed": tp["calls"]}
+                "algorithmic_bytes_per_launch": alg, "intermediate_bytes_per_launch": inter,
+                "launch_ms": per_launch_ms, "launches_timed": tp["calls"],
+                "build_bytes_per_step": build_bytes,
+                "build_achieved": build_bytes / (ms_step / 1e3) / 1e9,
+                "build_frac": build_bytes / (ms_step / 1e3) / 1e9 / hbm,
+                "note": "achieved counts only the bytes the method must move (outputs, input, edge keys, "
+                        "neighbour lists); intermediates are listed apart; of measured HBM copy bandwidth"}
 
     line = {"metric": METRIC, "value": value, "unit": "simplices/s", "n_gpus": world, "steps": args.steps,
-            "warmup": W, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "warmup": W, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype_name, "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": cloud.n, "d": cloud.d, "maxdim": cloud.maxdim,
                        "maxrad": cloud.maxrad, "simplices_per_step": simplices,
@@ -874,10 +996,67 @@ def main():
             "phases_note": "ms per call, from an untimed calibration pass before the timed region",
             "phase_launches": {k: v["launches_per_call"] for k, v in phases.items()},
             "clocks": clk.summary()}
-    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+    for k in ("max_rel_dist_err", "gram_max_rel_d_err", "gram_band_pairs", "near_tie_edges"):
+        if k in st:
+            line.setdefault("accuracy", {})[k] = st[k]
+    del flush
+    torch.cuda.empty_cache()
+    return line, cloud
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="length of each CPU-oracle baseline sample (0 skips them)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--config", default=DEFAULT_CONFIG, choices=sorted(WORKLOADS) + ["batch", "serve"],
+                    help="workload (default: the 4000-point float Gaussian-mixture cloud)")
+    ap.add_argument("--no-nested", action="store_true",
+                    help="skip the batched and served legs nested in the single-cloud line")
+    ap.add_argument("--n-clouds", type=int, default=4096, help="clouds of the batch workload")
+    ap.add_argument("--batch-steps", type=int, default=10, help="timed batches of the batch workload")
+    ap.add_argument("--n-requests", type=int, default=20000, help="requests of the serving workload")
+    ap.add_argument("--sweep-requests", type=int, default=4000, help="requests per point of the rate sweep")
+    ap.add_argument("--bars", action="store_true",
+                    help="time build + persistence barcodes of every dimension (the reduction step)")
+    args = ap.parse_args()
+    if args.bars and args.impl != "reference":
+        return run_bars_bench(args)
+    if args.config == "batch" and args.impl != "reference":
+        return run_batch_bench(args)
+    if args.config == "serve" and args.impl != "reference":
+        return run_serve_bench(args)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    nested = not args.no_nested
+    ahead = RequestsAhead(args.n_requests) if nested else None  # spawned before any CUDA call
+
+    import torch
+    world, rank, local = dist_env()
+    assert torch.cuda.is_available(), "bench needs a CUDA device"
+    torch.cuda.set_device(local)
+    ranks = Ranks()
+
+    line, cloud = single_cloud_leg(args, ranks, local)
+    if nested:
+        bat, clouds4 = batch_leg(args, ranks, local)
+        reqs_all = ahead.get()
+        srv, reqs = serve_leg(args, ranks, local, reqs_all)
+        line["batched"], line["served"] = bat, srv
+    # CPU baselines last, with the GPU legs and the request generator done.
+    if rank == 0 and args.cpu_seconds > 0:
         r, reps, el = oracle_rate(cloud, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": r, "unit": "simplices/s", "cores": 1, "kind": "oracle",
+        line["cpu_baseline"] = {"value": r, "unit": "simplices/s", "cores": 1, "nproc": host_cores(),
+                                "kind": "oracle",
                                 "sample": f"{reps} full builds of the workload in {el:.1f} s, single-threaded"}
+        if nested:
+            line["batched"]["cpu_baseline"] = cpu_batch_baseline(clouds4, args.cpu_seconds, host_cores())
+            line["served"]["cpu_baseline"] = cpu_serve_baseline(reqs, args.cpu_seconds, host_cores())
     if rank == 0:
         print(json.dumps(line), flush=True)
     ranks.close()

@@ -179,8 +179,16 @@ VR_API vr_status vr_complex_counts(const vr_complex *c, int64_t counts[VR_MAX_DI
 
 VR_API vr_status vr_complex_stats(const vr_complex *c, vr_build_stats *stats);
 
+/* Waits for the build's stream and reports what the device found after the
+ * build's last size read (vr_build returns before its last kernels finish):
+ * VR_ERR_TIMEOUT if a bounded device wait gave up, VR_ERR_INTERNAL if an
+ * internal check failed; then the arrays hold no valid result.  VR_OK
+ * otherwise.  vr_complex_to_host reports the same on its own. */
+VR_API vr_status vr_complex_status(const vr_complex *c);
+
 /* Copy dimension k to host arrays sized as in vr_dim_view (any may be NULL;
- * colptr/rowidx are ignored for k = 0).  Synchronous on the build stream. */
+ * colptr/rowidx are ignored for k = 0).  Synchronous on the build stream;
+ * returns vr_complex_status's error if the device raised one late. */
 VR_API vr_status vr_complex_to_host(const vr_complex *c, int32_t k, int32_t *verts,
                              int32_t *grade, int64_t *colptr, int32_t *rowidx);
 
@@ -248,6 +256,18 @@ VR_API vr_status vr_serve_submit(vr_server *srv, const void *points, int32_t n,
  * request's own error.  A ticket is delivered once. */
 VR_API vr_status vr_serve_poll(vr_server *srv, uint64_t ticket,
                                int64_t timeout_us, vr_complex **out);
+/* Counters of a server since its creation (a snapshot; for monitoring). */
+typedef struct vr_server_stats {
+  int64_t submitted;     /* requests accepted by vr_serve_submit             */
+  int64_t completed;     /* results delivered with VR_OK                     */
+  int64_t failed;        /* results delivered with an error                  */
+  int64_t deferred;      /* clouds sent back to the queue by memory admission */
+  int64_t batches;       /* micro-batches launched                           */
+  int64_t large_builds;  /* requests built alone (too large for the batch kernels) */
+  int64_t queued;        /* requests waiting now                             */
+} vr_server_stats;
+VR_API vr_status vr_server_get_stats(vr_server *srv, vr_server_stats *out);
+
 /* Finish the work in flight and release the server (undelivered results are
  * freed). */
 VR_API vr_status vr_server_destroy(vr_server *srv);

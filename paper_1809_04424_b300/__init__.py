@@ -69,8 +69,18 @@ def lib():
         L.vr_last_error.restype = ctypes.c_char_p
         L.vr_status_string.restype = ctypes.c_char_p
         L.vr_status_string.argtypes = [ctypes.c_int]
+        L.vr_complex_status.argtypes = [vp]
+        L.vr_inject_alloc_failure.argtypes = [i64]
+        L.vr_inject_lookback_stall.argtypes = [i64, i64]
+        L.vr_inject_gram_stall.argtypes = [i32, i64]
+        L.vr_inject_admission_refusals.argtypes = [i64]
+        L.vr_inject_clear.argtypes = []
+        L.vr_pool_used_bytes.argtypes = [ctypes.POINTER(i64)]
         for name in ("vr_build", "vr_complex_dim", "vr_complex_grade_values", "vr_complex_counts",
-                     "vr_complex_stats", "vr_complex_to_host", "vr_complex_grade_values_to_host"):
+                     "vr_complex_stats", "vr_complex_to_host", "vr_complex_grade_values_to_host",
+                     "vr_complex_status", "vr_inject_alloc_failure", "vr_inject_lookback_stall",
+                     "vr_inject_gram_stall", "vr_inject_admission_refusals", "vr_inject_clear",
+                     "vr_pool_used_bytes"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -134,6 +144,11 @@ class Complex:
 
     def stats(self) -> dict:
         return vr_complex_stats(self.handle)
+
+    def status(self) -> int:
+        """vr_complex_status: waits for the build and returns what the device
+        reported after the build's last size read (VR_OK or an error code)."""
+        return vr_complex_status(self.handle)
 
     def dim(self, k: int) -> dict:
         """Zero-copy torch views of dimension k's device arrays."""
@@ -225,6 +240,39 @@ def vr_build_dmat(D, maxdim: int, maxrad: float = float("inf"), stream=None, n=N
     _check(L.vr_build_dmat(ctypes.c_void_p(ptr), int(n0), code, int(maxdim), float(maxrad), ctypes.c_void_p(s),
                            ctypes.byref(h)))
     return Complex(h.value)
+
+
+def vr_complex_status(handle) -> int:
+    return lib().vr_complex_status(ctypes.c_void_p(handle))
+
+
+# ------------------------------------------------------ fault injection
+# (include/vr_inject.h: host-side and bounded-wait faults for tests)
+
+def vr_inject_alloc_failure(nth: int) -> None:
+    _check(lib().vr_inject_alloc_failure(int(nth)))
+
+
+def vr_inject_lookback_stall(tile: int, wait_limit: int) -> None:
+    _check(lib().vr_inject_lookback_stall(int(tile), int(wait_limit)))
+
+
+def vr_inject_gram_stall(tile: int, wait_limit: int) -> None:
+    _check(lib().vr_inject_gram_stall(int(tile), int(wait_limit)))
+
+
+def vr_inject_admission_refusals(k: int) -> None:
+    _check(lib().vr_inject_admission_refusals(int(k)))
+
+
+def vr_inject_clear() -> None:
+    _check(lib().vr_inject_clear())
+
+
+def vr_pool_used_bytes() -> int:
+    v = ctypes.c_int64()
+    _check(lib().vr_pool_used_bytes(ctypes.byref(v)))
+    return v.value
 
 
 def vr_complex_dim(handle, k: int) -> DimView:
@@ -382,6 +430,11 @@ def vr_batch_free(handle) -> None:
 
 # ---------------------------------------------------------------- serving
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [(nm, ctypes.c_int64) for nm in ("submitted", "completed", "failed", "deferred", "batches",
+                                                "large_builds", "queued")]
+
+
 class ServerOpts(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_queue", ctypes.c_int32),
                 ("n_streams", ctypes.c_int32), ("max_batch_clouds", ctypes.c_int32), ("device", ctypes.c_int32),
@@ -401,6 +454,8 @@ def _set_server_types(L):
     L.vr_serve_poll.restype = ctypes.c_int
     L.vr_server_destroy.argtypes = [vp]
     L.vr_server_destroy.restype = ctypes.c_int
+    L.vr_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    L.vr_server_get_stats.restype = ctypes.c_int
     L._server_types = True
 
 
@@ -423,6 +478,12 @@ class Server:
 
     def poll(self, ticket: int, timeout_us: int = 10_000_000) -> Complex:
         return vr_serve_poll(self.handle, ticket, timeout_us)
+
+    def stats(self) -> dict:
+        """vr_server_get_stats as a dict of counters."""
+        st = ServerStats()
+        _check(lib().vr_server_get_stats(ctypes.c_void_p(self.handle), ctypes.byref(st)))
+        return {nm: getattr(st, nm) for nm, _ in ServerStats._fields_}
 
     def close(self):
         if getattr(self, "handle", None):

@@ -1,13 +1,16 @@
 // api.cu -- the extern "C" entry points of vr.h: argument checks, host/device
 // input detection, result access and error reporting.
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <new>
 
+#include "../../include/vr_inject.h"
 #include "complex.h"
+#include "jobs.h"
 #include "prims.cuh"
 
 namespace vr {
@@ -19,6 +22,47 @@ void set_error(const char *fmt, ...) {
   va_start(ap, fmt);
   vsnprintf(g_err, sizeof(g_err), fmt, ap);
   va_end(ap);
+}
+
+static std::atomic<int64_t> g_inj_alloc_nth{0};  // 0: off; k: the k-th allocation from now fails
+
+cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t s) {
+  int64_t k = g_inj_alloc_nth.load(std::memory_order_relaxed);
+  while (k > 0) {
+    if (g_inj_alloc_nth.compare_exchange_weak(k, k - 1, std::memory_order_relaxed)) {
+      if (k == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMallocAsync(p, bytes, s);
+}
+
+// ---- one-shot stall hooks (armed by vr_inject_*; taken by the next launch
+// that can honour them)
+static std::mutex g_inj_mu;
+static bool g_rs_armed = false, g_gram_armed = false;
+static int64_t g_rs_tile = 0, g_gram_tile = 0;
+static long g_rs_limit = 0, g_gram_limit = 0;
+
+bool take_rs_stall(int64_t tiles, RsStall *out) {
+  std::lock_guard<std::mutex> lk(g_inj_mu);
+  if (!g_rs_armed || g_rs_tile >= tiles) return false;
+  g_rs_armed = false;
+  out->tile = g_rs_tile;
+  out->limit = g_rs_limit;
+  return true;
+}
+
+bool take_gram_stall(int tiles, int *tile, long *limit) {
+  std::lock_guard<std::mutex> lk(g_inj_mu);
+  if (!g_gram_armed || g_gram_tile >= tiles) return false;
+  g_gram_armed = false;
+  *tile = (int)g_gram_tile;
+  *limit = g_gram_limit;
+  return true;
 }
 
 int num_sms() {
@@ -116,7 +160,7 @@ vr_status vr_build(const void *points, int32_t n, int32_t d, vr_dtype dtype, int
   void *staged = nullptr;
   const size_t bytes = (size_t)n * d * elem_size(dtype);
   if (!is_device_pointer(points)) {
-    if (cudaMallocAsync(&staged, bytes, s) != cudaSuccess) {
+    if (dev_malloc(&staged, bytes, s) != cudaSuccess) {
       cudaGetLastError();
       delete res;
       set_error("device allocation for the input copy failed");
@@ -156,7 +200,7 @@ vr_status vr_build_dmat(const void *D, int32_t n, vr_dtype dtype, int32_t maxdim
   void *staged = nullptr;
   const size_t bytes = (size_t)n * n * 4;
   if (!is_device_pointer(D)) {
-    if (cudaMallocAsync(&staged, bytes, s) != cudaSuccess) {
+    if (dev_malloc(&staged, bytes, s) != cudaSuccess) {
       cudaGetLastError();
       delete res;
       set_error("device allocation for the matrix copy failed");
@@ -208,18 +252,29 @@ vr_status vr_complex_stats(const vr_complex *c, vr_build_stats *s) {
   return VR_OK;
 }
 
+vr_status vr_complex_status(const vr_complex *c) {
+  if (!c) { set_error("NULL complex"); return VR_ERR_ARG; }
+  VR_CUDA(cudaStreamSynchronize(c->stream));
+  if (!c->late_flags) return VR_OK;
+  int32_t f = 0;
+  VR_CUDA(cudaMemcpy(&f, c->late_flags, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return flags_to_status(f);
+}
+
 vr_status vr_complex_to_host(const vr_complex *c, int32_t k, int32_t *verts, int32_t *grade, int64_t *colptr,
                              int32_t *rowidx) {
   if (!c) { set_error("NULL complex"); return VR_ERR_ARG; }
   if (k < 0 || k > c->maxdim) { set_error("dimension %d outside [0, %d]", k, c->maxdim); return VR_ERR_ARG; }
   const int64_t m = c->count[k];
   cudaStream_t s = c->stream;
+  int32_t late = 0;
+  if (c->late_flags) VR_CUDA(cudaMemcpyAsync(&late, c->late_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   if (verts && m) VR_CUDA(cudaMemcpyAsync(verts, c->verts[k], sizeof(int32_t) * m * (k + 1), cudaMemcpyDeviceToHost, s));
   if (grade && m) VR_CUDA(cudaMemcpyAsync(grade, c->grade[k], sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
   if (k >= 1 && colptr) VR_CUDA(cudaMemcpyAsync(colptr, c->colptr[k], sizeof(int64_t) * (m + 1), cudaMemcpyDeviceToHost, s));
   if (k >= 1 && rowidx && m) VR_CUDA(cudaMemcpyAsync(rowidx, c->rowidx[k], sizeof(int32_t) * m * (k + 1), cudaMemcpyDeviceToHost, s));
   VR_CUDA(cudaStreamSynchronize(s));
-  return VR_OK;
+  return late ? flags_to_status(late) : VR_OK;
 }
 
 vr_status vr_complex_grade_values_to_host(const vr_complex *c, double *values) {
@@ -237,6 +292,8 @@ vr_status vr_complex_barcode(vr_complex *c, int32_t dim, vr_stream_t stream, int
     set_error("barcodes are computed on results of vr_build / vr_build_dmat / vr_serve_poll");
     return VR_ERR_UNSUPPORTED;
   }
+  // A build the device reported as failed holds no valid complex to reduce.
+  if (c->late_flags) VR_TRY(vr_complex_status(c));
   cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
   return vr::complex_barcode(c, dim, s, nbars);
 }
@@ -399,4 +456,59 @@ vr_status vr_profile_phase(int32_t i, const char **name, double *total_ms, int64
 }
 
 int64_t vr_launch_count(void) { return vr::g_launches.load(); }
+}  // extern "C"
+
+// ------------------------------------------------------- fault injection
+extern "C" {
+
+vr_status vr_inject_alloc_failure(int64_t nth) {
+  if (nth < 0) { vr::set_error("nth = %lld must be >= 0", (long long)nth); return VR_ERR_ARG; }
+  vr::g_inj_alloc_nth.store(nth, std::memory_order_relaxed);
+  return VR_OK;
+}
+
+vr_status vr_inject_lookback_stall(int64_t tile, int64_t wait_limit) {
+  if (tile < 0 || wait_limit < 1) { vr::set_error("tile >= 0 and wait_limit >= 1 required"); return VR_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(vr::g_inj_mu);
+  vr::g_rs_armed = true;
+  vr::g_rs_tile = tile;
+  vr::g_rs_limit = (long)wait_limit;
+  return VR_OK;
+}
+
+vr_status vr_inject_gram_stall(int32_t tile, int64_t wait_limit) {
+  if (tile < 0 || wait_limit < 1) { vr::set_error("tile >= 0 and wait_limit >= 1 required"); return VR_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(vr::g_inj_mu);
+  vr::g_gram_armed = true;
+  vr::g_gram_tile = tile;
+  vr::g_gram_limit = (long)wait_limit;
+  return VR_OK;
+}
+
+vr_status vr_inject_clear(void) {
+  vr::g_inj_alloc_nth.store(0, std::memory_order_relaxed);
+  vr::inject_admission_refusals(0);
+  std::lock_guard<std::mutex> lk(vr::g_inj_mu);
+  vr::g_rs_armed = vr::g_gram_armed = false;
+  return VR_OK;
+}
+
+vr_status vr_inject_admission_refusals(int64_t k) {
+  if (k < 0) { vr::set_error("k = %lld must be >= 0", (long long)k); return VR_ERR_ARG; }
+  vr::inject_admission_refusals(k);
+  return VR_OK;
+}
+
+vr_status vr_pool_used_bytes(int64_t *bytes) {
+  if (!bytes) { vr::set_error("bytes is NULL"); return VR_ERR_ARG; }
+  int dev = 0;
+  VR_CUDA(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  VR_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t v = 0;
+  VR_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v));
+  *bytes = (int64_t)v;
+  return VR_OK;
+}
+
 }  // extern "C"

@@ -667,7 +667,7 @@ struct Dev {
   template <typename T>
   vr_status get(T **p, int64_t count, bool keep = false, std::vector<void *> *owner = nullptr) {
     const size_t bytes = sizeof(T) * (size_t)std::max<int64_t>(count, 1);
-    cudaError_t e = cudaMallocAsync((void **)p, bytes, s);
+    cudaError_t e = dev_malloc((void **)p, bytes, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       set_error("barcode: device allocation of %zu bytes failed", bytes);

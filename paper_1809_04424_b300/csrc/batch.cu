@@ -18,6 +18,7 @@
 // 200 KB of shared memory, or a float run of equal fp32 keys longer than 64)
 // is rebuilt by the single-cloud path.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <numeric>
 #include <type_traits>
@@ -598,7 +599,7 @@ namespace vr {
 template <typename T>
 static vr_status dalloc(std::vector<void *> &v, T **p, int64_t count, cudaStream_t s) {
   size_t bytes = sizeof(T) * (size_t)std::max<int64_t>(count, 1);
-  cudaError_t e = cudaMallocAsync((void **)p, bytes, s);
+  cudaError_t e = dev_malloc((void **)p, bytes, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
@@ -676,6 +677,17 @@ struct Arenas {
     cudaGetLastError();
   }
 };
+
+// Test hook (vr_inject_admission_refusals): the next k admission decisions
+// of the request server refuse every cloud of their batch.
+static std::atomic<int64_t> g_inj_refuse{0};
+void inject_admission_refusals(int64_t k) { g_inj_refuse.store(k, std::memory_order_relaxed); }
+static bool take_refusal() {
+  int64_t k = g_inj_refuse.load(std::memory_order_relaxed);
+  while (k > 0)
+    if (g_inj_refuse.compare_exchange_weak(k, k - 1, std::memory_order_relaxed)) return true;
+  return false;
+}
 
 // Bytes of output a fused cloud writes.
 int64_t cloud_out_bytes(const CloudDesc &c) {
@@ -757,11 +769,12 @@ struct BatchJob {
     int64_t Etot = 0, Ttot = 0, Vtot = 0, Gtot = 0, Ctot = 0, Ktot = 0, Emax = 0, Tmax = 0;
     int nmax = 1;
     bool any = false;
+    const bool refuse_all = deferred && take_refusal();
     for (int ci = 0; ci < nc; ++ci) {
       CloudDesc &c = hd[ci];
       if (c.fallback || c.flags) continue;
       const int64_t ob = cloud_out_bytes(c);
-      if (deferred && any && out_bytes + ob > budget) {
+      if (deferred && (refuse_all || (any && out_bytes + ob > budget))) {
         c.fallback = 2;
         deferred->push_back(ci);
         continue;
@@ -798,6 +811,9 @@ struct BatchJob {
     VR_TRY(dalloc(ar->ptrs, &o.vgrade, Vtot, s));
     VR_TRY(dalloc(ar->ptrs, &o.gval, Gtot, s));
     if (!any) {
+      // Nothing admitted: finish() reads the descriptors back from the pinned
+      // mirror, so it must carry the deferral marks set above.
+      if (hpin) memcpy(hpin, hd.data(), sizeof(CloudDesc) * nc);
       VR_CUDA(cudaEventRecord(ev, s));
       return VR_OK;
     }
@@ -1003,7 +1019,7 @@ vr_status vr_build_batch(const void *points, const int64_t *offsets, int32_t n_c
   cudaGetLastError();
   if (!on_dev) {
     void *p = nullptr;
-    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    if (dev_malloc(&p, bytes, s) != cudaSuccess) {
       cudaGetLastError();
       delete b;
       set_error("device allocation for the input copy failed");

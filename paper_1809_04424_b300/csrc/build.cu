@@ -56,7 +56,7 @@ struct Arena {
       pend.push_back({(void **)p, bytes});
       return VR_OK;
     }
-    cudaError_t e = cudaMallocAsync((void **)p, bytes, s);
+    cudaError_t e = dev_malloc((void **)p, bytes, s);
     if (e != cudaSuccess) {
       cudaGetLastError();
       set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
@@ -199,8 +199,16 @@ bool gram_tc_eligible(vr_dtype dtype, int n, int d);
 vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, uint32_t *adj, DevStatus *st,
                          cudaStream_t s, unsigned int *worst_bits);
 
-// Clouds above this size always take the lex triangle order.
-constexpr int LEX_FORCE_N = 4096;
+// Time-sliced adjacency of the max-edge triangle enumeration: at most this
+// many bytes of snapshots (kept well inside L2), at most SNAP_MAX_S slices.
+constexpr int64_t SNAP_BUDGET = int64_t(32) << 20;
+static int snap_slices(int n, int W, int64_t E) {
+  const int64_t per = (int64_t)n * snap_stride(W) * 4;
+  int64_t S = 1 + SNAP_BUDGET / std::max<int64_t>(per, 1);
+  S = std::min<int64_t>(S, SNAP_MAX_S);
+  S = std::min<int64_t>(S, std::max<int64_t>(E, 1));
+  return (int)std::max<int64_t>(S, 1);
+}
 
 // Largest size of the tetrahedron stage's per-edge prefix table (E * W
 // 16-bit counts); beyond it the face positions come from bisections.
@@ -345,15 +353,15 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     if (!F) VR_TRY(radix_prepare(ecap, KEY_SHIFT, kbits, rs, s, &ekh, true));
     prof.begin("edge_keys");
     if constexpr (F) {
-      launch_dep(k_lex_edges, (n + 7) / 8, 256, 0, s, n, W, adj, lex_ptr, lexe, elp);
+      launch_dep(k_lex_edges, (n + 7) / 8, 256, 0, s, n, W, adj, lex_ptr, lexe, elp, st);
       launch_dep(k_edge_keys_f32, grid_for((ecap + 31) / 32, EKF_WARPS, 16), EKF_WARPS * 32, 0, s,
                  (const float *)X, d, lexe, keys, d64_lex, st);
       count_launch();
     } else if (dmat) {
-      if (dmf) launch_dep(k_dmat_keys<true>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, lexe, elp, ekh);
-      else launch_dep(k_dmat_keys<false>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, lexe, elp, ekh);
+      if (dmf) launch_dep(k_dmat_keys<true>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, lexe, elp, ekh, st);
+      else launch_dep(k_dmat_keys<false>, (n + 7) / 8, 256, 0, s, dmat, n, W, adj, lex_ptr, keys, lexe, elp, ekh, st);
     } else {
-      launch_dep(k_edge_keys<F>, (n + 7) / 8, 256, 0, s, X, n, d, W, adj, lex_ptr, keys, lexe, elp, ekh);
+      launch_dep(k_edge_keys<F>, (n + 7) / 8, 256, 0, s, X, n, d, W, adj, lex_ptr, keys, lexe, elp, ekh, st);
     }
     count_launch();
     VR_CUDA(cudaGetLastError());
@@ -464,6 +472,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(out.alloc(&ecol, E + 1));
   VR_TRY(out.alloc(&erow, 2 * E));
   VR_TRY(out.alloc(&gval, E + 1));
+  int32_t *late_flags = nullptr;
+  VR_TRY(out.alloc(&late_flags, 1));
   int32_t *split = nullptr, *gbeg = nullptr, *midq = nullptr, *bigq = nullptr;
   uint64_t *k1 = nullptr, *k2 = nullptr, *gk = nullptr;
   uint32_t *v1 = nullptr, *v2 = nullptr;
@@ -483,6 +493,27 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   }
   int32_t *tcnt = nullptr, *tsmallq = nullptr, *tmidq = nullptr, *tbigq = nullptr;
   int64_t *toff = nullptr;
+  // Triangle order: lex mode is forced for tetrahedra and for clouds whose
+  // rows are sparse (fewer neighbours on average than bitmap words): there
+  // the lex walk takes each edge's candidates from the lexicographic edge
+  // list, one bit test each, cheaper than the max-edge enumeration's
+  // time-sliced rows (the 7322-point WorldMap-shaped cloud: 77 neighbours
+  // per point, 229 words per row).  Otherwise lex_mode decides on the device
+  // by the share of tied grades.
+  const int sparse_rows = 2 * E < (int64_t)n * W ? 1 : 0;
+  const int force_lex = (maxdim >= 3 || sparse_rows) ? 1 : 0;
+  SnapIdx sx{nullptr, nullptr, nullptr, 1, 1, snap_stride(W)};
+  uint32_t *snap = nullptr;
+  uint64_t *sbl = nullptr;
+  int32_t *sboff = nullptr;
+  const bool want_snap = maxdim == 2 && E > 0 && !force_lex;
+  if (want_snap) {
+    sx.S = snap_slices(n, W, E);
+    sx.B = (E + sx.S - 1) / sx.S;
+    VR_TRY(ws.alloc(&sbl, 2 * E));
+    VR_TRY(ws.alloc(&sboff, (int64_t)n * (sx.S + 1)));
+    if (sx.S > 1) VR_TRY(ws.alloc(&snap, (int64_t)(sx.S - 1) * n * sx.Wp));
+  }
   // Small complexes (maxdim 2, E <= EARLY_TRI_MAX_E): the lexicographic
   // triangle keys get a buffer sized by the bound on the triangles of a graph
   // with E edges, T <= (sqrt 2 / 3) E^(3/2), so the generator can be enqueued
@@ -501,6 +532,9 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(ws.commit());
   VR_TRY(out.commit());
   rs.err = &st->flags;
+  sx.snap = snap;
+  sx.bl = sbl;
+  sx.boff = sboff;
 
   const unsigned ge = grid_for(E, 256);
   if (E > 0) {
@@ -514,10 +548,10 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       prof.begin("fp64_repair");
       count_launch(6);
       int tkf = prof.begin("fp64_values");
-      launch_dep(k_f64_gather, ge, 256, 0, s, keys, E, d64_lex, adj, adjpre, W, deg, up, lex_ptr, d64, split);
+      launch_dep(k_f64_gather, ge, 256, 0, s, keys, E, d64_lex, adj, adjpre, W, deg, up, lex_ptr, d64, split, st);
       prof.end(tkf);
       VR_TRY((scan_exclusive<int32_t, int32_t>(split, gex, E, bs_e, s)));
-      launch_dep(k_group_starts, ge, 256, 0, s, split, gex, E, gbeg);
+      launch_dep(k_group_starts, ge, 256, 0, s, split, gex, E, gbeg, st);
       // Group count is gex[E]; launch over the E upper bound, threads skip.
       int tkr = prof.begin("fp64_regroup");
       launch_dep(k_repair_small, ge, 256, 0, s, gbeg, gex + E, keys, d64, midq, bigq, st);
@@ -542,28 +576,25 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_CUDA(cudaMemcpyAsync(ecol, &zero64, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   }
 
-  // Triangle order: lex mode (generation by first edge, stable sort on the
-  // grade) is forced for tetrahedra and for clouds above LEX_FORCE_N points,
-  // where the max-edge enumeration (each triangle a candidate at all three of
-  // its edges, two order lookups per candidate) costs more than the sort
-  // (measured on the 7322-point WorldMap-shaped cloud: 0.76 ms in lex mode,
-  // 1.19 ms in max-edge mode).  Otherwise lex_mode decides by the edge count
-  // and the share of tied grades.
-  const int force_lex = (maxdim >= 3 || n > LEX_FORCE_N) ? 1 : 0;
-  // Lex-mode candidate walk: rows with fewer neighbours on average than
-  // bitmap words take their candidates from the lexicographic edge list (one
-  // bit test each) instead of walking the words above b (the 7322-point
-  // WorldMap-shaped cloud: 77 neighbours per point, 229 words per row).
-  const int sparse_rows = 2 * E < (int64_t)n * W ? 1 : 0;
   if (maxdim >= 2 && E > 0) {
+    if (want_snap) {
+      // Time-sliced adjacency for the max-edge enumeration (returns at once
+      // when the device finds lex mode).
+      prof.begin("tri_snap");
+      launch_dep(k_snap_build, grid_for(n, 8, 32), 256, 0, s, adj, adjpre, W, n, nbr_ptr, nbr_ord, st, force_lex,
+                 sx.S, sx.B, snap, sbl, sboff);
+      count_launch();
+      VR_CUDA(cudaGetLastError());
+      prof.end();
+    }
     prof.begin("tri_count");
     const EdgeIndex exc{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
     if (eidx)
       launch_dep(k_tri_count<true>, grid_for(E, 8, 32), 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
-                 nbr_ord, st, tcnt, force_lex, exc, (const int64_t *)lex_ptr, sparse_rows);
+                 nbr_ord, st, tcnt, force_lex, exc, (const int64_t *)lex_ptr, sparse_rows, sx);
     else
       launch_dep(k_tri_count<false>, grid_for(E, 8, 32), 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
-                 nbr_ord, st, tcnt, force_lex, exc, (const int64_t *)lex_ptr, sparse_rows);
+                 nbr_ord, st, tcnt, force_lex, exc, (const int64_t *)lex_ptr, sparse_rows, sx);
     count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int64_t>(tcnt, toff, E, bs_e, s)));
     launch_dep(k_tri_groups, grid_for(E + 1, 256), 256, 0, s, gstart, tcnt, toff, tsmallq, tmidq, tbigq, st,
@@ -621,8 +652,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   uint64_t *tk_lex = nullptr;  // tetrahedra: the triangles' keys in lexicographic order
   int32_t *ordidx = nullptr, *cnt4 = nullptr;
   int64_t *off4 = nullptr, *bs_t = nullptr;
+  if (T > 0 && !early_tri) VR_TRY(ws.alloc(&tk, T));  // lex keys, or max-edge keys (e << 32) | z
   if (lexm) {
-    if (!early_tri) VR_TRY(ws.alloc(&tk, T));
     VR_TRY(ws.alloc(&trs.tkeys, T));
     VR_TRY(ws.alloc(&trs.meta, rs_meta_bytes(T)));
   }
@@ -674,21 +705,29 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       prof.end();
       prof.begin("tri_final");
       if (eidx)
-        launch_dep(k_tri_final<true>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, ex, tverts, tgrade, tcol, trow);
+        launch_dep(k_tri_final<true>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, ex, tverts, tgrade, tcol, trow, st);
       else
-        launch_dep(k_tri_final<false>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, ex, tverts, tgrade, tcol, trow);
+        launch_dep(k_tri_final<false>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, ex, tverts, tgrade, tcol, trow, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();
     } else if (T > 0) {
-      prof.begin("tri_emit");
-      // The emission keeps the neighbour-CSR lookups even with the dense
-      // table: its two lookups per candidate land in the rows' contiguous
-      // neighbour lists, while the table's are spread over n^2 entries
-      // (measured: 0.58 vs 0.65 ms on 19.8M triangles at n = 4000).
+      // Max-edge order: keys (e << 32) | z generated in final order from the
+      // time-sliced adjacency, then the final write; tie groups merged after.
+      prof.begin("tri_gen");
+      launch_dep(k_tri_gen_me, grid_for(E, 8, 32), 256, 0, s, everts, E, W, n, nbr_ptr, toff, T, tk, sx, st,
+                 force_lex);
+      count_launch();
+      VR_CUDA(cudaGetLastError());
+      prof.end();
+      prof.begin("tri_final");
       const EdgeIndex exm{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
-      launch_dep(k_tri_emit<false>, grid_for(E, 8, 32), 256, 0, s, everts, egrade, E, adj, adjpre, W, nbr_ptr,
-                 nbr_ord, toff, T, tverts, tgrade, tcol, trow, exm, st);
+      if (eidx)
+        launch_dep(k_tri_final_me<true>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, everts, egrade, exm, tverts,
+                   tgrade, tcol, trow, st);
+      else
+        launch_dep(k_tri_final_me<false>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, everts, egrade, exm,
+                   tverts, tgrade, tcol, trow, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();
@@ -696,7 +735,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       if (hst->small_seg_count > 0) {
         const size_t smem = (size_t)TRI_SMALL * (8 + 4 + 12);
         launch_dep(k_tri_fix_smem<TRI_SMALL>, std::min(hst->small_seg_count, num_sms() * 8), 256, smem, s, gstart, toff,
-                   tsmallq, &st->small_seg_count, tverts, trow);
+                   tsmallq, &st->small_seg_count, tverts, trow, st);
         count_launch();
         VR_CUDA(cudaGetLastError());
       }
@@ -705,7 +744,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
         VR_CUDA(cudaFuncSetAttribute(k_tri_fix_smem<TRI_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
         launch_dep(k_tri_fix_smem<TRI_MID>, std::min(hst->mid_seg_count, num_sms()), 512, smem, s, gstart, toff, tmidq,
-                   &st->mid_seg_count, tverts, trow);
+                   &st->mid_seg_count, tverts, trow, st);
         count_launch();
         VR_CUDA(cudaGetLastError());
       }
@@ -728,12 +767,12 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     if (tets) {
       prof.begin("tet_count");
       if (tpre) {
-        launch_dep(k_lex_pre, grid_for(E, 8, 32), 256, 0, s, lexe, E, adj, W, tpre);
+        launch_dep(k_lex_pre, grid_for(E, 8, 32), 256, 0, s, lexe, E, adj, W, tpre, st);
         count_launch();
       }
       launch_dep(k_tri_ordidx, grid_for(T, 256), 256, 0, s, tk, T, tk_lex, ordidx, toff, adj, adjpre, W, deg, up,
-                 lex_ptr, elp, n, tpre);
-      launch_dep(k_tet_count, grid_for(T, 8, 32), 256, 0, s, tk_lex, T, adj, W, cnt4);
+                 lex_ptr, elp, n, tpre, st);
+      launch_dep(k_tet_count, grid_for(T, 8, 32), 256, 0, s, tk_lex, T, adj, W, cnt4, st);
       count_launch(2);
       VR_TRY((scan_exclusive<int32_t, int64_t>(cnt4, off4, T, bs_t, s)));
       VR_CUDA(cudaGetLastError());
@@ -784,7 +823,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       prof.end();
       prof.begin("tet_final");
       launch_dep(k_tet_final, grid_for(T4, 256), 256, 0, s, keys4, T4, lex4, tk_lex, toff, adj, adjpre, W, deg, up,
-                 lex_ptr, ordidx, elp, n, packed ? 1 : 0, tpre, qverts, qgrade, qcol, qrow);
+                 lex_ptr, ordidx, elp, n, packed ? 1 : 0, tpre, qverts, qgrade, qcol, qrow, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();
@@ -792,6 +831,10 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     // Value errors raised by the tetrahedron kernels (internal checks).
     VR_TRY(read_status(st, sm, s));
   }
+
+  // The flags as the last kernel left them, for vr_complex_status.
+  VR_CUDA(cudaMemcpyAsync(late_flags, &st->flags, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  res->late_flags = late_flags;
 
   // Hand the outputs to the result.
   res->n = n;

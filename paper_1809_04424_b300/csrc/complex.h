@@ -20,6 +20,11 @@ struct vr_complex {
   double *grade_value = nullptr;
   int64_t ngrades = 0;
   vr_build_stats stats{};
+  // Device flags word as the build's last kernel left it (flags raised after
+  // the build's last size read: a bounded wait that gave up, an internal
+  // check); read by vr_complex_status and vr_complex_to_host.  Null for
+  // batch results (their flags travel in the per-cloud descriptors).
+  int32_t *late_flags = nullptr;
   std::vector<void *> allocs;   // device allocations owned by this result
   std::shared_ptr<void> arena;  // shared batch arenas this result views
   bool owned = true;            // false for views into a batch's arenas

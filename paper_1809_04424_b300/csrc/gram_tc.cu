@@ -66,8 +66,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 // Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long it = 0; it < TC_WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long limit = TC_WAIT_LIMIT) {
+  for (long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -171,6 +171,7 @@ __global__ void k_gram_prep(const void *Xv, int n, int d, int npad, const float 
 // the pairs), bits ORed into both rows.
 __global__ void k_band_patch(const float *X, int d, int W, double r2, const uint64_t *band, const DevStatus *st,
                              uint64_t band_cap, uint32_t *adj) {
+  if (build_failed(st)) return;  // a timed-out tile left its bitmap words unwritten
   const uint64_t cnt = min((unsigned long long)st->band_count, (unsigned long long)band_cap);
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < cnt; t += (uint64_t)gridDim.x * blockDim.x) {
     const int i = (int)(band[t] >> 32), j = (int)(band[t] & 0xffffffffu);
@@ -213,12 +214,18 @@ struct TcSmem {
 // pairs within beta of the cap are appended to `band` (decided exactly by
 // k_band_patch); VALIDATE instead computes the canonical value of every pair
 // and records the worst observed |d2_tc - d2_fp64| / (|y_i|^2 + |y_j|^2).
-template <bool F, bool VALIDATE>
+// INJ (test hook, vr_inject_gram_stall): CTA `stall_tile` issues no MMA and
+// no completion, so its waits run out after `wait_limit` polls.
+template <bool F, bool VALIDATE, bool INJ = false>
 __global__ void __launch_bounds__(TC_THREADS) k_gram_bitmap_tc(const __grid_constant__ CUtensorMap tmh,
                                                         const __grid_constant__ CUtensorMap tml, const void *Xv,
                                                         int n, int d, int W, int nt, Cap cap, const float *norm,
                                                         uint32_t *adj, DevStatus *st, uint64_t *band,
-                                                        uint64_t band_cap, unsigned int *worst_bits) {
+                                                        uint64_t band_cap, unsigned int *worst_bits,
+                                                        int stall_tile = -1, long wait_limit = TC_WAIT_LIMIT) {
+  // Only the stalled CTA's completion wait takes the short limit: every other
+  // wait guards a TMA load or an MMA that is really in flight.
+  const bool stalled = INJ && (int)blockIdx.x == stall_tile;
   extern __shared__ unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // Tile pair from the linear block index.
@@ -266,7 +273,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_bitmap_tc(const __grid_cons
       tma_load_2d(S.al, &tml, 0, ti * TC_TILE, S.bar_tma);
       tma_load_2d(S.bl, &tml, 0, tj * TC_TILE, S.bar_tma);
     }
-    if (mbar_wait(S.bar_tma, 0)) {
+    if (stalled) {
+      // Test hook: the operands arrived (waited for, so nothing is in flight
+      // when TMEM is released), but no MMA and no completion are issued.
+      if (!mbar_wait(S.bar_tma, 0)) raise_flag(st, F_TIMEOUT);
+    } else if (mbar_wait(S.bar_tma, 0)) {
       tc_fence_after();
       uint32_t acc = 0;
       const uint32_t As[3] = {S.ah, S.ah, S.al}, Bs[3] = {S.bh, S.bl, S.bh};
@@ -282,7 +293,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_bitmap_tc(const __grid_cons
       mbar_arrive(S.bar_mma);  // release the other threads; nothing was issued
     }
   }
-  const bool ok = mbar_wait(S.bar_mma, 0);
+  const bool ok = mbar_wait(S.bar_mma, 0, stalled ? wait_limit : TC_WAIT_LIMIT);
   tc_fence_after();
   if (!ok && lane == 0) raise_flag(st, F_TIMEOUT);
 
@@ -393,6 +404,10 @@ static vr_status make_map(CUtensorMap *m, void *base, int npad) {
 
 static int g_gram_mode = 0;  // 0 auto, 1 tensor cores where eligible, 2 CUDA cores
 
+// Test hook: takes (and disarms) an armed Gram stall for a launch of `tiles`
+// tiles (api.cu, vr_inject_gram_stall).
+bool take_gram_stall(int tiles, int *tile, long *limit);
+
 // Tensor-core tiles pay off once there are enough 128x128 tiles to fill the
 // GPU (two per SM); mode 1 forces them wherever they apply.
 bool gram_tc_eligible(vr_dtype dtype, int n, int d) {
@@ -430,10 +445,10 @@ vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, ui
     return cuda_status(e, "gram_bitmap_tc", __FILE__, __LINE__);
   };
   cudaError_t e;
-  if ((e = cudaMallocAsync((void **)&Xh, (size_t)npad * TC_ROW_BYTES, s)) != cudaSuccess) return fail(e);
-  if ((e = cudaMallocAsync((void **)&Xl, (size_t)npad * TC_ROW_BYTES, s)) != cudaSuccess) return fail(e);
-  if ((e = cudaMallocAsync((void **)&norm, (size_t)npad * 4, s)) != cudaSuccess) return fail(e);
-  if ((e = cudaMallocAsync((void **)&centre, (size_t)TC_K * 4, s)) != cudaSuccess) return fail(e);
+  if ((e = dev_malloc((void **)&Xh, (size_t)npad * TC_ROW_BYTES, s)) != cudaSuccess) return fail(e);
+  if ((e = dev_malloc((void **)&Xl, (size_t)npad * TC_ROW_BYTES, s)) != cudaSuccess) return fail(e);
+  if ((e = dev_malloc((void **)&norm, (size_t)npad * 4, s)) != cudaSuccess) return fail(e);
+  if ((e = dev_malloc((void **)&centre, (size_t)TC_K * 4, s)) != cudaSuccess) return fail(e);
   CUtensorMap mh, ml;
   vr_status vs = make_map(&mh, Xh, npad);
   if (vs == VR_OK) vs = make_map(&ml, Xl, npad);
@@ -453,7 +468,7 @@ vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, ui
   const uint64_t npairs = (uint64_t)n * (n - 1) / 2;
   const uint64_t band_cap = std::min<uint64_t>(npairs, std::max<uint64_t>(1u << 20, npairs / 16));
   if (F && !worst_bits) {
-    if ((e = cudaMallocAsync((void **)&band, band_cap * 8, s)) != cudaSuccess) return fail(e);
+    if ((e = dev_malloc((void **)&band, band_cap * 8, s)) != cudaSuccess) return fail(e);
     if ((e = cudaMemsetAsync(&st->band_count, 0, 8, s)) != cudaSuccess) return fail(e);
   }
   if (F && worst_bits) {
@@ -463,19 +478,39 @@ vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, ui
     k_gram_bitmap_tc<true, true><<<ntiles, TC_THREADS, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st, nullptr, 0,
                                                            worst_bits);
   } else if (F) {
-    if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
-      return fail(e);
-    k_gram_bitmap_tc<true, false><<<ntiles, TC_THREADS, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st, band,
-                                                            band_cap, nullptr);
+    int stall_tile = -1;
+    long stall_limit = TC_WAIT_LIMIT;
+    if (take_gram_stall(ntiles, &stall_tile, &stall_limit)) {
+      if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem)) != cudaSuccess)
+        return fail(e);
+      k_gram_bitmap_tc<true, false, true><<<ntiles, TC_THREADS, smem, s>>>(
+          mh, ml, X, n, d, W, nt, cap, norm, adj, st, band, band_cap, nullptr, stall_tile, stall_limit);
+    } else {
+      if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem)) != cudaSuccess)
+        return fail(e);
+      k_gram_bitmap_tc<true, false><<<ntiles, TC_THREADS, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st, band,
+                                                              band_cap, nullptr);
+    }
     k_band_patch<<<num_sms() * 4, 256, 0, s>>>((const float *)X, d, W, cap.r2, band, st, band_cap, adj);
     count_launch();
   } else {
-    if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
-      return fail(e);
-    k_gram_bitmap_tc<false, false><<<ntiles, TC_THREADS, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st, nullptr, 0,
-                                                             nullptr);
+    int stall_tile = -1;
+    long stall_limit = TC_WAIT_LIMIT;
+    if (take_gram_stall(ntiles, &stall_tile, &stall_limit)) {
+      if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<false, false, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return fail(e);
+      k_gram_bitmap_tc<false, false, true><<<ntiles, TC_THREADS, smem, s>>>(
+          mh, ml, X, n, d, W, nt, cap, norm, adj, st, nullptr, 0, nullptr, stall_tile, stall_limit);
+    } else {
+      if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem)) != cudaSuccess)
+        return fail(e);
+      k_gram_bitmap_tc<false, false><<<ntiles, TC_THREADS, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st,
+                                                               nullptr, 0, nullptr);
+    }
   }
   count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
@@ -514,9 +549,9 @@ extern "C" vr_status vr_gram_error_check(const float *points, int32_t n, int32_t
   uint32_t *adj = nullptr;
   DevStatus *st = nullptr;
   unsigned int *worst = nullptr;
-  VR_CUDA(cudaMallocAsync((void **)&adj, (size_t)n * W * 4, s));
-  VR_CUDA(cudaMallocAsync((void **)&st, sizeof(DevStatus), s));
-  VR_CUDA(cudaMallocAsync((void **)&worst, 4, s));
+  VR_CUDA(dev_malloc((void **)&adj, (size_t)n * W * 4, s));
+  VR_CUDA(dev_malloc((void **)&st, sizeof(DevStatus), s));
+  VR_CUDA(dev_malloc((void **)&worst, 4, s));
   VR_CUDA(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
   VR_CUDA(cudaMemsetAsync(worst, 0, 4, s));
   Cap cap{};

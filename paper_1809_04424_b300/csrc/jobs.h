@@ -35,6 +35,7 @@ int64_t job_out_bytes(Job *j);                 // admitted output bytes
 void job_finish(Job *j, std::vector<vr_complex *> &results, std::vector<vr_status> &status, bool detach);
 void job_destroy(Job *j);
 bool fused_fits(int n, int d);                 // can the batch kernels take this cloud?
+void inject_admission_refusals(int64_t k);     // test hook: refuse the next k admissions outright
 vr_status check_cloud_args(int64_t n, int d, vr_dtype dtype, int maxdim, double maxrad);
 
 }  // namespace vr

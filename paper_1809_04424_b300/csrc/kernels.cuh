@@ -320,6 +320,7 @@ static __global__ void __launch_bounds__(256) k_rows_scan(const uint32_t *adj, i
                                                           int32_t *deg, int32_t *up, int32_t *nbr_ptr,
                                                           int64_t *lex_ptr, DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   __shared__ int64_t sh[33];
   __shared__ unsigned int ticket;
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -456,8 +457,10 @@ __device__ __forceinline__ int32_t bit_rank(const uint32_t *adj_row, const int32
 template <bool F>
 __global__ void __launch_bounds__(256) k_edge_keys(const void *Xv, int n, int d, int W, const uint32_t *adj,
                                                    const int64_t *lex_ptr, uint64_t *keys, uint32_t *lexe,
-                                                   int32_t *elp, KeyHist kh) {
+                                                   int32_t *elp, KeyHist kh,
+    const DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   using T = typename std::conditional<F, float, int32_t>::type;
   __shared__ KeyHistSmem hs;
   __shared__ uint16_t cbuf[8][CB_SLOTS];
@@ -564,8 +567,10 @@ static __global__ void __launch_bounds__(256) k_dmat_bitmap(const void *Dv, int 
 template <bool F>
 static __global__ void __launch_bounds__(256) k_dmat_keys(const void *Dv, int n, int W, const uint32_t *adj,
                                                           const int64_t *lex_ptr, uint64_t *keys, uint32_t *lexe,
-                                                          int32_t *elp, KeyHist kh) {
+                                                          int32_t *elp, KeyHist kh,
+    const DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   __shared__ KeyHistSmem hs;
   __shared__ uint16_t cbuf[8][CB_SLOTS];
   khist_init(hs, kh);
@@ -636,8 +641,10 @@ __device__ __forceinline__ double soft_value(const SoftAcc &s) {
 // kept j > i in ascending j at lex_ptr[i] + k (and its position in the dense
 // table elp, when given).
 static __global__ void __launch_bounds__(256) k_lex_edges(int n, int W, const uint32_t *adj, const int64_t *lex_ptr,
-                                                          uint32_t *lexe, int32_t *elp) {
+                                                          uint32_t *lexe, int32_t *elp,
+    const DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   __shared__ uint16_t cbuf[8][CB_SLOTS];
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int l = lane_id();
@@ -675,6 +682,7 @@ static __global__ void __launch_bounds__(EKF_WARPS * 32) k_edge_keys_f32(const f
                                                                          uint64_t *keys, double *d64_lex,
                                                                          DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   __shared__ float ti[EKF_WARPS][32][33], tj[EKF_WARPS][32][33];
   const int wid = threadIdx.x >> 5, l = lane_id();
   const int64_t E = st->E, nch = (E + 31) / 32;
@@ -748,8 +756,10 @@ __device__ __forceinline__ int key_j(uint64_t k) { return (int)(k & ID_MASK); }
 // FP64 order; only runs of equal keys need re-sorting by (FP64, i, j).
 static __global__ void k_f64_gather(const uint64_t *keys, int64_t E, const double *d64_lex, const uint32_t *adj,
                                     const int32_t *adjpre, int W, const int32_t *deg, const int32_t *up,
-                                    const int64_t *lex_ptr, double *d64, int32_t *split) {
+                                    const int64_t *lex_ptr, double *d64, int32_t *split,
+    const DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = keys[k];
     const int i = (int)((key >> ID_BITS) & ID_MASK), j = (int)(key & ID_MASK);
@@ -760,8 +770,10 @@ static __global__ void k_f64_gather(const uint64_t *keys, int64_t E, const doubl
 }
 
 // Group starts from the exclusive scan of split: gbeg[gid] = k.
-static __global__ void k_group_starts(const int32_t *split, const int32_t *gex, int64_t E, int32_t *gbeg) {
+static __global__ void k_group_starts(const int32_t *split, const int32_t *gex, int64_t E, int32_t *gbeg,
+    const DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x)
     if (split[k]) gbeg[gex[k]] = (int32_t)k;
   if (blockIdx.x == 0 && threadIdx.x == 0) gbeg[gex[E]] = (int32_t)E;
@@ -779,6 +791,7 @@ constexpr int REPAIR_MID = 2048;
 static __global__ void k_repair_small(const int32_t *gbeg, const int32_t *ngroups_ptr, uint64_t *keys, double *d64,
                                int32_t *midq, int32_t *bigq, DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   const int64_t ngroups = *ngroups_ptr;
   int64_t nt = 0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
@@ -817,6 +830,7 @@ static __global__ void k_repair_small(const int32_t *gbeg, const int32_t *ngroup
 static __global__ void __launch_bounds__(256) k_repair_mid(const int32_t *gbeg, const int32_t *midq, const DevStatus *st,
                                                     uint64_t *keys, double *d64) {
   pdl_entry();
+  if (build_failed(st)) return;
   __shared__ uint64_t hi[REPAIR_MID];
   __shared__ uint32_t lo[REPAIR_MID];
   __shared__ uint32_t val[REPAIR_MID];
@@ -879,6 +893,7 @@ static __global__ void __launch_bounds__(RS_THREADS) k_repair_big(const int32_t 
                                                            uint64_t *k1, uint32_t *v1, uint64_t *k2, uint32_t *v2,
                                                            uint64_t *gk, double *gd) {
   pdl_entry();
+  if (build_failed(st)) return;
   const int nq = (int)st->big_grp_count;
   for (int q = 0; q < nq; ++q) {
     const int g = bigq[q];
@@ -926,6 +941,7 @@ __global__ void __launch_bounds__(256) k_edge_grades(const uint64_t *keys, const
                                                      int32_t *nbr_ord, int32_t *eidx, int32_t *egd, int n, int key_f32,
                                                      uint64_t *lb, int64_t ntiles, DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   constexpr int PER = EG_TILE / 256;
   __shared__ int64_t sh[33];
   __shared__ int64_t tile_sh, pre_sh;
@@ -1024,14 +1040,13 @@ __device__ __forceinline__ uint64_t lex3(int a, int b, int c) {
 }
 
 // Triangles in lexicographic order + a sort on the grade bits: chosen when
-// more than 5% of edges share a grade, from LEX_MIN_E kept edges on (the
-// max-edge enumeration checks every triangle at all three of its edges and
-// costs more than the sort there: on Gaussian-mixture clouds with d = 8 and 32
-// the two meet near 150k edges), and always for tetrahedra (which are
-// generated from the lexicographic triangle list).
-constexpr int64_t LEX_MIN_E = 1 << 17;
+// more than 5% of edges share a grade (tie-heavy integer data: the max-edge
+// output would need most grade groups merged), and always when the caller
+// forces it (tetrahedra, which are generated from the lexicographic triangle
+// list; clouds with sparse rows, where the time-sliced rows of the max-edge
+// enumeration cost more than walking the few neighbours).
 __host__ __device__ __forceinline__ bool lex_mode(int64_t E, int64_t ngrades, int force = 0) {
-  return force || E >= LEX_MIN_E || (E - (ngrades - 1)) * 20 > E;
+  return force || (E - (ngrades - 1)) * 20 > E;
 }
 
 __device__ __forceinline__ int64_t lex_pos(int a, int b, const uint32_t *adj, const int32_t *adjpre, int W,
@@ -1063,16 +1078,93 @@ struct EdgeIndex {
   }
 };
 
+// ---- max-edge enumeration through time-sliced adjacency
+// In max-edge order a triangle {x, y, z} is produced by its largest edge
+// e = (x, y) (order index e) and its third vertices are
+//   S_e = { z : ord(x, z) < e and ord(y, z) < e } = B_x(e) & B_y(e),
+// B_v(e) being the bitmap of v's neighbours through edges earlier than e.
+// The edge orders are cut into S time slices of B consecutive edges; for
+// each slice b >= 1 a snapshot holds every vertex's bitmap B_v(b * B) (edges
+// of earlier slices), and every vertex's neighbour list is bucketed by slice.
+// Then B_v(e) = snapshot_{e / B}[v] | { z in bucket (v, e / B) : ord < e }:
+// one row read plus a short filtered bucket, no per-candidate lookup; S_e
+// comes out as a bitmap, in ascending z (lexicographic within the edge).
+constexpr int SNAP_MAX_S = 32;
+struct SnapIdx {
+  const uint32_t *snap;  // (S - 1) x n x Wp words: snapshot b (1 .. S - 1) at (b - 1) * n * Wp
+  const uint64_t *bl;    // 2E entries (order << 32) | neighbour, vertex v's from nbr_ptr[v], by slice
+  const int32_t *boff;   // n x (S + 1): slice starts within v's entries (relative to nbr_ptr[v])
+  int S;
+  int64_t B;
+  int Wp;                // snapshot row stride: W rounded up to 16-byte words (4 words), padding zero
+};
+__host__ __device__ __forceinline__ int snap_stride(int W) { return (W + 3) & ~3; }
+
+// One warp per vertex v: bucket v's neighbour entries by slice (counts, then
+// a scatter; the order inside a bucket is immaterial: buckets are filtered,
+// not walked in order) and write v's snapshot rows.  Runs in max-edge mode
+// only (decided on the device, like the count kernel).
+static __global__ void __launch_bounds__(256) k_snap_build(const uint32_t *adj, const int32_t *adjpre, int W, int n,
+                                                           const int32_t *nbr_ptr, const int32_t *nbr_ord,
+                                                           const DevStatus *st, int force_lex, int S, int64_t B,
+                                                           uint32_t *snap, uint64_t *bl, int32_t *boff) {
+  pdl_entry();
+  if (build_failed(st)) return;
+  if (lex_mode(st->E, st->ngrades, force_lex)) return;
+  __shared__ int32_t cur[8][SNAP_MAX_S + 1];
+  __shared__ uint32_t sw[8][SNAP_MAX_S - 1][32];  // one round: lane l's word in each snapshot
+  const int l = lane_id(), wid = threadIdx.x >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  const int64_t nWp = (int64_t)n * snap_stride(W);
+  for (int64_t v = blockIdx.x * 8 + wid; v < n; v += nwarps) {
+    const int32_t ptr = nbr_ptr[v], deg = nbr_ptr[v + 1] - ptr;
+    for (int b = l; b <= S; b += 32) cur[wid][b] = 0;
+    __syncwarp();
+    for (int k = l; k < deg; k += 32) atomicAdd(&cur[wid][(int)(nbr_ord[ptr + k] / B)], 1);
+    __syncwarp();
+    if (l == 0) {
+      int32_t run = 0;
+      for (int b = 0; b <= S; ++b) {
+        boff[v * (S + 1) + b] = run;
+        const int32_t c = cur[wid][b];
+        cur[wid][b] = run;
+        run += c;
+      }
+    }
+    __syncwarp();
+    const uint32_t *row = adj + v * W;
+    const int32_t *pre = adjpre + v * W;
+    const int Wp = snap_stride(W);
+    for (int w0 = 0; w0 < Wp; w0 += 32) {
+      const int w = w0 + l;
+      uint32_t m = w < W ? row[w] : 0u;
+      int32_t k = w < W ? pre[w] : 0;  // entry index of the word's lowest set bit
+      for (int b = 0; b < S - 1; ++b) sw[wid][b][l] = 0u;
+      for (; m; m &= m - 1, ++k) {
+        const int bit = __ffs(m) - 1;
+        const int32_t o = nbr_ord[ptr + k];
+        const int bb = (int)(o / B);
+        const int32_t slot = atomicAdd(&cur[wid][bb], 1);
+        bl[ptr + slot] = ((uint64_t)(uint32_t)o << 32) | (uint32_t)(w * 32 + bit);
+        for (int b = bb + 1; b < S; ++b) sw[wid][b - 1][l] |= 1u << bit;
+      }
+      if (w < Wp)
+        for (int b = 1; b < S; ++b) snap[(b - 1) * nWp + v * Wp + w] = sw[wid][b - 1][l];
+    }
+    __syncwarp();
+  }
+}
+
 template <bool DENSE>
 static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts, const uint32_t *lexe, int64_t E,
                                                           const uint32_t *adj, const int32_t *adjpre, int W,
                                                           const int32_t *nbr_ptr, const int32_t *nbr_ord,
                                                           const DevStatus *st, int32_t *tcnt, int force_lex,
-                                                          EdgeIndex ex, const int64_t *lex_ptr, int sparse) {
+                                                          EdgeIndex ex, const int64_t *lex_ptr, int sparse,
+                                                          SnapIdx sx) {
   pdl_entry();
-  __shared__ uint16_t cbuf[8][CB_SLOTS];
+  if (build_failed(st)) return;
   const int l = lane_id();
-  uint16_t *cb = cbuf[threadIdx.x >> 5];
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   if (lex_mode(E, st->ngrades, force_lex) && sparse) {
     // Lex mode on sparse rows (fewer neighbours than bitmap words): the
@@ -1149,44 +1241,163 @@ static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts,
     }
     return;
   }
-  // Max-edge mode: edges in filtration order; the count of edge e is the
-  // number of common neighbours c whose edges to a and b both come before e.
-  for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
-    const int a = everts[2 * e], b = everts[2 * e + 1];
-    const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
-    const int32_t *pa = adjpre + (int64_t)a * W, *pb = adjpre + (int64_t)b * W;
-    const int32_t *oa = nbr_ord + nbr_ptr[a], *ob = nbr_ord + nbr_ptr[b];
+  // Max-edge mode: edges in filtration order.  With Sx, Sy the slice
+  // snapshot rows of x and y and Dx, Dy their bucket entries earlier than e
+  // (disjoint from the snapshots; k_snap_build), the count of e = (x, y) is
+  //   |Sx & Sy| + |Dy & Sx| + |Dx & B_y(e)|,
+  // the last term by one adjacency bit and one order lookup per entry.  An
+  // edge per 8 lanes (4 per warp): every load of an edge is independent of
+  // the others, so each lane keeps many in flight (no shared memory, no
+  // dependent chain beyond the edge's endpoints and bucket bounds).
+  const int sub = l >> 3, sl = l & 7;
+  for (int64_t e = (blockIdx.x * 8 + (threadIdx.x >> 5)) * 4 + sub; e - sub < E; e += nwarps * 4) {
     int cnt = 0;
-    for (int w0 = 0; w0 < W; w0 += 32) {
-      const int w = w0 + l;
-      const uint32_t m = w < W ? ra[w] & rb[w] : 0u;
-      const int tot = bit_compact(m, w, cb);
-      __syncwarp();
-      for (int q0 = 0; q0 < tot; q0 += 32) {
-        const int q = q0 + l;
-        bool ok = false;
-        if (q < tot) {
-          const int cv = cb[q];
-          if constexpr (DENSE) {
-            ok = ex.ord<true>(min(a, cv), max(a, cv)) < (int32_t)e && ex.ord<true>(min(b, cv), max(b, cv)) < (int32_t)e;
-          } else {
-            const int ww = cv >> 5;
-            const uint32_t below = (1u << (cv & 31)) - 1u;
-            ok = oa[pa[ww] + __popc(ra[ww] & below)] < (int32_t)e && ob[pb[ww] + __popc(rb[ww] & below)] < (int32_t)e;
-          }
+    if (e < E) {
+      const int2 xy = ((const int2 *)everts)[e];
+      const int x = xy.x, y = xy.y;
+      const int b = (int)(e / sx.B);
+      const uint32_t *rx = b > 0 ? sx.snap + ((int64_t)(b - 1) * ex.n + x) * sx.Wp : nullptr;
+      const uint32_t *ry = b > 0 ? sx.snap + ((int64_t)(b - 1) * ex.n + y) * sx.Wp : nullptr;
+      if (b > 0) {
+        const uint4 *vx = (const uint4 *)rx, *vy = (const uint4 *)ry;
+#pragma unroll 4
+        for (int q = sl; q < (sx.Wp >> 2); q += 8) {
+          const uint4 a = vx[q], c = vy[q];
+          cnt += __popc(a.x & c.x) + __popc(a.y & c.y) + __popc(a.z & c.z) + __popc(a.w & c.w);
         }
-        cnt += __popc(__ballot_sync(0xffffffffu, ok));
       }
-      __syncwarp();
+      const int32_t *ox = sx.boff + (int64_t)x * (sx.S + 1) + b, *oy = sx.boff + (int64_t)y * (sx.S + 1) + b;
+      const int32_t ox0 = ox[0], ox1 = ox[1], oy0 = oy[0], oy1 = oy[1];
+      const uint64_t *lx = sx.bl + nbr_ptr[x], *ly = sx.bl + nbr_ptr[y];
+      const uint32_t *ay = adj + (int64_t)y * W;
+      for (int32_t k = ox0 + sl; k < ox1; k += 8) {
+        const uint64_t t = lx[k];
+        const int z = (int)(t & 0xffffu);
+        const bool adjy = (ay[z >> 5] >> (z & 31)) & 1u;
+        int32_t oyz;
+        if constexpr (DENSE) oyz = ex.ord<true>(min(y, z), max(y, z));  // in the table; used only when adjacent
+        else oyz = adjy ? ex.ord<false>(min(y, z), max(y, z)) : INT32_MAX;
+        cnt += (int64_t)(t >> 32) < e && adjy && oyz < (int32_t)e;
+      }
+      if (b > 0)
+        for (int32_t k = oy0 + sl; k < oy1; k += 8) {
+          const uint64_t t = ly[k];
+          const int z = (int)(t & 0xffffu);
+          cnt += (int64_t)(t >> 32) < e && ((rx[z >> 5] >> (z & 31)) & 1u);
+        }
     }
-    if (l == 0) tcnt[e] = cnt;  // every lane holds the warp total
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, 1);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, 2);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, 4);
+    if (sl == 0 && e < E) tcnt[e] = cnt;
+  }
+}
+
+// Max-edge generation: an edge e = (x, y) per half-warp (16 lanes), edges in
+// filtration order; its third vertices S_e = (Sx | Dx) & (Sy | Dy) in
+// ascending z go out as keys (e << 32) | z at toff[e] on.  Lane s of the
+// half owns the contiguous words [s K, s K + K) of both snapshot rows (K =
+// Wp / 16, 16-byte loads); the bucket entries earlier than e are or-ed into
+// two shared rows of the half; one scan of the lanes' bit counts places
+// every lane's run of keys, which the lane writes in order.  The keys are
+// in final (max-edge) order: no sort follows.
+constexpr int MEG_KMAX = VR_MAX_POINTS / 32 / 16;  // words per lane and row at most
+static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts, int64_t E, int W, int n,
+                                                           const int32_t *nbr_ptr, const int64_t *toff, int64_t T,
+                                                           uint64_t *tkeys, SnapIdx sx, DevStatus *st,
+                                                           int force_lex) {
+  pdl_entry();
+  if (build_failed(st)) return;
+  if (lex_mode(E, st->ngrades, force_lex)) return;  // (a launch ahead of the host's decision)
+  constexpr int WMAX = VR_MAX_POINTS / 32;
+  __shared__ uint4 drow[8][2][2 * WMAX / 4];  // per warp, per half: Dx then Dy (16-byte words)
+  const int l = lane_id(), wid = threadIdx.x >> 5, half = l >> 4, s16 = l & 15;
+  // Words per lane: Wp / 16 rounded up to whole 16-byte chunks (K <= 16 since
+  // Wp <= 256); a lane's chunks past Wp are neither loaded nor used.
+  const int Wp = sx.Wp, K = (((Wp + 15) >> 4) + 3) & ~3, K4 = K >> 2;
+  uint32_t *dx = (uint32_t *)drow[wid][half], *dy = dx + WMAX;
+  const int64_t nwarps = (int64_t)gridDim.x * 8;
+  for (int64_t e = (blockIdx.x * 8 + wid) * 2 + half; e - half < E; e += nwarps * 2) {
+    const bool live = e < E;
+    int x = 0, y = 0, b = 0;
+    if (live) {
+      const int2 xy = ((const int2 *)everts)[e];
+      x = xy.x;
+      y = xy.y;
+      b = (int)(e / sx.B);
+    }
+    // This lane's words [w0, w0 + K) of both rows (zero before the first
+    // snapshot and past Wp), and its delta words cleared.
+    const int w0 = s16 * K;
+    uint32_t wx[MEG_KMAX], wy[MEG_KMAX];
+    {
+      const uint4 *vx = (const uint4 *)(sx.snap + ((int64_t)(b > 0 ? b - 1 : 0) * n + x) * Wp + w0);
+      const uint4 *vy = (const uint4 *)(sx.snap + ((int64_t)(b > 0 ? b - 1 : 0) * n + y) * Wp + w0);
+      const bool in = live && b > 0;
+#pragma unroll
+      for (int q = 0; q < MEG_KMAX / 4; ++q) {
+        uint4 a = make_uint4(0u, 0u, 0u, 0u), c = a;
+        if (in && q < K4 && w0 + 4 * q < Wp) {
+          a = vx[q];
+          c = vy[q];
+        }
+        wx[4 * q] = a.x; wx[4 * q + 1] = a.y; wx[4 * q + 2] = a.z; wx[4 * q + 3] = a.w;
+        wy[4 * q] = c.x; wy[4 * q + 1] = c.y; wy[4 * q + 2] = c.z; wy[4 * q + 3] = c.w;
+        if (q < K4) {
+          ((uint4 *)(dx + w0))[q] = make_uint4(0u, 0u, 0u, 0u);
+          ((uint4 *)(dy + w0))[q] = make_uint4(0u, 0u, 0u, 0u);
+        }
+      }
+    }
+    __syncwarp();
+    if (live) {
+      const int32_t *ox = sx.boff + (int64_t)x * (sx.S + 1) + b, *oy = sx.boff + (int64_t)y * (sx.S + 1) + b;
+      const uint64_t *lx = sx.bl + nbr_ptr[x], *ly = sx.bl + nbr_ptr[y];
+      const int32_t ox1 = ox[1], oy1 = oy[1];
+      for (int32_t k = ox[0] + s16; k < ox1; k += 16) {
+        const uint64_t t = lx[k];
+        if ((int64_t)(t >> 32) < e) atomicOr(&dx[(t & 0xffffu) >> 5], 1u << (t & 31));
+      }
+      for (int32_t k = oy[0] + s16; k < oy1; k += 16) {
+        const uint64_t t = ly[k];
+        if ((int64_t)(t >> 32) < e) atomicOr(&dy[(t & 0xffffu) >> 5], 1u << (t & 31));
+      }
+    }
+    __syncwarp();
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < MEG_KMAX; ++k) {
+      if (k < K) {
+        wx[k] = (wx[k] | dx[w0 + k]) & (wy[k] | dy[w0 + k]);
+        c += __popc(wx[k]);
+      }
+    }
+    int inc = c;  // inclusive scan over the half's 16 lanes
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, d, 16);
+      if (s16 >= d) inc += v;
+    }
+    if (live && c) {
+      int64_t p = toff[e] + inc - c;
+      const uint64_t ek = (uint64_t)e << 32;
+#pragma unroll
+      for (int k = 0; k < MEG_KMAX; ++k) {
+        if (k >= K) break;
+        for (uint32_t mm = wx[k]; mm; mm &= mm - 1, ++p) {
+          if (p < T) tkeys[p] = ek | (uint32_t)((w0 + k) * 32 + __ffs(mm) - 1);
+          else raise_flag(st, F_INTERNAL);  // never write past the key array
+        }
+      }
+    }
+    __syncwarp();
   }
 }
 
 // Lex-order generation: warp per edge (a, b), taken in lexicographic order
 // (lexe); its triangles (a, b, c), c > b ascending, land at toff[e]; the key
 // carries the triangle's grade (largest of its three edge grades).
-// Coalesced chunked stores as in k_tri_emit.  T: the key buffer's capacity
+// Coalesced chunked stores.  T: the key buffer's capacity
 // (at least the triangle count).
 template <bool DENSE>
 static __global__ void __launch_bounds__(256) k_lex_tri_gen(const uint32_t *lexe, const int32_t *egrade, int64_t E,
@@ -1196,6 +1407,7 @@ static __global__ void __launch_bounds__(256) k_lex_tri_gen(const uint32_t *lexe
                                                             EdgeIndex ex, DevStatus *st, int force_lex,
                                                             const int64_t *lex_ptr, int sparse) {
   pdl_entry();
+  if (build_failed(st)) return;
   if (!lex_mode(E, st->ngrades, force_lex)) return;  // max-edge order (a launch ahead of the host's decision)
   if (sparse) {
     // Sparse rows (as in k_tri_count): the candidates c of edge (a, b) are
@@ -1305,8 +1517,10 @@ __device__ __forceinline__ void tri_final_one(uint64_t k, const EdgeIndex &ex, i
 template <bool DENSE>
 static __global__ void __launch_bounds__(256) k_tri_final(const uint64_t *tkeys, int64_t T, EdgeIndex ex,
                                                           int32_t *tverts, int32_t *tgrade, int64_t *tcolptr,
-                                                          int32_t *trow) {
+                                                          int32_t *trow,
+    const DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   __shared__ int4 sv[8][96], sr[8][96];  // per warp: 128 triangles x 3 ints
   const int wid = threadIdx.x >> 5, l = lane_id();
   int32_t *svi = (int32_t *)sv[wid], *sri = (int32_t *)sr[wid];
@@ -1351,79 +1565,75 @@ static __global__ void __launch_bounds__(256) k_tri_final(const uint64_t *tkeys,
   }
 }
 
-// Emission.  Each round (32 words, one per lane) the warp compacts the
-// candidates of its words (bit_compact) and checks them in chunks of 32, lane
-// q taking the round's q-th; the kept ones of a chunk take consecutive output
-// slots (ballot prefix), so stores are coalesced.
-// DENSE: the two edge positions of a candidate come from the dense
-// order-index table (one load each) instead of bitmap rank + CSR.
+// Final write of max-edge keys (e << 32) | z, already in (grade, lex) order
+// up to tie groups: the edge's endpoints from the edge list, the two other
+// faces' order indices from the dense table (or the neighbour CSR).  Same
+// store pattern as k_tri_final (128 triangles per warp, vertices and rows
+// staged in shared memory for 16-byte stores).
+__device__ __forceinline__ void tri_final_me_one(uint64_t k, const int32_t *everts, const int32_t *egrade,
+                                                 const EdgeIndex &ex, int32_t *v, int32_t *r, int32_t &g,
+                                                 bool dense) {
+  const int32_t e = (int32_t)(k >> 32);
+  const int z = (int)(k & 0xffffu);
+  const int2 xy = ((const int2 *)everts)[e];
+  const int x = xy.x, y = xy.y;
+  const int32_t oxz = dense ? ex.ord<true>(min(x, z), max(x, z)) : ex.ord<false>(min(x, z), max(x, z));
+  const int32_t oyz = dense ? ex.ord<true>(min(y, z), max(y, z)) : ex.ord<false>(min(y, z), max(y, z));
+  if (z < x) { v[0] = z; v[1] = x; v[2] = y; }
+  else if (z < y) { v[0] = x; v[1] = z; v[2] = y; }
+  else { v[0] = x; v[1] = y; v[2] = z; }
+  r[0] = min(oxz, oyz); r[1] = max(oxz, oyz); r[2] = e;
+  g = egrade[e];
+}
+
 template <bool DENSE>
-static __global__ void __launch_bounds__(256) k_tri_emit(const int32_t *everts, const int32_t *egrade, int64_t E,
-                                                         const uint32_t *adj, const int32_t *adjpre, int W,
-                                                         const int32_t *nbr_ptr, const int32_t *nbr_ord,
-                                                         const int64_t *toff, int64_t T, int32_t *tverts,
-                                                         int32_t *tgrade, int64_t *tcolptr, int32_t *trow,
-                                                         EdgeIndex ex, DevStatus *st) {
+static __global__ void __launch_bounds__(256) k_tri_final_me(const uint64_t *tkeys, int64_t T, const int32_t *everts,
+                                                             const int32_t *egrade, EdgeIndex ex, int32_t *tverts,
+                                                             int32_t *tgrade, int64_t *tcolptr, int32_t *trow,
+                                                             const DevStatus *st) {
   pdl_entry();
-  __shared__ uint16_t cbuf[8][CB_SLOTS];
-  const int l = lane_id();
-  uint16_t *cb = cbuf[threadIdx.x >> 5];
-  const uint32_t lt = lanemask_lt();
-  const int64_t nwarps = (int64_t)gridDim.x * 8;
-  for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
-    const int a = everts[2 * e], b = everts[2 * e + 1];
-    const int32_t g = egrade[e];
-    const uint32_t *ra = adj + (int64_t)a * W, *rb = adj + (int64_t)b * W;
-    const int32_t *pa = adjpre + (int64_t)a * W, *pb = adjpre + (int64_t)b * W;
-    const int32_t *oa = nbr_ord + nbr_ptr[a], *ob = nbr_ord + nbr_ptr[b];
-    int64_t t = toff[e];
-    for (int w0 = 0; w0 < W; w0 += 32) {
-      const int w = w0 + l;
-      const uint32_t m = w < W ? ra[w] & rb[w] : 0u;
-      const int tot = bit_compact(m, w, cb);
-      __syncwarp();
-      for (int q0 = 0; q0 < tot; q0 += 32) {
-        const int q = q0 + l;
-        bool ok = false;
-        int cv = 0;
-        int32_t oac = 0, obc = 0;
-        if (q < tot) {
-          cv = cb[q];
-          if constexpr (DENSE) {
-            oac = ex.ord<true>(min(a, cv), max(a, cv));
-            obc = ex.ord<true>(min(b, cv), max(b, cv));
-          } else {
-            const int ww = cv >> 5;
-            const uint32_t below = (1u << (cv & 31)) - 1u;
-            oac = oa[pa[ww] + __popc(ra[ww] & below)];
-            obc = ob[pb[ww] + __popc(rb[ww] & below)];
-          }
-          ok = oac < (int32_t)e && obc < (int32_t)e;
-        }
-        const uint32_t bal = __ballot_sync(0xffffffffu, ok);
-        if (ok && t + __popc(bal & lt) >= T) {  // never write past the outputs
-          raise_flag(st, F_INTERNAL);
-          ok = false;
-        }
-        if (ok) {
-          const int64_t p = t + __popc(bal & lt);
-          int x0, x1, x2;
-          if (cv < a) { x0 = cv; x1 = a; x2 = b; }
-          else if (cv < b) { x0 = a; x1 = cv; x2 = b; }
-          else { x0 = a; x1 = b; x2 = cv; }
-          tverts[3 * p] = x0;
-          tverts[3 * p + 1] = x1;
-          tverts[3 * p + 2] = x2;
-          tgrade[p] = g;
-          tcolptr[p] = 3 * p;
-          trow[3 * p] = min(oac, obc);
-          trow[3 * p + 1] = max(oac, obc);
-          trow[3 * p + 2] = (int32_t)e;
-        }
-        t += __popc(bal);
-      }
-      __syncwarp();
+  if (build_failed(st)) return;
+  __shared__ int4 sv[8][96], sr[8][96];  // per warp: 128 triangles x 3 ints
+  const int wid = threadIdx.x >> 5, l = lane_id();
+  int32_t *svi = (int32_t *)sv[wid], *sri = (int32_t *)sr[wid];
+  const int64_t nch = T / 128;
+  for (int64_t ch = blockIdx.x * 8 + wid; ch < nch; ch += (int64_t)gridDim.x * 8) {
+    const int64_t base = ch * 128;
+    const ulonglong2 kA = ((const ulonglong2 *)(tkeys + base))[l], kB = ((const ulonglong2 *)(tkeys + base))[32 + l];
+    int32_t v[12], r[12], g[4];
+    tri_final_me_one(kA.x, everts, egrade, ex, v, r, g[0], DENSE);
+    tri_final_me_one(kA.y, everts, egrade, ex, v + 3, r + 3, g[1], DENSE);
+    tri_final_me_one(kB.x, everts, egrade, ex, v + 6, r + 6, g[2], DENSE);
+    tri_final_me_one(kB.y, everts, egrade, ex, v + 9, r + 9, g[3], DENSE);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      svi[6 * l + k] = v[k];
+      sri[6 * l + k] = r[k];
+      svi[192 + 6 * l + k] = v[6 + k];
+      sri[192 + 6 * l + k] = r[6 + k];
     }
+    ((int2 *)(tgrade + base))[l] = make_int2(g[0], g[1]);
+    ((int2 *)(tgrade + base + 64))[l] = make_int2(g[2], g[3]);
+    const long long c0 = 3 * (base + 2 * l), c1 = c0 + 192;
+    ((longlong2 *)(tcolptr + base))[l] = make_longlong2(c0, c0 + 3);
+    ((longlong2 *)(tcolptr + base + 64))[l] = make_longlong2(c1, c1 + 3);
+    __syncwarp();
+    int4 *gv = (int4 *)(tverts + 3 * base), *gr = (int4 *)(trow + 3 * base);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      gv[32 * k + l] = sv[wid][32 * k + l];
+      gr[32 * k + l] = sr[wid][32 * k + l];
+    }
+    __syncwarp();
+  }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = nch * 128 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T; p += stride) {
+    int32_t v[3], r[3], g;
+    tri_final_me_one(tkeys[p], everts, egrade, ex, v, r, g, DENSE);
+    tverts[3 * p] = v[0]; tverts[3 * p + 1] = v[1]; tverts[3 * p + 2] = v[2];
+    trow[3 * p] = r[0]; trow[3 * p + 1] = r[1]; trow[3 * p + 2] = r[2];
+    tgrade[p] = g;
+    tcolptr[p] = 3 * p;
   }
 }
 
@@ -1437,6 +1647,7 @@ constexpr int TRI_MID = 8192;
 static __global__ void k_tri_groups(const int32_t *gstart, const int32_t *tcnt, const int64_t *toff, int32_t *smallq,
                                     int32_t *midq, int32_t *bigq, DevStatus *st, int force_lex) {
   pdl_entry();
+  if (build_failed(st)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) st->T = toff[st->E];  // triangle count
   const int64_t ngrades = st->ngrades;
   if (lex_mode(st->E, ngrades, force_lex)) return;  // lex mode needs no merge
@@ -1465,8 +1676,10 @@ static __global__ void k_tri_groups(const int32_t *gstart, const int32_t *tcnt, 
 // Dynamic shared memory: CAP * (8 + 4 + 12) bytes.
 template <int CAP>
 static __global__ void k_tri_fix_smem(const int32_t *gstart, const int64_t *toff, const int32_t *queue,
-                                      const int32_t *count, int32_t *tverts, int32_t *trow) {
+                                      const int32_t *count, int32_t *tverts, int32_t *trow,
+    const DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   extern __shared__ unsigned char smem[];
   uint64_t *key = (uint64_t *)smem;              // CAP
   uint32_t *val = (uint32_t *)(key + CAP);       // CAP
@@ -1513,6 +1726,7 @@ static __global__ void __launch_bounds__(RS_THREADS) k_tri_fix_big(const int32_t
                                                                    uint32_t *v1, uint64_t *k2, uint32_t *v2,
                                                                    int32_t *rtmp) {
   pdl_entry();
+  if (build_failed(st)) return;
   const int nq = (int)st->big_seg_count;
   for (int q = blockIdx.x; q < nq; q += gridDim.x) {
     const int g = bigq[q];
@@ -1569,8 +1783,10 @@ __device__ __forceinline__ void lex3_unpack(uint64_t k, int &a, int &b, int &c) 
 // (x, y, z)'s rank among edge e's triangles (z ascending) is then one read
 // of this table plus a popcount, instead of a bisection in the triangle keys.
 static __global__ void __launch_bounds__(256) k_lex_pre(const uint32_t *lexe, int64_t E, const uint32_t *adj, int W,
-                                                        uint16_t *pre) {
+                                                        uint16_t *pre,
+    const DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   for (int64_t e = blockIdx.x * 8 + (threadIdx.x >> 5); e < E; e += nwarps) {
@@ -1617,8 +1833,10 @@ __device__ __forceinline__ int64_t tri_lexpos(int x, int y, int z, const uint64_
 static __global__ void k_tri_ordidx(const uint64_t *tk, int64_t T, const uint64_t *tk_lex, int32_t *ordidx,
                                     const int64_t *toff, const uint32_t *adj, const int32_t *adjpre, int W,
                                     const int32_t *deg, const int32_t *up, const int64_t *lex_ptr, const int32_t *elp,
-                                    int n, const uint16_t *pre) {
+                                    int n, const uint16_t *pre,
+    const DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T; p += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t x = tk[p] & LEX3_MASK;
     int64_t lo;
@@ -1641,8 +1859,10 @@ static __global__ void k_tri_ordidx(const uint64_t *tk, int64_t T, const uint64_
 
 // Tetrahedra per lexicographic triangle (warp per triangle).
 static __global__ void __launch_bounds__(256) k_tet_count(const uint64_t *tk_lex, int64_t T, const uint32_t *adj,
-                                                          int W, int32_t *cnt4) {
+                                                          int W, int32_t *cnt4,
+    const DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   const int l = lane_id();
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   // Four triangles per warp at a time, their first-round loads in flight
@@ -1682,6 +1902,7 @@ static __global__ void __launch_bounds__(256) k_tet_gen(const uint64_t *tk_lex, 
                                                         int64_t T4, uint64_t *keys4, uint64_t *lex4, int packed,
                                                         DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   __shared__ uint16_t cbuf[8][CB_SLOTS];  // per warp: one chunk's fourth vertices (bit_compact)
   const int l = lane_id(), wid = threadIdx.x >> 5;
   uint16_t *cb = cbuf[wid];
@@ -1732,8 +1953,10 @@ static __global__ void k_tet_final(const uint64_t *keys4, int64_t T4, const uint
                                    const int32_t *deg, const int32_t *up, const int64_t *lex_ptr,
                                    const int32_t *ordidx, const int32_t *elp, int n, int packed,
                                    const uint16_t *pre, int32_t *verts, int32_t *grade, int64_t *colptr,
-                                   int32_t *rowidx) {
+                                   int32_t *rowidx,
+    const DevStatus *st) {
   pdl_entry();
+  if (build_failed(st)) return;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T4; p += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = keys4[p];
     const uint64_t v = packed ? key & ((1ull << TET_PACK_SHIFT) - 1) : lex4[key & 0xffffffffull];

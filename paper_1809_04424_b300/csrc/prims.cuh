@@ -19,6 +19,12 @@ namespace vr {
 void set_error(const char *fmt, ...);   // thread-local message (api.cu)
 vr_status cuda_status(cudaError_t e, const char *what, const char *file, int line);
 
+// cudaMallocAsync behind a test hook: vr_inject_alloc_failure(k) makes the
+// k-th call from then on fail with cudaErrorMemoryAllocation (a host-side
+// fault: nothing is allocated and nothing runs on the device).  Every device
+// allocation of the library goes through it.
+cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t s);
+
 // Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
 // read once per device and cached; 1 if the query fails).  Grid caps and path
 // thresholds are multiples of it.
@@ -68,6 +74,17 @@ struct DevStatus {
 };
 
 __device__ __forceinline__ void raise_flag(DevStatus *st, int32_t f) { atomicOr(&st->flags, f); }
+
+// Flags after which the build's data can no longer be trusted: a bounded
+// wait gave up (its tile's output positions, or a whole tile's output, are
+// wrong) or an internal check failed.  Every kernel that consumes such data
+// checks at entry (after griddepcontrol.wait, so the earlier kernels of the
+// build have finished) and writes nothing: garbage indices never reach a
+// load or a store.  The host reports the flag at its next status read.
+constexpr int32_t F_FATAL = F_TIMEOUT | F_INTERNAL;
+__device__ __forceinline__ bool build_failed(const DevStatus *st) {
+  return (__ldcg(&st->flags) & F_FATAL) != 0;
+}
 
 inline vr_status flags_to_status(int32_t f) {
   if (f & F_INTERNAL) { set_error("internal invariant violated on the device"); return VR_ERR_INTERNAL; }
@@ -389,6 +406,16 @@ static __global__ void __launch_bounds__(RS_THREADS) k_rs_hist_all(const uint64_
 // 0..t is published; anything else: not yet), value below.  Tags are
 // pass-specific, so one clearing serves every pass of a sort.
 constexpr long RS_WAIT_LIMIT = 1l << 24;
+
+// Test hook (vr_inject_lookback_stall): in one digit pass, tile `tile`
+// publishes no status at all, so later tiles' look-back waits run out after
+// `limit` polls.  Launched as a separate instantiation (INJ) only when armed.
+struct RsStall {
+  int64_t tile;
+  long limit;
+};
+// Takes (and disarms) an armed stall for a pass of `tiles` tiles.
+bool take_rs_stall(int64_t tiles, RsStall *out);
 __device__ __forceinline__ void rs_publish(uint64_t *w, uint32_t tag, uint64_t v) {
   *(volatile uint64_t *)w = ((uint64_t)tag << 56) | v;
 }
@@ -419,12 +446,18 @@ constexpr int OS_TILE = RS_THREADS * OS_ITEMS;
 constexpr int OS_SMALL_ITEMS = 4;
 constexpr int OS_SMALL_TILE = RS_THREADS * OS_SMALL_ITEMS;
 constexpr int64_t OS_SMALL_N = 1 << 18;
-template <bool HI, int OS_ITEMS, int OS_MIN_BLOCKS>
+template <bool HI, int OS_ITEMS, int OS_MIN_BLOCKS, bool INJ>
 __global__ void __launch_bounds__(RS_THREADS, OS_MIN_BLOCKS) k_rs_onesweep(const uint64_t *src, uint64_t *dst, int64_t n,
                                                                int sh, uint32_t mask, int pass,
                                                                const uint32_t *hist, uint64_t *status,
-                                                               uint32_t *ticket, int32_t *err) {
+                                                               uint32_t *ticket, int32_t *err, RsStall stall,
+                                                               uint32_t *tmask) {
   pdl_entry();
+  // An earlier pass of this sort timed out: its output is not a permutation
+  // of the keys, so this pass's digit counts would not match the histogram
+  // (positions could leave the array).  Write nothing.  (A timeout in this
+  // same pass only sets bit `pass`, so sibling tiles never skip.)
+  if (pass > 0 && (*(volatile uint32_t *)tmask & ((1u << pass) - 1u))) return;
   __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];  // per-warp digit counts, then each warp's run starts
   __shared__ int64_t gofs[RS_BINS];             // global position of a run's slot 0 in skey
   constexpr int OS_TILE = RS_THREADS * OS_ITEMS;
@@ -472,7 +505,9 @@ __global__ void __launch_bounds__(RS_THREADS, OS_MIN_BLOCKS) k_rs_onesweep(const
   if (b == (int)mask) v -= OS_TILE - c;  // the padding
   const uint32_t tag_agg = 2 * pass + 1, tag_inc = 2 * pass + 2;
   uint64_t *my = status + t * RS_BINS + b;
-  rs_publish(my, t == 0 ? tag_inc : tag_agg, v);
+  const bool withhold = INJ && t == stall.tile;  // test hook: this tile never publishes
+  const long wait_limit = INJ ? stall.limit : RS_WAIT_LIMIT;
+  if (!withhold) rs_publish(my, t == 0 ? tag_inc : tag_agg, v);
   // One scan for both starts: the digit's start over all keys (from the
   // histogram) in the high bits, its start inside the tile in the low 16.
   const uint64_t both = block_excl_scan<uint64_t>(((uint64_t)hist[b] << 16) | v, scan_sh, (uint64_t *)nullptr);
@@ -522,14 +557,18 @@ __global__ void __launch_bounds__(RS_THREADS, OS_MIN_BLOCKS) k_rs_onesweep(const
       k -= used;
       pk0 -= used * RS_BINS;
       if (!done && used == 0) {
-        if (++spins > RS_WAIT_LIMIT) {
+        if (++spins > wait_limit) {
+          // Gave up: excl holds only some earlier tiles' counts, so every
+          // position below stays inside the digit's range (in bounds, but
+          // the result is wrong and the flag reports it).
           atomicOr(err, F_TIMEOUT);
+          atomicOr(tmask, 1u << pass);
           break;
         }
         __nanosleep(64);  // yield issue slots to the warps still ranking
       }
     }
-    rs_publish(my, tag_inc, excl + v);
+    if (!withhold) rs_publish(my, tag_inc, excl + v);
   }
   gofs[b] = (int64_t)(both >> 16) + (int64_t)excl - (int64_t)lp;
   __syncthreads();
@@ -713,7 +752,12 @@ struct RadixScratch {
 inline int64_t rs_tiles(int64_t n) {  // tiles of a digit pass over n keys
   return n <= OS_SMALL_N ? (n + OS_SMALL_TILE - 1) / OS_SMALL_TILE : (n + OS_TILE - 1) / OS_TILE;
 }
+// Head of the scratch: the all-digit histogram, then 256 bytes holding the
+// passes' tile tickets (word p) and the timed-out-pass mask (word
+// RS_TMASK_WORD); the per-(tile, digit) status words follow.
 constexpr int64_t RS_META_HEAD = RS_MAX_PASSES * RS_BINS * 4 + 256;
+constexpr int RS_TMASK_WORD = 32;
+static_assert(RS_MAX_PASSES <= RS_TMASK_WORD && (RS_TMASK_WORD + 1) * 4 <= 256, "sort scratch head layout");
 // Room for the status words of a sort of any m <= n keys, whichever tile size
 // m takes (callers size the scratch from an upper bound on the key count).
 inline int64_t rs_meta_bytes(int64_t n) {
@@ -756,6 +800,7 @@ inline vr_status radix_sort(uint64_t *keys, int64_t n, int bit_lo, int nbits, co
   const int passes = (nbits + 7) / 8;
   uint32_t *hist = (uint32_t *)sc.meta;
   uint32_t *ticket = (uint32_t *)(sc.meta + RS_MAX_PASSES * RS_BINS * 4);
+  uint32_t *tmask = ticket + RS_TMASK_WORD;  // passes that timed out (bit per pass)
   uint64_t *status = (uint64_t *)(sc.meta + RS_META_HEAD);
   int tk_ = -1;
   if (prep != RS_PREP_HIST) {
@@ -772,21 +817,22 @@ inline vr_status radix_sort(uint64_t *keys, int64_t n, int bit_lo, int nbits, co
     tk_ = prof ? prof->begin(tag[1]) : -1;
     const int sh = bit_lo + 8 * p;
     const uint32_t dm = digit_mask(nbits, p);
+    RsStall stall{-1, RS_WAIT_LIMIT};
+    const bool inj = take_rs_stall(nt, &stall);
+    const int shp = sh >= 32 ? sh - 32 : sh;
+#define VR_ONESWEEP(HI, IT, MB)                                                                                   \
+  (inj ? launch_dep(k_rs_onesweep<HI, IT, MB, true>, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, shp, dm, p,       \
+                    hist + p * RS_BINS, status, ticket + p, sc.err, stall, tmask)                                   \
+       : launch_dep(k_rs_onesweep<HI, IT, MB, false>, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, shp, dm, p,      \
+                    hist + p * RS_BINS, status, ticket + p, sc.err, stall, tmask))
     if (n <= OS_SMALL_N) {
-      if (sh >= 32)
-        launch_dep(k_rs_onesweep<true, OS_SMALL_ITEMS, 8>, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, sh - 32, dm, p,
-                   hist + p * RS_BINS, status, ticket + p, sc.err);
-      else
-        launch_dep(k_rs_onesweep<false, OS_SMALL_ITEMS, 8>, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, sh, dm, p,
-                   hist + p * RS_BINS, status, ticket + p, sc.err);
+      if (sh >= 32) VR_ONESWEEP(true, OS_SMALL_ITEMS, 8);
+      else VR_ONESWEEP(false, OS_SMALL_ITEMS, 8);
     } else {
-      if (sh >= 32)
-        launch_dep(k_rs_onesweep<true, OS_ITEMS, 4>, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, sh - 32, dm, p,
-                   hist + p * RS_BINS, status, ticket + p, sc.err);
-      else
-        launch_dep(k_rs_onesweep<false, OS_ITEMS, 4>, (unsigned)nt, RS_THREADS, 0, s, src, dst, n, sh, dm, p,
-                   hist + p * RS_BINS, status, ticket + p, sc.err);
+      if (sh >= 32) VR_ONESWEEP(true, OS_ITEMS, 4);
+      else VR_ONESWEEP(false, OS_ITEMS, 4);
     }
+#undef VR_ONESWEEP
     count_launch(1);
     if (prof) prof->end(tk_);
     VR_CUDA(cudaGetLastError());

@@ -78,6 +78,7 @@ struct vr_server {
   std::vector<cudaStream_t> big_streams;
   std::thread batch_thr;
   std::vector<std::thread> big_thr;
+  vr_server_stats stats{};  // under mu
 };
 
 namespace {
@@ -86,6 +87,8 @@ using namespace vr;
 
 void deliver(vr_server *S, uint64_t ticket, vr_status st, vr_complex *c) {
   std::lock_guard<std::mutex> lk(S->mu);
+  if (st == VR_OK) ++S->stats.completed;
+  else ++S->stats.failed;
   S->done[ticket] = Done{st, c};
   S->cv_done.notify_all();
 }
@@ -147,7 +150,7 @@ void launch_slot(vr_server *S, Slot &sl, std::vector<Req> &batch) {
     if (sl.dbuf) cudaFreeAsync(sl.dbuf, sl.s);
     sl.dbuf = nullptr;
     sl.dcap = 0;
-    if (cudaMallocAsync(&sl.dbuf, std::max(bytes, (size_t)1 << 20), sl.s) != cudaSuccess) {
+    if (dev_malloc(&sl.dbuf, std::max(bytes, (size_t)1 << 20), sl.s) != cudaSuccess) {
       cudaGetLastError();
       return fail_members(S, sl, VR_ERR_OOM);
     }
@@ -189,6 +192,7 @@ void batch_worker(vr_server *S) {
           inflight += sl.bytes;
           if (!deferred.empty()) {  // back to the front of their queue
             std::lock_guard<std::mutex> lk(S->mu);
+            S->stats.deferred += (int64_t)deferred.size();
             auto &q = S->small_q[{(int)sl.members[0].dtype, sl.members[0].d}];
             for (auto it = deferred.rbegin(); it != deferred.rend(); ++it) {
               q.push_front(std::move(sl.members[*it]));
@@ -219,6 +223,10 @@ void batch_worker(vr_server *S) {
       if (sl.state != 0) continue;
       std::vector<Req> batch;
       if (!take_batch(S, batch)) break;
+      {
+        std::lock_guard<std::mutex> lk(S->mu);
+        ++S->stats.batches;
+      }
       launch_slot(S, sl, batch);
       progressed = true;
     }
@@ -254,6 +262,7 @@ void big_worker(vr_server *S, int k) {
       r = std::move(S->big_q.front());
       S->big_q.pop_front();
       --S->queued;
+      ++S->stats.large_builds;
     }
     vr_complex *c = nullptr;
     const vr_status st = vr_build(r.pts.data(), r.n, r.d, r.dtype, r.maxdim, r.maxrad, bs, &c);
@@ -339,6 +348,7 @@ vr_status vr_serve_submit(vr_server *S, const void *points, int32_t n, int32_t d
   r.ticket = S->next_ticket++;
   *ticket = r.ticket;
   ++S->queued;
+  ++S->stats.submitted;
   if (fused_fits(n, d)) {
     S->small_q[{(int)dtype, d}].push_back(std::move(r));
     S->cv_work.notify_one();
@@ -369,6 +379,14 @@ vr_status vr_serve_poll(vr_server *S, uint64_t ticket, int64_t timeout_us, vr_co
     return dn.st;
   }
   *out = dn.c;
+  return VR_OK;
+}
+
+vr_status vr_server_get_stats(vr_server *S, vr_server_stats *out) {
+  if (!S || !out) { set_error("NULL argument"); return VR_ERR_ARG; }
+  std::lock_guard<std::mutex> lk(S->mu);
+  *out = S->stats;
+  out->queued = S->queued;
   return VR_OK;
 }
 

@@ -28,9 +28,9 @@ extern "C" vr_status vr_sort_keys(uint64_t *keys, int64_t n, int32_t bit_lo, int
     if (rs.meta) cudaFreeAsync(rs.meta, s);
     if (flags) cudaFreeAsync(flags, s);
   };
-  cudaError_t e = cudaMallocAsync((void **)&rs.tkeys, sizeof(uint64_t) * n, s);
-  if (e == cudaSuccess) e = cudaMallocAsync((void **)&rs.meta, (size_t)rs_meta_bytes(n), s);
-  if (e == cudaSuccess) e = cudaMallocAsync((void **)&flags, sizeof(int32_t), s);
+  cudaError_t e = dev_malloc((void **)&rs.tkeys, sizeof(uint64_t) * n, s);
+  if (e == cudaSuccess) e = dev_malloc((void **)&rs.meta, (size_t)rs_meta_bytes(n), s);
+  if (e == cudaSuccess) e = dev_malloc((void **)&flags, sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -3,6 +3,8 @@ for bit (and so vr_build's), whatever the mix of sizes, dtypes, caps and
 maxdims; clouds too large for the fused path, tiny clouds and bad clouds
 included."""
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
@@ -40,6 +42,35 @@ def check_batch(torch, clouds, on_device=True):
             g[k] = view.to_host(k)
         assert_same(g, oracle.vr_build(c.points, c.maxdim, c.maxrad), c.maxdim)
     return b
+
+
+def oracle_many(clouds):
+    """Oracle complexes of many clouds, built by host threads (the oracle's C
+    call releases the interpreter lock, so they run in parallel)."""
+    with ThreadPoolExecutor(os.cpu_count() or 1) as ex:
+        return list(ex.map(lambda c: oracle.vr_build(c.points, c.maxdim, c.maxrad), clouds))
+
+
+@pytest.mark.timeout(900)
+def test_full_sphere_batch_4096_clouds(torch):
+    """The whole uneven sphere workload (4096 clouds, n ~ U[32, 512], int8,
+    cap 40, maxdim 2) in one vr_build_batch; every cloud equals the oracle."""
+    clouds = synth.config4(4096)
+    refs = oracle_many(clouds)
+    pts, off = concat(clouds)
+    b = vr.vr_build_batch(torch.from_numpy(pts).cuda(), off, 2, 40.0)
+    info = b.info()
+    assert info["n_failed"] == 0
+    total = 0
+    for i, c in enumerate(clouds):
+        st, view = b.get(i)
+        assert st == vr.VR_OK, (i, st)
+        g = {"gv": view.grade_values()}
+        for k in range(3):
+            g[k] = view.to_host(k)
+        assert_same(g, refs[i], 2)
+        total += sum(d.count for d in refs[i].dims)
+    assert info["total_simplices"] == total
 
 
 def test_sphere_batch_int8(torch):

@@ -2,6 +2,8 @@
 memory and overlapped; every result must be bit-for-bit the one vr_build
 gives for the same request alone (and the oracle's), in any mix."""
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
@@ -64,6 +66,25 @@ def test_mixed_stream_equals_alone(torch):
     for c in reqs[:12]:  # and the oracle, for a sample
         got = alone(torch, c)
         assert_same(got, oracle.vr_build(c.points, c.maxdim, c.maxrad), c.maxdim)
+    srv.close()
+
+
+def test_config5_stream_sample_equals_oracle(torch):
+    """The first 300 requests of the 20000-request serving stream, as drawn
+    (n log-uniform in [50, 5000], int8 d=3 and float32 d=16, maxdim 1 or 2,
+    per-request caps), all submitted at once: requests above 1400 points take
+    the server's single-cloud workers, the rest its batches.  Every result
+    equals the oracle's complex."""
+    reqs = synth.config5(300)[1]
+    big = [c for c in reqs if c.n > 1400]
+    assert any(c.points.dtype == np.int8 for c in big) and any(c.points.dtype == np.float32 for c in big)
+    assert max(c.n for c in reqs) > 4000
+    with ThreadPoolExecutor(os.cpu_count() or 1) as ex:
+        refs = list(ex.map(lambda c: oracle.vr_build(c.points, c.maxdim, c.maxrad), reqs))
+    srv = vr.Server(n_streams=3, max_batch_clouds=256, n_large_workers=4)
+    tickets = [srv.submit(c.points, c.maxdim, c.maxrad) for c in reqs]
+    for c, t, ref in zip(reqs, tickets, refs):
+        assert_same(result_dict(srv.poll(t, 120_000_000), c.maxdim), ref, c.maxdim)
     srv.close()
 
 
