@@ -1366,10 +1366,14 @@ static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts
     __syncwarp();
     int c = 0;
 #pragma unroll
-    for (int k = 0; k < MEG_KMAX; ++k) {
-      if (k < K) {
-        wx[k] = (wx[k] | dx[w0 + k]) & (wy[k] | dy[w0 + k]);
-        c += __popc(wx[k]);
+    for (int q = 0; q < MEG_KMAX / 4; ++q) {
+      if (q < K4) {
+        const uint4 ddx = ((const uint4 *)(dx + w0))[q], ddy = ((const uint4 *)(dy + w0))[q];
+        wx[4 * q] = (wx[4 * q] | ddx.x) & (wy[4 * q] | ddy.x);
+        wx[4 * q + 1] = (wx[4 * q + 1] | ddx.y) & (wy[4 * q + 1] | ddy.y);
+        wx[4 * q + 2] = (wx[4 * q + 2] | ddx.z) & (wy[4 * q + 2] | ddy.z);
+        wx[4 * q + 3] = (wx[4 * q + 3] | ddx.w) & (wy[4 * q + 3] | ddy.w);
+        c += __popc(wx[4 * q]) + __popc(wx[4 * q + 1]) + __popc(wx[4 * q + 2]) + __popc(wx[4 * q + 3]);
       }
     }
     int inc = c;  // inclusive scan over the half's 16 lanes
@@ -1385,7 +1389,7 @@ static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts
       for (int k = 0; k < MEG_KMAX; ++k) {
         if (k >= K) break;
         for (uint32_t mm = wx[k]; mm; mm &= mm - 1, ++p) {
-          if (p < T) tkeys[p] = ek | (uint32_t)((w0 + k) * 32 + __ffs(mm) - 1);
+          if (p < T) __stcs(tkeys + p, ek | (uint32_t)((w0 + k) * 32 + __ffs(mm) - 1));
           else raise_flag(st, F_INTERNAL);  // never write past the key array
         }
       }
@@ -1596,10 +1600,23 @@ static __global__ void __launch_bounds__(256) k_tri_final_me(const uint64_t *tke
   __shared__ int4 sv[8][96], sr[8][96];  // per warp: 128 triangles x 3 ints
   const int wid = threadIdx.x >> 5, l = lane_id();
   int32_t *svi = (int32_t *)sv[wid], *sri = (int32_t *)sr[wid];
-  const int64_t nch = T / 128;
-  for (int64_t ch = blockIdx.x * 8 + wid; ch < nch; ch += (int64_t)gridDim.x * 8) {
+  const int64_t nch = T / 128, cstride = (int64_t)gridDim.x * 8;
+  // Keys are read once and the outputs written once: streaming hints keep
+  // them from evicting the order table the lookups need from L2.  The next
+  // chunk's keys are loaded while this one is processed.
+  int64_t ch = blockIdx.x * 8 + wid;
+  ulonglong2 nA = make_ulonglong2(0, 0), nB = nA;
+  if (ch < nch) {
+    nA = __ldcs((const ulonglong2 *)(tkeys + ch * 128) + l);
+    nB = __ldcs((const ulonglong2 *)(tkeys + ch * 128) + 32 + l);
+  }
+  for (; ch < nch; ch += cstride) {
     const int64_t base = ch * 128;
-    const ulonglong2 kA = ((const ulonglong2 *)(tkeys + base))[l], kB = ((const ulonglong2 *)(tkeys + base))[32 + l];
+    const ulonglong2 kA = nA, kB = nB;
+    if (ch + cstride < nch) {
+      nA = __ldcs((const ulonglong2 *)(tkeys + (ch + cstride) * 128) + l);
+      nB = __ldcs((const ulonglong2 *)(tkeys + (ch + cstride) * 128) + 32 + l);
+    }
     int32_t v[12], r[12], g[4];
     tri_final_me_one(kA.x, everts, egrade, ex, v, r, g[0], DENSE);
     tri_final_me_one(kA.y, everts, egrade, ex, v + 3, r + 3, g[1], DENSE);
@@ -1612,17 +1629,17 @@ static __global__ void __launch_bounds__(256) k_tri_final_me(const uint64_t *tke
       svi[192 + 6 * l + k] = v[6 + k];
       sri[192 + 6 * l + k] = r[6 + k];
     }
-    ((int2 *)(tgrade + base))[l] = make_int2(g[0], g[1]);
-    ((int2 *)(tgrade + base + 64))[l] = make_int2(g[2], g[3]);
+    __stcs((int2 *)(tgrade + base) + l, make_int2(g[0], g[1]));
+    __stcs((int2 *)(tgrade + base + 64) + l, make_int2(g[2], g[3]));
     const long long c0 = 3 * (base + 2 * l), c1 = c0 + 192;
-    ((longlong2 *)(tcolptr + base))[l] = make_longlong2(c0, c0 + 3);
-    ((longlong2 *)(tcolptr + base + 64))[l] = make_longlong2(c1, c1 + 3);
+    __stcs((longlong2 *)(tcolptr + base) + l, make_longlong2(c0, c0 + 3));
+    __stcs((longlong2 *)(tcolptr + base + 64) + l, make_longlong2(c1, c1 + 3));
     __syncwarp();
     int4 *gv = (int4 *)(tverts + 3 * base), *gr = (int4 *)(trow + 3 * base);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      gv[32 * k + l] = sv[wid][32 * k + l];
-      gr[32 * k + l] = sr[wid][32 * k + l];
+      __stcs(gv + 32 * k + l, sv[wid][32 * k + l]);
+      __stcs(gr + 32 * k + l, sr[wid][32 * k + l]);
     }
     __syncwarp();
   }
