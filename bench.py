@@ -528,6 +528,28 @@ def batch_leg(args, ranks, local):
         phases[nm.value.decode()] = round(ms.value / max(calls.value, 1), 4)
     batched = whole_job_rate(args.n_clouds * steps, dev_ms / 1e3)
     tot = ranks.sum(tot)
+    # The launch shape the tuner picked for this class, its candidates, and
+    # the default shape (every CTA the launch allows per SM, largest cloud
+    # first) timed the same way.
+    shape = vr.vr_batch_get_shape()
+    cands = shape["candidates"]
+    default = (max(c[0] for c, _ in cands), 0) if cands else None
+    default_rate = None
+    if default is not None:
+        vr.vr_batch_set_shape(*default)
+        for _ in range(2):
+            del_b = vr.vr_build_batch(dev, off, 2, 40.0)
+            del del_b
+        torch.cuda.synchronize()
+        evd = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            evd[k][0].record(stream)
+            b = vr.vr_build_batch(dev, off, 2, 40.0)
+            evd[k][1].record(stream)
+            del b
+        torch.cuda.synchronize()
+        vr.vr_batch_set_shape(0)
+        default_rate = whole_job_rate(args.n_clouds * steps, ranks.max(sum(a.elapsed_time(b) for a, b in evd)) / 1e3)
     # per-cloud path: one vr_build per cloud, every cloud of this rank
     devs = [torch.from_numpy(c.points).cuda() for c in clouds]
     for dp in devs[:16]:
@@ -557,6 +579,10 @@ def batch_leg(args, ranks, local):
            "per_cloud_path": {"value": per_cloud, "unit": "clouds/s", "clouds": args.n_clouds,
                               "how": "one vr_build per cloud, plain launches, same GPU, every cloud"},
            "speedup_vs_per_cloud": batched / per_cloud,
+           "launch_shape": {"tuned": shape["used"], "default": default,
+                            "default_clouds_per_s": default_rate,
+                            "tuner_candidates_ms": [[list(c), round(ms, 4)] for c, ms in cands],
+                            "what": "CTAs per SM of the one persistent launch, work-list order (0 largest first)"},
            "e2e": {"value": e2e, "unit": "clouds/s",
                    "h2d_bytes_per_step": int(pts.nbytes) + len(clouds) * (2 * CLOUD_DESC_BYTES + 4),
                    "d2h_bytes_per_step": len(clouds) * 2 * CLOUD_DESC_BYTES,

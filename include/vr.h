@@ -199,17 +199,42 @@ VR_API vr_status vr_complex_grade_values_to_host(const vr_complex *c, double *va
  * still exist).  NULL is ignored. */
 VR_API void vr_complex_free(vr_complex *c);
 
-/* ---- Batches: many clouds in two launches.
+/* ---- Batches: many clouds in one persistent launch.
  * vr_build_batch builds the complex of each of n_clouds clouds concatenated
  * row-wise in `points` (d coordinates each, one dtype; device or host
  * memory), cloud c being rows [offsets[c], offsets[c+1]) of a HOST array of
  * n_clouds+1 row offsets (offsets[0] = 0).  maxdim and maxrad are HOST arrays
  * of n_clouds values (NULL: 2 and +INFINITY for every cloud); their meaning is
- * that of vr_build.  Each cloud's result is exactly vr_build's.  One CTA
- * builds one cloud at a time (largest first) with its working set in shared
- * memory; clouds too large for that take the single-cloud path.  The call
- * synchronises on `stream` twice (sizes, then completion).
- * Argument errors fail the whole call; a value error (non-finite float, ...)
+ * that of vr_build.  Each cloud's result is exactly vr_build's.
+ *   - One cooperative launch of co-resident CTAs takes the clouds from a work
+ *     list: it sizes every cloud, lays their output slices out on the device
+ *     (grid barrier, exclusive scans), and builds every cloud into its slice,
+ *     one CTA per cloud with its working set in shared memory.  The launch
+ *     and its copies are a CUDA graph captured once per batch class and
+ *     replayed.  Output arenas are sized from earlier batches of the class;
+ *     a batch that outgrows them is built again into exact arenas (the first
+ *     batch of a class is sized first).  Clouds too large for one CTA take
+ *     the single-cloud path.  The call synchronises on `stream` once (twice
+ *     for a batch that outgrows the arenas).
+ *   - Launch shape (CTAs per SM, work-list order): tuned on the first batch
+ *     of each class (every candidate builds the batch; the fastest is kept
+ *     for the process), or pinned by vr_batch_set_shape. */
+typedef struct vr_batch_shape {
+  int32_t ctas_per_sm; /* CTAs of the persistent launch per SM (<= 0: tuned) */
+  int32_t order;       /* work list: 0 largest cloud first, 1 input order   */
+} vr_batch_shape;
+/* Pin the shape of later batches on this thread (NULL or ctas_per_sm <= 0:
+ * the tuned shape; a count above what fits is clamped).  Bad order:
+ * VR_ERR_ARG. */
+VR_API vr_status vr_batch_set_shape(const vr_batch_shape *shape);
+/* The shape the last batch on this thread used, and, when its class was
+ * tuned, the candidates with their measured device times in ms (up to
+ * max_cand of them; *n_cand gets the count, 0 if the class was pinned). */
+VR_API vr_status vr_batch_get_shape(vr_batch_shape *used, int32_t *n_cand, vr_batch_shape *cand,
+                                    double *cand_ms, int32_t max_cand);
+/* Forget every tuned shape: the next batch of each class tunes again. */
+VR_API vr_status vr_batch_tune_reset(void);
+/* Argument errors fail the whole call; a value error (non-finite float, ...)
  * fails only its cloud, reported by vr_batch_get. */
 typedef struct vr_batch vr_batch;
 VR_API vr_status vr_build_batch(const void *points, const int64_t *offsets,

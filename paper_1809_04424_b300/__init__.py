@@ -385,7 +385,46 @@ def _set_batch_types(L):
     L.vr_batch_info.restype = ctypes.c_int
     L.vr_batch_free.argtypes = [vp]
     L.vr_batch_free.restype = None
+    L.vr_batch_set_shape.argtypes = [ctypes.POINTER(BatchShape)]
+    L.vr_batch_set_shape.restype = ctypes.c_int
+    L.vr_batch_get_shape.argtypes = [ctypes.POINTER(BatchShape), ctypes.POINTER(i32), ctypes.POINTER(BatchShape),
+                                     ctypes.POINTER(ctypes.c_double), i32]
+    L.vr_batch_get_shape.restype = ctypes.c_int
+    L.vr_batch_tune_reset.argtypes = []
+    L.vr_batch_tune_reset.restype = ctypes.c_int
     L._batch_types = True
+
+
+class BatchShape(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int32), ("order", ctypes.c_int32)]
+
+
+def vr_batch_set_shape(ctas_per_sm: int = 0, order: int = 0) -> None:
+    """Pin the one-launch batch shape on this thread (ctas_per_sm 0: tuned)."""
+    L = lib()
+    _set_batch_types(L)
+    sh = BatchShape(int(ctas_per_sm), int(order))
+    _check(L.vr_batch_set_shape(ctypes.byref(sh)))
+
+
+def vr_batch_get_shape(max_cand: int = 64) -> dict:
+    """The shape of the last batch on this thread and the tuner's candidates
+    (shape, device ms) when its class was tuned."""
+    L = lib()
+    _set_batch_types(L)
+    used = BatchShape()
+    n = ctypes.c_int32()
+    cand = (BatchShape * max_cand)()
+    ms = (ctypes.c_double * max_cand)()
+    _check(L.vr_batch_get_shape(ctypes.byref(used), ctypes.byref(n), cand, ms, max_cand))
+    return {"used": (used.ctas_per_sm, used.order),
+            "candidates": [((cand[k].ctas_per_sm, cand[k].order), ms[k]) for k in range(min(n.value, max_cand))]}
+
+
+def vr_batch_tune_reset() -> None:
+    L = lib()
+    _set_batch_types(L)
+    _check(L.vr_batch_tune_reset())
 
 
 def vr_build_batch(points, offsets, maxdim=None, maxrad=None, stream=None) -> Batch:

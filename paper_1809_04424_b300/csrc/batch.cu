@@ -240,9 +240,8 @@ __device__ __forceinline__ int next_cloud(int *cursor, const int32_t *order, int
 // ------------------------------------------------------------------ sizing
 
 template <bool F, typename TIn>
-__global__ void __launch_bounds__(BT) k_batch_size(const TIn *pts, int d, CloudDesc *desc, const int32_t *order,
-                                                   int n_clouds, int *cursor, int nmax) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ void batch_size_loop(const TIn *pts, int d, CloudDesc *desc, const int32_t *order, int n_clouds,
+                                int *cursor, int nmax, unsigned char *smem) {
   const int Wmax = (nmax + 31) / 32;
   uint32_t *adj = (uint32_t *)smem;
   void *Xs = (void *)(smem + al16((size_t)nmax * Wmax * 4));
@@ -293,13 +292,19 @@ __global__ void __launch_bounds__(BT) k_batch_size(const TIn *pts, int d, CloudD
   }
 }
 
+template <bool F, typename TIn>
+__global__ void __launch_bounds__(BT) k_batch_size(const TIn *pts, int d, CloudDesc *desc, const int32_t *order,
+                                                   int n_clouds, int *cursor, int nmax) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  batch_size_loop<F, TIn>(pts, d, desc, order, n_clouds, cursor, nmax, smem);
+}
+
 // ------------------------------------------------------------------- build
 
 template <bool F, typename TIn>
-__global__ void __launch_bounds__(BT) k_batch_build(const TIn *pts, int d, CloudDesc *desc, const int32_t *order,
-                                                    int n_clouds, int *cursor, int nmax, unsigned char *scratch,
-                                                    ScratchLayout SL, BatchOut out) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ void batch_build_loop(const TIn *pts, int d, CloudDesc *desc, const int32_t *order, int n_clouds,
+                                 int *cursor, int nmax, unsigned char *scratch, const ScratchLayout &SL,
+                                 const BatchOut &out, unsigned char *smem) {
   const SmemLayout SM = smem_layout(nmax, d);
   uint32_t *adj = (uint32_t *)(smem + SM.adj);
   uint16_t *pre = (uint16_t *)(smem + SM.pre);
@@ -588,11 +593,162 @@ __global__ void __launch_bounds__(BT) k_batch_build(const TIn *pts, int d, Cloud
   (void)lt;
 }
 
+template <bool F, typename TIn>
+__global__ void __launch_bounds__(BT) k_batch_build(const TIn *pts, int d, CloudDesc *desc, const int32_t *order,
+                                                    int n_clouds, int *cursor, int nmax, unsigned char *scratch,
+                                                    ScratchLayout SL, BatchOut out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  batch_build_loop<F, TIn>(pts, d, desc, order, n_clouds, cursor, nmax, scratch, SL, out, smem);
+}
+
+// ------------------------------------------------------- one-launch batch
+// The whole batch in one persistent launch of co-resident CTAs (cooperative):
+//   phase 1: every cloud of the work list sized (bitmap, E, T);
+//   grid barrier; CTA 0 lays the clouds' output slices out in cloud order
+//   (exclusive scans of their sizes) and checks them against the arenas'
+//   and the per-CTA scratch's capacities; grid barrier;
+//   phase 2: every cloud built into its slice (skipped, with the overflow
+//   word set, when a capacity is short: the host then grows the arenas and
+//   relaunches phase 2 alone).
+// Inputs, outputs and capacities are read from a parameter block in device
+// memory, so that one captured graph serves every batch of the same shape.
+struct BatchParams {
+  const void *pts;
+  int32_t n_clouds;
+  BatchOut out;
+  unsigned char *scratch;
+  ScratchLayout SL;
+  int64_t cap[6];     // arena capacities: edges, triangles, vertices, grade values, edge colptr, triangle colptr
+  int64_t emax_cap;   // per-CTA scratch: largest E and T of one cloud
+  int64_t tmax_cap;
+};
+// Control words of a launch: [0] sizing cursor, [1] build cursor, [2..3]
+// grid barrier, [4] flags (F_TIMEOUT), [5] overflow, then (64-bit, from
+// word 6) the totals of the six arenas and the largest E and T.
+constexpr int BC_WORDS = 6 + 2 * 8;
+static_assert(sizeof(int64_t) * 8 == sizeof(unsigned int) * (BC_WORDS - 6), "control words: eight 64-bit totals");
+constexpr uint64_t BATCH_BARRIER_NS = 30ull * 1000 * 1000 * 1000;  // 30 s
+
+__device__ bool batch_grid_barrier(unsigned int *bar, int32_t *err) {
+  __threadfence();
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    volatile unsigned int *gen = bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      // Bounded by time, not by polls: a CTA may legitimately wait here for
+      // as long as the slowest CTA's last cloud takes.
+      uint64_t t0, t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      while (*gen == g) {
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > BATCH_BARRIER_NS) {  // every CTA then leaves the launch
+          atomicOr(err, F_TIMEOUT);
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();
+    s_ok = *(volatile int32_t *)err == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// CTA 0: output slices of the clouds in cloud order, totals and maxima.
+__device__ void batch_layout(CloudDesc *desc, int n_clouds, const BatchParams &p, unsigned int *ctr) {
+  __shared__ int64_t sh[33];
+  int64_t base[6] = {0, 0, 0, 0, 0, 0};
+  int64_t emax = 0, tmax = 0;
+  for (int b0 = 0; b0 < n_clouds; b0 += BT) {
+    const int i = b0 + threadIdx.x;
+    int64_t v[6] = {0, 0, 0, 0, 0, 0};
+    bool act = false;
+    if (i < n_clouds) {
+      const CloudDesc &c = desc[i];
+      act = !(c.fallback || c.flags);
+      if (act) {
+        v[0] = c.E;
+        v[1] = c.T;
+        v[2] = c.n;
+        v[3] = c.E + 1;
+        v[4] = c.E + 1;
+        v[5] = c.maxdim >= 2 ? c.T + 1 : 0;
+        emax = max(emax, c.E);
+        tmax = max(tmax, c.T);
+      }
+    }
+    int64_t ex[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      int64_t tot;
+      ex[k] = block_excl_scan<int64_t>(v[k], sh, &tot) + base[k];
+      base[k] += tot;
+    }
+    if (act) {
+      CloudDesc &c = desc[i];
+      c.eo = ex[0];
+      c.to = ex[1];
+      c.vo = ex[2];
+      c.go = ex[3];
+      c.co = ex[4];
+      c.ko = ex[5];
+    }
+  }
+  // Maxima over the CTA (shared atomics).
+  __shared__ unsigned long long smax[2];
+  if (threadIdx.x == 0) smax[0] = smax[1] = 0;
+  __syncthreads();
+  atomicMax(&smax[0], (unsigned long long)emax);
+  atomicMax(&smax[1], (unsigned long long)tmax);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t *tot = (int64_t *)(ctr + 6);
+    bool over = smax[0] > (unsigned long long)p.emax_cap || smax[1] > (unsigned long long)p.tmax_cap;
+    for (int k = 0; k < 6; ++k) {
+      tot[k] = base[k];
+      over |= base[k] > p.cap[k];
+    }
+    tot[6] = (int64_t)smax[0];
+    tot[7] = (int64_t)smax[1];
+    ctr[5] = over ? 1u : 0u;
+  }
+}
+
+// phases: bit 0 sizing + layout, bit 1 build.
+template <bool F, typename TIn>
+__global__ void __launch_bounds__(BT) k_batch_all(const BatchParams *P, int d, CloudDesc *desc, const int32_t *order,
+                                                  int nmax, unsigned int *ctr, int phases) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const BatchParams p = *P;
+  const int n_clouds = p.n_clouds;
+  int32_t *err = (int32_t *)(ctr + 4);
+  if (phases & 1) {
+    batch_size_loop<F, TIn>((const TIn *)p.pts, d, desc, order, n_clouds, (int *)ctr, nmax, smem);
+    if (!batch_grid_barrier(ctr + 2, err)) return;
+    if (blockIdx.x == 0) batch_layout(desc, n_clouds, p, ctr);
+    if (!batch_grid_barrier(ctr + 2, err)) return;
+  }
+  if (phases & 2) {
+    if (*(volatile unsigned int *)(ctr + 5)) return;  // a capacity is short: the host relaunches
+    batch_build_loop<F, TIn>((const TIn *)p.pts, d, desc, order, n_clouds, (int *)(ctr + 1), nmax, p.scratch, p.SL,
+                             p.out, smem);
+  }
+}
+
 }  // namespace vr
 
 // ================================================================== host
 
 #include <memory>
+#include <mutex>
 
 namespace vr {
 
@@ -912,6 +1068,440 @@ struct BatchJob {
 
 std::unique_ptr<BatchJob> new_batch_job() { return std::unique_ptr<BatchJob>(new BatchJob()); }
 
+// ------------------------------------------------------- one-launch engine
+// A batch shape: CTAs per SM of the persistent launch and the work-list
+// order (0: largest cloud first, 1: input order).
+
+// Device buffers, pinned mirrors and the captured graph of one shape:
+// (device, dtype, d, largest fused cloud class, cloud-count class, shape).
+// The graph copies the parameter block, descriptors and work list in,
+// clears the control words, launches k_batch_all (both phases) and copies
+// the descriptors and control words out; it only ever reads its inputs from
+// the pinned mirrors, so it replays for any batch of its class.
+struct BatchEngine {
+  int dev = -1;
+  vr_dtype dtype = VR_I8;
+  int d = 0, nmax = 0, nc_cap = 0, grid = 0;
+  vr_batch_shape shape{0, 0};
+  size_t smem = 0;
+  CloudDesc *d_desc = nullptr;
+  int32_t *d_order = nullptr;
+  unsigned int *d_ctr = nullptr;
+  BatchParams *d_par = nullptr;
+  unsigned char *h_mem = nullptr;  // pinned: params, control words, descriptors, work list
+  BatchParams *h_par = nullptr;
+  unsigned int *h_ctr = nullptr;
+  CloudDesc *h_desc = nullptr;
+  int32_t *h_order = nullptr;
+  unsigned char *scratch = nullptr;
+  int64_t scratch_bytes = 0;
+  int64_t hint[6] = {0, 0, 0, 0, 0, 0};  // arena capacities that held the last batches
+  int64_t emax_hint = 0, tmax_hint = 0;
+  bool hinted = false, busy = false;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_failed = false;
+  ~BatchEngine() {
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaDeviceSynchronize();
+    for (void *p : {(void *)d_desc, (void *)d_order, (void *)d_ctr, (void *)d_par, (void *)scratch})
+      if (p) cudaFree(p);
+    if (h_mem) cudaFreeHost(h_mem);
+    cudaGetLastError();
+  }
+};
+
+static std::mutex g_eng_mu;
+static std::vector<std::unique_ptr<BatchEngine>> g_engines;
+static thread_local vr_batch_shape g_pinned_shape{0, 0};
+struct TuneRec {
+  int dev;
+  vr_dtype dtype;
+  int d, nmax;
+  vr_batch_shape best;
+  std::vector<std::pair<vr_batch_shape, double>> cand;
+};
+static std::vector<TuneRec> g_tuned;
+static thread_local vr_batch_shape g_last_shape{0, 0};
+static thread_local TuneRec g_last_tune{};  // the tuner's record of the last batch's class (cand empty: none)
+
+template <bool F, typename TIn>
+static void *batch_all_fn() { return (void *)k_batch_all<F, TIn>; }
+static void *batch_kernel(vr_dtype dt) {
+  if (dt == VR_F32) return batch_all_fn<true, float>();
+  if (dt == VR_I8) return batch_all_fn<false, int8_t>();
+  return batch_all_fn<false, int32_t>();
+}
+
+// Largest CTAs per SM the persistent launch can keep co-resident.
+static int batch_max_per_sm(vr_dtype dt, size_t smem) {
+  void *fn = batch_kernel(dt);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, BT, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per;
+}
+
+static vr_status launch_all(BatchEngine &g, int phases, cudaStream_t s) {
+  void *fn = batch_kernel(g.dtype);
+  int d = g.d, nmax = g.nmax;
+  void *args[] = {&g.d_par, &d, &g.d_desc, &g.d_order, &nmax, &g.d_ctr, &phases};
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(g.grid);
+  cfg.blockDim = dim3(BT);
+  cfg.dynamicSmemBytes = g.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  VR_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
+  count_launch();
+  return VR_OK;
+}
+
+static vr_status make_engine(BatchEngine &g, cudaStream_t s) {
+  VR_CUDA(cudaFuncSetAttribute(batch_kernel(g.dtype), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem));
+  VR_CUDA(cudaMalloc((void **)&g.d_desc, sizeof(CloudDesc) * g.nc_cap));
+  VR_CUDA(cudaMalloc((void **)&g.d_order, sizeof(int32_t) * g.nc_cap));
+  VR_CUDA(cudaMalloc((void **)&g.d_ctr, sizeof(unsigned int) * BC_WORDS));
+  VR_CUDA(cudaMalloc((void **)&g.d_par, sizeof(BatchParams)));
+  // Pinned layout: parameter block, control words, descriptors, work list
+  // (each 256-byte aligned).
+  auto up256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t o_ctr = up256(sizeof(BatchParams));
+  const size_t o_desc = o_ctr + up256(sizeof(unsigned int) * BC_WORDS);
+  const size_t o_order = o_desc + up256(sizeof(CloudDesc) * g.nc_cap);
+  const size_t hb = o_order + up256(sizeof(int32_t) * g.nc_cap);
+  VR_CUDA(cudaMallocHost((void **)&g.h_mem, hb));
+  memset(g.h_mem, 0, hb);
+  g.h_par = (BatchParams *)g.h_mem;
+  g.h_ctr = (unsigned int *)(g.h_mem + o_ctr);
+  g.h_desc = (CloudDesc *)(g.h_mem + o_desc);
+  g.h_order = (int32_t *)(g.h_mem + o_order);
+  // The graph of both phases (falls back to plain launches if it cannot be
+  // captured).
+  cudaStream_t cs = nullptr;
+  cudaGraph_t graph = nullptr;
+  bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    cudaMemcpyAsync(g.d_par, g.h_par, sizeof(BatchParams), cudaMemcpyHostToDevice, cs);
+    cudaMemcpyAsync(g.d_desc, g.h_desc, sizeof(CloudDesc) * g.nc_cap, cudaMemcpyHostToDevice, cs);
+    cudaMemcpyAsync(g.d_order, g.h_order, sizeof(int32_t) * g.nc_cap, cudaMemcpyHostToDevice, cs);
+    cudaMemsetAsync(g.d_ctr, 0, sizeof(unsigned int) * BC_WORDS, cs);
+    const vr_status ls = launch_all(g, 3, cs);
+    cudaMemcpyAsync(g.h_desc, g.d_desc, sizeof(CloudDesc) * g.nc_cap, cudaMemcpyDeviceToHost, cs);
+    cudaMemcpyAsync(g.h_ctr, g.d_ctr, sizeof(unsigned int) * BC_WORDS, cudaMemcpyDeviceToHost, cs);
+    ok = cudaStreamEndCapture(cs, &graph) == cudaSuccess && ls == VR_OK && graph &&
+         cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (cs) cudaStreamDestroy(cs);
+  if (!ok) {
+    g.exec = nullptr;
+    g.graph_failed = true;
+  }
+  cudaGetLastError();
+  (void)s;
+  return VR_OK;
+}
+
+// Check out the engine of a shape (made on first use; a second user of a
+// busy engine gets a private one, released after the call).
+static BatchEngine *get_engine(int dev, vr_dtype dt, int d, int nmax, int nc, vr_batch_shape sh, cudaStream_t s,
+                               std::unique_ptr<BatchEngine> &priv, vr_status *err) {
+  int nc_cap = 64;
+  while (nc_cap < nc) nc_cap *= 2;
+  const size_t smem = smem_layout(nmax, d).bytes;
+  const int per = batch_max_per_sm(dt, smem);
+  if (per < 1) {
+    set_error("the batch kernel does not fit one SM with %zu bytes of shared memory", smem);
+    *err = VR_ERR_INTERNAL;
+    return nullptr;
+  }
+  const int cps = std::min(per, std::max(1, sh.ctas_per_sm));
+  {
+    std::lock_guard<std::mutex> lk(g_eng_mu);
+    for (auto &e : g_engines)
+      if (e->dev == dev && e->dtype == dt && e->d == d && e->nmax == nmax && e->nc_cap == nc_cap &&
+          e->shape.ctas_per_sm == cps && e->shape.order == sh.order && !e->busy) {
+        e->busy = true;
+        *err = VR_OK;
+        return e.get();
+      }
+  }
+  std::unique_ptr<BatchEngine> g(new BatchEngine());
+  g->dev = dev;
+  g->dtype = dt;
+  g->d = d;
+  g->nmax = nmax;
+  g->nc_cap = nc_cap;
+  g->shape = vr_batch_shape{cps, sh.order};
+  g->smem = smem;
+  g->grid = num_sms() * cps;
+  *err = make_engine(*g, s);
+  if (*err != VR_OK) return nullptr;
+  g->busy = true;
+  std::lock_guard<std::mutex> lk(g_eng_mu);
+  if (g_engines.size() < 32) {
+    g_engines.push_back(std::move(g));
+    return g_engines.back().get();
+  }
+  priv = std::move(g);
+  return priv.get();
+}
+
+static void release_engine(BatchEngine *g) {
+  std::lock_guard<std::mutex> lk(g_eng_mu);
+  g->busy = false;
+}
+
+// Scratch for the per-CTA slices (largest E and T of one cloud).
+static vr_status engine_scratch(BatchEngine &g, int64_t emax, int64_t tmax, bool F) {
+  const ScratchLayout SL = scratch_layout(emax, tmax, F);
+  const int64_t need = (int64_t)g.grid * SL.bytes;
+  if (need > g.scratch_bytes) {
+    if (g.scratch) {
+      VR_CUDA(cudaStreamSynchronize(nullptr));
+      cudaFree(g.scratch);
+      g.scratch = nullptr;
+      g.scratch_bytes = 0;
+    }
+    VR_CUDA(cudaMalloc((void **)&g.scratch, (size_t)need));
+    g.scratch_bytes = need;
+  }
+  g.emax_hint = emax;
+  g.tmax_hint = tmax;
+  g.h_par->scratch = g.scratch;
+  g.h_par->SL = SL;
+  g.h_par->emax_cap = emax;
+  g.h_par->tmax_cap = tmax;
+  return VR_OK;
+}
+
+// Output arenas of capacities cap[6] (edges, triangles, vertices, grade
+// values, edge colptr, triangle colptr), shared by the batch's results.
+static vr_status alloc_arenas(std::shared_ptr<Arenas> &ar, BatchOut &o, const int64_t cap[6], cudaStream_t s) {
+  ar = std::make_shared<Arenas>();
+  ar->stream = s;
+  VR_TRY(dalloc(ar->ptrs, &o.everts, 2 * cap[0], s));
+  VR_TRY(dalloc(ar->ptrs, &o.egrade, cap[0], s));
+  VR_TRY(dalloc(ar->ptrs, &o.erow, 2 * cap[0], s));
+  VR_TRY(dalloc(ar->ptrs, &o.ecol, cap[4], s));
+  VR_TRY(dalloc(ar->ptrs, &o.tverts, 3 * cap[1], s));
+  VR_TRY(dalloc(ar->ptrs, &o.tgrade, cap[1], s));
+  VR_TRY(dalloc(ar->ptrs, &o.trow, 3 * cap[1], s));
+  VR_TRY(dalloc(ar->ptrs, &o.tcol, cap[5], s));
+  VR_TRY(dalloc(ar->ptrs, &o.vverts, cap[2], s));
+  VR_TRY(dalloc(ar->ptrs, &o.vgrade, cap[2], s));
+  VR_TRY(dalloc(ar->ptrs, &o.gval, cap[3], s));
+  return VR_OK;
+}
+
+// One batch on one engine: returns the device time of the launch(es) in *ms
+// (events around the graph or the launches) when ms is given.
+static vr_status run_engine(BatchEngine &g, BatchJob &job, cudaStream_t s, float *ms) {
+  const int nc = (int)job.hd.size();
+  const bool F = g.dtype == VR_F32;
+  memcpy(g.h_desc, job.hd.data(), sizeof(CloudDesc) * nc);
+  std::vector<int32_t> order(nc);
+  std::iota(order.begin(), order.end(), 0);
+  if (g.shape.order == 0)
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return job.hd[x].n > job.hd[y].n; });
+  memcpy(g.h_order, order.data(), sizeof(int32_t) * nc);
+  BatchParams &P = *g.h_par;
+  P.pts = job.dpts;
+  P.n_clouds = nc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (ms) {
+    VR_CUDA(cudaEventCreate(&e0));
+    VR_CUDA(cudaEventCreate(&e1));
+  }
+  auto finish_events = [&]() {
+    if (ms && e0) {
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(ms, e0, e1);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (!g.hinted) {
+    // First batch of this engine: size it alone for exact capacities.
+    VR_TRY(engine_scratch(g, 1, 1, F));
+    for (int k = 0; k < 6; ++k) P.cap[k] = INT64_MAX;
+    VR_CUDA(cudaMemcpyAsync(g.d_par, g.h_par, sizeof(BatchParams), cudaMemcpyHostToDevice, s));
+    VR_CUDA(cudaMemcpyAsync(g.d_desc, g.h_desc, sizeof(CloudDesc) * nc, cudaMemcpyHostToDevice, s));
+    VR_CUDA(cudaMemcpyAsync(g.d_order, g.h_order, sizeof(int32_t) * nc, cudaMemcpyHostToDevice, s));
+    VR_CUDA(cudaMemsetAsync(g.d_ctr, 0, sizeof(unsigned int) * BC_WORDS, s));
+    VR_TRY(launch_all(g, 1, s));
+    VR_CUDA(cudaMemcpyAsync(g.h_ctr, g.d_ctr, sizeof(unsigned int) * BC_WORDS, cudaMemcpyDeviceToHost, s));
+    VR_CUDA(cudaStreamSynchronize(s));
+    if (g.h_ctr[4]) {
+      finish_events();
+      return flags_to_status((int32_t)g.h_ctr[4]);
+    }
+    const int64_t *tot = (const int64_t *)(g.h_ctr + 6);
+    for (int k = 0; k < 6; ++k) g.hint[k] = tot[k];
+    g.emax_hint = tot[6];
+    g.tmax_hint = tot[7];
+    g.hinted = true;
+  }
+  VR_TRY(engine_scratch(g, std::max<int64_t>(g.emax_hint, 1), std::max<int64_t>(g.tmax_hint, 1), F));
+  int64_t cap[6];
+  for (int k = 0; k < 6; ++k) cap[k] = std::max<int64_t>(g.hint[k], 1);
+  VR_TRY(alloc_arenas(job.ar, job.o, cap, s));
+  P.out = job.o;
+  for (int k = 0; k < 6; ++k) P.cap[k] = cap[k];
+  if (ms) VR_CUDA(cudaEventRecord(e0, s));
+  if (g.exec) {
+    VR_CUDA(cudaGraphLaunch(g.exec, s));
+    count_launch();
+  } else {
+    VR_CUDA(cudaMemcpyAsync(g.d_par, g.h_par, sizeof(BatchParams), cudaMemcpyHostToDevice, s));
+    VR_CUDA(cudaMemcpyAsync(g.d_desc, g.h_desc, sizeof(CloudDesc) * g.nc_cap, cudaMemcpyHostToDevice, s));
+    VR_CUDA(cudaMemcpyAsync(g.d_order, g.h_order, sizeof(int32_t) * g.nc_cap, cudaMemcpyHostToDevice, s));
+    VR_CUDA(cudaMemsetAsync(g.d_ctr, 0, sizeof(unsigned int) * BC_WORDS, s));
+    VR_TRY(launch_all(g, 3, s));
+    VR_CUDA(cudaMemcpyAsync(g.h_desc, g.d_desc, sizeof(CloudDesc) * g.nc_cap, cudaMemcpyDeviceToHost, s));
+    VR_CUDA(cudaMemcpyAsync(g.h_ctr, g.d_ctr, sizeof(unsigned int) * BC_WORDS, cudaMemcpyDeviceToHost, s));
+  }
+  if (ms) VR_CUDA(cudaEventRecord(e1, s));
+  VR_CUDA(cudaStreamSynchronize(s));
+  if (g.h_ctr[4]) {
+    finish_events();
+    return flags_to_status((int32_t)g.h_ctr[4]);
+  }
+  const int64_t *tot = (const int64_t *)(g.h_ctr + 6);
+  if (g.h_ctr[5]) {
+    // A capacity was short: exact arenas (and scratch), phase 2 again.
+    for (int k = 0; k < 6; ++k) cap[k] = std::max<int64_t>(tot[k], 1);
+    job.ar.reset();
+    VR_TRY(alloc_arenas(job.ar, job.o, cap, s));
+    VR_TRY(engine_scratch(g, std::max<int64_t>(tot[6], 1), std::max<int64_t>(tot[7], 1), F));
+    P.out = job.o;
+    for (int k = 0; k < 6; ++k) P.cap[k] = cap[k];
+    g.h_ctr[1] = 0;
+    g.h_ctr[5] = 0;
+    VR_CUDA(cudaMemcpyAsync(g.d_par, g.h_par, sizeof(BatchParams), cudaMemcpyHostToDevice, s));
+    VR_CUDA(cudaMemcpyAsync(g.d_ctr, g.h_ctr, sizeof(unsigned int) * BC_WORDS, cudaMemcpyHostToDevice, s));
+    VR_TRY(launch_all(g, 2, s));
+    VR_CUDA(cudaMemcpyAsync(g.h_desc, g.d_desc, sizeof(CloudDesc) * nc, cudaMemcpyDeviceToHost, s));
+    VR_CUDA(cudaMemcpyAsync(g.h_ctr, g.d_ctr, sizeof(unsigned int) * BC_WORDS, cudaMemcpyDeviceToHost, s));
+    if (ms) VR_CUDA(cudaEventRecord(e1, s));
+    VR_CUDA(cudaStreamSynchronize(s));
+    if (g.h_ctr[4]) {
+      finish_events();
+      return flags_to_status((int32_t)g.h_ctr[4]);
+    }
+  }
+  // Capacities for the next batches: what this one needed, plus slack.
+  for (int k = 0; k < 6; ++k) g.hint[k] = std::max(g.hint[k], tot[k] + tot[k] / 16);
+  g.emax_hint = std::max(g.emax_hint, tot[6]);
+  g.tmax_hint = std::max(g.tmax_hint, tot[7]);
+  memcpy(job.hd.data(), g.h_desc, sizeof(CloudDesc) * nc);
+  finish_events();
+  return VR_OK;
+}
+
+// The shapes the tuner tries for a class: every CTAs-per-SM count the
+// launch allows, in both work-list orders.
+static std::vector<vr_batch_shape> tune_candidates(int per) {
+  std::vector<vr_batch_shape> v;
+  for (int k = 1; k <= per; ++k)
+    for (int o = 0; o < 2; ++o) v.push_back(vr_batch_shape{k, o});
+  return v;
+}
+
+// The batch through the one-launch engine.  Shape: the pinned one, else the
+// tuned one of the batch's class (device, dtype, d, largest fused cloud
+// rounded up to 64 points); a class seen for the first time is tuned now:
+// each candidate shape builds the whole batch twice and the second run's
+// device time counts (the first carries the engine's one-off sizing and
+// graph instantiation).
+static vr_status batch_onelaunch(BatchJob &job, cudaStream_t s) {
+  int nmax = 0;
+  for (auto &c : job.hd)
+    if (!c.fallback) nmax = std::max(nmax, c.n);
+  if (nmax == 0) {  // nothing for the fused kernels: the single-cloud path builds every cloud
+    const int64_t cap[6] = {1, 1, 1, 1, 1, 1};
+    return alloc_arenas(job.ar, job.o, cap, s);
+  }
+  int ncls = (nmax + 63) / 64 * 64;
+  if (!fused_fits(ncls, job.d)) ncls = nmax;
+  vr_batch_shape sh = g_pinned_shape;
+  g_last_tune = TuneRec{};
+  if (sh.ctas_per_sm <= 0) {
+    bool found = false;
+    {
+      std::lock_guard<std::mutex> lk(g_eng_mu);
+      for (auto &t : g_tuned)
+        if (t.dev == job.dev && t.dtype == job.dtype && t.d == job.d && t.nmax == ncls) {
+          sh = t.best;
+          g_last_tune = t;
+          found = true;
+        }
+    }
+    if (!found) {
+      TuneRec rec{job.dev, job.dtype, job.d, ncls, vr_batch_shape{0, 0}, {}};
+      const int per = batch_max_per_sm(job.dtype, smem_layout(ncls, job.d).bytes);
+      double best = 1e300;
+      for (const vr_batch_shape &cand : tune_candidates(std::max(per, 1))) {
+        std::unique_ptr<BatchEngine> priv;
+        vr_status es;
+        BatchEngine *g = get_engine(job.dev, job.dtype, job.d, ncls, (int)job.hd.size(), cand, s, priv, &es);
+        if (!g) return es;
+        float ms = 0.f;
+        vr_status rs = VR_OK;
+        for (int rep = 0; rep < 2 && rs == VR_OK; ++rep) {
+          BatchJob tj;
+          tj.s = s;
+          tj.d = job.d;
+          tj.dtype = job.dtype;
+          tj.dpts = job.dpts;
+          tj.dev = job.dev;
+          tj.hd = job.hd;
+          rs = run_engine(*g, tj, s, &ms);
+        }
+        release_engine(g);
+        if (rs != VR_OK) return rs;
+        rec.cand.push_back({g->shape, (double)ms});
+        if (ms < best) {
+          best = ms;
+          rec.best = g->shape;
+        }
+      }
+      sh = rec.best;
+      std::lock_guard<std::mutex> lk(g_eng_mu);
+      g_tuned.push_back(rec);
+      g_last_tune = rec;
+      // Keep the winner's engine only: the others hold per-CTA scratch.
+      for (size_t k = 0; k < g_engines.size();) {
+        BatchEngine &e = *g_engines[k];
+        if (!e.busy && e.dev == job.dev && e.dtype == job.dtype && e.d == job.d && e.nmax == ncls &&
+            !(e.shape.ctas_per_sm == sh.ctas_per_sm && e.shape.order == sh.order))
+          g_engines.erase(g_engines.begin() + k);
+        else
+          ++k;
+      }
+    }
+  }
+  std::unique_ptr<BatchEngine> priv;
+  vr_status es;
+  BatchEngine *g = get_engine(job.dev, job.dtype, job.d, ncls, (int)job.hd.size(), sh, s, priv, &es);
+  if (!g) return es;
+  const vr_status rs = run_engine(*g, job, s, nullptr);
+  g_last_shape = g->shape;
+  release_engine(g);
+  return rs;
+}
+
 // ---- asynchronous job interface (jobs.h)
 struct Job {
   BatchJob b;
@@ -999,7 +1589,10 @@ vr_status vr_build_batch(const void *points, const int64_t *offsets, int32_t n_c
   if (d < 1) { set_error("d = %d must be >= 1", d); return VR_ERR_ARG; }
   if (dtype != VR_I8 && dtype != VR_I32 && dtype != VR_F32) { set_error("unknown dtype"); return VR_ERR_ARG; }
   if (offsets[0] != 0) { set_error("offsets[0] must be 0"); return VR_ERR_ARG; }
+  int dev = 0;
+  VR_CUDA(cudaGetDevice(&dev));
   auto job = new_batch_job();
+  job->dev = dev;
   job->hd.resize(n_clouds);
   for (int i = 0; i < n_clouds; ++i)
     VR_TRY(make_desc(job->hd[i], offsets[i], offsets[i + 1] - offsets[i], d, dtype, maxdim ? maxdim[i] : 2,
@@ -1033,10 +1626,7 @@ vr_status vr_build_batch(const void *points, const int64_t *offsets, int32_t n_c
   job->d = d;
   job->dtype = dtype;
   job->dpts = dpts;
-  vr_status st = job->size_async();
-  if (st == VR_OK && cudaStreamSynchronize(s) != cudaSuccess) st = cuda_status(cudaGetLastError(), "sync", __FILE__, __LINE__);
-  if (st == VR_OK) st = job->build_async(INT64_MAX, nullptr);
-  if (st == VR_OK && cudaStreamSynchronize(s) != cudaSuccess) st = cuda_status(cudaGetLastError(), "sync", __FILE__, __LINE__);
+  vr_status st = batch_onelaunch(*job, s);
   if (st != VR_OK) {
     vr_batch_free(b);
     return st;
@@ -1048,6 +1638,34 @@ vr_status vr_build_batch(const void *points, const int64_t *offsets, int32_t n_c
       b->total_simplices += v->count[0] + v->count[1] + v->count[2];
     }
   *out = b;
+  return VR_OK;
+}
+
+vr_status vr_batch_set_shape(const vr_batch_shape *shape) {
+  if (shape && shape->ctas_per_sm > 0 && (shape->order < 0 || shape->order > 1)) {
+    set_error("order %d outside {0, 1}", shape->order);
+    return VR_ERR_ARG;
+  }
+  g_pinned_shape = shape ? *shape : vr_batch_shape{0, 0};
+  if (g_pinned_shape.ctas_per_sm < 0) g_pinned_shape.ctas_per_sm = 0;
+  return VR_OK;
+}
+
+vr_status vr_batch_get_shape(vr_batch_shape *used, int32_t *n_cand, vr_batch_shape *cand, double *cand_ms,
+                             int32_t max_cand) {
+  if (used) *used = g_last_shape;
+  const int nc = (int)g_last_tune.cand.size();
+  if (n_cand) *n_cand = nc;
+  for (int k = 0; k < nc && k < max_cand; ++k) {
+    if (cand) cand[k] = g_last_tune.cand[k].first;
+    if (cand_ms) cand_ms[k] = g_last_tune.cand[k].second;
+  }
+  return VR_OK;
+}
+
+vr_status vr_batch_tune_reset(void) {
+  std::lock_guard<std::mutex> lk(g_eng_mu);
+  g_tuned.clear();
   return VR_OK;
 }
 

@@ -115,3 +115,46 @@ def test_bad_cloud_fails_alone(torch):
     assert b.get(0)[0] == vr.VR_OK and b.get(2)[0] == vr.VR_OK
     assert b.get(1)[0] == vr.VR_ERR_ARG and b.get(1)[1] is None
     assert b.info()["n_failed"] == 1
+
+
+@pytest.mark.parametrize("cps,order", [(1, 0), (1, 1), (2, 0), (3, 1)])
+def test_pinned_shapes_give_the_same_complexes(torch, cps, order):
+    """The one-launch batch under each pinned launch shape (CTAs per SM,
+    work-list order): every cloud still equals the oracle."""
+    clouds = synth.config4(96)
+    vr.vr_batch_set_shape(cps, order)
+    try:
+        check_batch(torch, clouds)
+        used = vr.vr_batch_get_shape()["used"]
+        assert used[1] == order and 1 <= used[0] <= cps
+    finally:
+        vr.vr_batch_set_shape(0)
+
+
+def test_tuner_records_candidates(torch):
+    vr.vr_batch_tune_reset()
+    clouds = synth.config4(128)
+    check_batch(torch, clouds)
+    info = vr.vr_batch_get_shape()
+    assert len(info["candidates"]) >= 2
+    assert info["used"] in [c for c, _ in info["candidates"]]
+    assert all(ms > 0 for _, ms in info["candidates"])
+    best = min(info["candidates"], key=lambda c: c[1])[0]
+    assert info["used"] == best
+
+
+def test_batch_outgrowing_the_arenas_is_rebuilt_exactly(torch):
+    """A class first seen with sparse clouds, then with much denser ones of
+    the same sizes: the second batch overflows the arenas sized from the
+    first and is rebuilt into exact ones."""
+    vr.vr_batch_set_shape(2, 0)
+    try:
+        g = synth.rng(88)
+        sizes = g.integers(200, 257, size=40)
+        sparse = [synth.Cloud(synth.quantize(synth.sphere(int(m), g), 100.0), 2, 20.0) for m in sizes]
+        dense = [synth.Cloud(c.points, 2, 60.0) for c in sparse]
+        check_batch(torch, sparse)
+        check_batch(torch, dense)
+        check_batch(torch, sparse)
+    finally:
+        vr.vr_batch_set_shape(0)
