@@ -858,6 +858,37 @@ def oracle_build_keep(cloud):
     return oracle.vr_build(cloud.points, cloud.maxdim, cloud.maxrad, keep_handle=True)
 
 
+def gram_accuracy(cloud, pts_dev, step, read_phases, L, flush):
+    """The float tensor-core distance tiles against the canonical FP64 values
+    (every pair; untimed): max relative error in d over the kept pairs, the
+    normalised error and its bound beta, the pairs left to the exact FP64
+    decision; for the two-way split (the build's) and the three-way split,
+    with the distance phase's time in builds under each."""
+    import torch
+    import paper_1809_04424_b300 as vr
+    out = {"what": "max |d_tc - d_fp64| / d_fp64 over kept pairs; split 2 = hi+lo (3 products, used), "
+                   "3 = hi+mid+lo (6 products)"}
+    for split in (2, 3):
+        a = vr.vr_gram_accuracy_check(pts_dev, cloud.maxrad, split=split)
+        vr.vr_set_gram_split(split)
+        L.vr_profile_select(None)
+        L.vr_profile_reset()
+        L.vr_profile_enable(1)
+        for _ in range(10):
+            flush.zero_()
+            c = step()
+            del c
+        torch.cuda.synchronize()
+        L.vr_profile_enable(0)
+        ph = read_phases()
+        vr.vr_set_gram_split(2)
+        out[f"split{split}"] = {"max_rel_d_err": a["max_rel_d_err"], "max_norm_err": a["max_norm_err"],
+                                "beta": a["beta"], "kept_pairs": a["kept_pairs"], "band_pairs": a["band_pairs"],
+                                "distance_phase_ms": round(ph["distance"]["ms_per_call"], 4) if "distance" in ph
+                                else None}
+    return out
+
+
 def single_cloud_leg(args, ranks, local):
     """One vr_build per step of the chosen single-cloud workload; returns the
     contract's line (without the CPU baseline) and the cloud."""
@@ -1022,9 +1053,11 @@ def single_cloud_leg(args, ranks, local):
             "phases_note": "ms per call, from an untimed calibration pass before the timed region",
             "phase_launches": {k: v["launches_per_call"] for k, v in phases.items()},
             "clocks": clk.summary()}
-    for k in ("max_rel_dist_err", "gram_max_rel_d_err", "gram_band_pairs", "near_tie_edges"):
+    for k in ("max_rel_dist_err", "near_tie_edges"):
         if k in st:
             line.setdefault("accuracy", {})[k] = st[k]
+    if cloud.points.dtype == np.float32 and 16 < cloud.d <= 64 and not isinstance(cloud, synth.Matrix):
+        line.setdefault("accuracy", {})["gram"] = gram_accuracy(cloud, pts_dev, step, read_phases, L, flush)
     del flush
     torch.cuda.empty_cache()
     return line, cloud

@@ -310,6 +310,28 @@ VR_API vr_status vr_set_barcode_dense_min(int64_t min_entries);
  * way. */
 VR_API vr_status vr_set_gram_path(int32_t mode);
 
+/* Float split of the tensor-core distance tiles (no counterpart in the
+ * paper): 2 = two-way, y = hi + lo (bf16 each; products hi.hi, hi.lo,
+ * lo.hi; the default), 3 = three-way, y = hi + mid + lo (six products).
+ * Process-wide.  Either split decides the same pairs: pairs within the
+ * tiles' error bound of the cap are decided by the canonical FP64 value. */
+VR_API vr_status vr_set_gram_split(int32_t split);
+
+/* Accuracy of the float tensor-core distance tiles (no counterpart in the
+ * paper).  For device float points (n <= 8192, d <= 64) and a radius cap,
+ * the tiles of the given split (0: the current one) are run with every
+ * pair's canonical FP64 value beside them.  Synchronous; for tests and
+ * measurement. */
+typedef struct vr_gram_accuracy {
+  double max_rel_d_err;  /* max |d_tc - d_fp64| / d_fp64 over the kept pairs */
+  double max_norm_err;   /* max |d2_tc - d2_fp64| / (|y_i|^2 + |y_j|^2), all pairs */
+  double beta;           /* the tiles' bound on the latter (their cap test uses it) */
+  int64_t kept_pairs;    /* pairs with d_fp64 <= maxrad */
+  int64_t band_pairs;    /* pairs within beta of the cap: decided by the FP64 value */
+} vr_gram_accuracy;
+VR_API vr_status vr_gram_accuracy_check(const float *points, int32_t n, int32_t d, double maxrad,
+                                        int32_t split, vr_stream_t stream, vr_gram_accuracy *out);
+
 /* Validation of the float Gram-tile error bound (no counterpart in the
  * paper): for device float points (n <= 8192, d <= 64) compute every pair's
  * tensor-core value and canonical FP64 value and return the worst

@@ -275,6 +275,33 @@ def vr_pool_used_bytes() -> int:
     return v.value
 
 
+class GramAccuracy(ctypes.Structure):
+    _fields_ = [("max_rel_d_err", ctypes.c_double), ("max_norm_err", ctypes.c_double), ("beta", ctypes.c_double),
+                ("kept_pairs", ctypes.c_int64), ("band_pairs", ctypes.c_int64)]
+
+
+def vr_gram_accuracy_check(points, maxrad: float, split: int = 0, stream=None) -> dict:
+    """Tensor-core distance tiles against the canonical FP64 values on device
+    float32 points (a CUDA tensor): max relative error in d over the kept
+    pairs, the normalised error, beta, kept and band pair counts."""
+    L = lib()
+    L.vr_gram_accuracy_check.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                         ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(GramAccuracy)]
+    L.vr_gram_accuracy_check.restype = ctypes.c_int
+    a = GramAccuracy()
+    s = _current_stream() if stream is None else stream
+    _check(L.vr_gram_accuracy_check(ctypes.c_void_p(points.data_ptr()), points.shape[0], points.shape[1],
+                                    float(maxrad), int(split), ctypes.c_void_p(s), ctypes.byref(a)))
+    return {f: getattr(a, f) for f, _ in GramAccuracy._fields_}
+
+
+def vr_set_gram_split(split: int) -> None:
+    L = lib()
+    L.vr_set_gram_split.argtypes = [ctypes.c_int32]
+    L.vr_set_gram_split.restype = ctypes.c_int
+    _check(L.vr_set_gram_split(int(split)))
+
+
 def vr_complex_dim(handle, k: int) -> DimView:
     v = DimView()
     _check(lib().vr_complex_dim(ctypes.c_void_p(handle), k, ctypes.byref(v)))

@@ -196,8 +196,9 @@ static void launch_dist(const void *X, int n, int d, int W, const Cap &cap, uint
 }
 
 bool gram_tc_eligible(vr_dtype dtype, int n, int d);
+struct GramAcc;
 vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, uint32_t *adj, DevStatus *st,
-                         cudaStream_t s, unsigned int *worst_bits);
+                         cudaStream_t s, GramAcc *acc, int split = 0);
 
 // Time-sliced adjacency of the max-edge triangle enumeration: at most this
 // many bytes of snapshots (kept well inside L2), at most SNAP_MAX_S slices.

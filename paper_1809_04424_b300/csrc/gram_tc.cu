@@ -28,6 +28,11 @@
 // K * 2^-24 S^2; final subtraction 3 * 2^-23 S^2 -- in all below 7e-5 S^2 <=
 // 1.4e-4 (|y_i|^2 + |y_j|^2), so beta has more than 2x margin; a test measures
 // the observed error against beta on adversarial inputs.
+// Three-way split (vr_set_gram_split(3)): y = hi + mid + lo holds y's 24
+// significant bits exactly, the dropped mid.lo, lo.mid, lo.lo terms are below
+// 2^-23 S^2 / 4, and the accumulation bound doubles (6K = 384 products):
+// still below 7.5e-5 S^2, inside the same beta.  It shrinks the observed
+// error (no truncated lo.lo), not the band: the bound is the accumulation's.
 //
 // Every wait (TMA and MMA completion) is bounded; on a timeout the kernel
 // raises F_TIMEOUT, releases its TMEM and returns.
@@ -137,14 +142,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // Operand preparation: y = x - c, hi = bf16(y), lo = bf16(y - hi) (float), or
 // hi = x exactly (int8); rows padded to 64 coordinates and to whole tiles.
 // norm = |hi + lo|^2 in fp32 (fma in coordinate order).
+// Three-way split (Xm non-null): y = hi + mid + lo, mid = bf16(y - hi),
+// lo = bf16(y - hi - mid) (24 significant bits: y itself).
 template <bool F>
 // One warp per padded row: lane l owns coordinates 2l and 2l+1 (bf16x2
 // stores, coalesced), |y_i|^2 by a warp sum of the split values.
 __global__ void k_gram_prep(const void *Xv, int n, int d, int npad, const float *centre, __nv_bfloat16 *Xh,
-                            __nv_bfloat16 *Xl, float *norm) {
+                            __nv_bfloat16 *Xl, float *norm, __nv_bfloat16 *Xm = nullptr) {
   const int lane = threadIdx.x & 31;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < npad; i += (gridDim.x * blockDim.x) >> 5) {
-    float hi[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
+    float hi[2] = {0.f, 0.f}, mid[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int k = 2 * lane + h;
@@ -152,7 +159,12 @@ __global__ void k_gram_prep(const void *Xv, int n, int d, int npad, const float 
         if constexpr (F) {
           const float y = __fsub_rn(((const float *)Xv)[(int64_t)i * d + k], centre[k]);
           hi[h] = __bfloat162float(__float2bfloat16_rn(y));
-          lo[h] = __bfloat162float(__float2bfloat16_rn(__fsub_rn(y, hi[h])));
+          if (Xm) {
+            mid[h] = __bfloat162float(__float2bfloat16_rn(__fsub_rn(y, hi[h])));
+            lo[h] = __bfloat162float(__float2bfloat16_rn(__fsub_rn(__fsub_rn(y, hi[h]), mid[h])));
+          } else {
+            lo[h] = __bfloat162float(__float2bfloat16_rn(__fsub_rn(y, hi[h])));
+          }
         } else {
           hi[h] = (float)((const int32_t *)Xv)[(int64_t)i * d + k];
         }
@@ -160,7 +172,8 @@ __global__ void k_gram_prep(const void *Xv, int n, int d, int npad, const float 
     }
     ((__nv_bfloat162 *)(Xh + (int64_t)i * TC_K))[lane] = __floats2bfloat162_rn(hi[0], hi[1]);
     if constexpr (F) ((__nv_bfloat162 *)(Xl + (int64_t)i * TC_K))[lane] = __floats2bfloat162_rn(lo[0], lo[1]);
-    const float x0 = hi[0] + lo[0], x1 = hi[1] + lo[1];
+    if (F && Xm) ((__nv_bfloat162 *)(Xm + (int64_t)i * TC_K))[lane] = __floats2bfloat162_rn(mid[0], mid[1]);
+    const float x0 = __fadd_rn(__fadd_rn(hi[0], mid[0]), lo[0]), x1 = __fadd_rn(__fadd_rn(hi[1], mid[1]), lo[1]);
     const float acc = warp_sum(__fmaf_rn(x1, x1, x0 * x0));
     if (lane == 0) norm[i] = acc;
   }
@@ -207,7 +220,15 @@ __global__ void __launch_bounds__(1024) k_gram_centre(const float *X, int n, int
 }
 
 struct TcSmem {
-  uint32_t ah, bh, al, bl, bar_tma, bar_mma, tslot;
+  uint32_t ah, bh, al, bl, am, bm, bar_tma, bar_mma, tslot;
+};
+
+// Accuracy counters of the validation variant.
+struct GramAcc {
+  unsigned int worst_norm;       // float bits: max |d2_tc - d2_fp64| / (|y_i|^2 + |y_j|^2), all pairs
+  unsigned int worst_rel_d;      // float bits: max |d_tc - d_fp64| / d_fp64, kept pairs
+  unsigned long long kept;       // pairs with d2_fp64 <= r2
+  unsigned long long band;       // pairs the tiles leave to the exact decision
 };
 
 // One CTA (TC_THREADS) per upper-triangle tile pair (ti <= tj).  Float
@@ -216,13 +237,15 @@ struct TcSmem {
 // and records the worst observed |d2_tc - d2_fp64| / (|y_i|^2 + |y_j|^2).
 // INJ (test hook, vr_inject_gram_stall): CTA `stall_tile` issues no MMA and
 // no completion, so its waits run out after `wait_limit` polls.
-template <bool F, bool VALIDATE, bool INJ = false>
+// S3: three-way split (hi, mid, lo), six products hh, hm, mh, hl, lh, mm.
+template <bool F, bool VALIDATE, bool INJ = false, bool S3 = false>
 __global__ void __launch_bounds__(TC_THREADS) k_gram_bitmap_tc(const __grid_constant__ CUtensorMap tmh,
                                                         const __grid_constant__ CUtensorMap tml, const void *Xv,
                                                         int n, int d, int W, int nt, Cap cap, const float *norm,
                                                         uint32_t *adj, DevStatus *st, uint64_t *band,
-                                                        uint64_t band_cap, unsigned int *worst_bits,
-                                                        int stall_tile = -1, long wait_limit = TC_WAIT_LIMIT) {
+                                                        uint64_t band_cap, GramAcc *acc_out,
+                                                        int stall_tile = -1, long wait_limit = TC_WAIT_LIMIT,
+                                                        const __grid_constant__ CUtensorMap tmm = CUtensorMap{}) {
   // Only the stalled CTA's completion wait takes the short limit: every other
   // wait guards a TMA load or an MMA that is really in flight.
   const bool stalled = INJ && (int)blockIdx.x == stall_tile;
@@ -243,7 +266,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_bitmap_tc(const __grid_cons
   S.bh = base + TC_OPERAND_BYTES;
   S.al = base + 2 * TC_OPERAND_BYTES;
   S.bl = base + 3 * TC_OPERAND_BYTES;
-  S.bar_tma = base + 4 * TC_OPERAND_BYTES;
+  S.am = base + 4 * TC_OPERAND_BYTES;
+  S.bm = base + 5 * TC_OPERAND_BYTES;
+  S.bar_tma = base + (S3 ? 6 : 4) * TC_OPERAND_BYTES;
   S.bar_mma = S.bar_tma + 8;
   S.tslot = S.bar_tma + 16;
   uint32_t *tslot_ptr = (uint32_t *)(smem_raw + (S.tslot - raw));
@@ -265,13 +290,17 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_bitmap_tc(const __grid_cons
   const uint32_t tmem = *(volatile uint32_t *)tslot_ptr;
 
   if (threadIdx.x == 0) {
-    const uint32_t bytes = (F ? 4 : 2) * TC_OPERAND_BYTES;
+    const uint32_t bytes = (S3 ? 6 : F ? 4 : 2) * TC_OPERAND_BYTES;
     mbar_expect_tx(S.bar_tma, bytes);
     tma_load_2d(S.ah, &tmh, 0, ti * TC_TILE, S.bar_tma);
     tma_load_2d(S.bh, &tmh, 0, tj * TC_TILE, S.bar_tma);
     if (F) {
       tma_load_2d(S.al, &tml, 0, ti * TC_TILE, S.bar_tma);
       tma_load_2d(S.bl, &tml, 0, tj * TC_TILE, S.bar_tma);
+    }
+    if (S3) {
+      tma_load_2d(S.am, &tmm, 0, ti * TC_TILE, S.bar_tma);
+      tma_load_2d(S.bm, &tmm, 0, tj * TC_TILE, S.bar_tma);
     }
     if (stalled) {
       // Test hook: the operands arrived (waited for, so nothing is in flight
@@ -280,8 +309,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_bitmap_tc(const __grid_cons
     } else if (mbar_wait(S.bar_tma, 0)) {
       tc_fence_after();
       uint32_t acc = 0;
-      const uint32_t As[3] = {S.ah, S.ah, S.al}, Bs[3] = {S.bh, S.bl, S.bh};
-      const int nprod = F ? 3 : 1;
+      // Products: hi.hi, hi.lo, lo.hi (two-way split) or hi.hi, hi.mid,
+      // mid.hi, hi.lo, lo.hi, mid.mid (three-way split).
+      const uint32_t As[6] = {S.ah, S.ah, S.al, S.ah, S.am, S.am};
+      const uint32_t Bs[6] = {S.bh, S.bl, S.bh, S.bm, S.bh, S.bm};
+      const int nprod = S3 ? 6 : F ? 3 : 1;
       for (int p = 0; p < nprod; ++p)
         for (int k = 0; k < TC_K / 16; ++k) {
           umma_bf16(tmem, umma_desc_sw128(As[p] + 32 * k), umma_desc_sw128(Bs[p] + 32 * k), acc);
@@ -304,7 +336,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_bitmap_tc(const __grid_cons
     const int i = ti * TC_TILE + q * 32 + lane;  // this thread's pair row
     const float ni = i < n ? norm[i] : 0.f;
     const bool diag = ti == tj;
-    unsigned int worst = 0;
+    unsigned int worst = 0, worst_rel = 0;
+    unsigned int kept_cnt = 0, band_cnt = 0;
     for (int c0 = half * (TC_TILE / 2); c0 < (half + 1) * (TC_TILE / 2); c0 += 32) {
       float g[32];
       tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, g);
@@ -325,6 +358,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_bitmap_tc(const __grid_cons
               const double f = d2_canonical((const float *)Xv + (int64_t)i * d, (const float *)Xv + (int64_t)j * d, d);
               const float r = (float)(fabs((double)d2 - f) / ((double)ni + (double)nj + 1e-30));
               worst = max(worst, __float_as_uint(r));
+              if (i < j && (cap.keep_all || f <= cap.r2)) {
+                ++kept_cnt;
+                if (f > 0.0) {
+                  const double dt = sqrt(fmax((double)d2, 0.0)), df = sqrt(f);
+                  worst_rel = max(worst_rel, __float_as_uint((float)(fabs(dt - df) / df)));
+                }
+              }
+              band_cnt += in_band;
             }
           } else {
             const uint64_t v = (uint64_t)(int64_t)d2;  // exact: every term is an integer below 2^24
@@ -353,7 +394,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_bitmap_tc(const __grid_cons
       const int jrow = tj * TC_TILE + c0 + lane;
       if (!diag && jrow < n && wm < W) adj[(int64_t)jrow * W + wm] = mirror;
     }
-    if (VALIDATE && worst) atomicMax(worst_bits, worst);
+    if constexpr (VALIDATE) {
+      if (worst) atomicMax(&acc_out->worst_norm, worst);
+      if (worst_rel) atomicMax(&acc_out->worst_rel_d, worst_rel);
+      const unsigned int kc = warp_sum((int)kept_cnt), bc = warp_sum((int)band_cnt);
+      if (lane == 0) {
+        if (kc) atomicAdd(&acc_out->kept, (unsigned long long)kc);
+        if (bc) atomicAdd(&acc_out->band, (unsigned long long)bc);
+      }
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -424,101 +473,95 @@ bool gram_tc_eligible(vr_dtype dtype, int n, int d) {
   return nt * (nt + 1) / 2 >= 2 * num_sms();
 }
 
+// Float split: 2 = two-way (hi, lo; three products, the default), 3 =
+// three-way (hi, mid, lo; six products).  Process-wide.
+static int g_gram_split = 2;
+
+template <bool F, bool VALIDATE, bool INJ, bool S3>
+static cudaError_t launch_tiles(int ntiles, size_t smem, cudaStream_t s, const CUtensorMap &mh, const CUtensorMap &ml,
+                                const CUtensorMap &mm, const void *X, int n, int d, int W, int nt, const Cap &cap,
+                                const float *norm, uint32_t *adj, DevStatus *st, uint64_t *band, uint64_t band_cap,
+                                GramAcc *acc, int stall_tile, long stall_limit) {
+  cudaError_t e = cudaFuncSetAttribute(k_gram_bitmap_tc<F, VALIDATE, INJ, S3>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_gram_bitmap_tc<F, VALIDATE, INJ, S3><<<ntiles, TC_THREADS, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st,
+                                                                         band, band_cap, acc, stall_tile, stall_limit,
+                                                                         mm);
+  return cudaGetLastError();
+}
+
 // Bitmap of kept pairs on the tensor cores.  X is the staged point array
-// (int32 for int8 input, float for float input).  `worst_bits` non-null
-// turns on validation (float only).
+// (int32 for int8 input, float for float input).  `acc` non-null turns on
+// validation (float only: every pair's canonical value, accuracy counters).
+// split3: three-way float split (six products).
 vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, uint32_t *adj, DevStatus *st,
-                         cudaStream_t s, unsigned int *worst_bits) {
+                         cudaStream_t s, GramAcc *acc, int split = 0) {
+  const bool S3 = F && (split ? split == 3 : g_gram_split == 3);
   const int W = (n + 31) / 32;
   const int nt = (n + TC_TILE - 1) / TC_TILE;
   const int npad = nt * TC_TILE;
-  __nv_bfloat16 *Xh = nullptr, *Xl = nullptr;
+  __nv_bfloat16 *Xh = nullptr, *Xl = nullptr, *Xm = nullptr;
   float *norm = nullptr, *centre = nullptr;
   uint64_t *band = nullptr;
+  auto release = [&]() {
+    for (void *p : {(void *)Xh, (void *)Xl, (void *)Xm, (void *)norm, (void *)centre, (void *)band})
+      if (p) cudaFreeAsync(p, s);
+  };
   auto fail = [&](cudaError_t e) {
     cudaGetLastError();
-    if (Xh) cudaFreeAsync(Xh, s);
-    if (Xl) cudaFreeAsync(Xl, s);
-    if (norm) cudaFreeAsync(norm, s);
-    if (centre) cudaFreeAsync(centre, s);
-    if (band) cudaFreeAsync(band, s);
+    release();
     return cuda_status(e, "gram_bitmap_tc", __FILE__, __LINE__);
   };
   cudaError_t e;
   if ((e = dev_malloc((void **)&Xh, (size_t)npad * TC_ROW_BYTES, s)) != cudaSuccess) return fail(e);
   if ((e = dev_malloc((void **)&Xl, (size_t)npad * TC_ROW_BYTES, s)) != cudaSuccess) return fail(e);
+  if (S3 && (e = dev_malloc((void **)&Xm, (size_t)npad * TC_ROW_BYTES, s)) != cudaSuccess) return fail(e);
   if ((e = dev_malloc((void **)&norm, (size_t)npad * 4, s)) != cudaSuccess) return fail(e);
   if ((e = dev_malloc((void **)&centre, (size_t)TC_K * 4, s)) != cudaSuccess) return fail(e);
-  CUtensorMap mh, ml;
+  CUtensorMap mh, ml, mm;
   vr_status vs = make_map(&mh, Xh, npad);
   if (vs == VR_OK) vs = make_map(&ml, Xl, npad);
+  if (vs == VR_OK) vs = make_map(&mm, S3 ? Xm : Xh, npad);
   if (vs != VR_OK) {
-    fail(cudaSuccess);
+    release();
     return vs;
   }
   if (F) {
     k_gram_centre<<<1, 1024, 0, s>>>((const float *)X, n, d, centre);
-    k_gram_prep<true><<<(npad + 7) / 8, 256, 0, s>>>(X, n, d, npad, centre, Xh, Xl, norm);
+    k_gram_prep<true><<<(npad + 7) / 8, 256, 0, s>>>(X, n, d, npad, centre, Xh, Xl, norm, S3 ? Xm : nullptr);
   } else {
     k_gram_prep<false><<<(npad + 7) / 8, 256, 0, s>>>(X, n, d, npad, centre, Xh, Xl, norm);
   }
   count_launch(F ? 2 : 1);
-  const size_t smem = 4 * TC_OPERAND_BYTES + 1024 + 64;
+  const size_t smem = (S3 ? 6 : 4) * TC_OPERAND_BYTES + 1024 + 64;
   const int ntiles = nt * (nt + 1) / 2;
   const uint64_t npairs = (uint64_t)n * (n - 1) / 2;
   const uint64_t band_cap = std::min<uint64_t>(npairs, std::max<uint64_t>(1u << 20, npairs / 16));
-  if (F && !worst_bits) {
+  if (F && !acc) {
     if ((e = dev_malloc((void **)&band, band_cap * 8, s)) != cudaSuccess) return fail(e);
     if ((e = cudaMemsetAsync(&st->band_count, 0, 8, s)) != cudaSuccess) return fail(e);
   }
-  if (F && worst_bits) {
-    if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) != cudaSuccess)
-      return fail(e);
-    k_gram_bitmap_tc<true, true><<<ntiles, TC_THREADS, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st, nullptr, 0,
-                                                           worst_bits);
-  } else if (F) {
-    int stall_tile = -1;
-    long stall_limit = TC_WAIT_LIMIT;
-    if (take_gram_stall(ntiles, &stall_tile, &stall_limit)) {
-      if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem)) != cudaSuccess)
-        return fail(e);
-      k_gram_bitmap_tc<true, false, true><<<ntiles, TC_THREADS, smem, s>>>(
-          mh, ml, X, n, d, W, nt, cap, norm, adj, st, band, band_cap, nullptr, stall_tile, stall_limit);
-    } else {
-      if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem)) != cudaSuccess)
-        return fail(e);
-      k_gram_bitmap_tc<true, false><<<ntiles, TC_THREADS, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st, band,
-                                                              band_cap, nullptr);
-    }
+  int stall_tile = -1;
+  long stall_limit = TC_WAIT_LIMIT;
+  const bool inj = !acc && take_gram_stall(ntiles, &stall_tile, &stall_limit);
+#define VR_TILES(FF, VV, II, SS) \
+  launch_tiles<FF, VV, II, SS>(ntiles, smem, s, mh, ml, mm, X, n, d, W, nt, cap, norm, adj, st, band, band_cap, acc, \
+                               stall_tile, stall_limit)
+  if (F && acc) e = S3 ? VR_TILES(true, true, false, true) : VR_TILES(true, true, false, false);
+  else if (F && inj) e = S3 ? VR_TILES(true, false, true, true) : VR_TILES(true, false, true, false);
+  else if (F) e = S3 ? VR_TILES(true, false, false, true) : VR_TILES(true, false, false, false);
+  else if (inj) e = VR_TILES(false, false, true, false);
+  else e = VR_TILES(false, false, false, false);
+#undef VR_TILES
+  count_launch();
+  if (e != cudaSuccess) return fail(e);
+  if (F && !acc) {
     k_band_patch<<<num_sms() * 4, 256, 0, s>>>((const float *)X, d, W, cap.r2, band, st, band_cap, adj);
     count_launch();
-  } else {
-    int stall_tile = -1;
-    long stall_limit = TC_WAIT_LIMIT;
-    if (take_gram_stall(ntiles, &stall_tile, &stall_limit)) {
-      if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<false, false, true>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-        return fail(e);
-      k_gram_bitmap_tc<false, false, true><<<ntiles, TC_THREADS, smem, s>>>(
-          mh, ml, X, n, d, W, nt, cap, norm, adj, st, nullptr, 0, nullptr, stall_tile, stall_limit);
-    } else {
-      if ((e = cudaFuncSetAttribute(k_gram_bitmap_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem)) != cudaSuccess)
-        return fail(e);
-      k_gram_bitmap_tc<false, false><<<ntiles, TC_THREADS, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st,
-                                                               nullptr, 0, nullptr);
-    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
   }
-  count_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
-  if (band) cudaFreeAsync(band, s);
-  cudaFreeAsync(Xh, s);
-  cudaFreeAsync(Xl, s);
-  cudaFreeAsync(norm, s);
-  cudaFreeAsync(centre, s);
+  release();
   return VR_OK;
 }
 
@@ -535,43 +578,89 @@ vr_status vr_set_gram_path(int32_t mode) {
   return VR_OK;
 }
 
+vr_status vr_set_gram_split(int32_t split) {
+  if (split != 2 && split != 3) {
+    vr::set_error("gram split %d: 2 (hi, lo) or 3 (hi, mid, lo)", split);
+    return VR_ERR_ARG;
+  }
+  vr::g_gram_split = split;
+  return VR_OK;
+}
+
 }  // extern "C"
 
-extern "C" vr_status vr_gram_error_check(const float *points, int32_t n, int32_t d, vr_stream_t stream,
-                                         double *worst_ratio, double *beta_ratio) {
+// Accuracy of the float Gram tiles against the canonical FP64 values.
+extern "C" vr_status vr_gram_accuracy_check(const float *points, int32_t n, int32_t d, double maxrad, int32_t split,
+                                            vr_stream_t stream, vr_gram_accuracy *out) {
   using namespace vr;
-  if (!points || !worst_ratio || n < 2 || n > VR_MAX_POINTS || d < 1 || d > TC_K) {
-    set_error("bad argument (n in [2, 8192], 1 <= d <= 64, device float points)");
+  if (!points || !out || n < 2 || n > VR_MAX_POINTS || d < 1 || d > TC_K || !(maxrad >= 0) ||
+      (split != 0 && split != 2 && split != 3)) {
+    set_error("bad argument (n in [2, 8192], 1 <= d <= 64, maxrad >= 0, split 0/2/3, device float points)");
     return VR_ERR_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int W = (n + 31) / 32;
   uint32_t *adj = nullptr;
   DevStatus *st = nullptr;
-  unsigned int *worst = nullptr;
-  VR_CUDA(dev_malloc((void **)&adj, (size_t)n * W * 4, s));
-  VR_CUDA(dev_malloc((void **)&st, sizeof(DevStatus), s));
-  VR_CUDA(dev_malloc((void **)&worst, 4, s));
-  VR_CUDA(cudaMemsetAsync(st, 0, sizeof(DevStatus), s));
-  VR_CUDA(cudaMemsetAsync(worst, 0, 4, s));
+  GramAcc *acc = nullptr;
+  auto release = [&]() {
+    for (void *p : {(void *)adj, (void *)st, (void *)acc})
+      if (p) cudaFreeAsync(p, s);
+  };
+  cudaError_t e = dev_malloc((void **)&adj, (size_t)n * W * 4, s);
+  if (e == cudaSuccess) e = dev_malloc((void **)&st, sizeof(DevStatus), s);
+  if (e == cudaSuccess) e = dev_malloc((void **)&acc, sizeof(GramAcc), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, sizeof(GramAcc), s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    set_error("accuracy check workspace: %s", cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA;
+  }
+  // The build's cap parameters for these points.
   Cap cap{};
-  cap.keep_all = 1;
-  vr_status r = gram_bitmap_tc(points, n, d, true, cap, adj, st, s, worst);
-  unsigned int wb = 0;
+  const double r2 = maxrad * maxrad;
+  cap.keep_all = std::isinf(r2) || r2 >= 1e38 ? 1 : 0;
+  cap.r2 = r2;
+  if (!cap.keep_all) {
+    cap.r2f_dn = (float)r2;
+    if ((double)cap.r2f_dn > r2) cap.r2f_dn = std::nextafter(cap.r2f_dn, -INFINITY);
+    cap.r2f_up = (float)r2;
+    if ((double)cap.r2f_up < r2) cap.r2f_up = std::nextafter(cap.r2f_up, INFINITY);
+  }
+  vr_status r = gram_bitmap_tc(points, n, d, true, cap, adj, st, s, acc, split);
+  GramAcc h{};
   int32_t flags = 0;
   if (r == VR_OK) {
-    VR_CUDA(cudaMemcpyAsync(&wb, worst, 4, cudaMemcpyDeviceToHost, s));
-    VR_CUDA(cudaMemcpyAsync(&flags, &st->flags, 4, cudaMemcpyDeviceToHost, s));
-    VR_CUDA(cudaStreamSynchronize(s));
+    e = cudaMemcpyAsync(&h, acc, sizeof(GramAcc), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, &st->flags, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) r = cuda_status(e, "accuracy check", __FILE__, __LINE__);
   }
-  cudaFreeAsync(adj, s);
-  cudaFreeAsync(st, s);
-  cudaFreeAsync(worst, s);
+  release();
   if (r != VR_OK) return r;
   if (flags) return flags_to_status(flags);
-  float w;
-  memcpy(&w, &wb, 4);
-  *worst_ratio = w;
-  if (beta_ratio) *beta_ratio = TC_BETA;
+  float wn, wr;
+  memcpy(&wn, &h.worst_norm, 4);
+  memcpy(&wr, &h.worst_rel_d, 4);
+  out->max_norm_err = wn;
+  out->max_rel_d_err = wr;
+  out->beta = TC_BETA;
+  out->kept_pairs = (int64_t)h.kept;
+  out->band_pairs = (int64_t)h.band;
+  return VR_OK;
+}
+
+extern "C" vr_status vr_gram_error_check(const float *points, int32_t n, int32_t d, vr_stream_t stream,
+                                         double *worst_ratio, double *beta_ratio) {
+  if (!worst_ratio) {
+    vr::set_error("worst_ratio is NULL");
+    return VR_ERR_ARG;
+  }
+  vr_gram_accuracy a{};
+  VR_TRY(vr_gram_accuracy_check(points, n, d, INFINITY, 0, stream, &a));
+  *worst_ratio = a.max_norm_err;
+  if (beta_ratio) *beta_ratio = a.beta;
   return VR_OK;
 }

@@ -87,3 +87,52 @@ def test_band_list_overflow_falls_back_exactly(torch):
     finally:
         set_path(0)
     assert_same(gc, oracle.vr_build(pts, 1, 100.0), 1)
+
+
+def set_split(split):
+    vr.vr_set_gram_split(split)
+
+
+@pytest.mark.parametrize("case", ["gauss", "ragged_f", "clustered_far"])
+def test_three_way_split_matches_oracle(torch, case):
+    """The three-way float split (hi, mid, lo: six products per k-step) on the
+    forced tensor-core path gives the oracle's complex."""
+    if case == "gauss":
+        c = synth.config3(n=900)
+        pts, md, r = c.points, 2, c.maxrad
+    elif case == "ragged_f":
+        pts, md, r = synth.random_cloud(333, 29, np.float32, seed=8, lo=-3, hi=3), 2, 9.0
+    else:
+        g = synth.rng(12)
+        pts = (g.normal(size=(1, 20)) * 500 + g.normal(size=(400, 20))).astype(np.float32)
+        md, r = 2, 4.5
+    try:
+        set_path(1)
+        set_split(3)
+        gsplit = gpu_build(torch, pts, md, r)
+    finally:
+        set_split(2)
+        set_path(0)
+    assert_same(gsplit, oracle.vr_build(pts, md, r), md)
+
+
+@pytest.mark.parametrize("seed,scale,d", [(1, 1.0, 32), (2, 1000.0, 64), (4, 50.0, 3)])
+def test_both_splits_within_quarter_beta_and_three_way_tighter(torch, seed, scale, d):
+    """Both splits stay within beta/4 of the canonical FP64 value (normalised
+    by |y_i|^2 + |y_j|^2); the three-way split's relative error in d over
+    the kept pairs is below the two-way split's."""
+    g = synth.rng(900 + seed)
+    base = g.normal(size=(1, d)) * 10 * scale
+    pts = (base + g.normal(size=(600, d)) * scale * g.uniform(0.01, 1.0, size=(600, 1))).astype(np.float32)
+    dev = torch.from_numpy(pts).cuda()
+    q = pts.astype(np.float64)
+    d2 = ((q[:, None, :] - q[None, :, :]) ** 2).sum(-1)[np.triu_indices(600, 1)]
+    r = math.sqrt(float(np.quantile(d2, 0.2)))
+    a2 = vr.vr_gram_accuracy_check(dev, r, split=2)
+    a3 = vr.vr_gram_accuracy_check(dev, r, split=3)
+    for a in (a2, a3):
+        assert 0 <= a["max_norm_err"] <= a["beta"] / 4, a
+        assert a["kept_pairs"] > 0 and 0 <= a["band_pairs"] <= 600 * 599 // 2
+    assert a3["max_rel_d_err"] <= a2["max_rel_d_err"], (a2, a3)
+    # kept pairs are the pairs with canonical d^2 <= r^2: same count for both splits
+    assert a2["kept_pairs"] == a3["kept_pairs"]
