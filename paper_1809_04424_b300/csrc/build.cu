@@ -115,6 +115,11 @@ static StatusMirror *status_mirror() {
 
 // Copy the status word (and, if t_src is set, *t_src into its T field) to the
 // host mirror, then publish seq.
+static __global__ void k_keep_flags(const DevStatus *st, int32_t *late) {
+  pdl_entry();
+  if (threadIdx.x == 0) *late = __ldcg(&st->flags);
+}
+
 static __global__ void k_publish(const DevStatus *st, const int64_t *t_src, HostStatus *h, uint64_t seq) {
   pdl_entry();
   constexpr int NW = (int)(sizeof(DevStatus) / 4);
@@ -203,6 +208,8 @@ vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, ui
 // Time-sliced adjacency of the max-edge triangle enumeration: at most this
 // many bytes of snapshots (kept well inside L2), at most SNAP_MAX_S slices.
 constexpr int64_t SNAP_BUDGET = int64_t(32) << 20;
+// Below this many kept edges the lex order is taken (see force_lex).
+constexpr int64_t SNAP_MIN_E = int64_t(1) << 15;
 static int snap_slices(int n, int W, int64_t E) {
   const int64_t per = (int64_t)n * snap_stride(W) * 4;
   int64_t S = 1 + SNAP_BUDGET / std::max<int64_t>(per, 1);
@@ -502,7 +509,13 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   // per point, 229 words per row).  Otherwise lex_mode decides on the device
   // by the share of tied grades.
   const int sparse_rows = 2 * E < (int64_t)n * W ? 1 : 0;
-  const int force_lex = (maxdim >= 3 || sparse_rows) ? 1 : 0;
+  // Lex order is also certain, before the grades are known, when the keys'
+  // distance field cannot hold enough distinct values for 95 % of the edges
+  // (integer data: at most 2^kbits distinct squared distances), and it is
+  // taken for small edge counts, where the time-sliced adjacency's fixed
+  // cost exceeds the triangle sort's.
+  const bool ties_certain = !F && kbits < 62 && (E - ((int64_t)1 << kbits)) * 20 > E;
+  const int force_lex = (maxdim >= 3 || sparse_rows || ties_certain || E < SNAP_MIN_E) ? 1 : 0;
   SnapIdx sx{nullptr, nullptr, nullptr, 1, 1, snap_stride(W)};
   uint32_t *snap = nullptr;
   uint64_t *sbl = nullptr;
@@ -833,8 +846,12 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_TRY(read_status(st, sm, s));
   }
 
-  // The flags as the last kernel left them, for vr_complex_status.
-  VR_CUDA(cudaMemcpyAsync(late_flags, &st->flags, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  // The flags as the last kernel left them, for vr_complex_status (a
+  // one-warp dependent launch: a copy-engine copy would break the chain of
+  // dependent launches).
+  launch_dep(k_keep_flags, 1, 32, 0, s, (const DevStatus *)st, late_flags);
+  count_launch();
+  VR_CUDA(cudaGetLastError());
   res->late_flags = late_flags;
 
   // Hand the outputs to the result.

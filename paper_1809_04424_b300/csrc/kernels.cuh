@@ -1156,7 +1156,7 @@ static __global__ void __launch_bounds__(256) k_snap_build(const uint32_t *adj, 
 }
 
 template <bool DENSE>
-static __global__ void __launch_bounds__(256) k_tri_count(const int32_t *everts, const uint32_t *lexe, int64_t E,
+static __global__ void __launch_bounds__(256, 6) k_tri_count(const int32_t *everts, const uint32_t *lexe, int64_t E,
                                                           const uint32_t *adj, const int32_t *adjpre, int W,
                                                           const int32_t *nbr_ptr, const int32_t *nbr_ord,
                                                           const DevStatus *st, int32_t *tcnt, int force_lex,
