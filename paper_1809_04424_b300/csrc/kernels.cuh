@@ -678,6 +678,11 @@ static __global__ void __launch_bounds__(256) k_lex_edges(int n, int W, const ui
 // Key = RN32(FP64 value) bits, i, j.  E comes from the status word (the
 // launch may precede the host's read of it).
 constexpr int EKF_WARPS = 4;
+// EKF_HW_NUM chunks in EKF_HW_MOD are evaluated with the hardware FP64 pipe
+// (the same canonical sequence: IEEE 754 makes every step's result unique),
+// the others by the integer emulation: whole warps take one or the other, so
+// the two pipes work at once.
+constexpr int EKF_HW_MOD = 2, EKF_HW_NUM = 1;
 static __global__ void __launch_bounds__(EKF_WARPS * 32) k_edge_keys_f32(const float *X, int d, const uint32_t *lexe,
                                                                          uint64_t *keys, double *d64_lex,
                                                                          DevStatus *st) {
@@ -693,6 +698,8 @@ static __global__ void __launch_bounds__(EKF_WARPS * 32) k_edge_keys_f32(const f
     const uint32_t ab = lexe[has ? t : c * 32];  // idle lanes repeat the chunk's first pair
     const int i = (int)(ab >> ID_BITS), j = (int)(ab & ID_MASK);
     SoftAcc acc{0, 0, true};
+    const bool hw = (c % EKF_HW_MOD) < EKF_HW_NUM;  // warp-uniform
+    double acc64 = 0.0;
     float a = 0.f;
     for (int k0 = 0; k0 < d; k0 += 32) {
       const int kn = min(32, d - k0);
@@ -712,16 +719,26 @@ static __global__ void __launch_bounds__(EKF_WARPS * 32) k_edge_keys_f32(const f
 #pragma unroll
       for (int rr = 0; rr < 32; ++rr) ti[wid][rr][l] = v[rr];
       __syncwarp();
-      for (int k = 0; k < kn; ++k) {
-        const float xv = ti[wid][l][k], yv = tj[wid][l][k];
-        const float tt = __fsub_rn(xv, yv);
-        a = __fmaf_rn(tt, tt, a);
-        if (acc.ok) soft_step(acc, xv, yv);
+      if (hw) {
+        for (int k = 0; k < kn; ++k) {
+          const float xv = ti[wid][l][k], yv = tj[wid][l][k];
+          const float tt = __fsub_rn(xv, yv);
+          a = __fmaf_rn(tt, tt, a);
+          const double t64 = __dsub_rn((double)xv, (double)yv);
+          acc64 = __dadd_rn(acc64, __dmul_rn(t64, t64));
+        }
+      } else {
+        for (int k = 0; k < kn; ++k) {
+          const float xv = ti[wid][l][k], yv = tj[wid][l][k];
+          const float tt = __fsub_rn(xv, yv);
+          a = __fmaf_rn(tt, tt, a);
+          if (acc.ok) soft_step(acc, xv, yv);
+        }
       }
       __syncwarp();
     }
     if (has) {
-      const double f = acc.ok ? soft_value(acc) : d2_f64(X + (int64_t)i * d, X + (int64_t)j * d, d);
+      const double f = hw ? acc64 : acc.ok ? soft_value(acc) : d2_f64(X + (int64_t)i * d, X + (int64_t)j * d, d);
       d64_lex[t] = f;
       keys[t] = ((uint64_t)__float_as_uint(__double2float_rn(f)) << KEY_SHIFT) | ((uint64_t)i << ID_BITS) |
                 (uint64_t)j;
