@@ -1545,27 +1545,29 @@ static __global__ void __launch_bounds__(256) k_tri_final(const uint64_t *tkeys,
   __shared__ int4 sv[8][96], sr[8][96];  // per warp: 128 triangles x 3 ints
   const int wid = threadIdx.x >> 5, l = lane_id();
   int32_t *svi = (int32_t *)sv[wid], *sri = (int32_t *)sr[wid];
+  // Lane l takes triangles l, l + 32, l + 64, l + 96 of a chunk of 128
+  // (coalesced 8-byte key loads; staging at stride 3 words, no bank
+  // conflicts).
   const int64_t nch = T / 128;
   for (int64_t ch = blockIdx.x * 8 + wid; ch < nch; ch += (int64_t)gridDim.x * 8) {
     const int64_t base = ch * 128;
-    const ulonglong2 kA = ((const ulonglong2 *)(tkeys + base))[l], kB = ((const ulonglong2 *)(tkeys + base))[32 + l];
-    int32_t v[12], r[12], g[4];
-    tri_final_one(kA.x, ex, v, r, g[0], DENSE);
-    tri_final_one(kA.y, ex, v + 3, r + 3, g[1], DENSE);
-    tri_final_one(kB.x, ex, v + 6, r + 6, g[2], DENSE);
-    tri_final_one(kB.y, ex, v + 9, r + 9, g[3], DENSE);
+    uint64_t kk[4];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      svi[6 * l + k] = v[k];
-      sri[6 * l + k] = r[k];
-      svi[192 + 6 * l + k] = v[6 + k];
-      sri[192 + 6 * l + k] = r[6 + k];
+    for (int u = 0; u < 4; ++u) kk[u] = tkeys[base + 32 * u + l];
+    int32_t v[12], r[12], g[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) tri_final_one(kk[u], ex, v + 3 * u, r + 3 * u, g[u], DENSE);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = 32 * u + l;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        svi[3 * t + k] = v[3 * u + k];
+        sri[3 * t + k] = r[3 * u + k];
+      }
+      tgrade[base + t] = g[u];
+      tcolptr[base + t] = 3 * (base + t);
     }
-    ((int2 *)(tgrade + base))[l] = make_int2(g[0], g[1]);
-    ((int2 *)(tgrade + base + 64))[l] = make_int2(g[2], g[3]);
-    const long long c0 = 3 * (base + 2 * l), c1 = c0 + 192;
-    ((longlong2 *)(tcolptr + base))[l] = make_longlong2(c0, c0 + 3);
-    ((longlong2 *)(tcolptr + base + 64))[l] = make_longlong2(c1, c1 + 3);
     __syncwarp();
     int4 *gv = (int4 *)(tverts + 3 * base), *gr = (int4 *)(trow + 3 * base);
 #pragma unroll
@@ -1621,36 +1623,38 @@ static __global__ void __launch_bounds__(256) k_tri_final_me(const uint64_t *tke
   // Keys are read once and the outputs written once: streaming hints keep
   // them from evicting the order table the lookups need from L2.  The next
   // chunk's keys are loaded while this one is processed.
+  // Lane l takes triangles l, l + 32, l + 64, l + 96 of a chunk of 128:
+  // coalesced 8-byte key loads, and staging at stride 3 words (no bank
+  // conflicts).
   int64_t ch = blockIdx.x * 8 + wid;
-  ulonglong2 nA = make_ulonglong2(0, 0), nB = nA;
+  uint64_t nk[4] = {0, 0, 0, 0};
   if (ch < nch) {
-    nA = __ldcs((const ulonglong2 *)(tkeys + ch * 128) + l);
-    nB = __ldcs((const ulonglong2 *)(tkeys + ch * 128) + 32 + l);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) nk[u] = __ldcs(tkeys + ch * 128 + 32 * u + l);
   }
   for (; ch < nch; ch += cstride) {
     const int64_t base = ch * 128;
-    const ulonglong2 kA = nA, kB = nB;
+    uint64_t kk[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) kk[u] = nk[u];
     if (ch + cstride < nch) {
-      nA = __ldcs((const ulonglong2 *)(tkeys + (ch + cstride) * 128) + l);
-      nB = __ldcs((const ulonglong2 *)(tkeys + (ch + cstride) * 128) + 32 + l);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) nk[u] = __ldcs(tkeys + (ch + cstride) * 128 + 32 * u + l);
     }
     int32_t v[12], r[12], g[4];
-    tri_final_me_one(kA.x, everts, egrade, ex, v, r, g[0], DENSE);
-    tri_final_me_one(kA.y, everts, egrade, ex, v + 3, r + 3, g[1], DENSE);
-    tri_final_me_one(kB.x, everts, egrade, ex, v + 6, r + 6, g[2], DENSE);
-    tri_final_me_one(kB.y, everts, egrade, ex, v + 9, r + 9, g[3], DENSE);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      svi[6 * l + k] = v[k];
-      sri[6 * l + k] = r[k];
-      svi[192 + 6 * l + k] = v[6 + k];
-      sri[192 + 6 * l + k] = r[6 + k];
+    for (int u = 0; u < 4; ++u) tri_final_me_one(kk[u], everts, egrade, ex, v + 3 * u, r + 3 * u, g[u], DENSE);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = 32 * u + l;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        svi[3 * t + k] = v[3 * u + k];
+        sri[3 * t + k] = r[3 * u + k];
+      }
+      __stcs(tgrade + base + t, g[u]);
+      __stcs((long long *)tcolptr + base + t, (long long)(3 * (base + t)));
     }
-    __stcs((int2 *)(tgrade + base) + l, make_int2(g[0], g[1]));
-    __stcs((int2 *)(tgrade + base + 64) + l, make_int2(g[2], g[3]));
-    const long long c0 = 3 * (base + 2 * l), c1 = c0 + 192;
-    __stcs((longlong2 *)(tcolptr + base) + l, make_longlong2(c0, c0 + 3));
-    __stcs((longlong2 *)(tcolptr + base + 64) + l, make_longlong2(c1, c1 + 3));
     __syncwarp();
     int4 *gv = (int4 *)(tverts + 3 * base), *gr = (int4 *)(trow + 3 * base);
 #pragma unroll
