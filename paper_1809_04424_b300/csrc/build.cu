@@ -595,8 +595,9 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       // Time-sliced adjacency for the max-edge enumeration (returns at once
       // when the device finds lex mode).
       prof.begin("tri_snap");
-      launch_dep(k_snap_build, grid_for(n, 8, 32), 256, 0, s, adj, adjpre, W, n, nbr_ptr, nbr_ord, st, force_lex,
-                 sx.S, sx.B, snap, sbl, sboff);
+      const int snap_threads = 32 * ((sx.Wp + 31) / 32);  // a warp per 32-word round of a row
+      launch_dep(k_snap_build, (unsigned)std::min<int64_t>(n, (int64_t)num_sms() * 32), snap_threads, 0, s, adj,
+                 adjpre, W, n, nbr_ptr, nbr_ord, st, force_lex, sx.S, sx.B, snap, sbl, sboff);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();

@@ -1117,10 +1117,12 @@ struct SnapIdx {
 };
 __host__ __device__ __forceinline__ int snap_stride(int W) { return (W + 3) & ~3; }
 
-// One warp per vertex v: bucket v's neighbour entries by slice (counts, then
-// a scatter; the order inside a bucket is immaterial: buckets are filtered,
-// not walked in order) and write v's snapshot rows.  Runs in max-edge mode
-// only (decided on the device, like the count kernel).
+// One CTA per vertex v, one warp per 32-word round of v's row (blockDim =
+// 32 * ceil(Wp / 32) <= 256): the CTA buckets v's neighbour entries by slice
+// (a shared histogram, one prefix, shared cursors; the order inside a bucket
+// is immaterial: buckets are filtered, not walked in order) and each warp
+// writes its round's words of v's snapshot rows.  Runs in max-edge mode only
+// (decided on the device, like the count kernel).
 static __global__ void __launch_bounds__(256) k_snap_build(const uint32_t *adj, const int32_t *adjpre, int W, int n,
                                                            const int32_t *nbr_ptr, const int32_t *nbr_ord,
                                                            const DevStatus *st, int force_lex, int S, int64_t B,
@@ -1128,47 +1130,47 @@ static __global__ void __launch_bounds__(256) k_snap_build(const uint32_t *adj, 
   pdl_entry();
   if (build_failed(st)) return;
   if (lex_mode(st->E, st->ngrades, force_lex)) return;
-  __shared__ int32_t cur[8][SNAP_MAX_S + 1];
-  __shared__ uint32_t sw[8][SNAP_MAX_S - 1][32];  // one round: lane l's word in each snapshot
+  __shared__ int32_t cur[SNAP_MAX_S + 1];
+  __shared__ uint32_t sw[8][SNAP_MAX_S - 1][32];  // per warp: lane l's word in each snapshot
   const int l = lane_id(), wid = threadIdx.x >> 5;
-  const int64_t nwarps = (int64_t)gridDim.x * 8;
-  const int64_t nWp = (int64_t)n * snap_stride(W);
-  for (int64_t v = blockIdx.x * 8 + wid; v < n; v += nwarps) {
+  const int Wp = snap_stride(W);
+  const int64_t nWp = (int64_t)n * Wp;
+  const uint32_t Bu = (uint32_t)B;  // B <= E < 2^31: 32-bit divisions
+  for (int64_t v = blockIdx.x; v < n; v += gridDim.x) {
     const int32_t ptr = nbr_ptr[v], deg = nbr_ptr[v + 1] - ptr;
-    for (int b = l; b <= S; b += 32) cur[wid][b] = 0;
-    __syncwarp();
-    for (int k = l; k < deg; k += 32) atomicAdd(&cur[wid][(int)(nbr_ord[ptr + k] / B)], 1);
-    __syncwarp();
-    if (l == 0) {
+    for (int b = threadIdx.x; b <= S; b += blockDim.x) cur[b] = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < deg; k += blockDim.x) atomicAdd(&cur[(uint32_t)nbr_ord[ptr + k] / Bu], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
       int32_t run = 0;
       for (int b = 0; b <= S; ++b) {
         boff[v * (S + 1) + b] = run;
-        const int32_t c = cur[wid][b];
-        cur[wid][b] = run;
+        const int32_t c = cur[b];
+        cur[b] = run;
         run += c;
       }
     }
-    __syncwarp();
+    __syncthreads();
     const uint32_t *row = adj + v * W;
     const int32_t *pre = adjpre + v * W;
-    const int Wp = snap_stride(W);
-    for (int w0 = 0; w0 < Wp; w0 += 32) {
-      const int w = w0 + l;
+    const int w = wid * 32 + l;  // this lane's word
+    if (wid * 32 < Wp) {
       uint32_t m = w < W ? row[w] : 0u;
       int32_t k = w < W ? pre[w] : 0;  // entry index of the word's lowest set bit
       for (int b = 0; b < S - 1; ++b) sw[wid][b][l] = 0u;
       for (; m; m &= m - 1, ++k) {
         const int bit = __ffs(m) - 1;
         const int32_t o = nbr_ord[ptr + k];
-        const int bb = (int)(o / B);
-        const int32_t slot = atomicAdd(&cur[wid][bb], 1);
+        const int bb = (int)((uint32_t)o / Bu);
+        const int32_t slot = atomicAdd(&cur[bb], 1);
         bl[ptr + slot] = ((uint64_t)(uint32_t)o << 32) | (uint32_t)(w * 32 + bit);
         for (int b = bb + 1; b < S; ++b) sw[wid][b - 1][l] |= 1u << bit;
       }
       if (w < Wp)
         for (int b = 1; b < S; ++b) snap[(b - 1) * nWp + v * Wp + w] = sw[wid][b - 1][l];
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
