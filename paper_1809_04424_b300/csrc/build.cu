@@ -451,7 +451,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     return VR_ERR_RANGE;
   }
 
-  int32_t *gex, *nbr_ord, *gstart;
+  int32_t *nbr_ord, *gstart;
   int32_t *everts, *egrade, *erow;
   int64_t *ecol, *bs_e;
   double *gval, *d64 = nullptr;
@@ -466,7 +466,6 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     if (want_elp) VR_TRY(ws.alloc(&elp, (int64_t)n * n));
   }
   VR_TRY(ws.alloc(&rs.tkeys, E));
-  VR_TRY(ws.alloc(&gex, E + 1));
   VR_TRY(ws.alloc(&bs_e, scan_tmp_slots(E)));
   VR_TRY(ws.alloc(&nbr_ord, 2 * E));
   int32_t *eidx = nullptr, *egd = nullptr;  // dense (i, j) -> order index / grade tables for small clouds
@@ -482,14 +481,12 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(out.alloc(&gval, E + 1));
   int32_t *late_flags = nullptr;
   VR_TRY(out.alloc(&late_flags, 1));
-  int32_t *split = nullptr, *gbeg = nullptr, *midq = nullptr, *bigq = nullptr;
+  int32_t *midq = nullptr, *bigq = nullptr;
   uint64_t *k1 = nullptr, *k2 = nullptr, *gk = nullptr;
   uint32_t *v1 = nullptr, *v2 = nullptr;
   double *gd = nullptr;
   if (F && E > 0) {
     VR_TRY(ws.alloc(&d64, E));
-    VR_TRY(ws.alloc(&split, E));
-    VR_TRY(ws.alloc(&gbeg, E + 1));
     VR_TRY(ws.alloc(&midq, E));
     VR_TRY(ws.alloc(&bigq, E));
     VR_TRY(ws.alloc(&k1, E));
@@ -560,20 +557,13 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
 
     if (F) {
       prof.begin("fp64_repair");
-      count_launch(6);
-      int tkf = prof.begin("fp64_values");
-      launch_dep(k_f64_gather, ge, 256, 0, s, keys, E, d64_lex, adj, adjpre, W, deg, up, lex_ptr, d64, split, st);
-      prof.end(tkf);
-      VR_TRY((scan_exclusive<int32_t, int32_t>(split, gex, E, bs_e, s)));
-      launch_dep(k_group_starts, ge, 256, 0, s, split, gex, E, gbeg, st);
-      // Group count is gex[E]; launch over the E upper bound, threads skip.
-      int tkr = prof.begin("fp64_regroup");
-      launch_dep(k_repair_small, ge, 256, 0, s, gbeg, gex + E, keys, d64, midq, bigq, st);
+      count_launch(3);
+      const F64Src fsrc{d64_lex, adj, adjpre, W, deg, up, lex_ptr};
+      launch_dep(k_f64_repair_small, ge, 256, 0, s, keys, E, fsrc, d64, midq, bigq, st);
       VR_CUDA(cudaGetLastError());
-      launch_dep(k_repair_mid, (unsigned)num_sms() * 2, 256, 0, s, gbeg, midq, st, keys, d64);
-      launch_dep(k_repair_big, 1, RS_THREADS, 0, s, gbeg, bigq, st, keys, d64, k1, v1, k2, v2, gk, gd);
+      launch_dep(k_repair_mid, (unsigned)num_sms() * 2, 256, 0, s, midq, fsrc, st, keys, d64);
+      launch_dep(k_repair_big, 1, RS_THREADS, 0, s, bigq, fsrc, st, keys, d64, k1, v1, k2, v2, gk, gd);
       VR_CUDA(cudaGetLastError());
-      prof.end(tkr);
       prof.end();
     }
     prof.begin("edge_grades");

@@ -767,33 +767,15 @@ __device__ __forceinline__ int key_j(uint64_t k) { return (int)(k & ID_MASK); }
 // intervals overlap), re-sorted by (FP64 value, i, j).  Across a group
 // boundary the FP64 values are strictly ordered already.
 // After the sort: each edge's canonical value (computed in lexicographic
-// order by k_edge_keys_f32) is gathered through its lex position, and a
-// repair group starts wherever the fp32 key bits change.  Keys are RN32 of
-// the canonical value, which is monotone, so different keys are already in
-// FP64 order; only runs of equal keys need re-sorting by (FP64, i, j).
-static __global__ void k_f64_gather(const uint64_t *keys, int64_t E, const double *d64_lex, const uint32_t *adj,
-                                    const int32_t *adjpre, int W, const int32_t *deg, const int32_t *up,
-                                    const int64_t *lex_ptr, double *d64, int32_t *split,
-    const DevStatus *st) {
-  pdl_entry();
-  if (build_failed(st)) return;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t key = keys[k];
-    const int i = (int)((key >> ID_BITS) & ID_MASK), j = (int)(key & ID_MASK);
-    const int64_t lp = lex_ptr[i] + bit_rank(adj + (int64_t)i * W, adjpre + (int64_t)i * W, j) - (deg[i] - up[i]);
-    d64[k] = d64_lex[lp];
-    split[k] = (k == 0 || (key >> KEY_SHIFT) != (keys[k - 1] >> KEY_SHIFT)) ? 1 : 0;
-  }
-}
-
-// Group starts from the exclusive scan of split: gbeg[gid] = k.
-static __global__ void k_group_starts(const int32_t *split, const int32_t *gex, int64_t E, int32_t *gbeg,
-    const DevStatus *st) {
-  pdl_entry();
-  if (build_failed(st)) return;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x)
-    if (split[k]) gbeg[gex[k]] = (int32_t)k;
-  if (blockIdx.x == 0 && threadIdx.x == 0) gbeg[gex[E]] = (int32_t)E;
+// order by k_edge_keys_f32) is fetched through its lex position.  Keys are
+// RN32 of the canonical value, which is monotone, so different keys are
+// already in FP64 order; only runs of equal keys need re-sorting by
+// (FP64, i, j).
+__device__ __forceinline__ double f64_of(uint64_t key, const double *d64_lex, const uint32_t *adj,
+                                         const int32_t *adjpre, int W, const int32_t *deg, const int32_t *up,
+                                         const int64_t *lex_ptr) {
+  const int i = key_i(key), j = key_j(key);
+  return d64_lex[lex_ptr[i] + bit_rank(adj + (int64_t)i * W, adjpre + (int64_t)i * W, j) - (deg[i] - up[i])];
 }
 
 __device__ __forceinline__ bool f64_less(double da, uint64_t ka, double db, uint64_t kb) {
@@ -803,34 +785,68 @@ __device__ __forceinline__ bool f64_less(double da, uint64_t ka, double db, uint
 constexpr int REPAIR_SMALL = 32;
 constexpr int REPAIR_MID = 2048;
 
-// Thread per group: insertion sort of groups up to REPAIR_SMALL edges; larger
-// groups are queued for the CTA kernels.
-static __global__ void k_repair_small(const int32_t *gbeg, const int32_t *ngroups_ptr, uint64_t *keys, double *d64,
-                               int32_t *midq, int32_t *bigq, DevStatus *st) {
+struct F64Src {
+  const double *d64_lex;
+  const uint32_t *adj;
+  const int32_t *adjpre;
+  int W;
+  const int32_t *deg, *up;
+  const int64_t *lex_ptr;
+  __device__ __forceinline__ double of(uint64_t key) const { return f64_of(key, d64_lex, adj, adjpre, W, deg, up, lex_ptr); }
+};
+
+// Thread per sorted position k.  A position whose fp32 key differs from both
+// neighbours stands alone and fetches its FP64 value.  The first position of
+// a run of equal keys finds the run's end by a galloping search; a run of up
+// to REPAIR_SMALL edges is fetched and insertion-sorted by that thread, a
+// longer one is queued as a (begin, size) pair for the CTA kernels, which
+// fetch its values themselves.  Other positions inside runs do nothing.
+static __global__ void k_f64_repair_small(uint64_t *keys, int64_t E, F64Src src, double *d64, int32_t *midq,
+                                          int32_t *bigq, DevStatus *st) {
   pdl_entry();
   if (build_failed(st)) return;
-  const int64_t ngroups = *ngroups_ptr;
   int64_t nt = 0;
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = gbeg[g], e = gbeg[g + 1], s = e - b;
-    if (s < 2) continue;
-    nt += s;
-    if (s > REPAIR_MID) {
-      int q = (int)atomicAdd((unsigned long long *)&st->big_grp_count, 1ull);
-      bigq[q] = (int32_t)g;
-      atomicMax((unsigned long long *)&st->big_grp_max, (unsigned long long)s);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < E; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = keys[k];
+    const uint64_t top = key >> KEY_SHIFT;
+    if (k > 0 && (keys[k - 1] >> KEY_SHIFT) == top) continue;
+    if (k + 1 == E || (keys[k + 1] >> KEY_SHIFT) != top) {
+      d64[k] = src.of(key);
       continue;
     }
-    if (s > REPAIR_SMALL) {
-      int q = atomicAdd(&st->mid_grp_count, 1);
-      midq[q] = (int32_t)g;
+    // keys[lo] is in the run; hi is past it (or E).
+    int64_t lo = k + 1, step = 1;
+    while (lo + step < E && (keys[lo + step] >> KEY_SHIFT) == top) {
+      lo += step;
+      step <<= 1;
+    }
+    int64_t hi = lo + step < E ? lo + step : E;
+    while (hi - lo > 1) {
+      const int64_t mid = lo + ((hi - lo) >> 1);
+      if ((keys[mid] >> KEY_SHIFT) == top) lo = mid;
+      else hi = mid;
+    }
+    const int64_t sz = hi - k;
+    nt += sz;
+    if (sz > REPAIR_MID) {
+      const int q = (int)atomicAdd((unsigned long long *)&st->big_grp_count, 1ull);
+      bigq[2 * q] = (int32_t)k;
+      bigq[2 * q + 1] = (int32_t)sz;
+      atomicMax((unsigned long long *)&st->big_grp_max, (unsigned long long)sz);
       continue;
     }
-    for (int64_t x = b + 1; x < e; ++x) {
-      uint64_t kx = keys[x];
-      double dx = d64[x];
+    if (sz > REPAIR_SMALL) {
+      const int q = atomicAdd(&st->mid_grp_count, 1);
+      midq[2 * q] = (int32_t)k;
+      midq[2 * q + 1] = (int32_t)sz;
+      continue;
+    }
+    d64[k] = src.of(key);
+    for (int64_t x = k + 1; x < hi; ++x) {
+      const uint64_t kx = keys[x];
+      const double dx = src.of(kx);
       int64_t y = x - 1;
-      while (y >= b && f64_less(dx, kx, d64[y], keys[y])) {
+      while (y >= k && f64_less(dx, kx, d64[y], keys[y])) {
         keys[y + 1] = keys[y];
         d64[y + 1] = d64[y];
         --y;
@@ -844,7 +860,7 @@ static __global__ void k_repair_small(const int32_t *gbeg, const int32_t *ngroup
 
 // CTA per queued mid-size group: bitonic sort in shared memory on the pair
 // (FP64 bits, i<<13|j) packed as two words; val = position in the group.
-static __global__ void __launch_bounds__(256) k_repair_mid(const int32_t *gbeg, const int32_t *midq, const DevStatus *st,
+static __global__ void __launch_bounds__(256) k_repair_mid(const int32_t *midq, F64Src src, const DevStatus *st,
                                                     uint64_t *keys, double *d64) {
   pdl_entry();
   if (build_failed(st)) return;
@@ -853,15 +869,17 @@ static __global__ void __launch_bounds__(256) k_repair_mid(const int32_t *gbeg, 
   __shared__ uint32_t val[REPAIR_MID];
   const int nq = st->mid_grp_count;
   for (int q = blockIdx.x; q < nq; q += gridDim.x) {
-    const int g = midq[q];
-    const int64_t b = gbeg[g];
-    const int s = (int)(gbeg[g + 1] - b);
+    const int64_t b = midq[2 * q];
+    const int s = midq[2 * q + 1];
     int cap = 1;
     while (cap < s) cap <<= 1;
     for (int t = threadIdx.x; t < cap; t += blockDim.x) {
       if (t < s) {
-        hi[t] = (uint64_t)__double_as_longlong(d64[b + t]);
-        lo[t] = (uint32_t)(keys[b + t] & ((1ull << KEY_SHIFT) - 1));
+        const uint64_t kt = keys[b + t];
+        const double dt = src.of(kt);
+        d64[b + t] = dt;
+        hi[t] = (uint64_t)__double_as_longlong(dt);
+        lo[t] = (uint32_t)(kt & ((1ull << KEY_SHIFT) - 1));
       } else {
         hi[t] = ~0ull;
         lo[t] = ~0u;
@@ -905,7 +923,7 @@ static __global__ void __launch_bounds__(256) k_repair_mid(const int32_t *gbeg, 
 
 // One CTA for the queued large groups (rare: massive near-ties): stable LSD
 // sort by (i<<13|j), then by the FP64 bits, through global temporaries.
-static __global__ void __launch_bounds__(RS_THREADS) k_repair_big(const int32_t *gbeg, const int32_t *bigq,
+static __global__ void __launch_bounds__(RS_THREADS) k_repair_big(const int32_t *bigq, F64Src src,
                                                            const DevStatus *st, uint64_t *keys, double *d64,
                                                            uint64_t *k1, uint32_t *v1, uint64_t *k2, uint32_t *v2,
                                                            uint64_t *gk, double *gd) {
@@ -913,11 +931,12 @@ static __global__ void __launch_bounds__(RS_THREADS) k_repair_big(const int32_t 
   if (build_failed(st)) return;
   const int nq = (int)st->big_grp_count;
   for (int q = 0; q < nq; ++q) {
-    const int g = bigq[q];
-    const int64_t b = gbeg[g];
-    const int64_t s = gbeg[g + 1] - b;
+    const int64_t b = bigq[2 * q];
+    const int64_t s = bigq[2 * q + 1];
     for (int64_t t = threadIdx.x; t < s; t += blockDim.x) {
-      k1[t] = keys[b + t] & ((1ull << KEY_SHIFT) - 1);
+      const uint64_t kt = keys[b + t];
+      d64[b + t] = src.of(kt);
+      k1[t] = kt & ((1ull << KEY_SHIFT) - 1);
       v1[t] = (uint32_t)t;
     }
     __syncthreads();
