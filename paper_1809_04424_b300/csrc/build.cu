@@ -727,12 +727,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       prof.end();
       prof.begin("tri_final");
       const EdgeIndex exm{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
-      if (eidx)
-        launch_dep(k_tri_final_me<true>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, everts, egrade, exm, tverts,
-                   tgrade, tcol, trow, st);
-      else
-        launch_dep(k_tri_final_me<false>, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, everts, egrade, exm,
-                   tverts, tgrade, tcol, trow, st);
+      launch_dep(k_tri_final_me, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, everts, egrade, exm, tverts, tgrade,
+                 tcol, trow, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();

@@ -1611,18 +1611,22 @@ static __global__ void __launch_bounds__(256) k_tri_final(const uint64_t *tkeys,
 
 // Final write of max-edge keys (e << 32) | z, already in (grade, lex) order
 // up to tie groups: the edge's endpoints from the edge list, the two other
-// faces' order indices from the dense table (or the neighbour CSR).  Same
-// store pattern as k_tri_final (128 triangles per warp, vertices and rows
-// staged in shared memory for 16-byte stores).
+// faces' order indices from the neighbour CSR rows of x and of y (never the
+// dense table).  Consecutive triangles mostly share their edge (x, y) and
+// their z ascend, so a warp's 32 lookups fall in x's and y's compact rows (a
+// few hundred bytes each: adjacency word, its prefix, the order entry) and
+// the L1 sends a few line requests to L2 where the dense table's row would
+// cost a 32-byte sector per lookup.  Same store pattern as k_tri_final (128
+// triangles per warp, vertices and rows staged in shared memory for 16-byte
+// stores).
 __device__ __forceinline__ void tri_final_me_one(uint64_t k, const int32_t *everts, const int32_t *egrade,
-                                                 const EdgeIndex &ex, int32_t *v, int32_t *r, int32_t &g,
-                                                 bool dense) {
+                                                 const EdgeIndex &ex, int32_t *v, int32_t *r, int32_t &g) {
   const int32_t e = (int32_t)(k >> 32);
   const int z = (int)(k & 0xffffu);
   const int2 xy = ((const int2 *)everts)[e];
   const int x = xy.x, y = xy.y;
-  const int32_t oxz = dense ? ex.ord<true>(min(x, z), max(x, z)) : ex.ord<false>(min(x, z), max(x, z));
-  const int32_t oyz = dense ? ex.ord<true>(min(y, z), max(y, z)) : ex.ord<false>(min(y, z), max(y, z));
+  const int32_t oxz = ex.ord<false>(x, z);
+  const int32_t oyz = ex.ord<false>(y, z);
   if (z < x) { v[0] = z; v[1] = x; v[2] = y; }
   else if (z < y) { v[0] = x; v[1] = z; v[2] = y; }
   else { v[0] = x; v[1] = y; v[2] = z; }
@@ -1630,7 +1634,6 @@ __device__ __forceinline__ void tri_final_me_one(uint64_t k, const int32_t *ever
   g = egrade[e];
 }
 
-template <bool DENSE>
 static __global__ void __launch_bounds__(256) k_tri_final_me(const uint64_t *tkeys, int64_t T, const int32_t *everts,
                                                              const int32_t *egrade, EdgeIndex ex, int32_t *tverts,
                                                              int32_t *tgrade, int64_t *tcolptr, int32_t *trow,
@@ -1664,7 +1667,7 @@ static __global__ void __launch_bounds__(256) k_tri_final_me(const uint64_t *tke
     }
     int32_t v[12], r[12], g[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) tri_final_me_one(kk[u], everts, egrade, ex, v + 3 * u, r + 3 * u, g[u], DENSE);
+    for (int u = 0; u < 4; ++u) tri_final_me_one(kk[u], everts, egrade, ex, v + 3 * u, r + 3 * u, g[u]);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int t = 32 * u + l;
@@ -1688,7 +1691,7 @@ static __global__ void __launch_bounds__(256) k_tri_final_me(const uint64_t *tke
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = nch * 128 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T; p += stride) {
     int32_t v[3], r[3], g;
-    tri_final_me_one(tkeys[p], everts, egrade, ex, v, r, g, DENSE);
+    tri_final_me_one(tkeys[p], everts, egrade, ex, v, r, g);
     tverts[3 * p] = v[0]; tverts[3 * p + 1] = v[1]; tverts[3 * p + 2] = v[2];
     trow[3 * p] = r[0]; trow[3 * p + 1] = r[1]; trow[3 * p + 2] = r[2];
     tgrade[p] = g;
