@@ -1293,7 +1293,7 @@ static __global__ void __launch_bounds__(256, 6) k_tri_count(const int32_t *ever
     if (e < E) {
       const int2 xy = ((const int2 *)everts)[e];
       const int x = xy.x, y = xy.y;
-      const int b = (int)(e / sx.B);
+      const int b = (int)((uint32_t)e / (uint32_t)sx.B);  // e < E < 2^31
       const uint32_t *rx = b > 0 ? sx.snap + ((int64_t)(b - 1) * ex.n + x) * sx.Wp : nullptr;
       const uint32_t *ry = b > 0 ? sx.snap + ((int64_t)(b - 1) * ex.n + y) * sx.Wp : nullptr;
       if (b > 0) {
@@ -1362,7 +1362,7 @@ static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts
       const int2 xy = ((const int2 *)everts)[e];
       x = xy.x;
       y = xy.y;
-      b = (int)(e / sx.B);
+      b = (int)((uint32_t)e / (uint32_t)sx.B);  // e < E < 2^31
     }
     // This lane's words [w0, w0 + K) of both rows (zero before the first
     // snapshot and past Wp), and its delta words cleared.
@@ -1421,15 +1421,19 @@ static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts
       if (s16 >= d) inc += v;
     }
     if (live && c) {
-      int64_t p = toff[e] + inc - c;
-      const uint64_t ek = (uint64_t)e << 32;
+      const int64_t p = toff[e] + inc - c;
+      if (p + c <= T) {
+        // Key (e << 32) | z stored as its two 32-bit halves.
+        uint2 *out = (uint2 *)(tkeys + p);
+        const uint32_t eh = (uint32_t)e;
 #pragma unroll
-      for (int k = 0; k < MEG_KMAX; ++k) {
-        if (k >= K) break;
-        for (uint32_t mm = wx[k]; mm; mm &= mm - 1, ++p) {
-          if (p < T) __stcs(tkeys + p, ek | (uint32_t)((w0 + k) * 32 + __ffs(mm) - 1));
-          else raise_flag(st, F_INTERNAL);  // never write past the key array
+        for (int k = 0; k < MEG_KMAX; ++k) {
+          if (k >= K) break;
+          const uint32_t zb = (uint32_t)(w0 + k) * 32u - 1u;
+          for (uint32_t mm = wx[k]; mm; mm &= mm - 1) __stcs(out++, make_uint2(zb + __ffs(mm), eh));
         }
+      } else {
+        raise_flag(st, F_INTERNAL);  // never write past the key array
       }
     }
     __syncwarp();
