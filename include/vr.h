@@ -310,6 +310,14 @@ VR_API vr_status vr_set_barcode_dense_min(int64_t min_entries);
  * way. */
 VR_API vr_status vr_set_gram_path(int32_t mode);
 
+/* Max-edge triangle keys (the per-triangle word the generator writes in
+ * output order and the final write reads; no counterpart in the paper):
+ * 0 = automatic, (e << zbits) | z in 32 bits whenever the kept-edge count
+ * fits the 32 - bitlen(n - 1) bits left beside the vertex, else
+ * (e << 32) | z; 8 = always the 64-bit form.  Process-wide; results are
+ * identical either way.  VR_ERR_ARG for any other value. */
+VR_API vr_status vr_set_tri_key_width(int32_t bytes);
+
 /* Float split of the tensor-core distance tiles (no counterpart in the
  * paper): 2 = two-way, y = hi + lo (bf16 each; products hi.hi, hi.lo,
  * lo.hi; the default), 3 = three-way, y = hi + mid + lo (six products).

@@ -302,6 +302,15 @@ def vr_set_gram_split(split: int) -> None:
     _check(L.vr_set_gram_split(int(split)))
 
 
+def vr_set_tri_key_width(nbytes: int) -> None:
+    """0: automatic max-edge triangle keys (32-bit when the edge indices
+    fit), 8: always 64-bit."""
+    L = lib()
+    L.vr_set_tri_key_width.argtypes = [ctypes.c_int32]
+    L.vr_set_tri_key_width.restype = ctypes.c_int
+    _check(L.vr_set_tri_key_width(int(nbytes)))
+
+
 def vr_complex_dim(handle, k: int) -> DimView:
     v = DimView()
     _check(lib().vr_complex_dim(ctypes.c_void_p(handle), k, ctypes.byref(v)))

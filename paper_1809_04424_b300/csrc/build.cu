@@ -227,6 +227,10 @@ constexpr int64_t TET_PRE_MAX_BYTES = int64_t(1) << 28;
 // (sqrt 2 / 3) E^(3/2): at most 22M keys).
 constexpr int64_t EARLY_TRI_MAX_E = int64_t(1) << 17;
 
+// Max-edge key width: 0 = automatic (32-bit keys whenever the edge indices
+// fit), 8 = always (e << 32) | z.  Set by vr_set_tri_key_width.
+static std::atomic<int> g_tri_key_width{0};
+
 // Largest all-pairs count for which the edge keys are generated before the
 // host knows the kept-edge count (the key buffers then hold every pair: at
 // most 1M keys, n <= 1448).  Larger clouds gain nothing from it (their key
@@ -657,7 +661,11 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   uint64_t *tk_lex = nullptr;  // tetrahedra: the triangles' keys in lexicographic order
   int32_t *ordidx = nullptr, *cnt4 = nullptr;
   int64_t *off4 = nullptr, *bs_t = nullptr;
-  if (T > 0 && !early_tri) VR_TRY(ws.alloc(&tk, T));  // lex keys, or max-edge keys (e << 32) | z
+  // Max-edge keys take 32 bits, (e << zbits) | z, when the edge indices fit
+  // the bits n leaves (E <= 2^20 at n = 4000), else (e << 32) | z.
+  const int me_zbits = std::max(1, bitlen((uint64_t)(n - 1)));
+  const bool me_key32 = !lexm && g_tri_key_width.load() != 8 && E <= (int64_t(1) << (32 - me_zbits));
+  if (T > 0 && !early_tri) VR_TRY(ws.alloc(&tk, me_key32 ? (T + 1) / 2 : T));  // lex keys, or max-edge keys
   if (lexm) {
     VR_TRY(ws.alloc(&trs.tkeys, T));
     VR_TRY(ws.alloc(&trs.meta, rs_meta_bytes(T)));
@@ -720,15 +728,26 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       // Max-edge order: keys (e << 32) | z generated in final order from the
       // time-sliced adjacency, then the final write; tie groups merged after.
       prof.begin("tri_gen");
-      launch_dep(k_tri_gen_me, grid_for(E, 8, 32), 256, 0, s, everts, E, W, n, nbr_ptr, toff, T, tk, sx, st,
-                 force_lex);
-      count_launch();
-      VR_CUDA(cudaGetLastError());
-      prof.end();
-      prof.begin("tri_final");
       const EdgeIndex exm{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
-      launch_dep(k_tri_final_me, grid_for((T + 3) / 4, 256), 256, 0, s, tk, T, everts, egrade, exm, tverts, tgrade,
-                 tcol, trow, st);
+      if (me_key32) {
+        launch_dep(k_tri_gen_me<uint32_t>, grid_for(E, 8, 32), 256, 0, s, everts, E, W, n, nbr_ptr, toff, T,
+                   (uint32_t *)tk, me_zbits, sx, st, force_lex);
+        count_launch();
+        VR_CUDA(cudaGetLastError());
+        prof.end();
+        prof.begin("tri_final");
+        launch_dep(k_tri_final_me<uint32_t>, grid_for((T + 3) / 4, 256), 256, 0, s, (const uint32_t *)tk, me_zbits,
+                   T, everts, egrade, exm, tverts, tgrade, tcol, trow, st);
+      } else {
+        launch_dep(k_tri_gen_me<uint64_t>, grid_for(E, 8, 32), 256, 0, s, everts, E, W, n, nbr_ptr, toff, T, tk, 32,
+                   sx, st, force_lex);
+        count_launch();
+        VR_CUDA(cudaGetLastError());
+        prof.end();
+        prof.begin("tri_final");
+        launch_dep(k_tri_final_me<uint64_t>, grid_for((T + 3) / 4, 256), 256, 0, s, (const uint64_t *)tk, 32, T,
+                   everts, egrade, exm, tverts, tgrade, tcol, trow, st);
+      }
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();
@@ -891,3 +910,12 @@ vr_status build_cloud(const void *dpts, int32_t n, int32_t d, vr_dtype dtype, in
 }
 
 }  // namespace vr
+
+extern "C" vr_status vr_set_tri_key_width(int32_t bytes) {
+  if (bytes != 0 && bytes != 8) {
+    vr::set_error("triangle key width %d: 0 (automatic) or 8", bytes);
+    return VR_ERR_ARG;
+  }
+  vr::g_tri_key_width.store(bytes);
+  return VR_OK;
+}

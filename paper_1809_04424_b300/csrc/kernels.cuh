@@ -1340,9 +1340,11 @@ static __global__ void __launch_bounds__(256, 6) k_tri_count(const int32_t *ever
 // every lane's run of keys, which the lane writes in order.  The keys are
 // in final (max-edge) order: no sort follows.
 constexpr int MEG_KMAX = VR_MAX_POINTS / 32 / 16;  // words per lane and row at most
+// KT: the key word (see k_tri_final_me); T: the key buffer's capacity in keys.
+template <typename KT>
 static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts, int64_t E, int W, int n,
                                                            const int32_t *nbr_ptr, const int64_t *toff, int64_t T,
-                                                           uint64_t *tkeys, SnapIdx sx, DevStatus *st,
+                                                           KT *tkeys, int zbits, SnapIdx sx, DevStatus *st,
                                                            int force_lex) {
   pdl_entry();
   if (build_failed(st)) return;
@@ -1423,14 +1425,26 @@ static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts
     if (live && c) {
       const int64_t p = toff[e] + inc - c;
       if (p + c <= T) {
-        // Key (e << 32) | z stored as its two 32-bit halves.
-        uint2 *out = (uint2 *)(tkeys + p);
-        const uint32_t eh = (uint32_t)e;
+        if constexpr (sizeof(KT) == 8) {
+          // Key (e << 32) | z stored as its two 32-bit halves.
+          uint2 *out = (uint2 *)(tkeys + p);
+          const uint32_t eh = (uint32_t)e;
 #pragma unroll
-        for (int k = 0; k < MEG_KMAX; ++k) {
-          if (k >= K) break;
-          const uint32_t zb = (uint32_t)(w0 + k) * 32u - 1u;
-          for (uint32_t mm = wx[k]; mm; mm &= mm - 1) __stcs(out++, make_uint2(zb + __ffs(mm), eh));
+          for (int k = 0; k < MEG_KMAX; ++k) {
+            if (k >= K) break;
+            const uint32_t zb = (uint32_t)(w0 + k) * 32u - 1u;
+            for (uint32_t mm = wx[k]; mm; mm &= mm - 1) __stcs(out++, make_uint2(zb + __ffs(mm), eh));
+          }
+        } else {
+          // Key (e << zbits) | z (z < 2^zbits).
+          unsigned int *out = (unsigned int *)(tkeys + p);
+          const uint32_t ek = ((uint32_t)e << zbits) - 1u;
+#pragma unroll
+          for (int k = 0; k < MEG_KMAX; ++k) {
+            if (k >= K) break;
+            const uint32_t zb = ek + (uint32_t)(w0 + k) * 32u;
+            for (uint32_t mm = wx[k]; mm; mm &= mm - 1) __stcs(out++, zb + __ffs(mm));
+          }
         }
       } else {
         raise_flag(st, F_INTERNAL);  // never write past the key array
@@ -1623,10 +1637,11 @@ static __global__ void __launch_bounds__(256) k_tri_final(const uint64_t *tkeys,
 // cost a 32-byte sector per lookup.  Same store pattern as k_tri_final (128
 // triangles per warp, vertices and rows staged in shared memory for 16-byte
 // stores).
-__device__ __forceinline__ void tri_final_me_one(uint64_t k, const int32_t *everts, const int32_t *egrade,
-                                                 const EdgeIndex &ex, int32_t *v, int32_t *r, int32_t &g) {
-  const int32_t e = (int32_t)(k >> 32);
-  const int z = (int)(k & 0xffffu);
+__device__ __forceinline__ void tri_final_me_one(uint64_t k, int zbits, const int32_t *everts,
+                                                 const int32_t *egrade, const EdgeIndex &ex, int32_t *v, int32_t *r,
+                                                 int32_t &g) {
+  const int32_t e = (int32_t)(k >> zbits);
+  const int z = (int)(k & ((1ull << min(zbits, 16)) - 1ull));  // z < n <= 2^16
   const int2 xy = ((const int2 *)everts)[e];
   const int x = xy.x, y = xy.y;
   const int32_t oxz = ex.ord<false>(x, z);
@@ -1638,10 +1653,13 @@ __device__ __forceinline__ void tri_final_me_one(uint64_t k, const int32_t *ever
   g = egrade[e];
 }
 
-static __global__ void __launch_bounds__(256) k_tri_final_me(const uint64_t *tkeys, int64_t T, const int32_t *everts,
-                                                             const int32_t *egrade, EdgeIndex ex, int32_t *tverts,
-                                                             int32_t *tgrade, int64_t *tcolptr, int32_t *trow,
-                                                             const DevStatus *st) {
+// KT: the key word, uint64_t ((e << 32) | z, zbits = 32) or uint32_t
+// ((e << zbits) | z, when the edge count fits the bits that n leaves).
+template <typename KT>
+static __global__ void __launch_bounds__(256, 4) k_tri_final_me(const KT *tkeys, int zbits, int64_t T,
+                                                                const int32_t *everts, const int32_t *egrade,
+                                                                EdgeIndex ex, int32_t *tverts, int32_t *tgrade,
+                                                                int64_t *tcolptr, int32_t *trow, const DevStatus *st) {
   pdl_entry();
   if (build_failed(st)) return;
   __shared__ int4 sv[8][96], sr[8][96];  // per warp: 128 triangles x 3 ints
@@ -1652,17 +1670,16 @@ static __global__ void __launch_bounds__(256) k_tri_final_me(const uint64_t *tke
   // them from evicting the order table the lookups need from L2.  The next
   // chunk's keys are loaded while this one is processed.
   // Lane l takes triangles l, l + 32, l + 64, l + 96 of a chunk of 128:
-  // coalesced 8-byte key loads, and staging at stride 3 words (no bank
-  // conflicts).
+  // coalesced key loads, and staging at stride 3 words (no bank conflicts).
   int64_t ch = blockIdx.x * 8 + wid;
-  uint64_t nk[4] = {0, 0, 0, 0};
+  KT nk[4] = {0, 0, 0, 0};
   if (ch < nch) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) nk[u] = __ldcs(tkeys + ch * 128 + 32 * u + l);
   }
   for (; ch < nch; ch += cstride) {
     const int64_t base = ch * 128;
-    uint64_t kk[4];
+    KT kk[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) kk[u] = nk[u];
     if (ch + cstride < nch) {
@@ -1671,7 +1688,7 @@ static __global__ void __launch_bounds__(256) k_tri_final_me(const uint64_t *tke
     }
     int32_t v[12], r[12], g[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) tri_final_me_one(kk[u], everts, egrade, ex, v + 3 * u, r + 3 * u, g[u]);
+    for (int u = 0; u < 4; ++u) tri_final_me_one(kk[u], zbits, everts, egrade, ex, v + 3 * u, r + 3 * u, g[u]);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int t = 32 * u + l;
@@ -1695,7 +1712,7 @@ static __global__ void __launch_bounds__(256) k_tri_final_me(const uint64_t *tke
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = nch * 128 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < T; p += stride) {
     int32_t v[3], r[3], g;
-    tri_final_me_one(tkeys[p], everts, egrade, ex, v, r, g);
+    tri_final_me_one(tkeys[p], zbits, everts, egrade, ex, v, r, g);
     tverts[3 * p] = v[0]; tverts[3 * p + 1] = v[1]; tverts[3 * p + 2] = v[2];
     trow[3 * p] = r[0]; trow[3 * p + 1] = r[1]; trow[3 * p + 2] = r[2];
     tgrade[p] = g;

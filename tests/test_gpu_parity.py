@@ -239,6 +239,21 @@ def test_both_enumeration_orders_on_one_cloud(torch):
     check(torch, c.points, 2, 6.0)
 
 
+@pytest.mark.parametrize("width", [0, 8])
+def test_max_edge_key_widths(torch, width):
+    """1200 float32 points in d = 32 at the 5% cap (about 36k kept edges and
+    dense rows: max-edge order) with the triangle keys in 32 bits (automatic)
+    and forced to 64 bits, both in full."""
+    c = synth.config3(n=1200)
+    vr.vr_set_tri_key_width(width)
+    try:
+        g = check(torch, c.points, 2, c.maxrad)
+    finally:
+        vr.vr_set_tri_key_width(0)
+    E = len(g[1]["grade"])
+    assert E >= (1 << 15) and 2 * E >= 1200 * ((1200 + 31) // 32)
+
+
 @pytest.mark.parametrize("maxdim", [2, 1])
 def test_config3_gaussian_mixture_full(torch, maxdim):
     """Full size: 4000 float32 points in d = 32, cap keeping 5% of pairs
