@@ -961,8 +961,9 @@ static __global__ void __launch_bounds__(RS_THREADS) k_repair_big(const int32_t 
 // flag[k] = 1 where the squared distance differs from the previous edge's
 // (or from 0 for k = 0): the dense rank is the running sum of flags.
 // Grades and edge outputs in one launch: tiles of EG_TILE sorted keys (four
-// consecutive per thread; 1024-key tiles measured 2 us faster than one key
-// per thread on 75k edges: a shorter look-back chain) in ticket order; a key starts a new grade when its distance differs from the
+// per thread, 32 apart; 1024-key tiles measured 2 us faster than one key per
+// thread on 75k edges: a shorter look-back chain) in ticket order; a key
+// starts a new grade when its distance differs from the
 // previous key's (the first distance > 0 also does: grade 0 is d = 0); the
 // block scan of those flags plus the earlier tiles' counts (look-back) is the
 // dense rank; then the outputs: verts, grade, colptr/rowidx ({i, j}), grade
@@ -978,43 +979,55 @@ __global__ void __launch_bounds__(256) k_edge_grades(const uint64_t *keys, const
                                                      uint64_t *lb, int64_t ntiles, DevStatus *st) {
   pdl_entry();
   if (build_failed(st)) return;
+  // Warp w of the tile takes the keys k0 + w * 32 * PER + 32 q + l (q < PER):
+  // a new grade starts at a key whose value differs from its predecessor's;
+  // each key's grade is the tile's prefix plus the flags up to it (ballots),
+  // and consecutive lanes write consecutive entries of every output.
   constexpr int PER = EG_TILE / 256;
-  __shared__ int64_t sh[33];
-  __shared__ int64_t tile_sh, pre_sh;
+  __shared__ int64_t wpre[8];
+  __shared__ int64_t tile_sh;
   if (threadIdx.x == 0) tile_sh = atomicAdd((unsigned long long *)&lb[ntiles], 1ull);
   __syncthreads();
-  const int64_t tile = tile_sh, k0 = tile * EG_TILE;
-  // Flags of this thread's PER consecutive keys.
-  uint32_t fl = 0;
-  int cnt = 0;
+  const int w = threadIdx.x >> 5, l = lane_id();
+  const int64_t tile = tile_sh, kw = tile * EG_TILE + (int64_t)w * 32 * PER;
+  uint32_t fm[PER];
+  int wcnt = 0;
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
-    const int64_t k = k0 + threadIdx.x * PER + q;
+    const int64_t k = kw + 32 * q + l;
+    bool f = false;
     if (k < E) {
-      bool f;
       if constexpr (F) f = k == 0 ? (d64[0] != 0.0) : (d64[k] != d64[k - 1]);
       else f = k == 0 ? ((keys[0] >> KEY_SHIFT) != 0) : ((keys[k] >> KEY_SHIFT) != (keys[k - 1] >> KEY_SHIFT));
-      fl |= (uint32_t)f << q;
-      cnt += f;
     }
+    fm[q] = __ballot_sync(0xffffffffu, f);
+    wcnt += __popc(fm[q]);
   }
-  int64_t tot;
-  const int64_t ex = block_excl_scan<int64_t>((int64_t)cnt, sh, &tot);
-  if (threadIdx.x == 0) pre_sh = tile_lookback(lb, tile, tot, &st->flags);
+  if (l == 0) wpre[w] = wcnt;
   __syncthreads();
-  int64_t g = pre_sh + ex;  // grade before this thread's first key
+  if (w == 0) {
+    const int64_t v = l < 8 ? wpre[l] : 0;
+    const int64_t iv = warp_incl_scan(v);
+    const int64_t tot = __shfl_sync(0xffffffffu, iv, 31);
+    int64_t pre = 0;
+    if (l == 0) pre = tile_lookback(lb, tile, tot, &st->flags);
+    pre = __shfl_sync(0xffffffffu, pre, 0);
+    if (l < 8) wpre[l] = pre + iv - v;
+  }
+  __syncthreads();
+  int64_t gbase = wpre[w];  // grades started before this warp's q-th group
+  const uint32_t le = lanemask_lt() | (1u << l);
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
-    const int64_t k = k0 + threadIdx.x * PER + q;
-    if (k >= E) break;
-    const bool f = (fl >> q) & 1u;
-    g += f;
+    const int64_t k = kw + 32 * q + l;
+    const int64_t g = gbase + __popc(fm[q] & le);
+    gbase += __popc(fm[q]);
+    if (k >= E) continue;
+    const bool f = (fm[q] >> l) & 1u;
     const uint64_t key = keys[k];
     const int i = key_i(key), j = key_j(key);
-    verts[2 * k] = i;
-    verts[2 * k + 1] = j;
-    rowidx[2 * k] = i;
-    rowidx[2 * k + 1] = j;
+    ((int2 *)verts)[k] = make_int2(i, j);
+    ((int2 *)rowidx)[k] = make_int2(i, j);
     colptr[k] = 2 * k;
     grade[k] = (int32_t)g;
     if (f) {
