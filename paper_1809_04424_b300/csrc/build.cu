@@ -729,25 +729,28 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       // time-sliced adjacency, then the final write; tie groups merged after.
       prof.begin("tri_gen");
       const EdgeIndex exm{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
-      if (me_key32) {
-        launch_dep(k_tri_gen_me<uint32_t>, grid_for(E, 8, 32), 256, 0, s, everts, E, W, n, nbr_ptr, toff, T,
-                   (uint32_t *)tk, me_zbits, sx, st, force_lex);
+      // 16-byte chunks per lane and row: Wp / 16 words rounded up to whole
+      // chunks (a compile-time count per kernel).
+      const int k4 = ((((sx.Wp + 15) >> 4) + 3) & ~3) >> 2;
+      auto gen = [&](auto key) {
+        using KT = decltype(key);
+        KT *tkk = (KT *)tk;
+        const int zb = sizeof(KT) == 4 ? me_zbits : 32;
+        const unsigned g = grid_for(E, 8, 32);
+        if (k4 <= 1) launch_dep(k_tri_gen_me<KT, 1>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, T, tkk, zb, sx, st, force_lex);
+        else if (k4 == 2) launch_dep(k_tri_gen_me<KT, 2>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, T, tkk, zb, sx, st, force_lex);
+        else if (k4 == 3) launch_dep(k_tri_gen_me<KT, 3>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, T, tkk, zb, sx, st, force_lex);
+        else launch_dep(k_tri_gen_me<KT, 4>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, T, tkk, zb, sx, st, force_lex);
         count_launch();
         VR_CUDA(cudaGetLastError());
         prof.end();
         prof.begin("tri_final");
-        launch_dep(k_tri_final_me<uint32_t>, grid_for((T + 3) / 4, 256), 256, 0, s, (const uint32_t *)tk, me_zbits,
-                   T, everts, egrade, exm, tverts, tgrade, tcol, trow, st);
-      } else {
-        launch_dep(k_tri_gen_me<uint64_t>, grid_for(E, 8, 32), 256, 0, s, everts, E, W, n, nbr_ptr, toff, T, tk, 32,
-                   sx, st, force_lex);
-        count_launch();
-        VR_CUDA(cudaGetLastError());
-        prof.end();
-        prof.begin("tri_final");
-        launch_dep(k_tri_final_me<uint64_t>, grid_for((T + 3) / 4, 256), 256, 0, s, (const uint64_t *)tk, 32, T,
-                   everts, egrade, exm, tverts, tgrade, tcol, trow, st);
-      }
+        launch_dep(k_tri_final_me<KT>, grid_for((T + 3) / 4, 256), 256, 0, s, (const KT *)tk, zb, T, everts, egrade,
+                   exm, tverts, tgrade, tcol, trow, st);
+        return VR_OK;
+      };
+      if (me_key32) VR_TRY(gen(uint32_t{0}));
+      else VR_TRY(gen(uint64_t{0}));
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();

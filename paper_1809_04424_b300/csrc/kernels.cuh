@@ -1354,7 +1354,9 @@ static __global__ void __launch_bounds__(256, 6) k_tri_count(const int32_t *ever
 // in final (max-edge) order: no sort follows.
 constexpr int MEG_KMAX = VR_MAX_POINTS / 32 / 16;  // words per lane and row at most
 // KT: the key word (see k_tri_final_me); T: the key buffer's capacity in keys.
-template <typename KT>
+// K4: 16-byte chunks per lane and row, (Wp / 16 rounded up to whole chunks)
+// / 4, from 1 to 4 (Wp <= 256).
+template <typename KT, int K4>
 static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts, int64_t E, int W, int n,
                                                            const int32_t *nbr_ptr, const int64_t *toff, int64_t T,
                                                            KT *tkeys, int zbits, SnapIdx sx, DevStatus *st,
@@ -1365,9 +1367,11 @@ static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts
   constexpr int WMAX = VR_MAX_POINTS / 32;
   __shared__ uint4 drow[8][2][2 * WMAX / 4];  // per warp, per half: Dx then Dy (16-byte words)
   const int l = lane_id(), wid = threadIdx.x >> 5, half = l >> 4, s16 = l & 15;
-  // Words per lane: Wp / 16 rounded up to whole 16-byte chunks (K <= 16 since
-  // Wp <= 256); a lane's chunks past Wp are neither loaded nor used.
-  const int Wp = sx.Wp, K = (((Wp + 15) >> 4) + 3) & ~3, K4 = K >> 2;
+  // Words per lane: K = 4 K4; a lane's chunks past Wp are neither loaded nor
+  // used.
+  static_assert(K4 >= 1 && 4 * K4 <= MEG_KMAX, "chunks per lane");
+  constexpr int K = 4 * K4;
+  const int Wp = sx.Wp;
   uint32_t *dx = (uint32_t *)drow[wid][half], *dy = dx + WMAX;
   const int64_t nwarps = (int64_t)gridDim.x * 8;
   for (int64_t e = (blockIdx.x * 8 + wid) * 2 + half; e - half < E; e += nwarps * 2) {
@@ -1382,24 +1386,22 @@ static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts
     // This lane's words [w0, w0 + K) of both rows (zero before the first
     // snapshot and past Wp), and its delta words cleared.
     const int w0 = s16 * K;
-    uint32_t wx[MEG_KMAX], wy[MEG_KMAX];
+    uint32_t wx[K], wy[K];
     {
       const uint4 *vx = (const uint4 *)(sx.snap + ((int64_t)(b > 0 ? b - 1 : 0) * n + x) * Wp + w0);
       const uint4 *vy = (const uint4 *)(sx.snap + ((int64_t)(b > 0 ? b - 1 : 0) * n + y) * Wp + w0);
       const bool in = live && b > 0;
 #pragma unroll
-      for (int q = 0; q < MEG_KMAX / 4; ++q) {
+      for (int q = 0; q < K4; ++q) {
         uint4 a = make_uint4(0u, 0u, 0u, 0u), c = a;
-        if (in && q < K4 && w0 + 4 * q < Wp) {
+        if (in && w0 + 4 * q < Wp) {
           a = vx[q];
           c = vy[q];
         }
         wx[4 * q] = a.x; wx[4 * q + 1] = a.y; wx[4 * q + 2] = a.z; wx[4 * q + 3] = a.w;
         wy[4 * q] = c.x; wy[4 * q + 1] = c.y; wy[4 * q + 2] = c.z; wy[4 * q + 3] = c.w;
-        if (q < K4) {
-          ((uint4 *)(dx + w0))[q] = make_uint4(0u, 0u, 0u, 0u);
-          ((uint4 *)(dy + w0))[q] = make_uint4(0u, 0u, 0u, 0u);
-        }
+        ((uint4 *)(dx + w0))[q] = make_uint4(0u, 0u, 0u, 0u);
+        ((uint4 *)(dy + w0))[q] = make_uint4(0u, 0u, 0u, 0u);
       }
     }
     __syncwarp();
@@ -1419,8 +1421,8 @@ static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts
     __syncwarp();
     int c = 0;
 #pragma unroll
-    for (int q = 0; q < MEG_KMAX / 4; ++q) {
-      if (q < K4) {
+    for (int q = 0; q < K4; ++q) {
+      {
         const uint4 ddx = ((const uint4 *)(dx + w0))[q], ddy = ((const uint4 *)(dy + w0))[q];
         wx[4 * q] = (wx[4 * q] | ddx.x) & (wy[4 * q] | ddy.x);
         wx[4 * q + 1] = (wx[4 * q + 1] | ddx.y) & (wy[4 * q + 1] | ddy.y);
@@ -1443,8 +1445,7 @@ static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts
           uint2 *out = (uint2 *)(tkeys + p);
           const uint32_t eh = (uint32_t)e;
 #pragma unroll
-          for (int k = 0; k < MEG_KMAX; ++k) {
-            if (k >= K) break;
+          for (int k = 0; k < K; ++k) {
             const uint32_t zb = (uint32_t)(w0 + k) * 32u - 1u;
             for (uint32_t mm = wx[k]; mm; mm &= mm - 1) __stcs(out++, make_uint2(zb + __ffs(mm), eh));
           }
@@ -1453,8 +1454,7 @@ static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts
           unsigned int *out = (unsigned int *)(tkeys + p);
           const uint32_t ek = ((uint32_t)e << zbits) - 1u;
 #pragma unroll
-          for (int k = 0; k < MEG_KMAX; ++k) {
-            if (k >= K) break;
+          for (int k = 0; k < K; ++k) {
             const uint32_t zb = ek + (uint32_t)(w0 + k) * 32u;
             for (uint32_t mm = wx[k]; mm; mm &= mm - 1) __stcs(out++, zb + __ffs(mm));
           }

@@ -254,6 +254,19 @@ def test_max_edge_key_widths(torch, width):
     assert E >= (1 << 15) and 2 * E >= 1200 * ((1200 + 31) // 32)
 
 
+@pytest.mark.parametrize("n", [4500, 6200])
+def test_max_edge_wide_rows(torch, n):
+    """Gaussian-mixture clouds (d = 32, 5% cap) whose snapshot rows take 3
+    and 4 16-byte chunks per generator lane (144 and 196 words): 506k edges
+    and 28M triangles with 32-bit keys; 961k edges (more than a 13-bit vertex
+    leaves room for) and 73M triangles with 64-bit keys; in full."""
+    c = synth.config3(n=n)
+    g = check(torch, c.points, 2, c.maxrad)
+    E = len(g[1]["grade"])
+    assert 2 * E >= n * ((n + 31) // 32)  # dense rows: max-edge order
+    assert (E > 1 << 19) == (n == 6200)
+
+
 @pytest.mark.parametrize("maxdim", [2, 1])
 def test_config3_gaussian_mixture_full(torch, maxdim):
     """Full size: 4000 float32 points in d = 32, cap keeping 5% of pairs
