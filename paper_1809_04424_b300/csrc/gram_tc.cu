@@ -36,6 +36,8 @@
 //
 // Every wait (TMA and MMA completion) is bounded; on a timeout the kernel
 // raises F_TIMEOUT, releases its TMEM and returns.
+#include <atomic>
+
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -148,7 +150,8 @@ template <bool F>
 // One warp per padded row: lane l owns coordinates 2l and 2l+1 (bf16x2
 // stores, coalesced), |y_i|^2 by a warp sum of the split values.
 __global__ void k_gram_prep(const void *Xv, int n, int d, int npad, const float *centre, __nv_bfloat16 *Xh,
-                            __nv_bfloat16 *Xl, float *norm, __nv_bfloat16 *Xm = nullptr) {
+                            __nv_bfloat16 *Xl, float *norm, __nv_bfloat16 *Xm) {
+  pdl_entry();
   const int lane = threadIdx.x & 31;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < npad; i += (gridDim.x * blockDim.x) >> 5) {
     float hi[2] = {0.f, 0.f}, mid[2] = {0.f, 0.f}, lo[2] = {0.f, 0.f};
@@ -184,9 +187,12 @@ __global__ void k_gram_prep(const void *Xv, int n, int d, int npad, const float 
 // the pairs), bits ORed into both rows.
 __global__ void k_band_patch(const float *X, int d, int W, double r2, const uint64_t *band, const DevStatus *st,
                              uint64_t band_cap, uint32_t *adj) {
+  pdl_entry();
   if (build_failed(st)) return;  // a timed-out tile left its bitmap words unwritten
   const uint64_t cnt = min((unsigned long long)st->band_count, (unsigned long long)band_cap);
-  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < cnt; t += (uint64_t)gridDim.x * blockDim.x) {
+  // Pair t goes to CTA t mod grid: a short list still spreads over every SM
+  // (its FP64 chains, not its loads, set the time).
+  for (uint64_t t = threadIdx.x * (uint64_t)gridDim.x + blockIdx.x; t < cnt; t += (uint64_t)gridDim.x * blockDim.x) {
     const int i = (int)(band[t] >> 32), j = (int)(band[t] & 0xffffffffu);
     if (d2_f64(X + (int64_t)i * d, X + (int64_t)j * d, d) <= r2) {
       atomicOr(&adj[(int64_t)i * W + (j >> 5)], 1u << (j & 31));
@@ -197,9 +203,11 @@ __global__ void k_band_patch(const float *X, int d, int W, double r2, const uint
 
 // Centre c = mean of up to 256 evenly spaced points (one CTA).  Any c gives
 // the same distances; one near the middle of the cloud keeps |y|, and with it
-// the width of the near-cap band, small.
+// the width of the near-cap band, small.  Also clears the near-cap count.
 constexpr int TC_CENTRE_SAMPLE = 256;
-__global__ void __launch_bounds__(1024) k_gram_centre(const float *X, int n, int d, float *centre) {
+__global__ void __launch_bounds__(1024) k_gram_centre(const float *X, int n, int d, float *centre, DevStatus *st) {
+  pdl_entry();
+  if (threadIdx.x == 0) st->band_count = 0;
   __shared__ float part[32][TC_K];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m = min(n, TC_CENTRE_SAMPLE);
@@ -288,6 +296,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_bitmap_tc(const __grid_cons
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *(volatile uint32_t *)tslot_ptr;
+  // TMEM and barriers are set up while the operand preparation finishes.
+  pdl_entry();
 
   if (threadIdx.x == 0) {
     const uint32_t bytes = (S3 ? 6 : F ? 4 : 2) * TC_OPERAND_BYTES;
@@ -482,12 +492,20 @@ static cudaError_t launch_tiles(int ntiles, size_t smem, cudaStream_t s, const C
                                 const CUtensorMap &mm, const void *X, int n, int d, int W, int nt, const Cap &cap,
                                 const float *norm, uint32_t *adj, DevStatus *st, uint64_t *band, uint64_t band_cap,
                                 GramAcc *acc, int stall_tile, long stall_limit) {
-  cudaError_t e = cudaFuncSetAttribute(k_gram_bitmap_tc<F, VALIDATE, INJ, S3>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // The shared-memory size is fixed per kernel: set once per device.
+  static std::atomic<uint64_t> set_on{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  k_gram_bitmap_tc<F, VALIDATE, INJ, S3><<<ntiles, TC_THREADS, smem, s>>>(mh, ml, X, n, d, W, nt, cap, norm, adj, st,
-                                                                         band, band_cap, acc, stall_tile, stall_limit,
-                                                                         mm);
+  if (dev >= 64 || !((set_on.load() >> dev) & 1u)) {
+    e = cudaFuncSetAttribute(k_gram_bitmap_tc<F, VALIDATE, INJ, S3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) set_on.fetch_or(1ull << dev);
+  }
+  e = launch_dep(k_gram_bitmap_tc<F, VALIDATE, INJ, S3>, ntiles, TC_THREADS, smem, s, mh, ml, X, n, d, W, nt, cap,
+                 norm, adj, st, band, band_cap, acc, stall_tile, stall_limit, mm);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -501,12 +519,18 @@ vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, ui
   const int W = (n + 31) / 32;
   const int nt = (n + TC_TILE - 1) / TC_TILE;
   const int npad = nt * TC_TILE;
-  __nv_bfloat16 *Xh = nullptr, *Xl = nullptr, *Xm = nullptr;
-  float *norm = nullptr, *centre = nullptr;
-  uint64_t *band = nullptr;
+  const int ntiles = nt * (nt + 1) / 2;
+  const uint64_t npairs = (uint64_t)n * (n - 1) / 2;
+  const uint64_t band_cap = std::min<uint64_t>(npairs, std::max<uint64_t>(1u << 20, npairs / 16));
+  const bool want_band = F && !acc;
+  // One allocation: operands (hi, lo, mid), norms, centre, near-cap list.
+  auto up256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t opb = up256((size_t)npad * TC_ROW_BYTES);
+  const size_t o_l = opb, o_m = 2 * opb, o_norm = (S3 ? 3 : 2) * opb, o_c = o_norm + up256((size_t)npad * 4),
+               o_band = o_c + up256((size_t)TC_K * 4), total = o_band + (want_band ? band_cap * 8 : 0);
+  char *blk = nullptr;
   auto release = [&]() {
-    for (void *p : {(void *)Xh, (void *)Xl, (void *)Xm, (void *)norm, (void *)centre, (void *)band})
-      if (p) cudaFreeAsync(p, s);
+    if (blk) cudaFreeAsync(blk, s);
   };
   auto fail = [&](cudaError_t e) {
     cudaGetLastError();
@@ -514,11 +538,11 @@ vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, ui
     return cuda_status(e, "gram_bitmap_tc", __FILE__, __LINE__);
   };
   cudaError_t e;
-  if ((e = dev_malloc((void **)&Xh, (size_t)npad * TC_ROW_BYTES, s)) != cudaSuccess) return fail(e);
-  if ((e = dev_malloc((void **)&Xl, (size_t)npad * TC_ROW_BYTES, s)) != cudaSuccess) return fail(e);
-  if (S3 && (e = dev_malloc((void **)&Xm, (size_t)npad * TC_ROW_BYTES, s)) != cudaSuccess) return fail(e);
-  if ((e = dev_malloc((void **)&norm, (size_t)npad * 4, s)) != cudaSuccess) return fail(e);
-  if ((e = dev_malloc((void **)&centre, (size_t)TC_K * 4, s)) != cudaSuccess) return fail(e);
+  if ((e = dev_malloc((void **)&blk, total, s)) != cudaSuccess) return fail(e);
+  __nv_bfloat16 *Xh = (__nv_bfloat16 *)blk, *Xl = (__nv_bfloat16 *)(blk + o_l);
+  __nv_bfloat16 *Xm = S3 ? (__nv_bfloat16 *)(blk + o_m) : nullptr;
+  float *norm = (float *)(blk + o_norm), *centre = (float *)(blk + o_c);
+  uint64_t *band = want_band ? (uint64_t *)(blk + o_band) : nullptr;
   CUtensorMap mh, ml, mm;
   vr_status vs = make_map(&mh, Xh, npad);
   if (vs == VR_OK) vs = make_map(&ml, Xl, npad);
@@ -528,20 +552,18 @@ vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, ui
     return vs;
   }
   if (F) {
-    k_gram_centre<<<1, 1024, 0, s>>>((const float *)X, n, d, centre);
-    k_gram_prep<true><<<(npad + 7) / 8, 256, 0, s>>>(X, n, d, npad, centre, Xh, Xl, norm, S3 ? Xm : nullptr);
+    if ((e = launch_dep(k_gram_centre, 1, 1024, 0, s, (const float *)X, n, d, centre, st)) != cudaSuccess)
+      return fail(e);
+    if ((e = launch_dep(k_gram_prep<true>, (npad + 7) / 8, 256, 0, s, X, n, d, npad, (const float *)centre, Xh, Xl,
+                        norm, Xm)) != cudaSuccess)
+      return fail(e);
   } else {
-    k_gram_prep<false><<<(npad + 7) / 8, 256, 0, s>>>(X, n, d, npad, centre, Xh, Xl, norm);
+    if ((e = launch_dep(k_gram_prep<false>, (npad + 7) / 8, 256, 0, s, X, n, d, npad, (const float *)centre, Xh, Xl,
+                        norm, (__nv_bfloat16 *)nullptr)) != cudaSuccess)
+      return fail(e);
   }
   count_launch(F ? 2 : 1);
   const size_t smem = (S3 ? 6 : 4) * TC_OPERAND_BYTES + 1024 + 64;
-  const int ntiles = nt * (nt + 1) / 2;
-  const uint64_t npairs = (uint64_t)n * (n - 1) / 2;
-  const uint64_t band_cap = std::min<uint64_t>(npairs, std::max<uint64_t>(1u << 20, npairs / 16));
-  if (F && !acc) {
-    if ((e = dev_malloc((void **)&band, band_cap * 8, s)) != cudaSuccess) return fail(e);
-    if ((e = cudaMemsetAsync(&st->band_count, 0, 8, s)) != cudaSuccess) return fail(e);
-  }
   int stall_tile = -1;
   long stall_limit = TC_WAIT_LIMIT;
   const bool inj = !acc && take_gram_stall(ntiles, &stall_tile, &stall_limit);
@@ -556,10 +578,11 @@ vr_status gram_bitmap_tc(const void *X, int n, int d, bool F, const Cap &cap, ui
 #undef VR_TILES
   count_launch();
   if (e != cudaSuccess) return fail(e);
-  if (F && !acc) {
-    k_band_patch<<<num_sms() * 4, 256, 0, s>>>((const float *)X, d, W, cap.r2, band, st, band_cap, adj);
+  if (want_band) {
+    e = launch_dep(k_band_patch, num_sms() * 4, 256, 0, s, (const float *)X, d, W, cap.r2, (const uint64_t *)band,
+                   (const DevStatus *)st, band_cap, adj);
     count_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    if (e != cudaSuccess) return fail(e);
   }
   release();
   return VR_OK;
