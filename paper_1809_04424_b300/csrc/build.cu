@@ -231,6 +231,12 @@ constexpr int64_t EARLY_TRI_MAX_E = int64_t(1) << 17;
 // fit), 8 = always (e << 32) | z.  Set by vr_set_tri_key_width.
 static std::atomic<int> g_tri_key_width{0};
 
+// Max-edge order: the key generator is enqueued before the host reads T when
+// its buffer, sized by the wedge bound T <= sum_v C(deg v, 2) / 3, stays
+// under this many bytes (4000-point float cloud: 33.0M keys for 19.8M
+// triangles); the host's wait then overlaps the generator.
+constexpr int64_t EARLY_GEN_MAX_BYTES = int64_t(1) << 30;
+
 // Largest all-pairs count for which the edge keys are generated before the
 // host knows the kept-edge count (the key buffers then hold every pair: at
 // most 1M keys, n <= 1448).  Larger clouds gain nothing from it (their key
@@ -450,6 +456,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_TRY(wait_status(sm, s));
   }
   const int64_t E = hst->E;
+  const int64_t wedges = hst->wedges;
   if (E > INT32_MAX) {
     set_error("%lld edges exceed the 2^31-1 limit of one dimension", (long long)E);
     return VR_ERR_RANGE;
@@ -537,6 +544,14 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   const int64_t T_cap = early_tri ? (int64_t)std::ceil(std::sqrt(2.0) / 3.0 * std::pow((double)E, 1.5)) + 1 : 0;
   uint64_t *tk = nullptr;
   if (early_tri) VR_TRY(ws.alloc(&tk, T_cap));
+  // Max-edge keys take 32 bits, (e << zbits) | z, when the edge indices fit
+  // the bits n leaves (E <= 2^20 at n = 4000), else (e << 32) | z.
+  const int me_zbits = std::max(1, bitlen((uint64_t)(n - 1)));
+  const bool me_key32 = g_tri_key_width.load() != 8 && E <= (int64_t(1) << (32 - me_zbits));
+  const int64_t T_wedge = wedges / 3 + 1;
+  const bool early_gen = want_snap && (double)T_wedge * (me_key32 ? 4 : 8) <= (double)EARLY_GEN_MAX_BYTES;
+  uint64_t *tk_me = nullptr;  // max-edge keys
+  if (early_gen) VR_TRY(ws.alloc(&tk_me, me_key32 ? (T_wedge + 1) / 2 : T_wedge));
   if (maxdim >= 2 && E > 0) {
     VR_TRY(ws.alloc(&tcnt, E));
     VR_TRY(ws.alloc(&toff, E + 1));
@@ -628,7 +643,37 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     prof.end();
     return VR_OK;
   };
+  // Max-edge key generation (returns at once if the device chose lex order):
+  // into the bound-sized buffer before the host's wait, or after it.
+  const EdgeIndex exm{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
+  auto me_gen = [&](int64_t cap) -> vr_status {
+    prof.begin("tri_gen");
+    // 16-byte chunks per lane and row: Wp / 16 words rounded up to whole
+    // chunks (a compile-time count per kernel).
+    const int k4 = ((((sx.Wp + 15) >> 4) + 3) & ~3) >> 2;
+    const unsigned g = grid_for(E, 8, 32);
+    auto go = [&](auto key) {
+      using KT = decltype(key);
+      KT *tkk = (KT *)tk_me;
+      const int zb = sizeof(KT) == 4 ? me_zbits : 32;
+      if (k4 <= 1)
+        launch_dep(k_tri_gen_me<KT, 1>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, cap, tkk, zb, sx, st, force_lex);
+      else if (k4 == 2)
+        launch_dep(k_tri_gen_me<KT, 2>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, cap, tkk, zb, sx, st, force_lex);
+      else if (k4 == 3)
+        launch_dep(k_tri_gen_me<KT, 3>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, cap, tkk, zb, sx, st, force_lex);
+      else
+        launch_dep(k_tri_gen_me<KT, 4>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, cap, tkk, zb, sx, st, force_lex);
+    };
+    if (me_key32) go(uint32_t{0});
+    else go(uint64_t{0});
+    count_launch();
+    VR_CUDA(cudaGetLastError());
+    prof.end();
+    return VR_OK;
+  };
   if (early_tri) VR_TRY(lex_tri_gen(T_cap));
+  if (early_gen) VR_TRY(me_gen(T_wedge));
   VR_TRY(wait_status(sm, s));
   const int64_t ngrades = E > 0 ? hst->ngrades : 1;
   const int64_t T = (maxdim >= 2 && E > 0) ? hst->T : 0;
@@ -661,11 +706,12 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   uint64_t *tk_lex = nullptr;  // tetrahedra: the triangles' keys in lexicographic order
   int32_t *ordidx = nullptr, *cnt4 = nullptr;
   int64_t *off4 = nullptr, *bs_t = nullptr;
-  // Max-edge keys take 32 bits, (e << zbits) | z, when the edge indices fit
-  // the bits n leaves (E <= 2^20 at n = 4000), else (e << 32) | z.
-  const int me_zbits = std::max(1, bitlen((uint64_t)(n - 1)));
-  const bool me_key32 = !lexm && g_tri_key_width.load() != 8 && E <= (int64_t(1) << (32 - me_zbits));
-  if (T > 0 && !early_tri) VR_TRY(ws.alloc(&tk, me_key32 ? (T + 1) / 2 : T));  // lex keys, or max-edge keys
+  if (T > 0 && lexm && !early_tri) VR_TRY(ws.alloc(&tk, T));  // lex keys
+  if (T > 0 && !lexm && !early_gen) VR_TRY(ws.alloc(&tk_me, me_key32 ? (T + 1) / 2 : T));
+  if (early_gen && T > T_wedge) {
+    set_error("%lld triangles exceed their bound %lld", (long long)T, (long long)T_wedge);
+    return VR_ERR_INTERNAL;
+  }
   if (lexm) {
     VR_TRY(ws.alloc(&trs.tkeys, T));
     VR_TRY(ws.alloc(&trs.meta, rs_meta_bytes(T)));
@@ -725,32 +771,17 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_CUDA(cudaGetLastError());
       prof.end();
     } else if (T > 0) {
-      // Max-edge order: keys (e << 32) | z generated in final order from the
-      // time-sliced adjacency, then the final write; tie groups merged after.
-      prof.begin("tri_gen");
-      const EdgeIndex exm{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
-      // 16-byte chunks per lane and row: Wp / 16 words rounded up to whole
-      // chunks (a compile-time count per kernel).
-      const int k4 = ((((sx.Wp + 15) >> 4) + 3) & ~3) >> 2;
-      auto gen = [&](auto key) {
-        using KT = decltype(key);
-        KT *tkk = (KT *)tk;
-        const int zb = sizeof(KT) == 4 ? me_zbits : 32;
-        const unsigned g = grid_for(E, 8, 32);
-        if (k4 <= 1) launch_dep(k_tri_gen_me<KT, 1>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, T, tkk, zb, sx, st, force_lex);
-        else if (k4 == 2) launch_dep(k_tri_gen_me<KT, 2>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, T, tkk, zb, sx, st, force_lex);
-        else if (k4 == 3) launch_dep(k_tri_gen_me<KT, 3>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, T, tkk, zb, sx, st, force_lex);
-        else launch_dep(k_tri_gen_me<KT, 4>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, T, tkk, zb, sx, st, force_lex);
-        count_launch();
-        VR_CUDA(cudaGetLastError());
-        prof.end();
-        prof.begin("tri_final");
-        launch_dep(k_tri_final_me<KT>, grid_for((T + 3) / 4, 256), 256, 0, s, (const KT *)tk, zb, T, everts, egrade,
-                   exm, tverts, tgrade, tcol, trow, st);
-        return VR_OK;
-      };
-      if (me_key32) VR_TRY(gen(uint32_t{0}));
-      else VR_TRY(gen(uint64_t{0}));
+      // Max-edge order: keys in final order from the time-sliced adjacency
+      // (generated above when the bound-sized buffer was taken), then the
+      // final write; tie groups merged after.
+      if (!early_gen) VR_TRY(me_gen(T));
+      prof.begin("tri_final");
+      if (me_key32)
+        launch_dep(k_tri_final_me<uint32_t>, grid_for((T + 3) / 4, 256), 256, 0, s, (const uint32_t *)tk_me, me_zbits,
+                   T, everts, egrade, exm, tverts, tgrade, tcol, trow, st);
+      else
+        launch_dep(k_tri_final_me<uint64_t>, grid_for((T + 3) / 4, 256), 256, 0, s, (const uint64_t *)tk_me, 32, T,
+                   everts, egrade, exm, tverts, tgrade, tcol, trow, st);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();

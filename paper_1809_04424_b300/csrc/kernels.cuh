@@ -357,7 +357,7 @@ static __global__ void __launch_bounds__(256) k_rows_scan(const uint32_t *adj, i
   // bypassing L1 for the other CTAs' writes), 8 consecutive per thread.
   constexpr int PER = 8, CH = 256 * PER;
   __shared__ int32_t cd[CH], cu[CH];
-  int64_t base_d = 0, base_u = 0;
+  int64_t base_d = 0, base_u = 0, wedges = 0;
   for (int c0 = 0; c0 < n; c0 += CH) {
     for (int q = threadIdx.x; q < CH; q += 256) {
       const int j = c0 + q;
@@ -365,15 +365,19 @@ static __global__ void __launch_bounds__(256) k_rows_scan(const uint32_t *adj, i
       cu[q] = j < n ? __ldcg(up + j) : 0;
     }
     __syncthreads();
-    int64_t sd = 0, su = 0;
+    int64_t sd = 0, su = 0, sw = 0;
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-      sd += cd[threadIdx.x * PER + q];
+      const int64_t dq = cd[threadIdx.x * PER + q];
+      sd += dq;
       su += cu[threadIdx.x * PER + q];
+      sw += dq * (dq - 1) / 2;
     }
-    int64_t td, tu;
+    int64_t td, tu, tw;
     const int64_t ed = block_excl_scan<int64_t>(sd, sh, &td);
     const int64_t eu = block_excl_scan<int64_t>(su, sh, &tu);
+    block_excl_scan<int64_t>(sw, sh, &tw);
+    wedges += tw;
     int64_t rd = base_d + ed, ru = base_u + eu;
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
@@ -393,6 +397,7 @@ static __global__ void __launch_bounds__(256) k_rows_scan(const uint32_t *adj, i
     nbr_ptr[n] = (int32_t)base_d;
     lex_ptr[n] = base_u;
     st->E = base_u;
+    st->wedges = wedges;
     st->rows_done = 0;  // ready for another launch on the same status word
   }
 }

@@ -71,6 +71,7 @@ struct DevStatus {
   int64_t big_grp_count;
   uint64_t band_count;       // float Gram tiles: pairs left for the exact decision
   unsigned int rows_done;    // k_rows_scan: CTAs finished (the last one scans)
+  int64_t wedges;            // sum over vertices of C(deg, 2): at least three times the triangle count
 };
 
 __device__ __forceinline__ void raise_flag(DevStatus *st, int32_t f) { atomicOr(&st->flags, f); }
