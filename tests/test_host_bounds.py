@@ -3,8 +3,9 @@
 The build sizes the lexicographic triangle-key buffer of small complexes
 before it knows the triangle count, from the bound on the number of triangles
 of a graph with E edges, T <= (sqrt 2 / 3) E^(3/2) (a consequence of the
-Kruskal-Katona theorem; complete graphs approach it).  These tests check the
-capacity formula the build uses against exact triangle counts."""
+Kruskal-Katona theorem; complete graphs approach it), and the max-edge key
+buffer from the wedge bound T <= sum_v C(deg v, 2) / 3.  These tests check the
+capacity formulas the build uses against exact triangle counts."""
 import math
 
 import numpy as np
@@ -46,6 +47,32 @@ def test_random_and_clustered_graphs(seed):
     adj = (adj | adj.T).astype(np.int64)
     E = int(adj.sum()) // 2
     assert triangles(adj) <= capacity(E)
+
+
+def wedge_capacity(adj):
+    """The max-edge key buffer's capacity: every triangle holds three of the
+    sum_v C(deg v, 2) wedges (pairs of edges at a vertex), so
+    T <= sum_v C(deg v, 2) / 3; the build takes that plus one."""
+    deg = adj.sum(1)
+    return int((deg * (deg - 1) // 2).sum()) // 3 + 1
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_wedge_bound(seed):
+    g = np.random.default_rng(100 + seed)
+    n = int(g.integers(5, 160))
+    pts = g.normal(size=(n, 3))
+    d2 = ((pts[:, None, :] - pts[None, :, :]) ** 2).sum(-1)
+    r2 = float(np.quantile(d2, g.uniform(0.05, 1.0)))
+    adj = ((d2 <= r2) & ~np.eye(n, dtype=bool)).astype(np.int64)
+    assert triangles(adj) <= wedge_capacity(adj)
+
+
+@pytest.mark.parametrize("n", [3, 4, 7, 30])
+def test_wedge_bound_tight_on_complete_graphs(n):
+    """Complete graphs meet it: C(n, 3) = n C(n - 1, 2) / 3."""
+    adj = np.ones((n, n), dtype=np.int64) - np.eye(n, dtype=np.int64)
+    assert wedge_capacity(adj) == n * (n - 1) * (n - 2) // 6 + 1
 
 
 def test_small_cases():
