@@ -312,6 +312,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   void *X;
   uint32_t *adj;
   int32_t *adjpre, *deg, *up, *nbr_ptr;
+  int2 *adjx;  // {row word, prefix count} pairs for the max-edge final write
   int64_t *lex_ptr;
   // The edge sort's scratch (digit histogram, tile status) and the edge-grade
   // look-back words, sized for every possible edge, follow the status word
@@ -330,6 +331,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   if (!in_place) VR_TRY(F ? ws.alloc((float **)&X, nd) : ws.alloc((int32_t **)&X, nd));
   VR_TRY(ws.alloc(&adj, (int64_t)n * W));
   VR_TRY(ws.alloc(&adjpre, (int64_t)n * W));
+  VR_TRY(ws.alloc(&adjx, (int64_t)n * W));
   VR_TRY(ws.alloc(&deg, n));
   VR_TRY(ws.alloc(&up, n));
   VR_TRY(ws.alloc(&nbr_ptr, n + 1));
@@ -429,7 +431,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_CUDA(cudaGetLastError());
   prof.end();
   prof.begin("row_counts");
-  launch_dep(k_rows_scan, (n + 7) / 8, 256, 0, s, adj, n, W, adjpre, deg, up, nbr_ptr, lex_ptr, st);
+  launch_dep(k_rows_scan, (n + 7) / 8, 256, 0, s, adj, n, W, adjpre, deg, up, nbr_ptr, lex_ptr, st, adjx);
   count_launch();
   VR_CUDA(cudaGetLastError());
   prof.end();
@@ -446,7 +448,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_CUDA(cudaMemsetAsync(&st->flags, 0, sizeof(int32_t), s));
     dist_dispatch<F>(X, n, d, W, cap, adj, st, s);
     count_launch();
-    launch_dep(k_rows_scan, (n + 7) / 8, 256, 0, s, adj, n, W, adjpre, deg, up, nbr_ptr, lex_ptr, st);
+    launch_dep(k_rows_scan, (n + 7) / 8, 256, 0, s, adj, n, W, adjpre, deg, up, nbr_ptr, lex_ptr, st, adjx);
     count_launch();
     VR_TRY(publish_status(st, sm, s));
     if (early_keys) {
@@ -612,7 +614,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       prof.end();
     }
     prof.begin("tri_count");
-    const EdgeIndex exc{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
+    const EdgeIndex exc{adjx, adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
     if (eidx)
       launch_dep(k_tri_count<true>, grid_for(E, 8, 32), 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
                  nbr_ord, st, tcnt, force_lex, exc, (const int64_t *)lex_ptr, sparse_rows, sx);
@@ -631,7 +633,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(publish_status(st, sm, s));
   auto lex_tri_gen = [&](int64_t tcap) -> vr_status {
     prof.begin("tri_lex_gen");
-    const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
+    const EdgeIndex ex{adjx, adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
     if (eidx)
       launch_dep(k_lex_tri_gen<true>, grid_for(E, 8, 32), 256, 0, s, lexe, egrade, E, adj, adjpre, W, nbr_ptr,
                  nbr_ord, toff, tcap, tk, ex, st, force_lex, (const int64_t *)lex_ptr, sparse_rows);
@@ -645,7 +647,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   };
   // Max-edge key generation (returns at once if the device chose lex order):
   // into the bound-sized buffer before the host's wait, or after it.
-  const EdgeIndex exm{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
+  const EdgeIndex exm{adjx, adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
   auto me_gen = [&](int64_t cap) -> vr_status {
     prof.begin("tri_gen");
     // 16-byte chunks per lane and row: Wp / 16 words rounded up to whole
@@ -754,7 +756,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       // (The triangle generator is latency-bound: counting the sort's
       // histogram inside it cost more than the sort's own histogram pass.)
       if (!early_tri) VR_TRY(lex_tri_gen(T));
-      const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
+      const EdgeIndex ex{adjx, adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
       if (tets) VR_CUDA(cudaMemcpyAsync(tk_lex, tk, sizeof(uint64_t) * T, cudaMemcpyDeviceToDevice, s));
       prof.begin("tri_grade_sort");
       static const char *const ttag[2] = {"tri_sort.hist", "tri_sort.pass"};
@@ -862,7 +864,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_CUDA(cudaMemsetAsync(qcol, 0, sizeof(int64_t), s));
     } else {
       prof.begin("tet_gen");
-      const EdgeIndex ex{adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
+      const EdgeIndex ex{adjx, adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
       if (eidx)
         launch_dep(k_tet_gen<true>, grid_for(T, 8, 32), 256, 0, s, tk_lex, T, adj, W, tgrade, ordidx, egrade, ex,
                    off4, T4, keys4, lex4, packed ? 1 : 0, st);

@@ -316,9 +316,11 @@ __global__ void __launch_bounds__(256) k_dist_bitmap(const void *Xv, int n, int 
 // Row counts and both scans in one launch: every CTA does its rows; the last CTA
 // to finish (ticket after a fence; no CTA waits for another) scans deg and up
 // (n <= 8192) into nbr_ptr and lex_ptr and stores the edge count in st->E.
+// adjx (optional): each row word beside its prefix count, {word, prefix},
+// so that one 8-byte load gives a neighbour's rank (the max-edge final write).
 static __global__ void __launch_bounds__(256) k_rows_scan(const uint32_t *adj, int n, int W, int32_t *adjpre,
                                                           int32_t *deg, int32_t *up, int32_t *nbr_ptr,
-                                                          int64_t *lex_ptr, DevStatus *st) {
+                                                          int64_t *lex_ptr, DevStatus *st, int2 *adjx) {
   pdl_entry();
   if (build_failed(st)) return;
   __shared__ int64_t sh[33];
@@ -332,7 +334,10 @@ static __global__ void __launch_bounds__(256) k_rows_scan(const uint32_t *adj, i
       const uint32_t word = w < W ? adj[(int64_t)i * W + w] : 0u;
       const int c = __popc(word);
       const int inc = warp_incl_scan(c);
-      if (w < W) adjpre[(int64_t)i * W + w] = carry + inc - c;
+      if (w < W) {
+        adjpre[(int64_t)i * W + w] = carry + inc - c;
+        if (adjx) adjx[(int64_t)i * W + w] = make_int2((int)word, carry + inc - c);
+      }
       carry += __shfl_sync(0xffffffffu, inc, 31);
       uint32_t m;
       const int lo = w * 32;
@@ -1112,6 +1117,7 @@ __device__ __forceinline__ int64_t lex_pos(int a, int b, const uint32_t *adj, co
 // one (n <= DENSE_MAX_N), else through the neighbour CSR.
 constexpr int DENSE_MAX_N = 8192;  // every cloud (n <= 8192): two n x n int32 tables, at most 512 MB
 struct EdgeIndex {
+  const int2 *adjx;  // {row word, prefix count} pairs, or null
   const uint32_t *adj;
   const int32_t *adjpre;
   const int32_t *nbr_ptr;
@@ -1662,8 +1668,10 @@ __device__ __forceinline__ void tri_final_me_one(uint64_t k, int zbits, const in
   const int z = (int)(k & ((1ull << min(zbits, 16)) - 1ull));  // z < n <= 2^16
   const int2 xy = ((const int2 *)everts)[e];
   const int x = xy.x, y = xy.y;
-  const int32_t oxz = ex.ord<false>(x, z);
-  const int32_t oyz = ex.ord<false>(y, z);
+  const int2 px = ex.adjx[(int64_t)x * ex.W + (z >> 5)], py = ex.adjx[(int64_t)y * ex.W + (z >> 5)];
+  const uint32_t below = (1u << (z & 31)) - 1u;
+  const int32_t oxz = ex.nbr_ord[ex.nbr_ptr[x] + px.y + __popc((uint32_t)px.x & below)];
+  const int32_t oyz = ex.nbr_ord[ex.nbr_ptr[y] + py.y + __popc((uint32_t)py.x & below)];
   if (z < x) { v[0] = z; v[1] = x; v[2] = y; }
   else if (z < y) { v[0] = x; v[1] = z; v[2] = y; }
   else { v[0] = x; v[1] = y; v[2] = z; }
