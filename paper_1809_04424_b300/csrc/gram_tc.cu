@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_bitmap_tc(const __grid_cons
     for (int c0 = half * (TC_TILE / 2); c0 < (half + 1) * (TC_TILE / 2); c0 += 32) {
       float g[32];
       tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, g);
-      uint32_t rowword = 0, mirror = 0;
+      uint32_t rowword = 0, bandword = 0;
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int j = tj * TC_TILE + c0 + c;
@@ -382,21 +382,34 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_bitmap_tc(const __grid_cons
             kept = cap.keep_all || v <= cap.r2i;
           }
         }
-        if constexpr (F && !VALIDATE) {
-          const uint32_t bm = __ballot_sync(0xffffffffu, in_band);
-          if (bm) {
-            uint64_t at = 0;
-            if (lane == __ffs(bm) - 1) at = atomicAdd((unsigned long long *)&st->band_count, (unsigned long long)__popc(bm));
-            at = __shfl_sync(0xffffffffu, at, __ffs(bm) - 1) + __popc(bm & lanemask_lt());
-            if (in_band) {
-              if (at < band_cap) band[at] = ((uint64_t)i << 32) | (uint32_t)j;
-              else raise_flag(st, F_OVERFLOW);
-            }
+        rowword |= (uint32_t)kept << c;
+        bandword |= (uint32_t)in_band << c;
+      }
+      // The chunk's near-cap pairs: one warp-aggregated append.
+      if constexpr (F && !VALIDATE) {
+        const int nb = __popc(bandword);
+        const int incl = warp_incl_scan(nb);
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (tot) {
+          uint64_t at = 0;
+          if (lane == 31) at = atomicAdd((unsigned long long *)&st->band_count, (unsigned long long)tot);
+          at = __shfl_sync(0xffffffffu, at, 31) + (uint64_t)(incl - nb);
+          for (uint32_t m = bandword; m; m &= m - 1, ++at) {
+            const int j = tj * TC_TILE + c0 + __ffs(m) - 1;
+            if (at < band_cap) band[at] = ((uint64_t)i << 32) | (uint32_t)j;
+            else raise_flag(st, F_OVERFLOW);
           }
         }
-        rowword |= (uint32_t)kept << c;
-        const uint32_t b = __ballot_sync(0xffffffffu, kept);
-        if (lane == c) mirror = b;
+      }
+      // Mirrored column words: the 32 x 32 bit transpose of the lanes' row
+      // words (lane c gets bit r = row r's bit c), by five shuffle rounds.
+      uint32_t mirror = rowword;
+#pragma unroll
+      for (int sh = 16; sh >= 1; sh >>= 1) {
+        const uint32_t m = sh == 16 ? 0x0000ffffu : sh == 8 ? 0x00ff00ffu : sh == 4 ? 0x0f0f0f0fu
+                         : sh == 2 ? 0x33333333u : 0x55555555u;
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, mirror, sh);
+        mirror = (lane & sh) ? (mirror & ~m) | ((y & ~m) >> sh) : (mirror & m) | ((y & m) << sh);
       }
       // Padded columns of the last tile map past the row's W words: skip them.
       const int wr = (tj * TC_TILE + c0) / 32, wm = (ti * TC_TILE + q * 32) / 32;
