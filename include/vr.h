@@ -318,6 +318,17 @@ VR_API vr_status vr_set_gram_path(int32_t mode);
  * identical either way.  VR_ERR_ARG for any other value. */
 VR_API vr_status vr_set_tri_key_width(int32_t bytes);
 
+/* Max-edge triangle key space (no counterpart in the paper): 0 = automatic,
+ * the generator runs before any triangle count and claims room for each
+ * edge's third vertices (16 bits each) from striped counters in the
+ * bound-sized key buffer, its exact per-edge counts then scanned into the
+ * output offsets; 1 = counted, a triangle count and its scan first, then the
+ * generator writes keys at the scanned offsets; 2 = claimed with tiny
+ * sub-buffers (64 slots per counter), so that claims run out and the counted
+ * generator takes over, for tests of that path.  Process-wide; results are
+ * identical in every mode.  VR_ERR_ARG for any other value. */
+VR_API vr_status vr_set_tri_claim(int32_t mode);
+
 /* Float split of the tensor-core distance tiles (no counterpart in the
  * paper): 2 = two-way, y = hi + lo (bf16 each; products hi.hi, hi.lo,
  * lo.hi; the default), 3 = three-way, y = hi + mid + lo (six products).

@@ -311,6 +311,16 @@ def vr_set_tri_key_width(nbytes: int) -> None:
     _check(L.vr_set_tri_key_width(int(nbytes)))
 
 
+def vr_set_tri_claim(mode: int) -> None:
+    """Max-edge key space: 0 automatic (claimed by the generator, no count
+    first), 1 counted, 2 claimed with tiny sub-buffers (the counted generator
+    takes over; tests)."""
+    L = lib()
+    L.vr_set_tri_claim.argtypes = [ctypes.c_int32]
+    L.vr_set_tri_claim.restype = ctypes.c_int
+    _check(L.vr_set_tri_claim(int(mode)))
+
+
 def vr_complex_dim(handle, k: int) -> DimView:
     v = DimView()
     _check(lib().vr_complex_dim(ctypes.c_void_p(handle), k, ctypes.byref(v)))

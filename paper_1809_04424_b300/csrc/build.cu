@@ -231,6 +231,14 @@ constexpr int64_t EARLY_TRI_MAX_E = int64_t(1) << 17;
 // fit), 8 = always (e << 32) | z.  Set by vr_set_tri_key_width.
 static std::atomic<int> g_tri_key_width{0};
 
+// Max-edge key space: 0 = automatic (claimed by the generator, no triangle
+// count before it, whenever the wedge-bound buffer is taken), 1 = counted
+// (count, scan, then the generator at the scanned offsets), 2 = claimed with
+// sub-buffers of CLAIM_TEST_SLOTS slots, so that claims run out and the
+// counted generator takes over (tests).  Set by vr_set_tri_claim.
+static std::atomic<int> g_tri_claim{0};
+constexpr int64_t CLAIM_TEST_SLOTS = 64;
+
 // Max-edge order: the key generator is enqueued before the host reads T when
 // its buffer, sized by the wedge bound T <= sum_v C(deg v, 2) / 3, stays
 // under this many bytes (4000-point float cloud: 33.0M keys for 19.8M
@@ -322,7 +330,9 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   RadixScratch rs{};
   uint64_t *eg_lb;  // look-back status of the edge-grade tiles + their ticket
   ws.begin();
+  uint32_t *claim_ctr;  // the claiming generator's counters (zeroed with the status word)
   VR_TRY(ws.alloc(&st, 1));
+  VR_TRY(ws.alloc(&claim_ctr, (CLAIM_CTRS + 1) * 32));  // + the final write's group ticket
   VR_TRY(ws.alloc(&rs.meta, rs_meta_bytes(E_ub)));
   VR_TRY(ws.alloc(&eg_lb, eg_words));
   // Staged points: int32 input is used in place (the build only reads it
@@ -553,7 +563,22 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   const int64_t T_wedge = wedges / 3 + 1;
   const bool early_gen = want_snap && (double)T_wedge * (me_key32 ? 4 : 8) <= (double)EARLY_GEN_MAX_BYTES;
   uint64_t *tk_me = nullptr;  // max-edge keys
-  if (early_gen) VR_TRY(ws.alloc(&tk_me, me_key32 ? (T_wedge + 1) / 2 : T_wedge));
+  // Claimed key space (early_gen, unless counted keys are asked for): the
+  // generator runs before any triangle count, taking room for each edge's
+  // third vertices (16 bits each) from a buffer of 2 T_wedge slots (kpos[e]
+  // locates them), and the final write reads them directly; the key buffer
+  // is then needed only if a claim runs out, and is allocated after the
+  // host's wait.  Otherwise the keys go to the bound-sized buffer.
+  const int claim_mode = g_tri_claim.load();
+  const bool claim = early_gen && claim_mode != 1;
+  const int64_t tz_slots = 2 * T_wedge;
+  int32_t *kpos = nullptr;
+  uint16_t *tz = nullptr;
+  if (early_gen && !claim) VR_TRY(ws.alloc(&tk_me, me_key32 ? (T_wedge + 1) / 2 : T_wedge));
+  if (claim) {
+    VR_TRY(ws.alloc(&kpos, E));
+    VR_TRY(ws.alloc(&tz, tz_slots));
+  }
   if (maxdim >= 2 && E > 0) {
     VR_TRY(ws.alloc(&tcnt, E));
     VR_TRY(ws.alloc(&toff, E + 1));
@@ -601,6 +626,45 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_CUDA(cudaMemcpyAsync(ecol, &zero64, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   }
 
+  // Max-edge key generation (returns at once if the device chose lex order):
+  // claimed (cl: before the triangle count, which then skips max-edge
+  // edges), or at the counted offsets into the bound-sized buffer before the
+  // host's wait, or after it.
+  const EdgeIndex exm{adjx, adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
+  const int64_t claim_sub = claim_mode == 2 ? CLAIM_TEST_SLOTS : tz_slots / CLAIM_CTRS;
+  const ClaimBuf cb{tz, kpos, tcnt, claim_ctr, claim_sub};
+  auto me_gen = [&](int64_t cap, bool cl) -> vr_status {
+    prof.begin("tri_gen");
+    // 16-byte chunks per lane and row: Wp / 16 words rounded up to whole
+    // chunks (a compile-time count per kernel).
+    const int k4 = ((((sx.Wp + 15) >> 4) + 3) & ~3) >> 2;
+    const unsigned g = grid_for(E, 8, 32);
+    auto go = [&](auto key, auto clt) {
+      using KT = decltype(key);
+      constexpr bool CL = decltype(clt)::value;
+      KT *tkk = (KT *)tk_me;
+      const int zb = sizeof(KT) == 4 ? me_zbits : 32;
+      if (k4 <= 1)
+        launch_dep(k_tri_gen_me<KT, 1, CL>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, cap, tkk, zb, sx, st,
+                   force_lex, cb);
+      else if (k4 == 2)
+        launch_dep(k_tri_gen_me<KT, 2, CL>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, cap, tkk, zb, sx, st,
+                   force_lex, cb);
+      else if (k4 == 3)
+        launch_dep(k_tri_gen_me<KT, 3, CL>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, cap, tkk, zb, sx, st,
+                   force_lex, cb);
+      else
+        launch_dep(k_tri_gen_me<KT, 4, CL>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, cap, tkk, zb, sx, st,
+                   force_lex, cb);
+    };
+    if (cl) go(uint32_t{0}, std::true_type{});
+    else if (me_key32) go(uint32_t{0}, std::false_type{});
+    else go(uint64_t{0}, std::false_type{});
+    count_launch();
+    VR_CUDA(cudaGetLastError());
+    prof.end();
+    return VR_OK;
+  };
   if (maxdim >= 2 && E > 0) {
     if (want_snap) {
       // Time-sliced adjacency for the max-edge enumeration (returns at once
@@ -613,14 +677,16 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       VR_CUDA(cudaGetLastError());
       prof.end();
     }
+    if (claim) VR_TRY(me_gen(0, true));
     prof.begin("tri_count");
     const EdgeIndex exc{adjx, adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
+    const int me_claimed = claim ? 1 : 0;
     if (eidx)
       launch_dep(k_tri_count<true>, grid_for(E, 8, 32), 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
-                 nbr_ord, st, tcnt, force_lex, exc, (const int64_t *)lex_ptr, sparse_rows, sx);
+                 nbr_ord, st, tcnt, force_lex, exc, (const int64_t *)lex_ptr, sparse_rows, sx, me_claimed);
     else
       launch_dep(k_tri_count<false>, grid_for(E, 8, 32), 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
-                 nbr_ord, st, tcnt, force_lex, exc, (const int64_t *)lex_ptr, sparse_rows, sx);
+                 nbr_ord, st, tcnt, force_lex, exc, (const int64_t *)lex_ptr, sparse_rows, sx, me_claimed);
     count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int64_t>(tcnt, toff, E, bs_e, s)));
     launch_dep(k_tri_groups, grid_for(E + 1, 256), 256, 0, s, gstart, tcnt, toff, tsmallq, tmidq, tbigq, st,
@@ -645,37 +711,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     prof.end();
     return VR_OK;
   };
-  // Max-edge key generation (returns at once if the device chose lex order):
-  // into the bound-sized buffer before the host's wait, or after it.
-  const EdgeIndex exm{adjx, adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
-  auto me_gen = [&](int64_t cap) -> vr_status {
-    prof.begin("tri_gen");
-    // 16-byte chunks per lane and row: Wp / 16 words rounded up to whole
-    // chunks (a compile-time count per kernel).
-    const int k4 = ((((sx.Wp + 15) >> 4) + 3) & ~3) >> 2;
-    const unsigned g = grid_for(E, 8, 32);
-    auto go = [&](auto key) {
-      using KT = decltype(key);
-      KT *tkk = (KT *)tk_me;
-      const int zb = sizeof(KT) == 4 ? me_zbits : 32;
-      if (k4 <= 1)
-        launch_dep(k_tri_gen_me<KT, 1>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, cap, tkk, zb, sx, st, force_lex);
-      else if (k4 == 2)
-        launch_dep(k_tri_gen_me<KT, 2>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, cap, tkk, zb, sx, st, force_lex);
-      else if (k4 == 3)
-        launch_dep(k_tri_gen_me<KT, 3>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, cap, tkk, zb, sx, st, force_lex);
-      else
-        launch_dep(k_tri_gen_me<KT, 4>, g, 256, 0, s, everts, E, W, n, nbr_ptr, toff, cap, tkk, zb, sx, st, force_lex);
-    };
-    if (me_key32) go(uint32_t{0});
-    else go(uint64_t{0});
-    count_launch();
-    VR_CUDA(cudaGetLastError());
-    prof.end();
-    return VR_OK;
-  };
   if (early_tri) VR_TRY(lex_tri_gen(T_cap));
-  if (early_gen) VR_TRY(me_gen(T_wedge));
+  if (early_gen && !claim) VR_TRY(me_gen(T_wedge, false));
   VR_TRY(wait_status(sm, s));
   const int64_t ngrades = E > 0 ? hst->ngrades : 1;
   const int64_t T = (maxdim >= 2 && E > 0) ? hst->T : 0;
@@ -709,7 +746,8 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   int32_t *ordidx = nullptr, *cnt4 = nullptr;
   int64_t *off4 = nullptr, *bs_t = nullptr;
   if (T > 0 && lexm && !early_tri) VR_TRY(ws.alloc(&tk, T));  // lex keys
-  if (T > 0 && !lexm && !early_gen) VR_TRY(ws.alloc(&tk_me, me_key32 ? (T + 1) / 2 : T));
+  const bool claimed = claim && !(hst->flags & F_CLAIM);  // third vertices in claimed space
+  if (T > 0 && !lexm && (!early_gen || (claim && !claimed))) VR_TRY(ws.alloc(&tk_me, me_key32 ? (T + 1) / 2 : T));
   if (early_gen && T > T_wedge) {
     set_error("%lld triangles exceed their bound %lld", (long long)T, (long long)T_wedge);
     return VR_ERR_INTERNAL;
@@ -776,9 +814,16 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       // Max-edge order: keys in final order from the time-sliced adjacency
       // (generated above when the bound-sized buffer was taken), then the
       // final write; tie groups merged after.
-      if (!early_gen) VR_TRY(me_gen(T));
+      // Claimed third vertices go straight to the final write; if a claim
+      // ran out, the counted generator writes keys at the scanned offsets
+      // (the claiming run's counts are exact either way).
+      if (!early_gen || (claim && !claimed)) VR_TRY(me_gen(T, false));
       prof.begin("tri_final");
-      if (me_key32)
+      if (claimed)
+        launch_dep(k_tri_final_grp, grid_for((E + 31) / 32, 8, 4), 256, 0, s, (const uint16_t *)tz,
+                   (const int32_t *)kpos, (const int32_t *)tcnt, (const int64_t *)toff, E, everts, egrade, exm,
+                   tverts, tgrade, tcol, trow, claim_ctr + CLAIM_CTRS * 32, st);
+      else if (me_key32)
         launch_dep(k_tri_final_me<uint32_t>, grid_for((T + 3) / 4, 256), 256, 0, s, (const uint32_t *)tk_me, me_zbits,
                    T, everts, egrade, exm, tverts, tgrade, tcol, trow, st);
       else
@@ -946,6 +991,15 @@ vr_status build_cloud(const void *dpts, int32_t n, int32_t d, vr_dtype dtype, in
 }
 
 }  // namespace vr
+
+extern "C" vr_status vr_set_tri_claim(int32_t mode) {
+  if (mode < 0 || mode > 2) {
+    vr::set_error("triangle key space mode %d: 0 (automatic), 1 (counted) or 2 (claimed, test sub-buffers)", mode);
+    return VR_ERR_ARG;
+  }
+  vr::g_tri_claim.store(mode);
+  return VR_OK;
+}
 
 extern "C" vr_status vr_set_tri_key_width(int32_t bytes) {
   if (bytes != 0 && bytes != 8) {

@@ -1223,7 +1223,7 @@ static __global__ void __launch_bounds__(256, 6) k_tri_count(const int32_t *ever
                                                           const int32_t *nbr_ptr, const int32_t *nbr_ord,
                                                           const DevStatus *st, int32_t *tcnt, int force_lex,
                                                           EdgeIndex ex, const int64_t *lex_ptr, int sparse,
-                                                          SnapIdx sx) {
+                                                          SnapIdx sx, int me_claimed) {
   pdl_entry();
   if (build_failed(st)) return;
   const int l = lane_id();
@@ -1311,6 +1311,7 @@ static __global__ void __launch_bounds__(256, 6) k_tri_count(const int32_t *ever
   // edge per 8 lanes (4 per warp): every load of an edge is independent of
   // the others, so each lane keeps many in flight (no shared memory, no
   // dependent chain beyond the edge's endpoints and bucket bounds).
+  if (me_claimed) return;  // the claiming generator has written the counts
   const int sub = l >> 3, sl = l & 7;
   for (int64_t e = (blockIdx.x * 8 + (threadIdx.x >> 5)) * 4 + sub; e - sub < E; e += nwarps * 4) {
     int cnt = 0;
@@ -1364,14 +1365,32 @@ static __global__ void __launch_bounds__(256, 6) k_tri_count(const int32_t *ever
 // every lane's run of keys, which the lane writes in order.  The keys are
 // in final (max-edge) order: no sort follows.
 constexpr int MEG_KMAX = VR_MAX_POINTS / 32 / 16;  // words per lane and row at most
+
+// Claimed key space (the generator run before any triangle count): a warp
+// takes the room for its two edges' third vertices from one of CLAIM_CTRS
+// counters (one 128-byte line each, chosen by the warp, so the atomics
+// spread over L2), each owning a sub-buffer of sub_cap 16-bit slots.  Edge
+// e's third vertices, ascending, go to tz[kpos[e]] on and its count to
+// tcnt[e]; a claim past its sub-buffer raises F_CLAIM and writes no vertex
+// (the counts stay exact; the host then generates keys the counted way).
+constexpr int CLAIM_CTRS = 32;
+struct ClaimBuf {
+  uint16_t *tz;
+  int32_t *kpos;
+  int32_t *tcnt;
+  uint32_t *ctr;    // CLAIM_CTRS counters at a stride of 32 words, zero at the start
+  int64_t sub_cap;  // 16-bit slots per counter
+};
+
 // KT: the key word (see k_tri_final_me); T: the key buffer's capacity in keys.
 // K4: 16-byte chunks per lane and row, (Wp / 16 rounded up to whole chunks)
-// / 4, from 1 to 4 (Wp <= 256).
-template <typename KT, int K4>
+// / 4, from 1 to 4 (Wp <= 256).  CL: claimed key space (ClaimBuf; toff,
+// tkeys, T and zbits unused), else keys at toff[e] from the triangle count.
+template <typename KT, int K4, bool CL>
 static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts, int64_t E, int W, int n,
                                                            const int32_t *nbr_ptr, const int64_t *toff, int64_t T,
                                                            KT *tkeys, int zbits, SnapIdx sx, DevStatus *st,
-                                                           int force_lex) {
+                                                           int force_lex, ClaimBuf cb) {
   pdl_entry();
   if (build_failed(st)) return;
   if (lex_mode(E, st->ngrades, force_lex)) return;  // (a launch ahead of the host's decision)
@@ -1448,7 +1467,30 @@ static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts
       const int v = __shfl_up_sync(0xffffffffu, inc, d, 16);
       if (s16 >= d) inc += v;
     }
-    if (live && c) {
+    if constexpr (CL) {
+      // The half-warps' totals; one claim per warp for both edges.
+      const int t0 = __shfl_sync(0xffffffffu, inc, 15), t1 = __shfl_sync(0xffffffffu, inc, 31);
+      const int hw = (int)((blockIdx.x * 8 + wid) % CLAIM_CTRS);
+      uint32_t base = 0;
+      if (l == 0 && t0 + t1 > 0) base = atomicAdd(cb.ctr + hw * 32, (uint32_t)(t0 + t1));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      const bool fits = (int64_t)base + t0 + t1 <= cb.sub_cap;
+      const int64_t hb = (int64_t)hw * cb.sub_cap + base + (half ? t0 : 0);
+      if (live && s16 == 0) {
+        cb.tcnt[e] = half ? t1 : t0;
+        cb.kpos[e] = (int32_t)hb;
+      }
+      if (!fits) {
+        if (l == 0) raise_flag(st, F_CLAIM);
+      } else if (live && c) {
+        unsigned short *out = (unsigned short *)cb.tz + hb + inc - c;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const uint32_t zb = (uint32_t)(w0 + k) * 32u - 1u;
+          for (uint32_t mm = wx[k]; mm; mm &= mm - 1) __stcs(out++, (unsigned short)(zb + __ffs(mm)));
+        }
+      }
+    } else if (live && c) {
       const int64_t p = toff[e] + inc - c;
       if (p + c <= T) {
         if constexpr (sizeof(KT) == 8) {
@@ -1661,13 +1703,10 @@ static __global__ void __launch_bounds__(256) k_tri_final(const uint64_t *tkeys,
 // cost a 32-byte sector per lookup.  Same store pattern as k_tri_final (128
 // triangles per warp, vertices and rows staged in shared memory for 16-byte
 // stores).
-__device__ __forceinline__ void tri_final_me_one(uint64_t k, int zbits, const int32_t *everts,
-                                                 const int32_t *egrade, const EdgeIndex &ex, int32_t *v, int32_t *r,
-                                                 int32_t &g) {
-  const int32_t e = (int32_t)(k >> zbits);
-  const int z = (int)(k & ((1ull << min(zbits, 16)) - 1ull));  // z < n <= 2^16
-  const int2 xy = ((const int2 *)everts)[e];
-  const int x = xy.x, y = xy.y;
+// Triangle {x, y, z} with largest edge e = (x, y): sorted vertices and the
+// ascending order indices of its faces.
+__device__ __forceinline__ void tri_final_xyz(int32_t e, int x, int y, int z, const EdgeIndex &ex, int32_t *v,
+                                              int32_t *r) {
   const int2 px = ex.adjx[(int64_t)x * ex.W + (z >> 5)], py = ex.adjx[(int64_t)y * ex.W + (z >> 5)];
   const uint32_t below = (1u << (z & 31)) - 1u;
   const int32_t oxz = ex.nbr_ord[ex.nbr_ptr[x] + px.y + __popc((uint32_t)px.x & below)];
@@ -1676,7 +1715,19 @@ __device__ __forceinline__ void tri_final_me_one(uint64_t k, int zbits, const in
   else if (z < y) { v[0] = x; v[1] = z; v[2] = y; }
   else { v[0] = x; v[1] = y; v[2] = z; }
   r[0] = min(oxz, oyz); r[1] = max(oxz, oyz); r[2] = e;
+}
+
+__device__ __forceinline__ void tri_final_ez(int32_t e, int z, const int32_t *everts, const int32_t *egrade,
+                                             const EdgeIndex &ex, int32_t *v, int32_t *r, int32_t &g) {
+  const int2 xy = ((const int2 *)everts)[e];
+  tri_final_xyz(e, xy.x, xy.y, z, ex, v, r);
   g = egrade[e];
+}
+
+__device__ __forceinline__ void tri_final_me_one(uint64_t k, int zbits, const int32_t *everts,
+                                                 const int32_t *egrade, const EdgeIndex &ex, int32_t *v, int32_t *r,
+                                                 int32_t &g) {
+  tri_final_ez((int32_t)(k >> zbits), (int)(k & ((1ull << min(zbits, 16)) - 1ull)), everts, egrade, ex, v, r, g);
 }
 
 // KT: the key word, uint64_t ((e << 32) | z, zbits = 32) or uint32_t
@@ -1743,6 +1794,109 @@ static __global__ void __launch_bounds__(256, 4) k_tri_final_me(const KT *tkeys,
     trow[3 * p] = r[0]; trow[3 * p + 1] = r[1]; trow[3 * p + 2] = r[2];
     tgrade[p] = g;
     tcolptr[p] = 3 * p;
+  }
+}
+
+// Final write over claimed key space.  Edge e's third vertices are the
+// 16-bit values at tz[kpos[e]] on (tcnt[e] of them, ascending) and its
+// triangles take output positions toff[e] on.  A warp takes 32 consecutive
+// edges: lane l holds edge e0 + l's endpoints, grade, count and key position
+// in registers, and the group's triangles fill the contiguous output range
+// toff[e0] .. toff[e0] + S.  The warp walks that range by the 128-position
+// chunks of the whole output; lane l takes positions l, l + 32, l + 64,
+// l + 96 of a chunk and finds each one's edge by a five-step search over the
+// lanes' inclusive counts (shuffles only), so the only load before the face
+// lookups is the third vertex.  The faces come from the CSR rows of x and y
+// as in k_tri_final_me; chunks inside the range are staged in shared memory
+// for 16-byte stores, the (at most two) chunks the range shares with its
+// neighbours' are stored position by position.  ticket: a zeroed word.
+static __global__ void __launch_bounds__(256, 4) k_tri_final_grp(const uint16_t *__restrict__ tz,
+                                                                 const int32_t *__restrict__ kpos,
+                                                                 const int32_t *__restrict__ tcnt,
+                                                                 const int64_t *__restrict__ toff, int64_t E,
+                                                                 const int32_t *everts, const int32_t *egrade,
+                                                                 EdgeIndex ex, int32_t *tverts, int32_t *tgrade,
+                                                                 int64_t *tcolptr, int32_t *trow,
+                                                                 uint32_t *ticket, const DevStatus *st) {
+  pdl_entry();
+  if (build_failed(st)) return;
+  __shared__ int4 sv[8][96], sr[8][96];  // per warp: 128 triangles x 3 ints
+  const int wid = threadIdx.x >> 5, l = lane_id();
+  int32_t *svi = (int32_t *)sv[wid], *sri = (int32_t *)sr[wid];
+  // Groups are taken from a ticket (zero at the start), last group first:
+  // the late edges of the filtration carry most triangles, so the heavy
+  // groups go out first and the light ones even out the end.
+  const int64_t ngroups = (E + 31) / 32;
+  for (;;) {
+    uint32_t tk = 0;
+    if (l == 0) tk = atomicAdd(ticket, 1u);
+    tk = __shfl_sync(0xffffffffu, tk, 0);
+    if ((int64_t)tk >= ngroups) break;
+    const int64_t e0 = (ngroups - 1 - (int64_t)tk) * 32;
+    const int64_t e = e0 + l;
+    const bool ev = e < E;
+    const int32_t c = ev ? tcnt[e] : 0;
+    const int32_t kp = ev ? kpos[e] : 0;
+    const int2 xy = ev ? ((const int2 *)everts)[e] : make_int2(0, 0);
+    const int32_t ge = ev ? egrade[e] : 0;
+    const int64_t o0 = toff[e0];
+    int32_t incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t t = __shfl_up_sync(0xffffffffu, incl, d);
+      if (l >= d) incl += t;
+    }
+    const int32_t excl = incl - c;
+    const int64_t oend = o0 + __shfl_sync(0xffffffffu, incl, 31);
+    for (int64_t base = o0 & ~int64_t(127); base < oend; base += 128) {
+      int32_t v[12], r[12], g[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t p = base + 32 * u + l;
+        const bool ok = p >= o0 && p < oend;
+        const int32_t f = ok ? (int32_t)(p - o0) : 0;
+        int j = 0;  // edges before f's: inclusive counts at or below f (f < S keeps j <= 31)
+#pragma unroll
+        for (int step = 16; step; step >>= 1)
+          if (__shfl_sync(0xffffffffu, incl, j + step - 1) <= f) j += step;
+        const int32_t ej = __shfl_sync(0xffffffffu, excl, j), kj = __shfl_sync(0xffffffffu, kp, j);
+        const int xj = __shfl_sync(0xffffffffu, xy.x, j), yj = __shfl_sync(0xffffffffu, xy.y, j);
+        g[u] = __shfl_sync(0xffffffffu, ge, j);
+        if (ok) tri_final_xyz((int32_t)(e0 + j), xj, yj, (int)tz[kj + (f - ej)], ex, v + 3 * u, r + 3 * u);
+      }
+      if (base >= o0 && base + 128 <= oend) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int t = 32 * u + l;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            svi[3 * t + k] = v[3 * u + k];
+            sri[3 * t + k] = r[3 * u + k];
+          }
+          __stcs(tgrade + base + t, g[u]);
+          __stcs((long long *)tcolptr + base + t, (long long)(3 * (base + t)));
+        }
+        __syncwarp();
+        int4 *gv = (int4 *)(tverts + 3 * base), *gr = (int4 *)(trow + 3 * base);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          __stcs(gv + 32 * k + l, sv[wid][32 * k + l]);
+          __stcs(gr + 32 * k + l, sr[wid][32 * k + l]);
+        }
+        __syncwarp();
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t p = base + 32 * u + l;
+          if (p >= o0 && p < oend) {
+            tverts[3 * p] = v[3 * u]; tverts[3 * p + 1] = v[3 * u + 1]; tverts[3 * p + 2] = v[3 * u + 2];
+            trow[3 * p] = r[3 * u]; trow[3 * p + 1] = r[3 * u + 1]; trow[3 * p + 2] = r[3 * u + 2];
+            tgrade[p] = g[u];
+            tcolptr[p] = 3 * p;
+          }
+        }
+      }
+    }
   }
 }
 

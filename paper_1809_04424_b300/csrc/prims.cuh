@@ -51,6 +51,7 @@ enum : int32_t {
   F_TIMEOUT = 16,    // a bounded wait gave up                -> VR_ERR_TIMEOUT
   F_OVERFLOW = 32,   // an output arena was too small         -> retried by host
   F_DMAT = 64,       // distance matrix asymmetric or negative -> VR_ERR_ARG
+  F_CLAIM = 128,     // claimed triangle key space ran out    -> keys regenerated by host
 };
 
 // Device-resident status and counters of one build (read back at sync points).

@@ -254,6 +254,36 @@ def test_max_edge_key_widths(torch, width):
     assert E >= (1 << 15) and 2 * E >= 1200 * ((1200 + 31) // 32)
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_max_edge_key_space_modes(torch, mode):
+    """The 1200-point float cloud (max-edge order) with its keys in claimed
+    space (the generator before any count, then a compaction into keys in
+    output order), counted (count, scan, generator), and claimed with sub-buffers too
+    small for the claims (the counted generator takes over from the claiming
+    run's counts): every output in full."""
+    c = synth.config3(n=1200)
+    vr.vr_set_tri_claim(mode)
+    try:
+        check(torch, c.points, 2, c.maxrad)
+    finally:
+        vr.vr_set_tri_claim(0)
+
+
+def test_max_edge_claimed_ragged_chunks(torch):
+    """1500 uniform float32 points in d = 32 capped at 4% of pairs: few
+    triangles per edge and many edges with none, so each 32-edge group of the
+    compaction of claimed third vertices has short, uneven runs; a ragged
+    triangle count.  Max-edge order, claimed key space, in full."""
+    pts = synth.rng(77).uniform(-1.0, 1.0, size=(1500, 32)).astype(np.float32)
+    d2 = ((pts[:, None, :].astype(np.float64) - pts[None, :, :]) ** 2).sum(-1)[np.triu_indices(1500, 1)]
+    cap2 = float(np.quantile(d2, 0.04))
+    g = check(torch, pts, 2, math.sqrt(cap2))
+    T = len(g[2]["grade"])
+    E = len(g[1]["grade"])
+    assert E >= (1 << 15) and 2 * E >= 1500 * ((1500 + 31) // 32)  # max-edge order
+    assert T % 128 != 0 and T < 32 * E
+
+
 @pytest.mark.parametrize("n", [4500, 6200])
 def test_max_edge_wide_rows(torch, n):
     """Gaussian-mixture clouds (d = 32, 5% cap) whose snapshot rows take 3
