@@ -1705,16 +1705,22 @@ static __global__ void __launch_bounds__(256) k_tri_final(const uint64_t *tkeys,
 // stores).
 // Triangle {x, y, z} with largest edge e = (x, y): sorted vertices and the
 // ascending order indices of its faces.
-__device__ __forceinline__ void tri_final_xyz(int32_t e, int x, int y, int z, const EdgeIndex &ex, int32_t *v,
-                                              int32_t *r) {
+// npx, npy: nbr_ptr[x], nbr_ptr[y].
+__device__ __forceinline__ void tri_final_xyzn(int32_t e, int x, int y, int z, int32_t npx, int32_t npy,
+                                               const EdgeIndex &ex, int32_t *v, int32_t *r) {
   const int2 px = ex.adjx[(int64_t)x * ex.W + (z >> 5)], py = ex.adjx[(int64_t)y * ex.W + (z >> 5)];
   const uint32_t below = (1u << (z & 31)) - 1u;
-  const int32_t oxz = ex.nbr_ord[ex.nbr_ptr[x] + px.y + __popc((uint32_t)px.x & below)];
-  const int32_t oyz = ex.nbr_ord[ex.nbr_ptr[y] + py.y + __popc((uint32_t)py.x & below)];
+  const int32_t oxz = ex.nbr_ord[npx + px.y + __popc((uint32_t)px.x & below)];
+  const int32_t oyz = ex.nbr_ord[npy + py.y + __popc((uint32_t)py.x & below)];
   if (z < x) { v[0] = z; v[1] = x; v[2] = y; }
   else if (z < y) { v[0] = x; v[1] = z; v[2] = y; }
   else { v[0] = x; v[1] = y; v[2] = z; }
   r[0] = min(oxz, oyz); r[1] = max(oxz, oyz); r[2] = e;
+}
+
+__device__ __forceinline__ void tri_final_xyz(int32_t e, int x, int y, int z, const EdgeIndex &ex, int32_t *v,
+                                              int32_t *r) {
+  tri_final_xyzn(e, x, y, z, ex.nbr_ptr[x], ex.nbr_ptr[y], ex, v, r);
 }
 
 __device__ __forceinline__ void tri_final_ez(int32_t e, int z, const int32_t *everts, const int32_t *egrade,
@@ -1847,22 +1853,40 @@ static __global__ void __launch_bounds__(256, 4) k_tri_final_grp(const uint16_t 
       if (l >= d) incl += t;
     }
     const int32_t excl = incl - c;
+    const int32_t npx = ev ? ex.nbr_ptr[xy.x] : 0, npy = ev ? ex.nbr_ptr[xy.y] : 0;
     const int64_t oend = o0 + __shfl_sync(0xffffffffu, incl, 31);
-    for (int64_t base = o0 & ~int64_t(127); base < oend; base += 128) {
-      int32_t v[12], r[12], g[4];
+    // Position p's edge j (lanes' inclusive counts at or below f = p - o0;
+    // f < S keeps j <= 31) and third vertex, packed (j << 16) | z; the next
+    // chunk's are fetched before this chunk's faces are looked up.
+    auto fetch = [&](int64_t base, uint32_t *jz) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int64_t p = base + 32 * u + l;
         const bool ok = p >= o0 && p < oend;
         const int32_t f = ok ? (int32_t)(p - o0) : 0;
-        int j = 0;  // edges before f's: inclusive counts at or below f (f < S keeps j <= 31)
+        int j = 0;
 #pragma unroll
         for (int step = 16; step; step >>= 1)
           if (__shfl_sync(0xffffffffu, incl, j + step - 1) <= f) j += step;
         const int32_t ej = __shfl_sync(0xffffffffu, excl, j), kj = __shfl_sync(0xffffffffu, kp, j);
+        jz[u] = ((uint32_t)j << 16) | (ok ? (uint32_t)__ldcs(tz + kj + (f - ej)) : 0u);
+      }
+    };
+    uint32_t jzc[4];
+    fetch(o0 & ~int64_t(127), jzc);
+    for (int64_t base = o0 & ~int64_t(127); base < oend; base += 128) {
+      uint32_t jzn[4] = {0u, 0u, 0u, 0u};
+      if (base + 128 < oend) fetch(base + 128, jzn);
+      int32_t v[12], r[12], g[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t p = base + 32 * u + l;
+        const bool ok = p >= o0 && p < oend;
+        const int j = (int)(jzc[u] >> 16);
         const int xj = __shfl_sync(0xffffffffu, xy.x, j), yj = __shfl_sync(0xffffffffu, xy.y, j);
+        const int32_t nxj = __shfl_sync(0xffffffffu, npx, j), nyj = __shfl_sync(0xffffffffu, npy, j);
         g[u] = __shfl_sync(0xffffffffu, ge, j);
-        if (ok) tri_final_xyz((int32_t)(e0 + j), xj, yj, (int)tz[kj + (f - ej)], ex, v + 3 * u, r + 3 * u);
+        if (ok) tri_final_xyzn((int32_t)(e0 + j), xj, yj, (int)(jzc[u] & 0xffffu), nxj, nyj, ex, v + 3 * u, r + 3 * u);
       }
       if (base >= o0 && base + 128 <= oend) {
 #pragma unroll
@@ -1896,6 +1920,8 @@ static __global__ void __launch_bounds__(256, 4) k_tri_final_grp(const uint16_t 
           }
         }
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) jzc[u] = jzn[u];
     }
   }
 }
