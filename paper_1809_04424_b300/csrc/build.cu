@@ -632,13 +632,18 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   // host's wait, or after it.
   const EdgeIndex exm{adjx, adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
   const int64_t claim_sub = claim_mode == 2 ? CLAIM_TEST_SLOTS : tz_slots / CLAIM_CTRS;
-  const ClaimBuf cb{tz, kpos, tcnt, claim_ctr, claim_sub};
+  // The claiming generator runs one wave (five CTAs of 8 warps per SM at its
+  // register count); each warp claims slots in chunks whose total over all
+  // warps stays within the T_wedge slots of headroom (tz_slots >= T + T_wedge).
+  const unsigned g_claim = grid_for(E, 16, 5);
+  const int32_t claim_chunk = (int32_t)std::min<int64_t>(1024, T_wedge / ((int64_t)g_claim * 8));
+  const ClaimBuf cb{tz, kpos, tcnt, claim_ctr, claim_sub, claim_chunk};
   auto me_gen = [&](int64_t cap, bool cl) -> vr_status {
     prof.begin("tri_gen");
     // 16-byte chunks per lane and row: Wp / 16 words rounded up to whole
     // chunks (a compile-time count per kernel).
     const int k4 = ((((sx.Wp + 15) >> 4) + 3) & ~3) >> 2;
-    const unsigned g = grid_for(E, 8, 32);
+    const unsigned g = cl ? g_claim : grid_for(E, 8, 32);
     auto go = [&](auto key, auto clt) {
       using KT = decltype(key);
       constexpr bool CL = decltype(clt)::value;

@@ -1367,9 +1367,11 @@ static __global__ void __launch_bounds__(256, 6) k_tri_count(const int32_t *ever
 constexpr int MEG_KMAX = VR_MAX_POINTS / 32 / 16;  // words per lane and row at most
 
 // Claimed key space (the generator run before any triangle count): a warp
-// takes the room for its two edges' third vertices from one of CLAIM_CTRS
-// counters (one 128-byte line each, chosen by the warp, so the atomics
-// spread over L2), each owning a sub-buffer of sub_cap 16-bit slots.  Edge
+// takes room for its edges' third vertices from one of CLAIM_CTRS counters
+// (one 128-byte line each, chosen by the warp, so the atomics spread over
+// L2), each owning a sub-buffer of sub_cap 16-bit slots.  It claims `chunk`
+// slots at a time (or what its two current edges need, if more) and fills
+// them over its iterations, so most iterations make no global atomic.  Edge
 // e's third vertices, ascending, go to tz[kpos[e]] on and its count to
 // tcnt[e]; a claim past its sub-buffer raises F_CLAIM and writes no vertex
 // (the counts stay exact; the host then generates keys the counted way).
@@ -1380,6 +1382,7 @@ struct ClaimBuf {
   int32_t *tcnt;
   uint32_t *ctr;    // CLAIM_CTRS counters at a stride of 32 words, zero at the start
   int64_t sub_cap;  // 16-bit slots per counter
+  int32_t chunk;    // slots a warp claims at a time (more when its two edges need more)
 };
 
 // KT: the key word (see k_tri_final_me); T: the key buffer's capacity in keys.
@@ -1404,15 +1407,16 @@ static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts
   const int Wp = sx.Wp;
   uint32_t *dx = (uint32_t *)drow[wid][half], *dy = dx + WMAX;
   const int64_t nwarps = (int64_t)gridDim.x * 8;
-  for (int64_t e = (blockIdx.x * 8 + wid) * 2 + half; e - half < E; e += nwarps * 2) {
+  const int hw = (int)((blockIdx.x * 8 + wid) % CLAIM_CTRS);
+  int64_t cnext = 0, cend = 0;  // the warp's claimed slots [cnext, cend) in counter hw's space
+  // Endpoints are loaded one iteration ahead.
+  int64_t e = (blockIdx.x * 8 + wid) * 2 + half;
+  int2 nxy = e < E ? ((const int2 *)everts)[e] : make_int2(0, 0);
+  for (; e - half < E; e += nwarps * 2) {
     const bool live = e < E;
-    int x = 0, y = 0, b = 0;
-    if (live) {
-      const int2 xy = ((const int2 *)everts)[e];
-      x = xy.x;
-      y = xy.y;
-      b = (int)((uint32_t)e / (uint32_t)sx.B);  // e < E < 2^31
-    }
+    const int x = nxy.x, y = nxy.y;
+    const int b = live ? (int)((uint32_t)e / (uint32_t)sx.B) : 0;  // e < E < 2^31
+    if (e + nwarps * 2 < E) nxy = ((const int2 *)everts)[e + nwarps * 2];
     // This lane's words [w0, w0 + K) of both rows (zero before the first
     // snapshot and past Wp), and its delta words cleared.
     const int w0 = s16 * K;
@@ -1468,14 +1472,19 @@ static __global__ void __launch_bounds__(256) k_tri_gen_me(const int32_t *everts
       if (s16 >= d) inc += v;
     }
     if constexpr (CL) {
-      // The half-warps' totals; one claim per warp for both edges.
+      // The half-warps' totals; a new claim when the warp's slots run short.
       const int t0 = __shfl_sync(0xffffffffu, inc, 15), t1 = __shfl_sync(0xffffffffu, inc, 31);
-      const int hw = (int)((blockIdx.x * 8 + wid) % CLAIM_CTRS);
-      uint32_t base = 0;
-      if (l == 0 && t0 + t1 > 0) base = atomicAdd(cb.ctr + hw * 32, (uint32_t)(t0 + t1));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      const bool fits = (int64_t)base + t0 + t1 <= cb.sub_cap;
-      const int64_t hb = (int64_t)hw * cb.sub_cap + base + (half ? t0 : 0);
+      const int need = t0 + t1;
+      if (cnext + need > cend) {
+        const int len = max(need, cb.chunk);
+        uint32_t base = 0;
+        if (l == 0) base = atomicAdd(cb.ctr + hw * 32, (uint32_t)len);
+        cnext = __shfl_sync(0xffffffffu, base, 0);
+        cend = cnext + len;
+      }
+      const bool fits = cend <= cb.sub_cap;
+      const int64_t hb = (int64_t)hw * cb.sub_cap + cnext + (half ? t0 : 0);
+      cnext += need;
       if (live && s16 == 0) {
         cb.tcnt[e] = half ? t1 : t0;
         cb.kpos[e] = (int32_t)hb;
