@@ -1714,22 +1714,16 @@ static __global__ void __launch_bounds__(256) k_tri_final(const uint64_t *tkeys,
 // stores).
 // Triangle {x, y, z} with largest edge e = (x, y): sorted vertices and the
 // ascending order indices of its faces.
-// npx, npy: nbr_ptr[x], nbr_ptr[y].
-__device__ __forceinline__ void tri_final_xyzn(int32_t e, int x, int y, int z, int32_t npx, int32_t npy,
-                                               const EdgeIndex &ex, int32_t *v, int32_t *r) {
+__device__ __forceinline__ void tri_final_xyz(int32_t e, int x, int y, int z, const EdgeIndex &ex, int32_t *v,
+                                              int32_t *r) {
   const int2 px = ex.adjx[(int64_t)x * ex.W + (z >> 5)], py = ex.adjx[(int64_t)y * ex.W + (z >> 5)];
   const uint32_t below = (1u << (z & 31)) - 1u;
-  const int32_t oxz = ex.nbr_ord[npx + px.y + __popc((uint32_t)px.x & below)];
-  const int32_t oyz = ex.nbr_ord[npy + py.y + __popc((uint32_t)py.x & below)];
+  const int32_t oxz = ex.nbr_ord[ex.nbr_ptr[x] + px.y + __popc((uint32_t)px.x & below)];
+  const int32_t oyz = ex.nbr_ord[ex.nbr_ptr[y] + py.y + __popc((uint32_t)py.x & below)];
   if (z < x) { v[0] = z; v[1] = x; v[2] = y; }
   else if (z < y) { v[0] = x; v[1] = z; v[2] = y; }
   else { v[0] = x; v[1] = y; v[2] = z; }
   r[0] = min(oxz, oyz); r[1] = max(oxz, oyz); r[2] = e;
-}
-
-__device__ __forceinline__ void tri_final_xyz(int32_t e, int x, int y, int z, const EdgeIndex &ex, int32_t *v,
-                                              int32_t *r) {
-  tri_final_xyzn(e, x, y, z, ex.nbr_ptr[x], ex.nbr_ptr[y], ex, v, r);
 }
 
 __device__ __forceinline__ void tri_final_ez(int32_t e, int z, const int32_t *everts, const int32_t *egrade,
@@ -1886,16 +1880,39 @@ static __global__ void __launch_bounds__(256, 4) k_tri_final_grp(const uint16_t 
     for (int64_t base = o0 & ~int64_t(127); base < oend; base += 128) {
       uint32_t jzn[4] = {0u, 0u, 0u, 0u};
       if (base + 128 < oend) fetch(base + 128, jzn);
+      // The four positions' row words {adjacency word, prefix count} of x
+      // and y are all loaded before any order entry (eight loads in flight
+      // per lane at each level).  A position outside the range uses z = x:
+      // x is one of y's neighbours and has y above it, so both lookups stay
+      // inside the rows of x and y (the result is not stored).
       int32_t v[12], r[12], g[4];
+      int2 pxa[4], pya[4];
+      int32_t nxa[4], nya[4], za[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int64_t p = base + 32 * u + l;
         const bool ok = p >= o0 && p < oend;
         const int j = (int)(jzc[u] >> 16);
         const int xj = __shfl_sync(0xffffffffu, xy.x, j), yj = __shfl_sync(0xffffffffu, xy.y, j);
-        const int32_t nxj = __shfl_sync(0xffffffffu, npx, j), nyj = __shfl_sync(0xffffffffu, npy, j);
+        nxa[u] = __shfl_sync(0xffffffffu, npx, j);
+        nya[u] = __shfl_sync(0xffffffffu, npy, j);
         g[u] = __shfl_sync(0xffffffffu, ge, j);
-        if (ok) tri_final_xyzn((int32_t)(e0 + j), xj, yj, (int)(jzc[u] & 0xffffu), nxj, nyj, ex, v + 3 * u, r + 3 * u);
+        const int z = ok ? (int)(jzc[u] & 0xffffu) : xj;
+        za[u] = z;
+        pxa[u] = ex.adjx[(int64_t)xj * ex.W + (z >> 5)];
+        pya[u] = ex.adjx[(int64_t)yj * ex.W + (z >> 5)];
+        if (z < xj) { v[3 * u] = z; v[3 * u + 1] = xj; v[3 * u + 2] = yj; }
+        else if (z < yj) { v[3 * u] = xj; v[3 * u + 1] = z; v[3 * u + 2] = yj; }
+        else { v[3 * u] = xj; v[3 * u + 1] = yj; v[3 * u + 2] = z; }
+        r[3 * u + 2] = (int32_t)(e0 + j);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t below = (1u << (za[u] & 31)) - 1u;
+        const int32_t oxz = ex.nbr_ord[nxa[u] + pxa[u].y + __popc((uint32_t)pxa[u].x & below)];
+        const int32_t oyz = ex.nbr_ord[nya[u] + pya[u].y + __popc((uint32_t)pya[u].x & below)];
+        r[3 * u] = min(oxz, oyz);
+        r[3 * u + 1] = max(oxz, oyz);
       }
       if (base >= o0 && base + 128 <= oend) {
 #pragma unroll
