@@ -93,22 +93,27 @@ def method_bytes_per_step(cloud, counts):
     return int(cloud.points.nbytes) + 76 * E + 36 * T + 44 * T4
 
 
-def roofline_bytes(cloud, E, T, T4=0, ngrades=0, lex=False):
+def roofline_bytes(cloud, E, T, T4=0, ngrades=0, tri_order=1):
     """Per launch of each single-kernel phase: (method bytes, intermediate
     bytes).  Method bytes are the per-unit figures of method_bytes_per_step
     that the kernel moves; intermediates (sort keys, bitmaps) are listed
-    apart and never counted in `achieved`.  Max-edge triangle keys take 4 B
-    when the edge indices fit beside the vertex in 32 bits, else 8 B; lex
-    keys 8 B."""
+    apart and never counted in `achieved`.  tri_order is the build's
+    triangle path (vr_build_stats): 1 lex keys, 8 B; 2 max-edge keys, 4 B
+    when the edge indices fit beside the vertex in 32 bits, else 8 B; 3
+    max-edge third vertices in claimed space, 2 B per triangle plus each
+    edge's count and run start."""
     tet_read = 8 if (ngrades - 1).bit_length() <= 12 else 16
     n = cloud.n
     Wd = (n + 31) // 32
-    key = 8 if lex or E > 1 << (32 - max(1, (n - 1).bit_length())) else 4
+    if tri_order == 3:
+        key, key_e = 2, 8
+    else:
+        key, key_e = (8 if tri_order == 1 or E > 1 << (32 - max(1, (n - 1).bit_length())) else 4), 0
     return {
-        "tri_final": (36 * T, key * T),        # outputs 36 B; reads one key
+        "tri_final": (36 * T, key * T),        # outputs 36 B; reads one key (or third vertex)
         "tri_emit": (36 * T, 0),               # outputs 36 B, emitted at their final position
         "tri_lex_gen": (0, 8 * T),             # writes one 8 B key
-        "tri_gen": (0, key * T),               # max-edge order: writes one key, already in order
+        "tri_gen": (0, key * T + key_e * E),   # max-edge order: one key (or third vertex) per triangle
         "tri_sort.pass": (0, 16 * T),          # one digit pass over the keys
         "tri_sort.hist": (0, 8 * T),
         "edge_sort.pass": (16 * E, 0),         # the edge key: 8 B written + 8 B read
@@ -916,6 +921,7 @@ def single_cloud_leg(args, ranks, local):
         counts = c.counts()[0]
         st = c.stats()
         ngrades = st["ngrades"]
+        tri_order = st["tri_order"]
         del c
     torch.cuda.synchronize()
     simplices = sum(counts)
@@ -944,8 +950,7 @@ def single_cloud_leg(args, ranks, local):
     phases = read_phases()
     per_launch_bytes = roofline_bytes(cloud, counts[1] if len(counts) > 1 else 0,
                                       counts[2] if len(counts) > 2 else 0,
-                                      counts[3] if len(counts) > 3 else 0, ngrades,
-                                      lex="tri_lex_gen" in phases)
+                                      counts[3] if len(counts) > 3 else 0, ngrades, tri_order)
     # The roofline kernel: the longest single-kernel region that moves bytes
     # of the method's own (a sort's digit passes: several launches of the
     # same kernel, each timed).

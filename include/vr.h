@@ -96,6 +96,11 @@ typedef struct vr_build_stats {
   int64_t near_tie_edges;   /* float input: edges re-sorted by their FP64 value */
   double max_rel_dist_err;  /* float input: max |d_approx - d_fp64| / d_fp64
                                over kept edges of the fp32 first-pass value  */
+  int64_t tri_order;        /* how a single-cloud build ordered its triangles
+                               (no counterpart in the paper): 0 none or not
+                               reported, 1 lexicographic generation + stable
+                               grade sort, 2 max-edge order with counted keys,
+                               3 max-edge order in claimed key space          */
 } vr_build_stats;
 
 /* Build the filtered complex of one point cloud.

@@ -40,7 +40,8 @@ class DimView(ctypes.Structure):
 
 class BuildStats(ctypes.Structure):
     _fields_ = [("kept_edges", ctypes.c_int64), ("triangles", ctypes.c_int64), ("ngrades", ctypes.c_int64),
-                ("near_tie_edges", ctypes.c_int64), ("max_rel_dist_err", ctypes.c_double)]
+                ("near_tie_edges", ctypes.c_int64), ("max_rel_dist_err", ctypes.c_double),
+                ("tri_order", ctypes.c_int64)]
 
 
 _lib = None

@@ -980,6 +980,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   double mre = 0.0;
   memcpy(&mre, &hst->max_rel_err_bits, sizeof(double));
   res->stats.max_rel_dist_err = F ? mre : 0.0;
+  res->stats.tri_order = T == 0 ? 0 : lexm ? 1 : claimed ? 3 : 2;
   out.release_to(res->allocs);
   return VR_OK;
 }

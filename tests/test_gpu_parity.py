@@ -235,7 +235,7 @@ def test_both_enumeration_orders_on_one_cloud(torch):
     """The same torus cloud through both orders: lex order (ties, default cap)
     and, with a cap so small that few edges tie, max-edge order."""
     c = synth.config2(n=400)
-    check(torch, c.points, 2, c.maxrad)
+    assert check(torch, c.points, 2, c.maxrad)["stats"]["tri_order"] == 1
     check(torch, c.points, 2, 6.0)
 
 
@@ -264,9 +264,10 @@ def test_max_edge_key_space_modes(torch, mode):
     c = synth.config3(n=1200)
     vr.vr_set_tri_claim(mode)
     try:
-        check(torch, c.points, 2, c.maxrad)
+        g = check(torch, c.points, 2, c.maxrad)
     finally:
         vr.vr_set_tri_claim(0)
+    assert g["stats"]["tri_order"] == (3 if mode == 0 else 2)  # max-edge, claimed or counted
 
 
 def test_max_edge_claimed_ragged_chunks(torch):
