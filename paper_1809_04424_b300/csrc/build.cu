@@ -491,11 +491,7 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
   VR_TRY(ws.alloc(&rs.tkeys, E));
   VR_TRY(ws.alloc(&bs_e, scan_tmp_slots(E)));
   VR_TRY(ws.alloc(&nbr_ord, 2 * E));
-  int32_t *eidx = nullptr, *egd = nullptr;  // dense (i, j) -> order index / grade tables for small clouds
-  if (n <= DENSE_MAX_N && maxdim >= 2) {
-    VR_TRY(ws.alloc(&eidx, (int64_t)n * n));
-    VR_TRY(ws.alloc(&egd, (int64_t)n * n));
-  }
+  int32_t *eidx = nullptr, *egd = nullptr;  // dense (i, j) -> order index / grade tables (allocated below)
   VR_TRY(ws.alloc(&gstart, E + 2));
   VR_TRY(out.alloc(&everts, 2 * E));
   VR_TRY(out.alloc(&egrade, E));
@@ -579,6 +575,15 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     VR_TRY(ws.alloc(&kpos, E));
     VR_TRY(ws.alloc(&tz, tz_slots));
   }
+  // The dense order-index and grade tables serve the lex-order kernels and
+  // the counted max-edge count; on the claimed path nothing reads them, so
+  // the edge-grade kernel skips their two scattered writes per edge (if the
+  // device then takes lex order after all, its kernels look faces up
+  // through the neighbour CSR instead).
+  if (n <= DENSE_MAX_N && maxdim >= 2 && !claim) {
+    VR_TRY(ws.alloc(&eidx, (int64_t)n * n));
+    VR_TRY(ws.alloc(&egd, (int64_t)n * n));
+  }
   if (maxdim >= 2 && E > 0) {
     VR_TRY(ws.alloc(&tcnt, E));
     VR_TRY(ws.alloc(&toff, E + 1));
@@ -614,8 +619,9 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     }
     prof.begin("edge_grades");
     const int64_t egt = (E + EG_TILE - 1) / EG_TILE;
-    launch_dep(k_edge_grades<F>, (unsigned)egt, 256, 0, s, keys, d64, E, adj, adjpre, W, nbr_ptr, everts, egrade, ecol,
-               erow, gval, gstart, nbr_ord, eidx, egd, n, dmf ? 1 : 0, eg_lb, egt, st);
+    launch_dep(k_edge_grades<F>, (unsigned)egt, 256, 0, s, (const uint64_t *)keys, (const double *)d64, E,
+               (const int2 *)adjx, W, (const int32_t *)nbr_ptr, everts, egrade, ecol, erow, gval, gstart, nbr_ord,
+               eidx, egd, n, dmf ? 1 : 0, eg_lb, egt, st);
     count_launch();
     VR_CUDA(cudaGetLastError());
     prof.end();

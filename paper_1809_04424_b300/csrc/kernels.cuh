@@ -978,15 +978,20 @@ static __global__ void __launch_bounds__(RS_THREADS) k_repair_big(const int32_t 
 // block scan of those flags plus the earlier tiles' counts (look-back) is the
 // dense rank; then the outputs: verts, grade, colptr/rowidx ({i, j}), grade
 // values and group starts, the neighbour CSR scatter and the dense tables.  lb: the
-// tiles' zeroed status words followed by the ticket counter.
+// tiles' zeroed status words followed by the ticket counter.  Every load of
+// the outputs' inputs (keys, FP64 values, the endpoints' CSR offsets and
+// {row word, prefix count} pairs) is issued before the look-back, so its
+// latency overlaps warp 0's wait.
 constexpr int EG_TILE = 1024;
 template <bool F>
-__global__ void __launch_bounds__(256) k_edge_grades(const uint64_t *keys, const double *d64, int64_t E,
-                                                     const uint32_t *adj, const int32_t *adjpre, int W,
-                                                     const int32_t *nbr_ptr, int32_t *verts, int32_t *grade,
-                                                     int64_t *colptr, int32_t *rowidx, double *gval, int32_t *gstart,
-                                                     int32_t *nbr_ord, int32_t *eidx, int32_t *egd, int n, int key_f32,
-                                                     uint64_t *lb, int64_t ntiles, DevStatus *st) {
+__global__ void __launch_bounds__(256) k_edge_grades(const uint64_t *__restrict__ keys,
+                                                     const double *__restrict__ d64, int64_t E,
+                                                     const int2 *__restrict__ adjx, int W,
+                                                     const int32_t *__restrict__ nbr_ptr, int32_t *verts,
+                                                     int32_t *grade, int64_t *colptr, int32_t *rowidx, double *gval,
+                                                     int32_t *gstart, int32_t *nbr_ord, int32_t *eidx, int32_t *egd,
+                                                     int n, int key_f32, uint64_t *lb, int64_t ntiles,
+                                                     DevStatus *st) {
   pdl_entry();
   if (build_failed(st)) return;
   // Warp w of the tile takes the keys k0 + w * 32 * PER + 32 q + l (q < PER):
@@ -1000,18 +1005,44 @@ __global__ void __launch_bounds__(256) k_edge_grades(const uint64_t *keys, const
   __syncthreads();
   const int w = threadIdx.x >> 5, l = lane_id();
   const int64_t tile = tile_sh, kw = tile * EG_TILE + (int64_t)w * 32 * PER;
+  uint64_t kq[PER];
+  double dq[PER];
   uint32_t fm[PER];
   int wcnt = 0;
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int64_t k = kw + 32 * q + l;
+    kq[q] = k < E ? keys[k] : 0ull;
+    dq[q] = F && k < E ? d64[k] : 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int64_t k = kw + 32 * q + l;
     bool f = false;
     if (k < E) {
-      if constexpr (F) f = k == 0 ? (d64[0] != 0.0) : (d64[k] != d64[k - 1]);
-      else f = k == 0 ? ((keys[0] >> KEY_SHIFT) != 0) : ((keys[k] >> KEY_SHIFT) != (keys[k - 1] >> KEY_SHIFT));
+      if constexpr (F) f = k == 0 ? (dq[q] != 0.0) : (dq[q] != d64[k - 1]);
+      else f = k == 0 ? ((kq[q] >> KEY_SHIFT) != 0) : ((kq[q] >> KEY_SHIFT) != (keys[k - 1] >> KEY_SHIFT));
     }
     fm[q] = __ballot_sync(0xffffffffu, f);
     wcnt += __popc(fm[q]);
+  }
+  // The scatter's inputs: each endpoint's CSR offset and the {row word,
+  // prefix count} pair of the word holding the other endpoint.
+  int32_t npi[PER], npj[PER];
+  int2 ai[PER], aj[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int64_t k = kw + 32 * q + l;
+    const int i = key_i(kq[q]), j = key_j(kq[q]);
+    if (k < E) {
+      npi[q] = nbr_ptr[i];
+      npj[q] = nbr_ptr[j];
+      ai[q] = adjx[(int64_t)i * W + (j >> 5)];
+      aj[q] = adjx[(int64_t)j * W + (i >> 5)];
+    } else {
+      npi[q] = npj[q] = 0;
+      ai[q] = aj[q] = make_int2(0, 0);
+    }
   }
   if (l == 0) wpre[w] = wcnt;
   __syncthreads();
@@ -1019,9 +1050,7 @@ __global__ void __launch_bounds__(256) k_edge_grades(const uint64_t *keys, const
     const int64_t v = l < 8 ? wpre[l] : 0;
     const int64_t iv = warp_incl_scan(v);
     const int64_t tot = __shfl_sync(0xffffffffu, iv, 31);
-    int64_t pre = 0;
-    if (l == 0) pre = tile_lookback(lb, tile, tot, &st->flags);
-    pre = __shfl_sync(0xffffffffu, pre, 0);
+    const int64_t pre = tile_lookback(lb, tile, tot, &st->flags);
     if (l < 8) wpre[l] = pre + iv - v;
   }
   __syncthreads();
@@ -1034,19 +1063,19 @@ __global__ void __launch_bounds__(256) k_edge_grades(const uint64_t *keys, const
     gbase += __popc(fm[q]);
     if (k >= E) continue;
     const bool f = (fm[q] >> l) & 1u;
-    const uint64_t key = keys[k];
+    const uint64_t key = kq[q];
     const int i = key_i(key), j = key_j(key);
     ((int2 *)verts)[k] = make_int2(i, j);
     ((int2 *)rowidx)[k] = make_int2(i, j);
     colptr[k] = 2 * k;
     grade[k] = (int32_t)g;
     if (f) {
-      gval[g] = F ? d64[k]
+      gval[g] = F ? dq[q]
                   : key_f32 ? (double)__uint_as_float((uint32_t)(key >> KEY_SHIFT)) : (double)(key >> KEY_SHIFT);
       gstart[g] = (int32_t)k;
     }
-    nbr_ord[nbr_ptr[i] + bit_rank(adj + (int64_t)i * W, adjpre + (int64_t)i * W, j)] = (int32_t)k;
-    nbr_ord[nbr_ptr[j] + bit_rank(adj + (int64_t)j * W, adjpre + (int64_t)j * W, i)] = (int32_t)k;
+    nbr_ord[npi[q] + ai[q].y + __popc((uint32_t)ai[q].x & ((1u << (j & 31)) - 1u))] = (int32_t)k;
+    nbr_ord[npj[q] + aj[q].y + __popc((uint32_t)aj[q].x & ((1u << (i & 31)) - 1u))] = (int32_t)k;
     if (eidx) {
       eidx[(int64_t)i * n + j] = (int32_t)k;
       egd[(int64_t)i * n + j] = (int32_t)g;

@@ -714,32 +714,46 @@ __device__ __forceinline__ void khist_flush(KeyHistSmem &h, const KeyHist &kh) {
 // Decoupled look-back over tiles taken in ticket order: returns the sum of
 // the totals of every earlier tile.  status: one zeroed word per tile (flag
 // in the top two bits: 1 = the tile's own total, 2 = the inclusive total;
-// value below).  Called by one thread of the tile; every earlier tile's CTA
-// is already running (ticket order), so the wait ends; it is bounded anyway
-// (F_TIMEOUT in *err).
+// value below).  Every earlier tile's CTA is already running (ticket order),
+// so the wait ends; it is bounded anyway (F_TIMEOUT in *err).
 constexpr uint64_t LB_AGG = 1ull << 62, LB_INC = 2ull << 62, LB_VAL = (1ull << 62) - 1;
+// Called by a whole warp (the same tile and total in every lane): lane l
+// reads the status of tile k - l, so each step covers 32 earlier tiles; the
+// nearest tile that has published its inclusive count ends the walk.  A
+// step waits (bounded) only while a tile before that one has published
+// nothing.  Returns the exclusive prefix in every lane.
 __device__ __forceinline__ int64_t tile_lookback(uint64_t *status, int64_t tile, int64_t total, int32_t *err) {
+  const int l = lane_id();
   if (tile == 0) {
-    *(volatile uint64_t *)&status[0] = LB_INC | (uint64_t)total;
+    if (l == 0) *(volatile uint64_t *)&status[0] = LB_INC | (uint64_t)total;
     return 0;
   }
-  *(volatile uint64_t *)&status[tile] = LB_AGG | (uint64_t)total;
+  if (l == 0) *(volatile uint64_t *)&status[tile] = LB_AGG | (uint64_t)total;
   int64_t excl = 0, k = tile - 1;
   long spins = 0;
-  while (k >= 0) {
-    const uint64_t w = *(volatile const uint64_t *)&status[k];
-    if (w & (LB_AGG | LB_INC)) {
-      excl += (int64_t)(w & LB_VAL);
-      if (w & LB_INC) break;
-      --k;
-    } else if (++spins > RS_WAIT_LIMIT) {
-      atomicOr(err, F_TIMEOUT);
-      break;
-    } else {
+  for (;;) {
+    const int64_t idx = k - l;
+    const uint64_t w = idx >= 0 ? *(volatile const uint64_t *)&status[idx] : LB_INC;  // before tile 0: inclusive 0
+    const uint32_t inc = __ballot_sync(0xffffffffu, (w & LB_INC) != 0);
+    const uint32_t unset = __ballot_sync(0xffffffffu, (w & (LB_AGG | LB_INC)) == 0);
+    // Lanes up to the nearest inclusive one (all lanes if none).
+    const uint32_t upto = inc ? (2u << (__ffs(inc) - 1)) - 1u : 0xffffffffu;
+    if (unset & upto) {
+      if (++spins > RS_WAIT_LIMIT) {
+        if (l == 0) atomicOr(err, F_TIMEOUT);
+        break;
+      }
       __nanosleep(32);
+      continue;
     }
+    int64_t v = ((upto >> l) & 1u) ? (int64_t)(w & LB_VAL) : 0;
+#pragma unroll
+    for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    excl += v;
+    if (inc) break;
+    k -= 32;
   }
-  *(volatile uint64_t *)&status[tile] = LB_INC | (uint64_t)(excl + total);
+  if (l == 0) *(volatile uint64_t *)&status[tile] = LB_INC | (uint64_t)(excl + total);
   return excl;
 }
 

@@ -254,6 +254,17 @@ def test_max_edge_key_widths(torch, width):
     assert E >= (1 << 15) and 2 * E >= 1200 * ((1200 + 31) // 32)
 
 
+def test_float_ties_lex_order_without_dense_tables(torch):
+    """The 1000-point torus cloud as float32: its squared distances are
+    integers, so most edges tie.  The host, seeing float input with dense
+    rows, takes the claimed max-edge path and leaves out the dense order
+    tables; the device finds the ties and takes lex order, whose kernels then
+    look faces up through the neighbour CSR.  Every output in full."""
+    c = synth.config2()
+    g = check(torch, c.points.astype(np.float32), 2, c.maxrad)
+    assert g["stats"]["tri_order"] == 1 and g["counts"][2] > 100000
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_max_edge_key_space_modes(torch, mode):
     """The 1200-point float cloud (max-edge order) with its keys in claimed
