@@ -692,11 +692,15 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
     prof.begin("tri_count");
     const EdgeIndex exc{adjx, adj, adjpre, nbr_ptr, nbr_ord, eidx, egd, egrade, W, n};
     const int me_claimed = claim ? 1 : 0;
+    // After the claiming generator the count only has work in lex order (a
+    // device decision, rare there): two CTAs per SM, grid-stride, instead of
+    // a CTA per 64 edges that would mostly launch to return.
+    const unsigned gcnt = claim ? grid_for(E, 8, 2) : grid_for(E, 8, 32);
     if (eidx)
-      launch_dep(k_tri_count<true>, grid_for(E, 8, 32), 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
+      launch_dep(k_tri_count<true>, gcnt, 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
                  nbr_ord, st, tcnt, force_lex, exc, (const int64_t *)lex_ptr, sparse_rows, sx, me_claimed);
     else
-      launch_dep(k_tri_count<false>, grid_for(E, 8, 32), 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
+      launch_dep(k_tri_count<false>, gcnt, 256, 0, s, everts, lexe, E, adj, adjpre, W, nbr_ptr,
                  nbr_ord, st, tcnt, force_lex, exc, (const int64_t *)lex_ptr, sparse_rows, sx, me_claimed);
     count_launch(2);
     VR_TRY((scan_exclusive<int32_t, int64_t>(tcnt, toff, E, bs_e, s)));
