@@ -682,8 +682,9 @@ static vr_status build_impl(const void *dpts, int32_t n, int32_t d, vr_dtype dty
       // when the device finds lex mode).
       prof.begin("tri_snap");
       const int snap_threads = 32 * ((sx.Wp + 31) / 32);  // a warp per 32-word round of a row
-      launch_dep(k_snap_build, (unsigned)std::min<int64_t>(n, (int64_t)num_sms() * 32), snap_threads, 0, s, adj,
-                 adjpre, W, n, nbr_ptr, nbr_ord, st, force_lex, sx.S, sx.B, snap, sbl, sboff);
+      const size_t snap_smem = snap_build_smem(snap_threads / 32, sx.S);
+      launch_dep(k_snap_build, (unsigned)std::min<int64_t>(n, (int64_t)num_sms() * 32), snap_threads, snap_smem, s,
+                 adj, adjpre, W, n, nbr_ptr, nbr_ord, st, force_lex, sx.S, sx.B, snap, sbl, sboff);
       count_launch();
       VR_CUDA(cudaGetLastError());
       prof.end();

@@ -328,10 +328,21 @@ static __global__ void __launch_bounds__(256) k_rows_scan(const uint32_t *adj, i
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int l = lane_id();
   if (i < n) {
+    // The row's words are all loaded first (W <= 256: at most 8 per lane).
+    constexpr int RW = VR_MAX_POINTS / 32 / 32;
+    uint32_t words[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+      const int w = r * 32 + l;
+      words[r] = w < W ? adj[(int64_t)i * W + w] : 0u;
+    }
     int carry = 0, upc = 0;
-    for (int w0 = 0; w0 < W; w0 += 32) {
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+      const int w0 = r * 32;
+      if (w0 >= W) break;
       const int w = w0 + l;
-      const uint32_t word = w < W ? adj[(int64_t)i * W + w] : 0u;
+      const uint32_t word = words[r];
       const int c = __popc(word);
       const int inc = warp_incl_scan(c);
       if (w < W) {
@@ -350,9 +361,9 @@ static __global__ void __launch_bounds__(256) k_rows_scan(const uint32_t *adj, i
     if (l == 0) {
       deg[i] = carry;
       up[i] = upc;
+      __threadfence();  // the last CTA reads deg and up
     }
   }
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) ticket = atomicAdd(&st->rows_done, 1u);
   __syncthreads();
@@ -1193,8 +1204,15 @@ __host__ __device__ __forceinline__ int snap_stride(int W) { return (W + 3) & ~3
 // 32 * ceil(Wp / 32) <= 256): the CTA buckets v's neighbour entries by slice
 // (a shared histogram, one prefix, shared cursors; the order inside a bucket
 // is immaterial: buckets are filtered, not walked in order) and each warp
-// writes its round's words of v's snapshot rows.  Runs in max-edge mode only
-// (decided on the device, like the count kernel).
+// writes its round's words of v's snapshot rows.  The histogram pass keeps
+// the first SNAP_ORDC neighbour orders in shared memory, where the per-bit
+// pass finds them (no dependent L2 load per set bit).  Dynamic shared
+// memory: snap_build_smem(warps, S).  Runs in max-edge mode only (decided
+// on the device, like the count kernel).
+constexpr int SNAP_ORDC = 1024;
+__host__ __device__ __forceinline__ size_t snap_build_smem(int warps, int S) {
+  return (size_t)warps * (S - 1) * 32 * 4 + SNAP_ORDC * 4;
+}
 static __global__ void __launch_bounds__(256) k_snap_build(const uint32_t *adj, const int32_t *adjpre, int W, int n,
                                                            const int32_t *nbr_ptr, const int32_t *nbr_ord,
                                                            const DevStatus *st, int force_lex, int S, int64_t B,
@@ -1203,8 +1221,11 @@ static __global__ void __launch_bounds__(256) k_snap_build(const uint32_t *adj, 
   if (build_failed(st)) return;
   if (lex_mode(st->E, st->ngrades, force_lex)) return;
   __shared__ int32_t cur[SNAP_MAX_S + 1];
-  __shared__ uint32_t sw[8][SNAP_MAX_S - 1][32];  // per warp: lane l's word in each snapshot
+  extern __shared__ uint32_t snap_sm[];
+  const int nw = blockDim.x >> 5;
+  int32_t *ordc = (int32_t *)(snap_sm + (size_t)nw * (S - 1) * 32);
   const int l = lane_id(), wid = threadIdx.x >> 5;
+  uint32_t *sw = snap_sm + (size_t)wid * (S - 1) * 32;  // this warp: lane l's word in snapshot b at sw[(b - 1) * 32 + l]
   const int Wp = snap_stride(W);
   const int64_t nWp = (int64_t)n * Wp;
   const uint32_t Bu = (uint32_t)B;  // B <= E < 2^31: 32-bit divisions
@@ -1212,7 +1233,11 @@ static __global__ void __launch_bounds__(256) k_snap_build(const uint32_t *adj, 
     const int32_t ptr = nbr_ptr[v], deg = nbr_ptr[v + 1] - ptr;
     for (int b = threadIdx.x; b <= S; b += blockDim.x) cur[b] = 0;
     __syncthreads();
-    for (int k = threadIdx.x; k < deg; k += blockDim.x) atomicAdd(&cur[(uint32_t)nbr_ord[ptr + k] / Bu], 1);
+    for (int k = threadIdx.x; k < deg; k += blockDim.x) {
+      const int32_t o = nbr_ord[ptr + k];
+      if (k < SNAP_ORDC) ordc[k] = o;
+      atomicAdd(&cur[(uint32_t)o / Bu], 1);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       int32_t run = 0;
@@ -1230,17 +1255,17 @@ static __global__ void __launch_bounds__(256) k_snap_build(const uint32_t *adj, 
     if (wid * 32 < Wp) {
       uint32_t m = w < W ? row[w] : 0u;
       int32_t k = w < W ? pre[w] : 0;  // entry index of the word's lowest set bit
-      for (int b = 0; b < S - 1; ++b) sw[wid][b][l] = 0u;
+      for (int b = 0; b < S - 1; ++b) sw[b * 32 + l] = 0u;
       for (; m; m &= m - 1, ++k) {
         const int bit = __ffs(m) - 1;
-        const int32_t o = nbr_ord[ptr + k];
+        const int32_t o = k < SNAP_ORDC ? ordc[k] : nbr_ord[ptr + k];
         const int bb = (int)((uint32_t)o / Bu);
         const int32_t slot = atomicAdd(&cur[bb], 1);
         bl[ptr + slot] = ((uint64_t)(uint32_t)o << 32) | (uint32_t)(w * 32 + bit);
-        for (int b = bb + 1; b < S; ++b) sw[wid][b - 1][l] |= 1u << bit;
+        for (int b = bb + 1; b < S; ++b) sw[(b - 1) * 32 + l] |= 1u << bit;
       }
       if (w < Wp)
-        for (int b = 1; b < S; ++b) snap[(b - 1) * nWp + v * Wp + w] = sw[wid][b - 1][l];
+        for (int b = 1; b < S; ++b) snap[(b - 1) * nWp + v * Wp + w] = sw[(b - 1) * 32 + l];
     }
     __syncthreads();
   }
