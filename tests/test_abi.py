@@ -93,3 +93,35 @@ def test_sort_argument_checks(fn, n, lo, nb, status):
     buf = np.zeros(8, np.uint64)
     assert f(ctypes.c_void_p(buf.ctypes.data), n, lo, nb, None) == status
     assert f(None, 4, 0, 8, None) == vr.VR_ERR_ARG
+
+
+@pytest.mark.parametrize("fn,good,bad", [
+    ("vr_set_tri_claim", [0, 1, 2], [-1, 3, 8]),
+    ("vr_set_tri_key_width", [0, 8], [4, -1, 2]),
+])
+def test_process_wide_mode_setters(fn, good, bad):
+    """The triangle-path setters accept their documented modes and reject
+    any other value with VR_ERR_ARG, on the host (no device work); the
+    automatic mode is left in place."""
+    f = getattr(vr.lib(), fn)
+    f.argtypes = [ctypes.c_int32]
+    f.restype = ctypes.c_int
+    try:
+        for v in good:
+            assert f(v) == vr.VR_OK, (fn, v)
+        for v in bad:
+            assert f(v) == vr.VR_ERR_ARG, (fn, v)
+    finally:
+        assert f(0) == vr.VR_OK
+
+
+def test_build_stats_layout_matches_header():
+    """The binding's vr_build_stats mirror has the header's fields in order
+    (five 8-byte fields and the triangle path), so the C struct and the
+    ctypes one agree."""
+    hdr = open(os.path.join(ROOT, "include", "vr.h")).read()
+    body = re.search(r"typedef struct vr_build_stats \{(.*?)\} vr_build_stats;", hdr, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(?:int64_t|double)\s+(\w+);", body)
+    assert fields == [f for f, _ in vr.BuildStats._fields_]
+    assert ctypes.sizeof(vr.BuildStats) == 8 * len(fields)
