@@ -307,6 +307,13 @@ def test_max_edge_wide_rows(torch, n):
     E = len(g[1]["grade"])
     assert 2 * E >= n * ((n + 31) // 32)  # dense rows: max-edge order
     assert (E > 1 << 19) == (n == 6200)
+    # The host takes claimed key space while the wedge-bound buffer (T_wedge
+    # keys of 4 B, or 8 B when the edge index does not fit beside the vertex)
+    # stays within 1 GB, else the counted path.
+    deg = np.bincount(g[1]["verts"].ravel(), minlength=n).astype(np.int64)
+    t_wedge = int((deg * (deg - 1) // 2).sum()) // 3 + 1
+    key_bytes = 4 if E <= 1 << (32 - (n - 1).bit_length()) else 8
+    assert g["stats"]["tri_order"] == (3 if t_wedge * key_bytes <= 1 << 30 else 2)
 
 
 @pytest.mark.parametrize("maxdim", [2, 1])
@@ -316,6 +323,7 @@ def test_config3_gaussian_mixture_full(torch, maxdim):
     c = synth.config3(maxdim=maxdim)
     g = check(torch, c.points, maxdim, c.maxrad)
     assert g["stats"]["max_rel_dist_err"] <= 1e-6
+    assert g["stats"]["tri_order"] == (3 if maxdim == 2 else 0)  # max-edge order, claimed key space
 
 
 @pytest.mark.parametrize("seed", [1, 2])
