@@ -326,6 +326,20 @@ def test_config3_gaussian_mixture_full(torch, maxdim):
     assert g["stats"]["tri_order"] == (3 if maxdim == 2 else 0)  # max-edge order, claimed key space
 
 
+def test_config3_counted_path_full(torch):
+    """The full 4000-point float cloud through the counted max-edge path
+    (triangle count, scan, generator at the scanned offsets, key-reading final
+    write, dense order tables): every output bit-exact, as on the claimed
+    path."""
+    c = synth.config3()
+    vr.vr_set_tri_claim(1)
+    try:
+        g = check(torch, c.points, 2, c.maxrad)
+    finally:
+        vr.vr_set_tri_claim(0)
+    assert g["stats"]["tri_order"] == 2
+
+
 @pytest.mark.parametrize("seed", [1, 2])
 def test_float_wide_dynamic_range(torch, seed):
     """Coordinates spanning many binades, zeros included: the integer
